@@ -1,0 +1,32 @@
+"""Plain FP64 CPU oracle for the sparsifying-preconditioned Lippmann-Schwinger solve.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct restatement of
+the method of L. Ying, "Sparsifying Preconditioner for the Lippmann-Schwinger Equation"
+(arXiv:1408.4495) that the CUDA library is checked against.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs of
+``bench.py`` may import it.  It shares no code with ``paper_1408_4495_gb300`` and never
+imports it; inputs (media, directions) are passed in as arrays.
+
+Every function cites the passage of the paper it follows (section / equation).  Readings
+taken where the paper is silent are stated in the docstrings and listed in the design doc.
+
+Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
+
+* ``kernel_table`` / ``green`` (t != 0): Helmholtz-equation residual of the table away
+  from the origin; large-argument asymptotics.                                 pinned
+* ``k0_weight``: radial quadrature of the Green's function over the equal-area disk /
+  equal-volume ball (scipy.integrate), independent of the closed form.          pinned
+* ``apply_K_fft``: direct O(N^2) summation of the definition (Sec. 2.1).       pinned
+* ``stencil``: optimality against random unit vectors, Gram-matrix eigenvector route
+  at small n, mirror/dihedral symmetry, |alpha| = 1.                            pinned
+* ``assemble`` + ``Preconditioner``: m = 0 gives P = I exactly (M = [A;B]); the
+  sparse LU equals a dense solve of M; ND order is a permutation whose separators
+  disconnect the two halves.                                                    pinned
+* ``gmres_right``: dense solve of (I + K omega^2 m) u = g at n <= 32.          pinned
+* whole discrete solve: Mie series of a constant-contrast disk, error decreasing
+  with n (``mie.py``).                                                          pinned
+* the sparsity claim A K ~ C (Sec. 2.2): reported ratio only, the paper prints
+  no magnitude.                                                  parity unpinned
+"""
+
+from .ls_oracle import *  # noqa: F401,F403

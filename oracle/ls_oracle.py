@@ -1,0 +1,485 @@
+"""FP64 CPU oracle: every step of the sparsifying-preconditioned LS solve, written from the paper.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``): the product path never imports this.
+
+Notation follows L. Ying, arXiv:1408.4495.  Grid: ``x_i = i h`` with ``i in {1..n}^d`` and
+``h = 1/(n+1)`` (Sec. 2.1; the Laplace tables of Sec. 5 fix h = 1/(n+1)).  Arrays use the
+0-based index ``a = i - 1`` in C order (last index fastest).  Offsets ``t`` are integer
+d-tuples.  Complex numbers are numpy complex128 throughout.
+"""
+
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import scipy.fft
+import scipy.linalg
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
+import scipy.special as sp
+
+__all__ = [
+    "grid_h", "grid_coords", "green", "k0_weight", "kernel_value", "kernel_table",
+    "dense_K", "apply_K_direct", "apply_K_fft", "apply_operator", "plane_wave", "rhs",
+    "point_class", "class_mu", "class_far_set", "stencil", "all_stencils",
+    "assemble", "nd_order", "Preconditioner", "gmres_right", "solve",
+    "check_buffer", "sparsity_ratio",
+]
+
+
+# ----------------------------------------------------------------------------------------
+# Sec. 2.1: grid, Green's function, Nystrom weights
+# ----------------------------------------------------------------------------------------
+
+def grid_h(n: int) -> float:
+    """Step size h = 1/(n+1): n interior points per dimension of the unit cube (Sec. 2.1)."""
+    return 1.0 / (n + 1)
+
+
+def grid_coords(n: int, d: int):
+    """Coordinates x_i = i h, i = 1..n, as d arrays of shape (n,)*d (Sec. 2.1)."""
+    x = (np.arange(n, dtype=np.float64) + 1.0) * grid_h(n)
+    return np.meshgrid(*([x] * d), indexing="ij")
+
+
+def green(d: int, omega: float, r):
+    """Free-space Green's function of -(Delta + omega^2) at distance r > 0 (Sec. 1):
+    2D ``(i/4) H_0^(1)(omega r)``, 3D ``exp(i omega r) / (4 pi r)``."""
+    r = np.asarray(r, dtype=np.float64)
+    if d == 2:
+        return 0.25j * sp.hankel1(0, omega * r)
+    if d == 3:
+        return np.exp(1j * omega * r) / (4.0 * np.pi * r)
+    raise ValueError("d must be 2 or 3")
+
+
+def k0_weight(d: int, omega: float, h: float) -> complex:
+    """Weight k_0 of the singular point (Sec. 2.1).
+
+    The paper states only that k_0 comes from a one-point correction of the trapezoidal
+    rule.  Reading taken here: k_0 is the exact integral of G over the disk (2D) / ball
+    (3D) centred at the origin whose area / volume equals the cell, h^d.
+
+    2D, a = h / sqrt(pi):  int_0^a r H_0(omega r) dr = (a/omega) H_1(omega a) + 2i/(pi omega^2)
+        so k_0 = (i pi a / (2 omega)) H_1^(1)(omega a) - 1/omega^2.
+    3D, a = h (3/(4 pi))^(1/3):  int_0^a r e^{i omega r} dr
+        so k_0 = e^{i omega a}(1/omega^2 - i a/omega) - 1/omega^2.
+    """
+    if d == 2:
+        a = h / math.sqrt(math.pi)
+        return complex(1j * math.pi * a / (2.0 * omega) * sp.hankel1(1, omega * a) - 1.0 / omega**2)
+    if d == 3:
+        a = h * (3.0 / (4.0 * math.pi)) ** (1.0 / 3.0)
+        return complex(np.exp(1j * omega * a) * (1.0 / omega**2 - 1j * a / omega) - 1.0 / omega**2)
+    raise ValueError("d must be 2 or 3")
+
+
+def kernel_value(d: int, omega: float, h: float, t) -> np.ndarray:
+    """k_t = G(h t) h^d for t != 0 and k_0 at t = 0 (Sec. 2.1, 2D and 3D forms).
+
+    ``t`` is an integer array of shape (..., d)."""
+    t = np.asarray(t, dtype=np.float64)
+    r = h * np.sqrt(np.sum(t * t, axis=-1))
+    out = np.empty(r.shape, dtype=np.complex128)
+    nz = r > 0
+    out[nz] = green(d, omega, r[nz]) * h**d
+    out[~nz] = k0_weight(d, omega, h)
+    return out
+
+
+def kernel_table(n: int, d: int, omega: float) -> np.ndarray:
+    """Table of k_t for every t in (-n, n)^d, shape (2n-1,)*d, entry t stored at t + n - 1.
+
+    These are all the offsets i - j between two grid points (Sec. 2.1, eq. lsd)."""
+    t1 = np.arange(-(n - 1), n)
+    T = np.stack(np.meshgrid(*([t1] * d), indexing="ij"), axis=-1)
+    return kernel_value(d, omega, grid_h(n), T)
+
+
+# ----------------------------------------------------------------------------------------
+# Sec. 2.1, eq. (lsd)/(lso): the discrete operator I + K omega^2 m
+# ----------------------------------------------------------------------------------------
+
+def _flat_index_offsets(n: int, d: int) -> np.ndarray:
+    """All grid multi-indices in C order, shape (N, d)."""
+    return np.stack(np.meshgrid(*([np.arange(n)] * d), indexing="ij"), axis=-1).reshape(-1, d)
+
+
+def dense_K(ktab: np.ndarray, n: int, d: int) -> np.ndarray:
+    """Dense N x N matrix K(i, j) = k_{i-j} (Sec. 2.1, after eq. lso).  Small n only."""
+    idx = _flat_index_offsets(n, d)
+    diff = idx[:, None, :] - idx[None, :, :] + (n - 1)
+    return ktab[tuple(diff[..., a] for a in range(d))]
+
+
+def apply_K_direct(ktab: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """(K v)_i = sum_j k_{i-j} v_j by direct summation of the definition (eq. lsd)."""
+    n, d = v.shape[0], v.ndim
+    return (dense_K(ktab, n, d) @ v.reshape(-1)).reshape(v.shape)
+
+
+def apply_K_fft(ktab: np.ndarray, v: np.ndarray, workers: int | None = None) -> np.ndarray:
+    """(K v) via the FFT (Sec. 1, third remark): the (2n)^d circulant embedding of k.
+
+    k_t is placed at index t mod 2n for t in (-n, n)^d and the entries whose index has a
+    component equal to n are zero; v is zero-padded to (2n)^d; the convolution restricted
+    to the first n entries per dimension is exactly sum_j k_{i-j} v_j."""
+    n, d = v.shape[0], v.ndim
+    L = 2 * n
+    kpad = np.zeros((L,) * d, dtype=np.complex128)
+    src = np.arange(-(n - 1), n)
+    dst = src % L
+    kpad[np.ix_(*([dst] * d))] = ktab
+    vpad = np.zeros((L,) * d, dtype=np.complex128)
+    vpad[(slice(0, n),) * d] = v
+    c = scipy.fft.ifftn(scipy.fft.fftn(kpad, workers=workers) * scipy.fft.fftn(vpad, workers=workers),
+                        workers=workers)
+    return c[(slice(0, n),) * d]
+
+
+def apply_operator(ktab, omega: float, m: np.ndarray, u: np.ndarray, direct: bool = False,
+                   workers: int | None = None) -> np.ndarray:
+    """(I + K omega^2 m) u, eq. (lso)."""
+    v = omega**2 * m * u
+    Kv = apply_K_direct(ktab, v) if direct else apply_K_fft(ktab, v, workers)
+    return u + Kv
+
+
+def plane_wave(n: int, d: int, omega: float, direction) -> np.ndarray:
+    """Incident plane wave u_I(x_i) = exp(i omega x_i . dir) on the grid (Sec. 3.3)."""
+    X = grid_coords(n, d)
+    phase = sum(X[a] * float(direction[a]) for a in range(d))
+    return np.exp(1j * omega * phase)
+
+
+def rhs(ktab, omega: float, m: np.ndarray, direction, direct: bool = False,
+        workers: int | None = None) -> np.ndarray:
+    """Discrete right-hand side g = K(-omega^2 m u_I) (eq. ls and eq. lsd).
+
+    Reading: the paper calls g "the discretized value" of G * (-omega^2 m u_I); the same
+    Nystrom weights k_t as the operator are used."""
+    n, d = m.shape[0], m.ndim
+    uI = plane_wave(n, d, omega, direction)
+    v = -(omega**2) * m * uI
+    return apply_K_direct(ktab, v) if direct else apply_K_fft(ktab, v, workers)
+
+
+def check_buffer(m: np.ndarray, b: int) -> bool:
+    """m must vanish on the b+1 outermost layers of grid points (Sec. 2.1 and Sec. 3.1:
+    a buffer of b layers next to the boundary layer).  Returns True when it does."""
+    n, d = m.shape[0], m.ndim
+    w = b + 1
+    for a in range(d):
+        lo = [slice(None)] * d
+        hi = [slice(None)] * d
+        lo[a] = slice(0, w)
+        hi[a] = slice(n - w, n)
+        if np.any(m[tuple(lo)] != 0) or np.any(m[tuple(hi)] != 0):
+            return False
+    return True
+
+
+# ----------------------------------------------------------------------------------------
+# Sec. 2.2 and Sec. 3.1: the sparsifying stencils A, B and C
+# ----------------------------------------------------------------------------------------
+
+def point_class(n: int, d: int) -> np.ndarray:
+    """Class of every grid point, shape (n,)*d + (d,), entries in {-1, 0, +1} per dimension.
+
+    -1: the point lies on the low face of that dimension (index 0), +1 on the high face
+    (index n-1), 0 otherwise.  Class (0,..,0) is an interior point in the sense of Sec. 2.2
+    (all of mu(i) lies in Omega); every other class is a boundary point."""
+    idx = np.arange(n)
+    c1 = np.where(idx == 0, -1, np.where(idx == n - 1, 1, 0))
+    C = np.meshgrid(*([c1] * d), indexing="ij")
+    return np.stack(C, axis=-1)
+
+
+def class_mu(cls) -> list:
+    """Translated neighbourhood mu(0) of a class (Sec. 2.2: ||i-j||_inf <= 1 inside Omega).
+
+    Per dimension the offsets are {0, 1} on the low face, {-1, 0} on the high face and
+    {-1, 0, 1} elsewhere.  Listed in C order."""
+    per = [(0, 1) if c < 0 else (-1, 0) if c > 0 else (-1, 0, 1) for c in cls]
+    return [tuple(t) for t in itertools.product(*per)]
+
+
+def class_far_set(n: int, b: int, cls) -> np.ndarray:
+    """The far set of a class (Sec. 3.1), shape (F, d).
+
+    Interior (all zero): I_n = {-n < j_k < n} minus mu(0)  (eq. Fmin).
+    Otherwise the product over dimensions of -n < j < -b (high face), b < j < n (low face,
+    the mirror image) and -n < j < n (no face): E_n and C_n in 2D (eqs. Emin, Cmin) and
+    F_n, E_n, C_n in 3D.  Reading: the 3D corner is printed at x_1 = 2; it is read as
+    x_1 = 1 like every other face in that list."""
+    d = len(cls)
+    if all(c == 0 for c in cls):
+        r = np.arange(-(n - 1), n)
+        J = np.stack(np.meshgrid(*([r] * d), indexing="ij"), axis=-1).reshape(-1, d)
+        keep = np.max(np.abs(J), axis=1) > 1
+        return J[keep]
+    per = []
+    for c in cls:
+        if c > 0:
+            per.append(np.arange(-(n - 1), -b))
+        elif c < 0:
+            per.append(np.arange(b + 1, n))
+        else:
+            per.append(np.arange(-(n - 1), n))
+    return np.stack(np.meshgrid(*per, indexing="ij"), axis=-1).reshape(-1, d)
+
+
+def stencil(n: int, d: int, omega: float, b: int, cls, return_sigma: bool = False):
+    """alpha for one class: min over |alpha| = 1 of |alpha K(mu(0), far)| (eqs. Fmin, Emin, Cmin).
+
+    With K(mu(0), far) = U S V^*, alpha = U(:, |mu(0)|)^*, the conjugate of the left singular
+    vector of the smallest singular value.  alpha is determined up to a unit factor;
+    reading: it is normalised so that its centre coefficient (offset 0) is real and positive.
+    Returns (mu, alpha[, singular values])."""
+    h = grid_h(n)
+    mu = class_mu(cls)
+    far = class_far_set(n, b, cls)
+    T = np.array(mu)[:, None, :] - far[None, :, :]          # K(t, j) = k_{t - j}
+    Kmat = kernel_value(d, omega, h, T)
+    U, S, _ = np.linalg.svd(Kmat, full_matrices=False)
+    if S[-1] > 0 and S[-2] / S[-1] < 1.0 + 1e-8:
+        raise ValueError("smallest singular value of K(mu, far) is not simple")
+    alpha = np.conj(U[:, -1])
+    centre = mu.index((0,) * d)
+    ph = alpha[centre] / abs(alpha[centre])
+    alpha = alpha / ph
+    if return_sigma:
+        return mu, alpha, S
+    return mu, alpha
+
+
+def all_stencils(n: int, d: int, omega: float, b: int = 2):
+    """alpha for all 3^d classes and C(i, mu(i)) = alpha K(mu(0), mu(0)) for the interior class.
+
+    Sec. 2.2 defines C only for the interior rows (A); boundary rows of the preconditioner
+    matrix are B alone (eq. PC).  Returns dict cls -> (mu, alpha), and (mu0, c)."""
+    h = grid_h(n)
+    out = {}
+    for cls in itertools.product((-1, 0, 1), repeat=d):
+        out[cls] = stencil(n, d, omega, b, cls)
+    mu0, a0 = out[(0,) * d]
+    T = np.array(mu0)[:, None, :] - np.array(mu0)[None, :, :]
+    Kmm = kernel_value(d, omega, h, T)                         # K(mu, mu)(t, t') = k_{t - t'}
+    c = a0 @ Kmm                                               # C(0, t') = sum_t alpha_t k_{t-t'}
+    return out, (mu0, c)
+
+
+def assemble(n: int, d: int, omega: float, m: np.ndarray, sten, cint):
+    """Sparse M = [A + C omega^2 m ; B] and S = [A ; B] (eqs. PC, ABop).
+
+    Rows are kept in grid order rather than stacked interior-then-boundary; the
+    preconditioner M^{-1} S is unchanged by a common row permutation.  Row i:
+      S(i, i+t) = alpha_cls(i)(t)
+      M(i, i+t) = alpha_cls(i)(t) + [i interior] c(t) omega^2 m_{i+t}."""
+    N = n**d
+    cls_arr = point_class(n, d)
+    idx = np.arange(N).reshape((n,) * d)
+    rows, cols, sv, mv = [], [], [], []
+    mu0, c = cint
+    cmap = dict(zip(mu0, c))
+    w2m = omega**2 * m
+    for cls, (mu, alpha) in sten.items():
+        mask = np.all(cls_arr == np.array(cls), axis=-1)
+        pts = np.argwhere(mask)                       # (P, d)
+        if len(pts) == 0:
+            continue
+        interior = all(ci == 0 for ci in cls)
+        for t, a in zip(mu, alpha):
+            q = pts + np.array(t)
+            r = idx[tuple(pts.T)]
+            col = idx[tuple(q.T)]
+            rows.append(r)
+            cols.append(col)
+            sv.append(np.full(len(r), a))
+            if interior:
+                mv.append(a + cmap[t] * w2m[tuple(q.T)])
+            else:
+                mv.append(np.full(len(r), a))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    S = sps.csr_matrix((np.concatenate(sv), (rows, cols)), shape=(N, N))
+    M = sps.csr_matrix((np.concatenate(mv), (rows, cols)), shape=(N, N))
+    return M, S
+
+
+# ----------------------------------------------------------------------------------------
+# Sec. 2.2 / Sec. 3.2: nested dissection and the sparse solve of the preconditioner
+# ----------------------------------------------------------------------------------------
+
+def nd_order(n: int, d: int, leaf: int = 16) -> np.ndarray:
+    """Geometric nested-dissection elimination order of the grid (Sec. 2.2, George 1973).
+
+    A box is split along its longest side by a one-point-thick separator (the 3^d
+    stencil couples only points at infinity-distance <= 1, so a slab of width 1 separates
+    the two halves); the halves are ordered first, the separator last.  Boxes with at
+    most ``leaf`` points are not split further."""
+    idx = np.arange(n**d).reshape((n,) * d)
+    out = []
+
+    def rec(lo, hi):
+        size = [hi[a] - lo[a] for a in range(d)]
+        if min(size) <= 0:
+            return
+        if int(np.prod(size)) <= leaf or max(size) < 3:
+            out.append(idx[tuple(slice(lo[a], hi[a]) for a in range(d))].reshape(-1))
+            return
+        ax = int(np.argmax(size))
+        mid = (lo[ax] + hi[ax]) // 2
+        hi1 = list(hi); hi1[ax] = mid
+        lo2 = list(lo); lo2[ax] = mid + 1
+        rec(lo, hi1)
+        rec(lo2, hi)
+        sl = [slice(lo[a], hi[a]) for a in range(d)]
+        sl[ax] = slice(mid, mid + 1)
+        out.append(idx[tuple(sl)].reshape(-1))
+
+    rec([0] * d, [n] * d)
+    return np.concatenate(out)
+
+
+class Preconditioner:
+    """u <= [A + C omega^2 m ; B]^{-1} [A ; B] g  (eq. PC).
+
+    The sparse system is factored once with SuperLU (partial pivoting, FP64) after the
+    symmetric nested-dissection permutation; each apply is one stencil product and one
+    pair of triangular solves."""
+
+    def __init__(self, M, S, n: int, d: int):
+        self.M, self.S = M, S
+        self.perm = nd_order(n, d)
+        self.iperm = np.empty_like(self.perm)
+        self.iperm[self.perm] = np.arange(len(self.perm))
+        Mp = M[self.perm][:, self.perm].tocsc()
+        self.lu = spla.splu(Mp, permc_spec="NATURAL")
+
+    def solve_M(self, r: np.ndarray) -> np.ndarray:
+        """M^{-1} r."""
+        return self.lu.solve(r[self.perm])[self.iperm]
+
+    def __call__(self, v: np.ndarray) -> np.ndarray:
+        return self.solve_M(self.S @ v)
+
+
+# ----------------------------------------------------------------------------------------
+# Sec. 3.3: GMRES with relative tolerance 1e-6
+# ----------------------------------------------------------------------------------------
+
+def gmres_right(apply_A, apply_P, g: np.ndarray, tol: float = 1e-6, restart: int = 50,
+                max_iter: int = 500):
+    """Right-preconditioned restarted GMRES (Saad, Iterative Methods, Alg. 9.5) for A u = g.
+
+    Reading: the paper names GMRES with relative tolerance 1e-6 but not the side of the
+    preconditioner; right preconditioning makes the monitored quantity the true relative
+    residual |g - A u| / |g|.  Modified Gram-Schmidt Arnoldi, complex Givens rotations.
+    x0 = 0.  One iteration = one apply of P and one apply of A.
+    Returns (u, iterations, relative residual history of the estimates)."""
+    g = np.asarray(g, dtype=np.complex128).reshape(-1)
+    N = g.size
+    x = np.zeros(N, dtype=np.complex128)
+    gnorm = np.linalg.norm(g)
+    hist = []
+    if gnorm == 0.0:
+        return x, 0, hist
+    total = 0
+    while True:
+        r = g - apply_A(x) if total > 0 else g.copy()
+        beta = np.linalg.norm(r)
+        if beta <= tol * gnorm or total >= max_iter:
+            break
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        cs = np.zeros(restart, dtype=np.float64)
+        sn = np.zeros(restart, dtype=np.complex128)
+        s = np.zeros(restart + 1, dtype=np.complex128)
+        s[0] = beta
+        k = 0
+        for j in range(restart):
+            z = apply_P(V[j])
+            w = apply_A(z)
+            Z.append(z)
+            total += 1
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            for i in range(j):
+                a, bb = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * bb
+                H[i + 1, j] = -np.conj(sn[i]) * a + cs[i] * bb
+            a, bb = H[j, j], H[j + 1, j]
+            rr = math.hypot(abs(a), abs(bb))
+            if abs(a) == 0.0:
+                cs[j], sn[j] = 0.0, 1.0
+            else:
+                cs[j] = abs(a) / rr
+                sn[j] = (a / abs(a)) * np.conj(bb) / rr
+            H[j, j] = cs[j] * a + sn[j] * bb
+            H[j + 1, j] = 0.0
+            s[j + 1] = -np.conj(sn[j]) * s[j]
+            s[j] = cs[j] * s[j]
+            k = j + 1
+            res = abs(s[j + 1])
+            hist.append(res / gnorm)
+            hn = np.linalg.norm(w)
+            if hn > 0:
+                V.append(w / hn)
+            if res <= tol * gnorm or total >= max_iter or hn == 0:
+                break
+        y = scipy.linalg.solve_triangular(H[:k, :k], s[:k])
+        for i in range(k):
+            x = x + y[i] * Z[i]
+        if total >= max_iter:
+            break
+    return x, total, hist
+
+
+def solve(n: int, d: int, omega: float, m: np.ndarray, directions, b: int = 2,
+          tol: float = 1e-6, restart: int = 50, max_iter: int = 500, workers=None,
+          precond: bool = True):
+    """The whole preconditioned solve for each incident direction (Secs. 2-3).
+
+    Returns dict with u (nrhs, n^d), iterations, true relative residuals, g."""
+    if not check_buffer(m, b):
+        raise ValueError("m must vanish within b+1 layers of the boundary")
+    ktab = kernel_table(n, d, omega)
+    sten, cint = all_stencils(n, d, omega, b)
+    M, S = assemble(n, d, omega, m, sten, cint)
+    P = Preconditioner(M, S, n, d)
+    shape = (n,) * d
+
+    def A(x):
+        return apply_operator(ktab, omega, m, x.reshape(shape), workers=workers).reshape(-1)
+
+    Pf = (lambda v: P(v)) if precond else (lambda v: v)
+    us, its, res, gs = [], [], [], []
+    for dr in directions:
+        g = rhs(ktab, omega, m, dr, workers=workers).reshape(-1)
+        u, it, _ = gmres_right(A, Pf, g, tol, restart, max_iter)
+        gn = np.linalg.norm(g)
+        res.append(np.linalg.norm(g - A(u)) / gn if gn > 0 else 0.0)
+        us.append(u)
+        its.append(it)
+        gs.append(g)
+    return dict(u=np.array(us), iters=its, resid=res, g=np.array(gs), P=P, ktab=ktab,
+                sten=sten, cint=cint)
+
+
+def sparsity_ratio(n: int, d: int, omega: float, b: int = 2) -> float:
+    """max over far j of |(A K)(i, j)| divided by max |C(i, mu(i))| for an interior row
+    (the approximation A K ~ C of Sec. 2.2).  Reported only: the paper prints no value."""
+    h = grid_h(n)
+    mu, alpha = stencil(n, d, omega, b, (0,) * d)
+    far = class_far_set(n, b, (0,) * d)
+    T = np.array(mu)[:, None, :] - far[None, :, :]
+    off = alpha @ kernel_value(d, omega, h, T)
+    T2 = np.array(mu)[:, None, :] - np.array(mu)[None, :, :]
+    on = alpha @ kernel_value(d, omega, h, T2)
+    return float(np.max(np.abs(off)) / np.max(np.abs(on)))

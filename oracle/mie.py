@@ -1,0 +1,49 @@
+"""Mie series for scattering of a plane wave by a constant-contrast disk (2D).
+
+TEST INFRASTRUCTURE ONLY: an independent closed-form solution of eq. (helm) used to pin the
+whole discrete solve of the oracle (Sec. 1, eq. helm / eq. ls; the paper itself prints no
+such check).
+
+Medium: m = m0 inside the disk |x - c| < R, 0 outside, so the wavenumber is
+k1 = omega sqrt(1 - m0) inside and k0 = omega outside.  Incident field exp(i omega x_1)
+= exp(i omega c_1) sum_n i^n J_n(k0 r) e^{i n theta}.  Continuity of the total field and of
+its radial derivative at r = R gives, per angular index n,
+    scattered outside:  c_n H_n(k0 r)
+    total inside:       a_n J_n(k1 r)
+    c_n = i^n [k1 J_n'(k1R) J_n(k0R) - k0 J_n'(k0R) J_n(k1R)]
+              / [k0 H_n'(k0R) J_n(k1R) - k1 J_n'(k1R) H_n(k0R)]
+    a_n = (i^n J_n(k0R) + c_n H_n(k0R)) / J_n(k1R)
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.special as sp
+
+
+def mie_disk_scattered(X1, X2, omega: float, m0: float, R: float, centre=(0.5, 0.5), nmax=None):
+    """Scattered field u (total minus incident, the unknown of eq. ls) at points (X1, X2)."""
+    k0 = omega
+    k1 = omega * np.sqrt(1.0 - m0)
+    if nmax is None:
+        nmax = int(k1 * R + 4.0 * (k1 * R) ** (1.0 / 3.0) + 20)
+    dx = X1 - centre[0]
+    dy = X2 - centre[1]
+    r = np.hypot(dx, dy)
+    th = np.arctan2(dy, dx)
+    inside = r < R
+    u = np.zeros(np.shape(X1), dtype=np.complex128)
+    pref = np.exp(1j * omega * centre[0])
+    for n in range(-nmax, nmax + 1):
+        jn0, jn1 = sp.jv(n, k0 * R), sp.jv(n, k1 * R)
+        djn0, djn1 = sp.jvp(n, k0 * R), sp.jvp(n, k1 * R)
+        hn0, dhn0 = sp.hankel1(n, k0 * R), sp.h1vp(n, k0 * R)
+        inn = 1j ** (n % 4)
+        cn = inn * (k1 * djn1 * jn0 - k0 * djn0 * jn1) / (k0 * dhn0 * jn1 - k1 * djn1 * hn0)
+        an = (inn * jn0 + cn * hn0) / jn1
+        e = np.exp(1j * n * th)
+        out = cn * sp.hankel1(n, k0 * r[~inside]) * e[~inside]
+        u[~inside] += pref * out
+        inn_field = an * sp.jv(n, k1 * r[inside]) - inn * sp.jv(n, k0 * r[inside])
+        u[inside] += pref * inn_field * e[inside]
+    return u

@@ -1,0 +1,150 @@
+"""Seeded synthetic inputs: media m(x) and incident directions for the solver's workloads.
+
+This module holds no arithmetic of the method.  It only draws the inputs (the medium
+sampled on the grid and the plane-wave directions) from seeded generators, so that the
+CUDA library and the CPU checker receive identical arrays.
+
+Grid convention: n points per dimension at x = i h, i = 1..n, h = 1/(n+1).
+
+The paper's media (Sec. 3.3: Gaussian bumps and smoothed cavities with the velocity
+c = (1-m)^(-1/2) between 2/3 and 1) do not have printed parameters; these recipes are
+stand-ins of the same shape:
+
+* ``cutoff``: C-infinity step so that m vanishes within 0.1 of the boundary of the unit cube.
+* ``bumps``: sum of Gaussian bumps A exp(-|x-c|^2 / (2 w^2)) times the cutoff.
+* ``smooth_noise``: white noise convolved with a Gaussian of width 4h, scaled to a given
+  max |m|, times the cutoff.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def grid_x(n: int) -> np.ndarray:
+    return (np.arange(n, dtype=np.float64) + 1.0) / (n + 1)
+
+
+def _smooth_step(t: np.ndarray) -> np.ndarray:
+    """0 for t <= 0, 1 for t >= 1, e^{-1/t} / (e^{-1/t} + e^{-1/(1-t)}) in between."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.where(t >= 1.0, 1.0, 0.0)
+    mid = (t > 0.0) & (t < 1.0)
+    tm = t[mid]
+    a = np.exp(-1.0 / tm)
+    b = np.exp(-1.0 / (1.0 - tm))
+    out[mid] = a / (a + b)
+    return out
+
+
+def cutoff(n: int, d: int, width: float = 0.1) -> np.ndarray:
+    x = grid_x(n)
+    c1 = _smooth_step((x - width) / width) * _smooth_step((1.0 - width - x) / width)
+    out = c1
+    for _ in range(d - 1):
+        out = np.multiply.outer(out, c1)
+    return out
+
+
+def bumps(n: int, d: int, amps, widths, centres) -> np.ndarray:
+    X = np.meshgrid(*([grid_x(n)] * d), indexing="ij")
+    m = np.zeros((n,) * d)
+    for A, w, c in zip(amps, widths, centres):
+        r2 = sum((X[a] - c[a]) ** 2 for a in range(d))
+        m += A * np.exp(-r2 / (2.0 * w * w))
+    return m * cutoff(n, d)
+
+
+def smooth_noise(n: int, d: int, seed: int, sigma_h: float = 4.0, max_abs: float = 0.2) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal((n,) * d)
+    # zero-padded (linear) convolution with a Gaussian of width sigma_h grid steps
+    L = 2 * n
+    k1 = np.fft.fftfreq(L) * L
+    g1 = np.exp(-0.5 * (k1 / sigma_h) ** 2)
+    ker = g1
+    for _ in range(d - 1):
+        ker = np.multiply.outer(ker, g1)
+    pad = np.zeros((L,) * d)
+    pad[(slice(0, n),) * d] = noise
+    sm = np.real(np.fft.ifftn(np.fft.fftn(pad) * np.fft.fftn(ker)))[(slice(0, n),) * d]
+    sm *= max_abs / np.max(np.abs(sm))
+    return sm * cutoff(n, d)
+
+
+def directions_circle(count: int) -> np.ndarray:
+    a = 2.0 * np.pi * np.arange(count) / count
+    return np.stack([np.cos(a), np.sin(a)], axis=1)
+
+
+def directions_sphere(count: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((count, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+@dataclass
+class Workload:
+    name: str
+    d: int
+    n: int
+    omega: float
+    m: np.ndarray = field(repr=False)
+    directions: np.ndarray = field(repr=False)
+    mixed: bool = True
+    buffer_b: int = 2
+    restart: int = 50
+    tol: float = 1e-6
+
+    @property
+    def nrhs(self) -> int:
+        return len(self.directions)
+
+
+def plain_2d(n: int = 32) -> Workload:
+    """2D plain FP64: one bump A=-0.2, w=0.1 at (0.5,0.5); omega/2pi = 4; d = (1,0)."""
+    m = bumps(n, 2, [-0.2], [0.1], [(0.5, 0.5)])
+    return Workload(f"2d_plain_n{n}", 2, n, 2 * math.pi * 4, m, np.array([[1.0, 0.0]]), mixed=False)
+
+
+def bumps_2d(n: int = 256, freq: float = 32.0, nb: int = 8, nrhs: int = 16, seed: int = 1002) -> Workload:
+    """2D batched: nb seeded bumps, A ~ U[-0.3,0.3], w ~ U[0.03,0.1], c ~ U[0.2,0.8]^2."""
+    rng = np.random.default_rng(seed)
+    amps = rng.uniform(-0.3, 0.3, nb)
+    widths = rng.uniform(0.03, 0.1, nb)
+    centres = rng.uniform(0.2, 0.8, (nb, 2))
+    m = bumps(n, 2, amps, widths, centres)
+    return Workload(f"2d_bumps_n{n}", 2, n, 2 * math.pi * freq, m, directions_circle(nrhs))
+
+
+def noise_2d(n: int = 1024, freq: float = 128.0, nrhs: int = 64, seed: int = 1003) -> Workload:
+    """2D large: white noise * Gaussian(4h), max|m| = 0.2, times the cutoff."""
+    m = smooth_noise(n, 2, seed, 4.0, 0.2)
+    return Workload(f"2d_noise_n{n}", 2, n, 2 * math.pi * freq, m, directions_circle(nrhs))
+
+
+def bumps_3d(n: int = 64, freq: float = 8.0, nb: int = 6, nrhs: int = 8, seed: int = 1004) -> Workload:
+    """3D batched: nb seeded bumps, A ~ U[-0.2,0.2], w ~ U[0.05,0.12], c ~ U[0.2,0.8]^3."""
+    rng = np.random.default_rng(seed)
+    amps = rng.uniform(-0.2, 0.2, nb)
+    widths = rng.uniform(0.05, 0.12, nb)
+    centres = rng.uniform(0.2, 0.8, (nb, 3))
+    m = bumps(n, 3, amps, widths, centres)
+    return Workload(f"3d_bumps_n{n}", 3, n, 2 * math.pi * freq, m, directions_sphere(nrhs, seed))
+
+
+def enforce_buffer(m: np.ndarray, b: int) -> np.ndarray:
+    """Zero the b+1 outermost layers exactly (the cutoff already makes them ~0 there)."""
+    m = m.copy()
+    n, d = m.shape[0], m.ndim
+    w = b + 1
+    for a in range(d):
+        sl = [slice(None)] * d
+        sl[a] = slice(0, w)
+        m[tuple(sl)] = 0.0
+        sl[a] = slice(n - w, n)
+        m[tuple(sl)] = 0.0
+    return m

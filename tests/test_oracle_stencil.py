@@ -1,0 +1,99 @@
+"""Pins of the oracle's sparsifying stencils (Sec. 2.2, Sec. 3.1, eqs. Fmin / Emin / Cmin)."""
+
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+
+
+def _kmat(n, d, omega, b, cls):
+    mu = O.class_mu(cls)
+    far = O.class_far_set(n, b, cls)
+    T = np.array(mu)[:, None, :] - far[None, :, :]
+    return mu, O.kernel_value(d, omega, O.grid_h(n), T)
+
+
+@pytest.mark.parametrize("cls", [(0, 0), (1, 0), (0, -1), (1, 1), (-1, 1)])
+def test_alpha_is_unit_and_attains_sigma_min(cls):
+    n, d, omega, b = 12, 2, 2 * np.pi * 2, 2
+    mu, alpha, S = O.stencil(n, d, omega, b, cls, return_sigma=True)
+    _, K = _kmat(n, d, omega, b, cls)
+    assert abs(np.linalg.norm(alpha) - 1) < 1e-14
+    assert abs(np.linalg.norm(alpha @ K) - S[-1]) < 1e-12 * S[0]
+    # no other unit vector does better (optimality of eq. Fmin)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        beta = rng.standard_normal(len(mu)) + 1j * rng.standard_normal(len(mu))
+        beta /= np.linalg.norm(beta)
+        assert np.linalg.norm(beta @ K) >= np.linalg.norm(alpha @ K) * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("cls", [(0, 0), (1, 0), (1, 1)])
+def test_alpha_matches_gram_eigenvector_route(cls):
+    # an independent route, usable while K K^* is well enough conditioned (small n)
+    n, d, omega, b = 8, 2, 2 * np.pi * 2, 2
+    mu, alpha = O.stencil(n, d, omega, b, cls)
+    _, K = _kmat(n, d, omega, b, cls)
+    G = K @ K.conj().T
+    w, V = scipy.linalg.eigh(G)
+    beta = np.conj(V[:, 0])
+    c = mu.index((0, 0))
+    beta = beta * abs(beta[c]) / beta[c]
+    assert np.linalg.norm(beta - alpha) < 1e-6
+
+
+def test_centre_coefficient_real_positive():
+    sten, _ = O.all_stencils(10, 2, 30.0, 2)
+    for cls, (mu, alpha) in sten.items():
+        a0 = alpha[mu.index((0, 0))]
+        assert a0.real > 0 and abs(a0.imag) < 1e-15 * a0.real
+
+
+@pytest.mark.parametrize("d,n", [(2, 14), (3, 7)])
+def test_mirror_and_permutation_symmetry_of_classes(d, n):
+    # k_t depends on |t| only, so a class and its mirror / axis permutation have the same
+    # optimal stencil with offsets mapped accordingly
+    omega, b = 2 * np.pi * 2, 2
+    sten, _ = O.all_stencils(n, d, omega, b)
+    for cls, (mu, alpha) in sten.items():
+        amap = dict(zip(mu, alpha))
+        for flip in itertools.product((1, -1), repeat=d):
+            for perm in itertools.permutations(range(d)):
+                cls2 = tuple(cls[perm[a]] * flip[a] for a in range(d))
+                mu2, alpha2 = sten[cls2]
+                for t2, a2 in zip(mu2, alpha2):
+                    t = [0] * d
+                    for a in range(d):
+                        t[perm[a]] = t2[a] * flip[a]
+                    assert abs(amap[tuple(t)] - a2) < 1e-9
+
+
+@pytest.mark.parametrize("d,n,expect", [(2, 12, 3), (3, 6, 4)])
+def test_interior_alpha_dihedral_invariance(d, n, expect):
+    mu, alpha = O.stencil(n, d, 2 * np.pi * 2, 2, (0,) * d)
+    groups = {}
+    for t, a in zip(mu, alpha):
+        groups.setdefault(sum(abs(x) for x in t), []).append(a)
+    assert len(groups) == expect
+    for vals in groups.values():
+        assert max(abs(v - vals[0]) for v in vals) < 1e-9
+
+
+def test_c_is_alpha_times_local_kernel():
+    n, d, omega = 10, 2, 25.0
+    sten, (mu0, c) = O.all_stencils(n, d, omega, 2)
+    _, alpha = sten[(0, 0)]
+    h = O.grid_h(n)
+    for k, tp in enumerate(mu0):
+        ref = sum(alpha[j] * O.kernel_value(d, omega, h, np.array(t) - np.array(tp)) for j, t in enumerate(mu0))
+        assert abs(c[k] - ref) < 1e-15 + 1e-13 * abs(ref)
+
+
+def test_sparsity_claim_reported():
+    """A K ~ C (Sec. 2.2): the far entries of A K are small next to C.  The paper prints no
+    magnitude, so only 'much smaller than 1' is asserted (parity unpinned)."""
+    r1 = O.sparsity_ratio(24, 2, 2 * np.pi * 2)
+    assert r1 < 0.05
