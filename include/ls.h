@@ -1,0 +1,169 @@
+/*
+ * ls.h -- C-ABI of libls, a GB300 (sm_103a) implementation of the sparsifying-preconditioned
+ * iterative solve of the discretized Lippmann-Schwinger equation of
+ *   L. Ying, "Sparsifying Preconditioner for the Lippmann-Schwinger Equation", arXiv:1408.4495.
+ *
+ * Problem (Sec. 1, eq. ls; Sec. 2.1, eqs. lsd/lso):  (I + K omega^2 m) u = g on the grid
+ * x_i = i h, i in {1..n}^d, h = 1/(n+1), d in {2, 3}, K(i,j) = k_{i-j} the Nystrom weights
+ * of the Green's function.  Preconditioner (Sec. 2.2, eq. PC): u <= M^{-1} [A;B] g with
+ * M = [A + C omega^2 m ; B], factored by nested dissection (Sec. 2.2, Sec. 3.2).
+ * Iteration (Sec. 3.3): GMRES to a relative residual tolerance (1e-6 in the paper).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns ls_status.  None aborts, throws or exits; on failure the
+ *    message is available from ls_last_error().
+ *  - Arrays of complex numbers are interleaved (re, im) doubles ("double _Complex" layout),
+ *    in C order over the grid (last index fastest), right-hand sides outermost: element
+ *    (r, i) of an nrhs x n^d array is at [r * n^d + i].
+ *  - Any array argument may be a host pointer or a device pointer of the current device;
+ *    the library tells them apart with cudaPointerGetAttributes.  Host arrays are copied
+ *    inside the call; device arrays are read / written in place on the context's stream.
+ *  - The caller owns every array it passes; the library keeps no pointer to them after the
+ *    call returns.  The context owns all device memory it allocates.
+ *  - A context is not thread-safe; distinct contexts may be used from distinct threads.
+ *  - Calls are synchronous with respect to the host: when a call returns, its outputs
+ *    (host or device) are complete.
+ */
+#ifndef LS_H_
+#define LS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LS_OK = 0,
+  LS_EINVAL = 1,    /* invalid argument (size, dimension, NULL pointer, 1 - m <= 0, ...) */
+  LS_ENOMEM = 2,    /* device or host allocation failed */
+  LS_ECUDA = 3,     /* a CUDA call failed; message has the CUDA error string */
+  LS_ENOCONV = 4,   /* GMRES did not reach the tolerance within max_iter; outputs are filled */
+  LS_ESTATE = 5,    /* call out of order (e.g. ls_solve before ls_factor) */
+  LS_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up */
+  LS_EBUFFER = 7    /* m is not zero within b+1 layers of the boundary (Sec. 2.1, Sec. 3.1) */
+} ls_status;
+
+typedef enum {
+  LS_PREC_FP64 = 0,  /* every step in FP64 complex ("plain" path) */
+  LS_PREC_MIXED = 1  /* FP32 complex operator apply, stencil, fronts and solves; FP64 Arnoldi,
+                        Hessenberg least squares and outer residual g - A u (refinement) */
+} ls_prec;
+
+typedef struct {
+  int dim;       /* d: 2 or 3 */
+  int n;         /* points per dimension; 2n must be a power of two, 16 <= n <= 2048 (2D),
+                    8 <= n <= 128 (3D) */
+  int buffer_b;  /* b of Sec. 3.1: width (in grid steps) of the layer where m vanishes, >= 1;
+                    0 selects the default 2 */
+  int restart;   /* GMRES restart length; 0 selects 50 */
+  int max_iter;  /* cap on GMRES iterations per right-hand side; 0 selects 500 */
+  ls_prec prec;  /* arithmetic of the path, see ls_prec */
+} ls_grid;
+
+typedef struct ls_ctx ls_ctx; /* opaque */
+
+typedef struct {
+  int iters;        /* GMRES iterations (one preconditioner + one operator apply each) */
+  int refinements;  /* number of FP64 residual evaluations after the first cycle */
+  double rel_resid; /* |g - (I + K omega^2 m) u| / |g| evaluated in FP64 at the end */
+  int converged;    /* 1 if rel_resid <= tol */
+} ls_info;
+
+/*
+ * ls_setup -- Sec. 2.1 (grid, k_t, k_0), Sec. 1 (FFT of the convolution), Sec. 3.1 (stencils).
+ * Builds the Nystrom table k_t, the Fourier symbol of its (2n)^d circulant embedding, the
+ * 3^d stencils alpha (eqs. Fmin, Emin, Cmin; the centre coefficient made real positive) and
+ * C = alpha K(mu, mu), and the nested-dissection structure.  Tables that depend only on
+ * (d, n, omega, b) are cached inside the library and reused by later contexts.
+ *   g       grid description (copied).
+ *   omega   angular frequency, > 0.
+ *   m       n^d real doubles, C order: the medium m(x_i) (index of refraction 1 - m).  Host or
+ *           device pointer; copied.  Must vanish on the b+1 outermost layers (else LS_EBUFFER)
+ *           and satisfy 1 - m > 0 (else LS_EINVAL).
+ *   stream  cudaStream_t to run on, or NULL for a stream owned by the context.
+ *   out     receives the context; *out is NULL on failure.
+ */
+ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream, ls_ctx** out);
+
+/*
+ * ls_factor -- Sec. 2.2 eq. PC, Sec. 3.1 eq. ABop, Sec. 3.2: assembles M = [A + C omega^2 m; B]
+ * into the nested-dissection fronts and computes their partial LU factorizations (pivoting
+ * restricted to the fully-summed rows of each front).  FP32 fronts under LS_PREC_MIXED,
+ * FP64 under LS_PREC_FP64.  May be called again (e.g. to time it); LS_ESTATE if c is NULL.
+ */
+ls_status ls_factor(ls_ctx* c);
+
+/*
+ * ls_rhs_plane_wave -- Sec. 1 eq. ls, Sec. 2.1 eq. lsd: g = K(-omega^2 m u_I) with the
+ * incident plane wave u_I(x) = exp(i omega x . dir), computed on the device in FP64.
+ *   nrhs   number of directions, >= 1.
+ *   dirs   nrhs x d doubles (unit vectors are not required), host or device.
+ *   g_out  nrhs x n^d complex doubles, host or device, written.
+ */
+ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_out);
+
+/*
+ * ls_solve -- Sec. 3.3: right-preconditioned GMRES(restart) on (I + K omega^2 m) u = g with
+ * the sparsifying preconditioner, all right-hand sides batched in each launch.  Under
+ * LS_PREC_MIXED the inner cycles are flexible GMRES with FP32 preconditioner and operator and
+ * FP64 Arnoldi, wrapped in FP64 iterative refinement; the stopping test is always the FP64
+ * relative residual.  Requires ls_factor (else LS_ESTATE).
+ *   rhs    nrhs x n^d complex doubles (g), host or device.
+ *   tol    relative residual tolerance, > 0.
+ *   u_out  nrhs x n^d complex doubles, host or device, written (best iterate on LS_ENOCONV).
+ *   info   nrhs entries, may be NULL.
+ */
+ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u_out, ls_info* info);
+
+/* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
+ * Valid until the next call on c. */
+const char* ls_last_error(const ls_ctx* c);
+
+/* Releases every resource of c.  NULL-safe. */
+void ls_free(ls_ctx* c);
+
+/* ---------------------------------------------------------------------------------------
+ * Inspection entry points: the individual steps of the path, exposed so that each can be
+ * checked on its own.  Same pointer and layout conventions as above.
+ * --------------------------------------------------------------------------------------- */
+
+/* Sec. 2.1: k_t for t in [0, n]^d (the table is even in every component), (n+1)^d complex
+ * doubles in C order, written to out (host or device). */
+ls_status ls_kernel_table(ls_ctx* c, double* out);
+
+/* Sec. 3.1 / Sec. 2.2: alpha for each of the 3^d point classes and C for the interior class.
+ * Class index sum_a (cls_a + 1) 3^(d-1-a), cls_a = -1 on the low face of axis a, +1 on the
+ * high face, 0 otherwise; coefficient index sum_a (t_a + 1) 3^(d-1-a) for offset t.
+ * alpha_out: 3^d x 3^d complex doubles (zero outside mu), c_out: 3^d complex doubles.
+ * Host pointers only. */
+ls_status ls_stencils(ls_ctx* c, double* alpha_out, double* c_out);
+
+/* Sec. 2.1 eq. lso: out = (I + K omega^2 m) in, nrhs vectors, in the arithmetic prec
+ * (LS_PREC_MIXED = FP32 complex inside, FP64 at the boundary). */
+ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec);
+
+/* Sec. 2.2 eq. PC, right-hand factor: out = [A;B] in (the 3^d-point stencil of each point's
+ * class), in the arithmetic prec. */
+ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec);
+
+/* Sec. 2.2 eq. PC: out = M^{-1} [A;B] in, with the factors of ls_factor (their precision). */
+ls_status ls_precond(ls_ctx* c, int nrhs, const double* in, double* out);
+
+/* Sizes of the nested-dissection factorization (Sec. 3.2). */
+typedef struct {
+  int levels;              /* depth of the separator tree + 1 */
+  int fronts;              /* number of fronts */
+  int max_front;           /* largest front order (separator + boundary) */
+  int64_t factor_entries;  /* complex entries stored for all fronts (padded) */
+  double factor_flops;     /* real flops of the partial factorizations (padded shapes) */
+  double solve_bytes;      /* bytes of factor read by one forward + backward solve */
+} ls_nd_stats;
+
+ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LS_H_ */

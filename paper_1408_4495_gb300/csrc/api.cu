@@ -1,0 +1,691 @@
+// C-ABI of libls (include/ls.h) and the GMRES driver of Sec. 3.3.
+//
+// ls_solve runs right-preconditioned GMRES(restart) on (I + K omega^2 m) u = g for all
+// right-hand sides at once: each launch processes the whole batch, each right-hand side
+// keeps its own Krylov space, Hessenberg matrix and stopping point.  Under LS_PREC_MIXED an
+// iteration applies the FP32 stencil + ND solve (preconditioner) and the FP32 FFT operator,
+// and orthogonalises in FP64 (flexible GMRES: the preconditioned vectors Z are kept, in
+// FP32); every cycle ends with the FP64 residual g - A u (FP64 FFT apply), which decides
+// convergence and restarts the next cycle (iterative refinement).  Under LS_PREC_FP64 the
+// same loop runs with FP64 everywhere.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "krylov.h"
+#include "ls.h"
+
+using ls::Error;
+using cd = std::complex<double>;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ls_ctx {
+  ls_grid g{};
+  int d = 0, n = 0, L = 0, b = 2, restart = 50, max_iter = 500;
+  long N = 0;
+  double omega = 0, h = 0;
+  ls_prec prec = LS_PREC_MIXED;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  double* w2m64 = nullptr;
+  float* w2m32 = nullptr;
+  float2* tw32 = nullptr;
+  double2* tw64 = nullptr;
+  double2* ktq = nullptr;
+  float2* sym32 = nullptr;
+  double2* sym64 = nullptr;
+  double2* alpha64 = nullptr;
+  float2* alpha32 = nullptr;
+  double2* cint64 = nullptr;
+  std::vector<double2> alpha_h, cint_h;
+  ls::NdPlan* nd = nullptr;
+  bool factored = false;
+  std::map<std::string, DevBuf> bufs;
+  std::vector<double2*> V;
+  std::vector<void*> Z;
+  int Z_elem = 0;
+  long basis_cap = 0;  // elements per basis vector allocated
+  double2** dV = nullptr;
+  void** dZ = nullptr;
+  ls::ConvPlan plan{};
+};
+
+namespace {
+
+std::mutex g_mu;
+std::string g_setup_err;
+
+struct StencilKey {
+  int d, n, b;
+  double omega;
+  bool operator<(const StencilKey& o) const { return std::tie(d, n, b, omega) < std::tie(o.d, o.n, o.b, o.omega); }
+};
+std::map<StencilKey, std::pair<std::vector<double2>, std::vector<double2>>> g_stencil_cache;
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T> T* dalloc(size_t count) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    LS_FAIL(ls::ENOMEM_, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+  }
+  return (T*)p;
+}
+
+template <typename T> T* buf(ls_ctx* c, const std::string& name, size_t count) {
+  DevBuf& b = c->bufs[name];
+  const size_t need = std::max<size_t>(1, count) * sizeof(T);
+  if (b.bytes < need) {
+    if (b.p) {
+      LS_CUDA(cudaStreamSynchronize(c->st));
+      cudaFree(b.p);
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+    b.p = dalloc<unsigned char>(need);
+    b.bytes = need;
+  }
+  return (T*)b.p;
+}
+
+// copy count complex doubles (or doubles) between a caller array and a device buffer
+void copy_in(ls_ctx* c, void* dst, const void* src, size_t bytes) {
+  LS_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+}
+void copy_out(ls_ctx* c, void* dst, const void* src, size_t bytes) {
+  LS_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+}
+
+void ensure_basis(ls_ctx* c, int nvec, int nrhs, int z_elem) {
+  const long need = (long)nrhs * c->N;
+  if (need > c->basis_cap || z_elem != c->Z_elem) {
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    for (auto p : c->V) cudaFree(p);
+    for (auto p : c->Z) cudaFree(p);
+    c->V.clear();
+    c->Z.clear();
+    c->basis_cap = need;
+    c->Z_elem = z_elem;
+  }
+  bool grew = false;
+  while ((int)c->V.size() < nvec) {
+    c->V.push_back(dalloc<double2>(c->basis_cap));
+    grew = true;
+  }
+  while ((int)c->Z.size() < nvec) {
+    c->Z.push_back(dalloc<unsigned char>((size_t)c->basis_cap * z_elem));
+    grew = true;
+  }
+  if (grew || !c->dV) {
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    if (c->dV) cudaFree(c->dV);
+    if (c->dZ) cudaFree(c->dZ);
+    c->dV = dalloc<double2*>(c->V.size());
+    c->dZ = dalloc<void*>(c->Z.size());
+    LS_CUDA(cudaMemcpy(c->dV, c->V.data(), c->V.size() * sizeof(double2*), cudaMemcpyHostToDevice));
+    LS_CUDA(cudaMemcpy(c->dZ, c->Z.data(), c->Z.size() * sizeof(void*), cudaMemcpyHostToDevice));
+  }
+}
+
+template <typename C> void op_apply(ls_ctx* c, int nrhs, const C* u, C* y) {
+  const size_t s1 = ls::conv_scratch1_elems(c->d, c->n, nrhs), s2 = ls::conv_scratch2_elems(c->d, c->n, nrhs);
+  void* t1 = buf<C>(c, sizeof(C) == 8 ? "conv1_32" : "conv1_64", s1);
+  void* t2 = s2 ? buf<C>(c, sizeof(C) == 8 ? "conv2_32" : "conv2_64", s2) : nullptr;
+  ls::conv_apply<C>(c->plan, nrhs, u, y, nullptr, true, t1, t2, c->st);
+}
+
+// z = M^{-1} [A;B] v for FP64 input v; z in the factor precision C
+template <typename C> void precond_apply(ls_ctx* c, int nrhs, const double2* v, C* z) {
+  C* r = buf<C>(c, sizeof(C) == 8 ? "pre_r32" : "pre_r64", (size_t)nrhs * c->N);
+  const void* alpha = sizeof(C) == 8 ? (const void*)c->alpha32 : (const void*)c->alpha64;
+  ls::stencil_apply<double2, C>(c->d, c->n, nrhs, v, r, 1, c->N, alpha, c->st);
+  ls::nd_solve<C>(c->nd, nrhs, r, z, c->st);
+}
+
+ls_status fail(ls_ctx* c, const Error& e) {
+  if (c) c->err = e.msg;
+  return (ls_status)e.code;
+}
+
+void check_ctx(ls_ctx* c) {
+  if (!c) throw Error{ls::ESTATE_, "NULL context"};
+}
+
+// ---------------------------------------------------------------------------------------
+// GMRES cycles (Sec. 3.3), batched over right-hand sides
+// ---------------------------------------------------------------------------------------
+template <typename CZ>
+void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, ls_info* info) {
+  const long N = c->N, tot = N * nrhs;
+  const int R = c->restart;
+  const bool mixed = sizeof(CZ) == 8;
+  ensure_basis(c, 2, nrhs, sizeof(CZ));
+  double2* w = buf<double2>(c, "w64", tot);
+  double2* r = buf<double2>(c, "r64", tot);
+  double2* Au = buf<double2>(c, "Au64", tot);
+  CZ* wz = mixed ? buf<CZ>(c, "w32", tot) : nullptr;
+  const int nblk = ls::dots_blocks(N);
+  double2* partial = buf<double2>(c, "partial", (size_t)nrhs * (R + 2) * nblk);
+  double2* hd = buf<double2>(c, "hcol", (size_t)nrhs * (R + 2) * 2);
+  double* sd = buf<double>(c, "scale", nrhs);
+  double2* yd = buf<double2>(c, "ycoef", (size_t)nrhs * R);
+
+  LS_CUDA(cudaMemsetAsync(u, 0, tot * sizeof(double2), c->st));
+  std::vector<double2> hh((size_t)nrhs * (R + 2) * 2);
+  ls::norms2<double2>(g, N, nrhs, partial, hd, 1, c->st);
+  LS_CUDA(cudaMemcpyAsync(hh.data(), hd, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+  LS_CUDA(cudaStreamSynchronize(c->st));
+  std::vector<double> gn(nrhs), rn(nrhs);
+  for (int j = 0; j < nrhs; ++j) gn[j] = rn[j] = std::sqrt(hh[j].x);
+  std::vector<int> iters(nrhs, 0), cycles(nrhs, 0);
+  std::vector<char> conv(nrhs, 0);
+  for (int j = 0; j < nrhs; ++j) conv[j] = rn[j] <= tol * gn[j];
+  // r = g for the first cycle (u = 0)
+  LS_CUDA(cudaMemcpyAsync(r, g, tot * sizeof(double2), cudaMemcpyDeviceToDevice, c->st));
+
+  std::vector<cd> H((size_t)nrhs * (R + 1) * R), sn((size_t)nrhs * R), s((size_t)nrhs * (R + 1));
+  std::vector<double> cs((size_t)nrhs * R), sc(nrhs);
+  std::vector<int> kdone(nrhs);
+  std::vector<char> act(nrhs);
+  std::vector<double2> Y((size_t)nrhs * R);
+  const double inner = mixed ? 0.5 : 1.0;
+
+  while (true) {
+    bool any = false;
+    for (int j = 0; j < nrhs; ++j) {
+      act[j] = !conv[j] && iters[j] < c->max_iter;
+      any |= act[j];
+    }
+    if (!any) break;
+    // V_0 = r / |r|
+    for (int j = 0; j < nrhs; ++j) {
+      sc[j] = act[j] && rn[j] > 0 ? 1.0 / rn[j] : 0.0;
+      kdone[j] = 0;
+      s[(size_t)j * (R + 1)] = act[j] ? rn[j] : 0.0;
+    }
+    LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    ls::scale(r, c->V[0], sd, N, nrhs, c->st);
+    int k = 0;
+    for (; k < R; ++k) {
+      bool live = false;
+      for (int j = 0; j < nrhs; ++j) live |= act[j] && kdone[j] == 0;
+      if (!live) break;
+      ensure_basis(c, k + 2, nrhs, sizeof(CZ));
+      CZ* zk = (CZ*)c->Z[k];
+      precond_apply<CZ>(c, nrhs, c->V[k], zk);
+      const double2* const* dV = c->dV;
+      // w = A z_k, then CGS2 against V[0..k]
+      if (mixed) {
+        op_apply<CZ>(c, nrhs, zk, wz);
+        ls::dots<CZ>(dV, k + 1, wz, N, nrhs, partial, hd, R + 2, false, c->st);
+        ls::sub_proj<CZ>(dV, k + 1, wz, w, hd, R + 2, N, nrhs, c->st);
+      } else {
+        op_apply<double2>(c, nrhs, (const double2*)zk, w);
+        ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd, R + 2, false, c->st);
+        ls::sub_proj<double2>(dV, k + 1, w, w, hd, R + 2, N, nrhs, c->st);
+      }
+      double2* hd2 = hd + (size_t)nrhs * (R + 2);
+      ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd2, R + 2, false, c->st);
+      ls::sub_proj<double2>(dV, k + 1, w, w, hd2, R + 2, N, nrhs, c->st);
+      ls::norms2<double2>(w, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
+      LS_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+      LS_CUDA(cudaStreamSynchronize(c->st));
+      for (int j = 0; j < nrhs; ++j) {
+        sc[j] = 0.0;
+        if (!act[j] || kdone[j]) continue;
+        cd* Hj = &H[(size_t)j * (R + 1) * R];
+        cd* col = Hj + (size_t)k * (R + 1);
+        const double2* h1 = &hh[(size_t)j * (R + 2)];
+        const double2* h2 = &hh[(size_t)(nrhs + j) * (R + 2)];
+        for (int i = 0; i <= k; ++i) col[i] = cd(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+        const double beta = std::sqrt(std::max(0.0, h2[k + 1].x));
+        col[k + 1] = beta;
+        double* csj = &cs[(size_t)j * R];
+        cd* snj = &sn[(size_t)j * R];
+        cd* sj = &s[(size_t)j * (R + 1)];
+        for (int i = 0; i < k; ++i) {
+          const cd a = col[i], bb = col[i + 1];
+          col[i] = csj[i] * a + snj[i] * bb;
+          col[i + 1] = -std::conj(snj[i]) * a + csj[i] * bb;
+        }
+        const cd a = col[k], bb = col[k + 1];
+        const double rr = std::hypot(std::abs(a), std::abs(bb));
+        if (std::abs(a) == 0.0) { csj[k] = 0.0; snj[k] = 1.0; }
+        else { csj[k] = std::abs(a) / rr; snj[k] = (a / std::abs(a)) * std::conj(bb) / rr; }
+        col[k] = csj[k] * a + snj[k] * bb;
+        col[k + 1] = 0.0;
+        sj[k + 1] = -std::conj(snj[k]) * sj[k];
+        sj[k] = csj[k] * sj[k];
+        iters[j] += 1;
+        const double res = std::abs(sj[k + 1]);
+        if (res <= inner * tol * gn[j] || beta == 0.0 || iters[j] >= c->max_iter) kdone[j] = k + 1;
+        else sc[j] = 1.0 / beta;
+      }
+      LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      ls::scale(w, c->V[k + 1], sd, N, nrhs, c->st);
+    }
+    // least squares: H(0:k, 0:k) y = s(0:k), per right-hand side
+    int kmax = 0;
+    std::fill(Y.begin(), Y.end(), make_double2(0, 0));
+    for (int j = 0; j < nrhs; ++j) {
+      if (!act[j]) continue;
+      const int kj = kdone[j] ? kdone[j] : k;
+      kmax = std::max(kmax, kj);
+      const cd* Hj = &H[(size_t)j * (R + 1) * R];
+      std::vector<cd> y(kj);
+      for (int i = kj - 1; i >= 0; --i) {
+        cd acc = s[(size_t)j * (R + 1) + i];
+        for (int l = i + 1; l < kj; ++l) acc -= Hj[(size_t)l * (R + 1) + i] * y[l];
+        y[i] = acc / Hj[(size_t)i * (R + 1) + i];
+      }
+      for (int i = 0; i < kj; ++i) Y[(size_t)j * R + i] = make_double2(y[i].real(), y[i].imag());
+      cycles[j] += 1;
+    }
+    if (kmax > 0) {
+      LS_CUDA(cudaMemcpyAsync(yd, Y.data(), Y.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+      ls::update_u<CZ>((const CZ* const*)c->dZ, kmax, yd, R, u, N, nrhs, c->st);
+    }
+    // FP64 residual r = g - A u
+    op_apply<double2>(c, nrhs, u, Au);
+    ls::residual(g, Au, r, tot, c->st);
+    ls::norms2<double2>(r, N, nrhs, partial, hd, 1, c->st);
+    LS_CUDA(cudaMemcpyAsync(hh.data(), hd, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    for (int j = 0; j < nrhs; ++j) {
+      rn[j] = std::sqrt(hh[j].x);
+      conv[j] = rn[j] <= tol * gn[j];
+    }
+  }
+  bool all = true;
+  for (int j = 0; j < nrhs; ++j) {
+    if (info) {
+      info[j].iters = iters[j];
+      info[j].refinements = std::max(0, cycles[j] - 1);
+      info[j].rel_resid = gn[j] > 0 ? rn[j] / gn[j] : 0.0;
+      info[j].converged = conv[j] ? 1 : 0;
+    }
+    all &= conv[j] != 0;
+  }
+  if (!all) throw Error{ls::ENOCONV_, "GMRES did not reach the tolerance for every right-hand side"};
+}
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+}  // namespace
+
+// =======================================================================================
+// C-ABI
+// =======================================================================================
+extern "C" {
+
+ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream, ls_ctx** out) {
+  if (out) *out = nullptr;
+  ls_ctx* c = nullptr;
+  try {
+    if (!g || !m || !out) throw Error{ls::EINVAL_, "NULL argument"};
+    if (g->dim != 2 && g->dim != 3) throw Error{ls::EINVAL_, "dim must be 2 or 3"};
+    const int n = g->n;
+    if (!pow2(2 * n)) throw Error{ls::EINVAL_, "2n must be a power of two"};
+    if (g->dim == 2 && (n < 16 || n > 2048)) throw Error{ls::EINVAL_, "2D needs 16 <= n <= 2048"};
+    if (g->dim == 3 && (n < 8 || n > 128)) throw Error{ls::EINVAL_, "3D needs 8 <= n <= 128"};
+    if (!(omega > 0) || !std::isfinite(omega)) throw Error{ls::EINVAL_, "omega must be positive"};
+    const int b = g->buffer_b > 0 ? g->buffer_b : 2;
+    if (n <= 2 * (b + 1)) throw Error{ls::EINVAL_, "n too small for the buffer layers"};
+    if (g->prec != LS_PREC_FP64 && g->prec != LS_PREC_MIXED) throw Error{ls::EINVAL_, "unknown precision"};
+    c = new ls_ctx;
+    c->g = *g;
+    c->d = g->dim;
+    c->n = n;
+    c->L = 2 * n;
+    c->b = b;
+    c->restart = g->restart > 0 ? g->restart : 50;
+    c->max_iter = g->max_iter > 0 ? g->max_iter : 500;
+    c->prec = g->prec;
+    c->N = c->d == 2 ? (long)n * n : (long)n * n * n;
+    c->omega = omega;
+    c->h = 1.0 / (n + 1);
+    if (stream) c->st = (cudaStream_t)stream;
+    else {
+      LS_CUDA(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    // medium: checks on the host copy (Sec. 2.1: m vanishes within the buffer; 1 - m > 0)
+    std::vector<double> mh(c->N);
+    if (is_device_ptr(m)) LS_CUDA(cudaMemcpy(mh.data(), m, c->N * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memcpy(mh.data(), m, c->N * sizeof(double));
+    const int wl = b + 1;
+    for (long i = 0; i < c->N; ++i) {
+      if (!std::isfinite(mh[i]) || !(1.0 - mh[i] > 0)) throw Error{ls::EINVAL_, "m must be finite with 1 - m > 0"};
+      long q = i;
+      bool edge = false;
+      for (int a = 0; a < c->d; ++a) {
+        const long ia = q % n;
+        q /= n;
+        if (ia < wl || ia >= n - wl) edge = true;
+      }
+      if (edge && mh[i] != 0.0) throw Error{ls::EBUFFER_, "m must vanish within b+1 layers of the boundary"};
+    }
+    std::vector<double> w64(c->N);
+    std::vector<float> w32(c->N);
+    for (long i = 0; i < c->N; ++i) {
+      w64[i] = omega * omega * mh[i];
+      w32[i] = (float)w64[i];
+    }
+    c->w2m64 = dalloc<double>(c->N);
+    c->w2m32 = dalloc<float>(c->N);
+    LS_CUDA(cudaMemcpyAsync(c->w2m64, w64.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    LS_CUDA(cudaMemcpyAsync(c->w2m32, w32.data(), c->N * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    // twiddles exp(-2 pi i m / L)
+    const int L = c->L;
+    std::vector<double2> t64(L);
+    std::vector<float2> t32(L);
+    for (int q = 0; q < L; ++q) {
+      const double a = -2.0 * M_PI * (double)q / (double)L;
+      t64[q] = make_double2(std::cos(a), std::sin(a));
+      t32[q] = make_float2((float)t64[q].x, (float)t64[q].y);
+    }
+    c->tw64 = dalloc<double2>(L);
+    c->tw32 = dalloc<float2>(L);
+    LS_CUDA(cudaMemcpyAsync(c->tw64, t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    LS_CUDA(cudaMemcpyAsync(c->tw32, t32.data(), L * sizeof(float2), cudaMemcpyHostToDevice, c->st));
+    // Nystrom table quadrant and symbol (Sec. 2.1)
+    const long n1 = n + 1;
+    const long nq = c->d == 2 ? n1 * n1 : n1 * n1 * n1;
+    c->ktq = dalloc<double2>(nq);
+    c->sym64 = dalloc<double2>(nq);
+    c->sym32 = dalloc<float2>(nq);
+    ls::build_kernel_table(c->d, n, omega, c->h, c->ktq, c->st);
+    c->plan.d = c->d;
+    c->plan.n = n;
+    c->plan.omega = omega;
+    c->plan.h = c->h;
+    c->plan.tw32 = c->tw32;
+    c->plan.tw64 = c->tw64;
+    c->plan.w2m32 = c->w2m32;
+    c->plan.w2m64 = c->w2m64;
+    {
+      const long Ld = c->d == 2 ? (long)L * L : (long)L * L * L;
+      double2* work = dalloc<double2>(Ld);
+      try {
+        ls::build_symbol(c->plan, c->ktq, c->sym64, c->sym32, work, c->st);
+        LS_CUDA(cudaStreamSynchronize(c->st));
+      } catch (...) {
+        cudaFree(work);
+        throw;
+      }
+      cudaFree(work);
+    }
+    c->plan.sym32 = c->sym32;
+    c->plan.sym64 = c->sym64;
+    // stencils (Sec. 3.1), cached per (d, n, b, omega)
+    {
+      StencilKey key{c->d, n, b, omega};
+      bool hit = false;
+      {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_stencil_cache.find(key);
+        if (it != g_stencil_cache.end()) {
+          c->alpha_h = it->second.first;
+          c->cint_h = it->second.second;
+          hit = true;
+        }
+      }
+      if (!hit) {
+        std::vector<double2> kh(nq);
+        LS_CUDA(cudaMemcpy(kh.data(), c->ktq, nq * sizeof(double2), cudaMemcpyDeviceToHost));
+        ls::compute_stencils(c->d, n, b, kh, c->alpha_h, c->cint_h);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_stencil_cache[key] = {c->alpha_h, c->cint_h};
+      }
+    }
+    const size_t na = c->alpha_h.size();
+    std::vector<float2> a32(na);
+    for (size_t i = 0; i < na; ++i) a32[i] = make_float2((float)c->alpha_h[i].x, (float)c->alpha_h[i].y);
+    c->alpha64 = dalloc<double2>(na);
+    c->alpha32 = dalloc<float2>(na);
+    c->cint64 = dalloc<double2>(c->cint_h.size());
+    LS_CUDA(cudaMemcpyAsync(c->alpha64, c->alpha_h.data(), na * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    LS_CUDA(cudaMemcpyAsync(c->alpha32, a32.data(), na * sizeof(float2), cudaMemcpyHostToDevice, c->st));
+    LS_CUDA(cudaMemcpyAsync(c->cint64, c->cint_h.data(), c->cint_h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    // nested-dissection structure (Sec. 3.2)
+    c->nd = ls::nd_build(c->d, n, c->st);
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    *out = c;
+    return LS_OK;
+  } catch (const Error& e) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_setup_err = e.msg;
+    if (c) ls_free(c);
+    return (ls_status)e.code;
+  } catch (const std::bad_alloc&) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_setup_err = "host allocation failed";
+    if (c) ls_free(c);
+    return LS_ENOMEM;
+  }
+}
+
+ls_status ls_factor(ls_ctx* c) {
+  try {
+    check_ctx(c);
+    c->factored = false;
+    if (c->prec == LS_PREC_MIXED) ls::nd_factor<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
+    else ls::nd_factor<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
+    c->factored = true;
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::bad_alloc&) {
+    return fail(c, Error{ls::ENOMEM_, "host allocation failed"});
+  }
+}
+
+ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_out) {
+  try {
+    check_ctx(c);
+    if (nrhs < 1 || !dirs || !g_out) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t tot = (size_t)nrhs * c->N;
+    double* dd = buf<double>(c, "dirs", (size_t)nrhs * c->d);
+    copy_in(c, dd, dirs, (size_t)nrhs * c->d * sizeof(double));
+    double2* gd = buf<double2>(c, "rhs_out", tot);
+    const size_t s1 = ls::conv_scratch1_elems(c->d, c->n, nrhs), s2 = ls::conv_scratch2_elems(c->d, c->n, nrhs);
+    void* t1 = buf<double2>(c, "conv1_64", s1);
+    void* t2 = s2 ? buf<double2>(c, "conv2_64", s2) : nullptr;
+    ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, c->st);
+    copy_out(c, g_out, gd, tot * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u_out, ls_info* info) {
+  try {
+    check_ctx(c);
+    if (!c->factored) throw Error{ls::ESTATE_, "ls_solve before ls_factor"};
+    if (nrhs < 1 || !rhs || !u_out || !(tol > 0)) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t tot = (size_t)nrhs * c->N;
+    double2* g = buf<double2>(c, "solve_g", tot);
+    double2* u = buf<double2>(c, "solve_u", tot);
+    copy_in(c, g, rhs, tot * sizeof(double2));
+    ls_status st = LS_OK;
+    try {
+      if (c->prec == LS_PREC_MIXED) solve_impl<float2>(c, nrhs, g, tol, u, info);
+      else solve_impl<double2>(c, nrhs, g, tol, u, info);
+    } catch (const Error& e) {
+      if (e.code != ls::ENOCONV_) throw;
+      c->err = e.msg;
+      st = LS_ENOCONV;
+    }
+    copy_out(c, u_out, u, tot * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return st;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::bad_alloc&) {
+    return fail(c, Error{ls::ENOMEM_, "host allocation failed"});
+  }
+}
+
+const char* ls_last_error(const ls_ctx* c) {
+  if (!c) return g_setup_err.c_str();
+  return c->err.c_str();
+}
+
+void ls_free(ls_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : {(void*)c->w2m64, (void*)c->w2m32, (void*)c->tw32, (void*)c->tw64, (void*)c->ktq, (void*)c->sym32,
+                  (void*)c->sym64, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ})
+    if (p) cudaFree(p);
+  for (auto p : c->V) cudaFree(p);
+  for (auto p : c->Z) cudaFree(p);
+  for (auto& kv : c->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (c->nd) ls::nd_free(c->nd);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  cudaGetLastError();
+  delete c;
+}
+
+ls_status ls_kernel_table(ls_ctx* c, double* out) {
+  try {
+    check_ctx(c);
+    if (!out) throw Error{ls::EINVAL_, "NULL out"};
+    const long n1 = c->n + 1;
+    const long nq = c->d == 2 ? n1 * n1 : n1 * n1 * n1;
+    copy_out(c, out, c->ktq, nq * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_stencils(ls_ctx* c, double* alpha_out, double* c_out) {
+  try {
+    check_ctx(c);
+    if (alpha_out) std::memcpy(alpha_out, c->alpha_h.data(), c->alpha_h.size() * sizeof(double2));
+    if (c_out) std::memcpy(c_out, c->cint_h.data(), c->cint_h.size() * sizeof(double2));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec) {
+  try {
+    check_ctx(c);
+    if (nrhs < 1 || !in || !out) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t tot = (size_t)nrhs * c->N;
+    double2* x = buf<double2>(c, "io_in", tot);
+    double2* y = buf<double2>(c, "io_out", tot);
+    copy_in(c, x, in, tot * sizeof(double2));
+    if (prec == LS_PREC_MIXED) {
+      float2* x32 = buf<float2>(c, "io_in32", tot);
+      float2* y32 = buf<float2>(c, "io_out32", tot);
+      ls::cast<double2, float2>(x, x32, tot, c->st);
+      op_apply<float2>(c, nrhs, x32, y32);
+      ls::cast<float2, double2>(y32, y, tot, c->st);
+    } else {
+      op_apply<double2>(c, nrhs, x, y);
+    }
+    copy_out(c, out, y, tot * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec) {
+  try {
+    check_ctx(c);
+    if (nrhs < 1 || !in || !out) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t tot = (size_t)nrhs * c->N;
+    double2* x = buf<double2>(c, "io_in", tot);
+    double2* y = buf<double2>(c, "io_out", tot);
+    copy_in(c, x, in, tot * sizeof(double2));
+    if (prec == LS_PREC_MIXED) {
+      float2* y32 = buf<float2>(c, "io_out32", tot);
+      ls::stencil_apply<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->alpha32, c->st);
+      ls::cast<float2, double2>(y32, y, tot, c->st);
+    } else {
+      ls::stencil_apply<double2, double2>(c->d, c->n, nrhs, x, y, 1, c->N, c->alpha64, c->st);
+    }
+    copy_out(c, out, y, tot * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_precond(ls_ctx* c, int nrhs, const double* in, double* out) {
+  try {
+    check_ctx(c);
+    if (!c->factored) throw Error{ls::ESTATE_, "ls_precond before ls_factor"};
+    if (nrhs < 1 || !in || !out) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t tot = (size_t)nrhs * c->N;
+    double2* x = buf<double2>(c, "io_in", tot);
+    double2* y = buf<double2>(c, "io_out", tot);
+    copy_in(c, x, in, tot * sizeof(double2));
+    if (c->prec == LS_PREC_MIXED) {
+      float2* z32 = buf<float2>(c, "io_out32", tot);
+      precond_apply<float2>(c, nrhs, x, z32);
+      ls::cast<float2, double2>(z32, y, tot, c->st);
+    } else {
+      precond_apply<double2>(c, nrhs, x, y);
+    }
+    copy_out(c, out, y, tot * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out) {
+  try {
+    check_ctx(c);
+    if (!out) throw Error{ls::EINVAL_, "NULL out"};
+    const ls::NdInfo i = ls::nd_info(c->nd);
+    const int eb = c->prec == LS_PREC_MIXED ? 8 : 16;
+    out->levels = i.levels;
+    out->fronts = i.fronts;
+    out->max_front = i.max_front;
+    out->factor_entries = i.factor_entries;
+    out->factor_flops = i.factor_flops;
+    out->solve_bytes = i.solve_bytes * eb;
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+}  // extern "C"

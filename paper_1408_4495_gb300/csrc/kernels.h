@@ -1,0 +1,91 @@
+// Internal interfaces between the translation units of libls (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace ls {
+
+// ---------------------------------------------------------------- FFT passes (fft.cu)
+struct RowPassArgs {
+  const void* in;      // lines of complex (path precision), line stride in_ls
+  void* out;           // line stride out_ls
+  long lines;
+  int n_in, n_out;     // entries read (zero padded to L) / entries written
+  long in_ls, out_ls;
+  const void* pw;      // real weights [(line % pw_lines) * n_in + e], or null
+  long pw_lines;
+  const void* tw;      // twiddles exp(-2 pi i m / L), m < L
+  const double* plane_dirs;  // right-hand-side prologue (double only), or null
+  int d, n;
+  double omega, h;
+  const void* addv;    // epilogue: out += addv[line * add_ls + e], or null
+  long add_ls;
+};
+
+struct ColPassArgs {
+  const void* in;
+  void* out;
+  long outer, inner;   // lines = outer * inner, inner index contiguous in memory
+  long in_os, in_es, out_os, out_es;
+  int n_in, n_out;
+  const void* sym;     // symbol quadrant (n+1)^d for the symbol pass
+  int n, d;
+  const void* tw;
+};
+
+struct ConvPlan {
+  int d, n;
+  double omega, h;
+  const float2* tw32;
+  const double2* tw64;
+  const float2* sym32;
+  const double2* sym64;
+  const float* w2m32;   // omega^2 m, n^d
+  const double* w2m64;
+};
+
+template <typename C> void row_pass(int L, int sign, const RowPassArgs& a, cudaStream_t st);
+template <typename C> void col_pass(int L, int mode, const ColPassArgs& a, cudaStream_t st);
+template <typename C>
+void conv_apply(const ConvPlan& p, int nrhs, const C* u, C* y, const double* plane_dirs, bool add_u,
+                void* scratch1, void* scratch2, cudaStream_t st);
+size_t conv_scratch1_elems(int d, int n, int nrhs);
+size_t conv_scratch2_elems(int d, int n, int nrhs);
+void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st);
+void build_symbol(const ConvPlan& p, const double2* ktq, double2* sym64, float2* sym32, double2* work,
+                  cudaStream_t st);
+
+// ---------------------------------------------------------------- stencils (setup.cpp)
+// alpha for all 3^d classes (3^d x 3^d, zero outside mu) and C for the interior class,
+// computed on the host in FP64 from the (n+1)^d quadrant of k_t.
+void compute_stencils(int d, int n, int b, const std::vector<double2>& ktq, std::vector<double2>& alpha,
+                      std::vector<double2>& cint);
+
+// ---------------------------------------------------------------- stencil apply (stencil.cu)
+// r[i * rs_i + rhs * rs_r] = sum_t alpha_cls(i)(t) v[rhs * N + i + t]; v in the input
+// precision Cin, r in Cout.
+template <typename Cin, typename Cout>
+void stencil_apply(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, long rs_r, const void* alpha,
+                   cudaStream_t st);
+
+// ---------------------------------------------------------------- nested dissection (nd.cu)
+struct NdPlan;  // opaque: host symbolic + device index arrays
+NdPlan* nd_build(int d, int n, cudaStream_t st);
+void nd_free(NdPlan* p);
+struct NdInfo {
+  int levels, fronts, max_front;
+  int64_t factor_entries;
+  double factor_flops, solve_bytes;
+};
+NdInfo nd_info(const NdPlan* p);
+// factors: assembles M into the fronts and factors them, in C (float2 or double2)
+template <typename C>
+void nd_factor(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
+// x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
+template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);
+size_t nd_device_bytes(const NdPlan* p, int elem_bytes);
+
+}  // namespace ls

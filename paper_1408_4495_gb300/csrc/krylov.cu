@@ -1,0 +1,200 @@
+// FP64 Krylov kernels of the GMRES iteration (Sec. 3.3), batched over right-hand sides:
+// classical Gram-Schmidt with one reorthogonalisation (CGS2) against the Arnoldi basis,
+// norms, scaling, the solution update u += Z y and the residual g - A u.  Every vector is
+// laid out [nrhs][N] (complex128); reductions are two-stage with a fixed summation order,
+// so results do not depend on scheduling.
+#include "common.cuh"
+#include "krylov.h"
+
+namespace ls {
+
+constexpr int KT = 256;
+
+template <typename T> __device__ __forceinline__ double2 to64(T v) { return make_double2((double)v.x, (double)v.y); }
+
+__device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double2 r = make_double2(0, 0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { r.x += sh[i].x; r.y += sh[i].y; }
+  __syncthreads();
+  return r;
+}
+
+// partial[(rhs * nv + j) * nblk + blk] = sum over the block's chunk of conj(V_j) w
+template <typename Cw>
+__global__ void __launch_bounds__(KT) k_dots(const double2* const* __restrict__ V, int nv, const Cw* __restrict__ w,
+                                             long N, double2* __restrict__ partial, int nblk) {
+  __shared__ double2 sh[KT / 32];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  const long chunk = (N + nblk - 1) / nblk;
+  const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
+  const Cw* wr = w + (size_t)rhs * N;
+  for (int j = 0; j < nv; ++j) {
+    const double2* vr = V[j] + (size_t)rhs * N;
+    double2 acc = make_double2(0, 0);
+    for (long i = i0 + threadIdx.x; i < i1; i += KT) acc = cfma(acc, cconj(vr[i]), to64(wr[i]));
+    const double2 s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[((size_t)rhs * nv + j) * nblk + blk] = s;
+  }
+}
+
+// out[rhs * ostride + j] = sum_blk partial  (ordered), optionally accumulated into out
+__global__ void k_reduce(const double2* __restrict__ partial, int nv, int nrhs, int nblk, double2* out, int ostride,
+                         int accumulate) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv * nrhs) return;
+  const int rhs = t / nv, j = t % nv;
+  double2 s = make_double2(0, 0);
+  const double2* p = partial + ((size_t)rhs * nv + j) * nblk;
+  for (int b = 0; b < nblk; ++b) { s.x += p[b].x; s.y += p[b].y; }
+  double2* o = out + (size_t)rhs * ostride + j;
+  if (accumulate) { o->x += s.x; o->y += s.y; }
+  else *o = s;
+}
+
+// wout = win - sum_j V_j h[rhs][j]
+template <typename Cw>
+__global__ void k_sub_proj(const double2* const* __restrict__ V, int nv, const Cw* __restrict__ win, double2* wout,
+                           const double2* __restrict__ h, int hstride, long N, int nrhs) {
+  const long tot = N * nrhs;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x) {
+    const long rhs = idx / N;
+    double2 acc = to64(win[idx]);
+    const double2* hr = h + rhs * hstride;
+    for (int j = 0; j < nv; ++j) acc = cfms(acc, V[j][idx], hr[j]);
+    wout[idx] = acc;
+  }
+}
+
+// partial[rhs * nblk + blk] = sum |w|^2 over the chunk (as the .x of a double2)
+template <typename Cw>
+__global__ void __launch_bounds__(KT) k_norm2(const Cw* __restrict__ w, long N, double2* partial, int nblk) {
+  __shared__ double2 sh[KT / 32];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  const long chunk = (N + nblk - 1) / nblk;
+  const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
+  const Cw* wr = w + (size_t)rhs * N;
+  double2 acc = make_double2(0, 0);
+  for (long i = i0 + threadIdx.x; i < i1; i += KT) {
+    const double2 v = to64(wr[i]);
+    acc.x += v.x * v.x + v.y * v.y;
+  }
+  const double2 s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(size_t)rhs * nblk + blk] = s;
+}
+
+// out[rhs] = w[rhs] * scale[rhs]  (scale 0 clears)
+__global__ void k_scale(const double2* __restrict__ w, double2* out, const double* __restrict__ scale, long N, int nrhs) {
+  const long tot = N * nrhs;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x) {
+    const double s = scale[idx / N];
+    double2 v = w[idx];
+    v.x *= s;
+    v.y *= s;
+    out[idx] = v;
+  }
+}
+
+// u[rhs] += sum_j Z_j[rhs] y[rhs][j]
+template <typename Cz>
+__global__ void k_update_u(const Cz* const* __restrict__ Z, int nz, const double2* __restrict__ y, int ystride,
+                           double2* u, long N, int nrhs) {
+  const long tot = N * nrhs;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x) {
+    const long rhs = idx / N;
+    double2 acc = u[idx];
+    const double2* yr = y + rhs * ystride;
+    for (int j = 0; j < nz; ++j) acc = cfma(acc, to64(Z[j][idx]), yr[j]);
+    u[idx] = acc;
+  }
+}
+
+// r = g - Au
+__global__ void k_residual(const double2* __restrict__ g, const double2* __restrict__ Au, double2* r, long tot) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x)
+    r[idx] = csub(g[idx], Au[idx]);
+}
+
+template <typename Cin, typename Cout>
+__global__ void k_cast(const Cin* __restrict__ in, Cout* __restrict__ out, long tot) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x)
+    out[idx] = ccast<Cout>(in[idx]);
+}
+
+static unsigned grid_for(long tot) {
+  long b = (tot + 255) / 256;
+  if (b > 152L * 32) b = 152L * 32;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+int dots_blocks(long N) {
+  long b = (N + 4095) / 4096;
+  if (b > 64) b = 64;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename Cw>
+void dots(const double2* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride,
+          bool accumulate, cudaStream_t st) {
+  const int nblk = dots_blocks(N);
+  k_dots<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk);
+  LS_CHECK_LAUNCH();
+  k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, accumulate ? 1 : 0);
+  LS_CHECK_LAUNCH();
+}
+
+template <typename Cw>
+void sub_proj(const double2* const* V, int nv, const Cw* win, double2* wout, const double2* h, int hstride, long N,
+              int nrhs, cudaStream_t st) {
+  k_sub_proj<Cw><<<grid_for(N * nrhs), 256, 0, st>>>(V, nv, win, wout, h, hstride, N, nrhs);
+  LS_CHECK_LAUNCH();
+}
+
+template <typename Cw>
+void norms2(const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride, cudaStream_t st) {
+  const int nblk = dots_blocks(N);
+  k_norm2<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(w, N, partial, nblk);
+  LS_CHECK_LAUNCH();
+  k_reduce<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, 1, nrhs, nblk, out, ostride, 0);
+  LS_CHECK_LAUNCH();
+}
+
+void scale(const double2* w, double2* out, const double* s, long N, int nrhs, cudaStream_t st) {
+  k_scale<<<grid_for(N * nrhs), 256, 0, st>>>(w, out, s, N, nrhs);
+  LS_CHECK_LAUNCH();
+}
+
+template <typename Cz>
+void update_u(const Cz* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs, cudaStream_t st) {
+  k_update_u<Cz><<<grid_for(N * nrhs), 256, 0, st>>>(Z, nz, y, ystride, u, N, nrhs);
+  LS_CHECK_LAUNCH();
+}
+
+void residual(const double2* g, const double2* Au, double2* r, long tot, cudaStream_t st) {
+  k_residual<<<grid_for(tot), 256, 0, st>>>(g, Au, r, tot);
+  LS_CHECK_LAUNCH();
+}
+
+template <typename Cin, typename Cout> void cast(const Cin* in, Cout* out, long tot, cudaStream_t st) {
+  k_cast<Cin, Cout><<<grid_for(tot), 256, 0, st>>>(in, out, tot);
+  LS_CHECK_LAUNCH();
+}
+
+template void dots<float2>(const double2* const*, int, const float2*, long, int, double2*, double2*, int, bool, cudaStream_t);
+template void dots<double2>(const double2* const*, int, const double2*, long, int, double2*, double2*, int, bool, cudaStream_t);
+template void sub_proj<float2>(const double2* const*, int, const float2*, double2*, const double2*, int, long, int, cudaStream_t);
+template void sub_proj<double2>(const double2* const*, int, const double2*, double2*, const double2*, int, long, int, cudaStream_t);
+template void norms2<double2>(const double2*, long, int, double2*, double2*, int, cudaStream_t);
+template void update_u<float2>(const float2* const*, int, const double2*, int, double2*, long, int, cudaStream_t);
+template void update_u<double2>(const double2* const*, int, const double2*, int, double2*, long, int, cudaStream_t);
+template void cast<double2, float2>(const double2*, float2*, long, cudaStream_t);
+template void cast<float2, double2>(const float2*, double2*, long, cudaStream_t);
+
+}  // namespace ls

@@ -1,0 +1,26 @@
+// FP64 Krylov kernels (krylov.cu); vectors are [nrhs][N] complex.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ls {
+
+int dots_blocks(long N);
+// out[rhs * ostride + j] (+)= sum_i conj(V_j[rhs][i]) w[rhs][i], j < nv; partial: nrhs*nv*dots_blocks(N)
+template <typename Cw>
+void dots(const double2* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride,
+          bool accumulate, cudaStream_t st);
+// wout = win - sum_j V_j h[rhs * hstride + j]
+template <typename Cw>
+void sub_proj(const double2* const* V, int nv, const Cw* win, double2* wout, const double2* h, int hstride, long N,
+              int nrhs, cudaStream_t st);
+// out[rhs * ostride].x = |w[rhs]|^2
+template <typename Cw>
+void norms2(const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride, cudaStream_t st);
+void scale(const double2* w, double2* out, const double* s, long N, int nrhs, cudaStream_t st);
+template <typename Cz>
+void update_u(const Cz* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs, cudaStream_t st);
+void residual(const double2* g, const double2* Au, double2* r, long tot, cudaStream_t st);
+template <typename Cin, typename Cout> void cast(const Cin* in, Cout* out, long tot, cudaStream_t st);
+
+}  // namespace ls

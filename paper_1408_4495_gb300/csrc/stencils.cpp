@@ -1,0 +1,308 @@
+// Sparsifying stencils of Sec. 2.2 / Sec. 3.1 (eqs. Fmin, Emin, Cmin and the 3D sets
+// I_n, F_n, E_n, C_n), computed on the host in FP64.
+//
+// For a class of grid points with translated neighbourhood mu(0) and far set J, alpha is
+// the unit vector minimising |alpha K(mu(0), J)|: with K(mu, J) = U S V^*, alpha = U(:,end)^*.
+// K(mu, J) has |mu| <= 27 rows and up to (2n-1)^d columns, so it is never formed whole:
+//   1. X = K(mu, J)^* (tall, |J| x |mu|) is reduced to its R factor by a tall-skinny QR
+//      (Householder QR of row chunks, the R factors merged pairwise), chunks spread over
+//      host threads.  K = R^* Q^*, so the left singular vectors of K are the right
+//      singular vectors of R.
+//   2. R is diagonalised by one-sided (Hestenes) Jacobi rotations, R V = U S; alpha is the
+//      conjugate of the column of V with the smallest singular value.
+// Forming K K^* instead would square the condition number, and sigma_min / sigma_max is
+// small by design.  Only one class per number of faces is solved (interior, face, edge,
+// corner); the others are its mirror images and axis permutations, since k_t depends on
+// |t| only.  The centre coefficient of alpha is made real and positive.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ls {
+
+using cd = std::complex<double>;
+
+namespace {
+
+// In-place Householder QR of a column-major m x c matrix A (leading dimension m); on exit
+// the upper triangle of the top c x c block holds R.
+void householder_r(cd* A, int m, int c) {
+  for (int k = 0; k < c && k < m; ++k) {
+    cd* x = A + (size_t)k * m;
+    double nx2 = 0;
+    for (int i = k; i < m; ++i) nx2 += std::norm(x[i]);
+    const double nx = std::sqrt(nx2);
+    if (nx == 0) continue;
+    const double ax0 = std::abs(x[k]);
+    const cd ph = ax0 > 0 ? x[k] / ax0 : cd(1, 0);
+    const cd alpha = -ph * nx;
+    // v = x - alpha e_k (stored in x[k:m]), |v|^2 = 2 nx (nx + |x_k|)
+    x[k] -= alpha;
+    const double vn2 = 2.0 * nx * (nx + ax0);
+    for (int j = k + 1; j < c; ++j) {
+      cd* y = A + (size_t)j * m;
+      cd s = 0;
+      for (int i = k; i < m; ++i) s += std::conj(x[i]) * y[i];
+      s *= 2.0 / vn2;
+      for (int i = k; i < m; ++i) y[i] -= s * x[i];
+    }
+    x[k] = alpha;
+    for (int i = k + 1; i < m; ++i) x[i] = 0;
+  }
+}
+
+// R of [Ra; Rb] (both c x c upper triangular, row-major c x c)
+void merge_r(std::vector<cd>& Ra, const std::vector<cd>& Rb, int c) {
+  std::vector<cd> S((size_t)2 * c * c);  // column-major 2c x c
+  for (int j = 0; j < c; ++j)
+    for (int i = 0; i < c; ++i) {
+      S[(size_t)j * 2 * c + i] = Ra[(size_t)i * c + j];
+      S[(size_t)j * 2 * c + c + i] = Rb[(size_t)i * c + j];
+    }
+  householder_r(S.data(), 2 * c, c);
+  for (int i = 0; i < c; ++i)
+    for (int j = 0; j < c; ++j) Ra[(size_t)i * c + j] = j >= i ? S[(size_t)j * 2 * c + i] : cd(0, 0);
+}
+
+// One-sided Jacobi: returns singular values sig[c] and V (row-major c x c, column j is the
+// right singular vector of sig[j]) of the square matrix R (row-major).
+void jacobi_svd(const std::vector<cd>& R, int c, std::vector<double>& sig, std::vector<cd>& V) {
+  std::vector<cd> X(R);  // columns orthogonalised in place
+  V.assign((size_t)c * c, cd(0, 0));
+  for (int i = 0; i < c; ++i) V[(size_t)i * c + i] = 1;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < c - 1; ++p)
+      for (int q = p + 1; q < c; ++q) {
+        double a = 0, b = 0;
+        cd g = 0;
+        for (int i = 0; i < c; ++i) {
+          a += std::norm(X[(size_t)i * c + p]);
+          b += std::norm(X[(size_t)i * c + q]);
+          g += std::conj(X[(size_t)i * c + p]) * X[(size_t)i * c + q];
+        }
+        const double ag = std::abs(g);
+        if (ag == 0 || ag <= 1e-17 * std::sqrt(a * b)) continue;
+        off = std::max(off, ag / std::sqrt(a * b));
+        // rotate column q by the phase of g so that the pair's inner product is real,
+        // then apply the real Jacobi rotation that zeroes it
+        const cd e = std::conj(g) / ag;
+        const double zeta = (b - a) / (2 * ag);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::abs(zeta) + std::sqrt(1 + zeta * zeta));
+        const double cs = 1 / std::sqrt(1 + t * t), sn = cs * t;
+        for (int i = 0; i < c; ++i) {
+          const cd xp = X[(size_t)i * c + p], xq = X[(size_t)i * c + q] * e;
+          X[(size_t)i * c + p] = cs * xp - sn * xq;
+          X[(size_t)i * c + q] = sn * xp + cs * xq;
+          const cd vp = V[(size_t)i * c + p], vq = V[(size_t)i * c + q] * e;
+          V[(size_t)i * c + p] = cs * vp - sn * vq;
+          V[(size_t)i * c + q] = sn * vp + cs * vq;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  sig.assign(c, 0);
+  for (int j = 0; j < c; ++j) {
+    double s = 0;
+    for (int i = 0; i < c; ++i) s += std::norm(X[(size_t)i * c + j]);
+    sig[j] = std::sqrt(s);
+  }
+}
+
+struct ClassGeom {
+  int d;
+  std::vector<std::array<int, 3>> mu;  // offsets
+  int lo[3], hi[3];                    // far-set range per axis, inclusive
+  bool interior;
+};
+
+ClassGeom canonical_class(int d, int n, int b, int q) {
+  ClassGeom g;
+  g.d = d;
+  g.interior = (q == 0);
+  int mlo[3], mhi[3];
+  for (int a = 0; a < 3; ++a) {
+    mlo[a] = mhi[a] = 0;
+    g.lo[a] = g.hi[a] = 0;
+  }
+  for (int a = 0; a < d; ++a) {
+    if (a < q) {  // high face of axis a: mu in {-1, 0}, far set -n < j < -b
+      mlo[a] = -1; mhi[a] = 0;
+      g.lo[a] = -(n - 1); g.hi[a] = -b - 1;
+    } else {
+      mlo[a] = -1; mhi[a] = 1;
+      g.lo[a] = -(n - 1); g.hi[a] = n - 1;
+    }
+  }
+  for (int t0 = mlo[0]; t0 <= mhi[0]; ++t0)
+    for (int t1 = mlo[1]; t1 <= mhi[1]; ++t1)
+      for (int t2 = mlo[2]; t2 <= mhi[2]; ++t2) g.mu.push_back({t0, t1, t2});
+  return g;
+}
+
+// alpha for a canonical class (offsets in g.mu order)
+std::vector<cd> solve_class(const ClassGeom& g, int n, const std::vector<double2>& ktq) {
+  const int d = g.d, c = (int)g.mu.size();
+  const long n1 = n + 1;
+  long ext[3] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) ext[a] = g.hi[a] - g.lo[a] + 1;
+  const long M = ext[0] * ext[1] * ext[2];
+  auto kval = [&](int t0, int t1, int t2) -> cd {
+    long idx = std::abs(t0);
+    if (d >= 2) idx = idx * n1 + std::abs(t1);
+    if (d >= 3) idx = idx * n1 + std::abs(t2);
+    const double2 v = ktq[idx];
+    return cd(v.x, v.y);
+  };
+  const int nthreads = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  const long chunk = 4096;
+  const long nchunks = (M + chunk - 1) / chunk;
+  std::vector<std::vector<cd>> Rt(nthreads, std::vector<cd>((size_t)c * c, cd(0, 0)));
+  std::vector<char> have(nthreads, 0);
+  auto work = [&](int tid) {
+    std::vector<cd> A((size_t)chunk * c);
+    std::vector<cd> Rc((size_t)c * c);
+    for (long ch = tid; ch < nchunks; ch += nthreads) {
+      const long r0 = ch * chunk, r1 = std::min(M, r0 + chunk);
+      const int m = (int)(r1 - r0);
+      // skip far points that coincide with mu (interior class: J = box minus mu)
+      int rows = 0;
+      for (long r = r0; r < r1; ++r) {
+        long q = r;
+        int j[3] = {0, 0, 0};
+        for (int a = d - 1; a >= 0; --a) {
+          j[a] = (int)(q % ext[a]) + g.lo[a];
+          q /= ext[a];
+        }
+        if (g.interior) {
+          int mx = 0;
+          for (int a = 0; a < d; ++a) mx = std::max(mx, std::abs(j[a]));
+          if (mx <= 1) continue;
+        }
+        for (int col = 0; col < c; ++col) {
+          const auto& t = g.mu[col];
+          A[(size_t)col * m + rows] = std::conj(kval(t[0] - j[0], t[1] - j[1], t[2] - j[2]));
+        }
+        ++rows;
+      }
+      if (rows == 0) continue;
+      // compact columns to leading dimension `rows`
+      if (rows < m)
+        for (int col = 1; col < c; ++col)
+          std::copy(A.begin() + (size_t)col * m, A.begin() + (size_t)col * m + rows, A.begin() + (size_t)col * rows);
+      householder_r(A.data(), rows, c);
+      for (int i = 0; i < c; ++i)
+        for (int jj = 0; jj < c; ++jj)
+          Rc[(size_t)i * c + jj] = (jj >= i && i < rows) ? A[(size_t)jj * rows + i] : cd(0, 0);
+      if (!have[tid]) {
+        Rt[tid] = Rc;
+        have[tid] = 1;
+      } else {
+        merge_r(Rt[tid], Rc, c);
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto& t : th) t.join();
+  std::vector<cd> R;
+  bool first = true;
+  for (int t = 0; t < nthreads; ++t) {
+    if (!have[t]) continue;
+    if (first) { R = Rt[t]; first = false; }
+    else merge_r(R, Rt[t], c);
+  }
+  if (first) LS_FAIL(EINVAL_, "empty far set (n too small for buffer b)");
+  std::vector<double> sig;
+  std::vector<cd> V;
+  jacobi_svd(R, c, sig, V);
+  int jmin = 0, j2 = -1;
+  for (int j = 1; j < c; ++j)
+    if (sig[j] < sig[jmin]) jmin = j;
+  for (int j = 0; j < c; ++j)
+    if (j != jmin && (j2 < 0 || sig[j] < sig[j2])) j2 = j;
+  if (sig[jmin] > 0 && sig[j2] / sig[jmin] < 1.0 + 1e-8)
+    LS_FAIL(EINVAL_, "smallest singular value of K(mu, far) is not simple; stencil undetermined");
+  std::vector<cd> alpha(c);
+  for (int i = 0; i < c; ++i) alpha[i] = std::conj(V[(size_t)i * c + jmin]);
+  // centre coefficient real and positive
+  int ci = -1;
+  for (int i = 0; i < c; ++i)
+    if (g.mu[i][0] == 0 && g.mu[i][1] == 0 && g.mu[i][2] == 0) ci = i;
+  const cd ph = alpha[ci] / std::abs(alpha[ci]);
+  for (auto& a : alpha) a /= ph;
+  return alpha;
+}
+
+}  // namespace
+
+void compute_stencils(int d, int n, int b, const std::vector<double2>& ktq, std::vector<double2>& alpha,
+                      std::vector<double2>& cint) {
+  int p3 = 1;
+  for (int a = 0; a < d; ++a) p3 *= 3;
+  alpha.assign((size_t)p3 * p3, make_double2(0, 0));
+  cint.assign(p3, make_double2(0, 0));
+  std::vector<std::vector<cd>> can(d + 1);
+  std::vector<ClassGeom> geo;
+  for (int q = 0; q <= d; ++q) {
+    geo.push_back(canonical_class(d, n, b, q));
+    can[q] = solve_class(geo[q], n, ktq);
+  }
+  // map the canonical solutions onto all 3^d classes
+  for (int ci = 0; ci < p3; ++ci) {
+    int cls[3] = {0, 0, 0};
+    int rem = ci;
+    for (int a = d - 1; a >= 0; --a) {
+      cls[a] = rem % 3 - 1;
+      rem /= 3;
+    }
+    int perm[3], q = 0;  // perm[a] = canonical axis of class axis a
+    for (int a = 0; a < d; ++a)
+      if (cls[a] != 0) perm[a] = q++;
+    int z = q;
+    for (int a = 0; a < d; ++a)
+      if (cls[a] == 0) perm[a] = z++;
+    const ClassGeom& g = geo[q];
+    for (size_t k = 0; k < g.mu.size(); ++k) {
+      // canonical offset -> class offset: t[a] = f_a * t_can[perm[a]]
+      int t[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) {
+        const int f = cls[a] < 0 ? -1 : 1;
+        t[a] = f * g.mu[k][perm[a]];
+      }
+      int ti = 0;
+      for (int a = 0; a < d; ++a) ti = ti * 3 + (t[a] + 1);
+      alpha[(size_t)ci * p3 + ti] = make_double2(can[q][k].real(), can[q][k].imag());
+    }
+  }
+  // C(0, t') = sum_{t in mu} alpha_t k_{t - t'} for the interior class
+  const long n1 = n + 1;
+  const int interior = (p3 - 1) / 2;
+  for (int tp = 0; tp < p3; ++tp) {
+    int tpv[3] = {0, 0, 0};
+    int r = tp;
+    for (int a = d - 1; a >= 0; --a) { tpv[a] = r % 3 - 1; r /= 3; }
+    cd acc = 0;
+    for (int t = 0; t < p3; ++t) {
+      int tv[3] = {0, 0, 0};
+      int rr = t;
+      for (int a = d - 1; a >= 0; --a) { tv[a] = rr % 3 - 1; rr /= 3; }
+      long idx = 0;
+      for (int a = 0; a < d; ++a) idx = idx * n1 + std::abs(tv[a] - tpv[a]);
+      const double2 av = alpha[(size_t)interior * p3 + t];
+      acc += cd(av.x, av.y) * cd(ktq[idx].x, ktq[idx].y);
+    }
+    cint[tp] = make_double2(acc.real(), acc.imag());
+  }
+}
+
+}  // namespace ls

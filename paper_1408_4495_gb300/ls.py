@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libls (``include/ls.h``): argument marshalling only.
+
+Every step of the solve runs inside the CUDA library; this module only turns numpy arrays
+(host) or torch CUDA tensors (device) into pointers and sizes.  If the library has not
+been built, or cannot be loaded, every call raises: there is no CPU path.
+
+Complex arrays cross the boundary as interleaved (re, im) float64, C order, right-hand
+sides outermost, i.e. numpy ``complex128`` of shape ``(nrhs,) + (n,) * d`` or a torch
+``complex128`` CUDA tensor of that shape.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libls.so")
+
+LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ENOCONV, LS_ESTATE, LS_ETIMEOUT, LS_EBUFFER = range(8)
+LS_PREC_FP64, LS_PREC_MIXED = 0, 1
+STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS_ESTATE", "LS_ETIMEOUT", "LS_EBUFFER"]
+
+# every entry point declared in include/ls.h
+EXPORTS = ["ls_setup", "ls_factor", "ls_rhs_plane_wave", "ls_solve", "ls_last_error", "ls_free",
+           "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats"]
+
+
+class LsGrid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("buffer_b", ctypes.c_int),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class LsInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("rel_resid", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+class LsNdStats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("fronts", ctypes.c_int), ("max_front", ctypes.c_int),
+                ("factor_entries", ctypes.c_int64), ("factor_flops", ctypes.c_double),
+                ("solve_bytes", ctypes.c_double)]
+
+
+class LsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libls (raises if it is missing: build it with paper_1408_4495_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libls not built ({path} missing); run python -m paper_1408_4495_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ls_setup.argtypes = [ctypes.POINTER(LsGrid), dp, vp, vp, ctypes.POINTER(vp)]
+    lib.ls_factor.argtypes = [vp]
+    lib.ls_rhs_plane_wave.argtypes = [vp, ip, vp, vp]
+    lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
+    lib.ls_last_error.argtypes = [vp]
+    lib.ls_last_error.restype = ctypes.c_char_p
+    lib.ls_free.argtypes = [vp]
+    lib.ls_free.restype = None
+    lib.ls_kernel_table.argtypes = [vp, vp]
+    lib.ls_stencils.argtypes = [vp, vp, vp]
+    lib.ls_apply.argtypes = [vp, ip, vp, vp, ip]
+    lib.ls_stencil_apply.argtypes = [vp, ip, vp, vp, ip]
+    lib.ls_precond.argtypes = [vp, ip, vp, vp]
+    lib.ls_get_nd_stats.argtypes = [vp, ctypes.POINTER(LsNdStats)]
+    for name in EXPORTS:
+        if name not in ("ls_last_error", "ls_free"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (device or host)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    refinements: int
+    rel_resid: float
+    converged: bool
+
+
+class Solver:
+    """One medium on one grid: ``ls_setup`` at construction, ``ls_free`` on close."""
+
+    def __init__(self, m, omega: float, dim: int | None = None, buffer_b: int = 2, restart: int = 50,
+                 max_iter: int = 500, mixed: bool = True, stream=None):
+        self.lib = load()
+        if isinstance(m, np.ndarray):
+            m = np.ascontiguousarray(m, dtype=np.float64)
+        self.d = dim if dim is not None else m.ndim
+        self.n = int(m.shape[0])
+        self.N = self.n ** self.d
+        self.omega = float(omega)
+        self.mixed = mixed
+        g = LsGrid(self.d, self.n, buffer_b, restart, max_iter, LS_PREC_MIXED if mixed else LS_PREC_FP64)
+        h = ctypes.c_void_p()
+        st = self.lib.ls_setup(ctypes.byref(g), self.omega, _ptr(m), _stream_ptr(stream), ctypes.byref(h))
+        if st != LS_OK:
+            raise LsError(st, self.lib.ls_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st, allow=()):
+        if st != LS_OK and st not in allow:
+            raise LsError(st, self.lib.ls_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ls_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- the path
+    def factor(self):
+        self._check(self.lib.ls_factor(self.h))
+
+    def rhs_plane_wave(self, dirs, out=None):
+        dirs_np = dirs if not isinstance(dirs, np.ndarray) else np.ascontiguousarray(dirs, dtype=np.float64)
+        nrhs = int(dirs_np.shape[0])
+        if out is None:
+            shape = (nrhs,) + (self.n,) * self.d
+            if isinstance(dirs_np, np.ndarray):
+                out = np.empty(shape, dtype=np.complex128)
+            else:  # a torch tensor: output on the same device
+                import torch
+                out = torch.empty(shape, dtype=torch.complex128, device=dirs_np.device)
+        self._check(self.lib.ls_rhs_plane_wave(self.h, nrhs, _ptr(dirs_np), _ptr(out)))
+        return out
+
+    def solve(self, rhs, tol: float = 1e-6, out=None, raise_on_noconv: bool = True):
+        nrhs = int(rhs.shape[0])
+        if out is None:
+            out = np.empty_like(rhs) if isinstance(rhs, np.ndarray) else rhs.new_empty(rhs.shape)
+        infos = (LsInfo * nrhs)()
+        st = self.lib.ls_solve(self.h, nrhs, _ptr(rhs), float(tol), _ptr(out), infos)
+        self._check(st, allow=() if raise_on_noconv else (LS_ENOCONV,))
+        return out, [SolveInfo(i.iters, i.refinements, i.rel_resid, bool(i.converged)) for i in infos]
+
+    # ---- inspection entry points
+    def kernel_table(self):
+        out = np.empty((self.n + 1,) * self.d, dtype=np.complex128)
+        self._check(self.lib.ls_kernel_table(self.h, _ptr(out)))
+        return out
+
+    def stencils(self):
+        p3 = 3 ** self.d
+        a = np.empty((p3, p3), dtype=np.complex128)
+        c = np.empty(p3, dtype=np.complex128)
+        self._check(self.lib.ls_stencils(self.h, _ptr(a), _ptr(c)))
+        return a, c
+
+    def _unary(self, fn, x, *extra):
+        nrhs = int(x.shape[0])
+        out = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        self._check(fn(self.h, nrhs, _ptr(x), _ptr(out), *extra))
+        return out
+
+    def apply(self, x, mixed: bool | None = None):
+        mixed = self.mixed if mixed is None else mixed
+        return self._unary(self.lib.ls_apply, x, LS_PREC_MIXED if mixed else LS_PREC_FP64)
+
+    def stencil_apply(self, x, mixed: bool | None = None):
+        mixed = self.mixed if mixed is None else mixed
+        return self._unary(self.lib.ls_stencil_apply, x, LS_PREC_MIXED if mixed else LS_PREC_FP64)
+
+    def precond(self, x):
+        return self._unary(self.lib.ls_precond, x)
+
+    def nd_stats(self) -> dict:
+        s = LsNdStats()
+        self._check(self.lib.ls_get_nd_stats(self.h, ctypes.byref(s)))
+        return dict(levels=s.levels, fronts=s.fronts, max_front=s.max_front, factor_entries=s.factor_entries,
+                    factor_flops=s.factor_flops, solve_bytes=s.solve_bytes)

@@ -1,0 +1,224 @@
+"""Parity of each step of the CUDA path with the FP64 oracle, through the C-ABI.
+
+Tolerances: FP64 steps agree with the oracle to rounding (relative <= 1e-11 for the Nystrom
+table, the operator and the right-hand side: CUDA's j0/y0 and scipy's hankel1 differ by a
+few 1e-12 relative at large arguments; <= 1e-10 for the sparse solve whose condition
+number amplifies rounding);
+FP32 steps to the FP32 unit roundoff times a small growth factor (relative L2 <= 2e-5 for
+the FFT apply, whose error grows like eps32 * log2(L^d); <= 1e-3 for the FP32 ND solve of
+an indefinite matrix).  Solutions: relative residual <= 1e-6 and relative L2 difference
+<= 1e-5 from the oracle solved to 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1408_4495_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def medium(d, n, seed=0, amp=0.25):
+    rng = np.random.default_rng(seed)
+    nb = 3
+    m = W.bumps(n, d, rng.uniform(-amp, amp, nb), rng.uniform(0.06, 0.12, nb), rng.uniform(0.3, 0.7, (nb, d)))
+    return W.enforce_buffer(m, 2)
+
+
+def rand_c(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.fixture(scope="module")
+def LS():
+    from paper_1408_4495_gb300 import build, ls
+    build.build()
+    return ls
+
+
+CASES = [(2, 16, 2.0), (2, 32, 4.0), (2, 64, 6.0), (3, 8, 1.0), (3, 16, 2.0)]
+
+
+@pytest.mark.parametrize("d,n,freq", CASES)
+def test_kernel_table(LS, d, n, freq):
+    omega = 2 * np.pi * freq
+    with LS.Solver(medium(d, n), omega, mixed=False) as s:
+        kt = s.kernel_table()
+    q = np.arange(n + 1)
+    T = np.stack(np.meshgrid(*([q] * d), indexing="ij"), -1)
+    ref = O.kernel_value(d, omega, O.grid_h(n), T)
+    assert np.max(np.abs(kt - ref) / np.abs(ref)) < 1e-11
+
+
+@pytest.mark.parametrize("d,n,freq", CASES)
+def test_stencils(LS, d, n, freq):
+    omega = 2 * np.pi * freq
+    with LS.Solver(medium(d, n), omega, mixed=False) as s:
+        A, C = s.stencils()
+    sten, (mu0, c) = O.all_stencils(n, d, omega, 2)
+    p3 = 3**d
+    ref = np.zeros((p3, p3), complex)
+    for cls, (mu, alpha) in sten.items():
+        ci = sum((cls[a] + 1) * 3 ** (d - 1 - a) for a in range(d))
+        for t, a in zip(mu, alpha):
+            ref[ci, sum((t[x] + 1) * 3 ** (d - 1 - x) for x in range(d))] = a
+    refc = np.zeros(p3, complex)
+    for t, cv in zip(mu0, c):
+        refc[sum((t[x] + 1) * 3 ** (d - 1 - x) for x in range(d))] = cv
+    assert np.max(np.abs(A - ref)) < 1e-9
+    assert np.max(np.abs(C - refc)) < 1e-9 * np.max(np.abs(refc))
+
+
+@pytest.mark.parametrize("d,n,freq", CASES)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_operator_apply(LS, d, n, freq, mixed):
+    omega = 2 * np.pi * freq
+    m = medium(d, n)
+    nrhs = 3
+    x = rand_c((nrhs,) + (n,) * d, 11)
+    kt = O.kernel_table(n, d, omega)
+    ref = np.array([O.apply_operator(kt, omega, m, x[j]) for j in range(nrhs)])
+    with LS.Solver(m, omega, mixed=mixed) as s:
+        y = s.apply(x)
+    assert rel(y, ref) < (2e-5 if mixed else 1e-11)
+    if n <= 16 and d == 2:
+        direct = np.array([O.apply_operator(kt, omega, m, x[j], direct=True) for j in range(nrhs)])
+        assert rel(y, direct) < (2e-5 if mixed else 1e-11)
+
+
+@pytest.mark.parametrize("d,n,freq", CASES)
+def test_rhs_plane_wave(LS, d, n, freq):
+    omega = 2 * np.pi * freq
+    m = medium(d, n)
+    dirs = W.directions_circle(3) if d == 2 else W.directions_sphere(3, 5)
+    kt = O.kernel_table(n, d, omega)
+    ref = np.array([O.rhs(kt, omega, m, dr) for dr in dirs])
+    with LS.Solver(m, omega, mixed=True) as s:
+        g = s.rhs_plane_wave(dirs)
+    assert rel(g, ref) < 1e-11
+
+
+@pytest.mark.parametrize("d,n,freq", CASES)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_stencil_apply(LS, d, n, freq, mixed):
+    omega = 2 * np.pi * freq
+    m = medium(d, n)
+    x = rand_c((2,) + (n,) * d, 12)
+    sten, cint = O.all_stencils(n, d, omega, 2)
+    M, S = O.assemble(n, d, omega, m, sten, cint)
+    ref = np.array([(S @ x[j].reshape(-1)).reshape(x[j].shape) for j in range(2)])
+    with LS.Solver(m, omega, mixed=mixed) as s:
+        r = s.stencil_apply(x)
+    assert rel(r, ref) < (1e-6 if mixed else 1e-12)
+
+
+@pytest.mark.parametrize("d,n,freq", CASES)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_preconditioner(LS, d, n, freq, mixed):
+    omega = 2 * np.pi * freq
+    m = medium(d, n)
+    nrhs = 3
+    x = rand_c((nrhs,) + (n,) * d, 13)
+    sten, cint = O.all_stencils(n, d, omega, 2)
+    M, S = O.assemble(n, d, omega, m, sten, cint)
+    P = O.Preconditioner(M, S, n, d)
+    ref = np.array([P(x[j].reshape(-1)).reshape(x[j].shape) for j in range(nrhs)])
+    with LS.Solver(m, omega, mixed=mixed) as s:
+        s.factor()
+        z = s.precond(x)
+    assert rel(z, ref) < (1e-3 if mixed else 1e-10)
+
+
+def test_plain_fp64_solve_matches_oracle_iterates():
+    """2D n=32 plain FP64 workload: identical algorithm in FP64, so the same iteration count
+    and the same solution to rounding."""
+    from paper_1408_4495_gb300 import ls as LSm
+    w = W.plain_2d(32)
+    m = W.enforce_buffer(w.m, 2)
+    ref = O.solve(w.n, 2, w.omega, m, w.directions)
+    with LSm.Solver(m, w.omega, mixed=False) as s:
+        s.factor()
+        g = s.rhs_plane_wave(w.directions)
+        assert rel(g.reshape(1, -1), ref["g"]) < 1e-11
+        u, info = s.solve(g, tol=1e-6)
+    assert info[0].iters == ref["iters"][0]
+    assert info[0].rel_resid <= 1e-6
+    assert rel(u.reshape(1, -1), ref["u"]) < 1e-8
+
+
+@pytest.mark.parametrize("d,n,freq,nrhs", [(2, 64, 8.0, 4), (2, 128, 16.0, 3), (3, 16, 2.0, 3)])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batched_solve(LS, d, n, freq, nrhs, mixed):
+    omega = 2 * np.pi * freq
+    m = medium(d, n, seed=3)
+    dirs = W.directions_circle(nrhs) if d == 2 else W.directions_sphere(nrhs, 7)
+    ref = O.solve(n, d, omega, m, dirs, tol=1e-10)
+    ref6 = O.solve(n, d, omega, m, dirs, tol=1e-6)
+    with LS.Solver(m, omega, mixed=mixed) as s:
+        s.factor()
+        g = s.rhs_plane_wave(dirs)
+        u, info = s.solve(g, tol=1e-6)
+    for j in range(nrhs):
+        assert info[j].converged and info[j].rel_resid <= 1e-6
+        assert rel(u[j].reshape(-1), ref["u"][j]) < 1e-5
+        assert abs(info[j].iters - ref6["iters"][j]) <= 2
+        # the returned residual is the true one: check it with the oracle operator
+        kt = ref["ktab"]
+        r = ref["g"][j] - O.apply_operator(kt, omega, m, u[j]).reshape(-1)
+        assert np.linalg.norm(r) / np.linalg.norm(ref["g"][j]) < 1.01e-6
+
+
+def test_device_pointers_round_trip(LS):
+    torch = pytest.importorskip("torch")
+    d, n, freq = 2, 32, 4.0
+    omega = 2 * np.pi * freq
+    m = medium(d, n)
+    x = rand_c((2, n, n), 21)
+    with LS.Solver(m, omega, mixed=False) as s:
+        s.factor()
+        yh = s.apply(x)
+        xd = torch.from_numpy(x).cuda()
+        yd = s.apply(xd)
+        assert rel(yd.cpu().numpy(), yh) < 1e-15
+        g = s.rhs_plane_wave(torch.tensor(W.directions_circle(2)).cuda())
+        u, info = s.solve(g)
+        uh, infoh = s.solve(g.cpu().numpy())
+        assert rel(u.cpu().numpy(), uh) < 1e-14
+        assert [i.iters for i in info] == [i.iters for i in infoh]
+
+
+def test_zero_medium_gives_zero_in_zero_iterations(LS):
+    n = 32
+    with LS.Solver(np.zeros((n, n)), 2 * np.pi * 4, mixed=True) as s:
+        s.factor()
+        g = s.rhs_plane_wave(np.array([[1.0, 0.0]]))
+        assert np.all(g == 0)
+        u, info = s.solve(g)
+    assert np.all(u == 0) and info[0].iters == 0 and info[0].converged
+
+
+def test_errors_are_reported_not_raised_in_the_library(LS):
+    n = 32
+    m = np.zeros((n, n))
+    m[1, 10] = 0.1  # inside the buffer
+    with pytest.raises(LS.LsError) as e:
+        LS.Solver(m, 10.0)
+    assert e.value.status == LS.LS_EBUFFER
+    with pytest.raises(LS.LsError) as e:
+        LS.Solver(np.zeros((24, 24)), 10.0)
+    assert e.value.status == LS.LS_EINVAL
+    m2 = np.zeros((n, n))
+    m2[10, 10] = 1.5  # 1 - m <= 0
+    with pytest.raises(LS.LsError) as e:
+        LS.Solver(m2, 10.0)
+    assert e.value.status == LS.LS_EINVAL
+    with LS.Solver(np.zeros((n, n)), 10.0) as s:
+        with pytest.raises(LS.LsError) as e:
+            s.solve(np.zeros((1, n, n), complex))
+        assert e.value.status == LS.LS_ESTATE
