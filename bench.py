@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Throughput of the sparsifying-preconditioned Lippmann-Schwinger solve on one GB300.
+
+Workload (the 2D batched configuration): unit square, n = 256 (h = 1/257), omega = 2 pi 32,
+medium = 8 seeded Gaussian bumps (A ~ U[-0.3, 0.3], w ~ U[0.03, 0.1], c ~ U[0.2, 0.8]^2)
+times a smooth cutoff, 16 plane waves evenly spaced on the circle, GMRES(50) to relative
+residual 1e-6, mixed precision (FP32 operator / stencil / fronts, FP64 Arnoldi and FP64
+refinement).  One step = ls_factor (assembly + nested-dissection LU of the medium) +
+ls_rhs_plane_wave (16 right-hand sides) + ls_solve (16 right-hand sides).  The tables that
+depend only on (n, omega) -- the Nystrom symbol and the SVD stencils -- are built once by
+ls_setup before timing, as the library caches them per (n, omega).
+
+Metric: solves/s = right-hand sides converged to 1e-6 per second, whole job.
+The identical FP64 GPU path is timed beside it ("plain_fp64").
+
+--impl reference times the FP64 CPU oracle (oracle/) on the same workload and step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "solves/s at rel. residual 1e-6, mixed vs plain FP64 on 1 GB300; p50/p99 latency"
+TOL = 1e-6
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload():
+    from paper_1408_4495_gb300 import workloads as W
+    w = W.bumps_2d(256, 32.0, 8, 16, 1002)
+    w.m = W.enforce_buffer(w.m, w.buffer_b)
+    return w
+
+
+def config(w, extra=None):
+    c = {"workload": "2d_bumps_n256_omega2pi32_16rhs", "d": w.d, "n": w.n, "N": w.n ** w.d,
+         "omega": w.omega, "nrhs": w.nrhs, "tol": TOL, "restart": w.restart,
+         "precision": "mixed: FP32 complex operator/stencil/fronts, FP64 Arnoldi + refinement",
+         "step": "ls_factor + ls_rhs_plane_wave + ls_solve (all 16 right-hand sides)",
+         "cached_per_n_omega": "Nystrom symbol and SVD stencils (built by ls_setup before timing)",
+         "l2": "flushed between timed steps (256 MiB device write outside the events)",
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------ oracle timing
+def oracle_step(w, ktab, sten, cint, nrhs=None, workers=None):
+    """One step of the workload on the CPU oracle: assembly + sparse LU of the medium, the
+    right-hand sides and the preconditioned GMRES solves.  Returns (seconds, iterations)."""
+    import oracle as O
+    nr = w.nrhs if nrhs is None else nrhs
+    t0 = time.perf_counter()
+    M, S = O.assemble(w.n, w.d, w.omega, w.m, sten, cint)
+    P = O.Preconditioner(M, S, w.n, w.d)
+    shape = (w.n,) * w.d
+
+    def A(x):
+        return O.apply_operator(ktab, w.omega, w.m, x.reshape(shape), workers=workers).reshape(-1)
+
+    its = []
+    for j in range(nr):
+        g = O.rhs(ktab, w.omega, w.m, w.directions[j], workers=workers).reshape(-1)
+        _, it, _ = O.gmres_right(A, P, g, TOL, w.restart)
+        its.append(it)
+    return time.perf_counter() - t0, its
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_tables(w):
+    import oracle as O
+    return O.kernel_table(w.n, w.d, w.omega), *O.all_stencils(w.n, w.d, w.omega, w.buffer_b)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload()
+    cores = cpu_cores()
+    ktab, sten, cint = oracle_tables(w)
+    for _ in range(args.warmup):
+        oracle_step(w, ktab, sten, cint, workers=cores)
+    times, its = [], []
+    for _ in range(args.steps):
+        t, it = oracle_step(w, ktab, sten, cint, workers=cores)
+        times.append(t)
+        its += it
+    total = sum(times)
+    value = w.nrhs * args.steps / total
+    sample = (f"full step ({w.nrhs} right-hand sides, assembly + SuperLU factor + GMRES) per step; "
+              f"scipy.fft workers={cores}, SuperLU serial; Nystrom table and stencils built before timing")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(w, {"precision": "FP64 (CPU oracle)"}),
+            "iters": {"min": min(its), "max": max(its)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def algorithmic_bytes(cls, w):
+    """Bytes one launch of a kernel class must move (reads + writes), per the pass design:
+    FP32 complex = 8 B, FP64 complex = 16 B, lines of n (grid) or L = 2n (padded)."""
+    n, N, R = w.n, w.n ** w.d, w.nrhs
+    c = 8 if cls.endswith("_c64") else 16
+    wb = 4 if c == 8 else 8
+    if cls.startswith("fft_row_fwd"):      # read u (n per line), weights once; write L per line
+        return R * N * c * 3 + N * wb
+    if cls.startswith("fft_col_sym"):      # read and write n x L per right-hand side, symbol once
+        return R * 2 * (n * 2 * n) * c + (n + 1) ** 2 * c
+    if cls.startswith("fft_row_inv"):      # read L per line + u, write y
+        return R * N * c * 4
+    if cls.startswith("stencil"):
+        return R * N * (16 + c)             # read FP64 v, write r
+    raise ValueError(cls)
+
+
+def run_gpu(args):
+    import torch
+    from paper_1408_4495_gb300 import ls
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload()
+    stream = torch.cuda.Stream(device=dev)
+    m_dev = torch.tensor(w.m, device=dev)
+    dirs_dev = torch.tensor(w.directions, device=dev)
+    shape = (w.nrhs,) + (w.n,) * w.d
+    g = torch.empty(shape, dtype=torch.complex128, device=dev)
+    u = torch.empty(shape, dtype=torch.complex128, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def make(mixed):
+        t0 = time.perf_counter()
+        s = ls.Solver(m_dev, w.omega, dim=w.d, buffer_b=w.buffer_b, restart=w.restart, mixed=mixed, stream=stream)
+        return s, time.perf_counter() - t0
+
+    def step(s):
+        s.factor()
+        s.rhs_plane_wave(dirs_dev, out=g)
+        _, info = s.solve(g, TOL, out=u)
+        return info
+
+    def timed(s, steps, warmup, prof_class=None, clocks=False):
+        for _ in range(warmup):
+            step(s)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local_uuid(torch, local)) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        ls.profile_start(prof_class)
+        evs, infos = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(s))
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        prof = ls.profile_stop()
+        ck = sampler.stop() if sampler else None
+        total_ms = sum(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+            torch.distributed.barrier()
+        return total_ms, infos, prof, ck
+
+    # ---- mixed precision (the headline)
+    s_mix, setup_s = make(True)
+    nd = s_mix.nd_stats()
+    total_ms, infos, prof, clocks = timed(s_mix, args.steps, args.warmup, args.profile_class, clocks=True)
+    value = w.nrhs * args.steps * world / (total_ms / 1e3)
+    its = [i.iters for inf in infos for i in inf]
+    res = [i.rel_resid for inf in infos for i in inf]
+    conv = all(i.converged for inf in infos for i in inf)
+    launches = prof["total"]
+
+    # roofline of the timed kernel class
+    roof = None
+    tc = prof["timed"]
+    if tc["launches"] > 0:
+        avg_ms = tc["ms"] / tc["launches"]
+        abytes = algorithmic_bytes(tc["class"], w)
+        achieved = abytes / (avg_ms / 1e3) / 1e9
+        peak, peak_src = measured_hbm_peak()
+        roof = {"kernel": tc["class"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": args.traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_ms * 1e3,
+                "launches_timed": tc["launches"], "share_of_step_time": tc["ms"] / total_ms}
+
+    if args.only_mixed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "only_mixed": True,
+                              "ms_per_step": total_ms / args.steps, "iters": {"min": min(its), "max": max(its)},
+                              "gpu_launches": launches, "roofline": roof}), flush=True)
+        s_mix.close()
+        return 0
+
+    # ---- plain FP64 path beside it
+    s64, _ = make(False)
+    k64 = max(1, min(args.steps, 5))
+    ms64, infos64, _, _ = timed(s64, k64, 1)
+    value64 = w.nrhs * k64 * world / (ms64 / 1e3)
+    its64 = [i.iters for inf in infos64 for i in inf]
+    s64.close()
+
+    # ---- end to end through the public API with host buffers (pinned)
+    m_host = torch.tensor(w.m).pin_memory()
+    dirs_host = torch.tensor(w.directions).pin_memory()
+    u_host = torch.empty(shape, dtype=torch.complex128).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        with ls.Solver(m_host.numpy(), w.omega, dim=w.d, buffer_b=w.buffer_b, restart=w.restart, mixed=True,
+                       stream=stream) as s:
+            s.factor()
+            s.rhs_plane_wave(dirs_host.numpy(), out=g)
+            s.solve(g, TOL, out=u_host.numpy())
+        return float(np.abs(u_host.numpy()).max())
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": w.nrhs * e2e_steps * world / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": int(m_host.numel() * 8 + dirs_host.numel() * 8),
+           "d2h_bytes_per_step": int(u_host.numel() * 16),
+           "includes": "ls_setup (medium from pinned host) + ls_factor + ls_rhs_plane_wave + ls_solve "
+                       "(solution to pinned host) + ls_free, wall clock"}
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        ktab, sten, cint = oracle_tables(w)
+        t, _ = oracle_step(w, ktab, sten, cint, nrhs=4, workers=cores)
+        t_fac = oracle_factor_time(w, sten, cint)
+        per_rhs = (t - t_fac) / 4
+        step_s = t_fac + per_rhs * w.nrhs
+        cpu = {"value": w.nrhs / step_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"assembly + SuperLU factor + 4 of the {w.nrhs} right-hand sides (GMRES), "
+                         f"per-RHS time scaled to {w.nrhs}; scipy.fft workers={cores}, SuperLU serial"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128", "data": "synthetic",
+                "config": config(w), "iters": {"min": min(its), "max": max(its)},
+                "max_rel_resid": max(res), "all_converged": conv,
+                "plain_fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / k64, "steps": k64,
+                               "iters": {"min": min(its64), "max": max(its64)}},
+                "mixed_over_fp64": value / value64,
+                "setup_ms": setup_s * 1e3, "nd": nd,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "launches_by_class": prof["counts"], "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    s_mix.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def oracle_factor_time(w, sten, cint):
+    import oracle as O
+    t0 = time.perf_counter()
+    M, S = O.assemble(w.n, w.d, w.omega, w.m, sten, cint)
+    O.Preconditioner(M, S, w.n, w.d)
+    return time.perf_counter() - t0
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def local_uuid(torch, local):
+    try:
+        u = torch.cuda.get_device_properties(local).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[local]
+        return local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--profile-class", default="fft_col_sym_c64",
+                    help="kernel class timed with CUDA events for the roofline figure")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of that class from an ncu capture (null if not taken)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time the mixed-precision steps only (short runs under a profiler)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -25,6 +25,7 @@
 #include "kernels.h"
 #include "krylov.h"
 #include "ls.h"
+#include "prof.h"
 
 using ls::Error;
 using cd = std::complex<double>;
@@ -686,6 +687,16 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out) {
   } catch (const Error& e) {
     return fail(c, e);
   }
+}
+
+ls_status ls_profile_start(const char* timed_class) {
+  ls::prof_start(timed_class);
+  return LS_OK;
+}
+
+ls_status ls_profile_stop(char* report, int capacity) {
+  ls::prof_stop(report, capacity);
+  return LS_OK;
 }
 
 }  // extern "C"

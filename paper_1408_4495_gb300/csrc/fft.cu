@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace ls {
 
@@ -299,8 +300,9 @@ template <typename C, int L, int SIGN> static void launch_row_L(const RowPassArg
   }
   const long blocks = (a.lines + NL - 1) / NL;
   if (blocks == 0) return;
-  k_row_pass<C, L, SIGN><<<(unsigned)blocks, NT, smem, st>>>(a);
-  LS_CHECK_LAUNCH();
+  const char* cls = sizeof(C) == 8 ? (SIGN < 0 ? "fft_row_fwd_c64" : "fft_row_inv_c64")
+                                   : (SIGN < 0 ? "fft_row_fwd_c128" : "fft_row_inv_c128");
+  LS_LAUNCH(cls, st, k_row_pass<C, L, SIGN><<<(unsigned)blocks, NT, smem, st>>>(a));
 }
 
 template <typename C, int L, int MODE> static void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
@@ -314,8 +316,9 @@ template <typename C, int L, int MODE> static void launch_col_L(const ColPassArg
   const long tiles = (a.inner + TC - 1) / TC;
   const long blocks = tiles * a.outer;
   if (blocks == 0) return;
-  k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a);
-  LS_CHECK_LAUNCH();
+  const char* cls = sizeof(C) == 8 ? (MODE == 0 ? "fft_col_fwd_c64" : MODE == 1 ? "fft_col_inv_c64" : "fft_col_sym_c64")
+                                   : (MODE == 0 ? "fft_col_fwd_c128" : MODE == 1 ? "fft_col_inv_c128" : "fft_col_sym_c128");
+  LS_LAUNCH(cls, st, k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a));
 }
 
 #define LS_FOR_L(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
@@ -513,15 +516,13 @@ __global__ void k_symbol_quadrant(const double2* spec, double2* sym64, float2* s
 }
 
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st) {
-  k_kernel_quadrant<<<1024, 256, 0, st>>>(ktq, d, n, omega, h);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kernel_table", st, k_kernel_quadrant<<<1024, 256, 0, st>>>(ktq, d, n, omega, h));
 }
 
 void build_symbol(const ConvPlan& p, const double2* ktq, double2* sym64, float2* sym32, double2* work,
                   cudaStream_t st) {
   const int d = p.d, n = p.n, L = 2 * n;
-  k_kernel_pad<<<1024, 256, 0, st>>>(ktq, work, d, n);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kernel_pad", st, k_kernel_pad<<<1024, 256, 0, st>>>(ktq, work, d, n));
   const long lines = d == 2 ? (long)L : (long)L * L;
   RowPassArgs r{};
   r.in = work; r.out = work; r.lines = lines; r.n_in = L; r.n_out = L; r.in_ls = L; r.out_ls = L; r.tw = p.tw64;
@@ -537,8 +538,7 @@ void build_symbol(const ConvPlan& p, const double2* ktq, double2* sym64, float2*
     c.outer = 1; c.inner = (long)L * L; c.in_os = 0; c.out_os = 0; c.in_es = (long)L * L; c.out_es = c.in_es;
     col_pass<double2>(L, 0, c, st);
   }
-  k_symbol_quadrant<<<1024, 256, 0, st>>>(work, sym64, sym32, d, n);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("symbol", st, k_symbol_quadrant<<<1024, 256, 0, st>>>(work, sym64, sym32, d, n));
 }
 
 }  // namespace ls

@@ -5,6 +5,7 @@
 // so results do not depend on scheduling.
 #include "common.cuh"
 #include "krylov.h"
+#include "prof.h"
 
 namespace ls {
 
@@ -144,47 +145,39 @@ template <typename Cw>
 void dots(const double2* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride,
           bool accumulate, cudaStream_t st) {
   const int nblk = dots_blocks(N);
-  k_dots<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk);
-  LS_CHECK_LAUNCH();
-  k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, accumulate ? 1 : 0);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_dots", st, k_dots<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk));
+  LS_LAUNCH("kr_reduce", st,
+            k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, accumulate ? 1 : 0));
 }
 
 template <typename Cw>
 void sub_proj(const double2* const* V, int nv, const Cw* win, double2* wout, const double2* h, int hstride, long N,
               int nrhs, cudaStream_t st) {
-  k_sub_proj<Cw><<<grid_for(N * nrhs), 256, 0, st>>>(V, nv, win, wout, h, hstride, N, nrhs);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_sub_proj", st, k_sub_proj<Cw><<<grid_for(N * nrhs), 256, 0, st>>>(V, nv, win, wout, h, hstride, N, nrhs));
 }
 
 template <typename Cw>
 void norms2(const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride, cudaStream_t st) {
   const int nblk = dots_blocks(N);
-  k_norm2<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(w, N, partial, nblk);
-  LS_CHECK_LAUNCH();
-  k_reduce<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, 1, nrhs, nblk, out, ostride, 0);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_norm2", st, k_norm2<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(w, N, partial, nblk));
+  LS_LAUNCH("kr_reduce", st, k_reduce<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, 1, nrhs, nblk, out, ostride, 0));
 }
 
 void scale(const double2* w, double2* out, const double* s, long N, int nrhs, cudaStream_t st) {
-  k_scale<<<grid_for(N * nrhs), 256, 0, st>>>(w, out, s, N, nrhs);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_scale", st, k_scale<<<grid_for(N * nrhs), 256, 0, st>>>(w, out, s, N, nrhs));
 }
 
 template <typename Cz>
 void update_u(const Cz* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs, cudaStream_t st) {
-  k_update_u<Cz><<<grid_for(N * nrhs), 256, 0, st>>>(Z, nz, y, ystride, u, N, nrhs);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_update_u", st, k_update_u<Cz><<<grid_for(N * nrhs), 256, 0, st>>>(Z, nz, y, ystride, u, N, nrhs));
 }
 
 void residual(const double2* g, const double2* Au, double2* r, long tot, cudaStream_t st) {
-  k_residual<<<grid_for(tot), 256, 0, st>>>(g, Au, r, tot);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_residual", st, k_residual<<<grid_for(tot), 256, 0, st>>>(g, Au, r, tot));
 }
 
 template <typename Cin, typename Cout> void cast(const Cin* in, Cout* out, long tot, cudaStream_t st) {
-  k_cast<Cin, Cout><<<grid_for(tot), 256, 0, st>>>(in, out, tot);
-  LS_CHECK_LAUNCH();
+  LS_LAUNCH("kr_cast", st, k_cast<Cin, Cout><<<grid_for(tot), 256, 0, st>>>(in, out, tot));
 }
 
 template void dots<float2>(const double2* const*, int, const float2*, long, int, double2*, double2*, int, bool, cudaStream_t);

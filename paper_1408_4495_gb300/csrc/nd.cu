@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace ls {
 
@@ -605,13 +606,14 @@ void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w
   ensure_buffers(p, sizeof(C));
   LS_CUDA(cudaMemsetAsync(p->F, 0, p->F_elems * sizeof(C), st));
   LS_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
-  k_assemble<C><<<1024, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_asm, p->d_asm_off, p->d_asm_row, p->d_asm_t,
-                                      p->d, p->n, (const double2*)alpha64, (const double2*)cint64, (const double*)w2m64);
-  LS_CHECK_LAUNCH();
-  if (p->n_pad > 0) {
-    k_set_pad<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_pad, p->d_pad_off);
-    LS_CHECK_LAUNCH();
-  }
+  const bool f32 = sizeof(C) == 8;
+  LS_LAUNCH(f32 ? "nd_assemble_c64" : "nd_assemble_c128", st,
+            k_assemble<C><<<1024, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_asm, p->d_asm_off, p->d_asm_row,
+                                                p->d_asm_t, p->d, p->n, (const double2*)alpha64,
+                                                (const double2*)cint64, (const double*)w2m64));
+  if (p->n_pad > 0)
+    LS_LAUNCH(f32 ? "nd_pad_c64" : "nd_pad_c128", st,
+              k_set_pad<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_pad, p->d_pad_off));
   const int depth = (int)p->lev.size();
   for (int l = depth - 1; l >= 0; --l) {
     LevelK<C> L = level_k<C>(p, l);
@@ -620,25 +622,23 @@ void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w
       const long tot = (long)Ch.bmax * Ch.bmax;
       const unsigned bx = (unsigned)std::min<long>((tot + 255) / 256, 64);
       for (int k = 0; k < 2; ++k) {
-        k_extend_add<C><<<dim3(bx, Ch.nf), 256, 0, st>>>(L, Ch, k);
-        LS_CHECK_LAUNCH();
+        LS_LAUNCH(f32 ? "nd_extend_add_c64" : "nd_extend_add_c128", st,
+                  k_extend_add<C><<<dim3(bx, Ch.nf), 256, 0, st>>>(L, Ch, k));
       }
     }
     for (int k0 = 0; k0 < L.smax; k0 += NB) {
       const int k1 = std::min(k0 + NB, L.smax);
-      k_panel<C><<<L.nf, 256, 0, st>>>(L, k0, k1, p->d_err);
-      LS_CHECK_LAUNCH();
+      LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st, k_panel<C><<<L.nf, 256, 0, st>>>(L, k0, k1, p->d_err));
       const int m = L.fmax - k1;
       if (m > 0) {
-        k_trsm_row<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1);
-        LS_CHECK_LAUNCH();
+        LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                  k_trsm_row<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1));
         const int nt = (m + 63) / 64;
-        k_gemm_update<C><<<dim3(nt * nt, L.nf), 256, 0, st>>>(L, k0, k1);
-        LS_CHECK_LAUNCH();
+        LS_LAUNCH(f32 ? "nd_gemm_c64" : "nd_gemm_c128", st,
+                  k_gemm_update<C><<<dim3(nt * nt, L.nf), 256, 0, st>>>(L, k0, k1));
       }
     }
-    k_perm<<<(L.nf + 127) / 128, 128, 0, st>>>(L.piv, L.perm, L.iperm, L.nf, L.smax);
-    LS_CHECK_LAUNCH();
+    LS_LAUNCH("nd_perm", st, k_perm<<<(L.nf + 127) / 128, 128, 0, st>>>(L.piv, L.perm, L.iperm, L.nf, L.smax));
   }
   int err = 0;
   LS_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -779,13 +779,12 @@ template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaS
     for (int l = depth - 1; l >= 0; --l) {
       LevelK<C> L = level_k<C>(p, l);
       LevelK<C> Ch = l + 1 < depth ? level_k<C>(p, l + 1) : L;
-      k_nd_fwd<C><<<L.nf, 256, smem, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N);
-      LS_CHECK_LAUNCH();
+      LS_LAUNCH(sizeof(C) == 8 ? "nd_fwd_c64" : "nd_fwd_c128", st,
+                k_nd_fwd<C><<<L.nf, 256, smem, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N));
     }
     for (int l = 0; l < depth; ++l) {
       LevelK<C> L = level_k<C>(p, l);
-      k_nd_bwd<C><<<L.nf, 256, smem, st>>>(L, xx, nr, p->N);
-      LS_CHECK_LAUNCH();
+      LS_LAUNCH(sizeof(C) == 8 ? "nd_bwd_c64" : "nd_bwd_c128", st, k_nd_bwd<C><<<L.nf, 256, smem, st>>>(L, xx, nr, p->N));
     }
   }
 }

@@ -7,6 +7,7 @@
 // is staged in shared memory.
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace ls {
 
@@ -69,11 +70,11 @@ void stencil_apply(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, lon
   long blocks = (total + 255) / 256;
   if (blocks > 152L * 64) blocks = 152L * 64;
   if (blocks == 0) return;
+  const char* cls = sizeof(Cout) == 8 ? "stencil_c64" : "stencil_c128";
   if (d == 2)
-    k_stencil<Cin, Cout, 2><<<(unsigned)blocks, 256, 0, st>>>(n, nrhs, v, r, rs_i, rs_r, (const Cout*)alpha);
+    LS_LAUNCH(cls, st, k_stencil<Cin, Cout, 2><<<(unsigned)blocks, 256, 0, st>>>(n, nrhs, v, r, rs_i, rs_r, (const Cout*)alpha));
   else
-    k_stencil<Cin, Cout, 3><<<(unsigned)blocks, 256, 0, st>>>(n, nrhs, v, r, rs_i, rs_r, (const Cout*)alpha);
-  LS_CHECK_LAUNCH();
+    LS_LAUNCH(cls, st, k_stencil<Cin, Cout, 3><<<(unsigned)blocks, 256, 0, st>>>(n, nrhs, v, r, rs_i, rs_r, (const Cout*)alpha));
 }
 
 template void stencil_apply<float2, float2>(int, int, int, const float2*, float2*, long, long, const void*, cudaStream_t);

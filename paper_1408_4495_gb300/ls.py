@@ -26,7 +26,8 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_factor", "ls_rhs_plane_wave", "ls_solve", "ls_last_error", "ls_free",
-           "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats"]
+           "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
+           "ls_profile_start", "ls_profile_stop"]
 
 
 class LsGrid(ctypes.Structure):
@@ -77,6 +78,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_stencil_apply.argtypes = [vp, ip, vp, vp, ip]
     lib.ls_precond.argtypes = [vp, ip, vp, vp]
     lib.ls_get_nd_stats.argtypes = [vp, ctypes.POINTER(LsNdStats)]
+    lib.ls_profile_start.argtypes = [ctypes.c_char_p]
+    lib.ls_profile_stop.argtypes = [ctypes.c_char_p, ip]
     for name in EXPORTS:
         if name not in ("ls_last_error", "ls_free"):
             getattr(lib, name).restype = ctypes.c_int
@@ -103,6 +106,19 @@ def _stream_ptr(stream):
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
+
+
+def profile_start(timed_class: str | None = None) -> None:
+    """Reset the library's per-kernel-class launch counters; time one class with CUDA events."""
+    load().ls_profile_start(timed_class.encode() if timed_class else None)
+
+
+def profile_stop() -> dict:
+    """Counters and timed-class device time since profile_start (see include/ls.h)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    load().ls_profile_stop(buf, len(buf))
+    return json.loads(buf.value.decode())
 
 
 @dataclass
