@@ -1,23 +1,33 @@
-// Nested-dissection multifrontal LU of M = [A + C omega^2 m ; B] and its multi-right-hand-
-// side solves (Sec. 2.2 after eq. PC: nested dissection + multifrontal method; Sec. 3.2:
-// O(N^{3/2}) / O(N^2) factorization, O(N log N) / O(N^{4/3}) solve).
+// Nested-dissection multifrontal factorization of M = [A + C omega^2 m ; B] and its
+// multi-right-hand-side solves (Sec. 2.2 after eq. PC: nested dissection + multifrontal
+// method; Sec. 3.2: O(N^{3/2}) / O(N^2) factorization, O(N log N) / O(N^{4/3}) solve).
 //
 // Symbolic (host, once per (d, n)): the grid box is split recursively along its longest
 // side by a one-point-thick separator slab (the 3^d stencil couples only points at
 // infinity-distance <= 1, so the slab disconnects the halves).  A tree node owns its
 // separator (a leaf owns its whole box); its front is [own variables ; ring], the ring
 // being the grid points adjacent to the node's box (all of them belong to ancestors).
-// Nodes at equal depth form one level and are factored by one batch of launches; each
-// level stores its fronts densely as nf x fmax x fmax (column major), fmax = smax + bmax,
-// with smaller fronts padded (identity on padded own positions, zero ring positions).
+// Nodes at equal depth form one level and are processed by one batch of launches; each
+// level stores its fronts densely as nf x fmax x ncols (column major, ld = fmax),
+// fmax = smax + bmax, ncols = fmax + smax, smaller fronts padded (identity on padded own
+// positions, zero ring positions).
 //
-// Numeric (device, per medium), level by level from the leaves:
-//   assemble original entries -> extend-add children's Schur complements -> blocked
-//   right-looking partial LU of the own columns, pivot rows restricted to the own rows:
-//   panel (pivot, swap whole rows, scale, rank-1) / TRSM of the block row / GEMM update of
-//   the trailing block (which ends as the Schur complement F22 - L21 U12 for the parent).
-// Solve: forward y = L^{-1} P b from the leaves (children's update vectors extend-added
-// into the parent's front vector), backward x = U^{-1}(y - U12 x_ring) from the root.
+// Numeric (device, per medium), level by level from the leaves.  Each front is augmented
+// by an identity block on its own rows:
+//       [ F11  F12  I ]        own rows (s)
+//       [ F21  F22  0 ]        ring rows (b)
+// and eliminated in two sweeps:
+//   1. blocked right-looking LU of the own columns (pivot rows restricted to the own rows;
+//      panel / row-swap + unit-lower TRSM of the block row / GEMM of the trailing block),
+//      which leaves the Schur complement S = F22 - F21 F11^{-1} F12 in the ring block and
+//      Y = -F21 F11^{-1} in the ring rows of the identity columns;
+//   2. blocked backward substitution with U11 on the own rows of [F12 I] (Gauss-Jordan),
+//      which leaves H = F11^{-1} F12 and F11^{-1} there.
+// S is extend-added into the parent.  The solve then needs no triangular recurrences:
+//   forward (leaves to root):  update for the parent  u_ring = w_ring + Y w_own
+//   backward (root to leaves): x_own = F11^{-1} w_own - H x_ring
+// two batched multi-right-hand-side matrix-vector products per level, every factor entry
+// read once per sweep.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -38,22 +48,22 @@ struct Node {
 };
 
 struct LevelDev {
-  int nf = 0, smax = 0, bmax = 0, fmax = 0;
+  int nf = 0, smax = 0, bmax = 0, fmax = 0, ncols = 0;
   size_t F_off = 0, W_off = 0;
   int *own = nullptr, *ring = nullptr, *child = nullptr, *parent = nullptr, *kidx = nullptr, *ea = nullptr;
-  int *piv = nullptr, *perm = nullptr, *iperm = nullptr;
+  int* piv = nullptr;
 };
 
 template <typename C> struct LevelK {
   C* F;
   C* W;
-  int nf, smax, bmax, fmax;
+  int nf, smax, bmax, fmax, ncols;
   const int *own, *ring, *child, *parent, *kidx, *ea;
-  int *piv, *perm, *iperm;
+  int* piv;
 };
 
-constexpr int NB = 32;          // panel width
-constexpr int SOLVE_CHUNK = 64; // right-hand sides per solve launch
+constexpr int NB = 32;           // panel / block width
+constexpr int SOLVE_CHUNK = 64;  // right-hand sides per solve launch
 
 }  // namespace
 
@@ -63,11 +73,11 @@ struct NdPlan {
   std::vector<Node> nodes;
   std::vector<std::vector<int>> lev_nodes;
   std::vector<LevelDev> lev;
-  long n_asm = 0, n_pad = 0;
+  long n_asm = 0, n_one = 0;
   int64_t* d_asm_off = nullptr;
   int* d_asm_row = nullptr;
   unsigned char* d_asm_t = nullptr;
-  int64_t* d_pad_off = nullptr;
+  int64_t* d_one_off = nullptr;
   size_t F_elems = 0, W_elems = 0;
   void* F = nullptr;
   int F_bytes = 0;
@@ -189,14 +199,17 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
         L.bmax = std::max(L.bmax, (int)p->nodes[id].ring.size());
       }
       L.fmax = L.smax + L.bmax;
+      L.ncols = L.fmax + L.smax;
       L.F_off = F_off;
       L.W_off = W_off;
-      F_off += (size_t)L.nf * L.fmax * L.fmax;
+      F_off += (size_t)L.nf * L.fmax * L.ncols;
       W_off += (size_t)L.nf * SOLVE_CHUNK * L.fmax;
       max_front = std::max(max_front, L.fmax);
-      const double f = L.fmax, s = L.smax;
-      flops += L.nf * 8.0 * (f * f * f - (f - s) * (f - s) * (f - s)) / 3.0;
-      solve_entries += (double)L.nf * (s * s + 2.0 * s * L.bmax);
+      // complex multiply-adds of the two sweeps on the padded shapes, 8 real flops each
+      double cm = 0;
+      for (int j = 0; j < L.smax; ++j) cm += (double)(L.fmax - j - 1) * (L.ncols - j - 1) + (double)j * (L.ncols - L.smax);
+      flops += 8.0 * cm * L.nf;
+      solve_entries += (double)L.nf * ((double)L.smax * L.smax + 2.0 * L.smax * L.bmax);
     }
     p->F_elems = F_off;
     p->W_elems = W_off;
@@ -205,11 +218,11 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
     p->info.max_front = max_front;
     p->info.factor_entries = (int64_t)F_off;
     p->info.factor_flops = flops;
-    p->info.solve_bytes = solve_entries;  // scaled by element size by the caller
+    p->info.solve_bytes = solve_entries;  // entries; scaled by the element size by the caller
 
     // per-level index arrays, assembly list, extend-add maps
     std::vector<int> pos(p->N, -1);
-    std::vector<int64_t> asm_off, pad_off;
+    std::vector<int64_t> asm_off, one_off;
     std::vector<int> asm_row;
     std::vector<unsigned char> asm_t;
     const int n_ = n;
@@ -229,6 +242,9 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       l_ea[l].assign((size_t)L.nf * L.bmax, -1);
     }
     const int t_lo2 = d == 3 ? -1 : 0, t_hi2 = d == 3 ? 1 : 0;
+    auto tcode = [&](int t0, int t1, int t2) -> unsigned char {
+      return (unsigned char)(d == 2 ? (t0 + 1) * 3 + (t1 + 1) : ((t0 + 1) * 3 + (t1 + 1)) * 3 + (t2 + 1));
+    };
     for (int id = 0; id < (int)p->nodes.size(); ++id) {
       const Node& nd = p->nodes[id];
       const int l = nd.depth;
@@ -245,7 +261,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       }
       for (int q = 0; q < s; ++q) pos[nd.own[q]] = q;
       for (int q = 0; q < b; ++q) pos[nd.ring[q]] = L.smax + q;
-      const size_t base = L.F_off + (size_t)z * L.fmax * L.fmax;
+      const size_t base = L.F_off + (size_t)z * L.fmax * L.ncols;
       // rows of own variables: every stencil neighbour present in the front
       for (int q = 0; q < s; ++q) {
         int c[3];
@@ -259,10 +275,10 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
                 if (cc[a] < 0 || cc[a] >= n_) in = false;
               if (!in) continue;
               const int j = flat(cc);
-              if (pos[j] < 0) continue;
+              if (pos[j] < 0) continue;  // eliminated in a descendant
               asm_off.push_back((int64_t)(base + (size_t)pos[j] * L.fmax + q));
               asm_row.push_back(nd.own[q]);
-              asm_t.push_back((unsigned char)(d == 2 ? (t0 + 1) * 3 + (t1 + 1) : ((t0 + 1) * 3 + (t1 + 1)) * 3 + (t2 + 1)));
+              asm_t.push_back(tcode(t0, t1, t2));
             }
       }
       // rows of ring variables: columns of own variables only
@@ -281,10 +297,12 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
               if (pos[j] < 0 || pos[j] >= L.smax) continue;
               asm_off.push_back((int64_t)(base + (size_t)pos[j] * L.fmax + L.smax + q));
               asm_row.push_back(nd.ring[q]);
-              asm_t.push_back((unsigned char)(d == 2 ? (t0 + 1) * 3 + (t1 + 1) : ((t0 + 1) * 3 + (t1 + 1)) * 3 + (t2 + 1)));
+              asm_t.push_back(tcode(t0, t1, t2));
             }
       }
-      for (int q = s; q < L.smax; ++q) pad_off.push_back((int64_t)(base + (size_t)q * L.fmax + q));
+      // ones: identity on padded own positions and in the augmented block
+      for (int q = s; q < L.smax; ++q) one_off.push_back((int64_t)(base + (size_t)q * L.fmax + q));
+      for (int q = 0; q < L.smax; ++q) one_off.push_back((int64_t)(base + (size_t)(L.fmax + q) * L.fmax + q));
       // extend-add maps of the children: child ring variable -> position in this front
       for (int k = 0; k < 2; ++k) {
         const int cid = nd.child[k];
@@ -310,15 +328,13 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       L.ea = upload(p, l_ea[l], st);
       std::vector<int> zeros((size_t)L.nf * L.smax, 0);
       L.piv = upload(p, zeros, st);
-      L.perm = upload(p, zeros, st);
-      L.iperm = upload(p, zeros, st);
     }
     p->n_asm = (long)asm_off.size();
-    p->n_pad = (long)pad_off.size();
+    p->n_one = (long)one_off.size();
     p->d_asm_off = upload(p, asm_off, st);
     p->d_asm_row = upload(p, asm_row, st);
     p->d_asm_t = upload(p, asm_t, st);
-    p->d_pad_off = upload(p, pad_off, st);
+    p->d_one_off = upload(p, one_off, st);
     std::vector<int> zero1(1, 0);
     p->d_err = upload(p, zero1, st);
     LS_CUDA(cudaStreamSynchronize(st));
@@ -339,12 +355,10 @@ void nd_free(NdPlan* p) {
 
 NdInfo nd_info(const NdPlan* p) { return p->info; }
 
-size_t nd_device_bytes(const NdPlan* p, int elem_bytes) {
-  return (p->F_elems + p->W_elems) * (size_t)elem_bytes;
-}
+size_t nd_device_bytes(const NdPlan* p, int elem_bytes) { return (p->F_elems + p->W_elems) * (size_t)elem_bytes; }
 
 // ---------------------------------------------------------------------------------------
-// numeric factorization kernels
+// factorization kernels
 // ---------------------------------------------------------------------------------------
 
 template <typename C>
@@ -370,6 +384,7 @@ __global__ void k_assemble(C* F, long n_asm, const int64_t* __restrict__ off, co
       if (ca != 1) interior = false;
       cls = cls * 3 + ca;
     }
+    // M(i, i+t) = alpha_cls(i)(t) + [i interior] c(t) omega^2 m_{i+t}   (eq. PC)
     double2 v = alpha[cls * P3 + t];
     if (interior) {
       long j = 0;
@@ -382,8 +397,8 @@ __global__ void k_assemble(C* F, long n_asm, const int64_t* __restrict__ off, co
   }
 }
 
-template <typename C> __global__ void k_set_pad(C* F, long n_pad, const int64_t* __restrict__ off) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n_pad; e += (long)gridDim.x * blockDim.x) {
+template <typename C> __global__ void k_set_one(C* F, long n_one, const int64_t* __restrict__ off) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n_one; e += (long)gridDim.x * blockDim.x) {
     C one;
     one.x = 1;
     one.y = 0;
@@ -396,8 +411,8 @@ template <typename C> __global__ void k_extend_add(LevelK<C> P, LevelK<C> Ch, in
   const int c = blockIdx.y;
   if (Ch.kidx[c] != k) return;
   const int pz = Ch.parent[c];
-  C* Fp = P.F + (size_t)pz * P.fmax * P.fmax;
-  const C* Fc = Ch.F + (size_t)c * Ch.fmax * Ch.fmax;
+  C* Fp = P.F + (size_t)pz * P.fmax * P.ncols;
+  const C* Fc = Ch.F + (size_t)c * Ch.fmax * Ch.ncols;
   const int* ea = Ch.ea + (size_t)c * Ch.bmax;
   const long tot = (long)Ch.bmax * Ch.bmax;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x) {
@@ -410,86 +425,135 @@ template <typename C> __global__ void k_extend_add(LevelK<C> P, LevelK<C> Ch, in
   }
 }
 
-// Panel [k0, k1): pivot search over the own rows, whole-row swaps, scaling, rank-1 updates.
-template <typename C> __global__ void __launch_bounds__(256) k_panel(LevelK<C> L, int k0, int k1, int* err) {
+// (max |.|^2, smallest index) over a CTA; every thread gets the result
+template <typename Rl>
+__device__ __forceinline__ void argmax_block(Rl& v, int& i, Rl* sv, int* si) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const Rl ov = __shfl_down_sync(0xffffffffu, v, o);
+    const int oi = __shfl_down_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) { sv[wid] = v; si[wid] = i; }
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < nw ? sv[lane] : (Rl)-1;
+    i = lane < nw ? si[lane] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      const Rl ov = __shfl_down_sync(0xffffffffu, v, o);
+      const int oi = __shfl_down_sync(0xffffffffu, i, o);
+      if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+    if (lane == 0) { sv[0] = v; si[0] = i; }
+  }
+  __syncthreads();
+  v = sv[0];
+  i = si[0];
+  __syncthreads();
+}
+
+// Panel [k0, k1) held in shared memory (rows k0..fmax): pivot search over the own rows,
+// row swaps within the panel, scaling, rank-1 updates.  Rows above k0 are final U entries.
+template <typename C, bool SMEM>
+__global__ void __launch_bounds__(512) k_panel(LevelK<C> L, int k0, int k1, int* err) {
   using Rl = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Rl sv[32];
+  __shared__ int si[32];
   const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
   const int fmax = L.fmax, smax = L.smax;
-  C* A = L.F + (size_t)z * fmax * fmax;
-  __shared__ Rl rv[256];
-  __shared__ int ri[256];
-  for (int j = k0; j < k1; ++j) {
+  const int R = fmax - k0, w = k1 - k0, srow = smax - k0;
+  C* A = L.F + (size_t)z * fmax * L.ncols;
+  C* P;
+  int ld;
+  if constexpr (SMEM) {
+    P = reinterpret_cast<C*>(smem_raw);
+    ld = R;
+    for (int idx = tid; idx < R * w; idx += NT) {
+      const int c = idx / R, r = idx - c * R;
+      P[idx] = A[(size_t)(k0 + c) * fmax + k0 + r];
+    }
+    __syncthreads();
+  } else {
+    P = A + (size_t)k0 * fmax + k0;
+    ld = fmax;
+  }
+  for (int j = 0; j < w; ++j) {
     Rl best = -1;
-    int bi = j;
-    for (int r = j + tid; r < smax; r += NT) {
-      const Rl v = cabs2(A[(size_t)j * fmax + r]);
+    int bi = 0x7fffffff;
+    for (int r = j + tid; r < srow; r += NT) {
+      const Rl v = cabs2(P[(size_t)j * ld + r]);
       if (v > best) { best = v; bi = r; }
     }
-    rv[tid] = best;
-    ri[tid] = bi;
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-      if (tid < s) {
-        const Rl o = rv[tid + s];
-        const int oi = ri[tid + s];
-        if (o > rv[tid] || (o == rv[tid] && oi < ri[tid])) { rv[tid] = o; ri[tid] = oi; }
-      }
-      __syncthreads();
-    }
-    const int pr = ri[0];
-    const Rl pv = rv[0];
-    __syncthreads();
+    argmax_block(best, bi, sv, si);
+    if (bi == 0x7fffffff) bi = j;
     if (tid == 0) {
-      L.piv[(size_t)z * smax + j] = pr;
-      if (!(pv > 0)) atomicExch(err, 1);
+      L.piv[(size_t)z * smax + k0 + j] = k0 + bi;
+      if (!(best > 0)) atomicExch(err, 1);
     }
-    if (pr != j)
-      for (int col = tid; col < fmax; col += NT) {
-        C& x = A[(size_t)col * fmax + j];
-        C& y = A[(size_t)col * fmax + pr];
+    if (bi != j)
+      for (int c = tid; c < w; c += NT) {
+        C& x = P[(size_t)c * ld + j];
+        C& y = P[(size_t)c * ld + bi];
         const C t = x;
         x = y;
         y = t;
       }
     __syncthreads();
-    const C dg = A[(size_t)j * fmax + j];
+    const C dg = P[(size_t)j * ld + j];
     const Rl den = cabs2(dg);
     C inv;
     inv.x = den > 0 ? dg.x / den : (Rl)0;
     inv.y = den > 0 ? -dg.y / den : (Rl)0;
-    for (int r = j + 1 + tid; r < fmax; r += NT) {
-      C& x = A[(size_t)j * fmax + r];
+    for (int r = j + 1 + tid; r < R; r += NT) {
+      C& x = P[(size_t)j * ld + r];
       x = cmul(x, inv);
     }
     __syncthreads();
-    const int ncol = k1 - j - 1, nrow = fmax - j - 1;
+    const int ncol = w - j - 1, nrow = R - j - 1;
     for (int idx = tid; idx < ncol * nrow; idx += NT) {
-      const int col = j + 1 + idx / nrow, r = j + 1 + idx % nrow;
-      C& x = A[(size_t)col * fmax + r];
-      x = cfms(x, A[(size_t)j * fmax + r], A[(size_t)col * fmax + j]);
+      const int c = j + 1 + idx / nrow, r = j + 1 + idx % nrow;
+      C& x = P[(size_t)c * ld + r];
+      x = cfms(x, P[(size_t)j * ld + r], P[(size_t)c * ld + j]);
     }
     __syncthreads();
   }
+  if constexpr (SMEM) {
+    for (int idx = tid; idx < R * w; idx += NT) {
+      const int c = idx / R, r = idx - c * R;
+      A[(size_t)(k0 + c) * fmax + k0 + r] = P[idx];
+    }
+  }
 }
 
-// Block row: F[k0:k1, c] = L_kk^{-1} F[k0:k1, c] for c >= k1 (unit lower L_kk).
-template <typename C> __global__ void __launch_bounds__(128) k_trsm_row(LevelK<C> L, int k0, int k1) {
+// Columns c in [k1, ncols): apply the panel's row swaps, then F[k0:k1, c] = L_kk^{-1} F[k0:k1, c].
+template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK<C> L, int k0, int k1) {
   const int z = blockIdx.y;
   const int fmax = L.fmax, w = k1 - k0;
-  C* A = L.F + (size_t)z * fmax * fmax;
+  C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C Ld[NB][NB + 1];
+  __shared__ int pv[NB];
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     const int i = idx % w, l = idx / w;
     Ld[i][l] = A[(size_t)(k0 + l) * fmax + k0 + i];
   }
+  for (int j = threadIdx.x; j < w; j += blockDim.x) pv[j] = L.piv[(size_t)z * L.smax + k0 + j];
   __syncthreads();
   const int c = k1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= fmax) return;
+  if (c >= L.ncols) return;
+  C* col = A + (size_t)c * fmax;
+  for (int j = 0; j < w; ++j) {
+    const int q = pv[j];
+    if (q != k0 + j) {
+      const C t = col[k0 + j];
+      col[k0 + j] = col[q];
+      col[q] = t;
+    }
+  }
   C x[NB];
-  C* col = A + (size_t)c * fmax + k0;
 #pragma unroll
   for (int i = 0; i < NB; ++i)
-    if (i < w) x[i] = col[i];
+    if (i < w) x[i] = col[k0 + i];
 #pragma unroll
   for (int i = 1; i < NB; ++i) {
     if (i < w) {
@@ -502,19 +566,52 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_row(LevelK<C
   }
 #pragma unroll
   for (int i = 0; i < NB; ++i)
-    if (i < w) col[i] = x[i];
+    if (i < w) col[k0 + i] = x[i];
 }
 
-// Trailing update F[k1:, k1:] -= F[k1:, k0:k1] F[k0:k1, k1:], 64 x 64 tiles, K chunks of 16.
-template <typename C> __global__ void __launch_bounds__(256) k_gemm_update(LevelK<C> L, int k0, int k1) {
+// Columns c in [smax, ncols): F[j0:j1, c] = U_blk^{-1} F[j0:j1, c] (non-unit upper).
+template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK<C> L, int j0, int j1) {
+  const int z = blockIdx.y;
+  const int fmax = L.fmax, w = j1 - j0;
+  C* A = L.F + (size_t)z * fmax * L.ncols;
+  __shared__ C Ud[NB][NB + 1];
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, l = idx / w;
+    Ud[i][l] = A[(size_t)(j0 + l) * fmax + j0 + i];
+  }
+  __syncthreads();
+  const int c = L.smax + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.ncols) return;
+  C* col = A + (size_t)c * fmax;
+  C x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < w) x[i] = col[j0 + i];
+#pragma unroll
+  for (int i = NB - 1; i >= 0; --i) {
+    if (i < w) {
+      C acc = x[i];
+#pragma unroll
+      for (int l = 0; l < NB; ++l)
+        if (l > i && l < w) acc = cfms(acc, Ud[i][l], x[l]);
+      x[i] = cdiv(acc, Ud[i][i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < w) col[j0 + i] = x[i];
+}
+
+// F[r0:r1, c0:c1] -= F[r0:r1, k0:k1] F[k0:k1, c0:c1], 64 x 64 tiles, K chunks of 16.
+template <typename C>
+__global__ void __launch_bounds__(256) k_gemm(LevelK<C> L, int r0, int r1, int c0, int c1, int k0, int k1) {
   constexpr int TM = 64, TK = 16;
   const int z = blockIdx.y;
   const int fmax = L.fmax, w = k1 - k0;
-  const int m = fmax - k1;
-  const int nt = (m + TM - 1) / TM;
+  const int nt = (r1 - r0 + TM - 1) / TM;
   const int tr = blockIdx.x % nt, tcb = blockIdx.x / nt;
-  const int r0 = k1 + tr * TM, c0 = k1 + tcb * TM;
-  C* A = L.F + (size_t)z * fmax * fmax;
+  const int rb = r0 + tr * TM, cb = c0 + tcb * TM;
+  C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C As[TK][TM + 1];
   __shared__ C Bs[TK][TM + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -528,12 +625,10 @@ template <typename C> __global__ void __launch_bounds__(256) k_gemm_update(Level
     for (int idx = threadIdx.x; idx < TK * TM; idx += blockDim.x) {
       const int l = idx / TM, rr = idx % TM;
       C va = czero<C>(), vb = czero<C>();
-      if (l < kw) {
-        if (r0 + rr < fmax) va = A[(size_t)(k0 + kk + l) * fmax + r0 + rr];
-      }
+      if (l < kw && rb + rr < r1) va = A[(size_t)(k0 + kk + l) * fmax + rb + rr];
       As[l][rr] = va;
       const int l2 = idx % TK, cc = idx / TK;
-      if (l2 < kw && c0 + cc < fmax) vb = A[(size_t)(c0 + cc) * fmax + k0 + kk + l2];
+      if (l2 < kw && cb + cc < c1) vb = A[(size_t)(cb + cc) * fmax + k0 + kk + l2];
       Bs[l2][cc] = vb;
     }
     __syncthreads();
@@ -552,31 +647,16 @@ template <typename C> __global__ void __launch_bounds__(256) k_gemm_update(Level
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int c = c0 + ty + 16 * j;
-    if (c >= fmax) continue;
+    const int c = cb + ty + 16 * j;
+    if (c >= c1) continue;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int r = r0 + tx + 16 * i;
-      if (r >= fmax) continue;
+      const int r = rb + tx + 16 * i;
+      if (r >= r1) continue;
       C& x = A[(size_t)c * fmax + r];
       x = csub(x, acc[i][j]);
     }
   }
-}
-
-__global__ void k_perm(const int* piv, int* perm, int* iperm, int nf, int smax) {
-  const int z = blockIdx.x * blockDim.x + threadIdx.x;
-  if (z >= nf) return;
-  int* pm = perm + (size_t)z * smax;
-  const int* pv = piv + (size_t)z * smax;
-  for (int q = 0; q < smax; ++q) pm[q] = q;
-  for (int j = 0; j < smax; ++j) {
-    const int q = pv[j];
-    const int t = pm[j];
-    pm[j] = pm[q];
-    pm[q] = t;
-  }
-  for (int q = 0; q < smax; ++q) iperm[(size_t)z * smax + pm[q]] = q;
 }
 
 template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
@@ -584,9 +664,9 @@ template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
   LevelK<C> k;
   k.F = reinterpret_cast<C*>(p->F) + D.F_off;
   k.W = reinterpret_cast<C*>(p->W) + D.W_off;
-  k.nf = D.nf; k.smax = D.smax; k.bmax = D.bmax; k.fmax = D.fmax;
+  k.nf = D.nf; k.smax = D.smax; k.bmax = D.bmax; k.fmax = D.fmax; k.ncols = D.ncols;
   k.own = D.own; k.ring = D.ring; k.child = D.child; k.parent = D.parent; k.kidx = D.kidx; k.ea = D.ea;
-  k.piv = D.piv; k.perm = D.perm; k.iperm = D.iperm;
+  k.piv = D.piv;
   return k;
 }
 
@@ -594,51 +674,78 @@ static void ensure_buffers(NdPlan* p, int elem_bytes) {
   if (p->F && p->F_bytes == elem_bytes) return;
   if (p->F) { cudaFree(p->F); p->F = nullptr; }
   if (p->W) { cudaFree(p->W); p->W = nullptr; }
-  if (cudaMalloc(&p->F, p->F_elems * elem_bytes) != cudaSuccess)
+  if (cudaMalloc(&p->F, p->F_elems * elem_bytes) != cudaSuccess) {
+    cudaGetLastError();
     LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the fronts failed", p->F_elems * elem_bytes);
-  if (cudaMalloc(&p->W, std::max<size_t>(1, p->W_elems) * elem_bytes) != cudaSuccess)
+  }
+  if (cudaMalloc(&p->W, std::max<size_t>(1, p->W_elems) * elem_bytes) != cudaSuccess) {
+    cudaGetLastError();
     LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the front vectors failed", p->W_elems * elem_bytes);
+  }
   p->F_bytes = p->W_bytes = elem_bytes;
+}
+
+template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
+                                              cudaStream_t st) {
+  if (r1 <= r0 || c1 <= c0 || k1 <= k0) return;
+  const int nr = (r1 - r0 + 63) / 64, nc = (c1 - c0 + 63) / 64;
+  LS_LAUNCH(sizeof(C) == 8 ? "nd_gemm_c64" : "nd_gemm_c128", st,
+            k_gemm<C><<<dim3(nr * nc, L.nf), 256, 0, st>>>(L, r0, r1, c0, c1, k0, k1));
 }
 
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
   ensure_buffers(p, sizeof(C));
+  const bool f32 = sizeof(C) == 8;
   LS_CUDA(cudaMemsetAsync(p->F, 0, p->F_elems * sizeof(C), st));
   LS_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
-  const bool f32 = sizeof(C) == 8;
   LS_LAUNCH(f32 ? "nd_assemble_c64" : "nd_assemble_c128", st,
             k_assemble<C><<<1024, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_asm, p->d_asm_off, p->d_asm_row,
                                                 p->d_asm_t, p->d, p->n, (const double2*)alpha64,
                                                 (const double2*)cint64, (const double*)w2m64));
-  if (p->n_pad > 0)
-    LS_LAUNCH(f32 ? "nd_pad_c64" : "nd_pad_c128", st,
-              k_set_pad<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_pad, p->d_pad_off));
+  LS_LAUNCH(f32 ? "nd_ones_c64" : "nd_ones_c128", st,
+            k_set_one<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_one, p->d_one_off));
   const int depth = (int)p->lev.size();
+  constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    LS_CUDA(cudaFuncSetAttribute(k_panel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
+    attr = true;
+  }
   for (int l = depth - 1; l >= 0; --l) {
     LevelK<C> L = level_k<C>(p, l);
     if (l + 1 < depth) {
       LevelK<C> Ch = level_k<C>(p, l + 1);
       const long tot = (long)Ch.bmax * Ch.bmax;
-      const unsigned bx = (unsigned)std::min<long>((tot + 255) / 256, 64);
-      for (int k = 0; k < 2; ++k) {
+      const unsigned bx = (unsigned)std::max<long>(1, std::min<long>((tot + 255) / 256, 64));
+      for (int k = 0; k < 2; ++k)
         LS_LAUNCH(f32 ? "nd_extend_add_c64" : "nd_extend_add_c128", st,
                   k_extend_add<C><<<dim3(bx, Ch.nf), 256, 0, st>>>(L, Ch, k));
-      }
     }
+    // sweep 1: LU of the own columns, updates of [ring | identity] columns and ring rows
     for (int k0 = 0; k0 < L.smax; k0 += NB) {
       const int k1 = std::min(k0 + NB, L.smax);
-      LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st, k_panel<C><<<L.nf, 256, 0, st>>>(L, k0, k1, p->d_err));
-      const int m = L.fmax - k1;
-      if (m > 0) {
-        LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                  k_trsm_row<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1));
-        const int nt = (m + 63) / 64;
-        LS_LAUNCH(f32 ? "nd_gemm_c64" : "nd_gemm_c128", st,
-                  k_gemm_update<C><<<dim3(nt * nt, L.nf), 256, 0, st>>>(L, k0, k1));
-      }
+      const size_t psm = (size_t)(L.fmax - k0) * (k1 - k0) * sizeof(C);
+      if (psm <= PANEL_SMEM_MAX)
+        LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                  k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
+      else
+        LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                  k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
+      const int m = L.ncols - k1;
+      LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                k_trsm_lower<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1));
+      launch_gemm<C>(L, k1, L.fmax, k1, L.ncols, k0, k1, st);
     }
-    LS_LAUNCH("nd_perm", st, k_perm<<<(L.nf + 127) / 128, 128, 0, st>>>(L.piv, L.perm, L.iperm, L.nf, L.smax));
+    // sweep 2: backward substitution with U11 on the own rows of [F12 | I]
+    const int nblk = (L.smax + NB - 1) / NB;
+    for (int jb = nblk - 1; jb >= 0; --jb) {
+      const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
+      const int m = L.ncols - L.smax;
+      LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                k_trsm_upper<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, j0, j1));
+      launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st);
+    }
   }
   int err = 0;
   LS_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -650,21 +757,19 @@ void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w
 // solves
 // ---------------------------------------------------------------------------------------
 
+// W[z] = [w_own ; w_ring]: own entries from r plus the children's updates, ring entries
+// from the children's updates.
 template <typename C>
-__global__ void __launch_bounds__(256) k_nd_fwd(LevelK<C> L, LevelK<C> Ch, int has_child, const C* __restrict__ r,
-                                                int nrhs, long N) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* yb = reinterpret_cast<C*>(smem_raw);  // [nrhs][NB]
+__global__ void __launch_bounds__(256) k_fwd_gather(LevelK<C> L, LevelK<C> Ch, int has_child, const C* __restrict__ r,
+                                                    int nrhs, long N) {
   const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
   const int fmax = L.fmax, smax = L.smax;
   C* W = L.W + (size_t)z * nrhs * fmax;
-  const C* A = L.F + (size_t)z * fmax * fmax;
   for (int idx = tid; idx < nrhs * fmax; idx += NT) {
     const int rhs = idx / fmax, q = idx % fmax;
     C v = czero<C>();
     if (q < smax) {
-      const int o = L.perm[(size_t)z * smax + q];
-      const int g = L.own[(size_t)z * smax + o];
+      const int g = L.own[(size_t)z * smax + q];
       if (g >= 0) v = r[(size_t)rhs * N + g];
     }
     W[idx] = v;
@@ -680,112 +785,149 @@ __global__ void __launch_bounds__(256) k_nd_fwd(LevelK<C> L, LevelK<C> Ch, int h
         const int rhs = idx / Ch.bmax, a = idx % Ch.bmax;
         const int ps = ea[a];
         if (ps < 0) continue;
-        const int dst = ps < smax ? L.iperm[(size_t)z * smax + ps] : ps;
-        C& x = W[(size_t)rhs * fmax + dst];
+        C& x = W[(size_t)rhs * fmax + ps];
         x = cadd(x, Wc[(size_t)rhs * Ch.fmax + Ch.smax + a]);
       }
       __syncthreads();
     }
   }
-  for (int j0 = 0; j0 < smax; j0 += NB) {
-    const int w = min(NB, smax - j0);
-    for (int rhs = tid; rhs < nrhs; rhs += NT) {
-      C* Wr = W + (size_t)rhs * fmax;
-      C* y = yb + rhs * NB;
-      for (int i = 0; i < w; ++i) {
-        C acc = Wr[j0 + i];
-        for (int l = 0; l < i; ++l) acc = cfms(acc, A[(size_t)(j0 + l) * fmax + j0 + i], y[l]);
-        y[i] = acc;
-        Wr[j0 + i] = acc;
+}
+
+// Batched multi-right-hand-side products of the solve, one launch per level:
+//   MODE 0 (forward):  u_ring = w_ring + Y w_own, Y = -F21 F11^{-1} (ring rows of the
+//                      identity columns), written back into the ring part of W;
+//   MODE 1 (backward): x_own = F11^{-1} w_own - H x_ring (own rows of [H | F11^{-1}]),
+//                      scattered to the solution at the own grid points.
+// A CTA takes 32 rows (one warp-wide coalesced segment per column) and splits the columns
+// among its kg warps; the kg partial sums are added in a fixed order in shared memory.
+// The vector operand (RC right-hand sides) is staged in shared memory, KCH columns at a time.
+constexpr int KCH = 256;
+
+template <typename C, int RC, int MODE>
+__global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L, C* __restrict__ X, int nrhs, long N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* zs = reinterpret_cast<C*>(smem_raw);  // [KCH][RC], later [kg][32][RC]
+  const int z = blockIdx.y, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5;
+  const int fmax = L.fmax, smax = L.smax, bmax = L.bmax;
+  const int row = (MODE == 0 ? smax : 0) + blockIdx.x * 32 + lane;
+  const int rend = MODE == 0 ? fmax : smax;
+  const int K = MODE == 0 ? smax : bmax + smax;
+  const C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax;
+  C* W = L.W + (size_t)z * nrhs * fmax;
+  const int* ring = L.ring + (size_t)z * bmax;
+  C acc[RC];
+#pragma unroll
+  for (int j = 0; j < RC; ++j) acc[j] = czero<C>();
+  for (int cb = 0; cb < K; cb += KCH) {
+    const int kc = min(KCH, K - cb);
+    for (int idx = threadIdx.x; idx < kc * RC; idx += blockDim.x) {
+      const int k = idx / RC, j = idx % RC;
+      C v = czero<C>();
+      if (j < nr) {
+        const int c = cb + k;
+        if (MODE == 0) {
+          v = W[(size_t)(rc0 + j) * fmax + c];
+        } else if (c < bmax) {
+          const int gi = ring[c];
+          if (gi >= 0) {
+            v = X[(size_t)(rc0 + j) * N + gi];
+            v.x = -v.x;
+            v.y = -v.y;
+          }
+        } else {
+          v = W[(size_t)(rc0 + j) * fmax + (c - bmax)];
+        }
+      }
+      zs[idx] = v;
+    }
+    __syncthreads();
+    if (row < rend) {
+      const int per = (kc + kg - 1) / kg;
+      const int k0 = g * per, k1 = min(kc, k0 + per);
+      const C* a = A + (size_t)cb * fmax + row;
+      int k = k0;
+      for (; k + 4 <= k1; k += 4) {
+        const C a0 = a[(size_t)k * fmax], a1 = a[(size_t)(k + 1) * fmax];
+        const C a2 = a[(size_t)(k + 2) * fmax], a3 = a[(size_t)(k + 3) * fmax];
+        const C* z0 = zs + (size_t)k * RC;
+#pragma unroll
+        for (int j = 0; j < RC; ++j) {
+          acc[j] = cfma(acc[j], a0, z0[j]);
+          acc[j] = cfma(acc[j], a1, z0[RC + j]);
+          acc[j] = cfma(acc[j], a2, z0[2 * RC + j]);
+          acc[j] = cfma(acc[j], a3, z0[3 * RC + j]);
+        }
+      }
+      for (; k < k1; ++k) {
+        const C a0 = a[(size_t)k * fmax];
+        const C* z0 = zs + (size_t)k * RC;
+#pragma unroll
+        for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a0, z0[j]);
       }
     }
     __syncthreads();
-    const int cnt = fmax - j0 - w;
-    for (int idx = tid; idx < cnt * nrhs; idx += NT) {
-      const int rhs = idx / cnt, i = j0 + w + idx % cnt;
-      const C* y = yb + rhs * NB;
-      C acc = czero<C>();
-      for (int l = 0; l < w; ++l) acc = cfma(acc, A[(size_t)(j0 + l) * fmax + i], y[l]);
-      C& x = W[(size_t)rhs * fmax + i];
-      x = csub(x, acc);
+  }
+#pragma unroll
+  for (int j = 0; j < RC; ++j) zs[((size_t)g * 32 + lane) * RC + j] = acc[j];
+  __syncthreads();
+  for (int o = threadIdx.x; o < 32 * RC; o += blockDim.x) {
+    const int ln = o / RC, j = o % RC;
+    const int r = (MODE == 0 ? smax : 0) + blockIdx.x * 32 + ln;
+    if (r >= rend || j >= nr) continue;
+    C s = czero<C>();
+    for (int q = 0; q < kg; ++q) s = cadd(s, zs[((size_t)q * 32 + ln) * RC + j]);
+    if (MODE == 0) {
+      C& x = W[(size_t)(rc0 + j) * fmax + r];
+      x = cadd(x, s);
+    } else {
+      const int gi = L.own[(size_t)z * smax + r];
+      if (gi >= 0) X[(size_t)(rc0 + j) * N + gi] = s;
     }
-    __syncthreads();
   }
 }
 
-template <typename C>
-__global__ void __launch_bounds__(256) k_nd_bwd(LevelK<C> L, C* __restrict__ X, int nrhs, long N) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* xb = reinterpret_cast<C*>(smem_raw);  // [nrhs][NB]
-  const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
-  const int fmax = L.fmax, smax = L.smax, bmax = L.bmax;
-  C* W = L.W + (size_t)z * nrhs * fmax;
-  const C* A = L.F + (size_t)z * fmax * fmax;
-  for (int idx = tid; idx < nrhs * bmax; idx += NT) {
-    const int rhs = idx / bmax, q = idx % bmax;
-    const int g = L.ring[(size_t)z * bmax + q];
-    W[(size_t)rhs * fmax + smax + q] = g >= 0 ? X[(size_t)rhs * N + g] : czero<C>();
+template <typename C, int RC, int MODE>
+static void launch_gemv(const LevelK<C>& L, C* X, int nr, long N, cudaStream_t st) {
+  const int rows = MODE == 0 ? L.bmax : L.smax;
+  const int K = MODE == 0 ? L.smax : L.bmax + L.smax;
+  if (rows <= 0 || K <= 0) return;
+  const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, K / 16));
+  const size_t smem = (size_t)std::max(KCH, kg * 32) * RC * sizeof(C);
+  static bool attr = false;
+  if (!attr) {
+    LS_CUDA(cudaFuncSetAttribute(k_gemv<C, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)KCH * 2 * RC * sizeof(C))));
+    attr = true;
   }
-  __syncthreads();
-  // y_own -= U12 x_ring
-  for (int idx = tid; idx < nrhs * smax; idx += NT) {
-    const int rhs = idx / smax, q = idx % smax;
-    const C* xr = W + (size_t)rhs * fmax + smax;
-    C acc = czero<C>();
-    for (int b = 0; b < bmax; ++b) acc = cfma(acc, A[(size_t)(smax + b) * fmax + q], xr[b]);
-    C& x = W[(size_t)rhs * fmax + q];
-    x = csub(x, acc);
+  const dim3 grid((rows + 31) / 32, L.nf, (nr + RC - 1) / RC);
+  const bool f32 = sizeof(C) == 8;
+  LS_LAUNCH(MODE == 0 ? (f32 ? "nd_fwd_c64" : "nd_fwd_c128") : (f32 ? "nd_bwd_c64" : "nd_bwd_c128"), st,
+            k_gemv<C, RC, MODE><<<grid, 32 * kg, smem, st>>>(L, X, nr, N));
+}
+
+template <typename C, int RC>
+static void solve_chunk(NdPlan* p, int nr, const C* rr, C* xx, cudaStream_t st) {
+  const int depth = (int)p->lev.size();
+  const bool f32 = sizeof(C) == 8;
+  for (int l = depth - 1; l >= 0; --l) {
+    LevelK<C> L = level_k<C>(p, l);
+    LevelK<C> Ch = l + 1 < depth ? level_k<C>(p, l + 1) : L;
+    LS_LAUNCH(f32 ? "nd_fwd_gather_c64" : "nd_fwd_gather_c128", st,
+              k_fwd_gather<C><<<L.nf, 256, 0, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N));
+    launch_gemv<C, RC, 0>(L, xx, nr, p->N, st);
   }
-  __syncthreads();
-  for (int jend = smax; jend > 0; jend -= NB) {
-    const int j0 = max(0, jend - NB), w = jend - j0;
-    for (int rhs = tid; rhs < nrhs; rhs += NT) {
-      C* Wr = W + (size_t)rhs * fmax;
-      C* x = xb + rhs * NB;
-      for (int i = w - 1; i >= 0; --i) {
-        C acc = Wr[j0 + i];
-        for (int l = i + 1; l < w; ++l) acc = cfms(acc, A[(size_t)(j0 + l) * fmax + j0 + i], x[l]);
-        acc = cdiv(acc, A[(size_t)(j0 + i) * fmax + j0 + i]);
-        x[i] = acc;
-        Wr[j0 + i] = acc;
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < j0 * nrhs; idx += NT) {
-      const int rhs = idx / j0, i = idx % j0;
-      const C* x = xb + rhs * NB;
-      C acc = czero<C>();
-      for (int l = 0; l < w; ++l) acc = cfma(acc, A[(size_t)(j0 + l) * fmax + i], x[l]);
-      C& y = W[(size_t)rhs * fmax + i];
-      y = csub(y, acc);
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < nrhs * smax; idx += NT) {
-    const int rhs = idx / smax, q = idx % smax;
-    const int g = L.own[(size_t)z * smax + q];
-    if (g >= 0) X[(size_t)rhs * N + g] = W[(size_t)rhs * fmax + q];
-  }
+  for (int l = 0; l < depth; ++l) launch_gemv<C, RC, 1>(level_k<C>(p, l), xx, nr, p->N, st);
 }
 
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st) {
   if (!p->F || p->F_bytes != (int)sizeof(C)) LS_FAIL(ESTATE_, "preconditioner not factored in this precision");
-  const int depth = (int)p->lev.size();
   for (int c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
     const int nr = std::min(SOLVE_CHUNK, nrhs - c0);
     const C* rr = r + (size_t)c0 * p->N;
     C* xx = x + (size_t)c0 * p->N;
-    const size_t smem = (size_t)nr * NB * sizeof(C);
-    for (int l = depth - 1; l >= 0; --l) {
-      LevelK<C> L = level_k<C>(p, l);
-      LevelK<C> Ch = l + 1 < depth ? level_k<C>(p, l + 1) : L;
-      LS_LAUNCH(sizeof(C) == 8 ? "nd_fwd_c64" : "nd_fwd_c128", st,
-                k_nd_fwd<C><<<L.nf, 256, smem, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N));
-    }
-    for (int l = 0; l < depth; ++l) {
-      LevelK<C> L = level_k<C>(p, l);
-      LS_LAUNCH(sizeof(C) == 8 ? "nd_bwd_c64" : "nd_bwd_c128", st, k_nd_bwd<C><<<L.nf, 256, smem, st>>>(L, xx, nr, p->N));
-    }
+    if (nr <= 4) solve_chunk<C, 4>(p, nr, rr, xx, st);
+    else solve_chunk<C, 16>(p, nr, rr, xx, st);
   }
 }
 
