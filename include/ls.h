@@ -165,11 +165,12 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out);
 /* ---------------------------------------------------------------------------------------
  * Instrumentation (process-wide, for measurement; the paper has no counterpart).
  * ls_profile_start resets the per-kernel-class launch counters of the library and, when
- * timed_class is neither NULL nor empty, brackets every launch of that kernel class with a
- * pair of CUDA events recorded on the stream the kernel is launched on.
+ * timed_class is neither NULL nor empty, brackets every launch of that kernel class ("*":
+ * of every class) with a pair of CUDA events recorded on the stream the kernel is launched on.
  * ls_profile_stop waits for those events and writes a NUL-terminated JSON report
  *   {"counts": {class: launches, ...}, "total": n,
- *    "timed": {"class": name, "launches": k, "ms": summed device time}}
+ *    "timed": {"class": name, "launches": k, "ms": summed device time},
+ *    "ms_by_class": {class: summed device time, ...}}
  * into report (truncated to capacity bytes; report may be NULL).  Not thread-safe with
  * respect to other calls of the library running at the same time.
  * --------------------------------------------------------------------------------------- */

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -33,6 +34,15 @@ using cd = std::complex<double>;
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+};
+
+// A captured launch sequence: replayed while the buffers it was captured on are unchanged
+// (generation counter of the context), re-captured otherwise.
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  std::map<std::string, long> tally;  // kernel launches per class in one replay
+  uint64_t gen = 0;
+  bool seen = false;
 };
 
 struct ls_ctx {
@@ -65,6 +75,9 @@ struct ls_ctx {
   double2** dV = nullptr;
   void** dZ = nullptr;
   ls::ConvPlan plan{};
+  uint64_t gen = 1;  // bumped whenever a device buffer is (re)allocated
+  bool use_graphs = true;
+  std::map<std::string, GraphEntry> graphs;
 };
 
 namespace {
@@ -109,8 +122,59 @@ template <typename T> T* buf(ls_ctx* c, const std::string& name, size_t count) {
     b.bytes = 0;
     b.p = dalloc<unsigned char>(need);
     b.bytes = need;
+    ++c->gen;
   }
   return (T*)b.p;
+}
+
+// Runs `body` (stream-ordered work on c->st only, no allocation and no synchronisation)
+// through a cached CUDA graph: eager the first time a key is met with the current
+// buffers, captured the second time, replayed afterwards.  Bypassed while launches are
+// being timed individually.
+template <typename F> void run_graph(ls_ctx* c, const std::string& key, F&& body) {
+  if (!c->use_graphs || ls::prof_timing_active()) {
+    body();
+    return;
+  }
+  GraphEntry& e = c->graphs[key];
+  if (e.exec && e.gen == c->gen) {
+    LS_CUDA(cudaGraphLaunch(e.exec, c->st));
+    ls::prof_count_replay(e.tally);
+    return;
+  }
+  if (e.exec) {
+    cudaGraphExecDestroy(e.exec);
+    e.exec = nullptr;
+  }
+  if (!e.seen || e.gen != c->gen) {
+    e.seen = true;
+    e.gen = c->gen;
+    body();
+    return;
+  }
+  e.tally.clear();
+  cudaGraph_t g = nullptr;
+  LS_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  ls::prof_capture_begin(&e.tally);
+  try {
+    body();
+  } catch (...) {
+    ls::prof_capture_end();
+    cudaStreamEndCapture(c->st, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    throw;
+  }
+  ls::prof_capture_end();
+  LS_CUDA(cudaStreamEndCapture(c->st, &g));
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    e.exec = nullptr;
+    LS_CUDA(ie);
+  }
+  LS_CUDA(cudaGraphLaunch(e.exec, c->st));
+  ls::prof_count_replay(e.tally);
 }
 
 // copy count complex doubles (or doubles) between a caller array and a device buffer
@@ -142,6 +206,7 @@ void ensure_basis(ls_ctx* c, int nvec, int nrhs, int z_elem) {
     grew = true;
   }
   if (grew || !c->dV) {
+    ++c->gen;
     LS_CUDA(cudaStreamSynchronize(c->st));
     if (c->dV) cudaFree(c->dV);
     if (c->dZ) cudaFree(c->dZ);
@@ -237,15 +302,18 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       if (!live) break;
       ensure_basis(c, k + 2, nrhs, sizeof(CZ));
       CZ* zk = (CZ*)c->Z[k];
-      precond_apply<CZ>(c, nrhs, c->V[k], zk);
+      // z_k = P v_k (stencil + nested-dissection solve), w = A z_k (FFT operator)
+      run_graph(c, "iter:" + std::to_string(k) + ":" + std::to_string(nrhs) + (mixed ? ":m" : ":d"), [&] {
+        precond_apply<CZ>(c, nrhs, c->V[k], zk);
+        if (mixed) op_apply<CZ>(c, nrhs, zk, wz);
+        else op_apply<double2>(c, nrhs, (const double2*)zk, w);
+      });
       const double2* const* dV = c->dV;
-      // w = A z_k, then CGS2 against V[0..k]
+      // CGS2 against V[0..k]
       if (mixed) {
-        op_apply<CZ>(c, nrhs, zk, wz);
         ls::dots<CZ>(dV, k + 1, wz, N, nrhs, partial, hd, R + 2, false, c->st);
         ls::sub_proj<CZ>(dV, k + 1, wz, w, hd, R + 2, N, nrhs, c->st);
       } else {
-        op_apply<double2>(c, nrhs, (const double2*)zk, w);
         ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd, R + 2, false, c->st);
         ls::sub_proj<double2>(dV, k + 1, w, w, hd, R + 2, N, nrhs, c->st);
       }
@@ -311,9 +379,11 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       ls::update_u<CZ>((const CZ* const*)c->dZ, kmax, yd, R, u, N, nrhs, c->st);
     }
     // FP64 residual r = g - A u
-    op_apply<double2>(c, nrhs, u, Au);
-    ls::residual(g, Au, r, tot, c->st);
-    ls::norms2<double2>(r, N, nrhs, partial, hd, 1, c->st);
+    run_graph(c, "resid:" + std::to_string(nrhs), [&] {
+      op_apply<double2>(c, nrhs, u, Au);
+      ls::residual(g, Au, r, tot, c->st);
+      ls::norms2<double2>(r, N, nrhs, partial, hd, 1, c->st);
+    });
     LS_CUDA(cudaMemcpyAsync(hh.data(), hd, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
     LS_CUDA(cudaStreamSynchronize(c->st));
     for (int j = 0; j < nrhs; ++j) {
@@ -369,6 +439,8 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
     c->N = c->d == 2 ? (long)n * n : (long)n * n * n;
     c->omega = omega;
     c->h = 1.0 / (n + 1);
+    // LS_GRAPHS=0 runs every launch eagerly (for debugging and per-launch timing)
+    if (const char* e = std::getenv("LS_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
     if (stream) c->st = (cudaStream_t)stream;
     else {
       LS_CUDA(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
@@ -494,8 +566,13 @@ ls_status ls_factor(ls_ctx* c) {
   try {
     check_ctx(c);
     c->factored = false;
-    if (c->prec == LS_PREC_MIXED) ls::nd_factor<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
-    else ls::nd_factor<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
+    const bool mixed = c->prec == LS_PREC_MIXED;
+    if (mixed ? ls::nd_prepare<float2>(c->nd) : ls::nd_prepare<double2>(c->nd)) ++c->gen;
+    run_graph(c, "factor", [&] {
+      if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
+      else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
+    });
+    ls::nd_factor_check(c->nd, c->st);
     c->factored = true;
     return LS_OK;
   } catch (const Error& e) {
@@ -568,6 +645,8 @@ void ls_free(ls_ctx* c) {
   for (auto p : c->Z) cudaFree(p);
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
+  for (auto& kv : c->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->nd) ls::nd_free(c->nd);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   cudaGetLastError();

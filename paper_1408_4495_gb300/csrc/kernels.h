@@ -81,9 +81,16 @@ struct NdInfo {
   double factor_flops, solve_bytes;
 };
 NdInfo nd_info(const NdPlan* p);
-// factors: assembles M into the fronts and factors them, in C (float2 or double2)
+// factors: assembles M into the fronts and factors them, in C (float2 or double2);
+// alpha, cint: FP64 stencil tables, w2m: FP64 omega^2 m.  nd_factor = nd_prepare (device
+// allocations, returns true if it allocated) + nd_factor_launch (stream-ordered launches
+// only, capturable in a CUDA graph) + nd_factor_check (reads the singular-pivot flag).
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
+template <typename C> bool nd_prepare(NdPlan* p);
+template <typename C>
+void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
+void nd_factor_check(NdPlan* p, cudaStream_t st);
 // x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);
 size_t nd_device_bytes(const NdPlan* p, int elem_bytes);

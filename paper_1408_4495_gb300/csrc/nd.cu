@@ -178,7 +178,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
     p->d = d;
     p->n = n;
     p->N = d == 2 ? (long)n * n : (long)n * n * n;
-    build_tree(p, 64);
+    build_tree(p, d == 2 ? 16 : 27);
     int depth = 0;
     for (auto& nd : p->nodes) depth = std::max(depth, nd.depth + 1);
     p->lev_nodes.assign(depth, {});
@@ -207,7 +207,8 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       max_front = std::max(max_front, L.fmax);
       // complex multiply-adds of the two sweeps on the padded shapes, 8 real flops each
       double cm = 0;
-      for (int j = 0; j < L.smax; ++j) cm += (double)(L.fmax - j - 1) * (L.ncols - j - 1) + (double)j * (L.ncols - L.smax);
+      for (int j = 0; j < L.smax; ++j) cm += (double)(L.smax - j - 1) * (L.ncols - j - 1) + (double)j * (L.ncols - L.smax);
+      cm += (double)L.bmax * L.smax * (L.ncols - L.smax);
       flops += 8.0 * cm * L.nf;
       solve_entries += (double)L.nf * ((double)L.smax * L.smax + 2.0 * L.smax * L.bmax);
     }
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(512) k_panel(LevelK<C> L, int k0, int k1, int*
   __shared__ int si[32];
   const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
   const int fmax = L.fmax, smax = L.smax;
-  const int R = fmax - k0, w = k1 - k0, srow = smax - k0;
+  const int R = smax - k0, w = k1 - k0, srow = smax - k0;
   C* A = L.F + (size_t)z * fmax * L.ncols;
   C* P;
   int ld;
@@ -532,28 +533,47 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK
   const int fmax = L.fmax, w = k1 - k0;
   C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C Ld[NB][NB + 1];
-  __shared__ int pv[NB];
+  // net effect of the panel's row swaps: position pos[i] receives original row src[i];
+  // positions k0..k1-1 first, then the pivot rows below k1 that were swapped up
+  __shared__ int pos[2 * NB], src[2 * NB], npos;
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     const int i = idx % w, l = idx / w;
     Ld[i][l] = A[(size_t)(k0 + l) * fmax + k0 + i];
   }
-  for (int j = threadIdx.x; j < w; j += blockDim.x) pv[j] = L.piv[(size_t)z * L.smax + k0 + j];
+  if (threadIdx.x == 0) {
+    int cnt = w;
+    for (int i = 0; i < w; ++i) { pos[i] = k0 + i; src[i] = k0 + i; }
+    for (int j = 0; j < w; ++j) {
+      const int q = L.piv[(size_t)z * L.smax + k0 + j];
+      if (q == k0 + j) continue;
+      int iq = -1;
+      for (int i = 0; i < cnt; ++i)
+        if (pos[i] == q) { iq = i; break; }
+      if (iq < 0) { iq = cnt++; pos[iq] = q; src[iq] = q; }
+      const int t = src[j];
+      src[j] = src[iq];
+      src[iq] = t;
+    }
+    npos = cnt;
+  }
   __syncthreads();
   const int c = k1 + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.ncols) return;
   C* col = A + (size_t)c * fmax;
-  for (int j = 0; j < w; ++j) {
-    const int q = pv[j];
-    if (q != k0 + j) {
-      const C t = col[k0 + j];
-      col[k0 + j] = col[q];
-      col[q] = t;
-    }
-  }
+  const int np = npos;
   C x[NB];
 #pragma unroll
   for (int i = 0; i < NB; ++i)
-    if (i < w) x[i] = col[k0 + i];
+    if (i < w) x[i] = col[src[i]];
+  {
+    C extra[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (w + i < np) extra[i] = col[src[w + i]];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (w + i < np) col[pos[w + i]] = extra[i];
+  }
 #pragma unroll
   for (int i = 1; i < NB; ++i) {
     if (i < w) {
@@ -659,6 +679,109 @@ __global__ void __launch_bounds__(256) k_gemm(LevelK<C> L, int r0, int r1, int c
   }
 }
 
+// One CTA per front (fronts whose own-row block fits in shared memory): extend-add of the
+// children's Schur complements, then Gauss-Jordan elimination with partial pivoting over
+// the own rows of [F11 | F12 | I] held in shared memory, which leaves [I | H | F11^{-1}]
+// with H = F11^{-1} F12; the ring rows are updated by the tiled GEMM afterwards.
+template <typename C>
+__global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch, int has_child, int* err) {
+  using Rl = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* B = reinterpret_cast<C*>(smem_raw);  // column major, ld = smax
+  __shared__ Rl sv[32];
+  __shared__ int si[32];
+  const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+  const int s = L.smax, fmax = L.fmax, nc = L.ncols;
+  C* A = L.F + (size_t)z * fmax * nc;
+  if (has_child) {
+    // extend-add: the child's map is staged in shared memory (the front's own-row buffer
+    // is not in use yet), then batches of 4 independent loads per thread
+    int* eas = reinterpret_cast<int*>(smem_raw);
+    for (int k = 0; k < 2; ++k) {
+      const int c = L.child[(size_t)z * 2 + k];
+      if (c < 0) continue;
+      const C* __restrict__ Fc = Ch.F + (size_t)c * Ch.fmax * Ch.ncols + (size_t)Ch.smax * Ch.fmax + Ch.smax;
+      const int cb = Ch.bmax;
+      for (int a = tid; a < cb; a += NT) eas[a] = Ch.ea[(size_t)c * cb + a];
+      __syncthreads();
+      const int tot = cb * cb;
+      for (int base = tid; base < tot; base += 4 * NT) {
+        C v[4];
+        int dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = base + u * NT;
+          dst[u] = -1;
+          if (idx < tot) {
+            const int a = idx % cb, b = idx / cb;
+            const int pa = eas[a], pb = eas[b];
+            if (pa >= 0 && pb >= 0) {
+              dst[u] = pb * fmax + pa;
+              v[u] = Fc[(size_t)b * Ch.fmax + a];
+            }
+          }
+        }
+        C o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u] >= 0) o[u] = A[dst[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u] >= 0) A[dst[u]] = cadd(o[u], v[u]);
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < s * nc; idx += NT) {
+    const int c = idx / s, r = idx - c * s;
+    B[idx] = A[(size_t)c * fmax + r];
+  }
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    Rl best = -1;
+    int bi = 0x7fffffff;
+    for (int r = j + tid; r < s; r += NT) {
+      const Rl v = cabs2(B[(size_t)j * s + r]);
+      if (v > best) { best = v; bi = r; }
+    }
+    argmax_block(best, bi, sv, si);
+    if (bi == 0x7fffffff) bi = j;
+    if (tid == 0 && !(best > 0)) atomicExch(err, 1);
+    if (bi != j)
+      for (int c = j + tid; c < nc; c += NT) {
+        C& x = B[(size_t)c * s + j];
+        C& y = B[(size_t)c * s + bi];
+        const C t = x;
+        x = y;
+        y = t;
+      }
+    __syncthreads();
+    const C dg = B[(size_t)j * s + j];
+    const Rl den = cabs2(dg);
+    C inv;
+    inv.x = den > 0 ? dg.x / den : (Rl)0;
+    inv.y = den > 0 ? -dg.y / den : (Rl)0;
+    for (int c = j + 1 + tid; c < nc; c += NT) {
+      C& x = B[(size_t)c * s + j];
+      x = cmul(x, inv);
+    }
+    __syncthreads();
+    const int ncol = nc - j - 1;
+    for (int idx = tid; idx < ncol * s; idx += NT) {
+      const int cq = idx / s, r = idx - cq * s;
+      if (r == j) continue;
+      const int c = j + 1 + cq;
+      C& x = B[(size_t)c * s + r];
+      x = cfms(x, B[(size_t)j * s + r], B[(size_t)c * s + j]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < s * (nc - s); idx += NT) {
+    const int cq = idx / s, r = idx - cq * s;
+    A[(size_t)(s + cq) * fmax + r] = B[(size_t)(s + cq) * s + r];
+  }
+}
+
 template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
   const LevelDev& D = p->lev[l];
   LevelK<C> k;
@@ -670,8 +793,8 @@ template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
   return k;
 }
 
-static void ensure_buffers(NdPlan* p, int elem_bytes) {
-  if (p->F && p->F_bytes == elem_bytes) return;
+static bool ensure_buffers(NdPlan* p, int elem_bytes) {
+  if (p->F && p->F_bytes == elem_bytes) return false;
   if (p->F) { cudaFree(p->F); p->F = nullptr; }
   if (p->W) { cudaFree(p->W); p->W = nullptr; }
   if (cudaMalloc(&p->F, p->F_elems * elem_bytes) != cudaSuccess) {
@@ -683,6 +806,13 @@ static void ensure_buffers(NdPlan* p, int elem_bytes) {
     LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the front vectors failed", p->W_elems * elem_bytes);
   }
   p->F_bytes = p->W_bytes = elem_bytes;
+  return true;
+}
+
+// threads for the Gauss-Jordan CTA: about 16 entries of the own-row block per thread
+static int gj_threads(int s, int nc) {
+  const int t = ((s * nc / 16 + 31) / 32) * 32;
+  return std::max(32, std::min(256, t));
 }
 
 template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
@@ -693,9 +823,25 @@ template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1
             k_gemm<C><<<dim3(nr * nc, L.nf), 256, 0, st>>>(L, r0, r1, c0, c1, k0, k1));
 }
 
+template <typename C> bool nd_prepare(NdPlan* p) { return ensure_buffers(p, sizeof(C)); }
+
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
-  ensure_buffers(p, sizeof(C));
+  nd_prepare<C>(p);
+  nd_factor_launch<C>(p, alpha64, cint64, w2m64, st);
+  nd_factor_check(p, st);
+}
+
+void nd_factor_check(NdPlan* p, cudaStream_t st) {
+  int err = 0;
+  LS_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA(cudaStreamSynchronize(st));
+  if (err) LS_FAIL(EINVAL_, "nested-dissection factorization met an exactly singular front");
+}
+
+template <typename C>
+void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
+  if (!p->F || p->F_bytes != (int)sizeof(C)) LS_FAIL(ESTATE_, "front storage not prepared for this precision");
   const bool f32 = sizeof(C) == 8;
   LS_CUDA(cudaMemsetAsync(p->F, 0, p->F_elems * sizeof(C), st));
   LS_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
@@ -707,50 +853,66 @@ void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w
             k_set_one<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_one, p->d_one_off));
   const int depth = (int)p->lev.size();
   constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+  constexpr size_t GJ_SMEM_MAX = 160 * 1024;
   static bool attr = false;
   if (!attr) {
     LS_CUDA(cudaFuncSetAttribute(k_panel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
+    LS_CUDA(cudaFuncSetAttribute(k_gauss_jordan<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM_MAX));
     attr = true;
   }
   for (int l = depth - 1; l >= 0; --l) {
+    prof_tag(l);
     LevelK<C> L = level_k<C>(p, l);
-    if (l + 1 < depth) {
-      LevelK<C> Ch = level_k<C>(p, l + 1);
+    const bool has_child = l + 1 < depth;
+    LevelK<C> Ch = has_child ? level_k<C>(p, l + 1) : L;
+    // own rows: [F11 | F12 | I] -> [* | H | F11^{-1}]
+    const size_t gjm = (size_t)L.smax * L.ncols * sizeof(C);
+    if (gjm <= GJ_SMEM_MAX) {
+      // one CTA per front: extend-add, Gauss-Jordan in shared memory, ring rows
+      LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
+                k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, has_child ? 1 : 0,
+                                                                                   p->d_err));
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st);
+      continue;
+    }
+    if (has_child) {
       const long tot = (long)Ch.bmax * Ch.bmax;
       const unsigned bx = (unsigned)std::max<long>(1, std::min<long>((tot + 255) / 256, 64));
       for (int k = 0; k < 2; ++k)
         LS_LAUNCH(f32 ? "nd_extend_add_c64" : "nd_extend_add_c128", st,
                   k_extend_add<C><<<dim3(bx, Ch.nf), 256, 0, st>>>(L, Ch, k));
     }
-    // sweep 1: LU of the own columns, updates of [ring | identity] columns and ring rows
-    for (int k0 = 0; k0 < L.smax; k0 += NB) {
-      const int k1 = std::min(k0 + NB, L.smax);
-      const size_t psm = (size_t)(L.fmax - k0) * (k1 - k0) * sizeof(C);
-      if (psm <= PANEL_SMEM_MAX)
-        LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                  k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
-      else
-        LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                  k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
-      const int m = L.ncols - k1;
-      LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                k_trsm_lower<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1));
-      launch_gemm<C>(L, k1, L.fmax, k1, L.ncols, k0, k1, st);
+    {
+      // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
+      // them), the block rows of [F12 | I] carried along
+      for (int k0 = 0; k0 < L.smax; k0 += NB) {
+        const int k1 = std::min(k0 + NB, L.smax);
+        const size_t psm = (size_t)(L.smax - k0) * (k1 - k0) * sizeof(C);
+        if (psm <= PANEL_SMEM_MAX)
+          LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                    k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
+        else
+          LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                    k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
+        const int m = L.ncols - k1;
+        LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                  k_trsm_lower<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1));
+        launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st);
+      }
+      // sweep 2: backward substitution with U11 on the own rows of [F12 | I]
+      const int nblk = (L.smax + NB - 1) / NB;
+      for (int jb = nblk - 1; jb >= 0; --jb) {
+        const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
+        const int m = L.ncols - L.smax;
+        LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                  k_trsm_upper<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, j0, j1));
+        launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st);
+      }
     }
-    // sweep 2: backward substitution with U11 on the own rows of [F12 | I]
-    const int nblk = (L.smax + NB - 1) / NB;
-    for (int jb = nblk - 1; jb >= 0; --jb) {
-      const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
-      const int m = L.ncols - L.smax;
-      LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                k_trsm_upper<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, j0, j1));
-      launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st);
-    }
+    // ring rows: [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
+    launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st);
   }
-  int err = 0;
-  LS_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LS_CUDA(cudaStreamSynchronize(st));
-  if (err) LS_FAIL(EINVAL_, "nested-dissection factorization met an exactly singular front");
+  prof_tag(-1);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -793,6 +955,106 @@ __global__ void __launch_bounds__(256) k_fwd_gather(LevelK<C> L, LevelK<C> Ch, i
   }
 }
 
+// Forward sweep of one level, gather and product fused (fronts with smax <= FUSED_SMAX):
+// a CTA builds w_own (own entries of r plus the children's updates) and the children's
+// contributions to its 32 ring rows in shared memory, keeps w_own in W for the backward
+// sweep, and writes u_ring = w_ring + Y w_own for its rows.  Columns are split among the
+// kg warps and the partial sums added in a fixed order.
+constexpr int FUSED_SMAX = 1024;
+
+template <typename C, int RC>
+__global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256)
+    k_fwd(LevelK<C> L, LevelK<C> Ch, int has_child, const C* __restrict__ r, int nrhs, long N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z = blockIdx.y, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5, NT = blockDim.x;
+  const int fmax = L.fmax, smax = L.smax;
+  const int t0 = smax + blockIdx.x * 32;
+  // right-hand-side vectors of one item are RCP = RC + 1 entries apart (odd stride: the
+  // per-thread stores of different items fall in different banks)
+  constexpr int RCP = RC + 1;
+  C* wt = reinterpret_cast<C*>(smem_raw);  // [32][RCP] ring rows of this tile
+  C* wo = wt + 32 * RCP;                   // [smax][RCP], later [kg][32][RCP]
+  C* W = L.W + (size_t)z * nrhs * fmax;
+  const int* own = L.own + (size_t)z * smax;
+  // own entries of r: one own variable per thread, its RC right-hand sides loaded together
+  for (int q = threadIdx.x; q < smax; q += NT) {
+    const int gi = own[q];
+    C v[RC];
+#pragma unroll
+    for (int j = 0; j < RC; ++j) v[j] = (j < nr && gi >= 0) ? r[(size_t)(rc0 + j) * N + gi] : czero<C>();
+#pragma unroll
+    for (int j = 0; j < RC; ++j) wo[q * RCP + j] = v[j];
+  }
+  for (int idx = threadIdx.x; idx < 32 * RCP; idx += NT) wt[idx] = czero<C>();
+  __syncthreads();
+  if (has_child) {
+    for (int k = 0; k < 2; ++k) {
+      const int c = L.child[(size_t)z * 2 + k];
+      if (c < 0) continue;
+      const C* Wc = Ch.W + (size_t)c * nrhs * Ch.fmax + Ch.smax;
+      const int* ea = Ch.ea + (size_t)c * Ch.bmax;
+      for (int a = threadIdx.x; a < Ch.bmax; a += NT) {
+        const int ps = ea[a];
+        C* dst = ps < 0 ? nullptr : (ps < smax ? &wo[ps * RCP] : ((ps >= t0 && ps < t0 + 32) ? &wt[(ps - t0) * RCP] : nullptr));
+        if (!dst) continue;
+        C v[RC];
+#pragma unroll
+        for (int j = 0; j < RC; ++j) v[j] = j < nr ? Wc[(size_t)(rc0 + j) * Ch.fmax + a] : czero<C>();
+#pragma unroll
+        for (int j = 0; j < RC; ++j) dst[j] = cadd(dst[j], v[j]);
+      }
+      __syncthreads();
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int idx = threadIdx.x; idx < smax * RC; idx += NT) {
+      const int q = idx / RC, j = idx % RC;
+      if (j < nr) W[(size_t)(rc0 + j) * fmax + q] = wo[q * RCP + j];
+    }
+  const int row = t0 + lane;
+  C acc[RC];
+#pragma unroll
+  for (int j = 0; j < RC; ++j) acc[j] = czero<C>();
+  if (row < fmax) {
+    const C* a = L.F + (size_t)z * fmax * L.ncols + (size_t)fmax * fmax + row;  // Y, identity columns
+    const int per = (smax + kg - 1) / kg;
+    const int k0 = g * per, k1 = min(smax, k0 + per);
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+      const C a0 = a[(size_t)k * fmax], a1 = a[(size_t)(k + 1) * fmax];
+      const C a2 = a[(size_t)(k + 2) * fmax], a3 = a[(size_t)(k + 3) * fmax];
+      const C* z0 = wo + (size_t)k * RCP;
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        acc[j] = cfma(acc[j], a0, z0[j]);
+        acc[j] = cfma(acc[j], a1, z0[RCP + j]);
+        acc[j] = cfma(acc[j], a2, z0[2 * RCP + j]);
+        acc[j] = cfma(acc[j], a3, z0[3 * RCP + j]);
+      }
+    }
+    for (; k < k1; ++k) {
+      const C a0 = a[(size_t)k * fmax];
+      const C* z0 = wo + (size_t)k * RCP;
+#pragma unroll
+      for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a0, z0[j]);
+    }
+  }
+  __syncthreads();
+  C* red = wo;
+#pragma unroll
+  for (int j = 0; j < RC; ++j) red[((size_t)g * 32 + lane) * RCP + j] = acc[j];
+  __syncthreads();
+  for (int o = threadIdx.x; o < 32 * RC; o += NT) {
+    const int ln = o / RC, j = o % RC;
+    const int rr = t0 + ln;
+    if (rr >= fmax || j >= nr) continue;
+    C s = wt[ln * RCP + j];
+    for (int q = 0; q < kg; ++q) s = cadd(s, red[((size_t)q * 32 + ln) * RCP + j]);
+    W[(size_t)(rc0 + j) * fmax + rr] = s;
+  }
+}
+
 // Batched multi-right-hand-side products of the solve, one launch per level:
 //   MODE 0 (forward):  u_ring = w_ring + Y w_own, Y = -F21 F11^{-1} (ring rows of the
 //                      identity columns), written back into the ring part of W;
@@ -806,7 +1068,8 @@ constexpr int KCH = 256;
 template <typename C, int RC, int MODE>
 __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L, C* __restrict__ X, int nrhs, long N) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* zs = reinterpret_cast<C*>(smem_raw);  // [KCH][RC], later [kg][32][RC]
+  constexpr int RCP = RC + 1;  // odd item stride, see k_fwd
+  C* zs = reinterpret_cast<C*>(smem_raw);  // [KCH][RCP], later [kg][32][RCP]
   const int z = blockIdx.y, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5;
   const int fmax = L.fmax, smax = L.smax, bmax = L.bmax;
@@ -821,25 +1084,29 @@ __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L
   for (int j = 0; j < RC; ++j) acc[j] = czero<C>();
   for (int cb = 0; cb < K; cb += KCH) {
     const int kc = min(KCH, K - cb);
-    for (int idx = threadIdx.x; idx < kc * RC; idx += blockDim.x) {
-      const int k = idx / RC, j = idx % RC;
-      C v = czero<C>();
-      if (j < nr) {
-        const int c = cb + k;
-        if (MODE == 0) {
-          v = W[(size_t)(rc0 + j) * fmax + c];
-        } else if (c < bmax) {
-          const int gi = ring[c];
-          if (gi >= 0) {
-            v = X[(size_t)(rc0 + j) * N + gi];
-            v.x = -v.x;
-            v.y = -v.y;
-          }
-        } else {
-          v = W[(size_t)(rc0 + j) * fmax + (c - bmax)];
+    // one column per thread, its RC right-hand sides loaded together
+    for (int k = threadIdx.x; k < kc; k += blockDim.x) {
+      const int c = cb + k;
+      C v[RC];
+      if (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < RC; ++j) v[j] = j < nr ? W[(size_t)(rc0 + j) * fmax + c] : czero<C>();
+      } else if (c < bmax) {
+        const int gi = ring[c];
+#pragma unroll
+        for (int j = 0; j < RC; ++j) {
+          C x = czero<C>();
+          if (j < nr && gi >= 0) x = X[(size_t)(rc0 + j) * N + gi];
+          x.x = -x.x;
+          x.y = -x.y;
+          v[j] = x;
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < RC; ++j) v[j] = j < nr ? W[(size_t)(rc0 + j) * fmax + (c - bmax)] : czero<C>();
       }
-      zs[idx] = v;
+#pragma unroll
+      for (int j = 0; j < RC; ++j) zs[k * RCP + j] = v[j];
     }
     __syncthreads();
     if (row < rend) {
@@ -850,18 +1117,18 @@ __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L
       for (; k + 4 <= k1; k += 4) {
         const C a0 = a[(size_t)k * fmax], a1 = a[(size_t)(k + 1) * fmax];
         const C a2 = a[(size_t)(k + 2) * fmax], a3 = a[(size_t)(k + 3) * fmax];
-        const C* z0 = zs + (size_t)k * RC;
+        const C* z0 = zs + (size_t)k * RCP;
 #pragma unroll
         for (int j = 0; j < RC; ++j) {
           acc[j] = cfma(acc[j], a0, z0[j]);
-          acc[j] = cfma(acc[j], a1, z0[RC + j]);
-          acc[j] = cfma(acc[j], a2, z0[2 * RC + j]);
-          acc[j] = cfma(acc[j], a3, z0[3 * RC + j]);
+          acc[j] = cfma(acc[j], a1, z0[RCP + j]);
+          acc[j] = cfma(acc[j], a2, z0[2 * RCP + j]);
+          acc[j] = cfma(acc[j], a3, z0[3 * RCP + j]);
         }
       }
       for (; k < k1; ++k) {
         const C a0 = a[(size_t)k * fmax];
-        const C* z0 = zs + (size_t)k * RC;
+        const C* z0 = zs + (size_t)k * RCP;
 #pragma unroll
         for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a0, z0[j]);
       }
@@ -869,14 +1136,14 @@ __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L
     __syncthreads();
   }
 #pragma unroll
-  for (int j = 0; j < RC; ++j) zs[((size_t)g * 32 + lane) * RC + j] = acc[j];
+  for (int j = 0; j < RC; ++j) zs[((size_t)g * 32 + lane) * RCP + j] = acc[j];
   __syncthreads();
   for (int o = threadIdx.x; o < 32 * RC; o += blockDim.x) {
     const int ln = o / RC, j = o % RC;
     const int r = (MODE == 0 ? smax : 0) + blockIdx.x * 32 + ln;
     if (r >= rend || j >= nr) continue;
     C s = czero<C>();
-    for (int q = 0; q < kg; ++q) s = cadd(s, zs[((size_t)q * 32 + ln) * RC + j]);
+    for (int q = 0; q < kg; ++q) s = cadd(s, zs[((size_t)q * 32 + ln) * RCP + j]);
     if (MODE == 0) {
       C& x = W[(size_t)(rc0 + j) * fmax + r];
       x = cadd(x, s);
@@ -893,11 +1160,11 @@ static void launch_gemv(const LevelK<C>& L, C* X, int nr, long N, cudaStream_t s
   const int K = MODE == 0 ? L.smax : L.bmax + L.smax;
   if (rows <= 0 || K <= 0) return;
   const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, K / 16));
-  const size_t smem = (size_t)std::max(KCH, kg * 32) * RC * sizeof(C);
+  const size_t smem = (size_t)std::max(std::min(KCH, K), kg * 32) * (RC + 1) * sizeof(C);
   static bool attr = false;
   if (!attr) {
     LS_CUDA(cudaFuncSetAttribute(k_gemv<C, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)KCH * 2 * RC * sizeof(C))));
+                                 (int)((size_t)KCH * 2 * (RC + 1) * sizeof(C))));
     attr = true;
   }
   const dim3 grid((rows + 31) / 32, L.nf, (nr + RC - 1) / RC);
@@ -906,18 +1173,49 @@ static void launch_gemv(const LevelK<C>& L, C* X, int nr, long N, cudaStream_t s
             k_gemv<C, RC, MODE><<<grid, 32 * kg, smem, st>>>(L, X, nr, N));
 }
 
+constexpr size_t FUSED_SMEM_MAX = 200 * 1024;
+
+template <typename C, int RC> static size_t fwd_fused_smem(int smax) {
+  const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, smax / 16));
+  return (size_t)(32 + std::max(smax, kg * 32)) * (RC + 1) * sizeof(C);
+}
+
+template <typename C, int RC>
+static void launch_fwd_fused(const LevelK<C>& L, const LevelK<C>& Ch, int has_child, const C* r, int nr, long N,
+                             cudaStream_t st) {
+  const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, L.smax / 16));
+  const size_t smem = fwd_fused_smem<C, RC>(L.smax);
+  static bool attr = false;
+  if (!attr) {
+    LS_CUDA(cudaFuncSetAttribute(k_fwd<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM_MAX));
+    attr = true;
+  }
+  const dim3 grid(std::max(1, (L.bmax + 31) / 32), L.nf, (nr + RC - 1) / RC);
+  LS_LAUNCH(sizeof(C) == 8 ? "nd_fwd_c64" : "nd_fwd_c128", st,
+            k_fwd<C, RC><<<grid, 32 * kg, smem, st>>>(L, Ch, has_child, r, nr, N));
+}
+
 template <typename C, int RC>
 static void solve_chunk(NdPlan* p, int nr, const C* rr, C* xx, cudaStream_t st) {
   const int depth = (int)p->lev.size();
   const bool f32 = sizeof(C) == 8;
   for (int l = depth - 1; l >= 0; --l) {
+    prof_tag(l);
     LevelK<C> L = level_k<C>(p, l);
     LevelK<C> Ch = l + 1 < depth ? level_k<C>(p, l + 1) : L;
-    LS_LAUNCH(f32 ? "nd_fwd_gather_c64" : "nd_fwd_gather_c128", st,
-              k_fwd_gather<C><<<L.nf, 256, 0, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N));
-    launch_gemv<C, RC, 0>(L, xx, nr, p->N, st);
+    if (L.smax <= FUSED_SMAX && fwd_fused_smem<C, RC>(L.smax) <= FUSED_SMEM_MAX) {
+      launch_fwd_fused<C, RC>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N, st);
+    } else {
+      LS_LAUNCH(f32 ? "nd_fwd_gather_c64" : "nd_fwd_gather_c128", st,
+                k_fwd_gather<C><<<L.nf, 256, 0, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N));
+      launch_gemv<C, RC, 0>(L, xx, nr, p->N, st);
+    }
   }
-  for (int l = 0; l < depth; ++l) launch_gemv<C, RC, 1>(level_k<C>(p, l), xx, nr, p->N, st);
+  for (int l = 0; l < depth; ++l) {
+    prof_tag(l);
+    launch_gemv<C, RC, 1>(level_k<C>(p, l), xx, nr, p->N, st);
+  }
+  prof_tag(-1);
 }
 
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st) {
@@ -933,6 +1231,10 @@ template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaS
 
 template void nd_factor<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template void nd_factor<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
+template bool nd_prepare<float2>(NdPlan*);
+template bool nd_prepare<double2>(NdPlan*);
+template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
+template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template void nd_solve<float2>(NdPlan*, int, const float2*, float2*, cudaStream_t);
 template void nd_solve<double2>(NdPlan*, int, const double2*, double2*, cudaStream_t);
 

@@ -1,7 +1,9 @@
 // Launch instrumentation: every kernel launch of the library goes through prof_begin /
-// prof_end with its kernel class.  Counting is always on (one atomic add per launch); for
-// one selected class the launches are also bracketed by CUDA events on their own stream,
-// so that a caller can measure that class's average device duration inside a longer run.
+// prof_end with its kernel class.  While a measurement is active the launches are counted
+// per class; for one selected class (or all, "*" / "**") the launches are also bracketed by
+// CUDA events on their own stream, so that a caller can measure device durations inside a
+// longer run.  Launches recorded into a CUDA graph are counted into the graph's own tally
+// (prof_capture_begin / prof_capture_end), which is added to the counters at every replay.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -22,38 +24,57 @@ std::map<std::string, long> counts;
 std::string timed;
 struct Pair {
   cudaEvent_t a, b;
+  std::string cls;
 };
 std::vector<Pair> pairs;
 std::vector<cudaEvent_t> open_ev;
 std::atomic<bool> active{false};
 std::atomic<bool> timing{false};
+thread_local int tag = -1;
+thread_local std::map<std::string, long>* capture_sink = nullptr;
 
-cudaEvent_t take() {
-  cudaEvent_t e;
-  cudaEventCreate(&e);
-  return e;
-}
+bool timed_match(const char* cls) { return timed == cls || timed == "*" || timed == "**"; }
 }  // namespace
 
+void prof_tag(int t) { tag = t; }
+
+bool prof_timing_active() { return timing.load(std::memory_order_relaxed); }
+
+void prof_capture_begin(std::map<std::string, long>* sink) { capture_sink = sink; }
+void prof_capture_end() { capture_sink = nullptr; }
+
+void prof_count_replay(const std::map<std::string, long>& tally) {
+  if (!active.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& kv : tally) counts[kv.first] += kv.second;
+}
+
 void prof_begin(const char* cls, cudaStream_t st) {
+  if (capture_sink) {
+    (*capture_sink)[cls] += 1;
+    return;
+  }
   if (!active.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(mu);
   counts[cls] += 1;
-  if (timing && timed == cls) {
-    cudaEvent_t e = take();
+  if (timing && timed_match(cls)) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
     cudaEventRecord(e, st);
     open_ev.push_back(e);
   }
 }
 
 void prof_end(const char* cls, cudaStream_t st) {
-  if (!active.load(std::memory_order_relaxed) || !timing) return;
+  if (capture_sink || !active.load(std::memory_order_relaxed) || !timing) return;
   std::lock_guard<std::mutex> lk(mu);
-  if (timed == cls && !open_ev.empty()) {
+  if (timed_match(cls) && !open_ev.empty()) {
     cudaEvent_t b;
     cudaEventCreate(&b);
     cudaEventRecord(b, st);
-    pairs.push_back({open_ev.back(), b});
+    std::string key = cls;
+    if (timed == "**" && tag >= 0) key += "@L" + std::to_string(tag);
+    pairs.push_back({open_ev.back(), b, key});
     open_ev.pop_back();
   }
 }
@@ -77,12 +98,14 @@ int prof_stop(char* out, int cap) {
   timing = false;
   double ms = 0;
   long ok = 0;
+  std::map<std::string, double> per;
   for (auto& p : pairs) {
     cudaEventSynchronize(p.b);
     float t = 0;
     if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
       ms += t;
       ++ok;
+      per[p.cls] += t;
     }
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -100,9 +123,18 @@ int prof_stop(char* out, int cap) {
     first = false;
   }
   char b[256];
-  snprintf(b, sizeof b, "}, \"total\": %ld, \"timed\": {\"class\": \"%s\", \"launches\": %ld, \"ms\": %.9g}}", total,
+  snprintf(b, sizeof b, "}, \"total\": %ld, \"timed\": {\"class\": \"%s\", \"launches\": %ld, \"ms\": %.9g}", total,
            timed.c_str(), ok, ms);
   s += b;
+  s += ", \"ms_by_class\": {";
+  first = true;
+  for (auto& kv : per) {
+    char c[160];
+    snprintf(c, sizeof c, "%s\"%s\": %.6g", first ? "" : ", ", kv.first.c_str(), kv.second);
+    s += c;
+    first = false;
+  }
+  s += "}}";
   if (out && cap > 0) {
     std::strncpy(out, s.c_str(), (size_t)cap - 1);
     out[cap - 1] = 0;
