@@ -177,6 +177,33 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out);
 ls_status ls_profile_start(const char* timed_class);
 ls_status ls_profile_stop(char* report, int capacity);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free operator apply (the paper has no counterpart: this is a deployment aid).
+ *
+ * Computes the same y = (I + K omega^2 m) x as ls_apply(c, nrhs, x, y, LS_PREC_FP64) but
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.  It exists for
+ * callers that cannot allocate device memory when they need the operator, e.g. code running
+ * while another component owns the device memory pool, loops in which cudaMalloc/cudaFree
+ * would synchronise the device, or deployments that forbid allocation after start-up.
+ *
+ *   x, y   nrhs x n^d complex doubles (interleaved), DEVICE pointers of the current device,
+ *          owned by the caller; host pointers are rejected with LS_EINVAL.
+ *
+ * The FFT passes' intermediate buffer is a fixed 64 MiB array compiled into the library
+ * (it occupies 64 MiB on every GPU that loads the library until the process exits).  One
+ * call needs nrhs * n * 2n complex doubles in 2D (32 right-hand sides at n = 256) and
+ * nrhs * (n^2 * 2n + n * (2n)^2) in 3D; larger requests return LS_EINVAL with the sizes in
+ * the message.  No part of that buffer has to start at zero: every pass writes what the
+ * next one reads.  All calls, on every context of the process, share the one buffer per
+ * GPU, so calls whose work overlaps on the same GPU (different threads or streams) race
+ * and give wrong results; serialise them.
+ *
+ * The first call on each device looks up the buffer's device address
+ * (cudaGetSymbolAddress, which may load the library's module on that device); make that
+ * first call outside any CUDA stream capture.  Synchronous like every other entry point.
+ * --------------------------------------------------------------------------------------- */
+ls_status ls_apply_noalloc(ls_ctx* c, int nrhs, const double* x, double* y);
+
 #ifdef __cplusplus
 }
 #endif

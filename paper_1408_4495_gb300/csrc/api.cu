@@ -768,6 +768,17 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out) {
   }
 }
 
+}  // extern "C"
+
+// Context accessors for ls_apply_noalloc (noalloc.cu).
+namespace ls {
+const ConvPlan* ctx_plan(const ls_ctx* c) { return &c->plan; }
+cudaStream_t ctx_stream(const ls_ctx* c) { return c->st; }
+void ctx_set_error(ls_ctx* c, const char* msg) { c->err = msg; }
+}  // namespace ls
+
+extern "C" {
+
 ls_status ls_profile_start(const char* timed_class) {
   ls::prof_start(timed_class);
   return LS_OK;

@@ -27,7 +27,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_factor", "ls_rhs_plane_wave", "ls_solve", "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
-           "ls_profile_start", "ls_profile_stop"]
+           "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
 
 
 class LsGrid(ctypes.Structure):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_stencil_apply.argtypes = [vp, ip, vp, vp, ip]
     lib.ls_precond.argtypes = [vp, ip, vp, vp]
     lib.ls_get_nd_stats.argtypes = [vp, ctypes.POINTER(LsNdStats)]
+    lib.ls_apply_noalloc.argtypes = [vp, ip, vp, vp]
     lib.ls_profile_start.argtypes = [ctypes.c_char_p]
     lib.ls_profile_stop.argtypes = [ctypes.c_char_p, ip]
     for name in EXPORTS:
@@ -226,6 +227,12 @@ class Solver:
 
     def precond(self, x):
         return self._unary(self.lib.ls_precond, x)
+
+    def apply_noalloc(self, x, out):
+        """FP64 operator apply into a caller-provided device tensor, without any device
+        allocation inside the library (see ls_apply_noalloc in include/ls.h)."""
+        self._check(self.lib.ls_apply_noalloc(self.h, int(x.shape[0]), _ptr(x), _ptr(out)))
+        return out
 
     def nd_stats(self) -> dict:
         s = LsNdStats()
