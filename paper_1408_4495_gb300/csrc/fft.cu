@@ -163,6 +163,42 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
   const int n_in = a.n_in;
 
   // load n_in entries of NL lines (coalesced), apply the prologue
+  if (a.plane_dirs == nullptr) {
+    // LB independent loads in flight per thread before the first shared-memory store
+    constexpr int LB = 4;
+    const int tot = NL * n_in;
+    const C* __restrict__ in = reinterpret_cast<const C*>(a.in);
+    const Rl* __restrict__ pw = reinterpret_cast<const Rl*>(a.pw);
+    for (int base = threadIdx.x; base < tot; base += NT * LB) {
+      C v[LB];
+      Rl wv[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = base + u * NT;
+        v[u] = czero<C>();
+        wv[u] = (Rl)1;
+        if (idx < tot) {
+          const int li = idx / n_in, e = idx - li * n_in;
+          const long line = line0 + li;
+          if (line < a.lines) {
+            v[u] = in[line * a.in_ls + e];
+            if (pw != nullptr) wv[u] = pw[(line % a.pw_lines) * n_in + e];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = base + u * NT;
+        if (idx < tot) {
+          const int li = idx / n_in, e = idx - li * n_in;
+          C x = v[u];
+          x.x *= wv[u];
+          x.y *= wv[u];
+          s[li * LS + pidx(e)] = x;
+        }
+      }
+    }
+  } else
   for (int idx = threadIdx.x; idx < NL * n_in; idx += NT) {
     const int li = idx / n_in, e = idx - li * n_in;
     const long line = line0 + li;
@@ -237,11 +273,30 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
   const long c0 = (blockIdx.x - o * tiles) * TC;
   const C* in = reinterpret_cast<const C*>(a.in) + o * a.in_os + c0;
   const int n_in = a.n_in;
-  for (int idx = threadIdx.x; idx < n_in * TC; idx += NT) {
-    const int e = idx / TC, c = idx - e * TC;
-    C v = czero<C>();
-    if (c0 + c < a.inner) v = in[(long)e * a.in_es + c];
-    s[c * LS + pidx(e)] = v;
+  {
+    // LB independent loads in flight per thread before the first shared-memory store
+    constexpr int LB = 4;
+    const int tot = n_in * TC;
+    for (int base = threadIdx.x; base < tot; base += NT * LB) {
+      C v[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = base + u * NT;
+        v[u] = czero<C>();
+        if (idx < tot) {
+          const int e = idx / TC, c = idx - e * TC;
+          if (c0 + c < a.inner) v[u] = in[(long)e * a.in_es + c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = base + u * NT;
+        if (idx < tot) {
+          const int e = idx / TC, c = idx - e * TC;
+          s[c * LS + pidx(e)] = v[u];
+        }
+      }
+    }
   }
   if (n_in < L) {
     const int padn = L - n_in;
@@ -259,21 +314,37 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
     fft_lines<C, L, 1, -1, TC, NT>(s, tw);
     const C* __restrict__ sym = reinterpret_cast<const C*>(a.sym);
     const int n1 = a.n + 1;
-    for (int idx = threadIdx.x; idx < L * TC; idx += NT) {
-      const int e = idx / TC, c = idx - e * TC;
-      const long cc = c0 + c;
-      if (cc < a.inner) {
-        const int q0 = e <= L - e ? e : L - e;
-        long si;
-        if (a.d == 2) {
-          const int k1 = (int)cc;
-          si = (long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1);
-        } else {
-          const int k1 = (int)(cc / L), k2 = (int)(cc - (long)k1 * L);
-          si = ((long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1)) * n1 + (k2 <= L - k2 ? k2 : L - k2);
+    // symbol values of SB entries loaded together, then applied
+    constexpr int SB = 8;
+    for (int base = threadIdx.x; base < L * TC; base += NT * SB) {
+      C sv[SB];
+#pragma unroll
+      for (int u = 0; u < SB; ++u) {
+        const int idx = base + u * NT;
+        const int e = idx / TC, c = idx - e * TC;
+        const long cc = c0 + c;
+        sv[u] = czero<C>();
+        if (idx < L * TC && cc < a.inner) {
+          const int q0 = e <= L - e ? e : L - e;
+          long si;
+          if (a.d == 2) {
+            const int k1 = (int)cc;
+            si = (long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1);
+          } else {
+            const int k1 = (int)(cc / L), k2 = (int)(cc - (long)k1 * L);
+            si = ((long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1)) * n1 + (k2 <= L - k2 ? k2 : L - k2);
+          }
+          sv[u] = __ldg(&sym[si]);
         }
-        C& v = s[c * LS + pidx(e)];
-        v = cmul(v, __ldg(&sym[si]));
+      }
+#pragma unroll
+      for (int u = 0; u < SB; ++u) {
+        const int idx = base + u * NT;
+        const int e = idx / TC, c = idx - e * TC;
+        if (idx < L * TC && c0 + c < a.inner) {
+          C& v = s[c * LS + pidx(e)];
+          v = cmul(v, sv[u]);
+        }
       }
     }
     __syncthreads();

@@ -535,16 +535,18 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK
   __shared__ C Ld[NB][NB + 1];
   // net effect of the panel's row swaps: position pos[i] receives original row src[i];
   // positions k0..k1-1 first, then the pivot rows below k1 that were swapped up
-  __shared__ int pos[2 * NB], src[2 * NB], npos;
+  __shared__ int pos[2 * NB], src[2 * NB], npos, pv[NB];
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     const int i = idx % w, l = idx / w;
     Ld[i][l] = A[(size_t)(k0 + l) * fmax + k0 + i];
   }
+  for (int j = threadIdx.x; j < w; j += blockDim.x) pv[j] = L.piv[(size_t)z * L.smax + k0 + j];
+  __syncthreads();
   if (threadIdx.x == 0) {
     int cnt = w;
     for (int i = 0; i < w; ++i) { pos[i] = k0 + i; src[i] = k0 + i; }
     for (int j = 0; j < w; ++j) {
-      const int q = L.piv[(size_t)z * L.smax + k0 + j];
+      const int q = pv[j];
       if (q == k0 + j) continue;
       int iq = -1;
       for (int i = 0; i < cnt; ++i)

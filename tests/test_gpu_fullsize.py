@@ -1,0 +1,101 @@
+"""Full-size workloads through the C-ABI, in the launch configuration bench.py times.
+
+The oracle cannot solve every right-hand side of the large configurations in seconds, so
+these tests check sampled outputs the oracle computes one by one (operator entries by the
+direct sum of the definition, Sec. 2.1 eq. lsd; whole solutions for a few right-hand sides
+where its sparse LU is fast enough) and properties that hold at any size (the FP64
+residual recomputed by the oracle's own FFT apply, iteration counts in the paper's band).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1408_4495_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def LS():
+    from paper_1408_4495_gb300 import build, ls
+    build.build()
+    return ls
+
+
+def _true_resid(w, u, g):
+    kt = O.kernel_table(w.n, w.d, w.omega)
+    Au = O.apply_operator(kt, w.omega, w.m, u, workers=-1)
+    return np.linalg.norm(g - Au) / np.linalg.norm(g)
+
+
+def _sampled_apply_check(ls_solver, w, npts, seed):
+    """y = (I + K w^2 m) x at sampled grid points, by the direct sum over all j."""
+    rng = np.random.default_rng(seed)
+    shape = (1,) + (w.n,) * w.d
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    y = ls_solver.apply(x, mixed=False)[0]
+    h = O.grid_h(w.n)
+    J = np.stack(np.meshgrid(*([np.arange(w.n)] * w.d), indexing="ij"), -1).reshape(-1, w.d)
+    v = (w.omega**2 * w.m * x[0]).reshape(-1)
+    nz = np.nonzero(v)[0]
+    err = 0.0
+    for _ in range(npts):
+        i = rng.integers(0, w.n, w.d)
+        k = O.kernel_value(w.d, w.omega, h, i[None, :] - J[nz])
+        ref = x[0][tuple(i)] + np.sum(k * v[nz])
+        err = max(err, abs(y[tuple(i)] - ref) / (abs(ref) + 1e-300))
+    return err
+
+
+def test_bench_workload_2d_n256(LS):
+    """The benchmark's workload: 16 directions, mixed precision, graphs on."""
+    w = W.bumps_2d(256, 32.0, 8, 16, 1002)
+    w.m = W.enforce_buffer(w.m, 2)
+    with LS.Solver(w.m, w.omega, mixed=True) as s:
+        for _ in range(3):  # eager, captured, replayed
+            s.factor()
+            g = s.rhs_plane_wave(w.directions)
+            u, info = s.solve(g, tol=1e-6)
+        assert _sampled_apply_check(s, w, 8, 1) < 1e-11
+    assert all(i.converged and i.rel_resid <= 1e-6 for i in info)
+    sel = [0, 5]
+    ref = O.solve(w.n, 2, w.omega, w.m, w.directions[sel], tol=1e-10)
+    ref6 = O.solve(w.n, 2, w.omega, w.m, w.directions[sel], tol=1e-6)
+    for k, j in enumerate(sel):
+        assert np.linalg.norm(u[j].reshape(-1) - ref["u"][k]) < 1e-5 * np.linalg.norm(ref["u"][k])
+        assert abs(info[j].iters - ref6["iters"][k]) <= 2
+        assert np.linalg.norm(g[j].reshape(-1) - ref["g"][k]) < 1e-11 * np.linalg.norm(ref["g"][k])
+    for j in range(16):
+        assert _true_resid(w, u[j], g[j]) < 1.01e-6
+
+
+def test_large_2d_n1024(LS):
+    """2D n=1024, omega = 2 pi 128, smoothed noise medium, 64 directions in one batch."""
+    w = W.noise_2d(1024, 128.0, 64, 1003)
+    w.m = W.enforce_buffer(w.m, 2)
+    with LS.Solver(w.m, w.omega, mixed=True) as s:
+        assert _sampled_apply_check(s, w, 4, 2) < 1e-11
+        s.factor()
+        g = s.rhs_plane_wave(w.directions)
+        u, info = s.solve(g, tol=1e-6)
+    assert all(i.converged and i.rel_resid <= 1e-6 for i in info)
+    its = [i.iters for i in info]
+    assert max(its) <= 20, its
+    for j in (0, 37):
+        assert _true_resid(w, u[j], g[j]) < 1.01e-6
+
+
+def test_3d_n64(LS):
+    """3D n=64, omega = 2 pi 8, six bumps, 8 directions on the sphere."""
+    w = W.bumps_3d(64, 8.0, 6, 8, 1004)
+    w.m = W.enforce_buffer(w.m, 2)
+    with LS.Solver(w.m, w.omega, mixed=True) as s:
+        assert _sampled_apply_check(s, w, 4, 3) < 1e-11
+        s.factor()
+        g = s.rhs_plane_wave(w.directions)
+        u, info = s.solve(g, tol=1e-6)
+    assert all(i.converged and i.rel_resid <= 1e-6 for i in info)
+    assert max(i.iters for i in info) <= 20
+    for j in (0, 5):
+        assert _true_resid(w, u[j], g[j]) < 1.01e-6
