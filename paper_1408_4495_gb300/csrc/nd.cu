@@ -409,14 +409,14 @@ template <typename C> __global__ void k_set_one(C* F, long n_one, const int64_t*
 
 // Schur complements of the children with child index k into their parents' fronts.
 template <typename C> __global__ void k_extend_add(LevelK<C> P, LevelK<C> Ch, int k) {
-  const int c = blockIdx.y;
+  const int c = blockIdx.x;
   if (Ch.kidx[c] != k) return;
   const int pz = Ch.parent[c];
   C* Fp = P.F + (size_t)pz * P.fmax * P.ncols;
   const C* Fc = Ch.F + (size_t)c * Ch.fmax * Ch.ncols;
   const int* ea = Ch.ea + (size_t)c * Ch.bmax;
   const long tot = (long)Ch.bmax * Ch.bmax;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.x * blockDim.x) {
+  for (long idx = blockIdx.y * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.y * blockDim.x) {
     const int a = (int)(idx % Ch.bmax), b = (int)(idx / Ch.bmax);
     const int pa = ea[a], pb = ea[b];
     if (pa < 0 || pb < 0) continue;
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(512) k_panel(LevelK<C> L, int k0, int k1, int*
 
 // Columns c in [k1, ncols): apply the panel's row swaps, then F[k0:k1, c] = L_kk^{-1} F[k0:k1, c].
 template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK<C> L, int k0, int k1) {
-  const int z = blockIdx.y;
+  const int z = blockIdx.x;
   const int fmax = L.fmax, w = k1 - k0;
   C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C Ld[NB][NB + 1];
@@ -559,7 +559,7 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK
     npos = cnt;
   }
   __syncthreads();
-  const int c = k1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = k1 + blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= L.ncols) return;
   C* col = A + (size_t)c * fmax;
   const int np = npos;
@@ -593,7 +593,7 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK
 
 // Columns c in [smax, ncols): F[j0:j1, c] = U_blk^{-1} F[j0:j1, c] (non-unit upper).
 template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK<C> L, int j0, int j1) {
-  const int z = blockIdx.y;
+  const int z = blockIdx.x;
   const int fmax = L.fmax, w = j1 - j0;
   C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C Ud[NB][NB + 1];
@@ -602,7 +602,7 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
     Ud[i][l] = A[(size_t)(j0 + l) * fmax + j0 + i];
   }
   __syncthreads();
-  const int c = L.smax + blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = L.smax + blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= L.ncols) return;
   C* col = A + (size_t)c * fmax;
   C x[NB];
@@ -628,10 +628,10 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
 template <typename C>
 __global__ void __launch_bounds__(256) k_gemm(LevelK<C> L, int r0, int r1, int c0, int c1, int k0, int k1) {
   constexpr int TM = 64, TK = 16;
-  const int z = blockIdx.y;
+  const int z = blockIdx.x;
   const int fmax = L.fmax, w = k1 - k0;
   const int nt = (r1 - r0 + TM - 1) / TM;
-  const int tr = blockIdx.x % nt, tcb = blockIdx.x / nt;
+  const int tr = blockIdx.y % nt, tcb = blockIdx.y / nt;
   const int rb = r0 + tr * TM, cb = c0 + tcb * TM;
   C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C As[TK][TM + 1];
@@ -822,7 +822,7 @@ template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1
   if (r1 <= r0 || c1 <= c0 || k1 <= k0) return;
   const int nr = (r1 - r0 + 63) / 64, nc = (c1 - c0 + 63) / 64;
   LS_LAUNCH(sizeof(C) == 8 ? "nd_gemm_c64" : "nd_gemm_c128", st,
-            k_gemm<C><<<dim3(nr * nc, L.nf), 256, 0, st>>>(L, r0, r1, c0, c1, k0, k1));
+            k_gemm<C><<<dim3(L.nf, nr * nc), 256, 0, st>>>(L, r0, r1, c0, c1, k0, k1));
 }
 
 template <typename C> bool nd_prepare(NdPlan* p) { return ensure_buffers(p, sizeof(C)); }
@@ -882,7 +882,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       const unsigned bx = (unsigned)std::max<long>(1, std::min<long>((tot + 255) / 256, 64));
       for (int k = 0; k < 2; ++k)
         LS_LAUNCH(f32 ? "nd_extend_add_c64" : "nd_extend_add_c128", st,
-                  k_extend_add<C><<<dim3(bx, Ch.nf), 256, 0, st>>>(L, Ch, k));
+                  k_extend_add<C><<<dim3(Ch.nf, bx), 256, 0, st>>>(L, Ch, k));
     }
     {
       // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
@@ -898,7 +898,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
                     k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
         const int m = L.ncols - k1;
         LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                  k_trsm_lower<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, k0, k1));
+                  k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
         launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st);
       }
       // sweep 2: backward substitution with U11 on the own rows of [F12 | I]
@@ -907,7 +907,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
         const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
         const int m = L.ncols - L.smax;
         LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                  k_trsm_upper<C><<<dim3((m + 127) / 128, L.nf), 128, 0, st>>>(L, j0, j1));
+                  k_trsm_upper<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, j0, j1));
         launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st);
       }
     }
@@ -968,10 +968,10 @@ template <typename C, int RC>
 __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256)
     k_fwd(LevelK<C> L, LevelK<C> Ch, int has_child, const C* __restrict__ r, int nrhs, long N) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int z = blockIdx.y, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
+  const int z = blockIdx.x, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5, NT = blockDim.x;
   const int fmax = L.fmax, smax = L.smax;
-  const int t0 = smax + blockIdx.x * 32;
+  const int t0 = smax + blockIdx.y * 32;
   // right-hand-side vectors of one item are RCP = RC + 1 entries apart (odd stride: the
   // per-thread stores of different items fall in different banks)
   constexpr int RCP = RC + 1;
@@ -1009,7 +1009,7 @@ __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256)
       __syncthreads();
     }
   }
-  if (blockIdx.x == 0)
+  if (blockIdx.y == 0)
     for (int idx = threadIdx.x; idx < smax * RC; idx += NT) {
       const int q = idx / RC, j = idx % RC;
       if (j < nr) W[(size_t)(rc0 + j) * fmax + q] = wo[q * RCP + j];
@@ -1072,10 +1072,10 @@ __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RCP = RC + 1;  // odd item stride, see k_fwd
   C* zs = reinterpret_cast<C*>(smem_raw);  // [KCH][RCP], later [kg][32][RCP]
-  const int z = blockIdx.y, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
+  const int z = blockIdx.x, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5;
   const int fmax = L.fmax, smax = L.smax, bmax = L.bmax;
-  const int row = (MODE == 0 ? smax : 0) + blockIdx.x * 32 + lane;
+  const int row = (MODE == 0 ? smax : 0) + blockIdx.y * 32 + lane;
   const int rend = MODE == 0 ? fmax : smax;
   const int K = MODE == 0 ? smax : bmax + smax;
   const C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax;
@@ -1142,7 +1142,7 @@ __global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L
   __syncthreads();
   for (int o = threadIdx.x; o < 32 * RC; o += blockDim.x) {
     const int ln = o / RC, j = o % RC;
-    const int r = (MODE == 0 ? smax : 0) + blockIdx.x * 32 + ln;
+    const int r = (MODE == 0 ? smax : 0) + blockIdx.y * 32 + ln;
     if (r >= rend || j >= nr) continue;
     C s = czero<C>();
     for (int q = 0; q < kg; ++q) s = cadd(s, zs[((size_t)q * 32 + ln) * RCP + j]);
@@ -1169,7 +1169,7 @@ static void launch_gemv(const LevelK<C>& L, C* X, int nr, long N, cudaStream_t s
                                  (int)((size_t)KCH * 2 * (RC + 1) * sizeof(C))));
     attr = true;
   }
-  const dim3 grid((rows + 31) / 32, L.nf, (nr + RC - 1) / RC);
+  const dim3 grid(L.nf, (rows + 31) / 32, (nr + RC - 1) / RC);
   const bool f32 = sizeof(C) == 8;
   LS_LAUNCH(MODE == 0 ? (f32 ? "nd_fwd_c64" : "nd_fwd_c128") : (f32 ? "nd_bwd_c64" : "nd_bwd_c128"), st,
             k_gemv<C, RC, MODE><<<grid, 32 * kg, smem, st>>>(L, X, nr, N));
@@ -1192,7 +1192,7 @@ static void launch_fwd_fused(const LevelK<C>& L, const LevelK<C>& Ch, int has_ch
     LS_CUDA(cudaFuncSetAttribute(k_fwd<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM_MAX));
     attr = true;
   }
-  const dim3 grid(std::max(1, (L.bmax + 31) / 32), L.nf, (nr + RC - 1) / RC);
+  const dim3 grid(L.nf, std::max(1, (L.bmax + 31) / 32), (nr + RC - 1) / RC);
   LS_LAUNCH(sizeof(C) == 8 ? "nd_fwd_c64" : "nd_fwd_c128", st,
             k_fwd<C, RC><<<grid, 32 * kg, smem, st>>>(L, Ch, has_child, r, nr, N));
 }
