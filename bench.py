@@ -183,9 +183,11 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
-def algorithmic_bytes(cls, w):
-    """Bytes one launch of a kernel class must move (reads + writes), per the pass design:
-    FP32 complex = 8 B, FP64 complex = 16 B, lines of n (grid) or L = 2n (padded)."""
+def algorithmic_bytes(cls, w, nd, counts, steps):
+    """Average bytes one launch of a kernel class must move (reads + writes), from the pass
+    design: FP32 complex = 8 B, FP64 complex = 16 B, lines of n (grid) or L = 2n (padded).
+    The nested-dissection sweeps read every factor block once and move the front vectors;
+    one launch per level, so the per-launch figure is a sweep's bytes / its launches."""
     n, N, R = w.n, w.n ** w.d, w.nrhs
     c = 8 if cls.endswith("_c64") else 16
     wb = 4 if c == 8 else 8
@@ -197,7 +199,29 @@ def algorithmic_bytes(cls, w):
         return R * N * c * 4
     if cls.startswith("stencil"):
         return R * N * (16 + c)             # read FP64 v, write r
+    if cls.startswith("nd_fwd") or cls.startswith("nd_bwd"):
+        key = "fwd" if cls.startswith("nd_fwd") else "bwd"
+        per_sweep = nd[f"{key}_factor_bytes"] + R * nd[f"{key}_bytes_per_rhs"]
+        return per_sweep / nd["levels"]  # one launch per level in both sweeps
     raise ValueError(cls)
+
+
+# ncu DRAM traffic per launch of a kernel class, valid while the class's source file is
+# unchanged (sha1 of the file at capture time); see profiles/.
+TRAFFIC = {
+    "nd_fwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": None, "bytes": None},
+}
+
+
+def recorded_traffic(cls):
+    import hashlib
+    rec = TRAFFIC.get(cls)
+    if not rec or not rec["sha1"]:
+        return None
+    with open(os.path.join(ROOT, rec["file"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != rec["sha1"]:
+            return None
+    return rec["bytes"]
 
 
 def run_gpu(args):
@@ -273,22 +297,26 @@ def run_gpu(args):
     conv = all(i.converged for inf in infos for i in inf)
     launches = prof["total"]
 
-    # roofline region: the same steps again, every launch of one kernel class bracketed by
-    # CUDA events on its stream (graphs are bypassed while launches are timed)
+    # roofline region: the same steps again, every launch bracketed by CUDA events on its
+    # stream (graphs are bypassed while launches are timed); per-class device time shares
     roof = None
     k_roof = max(3, min(args.steps, 10))
-    roof_ms, _, rprof, _ = timed(s_mix, k_roof, 1, args.profile_class)
-    tc = rprof["timed"]
-    if tc["launches"] > 0:
-        avg_ms = tc["ms"] / tc["launches"]
-        abytes = algorithmic_bytes(tc["class"], w)
+    roof_ms, _, rprof, _ = timed(s_mix, k_roof, 1, "*")
+    by_cls = rprof.get("ms_by_class", {})
+    tot_cls = sum(by_cls.values()) or 1.0
+    shares = {k: round(v / tot_cls, 4) for k, v in sorted(by_cls.items(), key=lambda x: -x[1])}
+    cls = args.profile_class
+    if by_cls.get(cls, 0) > 0 and rprof["counts"].get(cls, 0) > 0:
+        nlaunch = rprof["counts"][cls]
+        avg_ms = by_cls[cls] / nlaunch
+        abytes = algorithmic_bytes(cls, w, nd, rprof["counts"], k_roof)
         achieved = abytes / (avg_ms / 1e3) / 1e9
         peak, peak_src = measured_hbm_peak()
-        roof = {"kernel": tc["class"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": args.traffic, "peak_source": peak_src,
+        roof = {"kernel": cls, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(cls), "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_ms * 1e3,
-                "launches_timed": tc["launches"], "steps_timed": k_roof,
-                "share_of_step_time": tc["ms"] / roof_ms}
+                "launches_timed": nlaunch, "steps_timed": k_roof,
+                "share_of_kernel_time": by_cls[cls] / tot_cls}
 
     if args.only_mixed:
         if rank == 0:
@@ -361,7 +389,7 @@ def run_gpu(args):
                 "mixed_over_fp64": value / value64,
                 "setup_ms": setup_s * 1e3, "nd": nd,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "launches_by_class": prof["counts"], "clocks": clocks}
+                "launches_by_class": prof["counts"], "device_time_shares": shares, "clocks": clocks}
         print(json.dumps(line), flush=True)
     s_mix.close()
     if world > 1:
@@ -404,10 +432,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--profile-class", default="fft_col_sym_c64",
-                    help="kernel class timed with CUDA events for the roofline figure")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per launch of that class from an ncu capture (null if not taken)")
+    ap.add_argument("--profile-class", default="nd_fwd_c64",
+                    help="kernel class whose roofline is reported (the largest share of device time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time the mixed-precision steps only (short runs under a profiler)")

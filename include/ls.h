@@ -158,6 +158,11 @@ typedef struct {
   int64_t factor_entries;  /* complex entries stored for all fronts (padded) */
   double factor_flops;     /* real flops of the partial factorizations (padded shapes) */
   double solve_bytes;      /* bytes of factor read by one forward + backward solve */
+  /* bytes moved by one forward sweep (leaves to root) and one backward sweep of the solve,
+   * split into the factor blocks read once per sweep and the vector traffic per
+   * right-hand side (gathers, children's updates, front vectors), padded shapes */
+  double fwd_factor_bytes, fwd_bytes_per_rhs;
+  double bwd_factor_bytes, bwd_bytes_per_rhs;
 } ls_nd_stats;
 
 ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out);

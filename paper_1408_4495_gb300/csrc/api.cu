@@ -762,6 +762,10 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out) {
     out->factor_entries = i.factor_entries;
     out->factor_flops = i.factor_flops;
     out->solve_bytes = i.solve_bytes * eb;
+    out->fwd_factor_bytes = i.fwd_factor_entries * eb;
+    out->fwd_bytes_per_rhs = i.fwd_vec_entries * eb;
+    out->bwd_factor_bytes = i.bwd_factor_entries * eb;
+    out->bwd_bytes_per_rhs = i.bwd_vec_entries * eb;
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);

@@ -79,6 +79,9 @@ struct NdInfo {
   int levels, fronts, max_front;
   int64_t factor_entries;
   double factor_flops, solve_bytes;
+  // entries (not bytes) touched by one forward / backward sweep: factor blocks, and
+  // vector entries per right-hand side
+  double fwd_factor_entries, fwd_vec_entries, bwd_factor_entries, bwd_vec_entries;
 };
 NdInfo nd_info(const NdPlan* p);
 // factors: assembles M into the fronts and factors them, in C (float2 or double2);

@@ -211,7 +211,16 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       cm += (double)L.bmax * L.smax * (L.ncols - L.smax);
       flops += 8.0 * cm * L.nf;
       solve_entries += (double)L.nf * ((double)L.smax * L.smax + 2.0 * L.smax * L.bmax);
+      // forward: Y (bmax x smax) once; per right-hand side: r at the own points, the front
+      // vector written (fmax); backward: [H | F11^-1] (smax x (bmax + smax)) once; per
+      // right-hand side: x at the ring points, w_own, x written at the own points
+      p->info.fwd_factor_entries += (double)L.nf * L.bmax * L.smax;
+      p->info.fwd_vec_entries += (double)L.nf * ((double)L.smax + L.fmax);
+      p->info.bwd_factor_entries += (double)L.nf * L.smax * ((double)L.bmax + L.smax);
+      p->info.bwd_vec_entries += (double)L.nf * ((double)L.bmax + 2.0 * L.smax);
     }
+    // the children's update vectors read by the parents' forward step
+    for (int l = 1; l < depth; ++l) p->info.fwd_vec_entries += (double)p->lev[l].nf * p->lev[l].bmax;
     p->F_elems = F_off;
     p->W_elems = W_off;
     p->info.levels = depth;

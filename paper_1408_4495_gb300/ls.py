@@ -43,7 +43,9 @@ class LsInfo(ctypes.Structure):
 class LsNdStats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("fronts", ctypes.c_int), ("max_front", ctypes.c_int),
                 ("factor_entries", ctypes.c_int64), ("factor_flops", ctypes.c_double),
-                ("solve_bytes", ctypes.c_double)]
+                ("solve_bytes", ctypes.c_double), ("fwd_factor_bytes", ctypes.c_double),
+                ("fwd_bytes_per_rhs", ctypes.c_double), ("bwd_factor_bytes", ctypes.c_double),
+                ("bwd_bytes_per_rhs", ctypes.c_double)]
 
 
 class LsError(RuntimeError):
@@ -237,5 +239,4 @@ class Solver:
     def nd_stats(self) -> dict:
         s = LsNdStats()
         self._check(self.lib.ls_get_nd_stats(self.h, ctypes.byref(s)))
-        return dict(levels=s.levels, fronts=s.fronts, max_front=s.max_front, factor_entries=s.factor_entries,
-                    factor_flops=s.factor_flops, solve_bytes=s.solve_bytes)
+        return {name: getattr(s, name) for name, _ in LsNdStats._fields_}

@@ -35,10 +35,11 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_structs_match_header_sizes():
-    # ls_grid: 6 ints; ls_info: int, int, double, int (padded to 24); ls_nd_stats: 3 ints + int64 + 2 doubles
+    # ls_grid: 6 ints; ls_info: int, int, double, int (padded to 24);
+    # ls_nd_stats: 3 ints (+pad) + int64 + 6 doubles
     assert ctypes.sizeof(LS.LsGrid) == 24
     assert ctypes.sizeof(LS.LsInfo) == 24
-    assert ctypes.sizeof(LS.LsNdStats) == 40
+    assert ctypes.sizeof(LS.LsNdStats) == 72
 
 
 def test_binding_refuses_without_library(tmp_path):
