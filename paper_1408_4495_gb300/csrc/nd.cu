@@ -30,6 +30,9 @@
 // read once per sweep.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -70,8 +73,6 @@ constexpr int SOLVE_CHUNK = 64;  // right-hand sides per solve launch
 struct NdPlan {
   int d = 0, n = 0;
   long N = 0;
-  std::vector<Node> nodes;
-  std::vector<std::vector<int>> lev_nodes;
   std::vector<LevelDev> lev;
   long n_asm = 0, n_one = 0;
   int64_t* d_asm_off = nullptr;
@@ -84,22 +85,42 @@ struct NdPlan {
   void* W = nullptr;
   int W_bytes = 0;
   int* d_err = nullptr;
-  std::vector<void*> allocs;
+  void* blob = nullptr;  // every index array of the plan, one device allocation
   NdInfo info{};
 };
 
 namespace {
 
-template <typename T> T* upload(NdPlan* p, const std::vector<T>& v, cudaStream_t st) {
-  T* d = nullptr;
-  const size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
-  if (cudaMalloc(&d, bytes) != cudaSuccess) LS_FAIL(ENOMEM_, "cudaMalloc(%zu) failed for the ND plan", bytes);
-  p->allocs.push_back(d);
-  if (!v.empty()) LS_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-  return d;
+// Host result of the symbolic analysis for one (d, n): level shapes and every index array,
+// packed in one blob (16-byte aligned pieces) that each context copies to the device once.
+struct NdHost {
+  int d = 0, n = 0;
+  long N = 0;
+  std::vector<LevelDev> lev;  // shapes and offsets; pointers are set per context
+  struct Off {
+    size_t own, ring, child, parent, kidx, ea, piv;
+  };
+  std::vector<Off> off;
+  size_t asm_off_o = 0, asm_row_o = 0, asm_t_o = 0, one_off_o = 0, err_o = 0;
+  long n_asm = 0, n_one = 0;
+  size_t F_elems = 0, W_elems = 0;
+  NdInfo info{};
+  std::vector<unsigned char> blob;
+};
+
+template <typename T> size_t put(std::vector<unsigned char>& blob, const std::vector<T>& v) {
+  const size_t o = (blob.size() + 15) / 16 * 16;
+  blob.resize(o + std::max<size_t>(1, v.size()) * sizeof(T), 0);
+  if (!v.empty()) std::memcpy(blob.data() + o, v.data(), v.size() * sizeof(T));
+  return o;
 }
 
-void build_tree(NdPlan* p, int leaf_max) {
+struct TreeBuild {
+  int d = 0, n = 0;
+  std::vector<Node> nodes;
+};
+
+void build_tree(TreeBuild* p, int leaf_max) {
   const int d = p->d, n = p->n;
   struct Item { int lo[3], hi[3], depth, parent, kidx; };
   std::vector<Item> stack;
@@ -170,33 +191,35 @@ void build_tree(NdPlan* p, int leaf_max) {
   }
 }
 
-}  // namespace
-
-NdPlan* nd_build(int d, int n, cudaStream_t st) {
-  NdPlan* p = new NdPlan;
-  try {
+std::shared_ptr<NdHost> host_symbolic(int d, int n) {
+  auto H = std::make_shared<NdHost>();
+  NdHost* p = H.get();
+  TreeBuild T;
+  {
     p->d = d;
     p->n = n;
     p->N = d == 2 ? (long)n * n : (long)n * n * n;
-    build_tree(p, d == 2 ? 16 : 27);
+    T.d = d;
+    T.n = n;
+    build_tree(&T, d == 2 ? 16 : 27);
     int depth = 0;
-    for (auto& nd : p->nodes) depth = std::max(depth, nd.depth + 1);
-    p->lev_nodes.assign(depth, {});
+    for (auto& nd : T.nodes) depth = std::max(depth, nd.depth + 1);
+    std::vector<std::vector<int>> lev_nodes(depth);
     p->lev.assign(depth, LevelDev{});
-    for (int id = 0; id < (int)p->nodes.size(); ++id) {
-      Node& nd = p->nodes[id];
-      nd.slot = (int)p->lev_nodes[nd.depth].size();
-      p->lev_nodes[nd.depth].push_back(id);
+    for (int id = 0; id < (int)T.nodes.size(); ++id) {
+      Node& nd = T.nodes[id];
+      nd.slot = (int)lev_nodes[nd.depth].size();
+      lev_nodes[nd.depth].push_back(id);
     }
     size_t F_off = 0, W_off = 0;
     double flops = 0, solve_entries = 0;
     int max_front = 0;
     for (int l = 0; l < depth; ++l) {
       LevelDev& L = p->lev[l];
-      L.nf = (int)p->lev_nodes[l].size();
-      for (int id : p->lev_nodes[l]) {
-        L.smax = std::max(L.smax, (int)p->nodes[id].own.size());
-        L.bmax = std::max(L.bmax, (int)p->nodes[id].ring.size());
+      L.nf = (int)lev_nodes[l].size();
+      for (int id : lev_nodes[l]) {
+        L.smax = std::max(L.smax, (int)T.nodes[id].own.size());
+        L.bmax = std::max(L.bmax, (int)T.nodes[id].ring.size());
       }
       L.fmax = L.smax + L.bmax;
       L.ncols = L.fmax + L.smax;
@@ -224,7 +247,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
     p->F_elems = F_off;
     p->W_elems = W_off;
     p->info.levels = depth;
-    p->info.fronts = (int)p->nodes.size();
+    p->info.fronts = (int)T.nodes.size();
     p->info.max_front = max_front;
     p->info.factor_entries = (int64_t)F_off;
     p->info.factor_flops = flops;
@@ -255,8 +278,8 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
     auto tcode = [&](int t0, int t1, int t2) -> unsigned char {
       return (unsigned char)(d == 2 ? (t0 + 1) * 3 + (t1 + 1) : ((t0 + 1) * 3 + (t1 + 1)) * 3 + (t2 + 1));
     };
-    for (int id = 0; id < (int)p->nodes.size(); ++id) {
-      const Node& nd = p->nodes[id];
+    for (int id = 0; id < (int)T.nodes.size(); ++id) {
+      const Node& nd = T.nodes[id];
       const int l = nd.depth;
       const LevelDev& L = p->lev[l];
       const int z = nd.slot;
@@ -264,9 +287,9 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       for (int q = 0; q < s; ++q) l_own[l][(size_t)z * L.smax + q] = nd.own[q];
       for (int q = 0; q < b; ++q) l_ring[l][(size_t)z * L.bmax + q] = nd.ring[q];
       for (int k = 0; k < 2; ++k)
-        if (nd.child[k] >= 0) l_child[l][(size_t)z * 2 + k] = p->nodes[nd.child[k]].slot;
+        if (nd.child[k] >= 0) l_child[l][(size_t)z * 2 + k] = T.nodes[nd.child[k]].slot;
       if (nd.parent >= 0) {
-        l_parent[l][z] = p->nodes[nd.parent].slot;
+        l_parent[l][z] = T.nodes[nd.parent].slot;
         l_kidx[l][z] = nd.kidx;
       }
       for (int q = 0; q < s; ++q) pos[nd.own[q]] = q;
@@ -317,7 +340,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       for (int k = 0; k < 2; ++k) {
         const int cid = nd.child[k];
         if (cid < 0) continue;
-        const Node& ch = p->nodes[cid];
+        const Node& ch = T.nodes[cid];
         const LevelDev& Lc = p->lev[l + 1];
         for (int a = 0; a < (int)ch.ring.size(); ++a) {
           const int ps = pos[ch.ring[a]];
@@ -328,25 +351,78 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       for (int q = 0; q < s; ++q) pos[nd.own[q]] = -1;
       for (int q = 0; q < b; ++q) pos[nd.ring[q]] = -1;
     }
+    p->off.resize(depth);
     for (int l = 0; l < depth; ++l) {
-      LevelDev& L = p->lev[l];
-      L.own = upload(p, l_own[l], st);
-      L.ring = upload(p, l_ring[l], st);
-      L.child = upload(p, l_child[l], st);
-      L.parent = upload(p, l_parent[l], st);
-      L.kidx = upload(p, l_kidx[l], st);
-      L.ea = upload(p, l_ea[l], st);
-      std::vector<int> zeros((size_t)L.nf * L.smax, 0);
-      L.piv = upload(p, zeros, st);
+      const LevelDev& L = p->lev[l];
+      NdHost::Off& o = p->off[l];
+      o.own = put(p->blob, l_own[l]);
+      o.ring = put(p->blob, l_ring[l]);
+      o.child = put(p->blob, l_child[l]);
+      o.parent = put(p->blob, l_parent[l]);
+      o.kidx = put(p->blob, l_kidx[l]);
+      o.ea = put(p->blob, l_ea[l]);
+      o.piv = put(p->blob, std::vector<int>((size_t)L.nf * L.smax, 0));
     }
     p->n_asm = (long)asm_off.size();
     p->n_one = (long)one_off.size();
-    p->d_asm_off = upload(p, asm_off, st);
-    p->d_asm_row = upload(p, asm_row, st);
-    p->d_asm_t = upload(p, asm_t, st);
-    p->d_one_off = upload(p, one_off, st);
-    std::vector<int> zero1(1, 0);
-    p->d_err = upload(p, zero1, st);
+    p->asm_off_o = put(p->blob, asm_off);
+    p->asm_row_o = put(p->blob, asm_row);
+    p->asm_t_o = put(p->blob, asm_t);
+    p->one_off_o = put(p->blob, one_off);
+    p->err_o = put(p->blob, std::vector<int>(1, 0));
+  }
+  return H;
+}
+
+}  // namespace
+
+NdPlan* nd_build(int d, int n, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, std::shared_ptr<NdHost>> cache;
+  std::shared_ptr<NdHost> H;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({d, n});
+    if (it != cache.end()) H = it->second;
+  }
+  if (!H) {
+    H = host_symbolic(d, n);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[{d, n}] = H;
+  }
+  NdPlan* p = new NdPlan;
+  try {
+    p->d = d;
+    p->n = n;
+    p->N = H->N;
+    p->lev = H->lev;
+    p->n_asm = H->n_asm;
+    p->n_one = H->n_one;
+    p->F_elems = H->F_elems;
+    p->W_elems = H->W_elems;
+    p->info = H->info;
+    if (cudaMalloc(&p->blob, H->blob.size()) != cudaSuccess) {
+      cudaGetLastError();
+      LS_FAIL(ENOMEM_, "cudaMalloc(%zu) failed for the ND plan", H->blob.size());
+    }
+    LS_CUDA(cudaMemcpyAsync(p->blob, H->blob.data(), H->blob.size(), cudaMemcpyHostToDevice, st));
+    unsigned char* b = static_cast<unsigned char*>(p->blob);
+    for (size_t l = 0; l < p->lev.size(); ++l) {
+      LevelDev& L = p->lev[l];
+      const NdHost::Off& o = H->off[l];
+      L.own = reinterpret_cast<int*>(b + o.own);
+      L.ring = reinterpret_cast<int*>(b + o.ring);
+      L.child = reinterpret_cast<int*>(b + o.child);
+      L.parent = reinterpret_cast<int*>(b + o.parent);
+      L.kidx = reinterpret_cast<int*>(b + o.kidx);
+      L.ea = reinterpret_cast<int*>(b + o.ea);
+      L.piv = reinterpret_cast<int*>(b + o.piv);
+    }
+    p->d_asm_off = reinterpret_cast<int64_t*>(b + H->asm_off_o);
+    p->d_asm_row = reinterpret_cast<int*>(b + H->asm_row_o);
+    p->d_asm_t = b + H->asm_t_o;
+    p->d_one_off = reinterpret_cast<int64_t*>(b + H->one_off_o);
+    p->d_err = reinterpret_cast<int*>(b + H->err_o);
     LS_CUDA(cudaStreamSynchronize(st));
   } catch (...) {
     nd_free(p);
@@ -357,7 +433,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
 
 void nd_free(NdPlan* p) {
   if (!p) return;
-  for (void* a : p->allocs) cudaFree(a);
+  if (p->blob) cudaFree(p->blob);
   if (p->F) cudaFree(p->F);
   if (p->W) cudaFree(p->W);
   delete p;
