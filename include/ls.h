@@ -46,8 +46,12 @@ typedef enum {
 
 typedef enum {
   LS_PREC_FP64 = 0,  /* every step in FP64 complex ("plain" path) */
-  LS_PREC_MIXED = 1  /* FP32 complex operator apply, stencil, fronts and solves; FP64 Arnoldi,
-                        Hessenberg least squares and outer residual g - A u (refinement) */
+  LS_PREC_MIXED = 1, /* FP32 complex operator apply, stencil, fronts and solves; FP64 Arnoldi
+                        and Hessenberg least squares; the outer residual g - A u (refinement)
+                        with the operator in float-float arithmetic (LS_PREC_FF) */
+  LS_PREC_FF = 2     /* ls_apply only: the FFT operator in float-float arithmetic (each real an
+                        unevaluated sum of two FP32 numbers, about 48 significant bits), FP64
+                        at the boundary */
 } ls_prec;
 
 typedef struct {
@@ -107,8 +111,8 @@ ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_o
  * ls_solve -- Sec. 3.3: right-preconditioned GMRES(restart) on (I + K omega^2 m) u = g with
  * the sparsifying preconditioner, all right-hand sides batched in each launch.  Under
  * LS_PREC_MIXED the inner cycles are flexible GMRES with FP32 preconditioner and operator and
- * FP64 Arnoldi, wrapped in FP64 iterative refinement; the stopping test is always the FP64
- * relative residual.  Requires ls_factor (else LS_ESTATE).
+ * FP64 Arnoldi, wrapped in iterative refinement whose residual g - A u is formed in FP64 with
+ * the operator in float-float arithmetic; the stopping test is that relative residual.  Requires ls_factor (else LS_ESTATE).
  *   rhs    nrhs x n^d complex doubles (g), host or device.
  *   tol    relative residual tolerance, > 0.
  *   u_out  nrhs x n^d complex doubles, host or device, written (best iterate on LS_ENOCONV).
@@ -140,7 +144,8 @@ ls_status ls_kernel_table(ls_ctx* c, double* out);
 ls_status ls_stencils(ls_ctx* c, double* alpha_out, double* c_out);
 
 /* Sec. 2.1 eq. lso: out = (I + K omega^2 m) in, nrhs vectors, in the arithmetic prec
- * (LS_PREC_MIXED = FP32 complex inside, FP64 at the boundary). */
+ * (LS_PREC_MIXED = FP32 complex inside, LS_PREC_FF = float-float inside, FP64 at the
+ * boundary). */
 ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec);
 
 /* Sec. 2.2 eq. PC, right-hand factor: out = [A;B] in (the 3^d-point stencil of each point's

@@ -61,6 +61,7 @@ struct ls_ctx {
   double2* ktq = nullptr;
   float2* sym32 = nullptr;
   double2* sym64 = nullptr;
+  float2* ffbuf = nullptr;  // float-float twiddles, symbol and omega^2 m
   double2* alpha64 = nullptr;
   float2* alpha32 = nullptr;
   double2* cint64 = nullptr;
@@ -224,6 +225,15 @@ template <typename C> void op_apply(ls_ctx* c, int nrhs, const C* u, C* y) {
   ls::conv_apply<C>(c->plan, nrhs, u, y, nullptr, true, t1, t2, c->st);
 }
 
+// y = (I + K omega^2 m) u, or y = sub - (I + K omega^2 m) u, in float-float arithmetic
+// (16-byte intermediates: the FP64 scratch buffers)
+void op_apply_ff(ls_ctx* c, int nrhs, const double2* u, double2* y, const double2* sub) {
+  const size_t s1 = ls::conv_scratch1_elems(c->d, c->n, nrhs), s2 = ls::conv_scratch2_elems(c->d, c->n, nrhs);
+  void* t1 = buf<double2>(c, "conv1_64", s1);
+  void* t2 = s2 ? buf<double2>(c, "conv2_64", s2) : nullptr;
+  ls::conv_apply_ff(c->plan, nrhs, u, y, sub, t1, t2, c->st);
+}
+
 // z = M^{-1} [A;B] v for FP64 input v; z in the factor precision C
 template <typename C> void precond_apply(ls_ctx* c, int nrhs, const double2* v, C* z) {
   C* r = buf<C>(c, sizeof(C) == 8 ? "pre_r32" : "pre_r64", (size_t)nrhs * c->N);
@@ -252,7 +262,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
   ensure_basis(c, 2, nrhs, sizeof(CZ));
   double2* w = buf<double2>(c, "w64", tot);
   double2* r = buf<double2>(c, "r64", tot);
-  double2* Au = buf<double2>(c, "Au64", tot);
+  double2* Au = mixed ? nullptr : buf<double2>(c, "Au64", tot);
   CZ* wz = mixed ? buf<CZ>(c, "w32", tot) : nullptr;
   const int nblk = ls::dots_blocks(N);
   double2* partial = buf<double2>(c, "partial", (size_t)nrhs * (R + 2) * nblk);
@@ -378,10 +388,15 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       LS_CUDA(cudaMemcpyAsync(yd, Y.data(), Y.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
       ls::update_u<CZ>((const CZ* const*)c->dZ, kmax, yd, R, u, N, nrhs, c->st);
     }
-    // FP64 residual r = g - A u
+    // residual r = g - A u in FP64 storage; the operator in float-float arithmetic on the
+    // mixed path (GB300's FP64 rate is a small fraction of its FP32 rate), FP64 otherwise
     run_graph(c, "resid:" + std::to_string(nrhs), [&] {
-      op_apply<double2>(c, nrhs, u, Au);
-      ls::residual(g, Au, r, tot, c->st);
+      if (mixed) {
+        op_apply_ff(c, nrhs, u, r, g);
+      } else {
+        op_apply<double2>(c, nrhs, u, Au);
+        ls::residual(g, Au, r, tot, c->st);
+      }
       ls::norms2<double2>(r, N, nrhs, partial, hd, 1, c->st);
     });
     LS_CUDA(cudaMemcpyAsync(hh.data(), hd, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
@@ -514,6 +529,16 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
     }
     c->plan.sym32 = c->sym32;
     c->plan.sym64 = c->sym64;
+    {
+      const size_t ntw = 2 * (size_t)L, nsy = 2 * (size_t)nq;
+      c->ffbuf = dalloc<float2>(ntw + nsy + (size_t)c->N);
+      ls::to_ff(reinterpret_cast<const double*>(c->tw64), c->ffbuf, (long)ntw, c->st);
+      ls::to_ff(reinterpret_cast<const double*>(c->sym64), c->ffbuf + ntw, (long)nsy, c->st);
+      ls::to_ff(c->w2m64, c->ffbuf + ntw + nsy, c->N, c->st);
+      c->plan.twff = c->ffbuf;
+      c->plan.symff = c->ffbuf + ntw;
+      c->plan.w2mff = c->ffbuf + ntw + nsy;
+    }
     // stencils (Sec. 3.1), cached per (d, n, b, omega)
     {
       StencilKey key{c->d, n, b, omega};
@@ -593,7 +618,9 @@ ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_o
     const size_t s1 = ls::conv_scratch1_elems(c->d, c->n, nrhs), s2 = ls::conv_scratch2_elems(c->d, c->n, nrhs);
     void* t1 = buf<double2>(c, "conv1_64", s1);
     void* t2 = s2 ? buf<double2>(c, "conv2_64", s2) : nullptr;
-    ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, c->st);
+    // float-float passes on the mixed path, FP64 on the plain path
+    if (c->prec == LS_PREC_MIXED) ls::conv_rhs_ff(c->plan, nrhs, dd, gd, t1, t2, c->st);
+    else ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, c->st);
     copy_out(c, g_out, gd, tot * sizeof(double2));
     LS_CUDA(cudaStreamSynchronize(c->st));
     return LS_OK;
@@ -639,7 +666,7 @@ void ls_free(ls_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : {(void*)c->w2m64, (void*)c->w2m32, (void*)c->tw32, (void*)c->tw64, (void*)c->ktq, (void*)c->sym32,
-                  (void*)c->sym64, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ})
+                  (void*)c->sym64, (void*)c->ffbuf, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ})
     if (p) cudaFree(p);
   for (auto p : c->V) cudaFree(p);
   for (auto p : c->Z) cudaFree(p);
@@ -692,8 +719,12 @@ ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec p
       ls::cast<double2, float2>(x, x32, tot, c->st);
       op_apply<float2>(c, nrhs, x32, y32);
       ls::cast<float2, double2>(y32, y, tot, c->st);
-    } else {
+    } else if (prec == LS_PREC_FF) {
+      op_apply_ff(c, nrhs, x, y, nullptr);
+    } else if (prec == LS_PREC_FP64) {
       op_apply<double2>(c, nrhs, x, y);
+    } else {
+      throw Error{ls::EINVAL_, "unknown precision"};
     }
     copy_out(c, out, y, tot * sizeof(double2));
     LS_CUDA(cudaStreamSynchronize(c->st));

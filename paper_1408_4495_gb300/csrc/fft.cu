@@ -21,10 +21,29 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "ffloat.cuh"
 #include "kernels.h"
 #include "prof.h"
 
 namespace ls {
+
+template <> struct RealOf<ffc> { using T = ff; };
+
+// read-only cached load of one complex entry
+template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
+template <> __device__ __forceinline__ ffc ldg_c<ffc>(const ffc* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  ffc r;
+  r.x = ff(v.x, v.y);
+  r.y = ff(v.z, v.w);
+  return r;
+}
+
+// kernel-class names of the three arithmetics
+template <typename C> constexpr const char* arith_tag();
+template <> constexpr const char* arith_tag<float2>() { return "c64"; }
+template <> constexpr const char* arith_tag<double2>() { return "c128"; }
+template <> constexpr const char* arith_tag<ffc>() { return "cff"; }
 
 // Padded shared-memory index: one spare slot every 8 complex entries keeps the strided
 // Stockham writes (stride R = 8 in the first pass) free of bank conflicts.
@@ -43,6 +62,8 @@ template <> __device__ __forceinline__ void dft<2, -1, float2>(float2* v) { floa
 template <> __device__ __forceinline__ void dft<2, 1, float2>(float2* v) { float2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
 template <> __device__ __forceinline__ void dft<2, -1, double2>(double2* v) { double2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
 template <> __device__ __forceinline__ void dft<2, 1, double2>(double2* v) { double2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
+template <> __device__ __forceinline__ void dft<2, -1, ffc>(ffc* v) { ffc a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
+template <> __device__ __forceinline__ void dft<2, 1, ffc>(ffc* v) { ffc a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
 
 template <int SIGN, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
   C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = rot_i<SIGN>(csub(a1, a3));
@@ -54,9 +75,13 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft4(C& a0, C& a
 
 template <int SIGN, typename C> __device__ __forceinline__ void dft4v(C* v) { dft4<SIGN>(v[0], v[1], v[2], v[3]); }
 
+template <typename Rl> __device__ __forceinline__ Rl cos_pi4() { return (Rl)0.70710678118654752440; }
+// cos(pi/4) as an FP32 pair: 0.70710677 + 1.21016175e-8
+template <> __device__ __forceinline__ ff cos_pi4<ff>() { return ff(0.70710677f, 1.21016175e-8f); }
+
 template <int SIGN, typename C> __device__ __forceinline__ void dft8v(C* v) {
   using Rl = typename RealOf<C>::T;
-  const Rl c = (Rl)0.70710678118654752440;  // cos(pi/4)
+  const Rl c = cos_pi4<Rl>();
   C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
   C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
   dft4<SIGN>(e0, e1, e2, e3);
@@ -101,7 +126,7 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
         const int k = j & (NS - 1);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          C w = __ldg(&tw[r * k * (L / (NS * R))]);
+          C w = ldg_c(&tw[r * k * (L / (NS * R))]);
           if (SIGN > 0) w.y = -w.y;
           v[q][r] = cmul(v[q][r], w);
         }
@@ -181,7 +206,12 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
           const int li = idx / n_in, e = idx - li * n_in;
           const long line = line0 + li;
           if (line < a.lines) {
-            v[u] = in[line * a.in_ls + e];
+            if constexpr (std::is_same<C, ffc>::value) {
+              v[u] = a.in64 ? ffc_from(reinterpret_cast<const double2*>(a.in)[line * a.in_ls + e])
+                            : in[line * a.in_ls + e];
+            } else {
+              v[u] = in[line * a.in_ls + e];
+            }
             if (pw != nullptr) wv[u] = pw[(line % a.pw_lines) * n_in + e];
           }
         }
@@ -205,8 +235,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
     C v = czero<C>();
     if (line < a.lines) {
       if (a.plane_dirs != nullptr) {
-        if constexpr (std::is_same<C, double2>::value) {
-          // v = -omega^2 m(x) exp(i omega x . dir) (right-hand side, eq. ls)
+        if constexpr (std::is_same<C, double2>::value || std::is_same<C, ffc>::value) {
+          // v = -omega^2 m(x) exp(i omega x . dir) (right-hand side, eq. ls), in FP64
           const long q = line % a.pw_lines;      // row within the grid
           const long rhs = line / a.pw_lines;
           const double* dir = a.plane_dirs + rhs * a.d;
@@ -220,9 +250,9 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
           ph *= a.omega * a.h;
           double sn, cs;
           sincos(ph, &sn, &cs);
-          const double w = reinterpret_cast<const double*>(a.pw)[q * n_in + e];
-          v.x = -w * cs;
-          v.y = -w * sn;
+          const double w = a.pw64[q * n_in + e];
+          if constexpr (std::is_same<C, ffc>::value) v = ffc_from(make_double2(-w * cs, -w * sn));
+          else v = make_double2(-w * cs, -w * sn);
         }
       } else {
         v = reinterpret_cast<const C*>(a.in)[line * a.in_ls + e];
@@ -252,6 +282,16 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
     const long line = line0 + li;
     if (line < a.lines) {
       C v = s[li * LS + pidx(e)];
+      if constexpr (std::is_same<C, ffc>::value) {
+        if (a.out64) {
+          // FP64 epilogue: y = v + addv, or y = subv - (v + addv)
+          double2 o = ffc_to(v);
+          if (a.addv != nullptr) o = cadd(o, reinterpret_cast<const double2*>(a.addv)[line * a.add_ls + e]);
+          if (a.subv != nullptr) o = csub(reinterpret_cast<const double2*>(a.subv)[line * a.add_ls + e], o);
+          reinterpret_cast<double2*>(a.out)[line * a.out_ls + e] = o;
+          continue;
+        }
+      }
       if (addv != nullptr) v = cadd(v, addv[line * a.add_ls + e]);
       out[line * a.out_ls + e] = v;
     }
@@ -334,7 +374,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
             const int k1 = (int)(cc / L), k2 = (int)(cc - (long)k1 * L);
             si = ((long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1)) * n1 + (k2 <= L - k2 ? k2 : L - k2);
           }
-          sv[u] = __ldg(&sym[si]);
+          sv[u] = ldg_c(&sym[si]);
         }
       }
 #pragma unroll
@@ -371,9 +411,8 @@ template <typename C, int L, int SIGN> static void launch_row_L(const RowPassArg
   }
   const long blocks = (a.lines + NL - 1) / NL;
   if (blocks == 0) return;
-  const char* cls = sizeof(C) == 8 ? (SIGN < 0 ? "fft_row_fwd_c64" : "fft_row_inv_c64")
-                                   : (SIGN < 0 ? "fft_row_fwd_c128" : "fft_row_inv_c128");
-  LS_LAUNCH(cls, st, k_row_pass<C, L, SIGN><<<(unsigned)blocks, NT, smem, st>>>(a));
+  static const std::string cls = std::string(SIGN < 0 ? "fft_row_fwd_" : "fft_row_inv_") + arith_tag<C>();
+  LS_LAUNCH(cls.c_str(), st, k_row_pass<C, L, SIGN><<<(unsigned)blocks, NT, smem, st>>>(a));
 }
 
 template <typename C, int L, int MODE> static void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
@@ -387,9 +426,9 @@ template <typename C, int L, int MODE> static void launch_col_L(const ColPassArg
   const long tiles = (a.inner + TC - 1) / TC;
   const long blocks = tiles * a.outer;
   if (blocks == 0) return;
-  const char* cls = sizeof(C) == 8 ? (MODE == 0 ? "fft_col_fwd_c64" : MODE == 1 ? "fft_col_inv_c64" : "fft_col_sym_c64")
-                                   : (MODE == 0 ? "fft_col_fwd_c128" : MODE == 1 ? "fft_col_inv_c128" : "fft_col_sym_c128");
-  LS_LAUNCH(cls, st, k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a));
+  static const std::string cls =
+      std::string(MODE == 0 ? "fft_col_fwd_" : MODE == 1 ? "fft_col_inv_" : "fft_col_sym_") + arith_tag<C>();
+  LS_LAUNCH(cls.c_str(), st, k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a));
 }
 
 #define LS_FOR_L(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
@@ -425,27 +464,29 @@ template void row_pass<float2>(int, int, const RowPassArgs&, cudaStream_t);
 template void row_pass<double2>(int, int, const RowPassArgs&, cudaStream_t);
 template void col_pass<float2>(int, int, const ColPassArgs&, cudaStream_t);
 template void col_pass<double2>(int, int, const ColPassArgs&, cudaStream_t);
+template void row_pass<ffc>(int, int, const RowPassArgs&, cudaStream_t);
+template void col_pass<ffc>(int, int, const ColPassArgs&, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
 // Operator-level sequences
 // ------------------------------------------------------------------------------------
 
 // y = (I + K omega^2 m) u  (add_u = true)  or  y = K (omega^2 m u)  (add_u = false),
-// or the right-hand side g = K(-omega^2 m u_I) when plane_dirs != null (double only).
+// or the right-hand side g = K(-omega^2 m u_I) when plane_dirs != null (FP64 or float-float).
+// C is the arithmetic of the passes; with in64 / out64 the first pass reads and the last
+// pass writes FP64 (u, y, sub are then double2), and sub != null gives y = sub - (...).
 template <typename C>
-void conv_apply(const ConvPlan& p, int nrhs, const C* u, C* y, const double* plane_dirs, bool add_u,
-                void* scratch1, void* scratch2, cudaStream_t st) {
-  using Rl = typename RealOf<C>::T;
+static void conv_run(const ConvPlan& p, int nrhs, const void* u, void* y, const double* plane_dirs, bool add_u,
+                     const void* sub, int in64, int out64, const void* tw, const void* sym, const void* w2m,
+                     void* scratch1, void* scratch2, cudaStream_t st) {
   const int n = p.n, L = 2 * n, d = p.d;
   const long rows = (d == 2) ? (long)n : (long)n * n;  // lines of one grid along the last axis
-  const void* tw = std::is_same<C, float2>::value ? (const void*)p.tw32 : (const void*)p.tw64;
-  const void* sym = std::is_same<C, float2>::value ? (const void*)p.sym32 : (const void*)p.sym64;
-  const void* w2m = std::is_same<C, float2>::value ? (const void*)p.w2m32 : (const void*)p.w2m64;
   C* T1 = reinterpret_cast<C*>(scratch1);
   RowPassArgs r{};
   r.in = u; r.out = T1; r.lines = (long)nrhs * rows; r.n_in = n; r.n_out = L;
   r.in_ls = n; r.out_ls = L; r.pw = w2m; r.pw_lines = rows; r.tw = tw;
-  r.plane_dirs = plane_dirs; r.d = d; r.n = n; r.omega = p.omega; r.h = p.h;
+  r.plane_dirs = plane_dirs; r.d = d; r.n = n; r.omega = p.omega; r.h = p.h; r.in64 = in64;
+  r.pw64 = p.w2m64;
   row_pass<C>(L, -1, r, st);
   if (d == 2) {
     ColPassArgs c{};
@@ -473,8 +514,30 @@ void conv_apply(const ConvPlan& p, int nrhs, const C* u, C* y, const double* pla
   RowPassArgs q{};
   q.in = T1; q.out = y; q.lines = (long)nrhs * rows; q.n_in = L; q.n_out = n;
   q.in_ls = L; q.out_ls = n; q.tw = tw; q.addv = add_u ? u : nullptr; q.add_ls = n;
+  q.subv = sub; q.out64 = out64;
   row_pass<C>(L, 1, q, st);
-  (void)sizeof(Rl);
+}
+
+template <typename C>
+void conv_apply(const ConvPlan& p, int nrhs, const C* u, C* y, const double* plane_dirs, bool add_u,
+                void* scratch1, void* scratch2, cudaStream_t st) {
+  const bool f32 = std::is_same<C, float2>::value;
+  conv_run<C>(p, nrhs, u, y, plane_dirs, add_u, nullptr, 0, 0, f32 ? (const void*)p.tw32 : (const void*)p.tw64,
+              f32 ? (const void*)p.sym32 : (const void*)p.sym64, f32 ? (const void*)p.w2m32 : (const void*)p.w2m64,
+              scratch1, scratch2, st);
+}
+
+void conv_apply_ff(const ConvPlan& p, int nrhs, const double2* u, double2* y, const double2* sub, void* scratch1,
+                   void* scratch2, cudaStream_t st) {
+  if (!p.twff || !p.symff || !p.w2mff) LS_FAIL(ESTATE_, "float-float operator tables missing");
+  conv_run<ffc>(p, nrhs, u, y, nullptr, true, sub, 1, 1, p.twff, p.symff, p.w2mff, scratch1, scratch2, st);
+}
+
+void conv_rhs_ff(const ConvPlan& p, int nrhs, const double* plane_dirs, double2* g, void* scratch1, void* scratch2,
+                 cudaStream_t st) {
+  if (!p.twff || !p.symff) LS_FAIL(ESTATE_, "float-float operator tables missing");
+  conv_run<ffc>(p, nrhs, nullptr, g, plane_dirs, false, nullptr, 0, 1, p.twff, p.symff, p.w2mff, scratch1, scratch2,
+                st);
 }
 
 template void conv_apply<float2>(const ConvPlan&, int, const float2*, float2*, const double*, bool, void*, void*, cudaStream_t);
@@ -584,6 +647,19 @@ __global__ void k_symbol_quadrant(const double2* spec, double2* sym64, float2* s
     sym64[idx] = v;
     sym32[idx] = make_float2((float)v.x, (float)v.y);
   }
+}
+
+// float-float copies of FP64 tables (two floats per real)
+__global__ void k_to_ff(const double* __restrict__ src, float2* __restrict__ dst, long count) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const ff v = ff_from(src[i]);
+    dst[i] = make_float2(v.hi, v.lo);
+  }
+}
+
+void to_ff(const double* src, void* dst, long count, cudaStream_t st) {
+  if (count <= 0) return;
+  LS_LAUNCH("to_ff", st, k_to_ff<<<512, 256, 0, st>>>(src, reinterpret_cast<float2*>(dst), count));
 }
 
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st) {

@@ -18,11 +18,14 @@ struct RowPassArgs {
   const void* pw;      // real weights [(line % pw_lines) * n_in + e], or null
   long pw_lines;
   const void* tw;      // twiddles exp(-2 pi i m / L), m < L
-  const double* plane_dirs;  // right-hand-side prologue (double only), or null
+  const double* plane_dirs;  // right-hand-side prologue (FP64 and float-float passes), or null
+  const double* pw64;  // omega^2 m in FP64 for that prologue
   int d, n;
   double omega, h;
   const void* addv;    // epilogue: out += addv[line * add_ls + e], or null
   long add_ls;
+  const void* subv;    // epilogue: out = subv - (...), or null (float-float passes only)
+  int in64, out64;     // float-float passes: in / out, addv, subv are FP64 complex
 };
 
 struct ColPassArgs {
@@ -45,6 +48,9 @@ struct ConvPlan {
   const double2* sym64;
   const float* w2m32;   // omega^2 m, n^d
   const double* w2m64;
+  const void* twff;     // float-float copies (two floats per real) of tw64, sym64, w2m64
+  const void* symff;
+  const void* w2mff;
 };
 
 template <typename C> void row_pass(int L, int sign, const RowPassArgs& a, cudaStream_t st);
@@ -52,6 +58,15 @@ template <typename C> void col_pass(int L, int mode, const ColPassArgs& a, cudaS
 template <typename C>
 void conv_apply(const ConvPlan& p, int nrhs, const C* u, C* y, const double* plane_dirs, bool add_u,
                 void* scratch1, void* scratch2, cudaStream_t st);
+// y = (I + K omega^2 m) u in float-float arithmetic with FP64 input and output; with
+// sub != null, y = sub - (I + K omega^2 m) u (the residual)
+void conv_apply_ff(const ConvPlan& p, int nrhs, const double2* u, double2* y, const double2* sub, void* scratch1,
+                   void* scratch2, cudaStream_t st);
+// g = K(-omega^2 m u_inc) for plane waves (the right-hand side), float-float passes, FP64 g
+void conv_rhs_ff(const ConvPlan& p, int nrhs, const double* plane_dirs, double2* g, void* scratch1, void* scratch2,
+                 cudaStream_t st);
+// float-float copy of count FP64 reals (dst: 2 * count floats)
+void to_ff(const double* src, void* dst, long count, cudaStream_t st);
 size_t conv_scratch1_elems(int d, int n, int nrhs);
 size_t conv_scratch2_elems(int d, int n, int nrhs);
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st);

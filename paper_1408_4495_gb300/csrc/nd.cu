@@ -55,6 +55,7 @@ struct LevelDev {
   size_t F_off = 0, W_off = 0;
   int *own = nullptr, *ring = nullptr, *child = nullptr, *parent = nullptr, *kidx = nullptr, *ea = nullptr;
   int* piv = nullptr;
+  int* fsrc = nullptr;  // per front position: the two children's W items that add into it (-1: none)
 };
 
 template <typename C> struct LevelK {
@@ -84,6 +85,7 @@ struct NdPlan {
   int F_bytes = 0;
   void* W = nullptr;
   int W_bytes = 0;
+  void* T = nullptr;  // grid-point items of the solve (N x SOLVE_CHUNK)
   int* d_err = nullptr;
   void* blob = nullptr;  // every index array of the plan, one device allocation
   NdInfo info{};
@@ -98,7 +100,7 @@ struct NdHost {
   long N = 0;
   std::vector<LevelDev> lev;  // shapes and offsets; pointers are set per context
   struct Off {
-    size_t own, ring, child, parent, kidx, ea, piv;
+    size_t own, ring, child, parent, kidx, ea, piv, fsrc;
   };
   std::vector<Off> off;
   size_t asm_off_o = 0, asm_row_o = 0, asm_t_o = 0, one_off_o = 0, err_o = 0;
@@ -362,6 +364,21 @@ std::shared_ptr<NdHost> host_symbolic(int d, int n) {
       o.kidx = put(p->blob, l_kidx[l]);
       o.ea = put(p->blob, l_ea[l]);
       o.piv = put(p->blob, std::vector<int>((size_t)L.nf * L.smax, 0));
+      // forward-solve sources: child k's ring entry a lands at position ea[a] of the parent
+      std::vector<int> fsrc((size_t)L.nf * L.fmax * 2, -1);
+      if (l + 1 < depth) {
+        const LevelDev& Lc = p->lev[l + 1];
+        for (int z = 0; z < L.nf; ++z)
+          for (int k = 0; k < 2; ++k) {
+            const int c = l_child[l][(size_t)z * 2 + k];
+            if (c < 0) continue;
+            for (int a = 0; a < Lc.bmax; ++a) {
+              const int ps = l_ea[l + 1][(size_t)c * Lc.bmax + a];
+              if (ps >= 0) fsrc[((size_t)z * L.fmax + ps) * 2 + k] = c * Lc.fmax + Lc.smax + a;
+            }
+          }
+      }
+      o.fsrc = put(p->blob, fsrc);
     }
     p->n_asm = (long)asm_off.size();
     p->n_one = (long)one_off.size();
@@ -417,6 +434,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
       L.kidx = reinterpret_cast<int*>(b + o.kidx);
       L.ea = reinterpret_cast<int*>(b + o.ea);
       L.piv = reinterpret_cast<int*>(b + o.piv);
+      L.fsrc = reinterpret_cast<int*>(b + o.fsrc);
     }
     p->d_asm_off = reinterpret_cast<int64_t*>(b + H->asm_off_o);
     p->d_asm_row = reinterpret_cast<int*>(b + H->asm_row_o);
@@ -436,12 +454,15 @@ void nd_free(NdPlan* p) {
   if (p->blob) cudaFree(p->blob);
   if (p->F) cudaFree(p->F);
   if (p->W) cudaFree(p->W);
+  if (p->T) cudaFree(p->T);
   delete p;
 }
 
 NdInfo nd_info(const NdPlan* p) { return p->info; }
 
-size_t nd_device_bytes(const NdPlan* p, int elem_bytes) { return (p->F_elems + p->W_elems) * (size_t)elem_bytes; }
+size_t nd_device_bytes(const NdPlan* p, int elem_bytes) {
+  return (p->F_elems + p->W_elems + (size_t)p->N * SOLVE_CHUNK) * (size_t)elem_bytes;
+}
 
 // ---------------------------------------------------------------------------------------
 // factorization kernels
@@ -884,6 +905,7 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes) {
   if (p->F && p->F_bytes == elem_bytes) return false;
   if (p->F) { cudaFree(p->F); p->F = nullptr; }
   if (p->W) { cudaFree(p->W); p->W = nullptr; }
+  if (p->T) { cudaFree(p->T); p->T = nullptr; }
   if (cudaMalloc(&p->F, p->F_elems * elem_bytes) != cudaSuccess) {
     cudaGetLastError();
     LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the fronts failed", p->F_elems * elem_bytes);
@@ -891,6 +913,10 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes) {
   if (cudaMalloc(&p->W, std::max<size_t>(1, p->W_elems) * elem_bytes) != cudaSuccess) {
     cudaGetLastError();
     LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the front vectors failed", p->W_elems * elem_bytes);
+  }
+  if (cudaMalloc(&p->T, (size_t)p->N * SOLVE_CHUNK * elem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the solve items failed", (size_t)p->N * SOLVE_CHUNK * elem_bytes);
   }
   p->F_bytes = p->W_bytes = elem_bytes;
   return true;
@@ -1005,304 +1031,371 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
 // ---------------------------------------------------------------------------------------
 // solves
 // ---------------------------------------------------------------------------------------
+// The two sweeps of the multifrontal solve with the factored fronts, one launch per level:
+//   forward (leaves to root):  w_own  = r_own + the children's updates at the own positions,
+//                              u_ring = the children's updates at the ring positions + Y w_own;
+//   backward (root to leaves): x_own  = F11^{-1} w_own - H x_ring.
+// Vectors move as items: the RC right-hand sides of one grid point or one front position
+// are contiguous (RC * sizeof(C) bytes, copied as 16-byte pieces).  T holds r at the grid
+// points on the way down and x on the way up: every grid point is own in exactly one front
+// and the backward sweep reads only ring points, which ancestors own and have written.
+// W holds, per level, group of RC right-hand sides and front, [w_own | u_ring].
+// Every launch of a solve is a programmatic dependent of the one before: its prologue
+// (index loads and the first chunk of the factor tile, all written by the factorization,
+// which completed before the solve's first kernel started) overlaps the previous level's
+// tail, and griddepcontrol.wait orders every read of T and W after the previous level.
+// Reads of T and W bypass L1 (ld.global.cg).
 
-// W[z] = [w_own ; w_ring]: own entries from r plus the children's updates, ring entries
-// from the children's updates.
-template <typename C>
-__global__ void __launch_bounds__(256) k_fwd_gather(LevelK<C> L, LevelK<C> Ch, int has_child, const C* __restrict__ r,
-                                                    int nrhs, long N) {
-  const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
-  const int fmax = L.fmax, smax = L.smax;
-  C* W = L.W + (size_t)z * nrhs * fmax;
-  for (int idx = tid; idx < nrhs * fmax; idx += NT) {
-    const int rhs = idx / fmax, q = idx % fmax;
-    C v = czero<C>();
-    if (q < smax) {
-      const int g = L.own[(size_t)z * smax + q];
-      if (g >= 0) v = r[(size_t)rhs * N + g];
-    }
-    W[idx] = v;
-  }
-  __syncthreads();
-  if (has_child) {
-    for (int k = 0; k < 2; ++k) {
-      const int c = L.child[(size_t)z * 2 + k];
-      if (c < 0) continue;
-      const C* Wc = Ch.W + (size_t)c * nrhs * Ch.fmax;
-      const int* ea = Ch.ea + (size_t)c * Ch.bmax;
-      for (int idx = tid; idx < nrhs * Ch.bmax; idx += NT) {
-        const int rhs = idx / Ch.bmax, a = idx % Ch.bmax;
-        const int ps = ea[a];
-        if (ps < 0) continue;
-        C& x = W[(size_t)rhs * fmax + ps];
-        x = cadd(x, Wc[(size_t)rhs * Ch.fmax + Ch.smax + a]);
+template <typename C> struct Piece;
+template <> struct Piece<float2> { using T = float4; };
+template <> struct Piece<double2> { using T = double2; };
+
+__device__ __forceinline__ float4 padd(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+template <typename P> __device__ __forceinline__ P pzero() {
+  P p;
+  memset(&p, 0, sizeof(P));
+  return p;
+}
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// asynchronous global -> shared copy of one element; a row outside the tile is zero-filled
+template <int B> __device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  const int nb = valid ? B : 0;
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(nb) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(src), "n"(B), "r"(nb) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename C> struct SweepK {
+  const C* F;       // factored fronts of this level
+  C* W;             // front vectors of this level
+  const C* Wc;      // front vectors of the child level (forward)
+  C* T;             // grid-point items
+  const int *own, *ring, *fsrc;
+  int nf, smax, bmax, fmax, ncols;
+  int nf_c, fmax_c;  // child level: fronts and front size (group stride of Wc)
+  int kv;            // items of the vector operand held in shared memory at once
+  long N;
+};
+
+// columns of the factor tile per chunk, and the largest vector operand staged whole
+template <typename C> __host__ __device__ constexpr int sweep_ka() { return sizeof(C) == 8 ? 128 : 64; }
+constexpr size_t SWEEP_VS_MAX = 64 * 1024;
+constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
+
+struct SweepShape {
+  int K, kv, kg, nbuf, kc0;
+  size_t region0, smem;  // region0 in elements
+};
+
+template <typename C, int RC, int MODE> __host__ __device__ SweepShape sweep_shape(int smax, int bmax, int kg_in) {
+  SweepShape s;
+  constexpr int KA = sweep_ka<C>();
+  s.K = MODE == 0 ? smax : bmax + smax;
+  s.kc0 = s.K < KA ? s.K : KA;
+  s.nbuf = s.K > KA ? 2 : 1;
+  s.kv = (size_t)s.K * RC * sizeof(C) <= SWEEP_VS_MAX ? s.K : KA;
+  if (kg_in > 0) s.kg = kg_in;
+  else s.kg = s.K > KA ? 8 : (s.K / 16 < 1 ? 1 : (s.K / 16 > 8 ? 8 : s.K / 16));
+  const size_t a = (size_t)s.nbuf * s.kc0 * 32 + (size_t)s.kv * RC;
+  const size_t red = (size_t)s.kg * 32 * (RC + 1);
+  s.region0 = a > red ? a : red;
+  const size_t wt = MODE == 0 ? 32 * RC : 0;
+  const size_t idx = MODE == 0 ? 3 * (size_t)s.kv + 64 : (size_t)s.kv + 32;
+  s.smem = (s.region0 + wt) * sizeof(C) + idx * sizeof(int);
+  return s;
+}
+
+// vector operand items [c0, c0 + kc) of one front into dst (item-major, RC per item);
+// forward: w_own (also stored to W by the first row tile); backward: [x_ring | w_own]
+template <typename C, int RC, int MODE>
+__device__ __forceinline__ void sweep_gather(const SweepK<C>& S, int z, int g, int c0, int kc, const int* ixs,
+                                             C* dst, bool write_own) {
+  using P = typename Piece<C>::T;
+  constexpr int NV = RC * (int)sizeof(C) / 16;
+  const size_t wrow = (size_t)g * S.nf * S.fmax + (size_t)z * S.fmax;
+  for (int u = threadIdx.x; u < kc * NV; u += blockDim.x) {
+    const int ci = u / NV, v = u % NV, c = c0 + ci;
+    P s = pzero<P>();
+    if (MODE == 0) {
+      int pt, s0, s1;
+      if (ixs) {
+        pt = ixs[3 * ci];
+        s0 = ixs[3 * ci + 1];
+        s1 = ixs[3 * ci + 2];
+      } else {
+        pt = __ldg(S.own + (size_t)z * S.smax + c);
+        s0 = __ldg(S.fsrc + ((size_t)z * S.fmax + c) * 2);
+        s1 = __ldg(S.fsrc + ((size_t)z * S.fmax + c) * 2 + 1);
       }
-      __syncthreads();
+      const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+      P a = pzero<P>(), b = pzero<P>();
+      if (pt >= 0) s = __ldcg(reinterpret_cast<const P*>(S.T + ((size_t)g * S.N + pt) * RC) + v);
+      if (s0 >= 0) a = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s0) * RC) + v);
+      if (s1 >= 0) b = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s1) * RC) + v);
+      s = padd(padd(s, a), b);
+      if (write_own) reinterpret_cast<P*>(S.W + (wrow + c) * RC)[v] = s;
+    } else if (c < S.bmax) {
+      const int pt = ixs ? ixs[ci] : __ldg(S.ring + (size_t)z * S.bmax + c);
+      if (pt >= 0) s = __ldcg(reinterpret_cast<const P*>(S.T + ((size_t)g * S.N + pt) * RC) + v);
+    } else {
+      s = __ldcg(reinterpret_cast<const P*>(S.W + (wrow + c - S.bmax) * RC) + v);
     }
+    reinterpret_cast<P*>(dst)[u] = s;
   }
 }
 
-// Forward sweep of one level, gather and product fused (fronts with smax <= FUSED_SMAX):
-// a CTA builds w_own (own entries of r plus the children's updates) and the children's
-// contributions to its 32 ring rows in shared memory, keeps w_own in W for the backward
-// sweep, and writes u_ring = w_ring + Y w_own for its rows.  Columns are split among the
-// kg warps and the partial sums added in a fixed order.
-constexpr int FUSED_SMAX = 1024;
-
-template <typename C, int RC>
-__global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256)
-    k_fwd(LevelK<C> L, LevelK<C> Ch, int has_child, const C* __restrict__ r, int nrhs, long N) {
+// One level of either sweep.  grid (fronts, row tiles of 32, groups of RC right-hand
+// sides); lane = row of the tile, the kg warps split the columns of each chunk and add
+// their partial sums in a fixed order.  Forward rows are the ring rows of Y (the identity
+// columns of the augmented front); backward rows are the own rows of [H | F11^{-1}].
+template <typename C, int RC, int MODE> __global__ void __launch_bounds__(256) k_sweep(SweepK<C> S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int z = blockIdx.x, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5, NT = blockDim.x;
-  const int fmax = L.fmax, smax = L.smax;
-  const int t0 = smax + blockIdx.y * 32;
-  // right-hand-side vectors of one item are RCP = RC + 1 entries apart (odd stride: the
-  // per-thread stores of different items fall in different banks)
-  constexpr int RCP = RC + 1;
-  C* wt = reinterpret_cast<C*>(smem_raw);  // [32][RCP] ring rows of this tile
-  C* wo = wt + 32 * RCP;                   // [smax][RCP], later [kg][32][RCP]
-  C* W = L.W + (size_t)z * nrhs * fmax;
-  const int* own = L.own + (size_t)z * smax;
-  // own entries of r: one own variable per thread, its RC right-hand sides loaded together
-  for (int q = threadIdx.x; q < smax; q += NT) {
-    const int gi = own[q];
-    C v[RC];
-#pragma unroll
-    for (int j = 0; j < RC; ++j) v[j] = (j < nr && gi >= 0) ? r[(size_t)(rc0 + j) * N + gi] : czero<C>();
-#pragma unroll
-    for (int j = 0; j < RC; ++j) wo[q * RCP + j] = v[j];
-  }
-  for (int idx = threadIdx.x; idx < 32 * RCP; idx += NT) wt[idx] = czero<C>();
-  __syncthreads();
-  if (has_child) {
-    for (int k = 0; k < 2; ++k) {
-      const int c = L.child[(size_t)z * 2 + k];
-      if (c < 0) continue;
-      const C* Wc = Ch.W + (size_t)c * nrhs * Ch.fmax + Ch.smax;
-      const int* ea = Ch.ea + (size_t)c * Ch.bmax;
-      for (int a = threadIdx.x; a < Ch.bmax; a += NT) {
-        const int ps = ea[a];
-        C* dst = ps < 0 ? nullptr : (ps < smax ? &wo[ps * RCP] : ((ps >= t0 && ps < t0 + 32) ? &wt[(ps - t0) * RCP] : nullptr));
-        if (!dst) continue;
-        C v[RC];
-#pragma unroll
-        for (int j = 0; j < RC; ++j) v[j] = j < nr ? Wc[(size_t)(rc0 + j) * Ch.fmax + a] : czero<C>();
-#pragma unroll
-        for (int j = 0; j < RC; ++j) dst[j] = cadd(dst[j], v[j]);
+  constexpr int KA = sweep_ka<C>();
+  const int z = blockIdx.x, g = blockIdx.z, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kg = blockDim.x >> 5, NT = blockDim.x;
+  const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
+  const SweepShape sh = sweep_shape<C, RC, MODE>(smax, bmax, kg);
+  const int K = sh.K, kv = S.kv, t0 = blockIdx.y * 32;
+  const int nrows = MODE == 0 ? bmax : smax;
+  const int rvalid = min(32, nrows - t0);
+  C* as = reinterpret_cast<C*>(smem_raw);         // [nbuf][kc0][32] factor tile chunks
+  C* vs = as + (size_t)sh.nbuf * sh.kc0 * 32;     // [kv][RC] vector operand
+  C* wt = reinterpret_cast<C*>(smem_raw) + sh.region0;  // forward: [32][RC] ring-tile updates
+  int* ixs = reinterpret_cast<int*>(wt + (MODE == 0 ? 32 * RC : 0));
+  const C* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
+               (MODE == 0 ? smax : 0) + t0;
+  auto load_chunk = [&](int ch) {
+    const int cb = ch * KA, kc = min(KA, K - cb);
+    C* dst = as + (size_t)(ch % sh.nbuf) * sh.kc0 * 32;
+    if (rvalid > 0)
+      for (int e = threadIdx.x; e < kc * 32; e += NT) {
+        const int c = e >> 5, i = e & 31;
+        cp_async_elem<sizeof(C)>(dst + e, i < rvalid ? A + (size_t)(cb + c) * fmax + i : A, i < rvalid);
       }
-      __syncthreads();
+    cp_async_commit();
+  };
+
+  // ---- prologue: static data only
+  if (MODE == 0) {
+    for (int c = threadIdx.x; c < kv; c += NT) {
+      ixs[3 * c] = __ldg(S.own + (size_t)z * smax + c);
+      ixs[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
+      ixs[3 * c + 2] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
+    }
+    for (int i = threadIdx.x; i < 32; i += NT) {
+      const int p = smax + t0 + i;
+      ixs[3 * kv + 2 * i] = i < rvalid ? __ldg(S.fsrc + ((size_t)z * fmax + p) * 2) : -1;
+      ixs[3 * kv + 2 * i + 1] = i < rvalid ? __ldg(S.fsrc + ((size_t)z * fmax + p) * 2 + 1) : -1;
+    }
+  } else {
+    for (int c = threadIdx.x; c < kv; c += NT) ixs[c] = c < bmax ? __ldg(S.ring + (size_t)z * bmax + c) : -1;
+    for (int i = threadIdx.x; i < 32; i += NT) ixs[kv + i] = i < rvalid ? __ldg(S.own + (size_t)z * smax + t0 + i) : -1;
+  }
+  const int nch = (K + KA - 1) / KA;
+  if (K > 0) load_chunk(0);
+
+  // ---- after the previous level
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  const bool write_own = MODE == 0 && blockIdx.y == 0;
+  if (K > 0) sweep_gather<C, RC, MODE>(S, z, g, 0, kv, ixs, vs, write_own);
+  if (MODE == 0) {
+    using P = typename Piece<C>::T;
+    constexpr int NV = RC * (int)sizeof(C) / 16;
+    const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+    for (int u = threadIdx.x; u < 32 * NV; u += NT) {
+      const int i = u / NV, v = u % NV;
+      const int s0 = ixs[3 * kv + 2 * i], s1 = ixs[3 * kv + 2 * i + 1];
+      P a = pzero<P>(), b = pzero<P>();
+      if (s0 >= 0) a = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s0) * RC) + v);
+      if (s1 >= 0) b = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s1) * RC) + v);
+      reinterpret_cast<P*>(wt)[u] = padd(a, b);
     }
   }
-  if (blockIdx.y == 0)
-    for (int idx = threadIdx.x; idx < smax * RC; idx += NT) {
-      const int q = idx / RC, j = idx % RC;
-      if (j < nr) W[(size_t)(rc0 + j) * fmax + q] = wo[q * RCP + j];
-    }
-  const int row = t0 + lane;
+
   C acc[RC];
 #pragma unroll
   for (int j = 0; j < RC; ++j) acc[j] = czero<C>();
-  if (row < fmax) {
-    const C* a = L.F + (size_t)z * fmax * L.ncols + (size_t)fmax * fmax + row;  // Y, identity columns
-    const int per = (smax + kg - 1) / kg;
-    const int k0 = g * per, k1 = min(smax, k0 + per);
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
-      const C a0 = a[(size_t)k * fmax], a1 = a[(size_t)(k + 1) * fmax];
-      const C a2 = a[(size_t)(k + 2) * fmax], a3 = a[(size_t)(k + 3) * fmax];
-      const C* z0 = wo + (size_t)k * RCP;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int cb = ch * KA, kc = min(KA, K - cb);
+    if (ch + 1 < nch) {
+      load_chunk(ch + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    // the staged vector operand covers [vb, vb + kv); when it is smaller than K it is
+    // refilled chunk by chunk (kv == KA then)
+    const int vb = kv >= K ? 0 : cb;
+    if (kv < K && ch > 0) {
+      __syncthreads();
+      sweep_gather<C, RC, MODE>(S, z, g, cb, kc, nullptr, vs, write_own);
+    }
+    __syncthreads();
+    if (rvalid > 0) {
+      const C* ab = as + (size_t)(ch % sh.nbuf) * sh.kc0 * 32;
+      const int per = (kc + kg - 1) / kg;
+      const int k0 = w * per, k1 = min(kc, k0 + per);
+      for (int k = k0; k < k1; ++k) {
+        C a = ab[k * 32 + lane];
+        if (MODE == 1 && cb + k < bmax) {
+          a.x = -a.x;
+          a.y = -a.y;
+        }
+        const C* vv = vs + (size_t)(cb + k - vb) * RC;
 #pragma unroll
-      for (int j = 0; j < RC; ++j) {
-        acc[j] = cfma(acc[j], a0, z0[j]);
-        acc[j] = cfma(acc[j], a1, z0[RCP + j]);
-        acc[j] = cfma(acc[j], a2, z0[2 * RCP + j]);
-        acc[j] = cfma(acc[j], a3, z0[3 * RCP + j]);
+        for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a, vv[j]);
       }
     }
-    for (; k < k1; ++k) {
-      const C a0 = a[(size_t)k * fmax];
-      const C* z0 = wo + (size_t)k * RCP;
-#pragma unroll
-      for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a0, z0[j]);
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  C* red = wo;
+  if (rvalid <= 0) return;
+  C* red = reinterpret_cast<C*>(smem_raw);
 #pragma unroll
-  for (int j = 0; j < RC; ++j) red[((size_t)g * 32 + lane) * RCP + j] = acc[j];
+  for (int j = 0; j < RC; ++j) red[((size_t)w * 32 + lane) * (RC + 1) + j] = acc[j];
   __syncthreads();
   for (int o = threadIdx.x; o < 32 * RC; o += NT) {
-    const int ln = o / RC, j = o % RC;
-    const int rr = t0 + ln;
-    if (rr >= fmax || j >= nr) continue;
-    C s = wt[ln * RCP + j];
-    for (int q = 0; q < kg; ++q) s = cadd(s, red[((size_t)q * 32 + ln) * RCP + j]);
-    W[(size_t)(rc0 + j) * fmax + rr] = s;
-  }
-}
-
-// Batched multi-right-hand-side products of the solve, one launch per level:
-//   MODE 0 (forward):  u_ring = w_ring + Y w_own, Y = -F21 F11^{-1} (ring rows of the
-//                      identity columns), written back into the ring part of W;
-//   MODE 1 (backward): x_own = F11^{-1} w_own - H x_ring (own rows of [H | F11^{-1}]),
-//                      scattered to the solution at the own grid points.
-// A CTA takes 32 rows (one warp-wide coalesced segment per column) and splits the columns
-// among its kg warps; the kg partial sums are added in a fixed order in shared memory.
-// The vector operand (RC right-hand sides) is staged in shared memory, KCH columns at a time.
-constexpr int KCH = 256;
-
-template <typename C, int RC, int MODE>
-__global__ void __launch_bounds__(sizeof(C) == 8 ? 512 : 256) k_gemv(LevelK<C> L, C* __restrict__ X, int nrhs, long N) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int RCP = RC + 1;  // odd item stride, see k_fwd
-  C* zs = reinterpret_cast<C*>(smem_raw);  // [KCH][RCP], later [kg][32][RCP]
-  const int z = blockIdx.x, rc0 = blockIdx.z * RC, nr = min(RC, nrhs - rc0);
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, kg = blockDim.x >> 5;
-  const int fmax = L.fmax, smax = L.smax, bmax = L.bmax;
-  const int row = (MODE == 0 ? smax : 0) + blockIdx.y * 32 + lane;
-  const int rend = MODE == 0 ? fmax : smax;
-  const int K = MODE == 0 ? smax : bmax + smax;
-  const C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax;
-  C* W = L.W + (size_t)z * nrhs * fmax;
-  const int* ring = L.ring + (size_t)z * bmax;
-  C acc[RC];
-#pragma unroll
-  for (int j = 0; j < RC; ++j) acc[j] = czero<C>();
-  for (int cb = 0; cb < K; cb += KCH) {
-    const int kc = min(KCH, K - cb);
-    // one column per thread, its RC right-hand sides loaded together
-    for (int k = threadIdx.x; k < kc; k += blockDim.x) {
-      const int c = cb + k;
-      C v[RC];
-      if (MODE == 0) {
-#pragma unroll
-        for (int j = 0; j < RC; ++j) v[j] = j < nr ? W[(size_t)(rc0 + j) * fmax + c] : czero<C>();
-      } else if (c < bmax) {
-        const int gi = ring[c];
-#pragma unroll
-        for (int j = 0; j < RC; ++j) {
-          C x = czero<C>();
-          if (j < nr && gi >= 0) x = X[(size_t)(rc0 + j) * N + gi];
-          x.x = -x.x;
-          x.y = -x.y;
-          v[j] = x;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < RC; ++j) v[j] = j < nr ? W[(size_t)(rc0 + j) * fmax + (c - bmax)] : czero<C>();
-      }
-#pragma unroll
-      for (int j = 0; j < RC; ++j) zs[k * RCP + j] = v[j];
-    }
-    __syncthreads();
-    if (row < rend) {
-      const int per = (kc + kg - 1) / kg;
-      const int k0 = g * per, k1 = min(kc, k0 + per);
-      const C* a = A + (size_t)cb * fmax + row;
-      int k = k0;
-      for (; k + 4 <= k1; k += 4) {
-        const C a0 = a[(size_t)k * fmax], a1 = a[(size_t)(k + 1) * fmax];
-        const C a2 = a[(size_t)(k + 2) * fmax], a3 = a[(size_t)(k + 3) * fmax];
-        const C* z0 = zs + (size_t)k * RCP;
-#pragma unroll
-        for (int j = 0; j < RC; ++j) {
-          acc[j] = cfma(acc[j], a0, z0[j]);
-          acc[j] = cfma(acc[j], a1, z0[RCP + j]);
-          acc[j] = cfma(acc[j], a2, z0[2 * RCP + j]);
-          acc[j] = cfma(acc[j], a3, z0[3 * RCP + j]);
-        }
-      }
-      for (; k < k1; ++k) {
-        const C a0 = a[(size_t)k * fmax];
-        const C* z0 = zs + (size_t)k * RCP;
-#pragma unroll
-        for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a0, z0[j]);
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < RC; ++j) zs[((size_t)g * 32 + lane) * RCP + j] = acc[j];
-  __syncthreads();
-  for (int o = threadIdx.x; o < 32 * RC; o += blockDim.x) {
-    const int ln = o / RC, j = o % RC;
-    const int r = (MODE == 0 ? smax : 0) + blockIdx.y * 32 + ln;
-    if (r >= rend || j >= nr) continue;
-    C s = czero<C>();
-    for (int q = 0; q < kg; ++q) s = cadd(s, zs[((size_t)q * 32 + ln) * RCP + j]);
+    const int i = o / RC, j = o % RC;
+    if (i >= rvalid) continue;
+    C s = MODE == 0 ? wt[i * RC + j] : czero<C>();
+    for (int q = 0; q < kg; ++q) s = cadd(s, red[((size_t)q * 32 + i) * (RC + 1) + j]);
     if (MODE == 0) {
-      C& x = W[(size_t)(rc0 + j) * fmax + r];
-      x = cadd(x, s);
+      S.W[((size_t)g * S.nf * fmax + (size_t)z * fmax + smax + t0 + i) * RC + j] = s;
     } else {
-      const int gi = L.own[(size_t)z * smax + r];
-      if (gi >= 0) X[(size_t)(rc0 + j) * N + gi] = s;
+      const int pt = ixs[kv + i];
+      if (pt >= 0) S.T[((size_t)g * S.N + pt) * RC + j] = s;
     }
   }
 }
 
-template <typename C, int RC, int MODE>
-static void launch_gemv(const LevelK<C>& L, C* X, int nr, long N, cudaStream_t st) {
-  const int rows = MODE == 0 ? L.bmax : L.smax;
-  const int K = MODE == 0 ? L.smax : L.bmax + L.smax;
-  if (rows <= 0 || K <= 0) return;
-  const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, K / 16));
-  const size_t smem = (size_t)std::max(std::min(KCH, K), kg * 32) * (RC + 1) * sizeof(C);
+// r[rhs][N] -> T[group][N][RC] (right-hand sides past nr are zero)
+template <typename C, int RC> __global__ void __launch_bounds__(256) k_items_in(const C* __restrict__ r, C* T, int nr, long N) {
+  constexpr int TP = 512 / RC;
+  __shared__ C s[RC][TP + 1];
+  pdl_wait();
+  pdl_trigger();
+  const long i0 = (long)blockIdx.x * TP;
+  const int g = blockIdx.y;
+  for (int e = threadIdx.x; e < TP * RC; e += blockDim.x) {
+    const int j = e / TP, ii = e % TP;
+    const long i = i0 + ii;
+    const int rhs = g * RC + j;
+    s[j][ii] = (i < N && rhs < nr) ? __ldcg(r + (size_t)rhs * N + i) : czero<C>();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TP * RC; e += blockDim.x) {
+    const int ii = e / RC, j = e % RC;
+    const long i = i0 + ii;
+    if (i < N) T[((size_t)g * N + i) * RC + j] = s[j][ii];
+  }
+}
+
+// T[group][N][RC] -> x[rhs][N] for the nr right-hand sides
+template <typename C, int RC> __global__ void __launch_bounds__(256) k_items_out(const C* T, C* __restrict__ x, int nr, long N) {
+  constexpr int TP = 512 / RC;
+  __shared__ C s[RC][TP + 1];
+  pdl_wait();
+  pdl_trigger();
+  const long i0 = (long)blockIdx.x * TP;
+  const int g = blockIdx.y;
+  for (int e = threadIdx.x; e < TP * RC; e += blockDim.x) {
+    const int ii = e / RC, j = e % RC;
+    const long i = i0 + ii;
+    s[j][ii] = i < N ? __ldcg(T + ((size_t)g * N + i) * RC + j) : czero<C>();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TP * RC; e += blockDim.x) {
+    const int j = e / TP, ii = e % TP;
+    const long i = i0 + ii;
+    const int rhs = g * RC + j;
+    if (i < N && rhs < nr) x[(size_t)rhs * N + i] = s[j][ii];
+  }
+}
+
+// launch as a programmatic dependent of the previous kernel in the stream
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  LS_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+
+template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int l, C* T, int ng, cudaStream_t st) {
+  const LevelDev& D = p->lev[l];
+  const int depth = (int)p->lev.size();
+  const SweepShape sh = sweep_shape<C, RC, MODE>(D.smax, D.bmax, 0);
+  if (sh.K <= 0 && MODE == 1) return;
+  if (sh.smem > SWEEP_SMEM_MAX) LS_FAIL(EINVAL_, "front too large for the solve kernels (%zu bytes of shared memory)", sh.smem);
   static bool attr = false;
   if (!attr) {
-    LS_CUDA(cudaFuncSetAttribute(k_gemv<C, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)KCH * 2 * (RC + 1) * sizeof(C))));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep<C, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_MAX));
     attr = true;
   }
-  const dim3 grid(L.nf, (rows + 31) / 32, (nr + RC - 1) / RC);
+  SweepK<C> S;
+  S.F = reinterpret_cast<const C*>(p->F) + D.F_off;
+  S.W = reinterpret_cast<C*>(p->W) + D.W_off;
+  const bool has_child = l + 1 < depth;
+  S.Wc = has_child ? reinterpret_cast<const C*>(p->W) + p->lev[l + 1].W_off : S.W;
+  S.T = T;
+  S.own = D.own;
+  S.ring = D.ring;
+  S.fsrc = D.fsrc;
+  S.nf = D.nf;
+  S.smax = D.smax;
+  S.bmax = D.bmax;
+  S.fmax = D.fmax;
+  S.ncols = D.ncols;
+  S.nf_c = has_child ? p->lev[l + 1].nf : 0;
+  S.fmax_c = has_child ? p->lev[l + 1].fmax : 0;
+  S.kv = sh.kv;
+  S.N = p->N;
+  const int nrows = MODE == 0 ? D.bmax : D.smax;
+  const dim3 grid(D.nf, std::max(1, (nrows + 31) / 32), ng);
   const bool f32 = sizeof(C) == 8;
   LS_LAUNCH(MODE == 0 ? (f32 ? "nd_fwd_c64" : "nd_fwd_c128") : (f32 ? "nd_bwd_c64" : "nd_bwd_c128"), st,
-            k_gemv<C, RC, MODE><<<grid, 32 * kg, smem, st>>>(L, X, nr, N));
-}
-
-constexpr size_t FUSED_SMEM_MAX = 200 * 1024;
-
-template <typename C, int RC> static size_t fwd_fused_smem(int smax) {
-  const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, smax / 16));
-  return (size_t)(32 + std::max(smax, kg * 32)) * (RC + 1) * sizeof(C);
+            launch_pdl(k_sweep<C, RC, MODE>, grid, dim3(32 * sh.kg), sh.smem, st, S));
 }
 
 template <typename C, int RC>
-static void launch_fwd_fused(const LevelK<C>& L, const LevelK<C>& Ch, int has_child, const C* r, int nr, long N,
-                             cudaStream_t st) {
-  const int kg = std::max(1, std::min(sizeof(C) == 8 ? 16 : 8, L.smax / 16));
-  const size_t smem = fwd_fused_smem<C, RC>(L.smax);
-  static bool attr = false;
-  if (!attr) {
-    LS_CUDA(cudaFuncSetAttribute(k_fwd<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM_MAX));
-    attr = true;
-  }
-  const dim3 grid(L.nf, std::max(1, (L.bmax + 31) / 32), (nr + RC - 1) / RC);
-  LS_LAUNCH(sizeof(C) == 8 ? "nd_fwd_c64" : "nd_fwd_c128", st,
-            k_fwd<C, RC><<<grid, 32 * kg, smem, st>>>(L, Ch, has_child, r, nr, N));
-}
-
-template <typename C, int RC>
-static void solve_chunk(NdPlan* p, int nr, const C* rr, C* xx, cudaStream_t st) {
+static void solve_chunk(NdPlan* p, int nr, const C* r, C* x, cudaStream_t st) {
   const int depth = (int)p->lev.size();
+  const int ng = (nr + RC - 1) / RC;
   const bool f32 = sizeof(C) == 8;
+  C* T = reinterpret_cast<C*>(p->T);
+  constexpr int TP = 512 / RC;
+  const dim3 tgrid((unsigned)((p->N + TP - 1) / TP), ng);
+  LS_LAUNCH(f32 ? "nd_items_c64" : "nd_items_c128", st,
+            launch_pdl(k_items_in<C, RC>, tgrid, dim3(256), 0, st, r, T, nr, p->N));
   for (int l = depth - 1; l >= 0; --l) {
     prof_tag(l);
-    LevelK<C> L = level_k<C>(p, l);
-    LevelK<C> Ch = l + 1 < depth ? level_k<C>(p, l + 1) : L;
-    if (L.smax <= FUSED_SMAX && fwd_fused_smem<C, RC>(L.smax) <= FUSED_SMEM_MAX) {
-      launch_fwd_fused<C, RC>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N, st);
-    } else {
-      LS_LAUNCH(f32 ? "nd_fwd_gather_c64" : "nd_fwd_gather_c128", st,
-                k_fwd_gather<C><<<L.nf, 256, 0, st>>>(L, Ch, l + 1 < depth ? 1 : 0, rr, nr, p->N));
-      launch_gemv<C, RC, 0>(L, xx, nr, p->N, st);
-    }
+    launch_sweep<C, RC, 0>(p, l, T, ng, st);
   }
   for (int l = 0; l < depth; ++l) {
     prof_tag(l);
-    launch_gemv<C, RC, 1>(level_k<C>(p, l), xx, nr, p->N, st);
+    launch_sweep<C, RC, 1>(p, l, T, ng, st);
   }
   prof_tag(-1);
+  LS_LAUNCH(f32 ? "nd_items_c64" : "nd_items_c128", st,
+            launch_pdl(k_items_out<C, RC>, tgrid, dim3(256), 0, st, (const C*)T, x, nr, p->N));
 }
 
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st) {

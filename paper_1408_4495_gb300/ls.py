@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libls.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ENOCONV, LS_ESTATE, LS_ETIMEOUT, LS_EBUFFER = range(8)
-LS_PREC_FP64, LS_PREC_MIXED = 0, 1
+LS_PREC_FP64, LS_PREC_MIXED, LS_PREC_FF = 0, 1, 2
 STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS_ESTATE", "LS_ETIMEOUT", "LS_EBUFFER"]
 
 # every entry point declared in include/ls.h
@@ -219,9 +219,12 @@ class Solver:
         self._check(fn(self.h, nrhs, _ptr(x), _ptr(out), *extra))
         return out
 
-    def apply(self, x, mixed: bool | None = None):
-        mixed = self.mixed if mixed is None else mixed
-        return self._unary(self.lib.ls_apply, x, LS_PREC_MIXED if mixed else LS_PREC_FP64)
+    def apply(self, x, mixed: bool | None = None, prec: int | None = None):
+        """(I + K omega^2 m) x; prec overrides mixed (LS_PREC_FF: float-float operator)."""
+        if prec is None:
+            mixed = self.mixed if mixed is None else mixed
+            prec = LS_PREC_MIXED if mixed else LS_PREC_FP64
+        return self._unary(self.lib.ls_apply, x, prec)
 
     def stencil_apply(self, x, mixed: bool | None = None):
         mixed = self.mixed if mixed is None else mixed

@@ -92,14 +92,32 @@ def test_operator_apply(LS, d, n, freq, mixed):
         assert rel(y, direct) < (2e-5 if mixed else 1e-11)
 
 
+@pytest.mark.parametrize("d,n,freq", CASES + [(2, 128, 16.0), (2, 256, 32.0)])
+def test_operator_apply_float_float(LS, d, n, freq):
+    # the float-float operator of the refinement residual: FP32 pairs carry about 48
+    # significant bits, so it matches the FP64 oracle as closely as the FP64 path does
+    omega = 2 * np.pi * freq
+    m = medium(d, n)
+    nrhs = 2
+    x = rand_c((nrhs,) + (n,) * d, 12)
+    kt = O.kernel_table(n, d, omega)
+    ref = np.array([O.apply_operator(kt, omega, m, x[j]) for j in range(nrhs)])
+    with LS.Solver(m, omega, mixed=True) as s:
+        y = s.apply(x, prec=LS.LS_PREC_FF)
+    assert rel(y, ref) < 1e-11
+    assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("d,n,freq", CASES)
-def test_rhs_plane_wave(LS, d, n, freq):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_rhs_plane_wave(LS, d, n, freq, mixed):
+    # FP64 passes on the plain path, float-float passes on the mixed path
     omega = 2 * np.pi * freq
     m = medium(d, n)
     dirs = W.directions_circle(3) if d == 2 else W.directions_sphere(3, 5)
     kt = O.kernel_table(n, d, omega)
     ref = np.array([O.rhs(kt, omega, m, dr) for dr in dirs])
-    with LS.Solver(m, omega, mixed=True) as s:
+    with LS.Solver(m, omega, mixed=mixed) as s:
         g = s.rhs_plane_wave(dirs)
     assert rel(g, ref) < 1e-11
 
@@ -222,3 +240,6 @@ def test_errors_are_reported_not_raised_in_the_library(LS):
         with pytest.raises(LS.LsError) as e:
             s.solve(np.zeros((1, n, n), complex))
         assert e.value.status == LS.LS_ESTATE
+        with pytest.raises(LS.LsError) as e:
+            s.apply(np.zeros((1, n, n), complex), prec=7)
+        assert e.value.status == LS.LS_EINVAL
