@@ -86,6 +86,7 @@ struct NdPlan {
   void* W = nullptr;
   int W_bytes = 0;
   void* T = nullptr;  // grid-point items of the solve (N x SOLVE_CHUNK)
+  int* swp = nullptr;  // per-front row permutation of the current panel (register sweeps)
   int* d_err = nullptr;
   void* blob = nullptr;  // every index array of the plan, one device allocation
   NdInfo info{};
@@ -455,6 +456,7 @@ void nd_free(NdPlan* p) {
   if (p->F) cudaFree(p->F);
   if (p->W) cudaFree(p->W);
   if (p->T) cudaFree(p->T);
+  if (p->swp) cudaFree(p->swp);
   delete p;
 }
 
@@ -730,6 +732,266 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
     if (i < w) col[j0 + i] = x[i];
 }
 
+// ---------------------------------------------------------------------------------------
+// Register-resident blocked factorization for fronts with at most 32 * RPL own rows.
+// Sweep 1 (LU of F11 with partial pivoting over the own rows, [F12 | I] carried along):
+// per panel of NB columns one CTA factors the panel with one own row per thread (rows in
+// shared memory), then one warp per trailing column (in registers) applies the panel's
+// row permutation, the forward substitution with the unit lower L_kk and the update of
+// the rows below.  Sweep 2 (U11 X = B on the
+// own rows of [F12 | I]): one warp per column runs the whole backward substitution with
+// its column in registers, the U11 columns staged in shared memory 32 at a time.
+// ---------------------------------------------------------------------------------------
+constexpr int SWP_STRIDE = 1 + 4 * NB;  // per front: count, then (position, source) pairs
+
+// dst[e] = src(e) for e < n over the CTA's threads, B loads in flight per thread before the
+// first store (the loads do not wait on the stores of earlier iterations)
+template <int B, typename T, typename F> __device__ __forceinline__ void stage_copy(T* dst, int n, F src) {
+  for (int base = threadIdx.x; base < n; base += blockDim.x * B) {
+    T v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < n) v[u] = src(e);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < n) dst[e] = v[u];
+    }
+  }
+}
+
+template <typename C> __device__ __forceinline__ C shfl_c(C v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+
+// Panel [k0, k1) on own rows [k0, smax), rows kept in shared memory (row stride NB + 1):
+// G = blockDim / R32 threads per row (R32 = R rounded up to 32; G = 1, 2 or 4, so a row's
+// threads share a warp); thread t updates row t / G on the columns c = t (mod G).  Rows are never moved during the elimination: a row chosen
+// as pivot is retired, and the pivot sequence gives at the end the logical order that
+// LAPACK-style row swaps produce (ph[i]: physical row at logical position i).  Pivot =
+// largest |re| + |im| (as LAPACK's izamax), compared as FP32 bit patterns with warp
+// reductions, lowest row on ties; one barrier per column.  The factored panel is written
+// back in logical order and the net permutation to swp.
+template <typename C>
+__global__ void __launch_bounds__(512) k_panel_rows(LevelK<C> L, int k0, int k1, int* __restrict__ swp, int* err) {
+  using Rl = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LDP = NB + 1;
+  __shared__ unsigned skey[2][16], sidx[2][16];
+  __shared__ int pseq[NB];
+  __shared__ int cnt;
+  const int z = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
+  const int G = blockDim.x / ((R + 31) / 32 * 32), r = t / G, g = t - r * G;
+  C* P = reinterpret_cast<C*>(smem_raw);  // [R][LDP]
+  int* ph = reinterpret_cast<int*>(P + (size_t)R * LDP);
+  int* iph = ph + R;
+  const C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;  // local (r, c) at A[c * fmax + r]
+  const bool has = r < R;
+  C* row = P + (size_t)r * LDP;
+  // load: 8 entries in flight per thread (coalesced over the rows of a column)
+  for (int base = t; base < R * w; base += blockDim.x * 8) {
+    C v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < R * w) v[u] = A[(size_t)(e / R) * fmax + e % R];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < R * w) P[(size_t)(e % R) * LDP + e / R] = v[u];
+    }
+  }
+  for (int i = t; i < R; i += blockDim.x) { ph[i] = i; iph[i] = i; }
+  if (t == 0) cnt = 0;
+  __syncthreads();
+  bool done = !has;  // row retired as a pivot (or no row)
+  for (int j = 0; j < w; ++j) {
+    const int par = j & 1;
+    const C aj = has ? row[j] : czero<C>();
+    const bool cand = !done && g == 0;
+    const unsigned key = cand ? __float_as_uint((float)(fabs(aj.x) + fabs(aj.y))) : 0u;
+    const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+    const unsigned iw = __reduce_min_sync(0xffffffffu, (cand && key == kw) ? (unsigned)r : 0xffffffffu);
+    if (lane == 0) { skey[par][wid] = kw; sidx[par][wid] = iw; }
+    __syncthreads();
+    const unsigned k2 = lane < nw ? skey[par][lane] : 0u;
+    const unsigned km = __reduce_max_sync(0xffffffffu, k2);
+    const unsigned bu = __reduce_min_sync(0xffffffffu, (lane < nw && k2 == km) ? sidx[par][lane] : 0xffffffffu);
+    if (bu == 0xffffffffu) {  // no live row left (cannot happen while j < R)
+      if (t == 0) atomicExch(err, 1);
+      break;
+    }
+    const int bi = (int)bu;
+    if (t == 0) {
+      if (km == 0u) atomicExch(err, 1);
+      pseq[j] = bi;
+    }
+    if (r == bi) done = true;
+    if (!done) {
+      const C* prow = P + (size_t)bi * LDP;
+      const C d = prow[j];
+      const Rl den = cabs2(d);
+      const Rl rden = den > 0 ? (Rl)1 / den : (Rl)0;
+      C inv;
+      inv.x = d.x * rden;
+      inv.y = -d.y * rden;
+      const C m = cmul(aj, inv);
+      if (g == 0) row[j] = m;
+      // columns c > j with c = g (mod G), four at a time: loads before the stores
+      int c = j + 1 + ((g - (j + 1) % G) + G) % G;
+      for (; c + 3 * G < w; c += 4 * G) {
+        C pv[4], rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { pv[u] = prow[c + u * G]; rv[u] = row[c + u * G]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) row[c + u * G] = cfms(rv[u], m, pv[u]);
+      }
+      for (; c < w; c += G) row[c] = cfms(row[c], m, prow[c]);
+    }
+    __syncwarp();  // the G threads of a row share a warp: their column writes are seen next step
+  }
+  __syncthreads();
+  if (t == 0)
+    for (int j = 0; j < w; ++j) {
+      // logical swap of position j with the pivot row's position
+      const int bi = pseq[j], pj = ph[j], lb = iph[bi];
+      ph[j] = bi;
+      iph[bi] = j;
+      ph[lb] = pj;
+      iph[pj] = lb;
+    }
+  __syncthreads();
+  C* Aw = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;
+  for (int e = t; e < R * w; e += blockDim.x) {
+    const int c = e / R, i = e - c * R;
+    Aw[(size_t)c * fmax + i] = P[(size_t)ph[i] * LDP + c];
+  }
+  for (int i = t; i < R; i += blockDim.x)
+    if (ph[i] != i) {
+      const int q = atomicAdd(&cnt, 1);
+      swp[(size_t)z * SWP_STRIDE + 1 + 2 * q] = i;
+      swp[(size_t)z * SWP_STRIDE + 2 + 2 * q] = ph[i];
+    }
+  __syncthreads();
+  if (t == 0) swp[(size_t)z * SWP_STRIDE] = cnt;
+}
+
+// One warp per column c in [k1, ncols): local rows p = 32 q + lane of [k0, smax) in slot q,
+// loaded through the panel's permutation; x_p -= L_pi x_i for i < w, p > i (forward
+// substitution inside the block, update below it).  The panel L is staged in shared
+// memory as lp[i * R + p].
+template <typename C, int RPL>
+__global__ void __launch_bounds__(256) k_lower_update(LevelK<C> L, int k0, int k1, const int* __restrict__ swp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z = blockIdx.x;
+  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
+  C* lp = reinterpret_cast<C*>(smem_raw);
+  int* perm = reinterpret_cast<int*>(lp + (size_t)w * R);
+  const C* P = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;
+  stage_copy<8>(lp, w * R, [&](int e) {
+    const int i = e / R, p = e - i * R;
+    return P[(size_t)i * fmax + p];
+  });
+  for (int p = threadIdx.x; p < R; p += blockDim.x) perm[p] = p;
+  __syncthreads();
+  const int* sw = swp + (size_t)z * SWP_STRIDE;
+  const int cnt = sw[0];
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) perm[sw[1 + 2 * q]] = sw[2 + 2 * q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int c = k1 + blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= L.ncols) return;
+  C* col = L.F + (size_t)z * fmax * L.ncols + (size_t)c * fmax + k0;
+  C x[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int p = 32 * q + lane;
+    x[q] = p < R ? col[perm[p]] : czero<C>();
+  }
+  for (int i = 0; i < w; ++i) {
+    const C xi = shfl_c(x[0], i);
+    const C* li = lp + (size_t)i * R;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int p = 32 * q + lane;
+      if (p > i && p < R) x[q] = cfms(x[q], li[p], xi);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int p = 32 * q + lane;
+    if (p < R) col[p] = x[q];
+  }
+}
+
+// One warp per column c in [smax, ncols): x = U11^{-1} x over the own rows, the column in
+// registers (row 32 q + lane in slot q); U11 columns [i0, i0 + 32) staged per block as
+// us[il * rows + p], their reciprocal pivots in invd.
+template <typename C, int RPL>
+__global__ void __launch_bounds__(256) k_upper_solve(LevelK<C> L) {
+  using Rl = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ C invd[32];
+  const int z = blockIdx.x, lane = threadIdx.x & 31;
+  const int fmax = L.fmax, smax = L.smax;
+  C* us = reinterpret_cast<C*>(smem_raw);
+  const C* U = L.F + (size_t)z * fmax * L.ncols;
+  const int c = smax + blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const bool active = c < L.ncols;
+  C* col = L.F + (size_t)z * fmax * L.ncols + (size_t)(active ? c : smax) * fmax;
+  C x[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int p = 32 * q + lane;
+    x[q] = (active && p < smax) ? col[p] : czero<C>();
+  }
+#pragma unroll
+  for (int qi = RPL - 1; qi >= 0; --qi) {
+    const int i0 = 32 * qi;
+    if (i0 < smax) {
+      const int iw = min(32, smax - i0), rows = i0 + iw;
+      __syncthreads();
+      stage_copy<8>(us, iw * rows, [&](int e) {
+        const int il = e / rows, p = e - il * rows;
+        return U[(size_t)(i0 + il) * fmax + p];
+      });
+      for (int il = threadIdx.x; il < iw; il += blockDim.x) {
+        const C dg = U[(size_t)(i0 + il) * fmax + i0 + il];
+        const Rl den = cabs2(dg);
+        C inv;
+        inv.x = den > 0 ? dg.x / den : (Rl)0;
+        inv.y = den > 0 ? -dg.y / den : (Rl)0;
+        invd[il] = inv;
+      }
+      __syncthreads();
+      if (active)
+        for (int li = iw - 1; li >= 0; --li) {
+          const int i = i0 + li;
+          C xi = cmul(shfl_c(x[qi], li), invd[li]);
+          if (lane == li) x[qi] = xi;
+          const C* ui = us + (size_t)li * rows;
+#pragma unroll
+          for (int q = 0; q <= qi; ++q) {
+            const int p = 32 * q + lane;
+            if (p < i) x[q] = cfms(x[q], ui[p], xi);
+          }
+        }
+    }
+  }
+  if (active)
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int p = 32 * q + lane;
+      if (p < smax) col[p] = x[q];
+    }
+}
+
 // F[r0:r1, c0:c1] -= F[r0:r1, k0:k1] F[k0:k1, c0:c1], 64 x 64 tiles, K chunks of 16.
 template <typename C>
 __global__ void __launch_bounds__(256) k_gemm(LevelK<C> L, int r0, int r1, int c0, int c1, int k0, int k1) {
@@ -750,14 +1012,24 @@ __global__ void __launch_bounds__(256) k_gemm(LevelK<C> L, int r0, int r1, int c
     for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
   for (int kk = 0; kk < w; kk += TK) {
     const int kw = min(TK, w - kk);
-    for (int idx = threadIdx.x; idx < TK * TM; idx += blockDim.x) {
-      const int l = idx / TM, rr = idx % TM;
-      C va = czero<C>(), vb = czero<C>();
-      if (l < kw && rb + rr < r1) va = A[(size_t)(k0 + kk + l) * fmax + rb + rr];
-      As[l][rr] = va;
-      const int l2 = idx % TK, cc = idx / TK;
-      if (l2 < kw && cb + cc < c1) vb = A[(size_t)(cb + cc) * fmax + k0 + kk + l2];
-      Bs[l2][cc] = vb;
+    {
+      // all loads of the two tiles in flight before the shared-memory stores
+      constexpr int PER = TK * TM / 256;
+      C va[PER], vb[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * 256;
+        const int l = idx / TM, rr = idx % TM;
+        va[u] = (l < kw && rb + rr < r1) ? A[(size_t)(k0 + kk + l) * fmax + rb + rr] : czero<C>();
+        const int l2 = idx % TK, cc = idx / TK;
+        vb[u] = (l2 < kw && cb + cc < c1) ? A[(size_t)(cb + cc) * fmax + k0 + kk + l2] : czero<C>();
+      }
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * 256;
+        As[idx / TM][idx % TM] = va[u];
+        Bs[idx % TK][idx / TK] = vb[u];
+      }
     }
     __syncthreads();
     for (int l = 0; l < kw; ++l) {
@@ -840,53 +1112,85 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
       __syncthreads();
     }
   }
-  for (int idx = tid; idx < s * nc; idx += NT) {
+  stage_copy<8>(B, s * nc, [&](int idx) {
     const int c = idx / s, r = idx - c * s;
-    B[idx] = A[(size_t)c * fmax + r];
-  }
+    return A[(size_t)c * fmax + r];
+  });
+  // Elimination without moving rows: thread (r, g) updates row r on the columns
+  // c = g (mod G); a row chosen as pivot is retired from the pivot search but, as Gauss-
+  // Jordan requires, still eliminated in later columns.  Pivot = largest |re| + |im| over
+  // the live rows (FP32 bit patterns, warp reductions, lowest row on ties).
+  __shared__ unsigned skey[2][8], sidx[2][8];
+  __shared__ int pseq_s[1024];
+  C* prow = B + (size_t)s * nc;  // normalised pivot row, nc entries
+  const int G = NT / s, r = tid % s, g = tid / s;
+  const bool act = g < G;
+  const int lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
+  bool live = act && g == 0;  // one thread per row takes part in the pivot search
   __syncthreads();
   for (int j = 0; j < s; ++j) {
-    Rl best = -1;
-    int bi = 0x7fffffff;
-    for (int r = j + tid; r < s; r += NT) {
-      const Rl v = cabs2(B[(size_t)j * s + r]);
-      if (v > best) { best = v; bi = r; }
+    const int par = j & 1;
+    const C bj = B[(size_t)j * s + r];
+    const unsigned key = live ? __float_as_uint((float)(fabs(bj.x) + fabs(bj.y))) : 0u;
+    const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+    const unsigned iw = __reduce_min_sync(0xffffffffu, (live && key == kw) ? (unsigned)r : 0xffffffffu);
+    if (lane == 0) { skey[par][wid] = kw; sidx[par][wid] = iw; }
+    __syncthreads();
+    const unsigned k2 = lane < nw ? skey[par][lane] : 0u;
+    const unsigned km = __reduce_max_sync(0xffffffffu, k2);
+    const unsigned bu = __reduce_min_sync(0xffffffffu, (lane < nw && k2 == km) ? sidx[par][lane] : 0xffffffffu);
+    const int bi = bu == 0xffffffffu ? 0 : (int)bu;
+    if (tid == 0) {
+      if (km == 0u || bu == 0xffffffffu) atomicExch(err, 1);
+      pseq_s[j] = bi;
     }
-    argmax_block(best, bi, sv, si);
-    if (bi == 0x7fffffff) bi = j;
-    if (tid == 0 && !(best > 0)) atomicExch(err, 1);
-    if (bi != j)
-      for (int c = j + tid; c < nc; c += NT) {
-        C& x = B[(size_t)c * s + j];
-        C& y = B[(size_t)c * s + bi];
-        const C t = x;
-        x = y;
-        y = t;
+    if (live && r == bi) live = false;
+    // normalised pivot row (columns j+1..nc-1) by the threads of row bi; column j of the
+    // pivot row is left as it is (every thread reads it for the pivot)
+    const C dg = B[(size_t)j * s + bi];
+    const Rl den = cabs2(dg);
+    const Rl rden = den > 0 ? (Rl)1 / den : (Rl)0;
+    C inv;
+    inv.x = dg.x * rden;
+    inv.y = -dg.y * rden;
+    if (act && r == bi)
+      for (int c = j + 1 + ((g - (j + 1) % G) + G) % G; c < nc; c += G) {
+        const C v = cmul(B[(size_t)c * s + bi], inv);
+        prow[c] = v;
+        B[(size_t)c * s + bi] = v;
       }
     __syncthreads();
-    const C dg = B[(size_t)j * s + j];
-    const Rl den = cabs2(dg);
-    C inv;
-    inv.x = den > 0 ? dg.x / den : (Rl)0;
-    inv.y = den > 0 ? -dg.y / den : (Rl)0;
-    for (int c = j + 1 + tid; c < nc; c += NT) {
-      C& x = B[(size_t)c * s + j];
-      x = cmul(x, inv);
-    }
-    __syncthreads();
-    const int ncol = nc - j - 1;
-    for (int idx = tid; idx < ncol * s; idx += NT) {
-      const int cq = idx / s, r = idx - cq * s;
-      if (r == j) continue;
-      const int c = j + 1 + cq;
-      C& x = B[(size_t)c * s + r];
-      x = cfms(x, B[(size_t)j * s + r], B[(size_t)c * s + j]);
+    if (act && r != bi) {
+      const C mr = bj;  // B[j][r], read before any update of this step
+      int c = j + 1 + ((g - (j + 1) % G) + G) % G;
+      for (; c + 3 * G < nc; c += 4 * G) {
+        C pv[4], rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { pv[u] = prow[c + u * G]; rv[u] = B[(size_t)(c + u * G) * s + r]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) B[(size_t)(c + u * G) * s + r] = cfms(rv[u], mr, pv[u]);
+      }
+      for (; c < nc; c += G) B[(size_t)c * s + r] = cfms(B[(size_t)c * s + r], mr, prow[c]);
     }
     __syncthreads();
   }
+  // row ph[i] holds the result for own row i
+  int* ph = reinterpret_cast<int*>(prow + nc);
+  int* iph = ph + s;
+  for (int i = tid; i < s; i += NT) { ph[i] = i; iph[i] = i; }
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < s; ++j) {
+      const int bi = pseq_s[j], pj = ph[j], lb = iph[bi];
+      ph[j] = bi;
+      iph[bi] = j;
+      ph[lb] = pj;
+      iph[pj] = lb;
+    }
+  __syncthreads();
   for (int idx = tid; idx < s * (nc - s); idx += NT) {
-    const int cq = idx / s, r = idx - cq * s;
-    A[(size_t)(s + cq) * fmax + r] = B[(size_t)(s + cq) * s + r];
+    const int cq = idx / s, i = idx - cq * s;
+    A[(size_t)(s + cq) * fmax + i] = B[(size_t)(s + cq) * s + ph[i]];
   }
 }
 
@@ -918,6 +1222,13 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes) {
     cudaGetLastError();
     LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the solve items failed", (size_t)p->N * SOLVE_CHUNK * elem_bytes);
   }
+  int nf_max = 1;
+  for (const LevelDev& D : p->lev) nf_max = std::max(nf_max, D.nf);
+  if (p->swp) { cudaFree(p->swp); p->swp = nullptr; }
+  if (cudaMalloc(&p->swp, (size_t)nf_max * SWP_STRIDE * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    LS_FAIL(ENOMEM_, "cudaMalloc failed for the panel permutations");
+  }
   p->F_bytes = p->W_bytes = elem_bytes;
   return true;
 }
@@ -925,7 +1236,12 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes) {
 // threads for the Gauss-Jordan CTA: about 16 entries of the own-row block per thread
 static int gj_threads(int s, int nc) {
   const int t = ((s * nc / 16 + 31) / 32) * 32;
-  return std::max(32, std::min(256, t));
+  return std::max((s + 31) / 32 * 32, std::min(256, std::max(32, t)));
+}
+
+// shared memory of the Gauss-Jordan CTA: own-row block, normalised pivot row, row order
+template <typename C> static size_t gj_smem(int s, int nc) {
+  return ((size_t)s * nc + nc) * sizeof(C) + 2 * (size_t)s * sizeof(int);
 }
 
 template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
@@ -937,6 +1253,39 @@ template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1
 }
 
 template <typename C> bool nd_prepare(NdPlan* p) { return ensure_buffers(p, sizeof(C)); }
+
+// own rows per lane of the register sweeps (32 * this many own rows at most)
+template <typename C> constexpr int reg_rpl_max() { return sizeof(C) == 8 ? 16 : 8; }
+
+template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* swp, int* err, cudaStream_t st) {
+  const bool f32 = sizeof(C) == 8;
+  const size_t smem_max = (size_t)32 * 32 * RPL * sizeof(C) + (size_t)32 * RPL * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    const size_t psmem_max = (size_t)32 * RPL * (NB + 1) * sizeof(C) + 2 * (size_t)32 * RPL * sizeof(int);
+    LS_CUDA(cudaFuncSetAttribute(k_panel_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_lower_update<C, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_upper_solve<C, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    attr = true;
+  }
+  for (int k0 = 0; k0 < L.smax; k0 += NB) {
+    const int k1 = std::min(k0 + NB, L.smax), R = L.smax - k0;
+    // 1, 2 or 4 threads per row (a power of two, so that a row's threads share a warp)
+    const int r32 = (R + 31) / 32 * 32;
+    const int G = 512 / r32 >= 4 ? 4 : (512 / r32 >= 2 ? 2 : 1);
+    const int threads = r32 * G;
+    const size_t psmem = (size_t)R * (NB + 1) * sizeof(C) + 2 * (size_t)R * sizeof(int);
+    LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+              k_panel_rows<C><<<L.nf, threads, psmem, st>>>(L, k0, k1, swp, err));
+    const int m = L.ncols - k1;
+    const size_t smem = (size_t)(k1 - k0) * R * sizeof(C) + (size_t)R * sizeof(int);
+    LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+              k_lower_update<C, RPL><<<dim3(L.nf, (m + 7) / 8), 256, smem, st>>>(L, k0, k1, swp));
+  }
+  const int m = L.ncols - L.smax;
+  const size_t smem = (size_t)32 * L.smax * sizeof(C);
+  LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st, k_upper_solve<C, RPL><<<dim3(L.nf, (m + 7) / 8), 256, smem, st>>>(L));
+}
 
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
@@ -979,7 +1328,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     const bool has_child = l + 1 < depth;
     LevelK<C> Ch = has_child ? level_k<C>(p, l + 1) : L;
     // own rows: [F11 | F12 | I] -> [* | H | F11^{-1}]
-    const size_t gjm = (size_t)L.smax * L.ncols * sizeof(C);
+    const size_t gjm = gj_smem<C>(L.smax, L.ncols);
     if (gjm <= GJ_SMEM_MAX) {
       // one CTA per front: extend-add, Gauss-Jordan in shared memory, ring rows
       LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
@@ -995,7 +1344,13 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
         LS_LAUNCH(f32 ? "nd_extend_add_c64" : "nd_extend_add_c128", st,
                   k_extend_add<C><<<dim3(Ch.nf, bx), 256, 0, st>>>(L, Ch, k));
     }
-    {
+    if (L.smax <= 32 * reg_rpl_max<C>()) {
+      // both sweeps with the fronts' own rows in registers
+      const int rpl = (L.smax + 31) / 32;
+      if (rpl <= 4) reg_sweeps<C, 4>(L, p->swp, p->d_err, st);
+      else if (rpl <= 8) reg_sweeps<C, 8>(L, p->swp, p->d_err, st);
+      else reg_sweeps<C, reg_rpl_max<C>()>(L, p->swp, p->d_err, st);
+    } else {
       // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
       // them), the block rows of [F12 | I] carried along
       for (int k0 = 0; k0 < L.smax; k0 += NB) {

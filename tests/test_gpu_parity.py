@@ -136,7 +136,8 @@ def test_stencil_apply(LS, d, n, freq, mixed):
     assert rel(r, ref) < (1e-6 if mixed else 1e-12)
 
 
-@pytest.mark.parametrize("d,n,freq", CASES)
+# n = 128 and 256 take the register-resident blocked factorization for their top fronts
+@pytest.mark.parametrize("d,n,freq", CASES + [(2, 128, 16.0), (2, 256, 32.0)])
 @pytest.mark.parametrize("mixed", [False, True])
 def test_preconditioner(LS, d, n, freq, mixed):
     omega = 2 * np.pi * freq
@@ -150,7 +151,21 @@ def test_preconditioner(LS, d, n, freq, mixed):
     with LS.Solver(m, omega, mixed=mixed) as s:
         s.factor()
         z = s.precond(x)
-    assert rel(z, ref) < (1e-3 if mixed else 1e-10)
+    # Forward error: FP64 at rounding level; FP32 grows with the condition number of the
+    # indefinite M (about 1e-2 at n = 256, 32 wavelengths), so it is checked on the smaller
+    # grids only.  Backward error |M z - [A;B] x| / (|M| |z|): the sweeps multiply by the
+    # explicit F11^{-1} of every front, so it grows like cond(F11) u with the separator size;
+    # the FP32 / FP64 ratio of the measured values (u32 / u64 ~ 5e8 at every size) shows
+    # that growth is the conditioning, not a defect.  Bounds: ~5x the values measured on
+    # GB300 (FP64 6e-16, 8e-15, 5e-13; FP32 3e-7, 3e-6, 3e-4 at n <= 64, 128, 256).
+    if not mixed or n <= 128:
+        assert rel(z, ref) < (1e-3 if mixed else 1e-10)
+    bound = {64: (5e-15, 2e-6), 128: (5e-14, 2e-5), 256: (3e-12, 2e-3)}[max(64, n)][1 if mixed else 0]
+    normM = abs(M).sum(axis=1).max()
+    for j in range(nrhs):
+        zj = z[j].reshape(-1)
+        be = np.linalg.norm(M @ zj - S @ x[j].reshape(-1)) / (normM * np.linalg.norm(zj))
+        assert be < bound, be
 
 
 def test_plain_fp64_solve_matches_oracle_iterates():
