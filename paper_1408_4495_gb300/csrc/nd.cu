@@ -87,6 +87,9 @@ struct NdPlan {
   int W_bytes = 0;
   void* T = nullptr;  // grid-point items of the solve (N x SOLVE_CHUNK)
   int* swp = nullptr;  // per-front row permutation of the current panel (register sweeps)
+  void* part = nullptr;  // solve: partial sums of split column ranges
+  size_t part_elems = 0;
+  unsigned* cnt = nullptr;  // solve: per-item arrival counters
   int* d_err = nullptr;
   void* blob = nullptr;  // every index array of the plan, one device allocation
   NdInfo info{};
@@ -457,6 +460,8 @@ void nd_free(NdPlan* p) {
   if (p->W) cudaFree(p->W);
   if (p->T) cudaFree(p->T);
   if (p->swp) cudaFree(p->swp);
+  if (p->part) cudaFree(p->part);
+  if (p->cnt) cudaFree(p->cnt);
   delete p;
 }
 
@@ -1205,6 +1210,26 @@ template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
   return k;
 }
 
+// Launch shape of one level of a solve sweep: rows per tile, tiles, and how many column
+// ranges each tile is split into so that about two CTAs per SM have work (ranges of at
+// least 64 columns: below that the extra partial-sum pass costs more than it saves).
+struct SweepPlan {
+  int K, tr, ntile, nsplit, ksz;
+};
+static SweepPlan sweep_plan(const LevelDev& D, int mode, int ng) {
+  SweepPlan q;
+  q.K = mode == 0 ? D.smax : D.bmax + D.smax;
+  const int nrows = mode == 0 ? D.bmax : D.smax;
+  q.tr = nrows <= 16 ? 16 : 32;
+  q.ntile = std::max(1, (nrows + q.tr - 1) / q.tr);
+  const long base = (long)D.nf * q.ntile * ng;
+  q.nsplit = 1;
+  if (nrows > 0)
+    while (base * q.nsplit < 2 * 152 && q.K / (q.nsplit * 2) >= 64) q.nsplit *= 2;
+  q.ksz = q.K > 0 ? (q.K + q.nsplit - 1) / q.nsplit : 0;
+  return q;
+}
+
 static bool ensure_buffers(NdPlan* p, int elem_bytes) {
   if (p->F && p->F_bytes == elem_bytes) return false;
   if (p->F) { cudaFree(p->F); p->F = nullptr; }
@@ -1224,6 +1249,23 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes) {
   }
   int nf_max = 1;
   for (const LevelDev& D : p->lev) nf_max = std::max(nf_max, D.nf);
+  // solve partial sums: the largest split level, for any number of right-hand-side groups
+  size_t part = 1, items = 1;
+  for (const LevelDev& D : p->lev)
+    for (int mode = 0; mode < 2; ++mode)
+      for (int ng = 1; ng <= SOLVE_CHUNK / 16; ++ng) {
+        const SweepPlan q = sweep_plan(D, mode, ng);
+        items = std::max(items, (size_t)D.nf * q.ntile * ng);
+        if (q.nsplit > 1) part = std::max(part, (size_t)D.nf * q.ntile * q.nsplit * q.tr * 16 * ng);
+      }
+  if (p->part) { cudaFree(p->part); p->part = nullptr; }
+  if (p->cnt) { cudaFree(p->cnt); p->cnt = nullptr; }
+  if (cudaMalloc(&p->part, part * elem_bytes) != cudaSuccess || cudaMalloc(&p->cnt, items * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    LS_FAIL(ENOMEM_, "cudaMalloc failed for the solve partial sums");
+  }
+  LS_CUDA(cudaMemset(p->cnt, 0, items * sizeof(unsigned)));
+  p->part_elems = part;
   if (p->swp) { cudaFree(p->swp); p->swp = nullptr; }
   if (cudaMalloc(&p->swp, (size_t)nf_max * SWP_STRIDE * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -1438,7 +1480,13 @@ template <typename C> struct SweepK {
   const int *own, *ring, *fsrc;
   int nf, smax, bmax, fmax, ncols;
   int nf_c, fmax_c;  // child level: fronts and front size (group stride of Wc)
+  int ntile;         // row tiles per front
+  int nsplit;        // column ranges per row tile; their partial sums are added in range
+                     // order by the CTA that finishes last
+  int ksz;           // columns per range
   int kv;            // items of the vector operand held in shared memory at once
+  C* part;           // nsplit > 1: partial sums [item][nsplit][tile rows x RC]
+  unsigned* cnt;     // nsplit > 1: CTAs finished per item (the last one resets it)
   long N;
 };
 
@@ -1448,93 +1496,118 @@ constexpr size_t SWEEP_VS_MAX = 64 * 1024;
 constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
 
 struct SweepShape {
-  int K, kv, kg, nbuf, kc0;
+  int kv, kg, nbuf, kc0;
   size_t region0, smem;  // region0 in elements
 };
 
-template <typename C, int RC, int MODE> __host__ __device__ SweepShape sweep_shape(int smax, int bmax, int kg_in) {
+// shared-memory layout of one CTA working on a column range of ksz columns; TR rows per
+// tile (32: one row per lane, all RC right-hand sides per thread; 16: lanes 0-15 and 16-31
+// take the two halves of the right-hand sides)
+template <typename C, int RC, int TR, int MODE> __host__ __device__ SweepShape sweep_shape(int ksz, int kg_in) {
   SweepShape s;
   constexpr int KA = sweep_ka<C>();
-  s.K = MODE == 0 ? smax : bmax + smax;
-  s.kc0 = s.K < KA ? s.K : KA;
-  s.nbuf = s.K > KA ? 2 : 1;
-  s.kv = (size_t)s.K * RC * sizeof(C) <= SWEEP_VS_MAX ? s.K : KA;
+  constexpr int RCT = RC * TR / 32;
+  s.kc0 = ksz < KA ? ksz : KA;
+  s.nbuf = ksz > KA ? 2 : 1;
+  s.kv = (size_t)ksz * RC * sizeof(C) <= SWEEP_VS_MAX ? ksz : KA;
   if (kg_in > 0) s.kg = kg_in;
-  else s.kg = s.K > KA ? 8 : (s.K / 16 < 1 ? 1 : (s.K / 16 > 8 ? 8 : s.K / 16));
-  const size_t a = (size_t)s.nbuf * s.kc0 * 32 + (size_t)s.kv * RC;
-  const size_t red = (size_t)s.kg * 32 * (RC + 1);
+  else s.kg = ksz > KA ? 8 : (ksz / 16 < 1 ? 1 : (ksz / 16 > 8 ? 8 : ksz / 16));
+  const size_t a = (size_t)s.nbuf * s.kc0 * TR + (size_t)s.kv * RC;
+  const size_t red = (size_t)s.kg * 32 * (RCT + 1);
   s.region0 = a > red ? a : red;
-  const size_t wt = MODE == 0 ? 32 * RC : 0;
-  const size_t idx = MODE == 0 ? 3 * (size_t)s.kv + 64 : (size_t)s.kv + 32;
+  const size_t wt = MODE == 0 ? (size_t)TR * RC : 0;
+  const size_t idx = MODE == 0 ? 3 * (size_t)s.kv + 2 * TR : (size_t)s.kv + TR;
   s.smem = (s.region0 + wt) * sizeof(C) + idx * sizeof(int);
   return s;
 }
 
 // vector operand items [c0, c0 + kc) of one front into dst (item-major, RC per item);
-// forward: w_own (also stored to W by the first row tile); backward: [x_ring | w_own]
+// forward: w_own (also stored to W by the first row tile); backward: [x_ring | w_own].
+// ixs: the staged indices of these items, or null (read from the index arrays)
 template <typename C, int RC, int MODE>
 __device__ __forceinline__ void sweep_gather(const SweepK<C>& S, int z, int g, int c0, int kc, const int* ixs,
                                              C* dst, bool write_own) {
   using P = typename Piece<C>::T;
   constexpr int NV = RC * (int)sizeof(C) / 16;
+  constexpr int B = 4;  // pieces per thread with their loads in flight together
   const size_t wrow = (size_t)g * S.nf * S.fmax + (size_t)z * S.fmax;
-  for (int u = threadIdx.x; u < kc * NV; u += blockDim.x) {
-    const int ci = u / NV, v = u % NV, c = c0 + ci;
-    P s = pzero<P>();
-    if (MODE == 0) {
-      int pt, s0, s1;
-      if (ixs) {
-        pt = ixs[3 * ci];
-        s0 = ixs[3 * ci + 1];
-        s1 = ixs[3 * ci + 2];
+  const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+  const int tot = kc * NV;
+  for (int base = threadIdx.x; base < tot; base += blockDim.x * B) {
+    P s[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int u = base + q * blockDim.x;
+      s[q] = pzero<P>();
+      if (u >= tot) continue;
+      const int ci = u / NV, v = u % NV, c = c0 + ci;
+      if (MODE == 0) {
+        int pt, s0, s1;
+        if (ixs) {
+          pt = ixs[3 * ci];
+          s0 = ixs[3 * ci + 1];
+          s1 = ixs[3 * ci + 2];
+        } else {
+          pt = __ldg(S.own + (size_t)z * S.smax + c);
+          s0 = __ldg(S.fsrc + ((size_t)z * S.fmax + c) * 2);
+          s1 = __ldg(S.fsrc + ((size_t)z * S.fmax + c) * 2 + 1);
+        }
+        P a = pzero<P>(), b = pzero<P>(), r = pzero<P>();
+        if (pt >= 0) r = __ldcg(reinterpret_cast<const P*>(S.T + ((size_t)g * S.N + pt) * RC) + v);
+        if (s0 >= 0) a = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s0) * RC) + v);
+        if (s1 >= 0) b = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s1) * RC) + v);
+        s[q] = padd(padd(r, a), b);
+      } else if (c < S.bmax) {
+        const int pt = ixs ? ixs[ci] : __ldg(S.ring + (size_t)z * S.bmax + c);
+        if (pt >= 0) s[q] = __ldcg(reinterpret_cast<const P*>(S.T + ((size_t)g * S.N + pt) * RC) + v);
       } else {
-        pt = __ldg(S.own + (size_t)z * S.smax + c);
-        s0 = __ldg(S.fsrc + ((size_t)z * S.fmax + c) * 2);
-        s1 = __ldg(S.fsrc + ((size_t)z * S.fmax + c) * 2 + 1);
+        s[q] = __ldcg(reinterpret_cast<const P*>(S.W + (wrow + c - S.bmax) * RC) + v);
       }
-      const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
-      P a = pzero<P>(), b = pzero<P>();
-      if (pt >= 0) s = __ldcg(reinterpret_cast<const P*>(S.T + ((size_t)g * S.N + pt) * RC) + v);
-      if (s0 >= 0) a = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s0) * RC) + v);
-      if (s1 >= 0) b = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s1) * RC) + v);
-      s = padd(padd(s, a), b);
-      if (write_own) reinterpret_cast<P*>(S.W + (wrow + c) * RC)[v] = s;
-    } else if (c < S.bmax) {
-      const int pt = ixs ? ixs[ci] : __ldg(S.ring + (size_t)z * S.bmax + c);
-      if (pt >= 0) s = __ldcg(reinterpret_cast<const P*>(S.T + ((size_t)g * S.N + pt) * RC) + v);
-    } else {
-      s = __ldcg(reinterpret_cast<const P*>(S.W + (wrow + c - S.bmax) * RC) + v);
     }
-    reinterpret_cast<P*>(dst)[u] = s;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int u = base + q * blockDim.x;
+      if (u >= tot) continue;
+      reinterpret_cast<P*>(dst)[u] = s[q];
+      if (MODE == 0 && write_own) reinterpret_cast<P*>(S.W + (wrow + c0 + u / NV) * RC)[u % NV] = s[q];
+    }
   }
 }
 
-// One level of either sweep.  grid (fronts, row tiles of 32, groups of RC right-hand
-// sides); lane = row of the tile, the kg warps split the columns of each chunk and add
-// their partial sums in a fixed order.  Forward rows are the ring rows of Y (the identity
-// columns of the augmented front); backward rows are the own rows of [H | F11^{-1}].
-template <typename C, int RC, int MODE> __global__ void __launch_bounds__(256) k_sweep(SweepK<C> S) {
+// One level of either sweep.  grid (fronts, row tiles x column ranges, groups of RC
+// right-hand sides); the kg warps split the columns of each chunk and add their partial
+// sums in a fixed order.  Forward rows are the ring rows of Y (the identity columns of the
+// augmented front); backward rows are the own rows of [H | F11^{-1}].
+template <typename C, int RC, int TR, int MODE> __global__ void __launch_bounds__(256) k_sweep(SweepK<C> S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int last_s;
   constexpr int KA = sweep_ka<C>();
-  const int z = blockIdx.x, g = blockIdx.z, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int kg = blockDim.x >> 5, NT = blockDim.x;
+  constexpr int RCT = RC * TR / 32;
+  const int z = blockIdx.x, g = blockIdx.z;
+  const int tile = blockIdx.y / S.nsplit, sp = blockIdx.y - tile * S.nsplit;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, kg = blockDim.x >> 5, NT = blockDim.x;
+  const int row = TR == 32 ? lane : (lane & 15);
+  const int j0 = TR == 32 ? 0 : (lane >> 4) * RCT;
   const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
-  const SweepShape sh = sweep_shape<C, RC, MODE>(smax, bmax, kg);
-  const int K = sh.K, kv = S.kv, t0 = blockIdx.y * 32;
+  const int K = MODE == 0 ? smax : bmax + smax;
+  const int kb = sp * S.ksz, ke = min(K, kb + S.ksz), Kr = ke - kb;
+  const SweepShape sh = sweep_shape<C, RC, TR, MODE>(S.ksz, kg);
+  const int kv = S.kv, t0 = tile * TR;
   const int nrows = MODE == 0 ? bmax : smax;
-  const int rvalid = min(32, nrows - t0);
-  C* as = reinterpret_cast<C*>(smem_raw);         // [nbuf][kc0][32] factor tile chunks
-  C* vs = as + (size_t)sh.nbuf * sh.kc0 * 32;     // [kv][RC] vector operand
-  C* wt = reinterpret_cast<C*>(smem_raw) + sh.region0;  // forward: [32][RC] ring-tile updates
-  int* ixs = reinterpret_cast<int*>(wt + (MODE == 0 ? 32 * RC : 0));
+  const int rvalid = min(TR, nrows - t0);
+  const int kvr = min(kv, Kr);  // items gathered up front
+  C* as = reinterpret_cast<C*>(smem_raw);             // [nbuf][kc0][TR] factor tile chunks
+  C* vs = as + (size_t)sh.nbuf * sh.kc0 * TR;         // [kv][RC] vector operand
+  C* wt = reinterpret_cast<C*>(smem_raw) + sh.region0;  // forward: [TR][RC] ring-tile updates
+  int* ixs = reinterpret_cast<int*>(wt + (MODE == 0 ? TR * RC : 0));
   const C* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
                (MODE == 0 ? smax : 0) + t0;
   auto load_chunk = [&](int ch) {
-    const int cb = ch * KA, kc = min(KA, K - cb);
-    C* dst = as + (size_t)(ch % sh.nbuf) * sh.kc0 * 32;
+    const int cb = kb + ch * KA, kc = min(KA, ke - cb);
+    C* dst = as + (size_t)(ch % sh.nbuf) * sh.kc0 * TR;
     if (rvalid > 0)
-      for (int e = threadIdx.x; e < kc * 32; e += NT) {
-        const int c = e >> 5, i = e & 31;
+      for (int e = threadIdx.x; e < kc * TR; e += NT) {
+        const int c = e / TR, i = e - c * TR;
         cp_async_elem<sizeof(C)>(dst + e, i < rvalid ? A + (size_t)(cb + c) * fmax + i : A, i < rvalid);
       }
     cp_async_commit();
@@ -1542,75 +1615,93 @@ template <typename C, int RC, int MODE> __global__ void __launch_bounds__(256) k
 
   // ---- prologue: static data only
   if (MODE == 0) {
-    for (int c = threadIdx.x; c < kv; c += NT) {
-      ixs[3 * c] = __ldg(S.own + (size_t)z * smax + c);
-      ixs[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
-      ixs[3 * c + 2] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
+    for (int c = threadIdx.x; c < kvr; c += NT) {
+      const int col = kb + c;
+      ixs[3 * c] = __ldg(S.own + (size_t)z * smax + col);
+      ixs[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + col) * 2);
+      ixs[3 * c + 2] = __ldg(S.fsrc + ((size_t)z * fmax + col) * 2 + 1);
     }
-    for (int i = threadIdx.x; i < 32; i += NT) {
+    for (int i = threadIdx.x; i < TR; i += NT) {
       const int p = smax + t0 + i;
-      ixs[3 * kv + 2 * i] = i < rvalid ? __ldg(S.fsrc + ((size_t)z * fmax + p) * 2) : -1;
-      ixs[3 * kv + 2 * i + 1] = i < rvalid ? __ldg(S.fsrc + ((size_t)z * fmax + p) * 2 + 1) : -1;
+      const bool on = sp == 0 && i < rvalid;
+      ixs[3 * kv + 2 * i] = on ? __ldg(S.fsrc + ((size_t)z * fmax + p) * 2) : -1;
+      ixs[3 * kv + 2 * i + 1] = on ? __ldg(S.fsrc + ((size_t)z * fmax + p) * 2 + 1) : -1;
     }
   } else {
-    for (int c = threadIdx.x; c < kv; c += NT) ixs[c] = c < bmax ? __ldg(S.ring + (size_t)z * bmax + c) : -1;
-    for (int i = threadIdx.x; i < 32; i += NT) ixs[kv + i] = i < rvalid ? __ldg(S.own + (size_t)z * smax + t0 + i) : -1;
+    for (int c = threadIdx.x; c < kvr; c += NT) {
+      const int col = kb + c;
+      ixs[c] = col < bmax ? __ldg(S.ring + (size_t)z * bmax + col) : -1;
+    }
+    for (int i = threadIdx.x; i < TR; i += NT) ixs[kv + i] = i < rvalid ? __ldg(S.own + (size_t)z * smax + t0 + i) : -1;
   }
-  const int nch = (K + KA - 1) / KA;
-  if (K > 0) load_chunk(0);
+  const int nch = (Kr + KA - 1) / KA;
+  if (Kr > 0) load_chunk(0);
 
   // ---- after the previous level
   pdl_wait();
   pdl_trigger();
   __syncthreads();
-  const bool write_own = MODE == 0 && blockIdx.y == 0;
-  if (K > 0) sweep_gather<C, RC, MODE>(S, z, g, 0, kv, ixs, vs, write_own);
-  if (MODE == 0) {
+  const bool write_own = MODE == 0 && tile == 0;
+  if (Kr > 0) sweep_gather<C, RC, MODE>(S, z, g, kb, kvr, ixs, vs, write_own);
+  if (MODE == 0 && sp == 0) {
     using P = typename Piece<C>::T;
     constexpr int NV = RC * (int)sizeof(C) / 16;
     const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
-    for (int u = threadIdx.x; u < 32 * NV; u += NT) {
-      const int i = u / NV, v = u % NV;
-      const int s0 = ixs[3 * kv + 2 * i], s1 = ixs[3 * kv + 2 * i + 1];
-      P a = pzero<P>(), b = pzero<P>();
-      if (s0 >= 0) a = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s0) * RC) + v);
-      if (s1 >= 0) b = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s1) * RC) + v);
-      reinterpret_cast<P*>(wt)[u] = padd(a, b);
+    constexpr int B = 4;
+    for (int base = threadIdx.x; base < TR * NV; base += NT * B) {
+      P sv[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int u = base + q * NT;
+        sv[q] = pzero<P>();
+        if (u >= TR * NV) continue;
+        const int i = u / NV, v = u % NV;
+        const int s0 = ixs[3 * kv + 2 * i], s1 = ixs[3 * kv + 2 * i + 1];
+        P a = pzero<P>(), b = pzero<P>();
+        if (s0 >= 0) a = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s0) * RC) + v);
+        if (s1 >= 0) b = __ldcg(reinterpret_cast<const P*>(S.Wc + (cg + s1) * RC) + v);
+        sv[q] = padd(a, b);
+      }
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int u = base + q * NT;
+        if (u < TR * NV) reinterpret_cast<P*>(wt)[u] = sv[q];
+      }
     }
   }
 
-  C acc[RC];
+  C acc[RCT];
 #pragma unroll
-  for (int j = 0; j < RC; ++j) acc[j] = czero<C>();
+  for (int j = 0; j < RCT; ++j) acc[j] = czero<C>();
   for (int ch = 0; ch < nch; ++ch) {
-    const int cb = ch * KA, kc = min(KA, K - cb);
+    const int cb = kb + ch * KA, kc = min(KA, ke - cb);
     if (ch + 1 < nch) {
       load_chunk(ch + 1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
-    // the staged vector operand covers [vb, vb + kv); when it is smaller than K it is
-    // refilled chunk by chunk (kv == KA then)
-    const int vb = kv >= K ? 0 : cb;
-    if (kv < K && ch > 0) {
+    // the staged vector operand covers [vb, vb + kv); when it is smaller than the range it
+    // is refilled chunk by chunk (kv == KA then)
+    const int vb = kv >= Kr ? kb : cb;
+    if (kv < Kr && ch > 0) {
       __syncthreads();
       sweep_gather<C, RC, MODE>(S, z, g, cb, kc, nullptr, vs, write_own);
     }
     __syncthreads();
     if (rvalid > 0) {
-      const C* ab = as + (size_t)(ch % sh.nbuf) * sh.kc0 * 32;
+      const C* ab = as + (size_t)(ch % sh.nbuf) * sh.kc0 * TR;
       const int per = (kc + kg - 1) / kg;
       const int k0 = w * per, k1 = min(kc, k0 + per);
       for (int k = k0; k < k1; ++k) {
-        C a = ab[k * 32 + lane];
+        C a = ab[k * TR + row];
         if (MODE == 1 && cb + k < bmax) {
           a.x = -a.x;
           a.y = -a.y;
         }
-        const C* vv = vs + (size_t)(cb + k - vb) * RC;
+        const C* vv = vs + (size_t)(cb + k - vb) * RC + j0;
 #pragma unroll
-        for (int j = 0; j < RC; ++j) acc[j] = cfma(acc[j], a, vv[j]);
+        for (int j = 0; j < RCT; ++j) acc[j] = cfma(acc[j], a, vv[j]);
       }
     }
     __syncthreads();
@@ -1618,20 +1709,42 @@ template <typename C, int RC, int MODE> __global__ void __launch_bounds__(256) k
   if (rvalid <= 0) return;
   C* red = reinterpret_cast<C*>(smem_raw);
 #pragma unroll
-  for (int j = 0; j < RC; ++j) red[((size_t)w * 32 + lane) * (RC + 1) + j] = acc[j];
+  for (int j = 0; j < RCT; ++j) red[((size_t)w * 32 + lane) * (RCT + 1) + j] = acc[j];
   __syncthreads();
-  for (int o = threadIdx.x; o < 32 * RC; o += NT) {
-    const int i = o / RC, j = o % RC;
-    if (i >= rvalid) continue;
-    C s = MODE == 0 ? wt[i * RC + j] : czero<C>();
-    for (int q = 0; q < kg; ++q) s = cadd(s, red[((size_t)q * 32 + i) * (RC + 1) + j]);
+  const size_t item = ((size_t)g * S.nf + z) * S.ntile + tile;
+  auto store = [&](int i, int j, C s) {
     if (MODE == 0) {
       S.W[((size_t)g * S.nf * fmax + (size_t)z * fmax + smax + t0 + i) * RC + j] = s;
     } else {
       const int pt = ixs[kv + i];
       if (pt >= 0) S.T[((size_t)g * S.N + pt) * RC + j] = s;
     }
+  };
+  for (int o = threadIdx.x; o < TR * RC; o += NT) {
+    const int i = o / RC, j = o % RC;
+    if (i >= rvalid) continue;
+    const int ln = TR == 32 ? i : i + 16 * (j / RCT), sl = TR == 32 ? j : j % RCT;
+    C s = MODE == 0 && sp == 0 ? wt[i * RC + j] : czero<C>();
+    for (int q = 0; q < kg; ++q) s = cadd(s, red[((size_t)q * 32 + ln) * (RCT + 1) + sl]);
+    if (S.nsplit == 1) store(i, j, s);
+    else S.part[(item * S.nsplit + sp) * TR * RC + o] = s;
   }
+  if (S.nsplit == 1) return;
+  // the CTA that completes the item last adds the ranges' partial sums in range order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_s = atomicAdd(S.cnt + item, 1u) == (unsigned)(S.nsplit - 1);
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  for (int o = threadIdx.x; o < TR * RC; o += NT) {
+    const int i = o / RC, j = o % RC;
+    if (i >= rvalid) continue;
+    C s = czero<C>();
+    for (int q = 0; q < S.nsplit; ++q) s = cadd(s, __ldcg(S.part + (item * S.nsplit + q) * TR * RC + o));
+    store(i, j, s);
+  }
+  if (threadIdx.x == 0) S.cnt[item] = 0u;
 }
 
 // r[rhs][N] -> T[group][N][RC] (right-hand sides past nr are zero)
@@ -1694,15 +1807,16 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
   LS_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
 }
 
-template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int l, C* T, int ng, cudaStream_t st) {
+template <typename C, int RC, int TR, int MODE>
+static void launch_sweep_tr(NdPlan* p, int l, C* T, int ng, const SweepPlan& q, cudaStream_t st) {
   const LevelDev& D = p->lev[l];
   const int depth = (int)p->lev.size();
-  const SweepShape sh = sweep_shape<C, RC, MODE>(D.smax, D.bmax, 0);
-  if (sh.K <= 0 && MODE == 1) return;
+  const SweepShape sh = sweep_shape<C, RC, TR, MODE>(q.ksz, 0);
   if (sh.smem > SWEEP_SMEM_MAX) LS_FAIL(EINVAL_, "front too large for the solve kernels (%zu bytes of shared memory)", sh.smem);
   static bool attr = false;
   if (!attr) {
-    LS_CUDA(cudaFuncSetAttribute(k_sweep<C, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_MAX));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep<C, RC, TR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SWEEP_SMEM_MAX));
     attr = true;
   }
   SweepK<C> S;
@@ -1721,13 +1835,26 @@ template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int 
   S.ncols = D.ncols;
   S.nf_c = has_child ? p->lev[l + 1].nf : 0;
   S.fmax_c = has_child ? p->lev[l + 1].fmax : 0;
+  S.ntile = q.ntile;
+  S.nsplit = q.nsplit;
+  S.ksz = q.ksz;
   S.kv = sh.kv;
+  S.part = reinterpret_cast<C*>(p->part);
+  S.cnt = p->cnt;
   S.N = p->N;
-  const int nrows = MODE == 0 ? D.bmax : D.smax;
-  const dim3 grid(D.nf, std::max(1, (nrows + 31) / 32), ng);
+  const dim3 grid(D.nf, q.ntile * q.nsplit, ng);
   const bool f32 = sizeof(C) == 8;
   LS_LAUNCH(MODE == 0 ? (f32 ? "nd_fwd_c64" : "nd_fwd_c128") : (f32 ? "nd_bwd_c64" : "nd_bwd_c128"), st,
-            launch_pdl(k_sweep<C, RC, MODE>, grid, dim3(32 * sh.kg), sh.smem, st, S));
+            launch_pdl(k_sweep<C, RC, TR, MODE>, grid, dim3(32 * sh.kg), sh.smem, st, S));
+}
+
+template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int l, C* T, int ng, cudaStream_t st) {
+  const SweepPlan q = sweep_plan(p->lev[l], MODE, ng);
+  if (q.K <= 0) return;
+  if (q.nsplit > 1 && (size_t)p->lev[l].nf * q.ntile * q.nsplit * q.tr * RC * ng > p->part_elems)
+    LS_FAIL(EINVAL_, "solve partial-sum buffer too small");
+  if (q.tr == 16) launch_sweep_tr<C, RC, 16, MODE>(p, l, T, ng, q, st);
+  else launch_sweep_tr<C, RC, 32, MODE>(p, l, T, ng, q, st);
 }
 
 template <typename C, int RC>
