@@ -22,6 +22,7 @@
 #include <tuple>
 #include <vector>
 
+#include "alloc.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "krylov.h"
@@ -103,12 +104,7 @@ bool is_device_ptr(const void* p) {
 }
 
 template <typename T> T* dalloc(size_t count) {
-  void* p = nullptr;
-  if (cudaMalloc(&p, std::max<size_t>(1, count) * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    LS_FAIL(ls::ENOMEM_, "cudaMalloc of %zu bytes failed", count * sizeof(T));
-  }
-  return (T*)p;
+  return (T*)ls::dev_alloc(std::max<size_t>(1, count) * sizeof(T));
 }
 
 template <typename T> T* buf(ls_ctx* c, const std::string& name, size_t count) {
@@ -117,7 +113,7 @@ template <typename T> T* buf(ls_ctx* c, const std::string& name, size_t count) {
   if (b.bytes < need) {
     if (b.p) {
       LS_CUDA(cudaStreamSynchronize(c->st));
-      cudaFree(b.p);
+      ls::dev_free(b.p);
     }
     b.p = nullptr;
     b.bytes = 0;
@@ -190,8 +186,8 @@ void ensure_basis(ls_ctx* c, int nvec, int nrhs, int z_elem) {
   const long need = (long)nrhs * c->N;
   if (need > c->basis_cap || z_elem != c->Z_elem) {
     LS_CUDA(cudaStreamSynchronize(c->st));
-    for (auto p : c->V) cudaFree(p);
-    for (auto p : c->Z) cudaFree(p);
+    for (auto p : c->V) ls::dev_free(p);
+    for (auto p : c->Z) ls::dev_free(p);
     c->V.clear();
     c->Z.clear();
     c->basis_cap = need;
@@ -209,8 +205,8 @@ void ensure_basis(ls_ctx* c, int nvec, int nrhs, int z_elem) {
   if (grew || !c->dV) {
     ++c->gen;
     LS_CUDA(cudaStreamSynchronize(c->st));
-    if (c->dV) cudaFree(c->dV);
-    if (c->dZ) cudaFree(c->dZ);
+    if (c->dV) ls::dev_free(c->dV);
+    if (c->dZ) ls::dev_free(c->dZ);
     c->dV = dalloc<double2*>(c->V.size());
     c->dZ = dalloc<void*>(c->Z.size());
     LS_CUDA(cudaMemcpy(c->dV, c->V.data(), c->V.size() * sizeof(double2*), cudaMemcpyHostToDevice));
@@ -522,10 +518,10 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
         ls::build_symbol(c->plan, c->ktq, c->sym64, c->sym32, work, c->st);
         LS_CUDA(cudaStreamSynchronize(c->st));
       } catch (...) {
-        cudaFree(work);
+        ls::dev_free(work);
         throw;
       }
-      cudaFree(work);
+      ls::dev_free(work);
     }
     c->plan.sym32 = c->sym32;
     c->plan.sym64 = c->sym64;
@@ -592,7 +588,7 @@ ls_status ls_factor(ls_ctx* c) {
     check_ctx(c);
     c->factored = false;
     const bool mixed = c->prec == LS_PREC_MIXED;
-    if (mixed ? ls::nd_prepare<float2>(c->nd) : ls::nd_prepare<double2>(c->nd)) ++c->gen;
+    if (mixed ? ls::nd_prepare<float2>(c->nd, c->st) : ls::nd_prepare<double2>(c->nd, c->st)) ++c->gen;
     run_graph(c, "factor", [&] {
       if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
       else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
@@ -667,11 +663,11 @@ void ls_free(ls_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : {(void*)c->w2m64, (void*)c->w2m32, (void*)c->tw32, (void*)c->tw64, (void*)c->ktq, (void*)c->sym32,
                   (void*)c->sym64, (void*)c->ffbuf, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ})
-    if (p) cudaFree(p);
-  for (auto p : c->V) cudaFree(p);
-  for (auto p : c->Z) cudaFree(p);
+    if (p) ls::dev_free(p);
+  for (auto p : c->V) ls::dev_free(p);
+  for (auto p : c->Z) ls::dev_free(p);
   for (auto& kv : c->bufs)
-    if (kv.second.p) cudaFree(kv.second.p);
+    if (kv.second.p) ls::dev_free(kv.second.p);
   for (auto& kv : c->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->nd) ls::nd_free(c->nd);

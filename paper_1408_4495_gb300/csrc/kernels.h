@@ -105,7 +105,7 @@ NdInfo nd_info(const NdPlan* p);
 // only, capturable in a CUDA graph) + nd_factor_check (reads the singular-pivot flag).
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
-template <typename C> bool nd_prepare(NdPlan* p);
+template <typename C> bool nd_prepare(NdPlan* p, cudaStream_t st);
 template <typename C>
 void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
 void nd_factor_check(NdPlan* p, cudaStream_t st);

@@ -35,6 +35,7 @@
 #include <mutex>
 #include <vector>
 
+#include "alloc.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "prof.h"
@@ -422,10 +423,7 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
     p->F_elems = H->F_elems;
     p->W_elems = H->W_elems;
     p->info = H->info;
-    if (cudaMalloc(&p->blob, H->blob.size()) != cudaSuccess) {
-      cudaGetLastError();
-      LS_FAIL(ENOMEM_, "cudaMalloc(%zu) failed for the ND plan", H->blob.size());
-    }
+    p->blob = dev_alloc(H->blob.size());
     LS_CUDA(cudaMemcpyAsync(p->blob, H->blob.data(), H->blob.size(), cudaMemcpyHostToDevice, st));
     unsigned char* b = static_cast<unsigned char*>(p->blob);
     for (size_t l = 0; l < p->lev.size(); ++l) {
@@ -455,13 +453,13 @@ NdPlan* nd_build(int d, int n, cudaStream_t st) {
 
 void nd_free(NdPlan* p) {
   if (!p) return;
-  if (p->blob) cudaFree(p->blob);
-  if (p->F) cudaFree(p->F);
-  if (p->W) cudaFree(p->W);
-  if (p->T) cudaFree(p->T);
-  if (p->swp) cudaFree(p->swp);
-  if (p->part) cudaFree(p->part);
-  if (p->cnt) cudaFree(p->cnt);
+  if (p->blob) dev_free(p->blob);
+  if (p->F) dev_free(p->F);
+  if (p->W) dev_free(p->W);
+  if (p->T) dev_free(p->T);
+  if (p->swp) dev_free(p->swp);
+  if (p->part) dev_free(p->part);
+  if (p->cnt) dev_free(p->cnt);
   delete p;
 }
 
@@ -1230,23 +1228,14 @@ static SweepPlan sweep_plan(const LevelDev& D, int mode, int ng) {
   return q;
 }
 
-static bool ensure_buffers(NdPlan* p, int elem_bytes) {
+static bool ensure_buffers(NdPlan* p, int elem_bytes, cudaStream_t st) {
   if (p->F && p->F_bytes == elem_bytes) return false;
-  if (p->F) { cudaFree(p->F); p->F = nullptr; }
-  if (p->W) { cudaFree(p->W); p->W = nullptr; }
-  if (p->T) { cudaFree(p->T); p->T = nullptr; }
-  if (cudaMalloc(&p->F, p->F_elems * elem_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the fronts failed", p->F_elems * elem_bytes);
-  }
-  if (cudaMalloc(&p->W, std::max<size_t>(1, p->W_elems) * elem_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the front vectors failed", p->W_elems * elem_bytes);
-  }
-  if (cudaMalloc(&p->T, (size_t)p->N * SOLVE_CHUNK * elem_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    LS_FAIL(ENOMEM_, "cudaMalloc of %zu bytes for the solve items failed", (size_t)p->N * SOLVE_CHUNK * elem_bytes);
-  }
+  if (p->F) { dev_free(p->F); p->F = nullptr; }
+  if (p->W) { dev_free(p->W); p->W = nullptr; }
+  if (p->T) { dev_free(p->T); p->T = nullptr; }
+  p->F = dev_alloc(p->F_elems * elem_bytes);
+  p->W = dev_alloc(std::max<size_t>(1, p->W_elems) * elem_bytes);
+  p->T = dev_alloc((size_t)p->N * SOLVE_CHUNK * elem_bytes);
   int nf_max = 1;
   for (const LevelDev& D : p->lev) nf_max = std::max(nf_max, D.nf);
   // solve partial sums: the largest split level, for any number of right-hand-side groups
@@ -1258,19 +1247,14 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes) {
         items = std::max(items, (size_t)D.nf * q.ntile * ng);
         if (q.nsplit > 1) part = std::max(part, (size_t)D.nf * q.ntile * q.nsplit * q.tr * 16 * ng);
       }
-  if (p->part) { cudaFree(p->part); p->part = nullptr; }
-  if (p->cnt) { cudaFree(p->cnt); p->cnt = nullptr; }
-  if (cudaMalloc(&p->part, part * elem_bytes) != cudaSuccess || cudaMalloc(&p->cnt, items * sizeof(unsigned)) != cudaSuccess) {
-    cudaGetLastError();
-    LS_FAIL(ENOMEM_, "cudaMalloc failed for the solve partial sums");
-  }
-  LS_CUDA(cudaMemset(p->cnt, 0, items * sizeof(unsigned)));
+  if (p->part) { dev_free(p->part); p->part = nullptr; }
+  if (p->cnt) { dev_free(p->cnt); p->cnt = nullptr; }
+  p->part = dev_alloc(part * elem_bytes);
+  p->cnt = static_cast<unsigned*>(dev_alloc(items * sizeof(unsigned)));
+  LS_CUDA(cudaMemsetAsync(p->cnt, 0, items * sizeof(unsigned), st));
   p->part_elems = part;
-  if (p->swp) { cudaFree(p->swp); p->swp = nullptr; }
-  if (cudaMalloc(&p->swp, (size_t)nf_max * SWP_STRIDE * sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    LS_FAIL(ENOMEM_, "cudaMalloc failed for the panel permutations");
-  }
+  if (p->swp) { dev_free(p->swp); p->swp = nullptr; }
+  p->swp = static_cast<int*>(dev_alloc((size_t)nf_max * SWP_STRIDE * sizeof(int)));
   p->F_bytes = p->W_bytes = elem_bytes;
   return true;
 }
@@ -1294,7 +1278,7 @@ template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1
             k_gemm<C><<<dim3(L.nf, nr * nc), 256, 0, st>>>(L, r0, r1, c0, c1, k0, k1));
 }
 
-template <typename C> bool nd_prepare(NdPlan* p) { return ensure_buffers(p, sizeof(C)); }
+template <typename C> bool nd_prepare(NdPlan* p, cudaStream_t st) { return ensure_buffers(p, sizeof(C), st); }
 
 // own rows per lane of the register sweeps (32 * this many own rows at most)
 template <typename C> constexpr int reg_rpl_max() { return sizeof(C) == 8 ? 16 : 8; }
@@ -1331,7 +1315,7 @@ template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* s
 
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
-  nd_prepare<C>(p);
+  nd_prepare<C>(p, st);
   nd_factor_launch<C>(p, alpha64, cint64, w2m64, st);
   nd_factor_check(p, st);
 }
@@ -1893,8 +1877,8 @@ template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaS
 
 template void nd_factor<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template void nd_factor<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
-template bool nd_prepare<float2>(NdPlan*);
-template bool nd_prepare<double2>(NdPlan*);
+template bool nd_prepare<float2>(NdPlan*, cudaStream_t);
+template bool nd_prepare<double2>(NdPlan*, cudaStream_t);
 template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template void nd_solve<float2>(NdPlan*, int, const float2*, float2*, cudaStream_t);
