@@ -183,6 +183,9 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+MODELED = ("fft_row_fwd", "fft_col_sym", "fft_row_inv", "stencil", "nd_fwd", "nd_bwd")
+
+
 def algorithmic_bytes(cls, w, nd, counts, steps):
     """Average bytes one launch of a kernel class must move (reads + writes), from the pass
     design: FP32 complex = 8 B, FP64 complex = 16 B, lines of n (grid) or L = 2n (padded).
@@ -209,7 +212,10 @@ def algorithmic_bytes(cls, w, nd, counts, steps):
 # ncu DRAM traffic per launch of a kernel class, valid while the class's source file is
 # unchanged (sha1 of the file at capture time); see profiles/.
 TRAFFIC = {
-    "nd_fwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": None, "bytes": None},
+    "nd_fwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "258dc65474791ca701789d6b24e9ceb8a9ab4e8b",
+                   "bytes": 5847414},
+    "nd_bwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "258dc65474791ca701789d6b24e9ceb8a9ab4e8b",
+                   "bytes": 8078789},
 }
 
 
@@ -305,7 +311,9 @@ def run_gpu(args):
     by_cls = rprof.get("ms_by_class", {})
     tot_cls = sum(by_cls.values()) or 1.0
     shares = {k: round(v / tot_cls, 4) for k, v in sorted(by_cls.items(), key=lambda x: -x[1])}
-    cls = args.profile_class
+    # the kernel class with the largest share of device time among those with a byte model
+    cls = args.profile_class or max((k for k in by_cls if k.startswith(MODELED)), key=lambda k: by_cls[k],
+                                    default="nd_fwd_c64")
     if by_cls.get(cls, 0) > 0 and rprof["counts"].get(cls, 0) > 0:
         nlaunch = rprof["counts"][cls]
         avg_ms = by_cls[cls] / nlaunch
@@ -432,7 +440,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--profile-class", default="nd_fwd_c64",
+    ap.add_argument("--profile-class", default=None,
                     help="kernel class whose roofline is reported (the largest share of device time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true",
