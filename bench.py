@@ -119,6 +119,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device, world):
+    """The largest x over the ranks of the process group (x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------------------ oracle timing
 def oracle_step(w, ktab, sten, cint, nrhs=None, workers=None):
     """One step of the workload on the CPU oracle: assembly + sparse LU of the medium, the
@@ -284,11 +300,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         prof = ls.profile_stop()
         ck = sampler.stop() if sampler else None
-        total_ms = sum(a.elapsed_time(b) for a, b in evs)
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev, world)
         if world > 1:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
             torch.distributed.barrier()
         return total_ms, infos, prof, ck
 
@@ -297,7 +310,7 @@ def run_gpu(args):
     nd = s_mix.nd_stats()
     # headline region: launches counted, replayed through the library's CUDA graphs
     total_ms, infos, prof, clocks = timed(s_mix, args.steps, args.warmup, None, clocks=True)
-    value = w.nrhs * args.steps * world / (total_ms / 1e3)
+    value = job_rate(w.nrhs * args.steps, world, total_ms / 1e3)
     its = [i.iters for inf in infos for i in inf]
     res = [i.rel_resid for inf in infos for i in inf]
     conv = all(i.converged for inf in infos for i in inf)
@@ -338,7 +351,7 @@ def run_gpu(args):
     s64, _ = make(False)
     k64 = max(1, min(args.steps, 5))
     ms64, infos64, _, _ = timed(s64, k64, 1)
-    value64 = w.nrhs * k64 * world / (ms64 / 1e3)
+    value64 = job_rate(w.nrhs * k64, world, ms64 / 1e3)
     its64 = [i.iters for inf in infos64 for i in inf]
     s64.close()
 
@@ -362,12 +375,8 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": w.nrhs * e2e_steps * world / e2e_s, "unit": "solves/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev, world)
+    e2e = {"value": job_rate(w.nrhs * e2e_steps, world, e2e_s), "unit": "solves/s",
            "h2d_bytes_per_step": int(m_host.numel() * 8 + dirs_host.numel() * 8),
            "d2h_bytes_per_step": int(u_host.numel() * 16),
            "includes": "ls_setup (medium from pinned host) + ls_factor + ls_rhs_plane_wave + ls_solve "
