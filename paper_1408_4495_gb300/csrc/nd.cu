@@ -765,6 +765,10 @@ template <int B, typename T, typename F> __device__ __forceinline__ void stage_c
   }
 }
 
+// 1 / x, correctly rounded
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <typename C> __device__ __forceinline__ C shfl_c(C v, int src) {
   v.x = __shfl_sync(0xffffffffu, v.x, src);
   v.y = __shfl_sync(0xffffffffu, v.y, src);
@@ -789,7 +793,8 @@ __global__ void __launch_bounds__(512) k_panel_rows(LevelK<C> L, int k0, int k1,
   __shared__ int cnt;
   const int z = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
   const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
-  const int G = blockDim.x / ((R + 31) / 32 * 32), r = t / G, g = t - r * G;
+  const int G = blockDim.x / ((R + 31) / 32 * 32);  // 1, 2 or 4
+  const int lgG = G == 4 ? 2 : (G == 2 ? 1 : 0), r = t >> lgG, g = t & (G - 1);
   C* P = reinterpret_cast<C*>(smem_raw);  // [R][LDP]
   int* ph = reinterpret_cast<int*>(P + (size_t)R * LDP);
   int* iph = ph + R;
@@ -840,14 +845,14 @@ __global__ void __launch_bounds__(512) k_panel_rows(LevelK<C> L, int k0, int k1,
       const C* prow = P + (size_t)bi * LDP;
       const C d = prow[j];
       const Rl den = cabs2(d);
-      const Rl rden = den > 0 ? (Rl)1 / den : (Rl)0;
+      const Rl rden = den > 0 ? recip(den) : (Rl)0;
       C inv;
       inv.x = d.x * rden;
       inv.y = -d.y * rden;
       const C m = cmul(aj, inv);
       if (g == 0) row[j] = m;
       // columns c > j with c = g (mod G), four at a time: loads before the stores
-      int c = j + 1 + ((g - (j + 1) % G) + G) % G;
+      int c = j + 1 + ((g - j - 1) & (G - 1));
       for (; c + 3 * G < w; c += 4 * G) {
         C pv[4], rv[4];
 #pragma unroll
@@ -1115,10 +1120,6 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
       __syncthreads();
     }
   }
-  stage_copy<8>(B, s * nc, [&](int idx) {
-    const int c = idx / s, r = idx - c * s;
-    return A[(size_t)c * fmax + r];
-  });
   // Elimination without moving rows: thread (r, g) updates row r on the columns
   // c = g (mod G); a row chosen as pivot is retired from the pivot search but, as Gauss-
   // Jordan requires, still eliminated in later columns.  Pivot = largest |re| + |im| over
@@ -1130,6 +1131,20 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
   const bool act = g < G;
   const int lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
   bool live = act && g == 0;  // one thread per row takes part in the pivot search
+  // off = (g - j - 1) mod G: this thread's first column after column j
+  int off = G > 0 ? ((g - 1) % G + G) % G : 0;
+  // own-row block into shared memory: thread (r, g) copies row r on columns g (mod G),
+  // four loads in flight before the stores
+  if (act)
+    for (int c = g; c < nc; c += 4 * G) {
+      C v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c + u * G < nc) v[u] = A[(size_t)(c + u * G) * fmax + r];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c + u * G < nc) B[(size_t)(c + u * G) * s + r] = v[u];
+    }
   __syncthreads();
   for (int j = 0; j < s; ++j) {
     const int par = j & 1;
@@ -1152,12 +1167,12 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
     // pivot row is left as it is (every thread reads it for the pivot)
     const C dg = B[(size_t)j * s + bi];
     const Rl den = cabs2(dg);
-    const Rl rden = den > 0 ? (Rl)1 / den : (Rl)0;
+    const Rl rden = den > 0 ? recip(den) : (Rl)0;
     C inv;
     inv.x = dg.x * rden;
     inv.y = -dg.y * rden;
     if (act && r == bi)
-      for (int c = j + 1 + ((g - (j + 1) % G) + G) % G; c < nc; c += G) {
+      for (int c = j + 1 + off; c < nc; c += G) {
         const C v = cmul(B[(size_t)c * s + bi], inv);
         prow[c] = v;
         B[(size_t)c * s + bi] = v;
@@ -1165,7 +1180,7 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
     __syncthreads();
     if (act && r != bi) {
       const C mr = bj;  // B[j][r], read before any update of this step
-      int c = j + 1 + ((g - (j + 1) % G) + G) % G;
+      int c = j + 1 + off;
       for (; c + 3 * G < nc; c += 4 * G) {
         C pv[4], rv[4];
 #pragma unroll
@@ -1175,6 +1190,7 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
       }
       for (; c < nc; c += G) B[(size_t)c * s + r] = cfms(B[(size_t)c * s + r], mr, prow[c]);
     }
+    off = off == 0 ? G - 1 : off - 1;
     __syncthreads();
   }
   // row ph[i] holds the result for own row i
@@ -1191,9 +1207,9 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
       iph[pj] = lb;
     }
   __syncthreads();
-  for (int idx = tid; idx < s * (nc - s); idx += NT) {
-    const int cq = idx / s, i = idx - cq * s;
-    A[(size_t)(s + cq) * fmax + i] = B[(size_t)(s + cq) * s + ph[i]];
+  if (act) {
+    const int src = ph[r];
+    for (int c = s + g; c < nc; c += G) A[(size_t)c * fmax + r] = B[(size_t)c * s + src];
   }
 }
 
