@@ -519,21 +519,40 @@ template <typename C> __global__ void k_set_one(C* F, long n_one, const int64_t*
 }
 
 // Schur complements of the children with child index k into their parents' fronts.
-template <typename C> __global__ void k_extend_add(LevelK<C> P, LevelK<C> Ch, int k) {
+template <typename C> __global__ void __launch_bounds__(256) k_extend_add(LevelK<C> P, LevelK<C> Ch, int k) {
   const int c = blockIdx.x;
   if (Ch.kidx[c] != k) return;
   const int pz = Ch.parent[c];
   C* Fp = P.F + (size_t)pz * P.fmax * P.ncols;
   const C* Fc = Ch.F + (size_t)c * Ch.fmax * Ch.ncols;
   const int* ea = Ch.ea + (size_t)c * Ch.bmax;
-  const long tot = (long)Ch.bmax * Ch.bmax;
-  for (long idx = blockIdx.y * (long)blockDim.x + threadIdx.x; idx < tot; idx += (long)gridDim.y * blockDim.x) {
-    const int a = (int)(idx % Ch.bmax), b = (int)(idx / Ch.bmax);
-    const int pa = ea[a], pb = ea[b];
-    if (pa < 0 || pb < 0) continue;
-    const C v = Fc[(size_t)(Ch.smax + b) * Ch.fmax + Ch.smax + a];
-    C& dst = Fp[(size_t)pb * P.fmax + pa];
-    dst = cadd(dst, v);
+  const int cb = Ch.bmax;
+  const long tot = (long)cb * cb;
+  // four entries per thread: index, child and parent loads in flight before the stores
+  constexpr int B = 4;
+  const long step = (long)gridDim.y * blockDim.x;
+  for (long base = blockIdx.y * (long)blockDim.x + threadIdx.x; base < tot; base += step * B) {
+    C v[B], o[B];
+    long dst[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const long idx = base + u * step;
+      dst[u] = -1;
+      if (idx < tot) {
+        const int a = (int)(idx % cb), b = (int)(idx / cb);
+        const int pa = ea[a], pb = ea[b];
+        if (pa >= 0 && pb >= 0) {
+          dst[u] = (long)pb * P.fmax + pa;
+          v[u] = Fc[(size_t)(Ch.smax + b) * Ch.fmax + Ch.smax + a];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (dst[u] >= 0) o[u] = Fp[dst[u]];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (dst[u] >= 0) Fp[dst[u]] = cadd(o[u], v[u]);
   }
 }
 
@@ -1371,20 +1390,24 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     LevelK<C> Ch = has_child ? level_k<C>(p, l + 1) : L;
     // own rows: [F11 | F12 | I] -> [* | H | F11^{-1}]
     const size_t gjm = gj_smem<C>(L.smax, L.ncols);
-    if (gjm <= GJ_SMEM_MAX) {
-      // one CTA per front: extend-add, Gauss-Jordan in shared memory, ring rows
-      LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
-                k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, has_child ? 1 : 0,
-                                                                                   p->d_err));
-      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st);
-      continue;
-    }
-    if (has_child) {
+    // the children's Schur complements: by a GPU-wide kernel, or inside the Gauss-Jordan
+    // CTA when they are small (one CTA per front would serialise large ones)
+    const bool gj = gjm <= GJ_SMEM_MAX;
+    const bool fused_ea = gj && has_child && Ch.bmax < 48;
+    if (has_child && !fused_ea) {
       const long tot = (long)Ch.bmax * Ch.bmax;
-      const unsigned bx = (unsigned)std::max<long>(1, std::min<long>((tot + 255) / 256, 64));
+      const unsigned bx = (unsigned)std::max<long>(1, std::min<long>((tot + 1023) / 1024, 64));
       for (int k = 0; k < 2; ++k)
         LS_LAUNCH(f32 ? "nd_extend_add_c64" : "nd_extend_add_c128", st,
                   k_extend_add<C><<<dim3(Ch.nf, bx), 256, 0, st>>>(L, Ch, k));
+    }
+    if (gj) {
+      // one CTA per front: Gauss-Jordan in shared memory (with the extend-add if fused)
+      LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
+                k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, fused_ea ? 1 : 0,
+                                                                                   p->d_err));
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st);
+      continue;
     }
     if (L.smax <= 32 * reg_rpl_max<C>()) {
       // both sweeps with the fronts' own rows in registers
