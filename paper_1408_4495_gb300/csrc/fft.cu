@@ -167,10 +167,13 @@ template <int L> struct RowShape {
   static constexpr int NT = (L / 8 > 256) ? L / 8 : 256;
   static constexpr int NL = NT * 8 / L;
 };
+// TC adjacent lines per CTA (about 64 KB of shared memory); FP32 lines of 512 and more
+// take 8 lines and 2 butterflies per thread, so that two CTAs fit an SM's registers
 template <typename C, int L> struct ColShape {
   static constexpr int raw = 65536 / (L * (int)sizeof(C));
-  static constexpr int TC = raw < 2 ? 2 : (raw > 16 ? 16 : raw);
-  static constexpr int t = TC * L / 8;
+  static constexpr bool f32_long = sizeof(C) == 8 && L >= 512;
+  static constexpr int TC = f32_long ? 8 : (raw < 2 ? 2 : (raw > 16 ? 16 : raw));
+  static constexpr int t = f32_long ? TC * L / 16 : TC * L / 8;
   static constexpr int NT = t > 512 ? 512 : (t < 64 ? 64 : t);
 };
 
