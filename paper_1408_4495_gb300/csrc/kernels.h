@@ -65,6 +65,13 @@ void conv_apply_ff(const ConvPlan& p, int nrhs, const double2* u, double2* y, co
 // g = K(-omega^2 m u_inc) for plane waves (the right-hand side), float-float passes, FP64 g
 void conv_rhs_ff(const ConvPlan& p, int nrhs, const double* plane_dirs, double2* g, void* scratch1, void* scratch2,
                  cudaStream_t st);
+// C -= A B on the complex FP32 fronts of a level on the tensor cores (tc_gemm.cu): A, B, C
+// are the blocks [r0,r1)x[k0,k1), [k0,k1)x[c0,c1), [r0,r1)x[c0,c1) of each column-major
+// front (ld = fmax, fstride elements apart); *err = 2 if a bounded wait expired
+void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0, int c1, int k0, int k1, int* err,
+              cudaStream_t st);
+// tensor-core products on (LS_TC=0 in the environment turns them off, for comparisons)
+bool tc_enabled();
 // float-float copy of count FP64 reals (dst: 2 * count floats)
 void to_ff(const double* src, void* dst, long count, cudaStream_t st);
 size_t conv_scratch1_elems(int d, int n, int nrhs);

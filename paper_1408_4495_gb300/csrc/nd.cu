@@ -1305,9 +1305,18 @@ template <typename C> static size_t gj_smem(int s, int nc) {
   return ((size_t)s * nc + nc) * sizeof(C) + 2 * (size_t)s * sizeof(int);
 }
 
+// FP32 products with at least this many rows and k go to the tensor cores (3xTF32)
+constexpr int TC_MIN_ROWS = 64, TC_MIN_K = 16;
+
 template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
-                                              cudaStream_t st) {
+                                              cudaStream_t st, int* err) {
   if (r1 <= r0 || c1 <= c0 || k1 <= k0) return;
+  if constexpr (sizeof(C) == 8) {
+    if (r1 - r0 >= TC_MIN_ROWS && k1 - k0 >= TC_MIN_K && tc_enabled()) {
+      tc_cgemm(reinterpret_cast<float2*>(L.F), (long)L.fmax * L.ncols, L.fmax, L.nf, r0, r1, c0, c1, k0, k1, err, st);
+      return;
+    }
+  }
   const int nr = (r1 - r0 + 63) / 64, nc = (c1 - c0 + 63) / 64;
   LS_LAUNCH(sizeof(C) == 8 ? "nd_gemm_c64" : "nd_gemm_c128", st,
             k_gemm<C><<<dim3(L.nf, nr * nc), 256, 0, st>>>(L, r0, r1, c0, c1, k0, k1));
@@ -1359,6 +1368,7 @@ void nd_factor_check(NdPlan* p, cudaStream_t st) {
   int err = 0;
   LS_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA(cudaStreamSynchronize(st));
+  if (err == 2) LS_FAIL(ETIMEOUT_, "a bounded wait of the tensor-core front update expired");
   if (err) LS_FAIL(EINVAL_, "nested-dissection factorization met an exactly singular front");
 }
 
@@ -1406,7 +1416,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
                 k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, fused_ea ? 1 : 0,
                                                                                    p->d_err));
-      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st);
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err);
       continue;
     }
     if (L.smax <= 32 * reg_rpl_max<C>()) {
@@ -1430,7 +1440,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
         const int m = L.ncols - k1;
         LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                   k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
-        launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st);
+        launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
       }
       // sweep 2: backward substitution with U11 on the own rows of [F12 | I]
       const int nblk = (L.smax + NB - 1) / NB;
@@ -1439,11 +1449,11 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
         const int m = L.ncols - L.smax;
         LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                   k_trsm_upper<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, j0, j1));
-        launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st);
+        launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st, p->d_err);
       }
     }
     // ring rows: [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
-    launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st);
+    launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err);
   }
   prof_tag(-1);
 }

@@ -1,0 +1,293 @@
+// Schur-complement updates of the fronts on the 5th-generation tensor cores (tcgen05):
+//
+//   C[r0:r1, c0:c1] -= A[r0:r1, k0:k1] B[k0:k1, c0:c1]   (complex FP32, one front per CTA
+//                                                         column of the grid)
+//
+// with A, B, C blocks of the same column-major front (ld = fmax).  The complex product is
+// one real product of twice the size,
+//   [Re C | Im C] = A' B',  A'[m][2k + {0,1}] = (Re, Im) A[m][k],
+//   B' = [[Re B, Im B]; [-Im B, Re B]] (rows 2k, 2k+1),
+// and each FP32 operand is split into two TF32 numbers, x = hi + lo, so that
+// A'B' ~ A'hi B'hi + A'hi B'lo + A'lo B'hi ("3xTF32": error about 2^-22 relative, the
+// accuracy of the FP32 fronts).  A CTA owns a 128-row tile of C and NT = 64 complex columns:
+// D = 128 x 128 FP32 accumulators in tensor memory, filled by tcgen05.mma kind::tf32
+// (M = 128, N = 128, K = 8 per instruction) from K-major operands in shared memory
+// (no-swizzle canonical layout: 8-row x 16-byte core matrices).  One thread issues the MMAs
+// and commits them to an mbarrier; all waits are bounded and set *err on expiry.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "prof.h"
+
+namespace ls {
+
+namespace tc {
+
+constexpr int TM = 128;        // rows of C per CTA
+constexpr int NT = 64;         // complex columns of C per CTA
+constexpr int NP = 2 * NT;     // real columns (Re | Im)
+constexpr int KC = 16;         // complex k per chunk
+constexpr int KP = 2 * KC;     // real k per chunk
+constexpr int KSTEP = 8;       // tf32 k per instruction
+constexpr int NSTEP = KP / KSTEP;
+constexpr int THREADS = 256;
+// one operand slice of KSTEP real k: rows x 32 bytes
+constexpr int A_SLICE = TM * KSTEP * 4;   // 4 KB
+constexpr int B_SLICE = NP * KSTEP * 4;   // 4 KB
+constexpr int A_BYTES = NSTEP * A_SLICE;  // 16 KB (hi or lo)
+constexpr int B_BYTES = NSTEP * B_SLICE;  // 16 KB
+constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 1024;  // + barrier and TMEM address
+constexpr long WAIT_LIMIT = 1L << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// byte offset of element (row, k) of a K-major no-swizzle operand slice: core matrices of
+// 8 rows x 16 bytes (4 tf32), the two K halves of a row group 128 bytes apart (LBO), row
+// groups 256 bytes apart (SBO)
+__device__ __forceinline__ int core_off(int row, int k) {
+  return ((row >> 3) * 2 + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45),
+// fixed 0b001 (46-48), no swizzle (61-63 = 0)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  const uint64_t lbo = 128 >> 4, sbo = 256 >> 4;
+  return (uint64_t)((addr >> 4) & 0x3FFF) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (7-9, 10-12 = 2),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// waits for the given phase of the barrier; false if the bound expired
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(mbar, phase)) return true;
+  return false;
+}
+
+}  // namespace tc
+
+struct TcArgs {
+  float2* F;         // fronts of the level
+  long fstride;      // elements per front (fmax * ncols)
+  int fmax;          // leading dimension
+  int r0, r1, c0, c1, k0, k1;
+  int ntr;           // row tiles (grid.y = ntr * column tiles)
+  int* err;
+};
+
+__global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* Ahi = smem_raw;
+  unsigned char* Alo = Ahi + A_BYTES;
+  unsigned char* Bhi = Alo + A_BYTES;
+  unsigned char* Blo = Bhi + B_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  __shared__ int failed;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int z = blockIdx.x;
+  const int tr = blockIdx.y % a.ntr, tcn = blockIdx.y / a.ntr;
+  const int rb = a.r0 + tr * TM, cb = a.c0 + tcn * NT;
+  float2* F = a.F + (size_t)z * a.fstride;
+  const int fmax = a.fmax;
+
+  if (tid == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(NP)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t mb = smem_u32(mbar);
+
+  uint32_t phase = 0;
+  const int K = a.k1 - a.k0;
+  const int nchunk = (K + KC - 1) / KC;
+  // global loads of one chunk into registers: A 128 x KC (8 per thread), B KC x 64 (4 per
+  // thread); the next chunk's loads are issued while the tensor core works on this one
+  constexpr int PA = TM * KC / THREADS, PB = NT * KC / THREADS;
+  float2 va[PA], vb[PB];
+  auto load = [&](int kc) {
+    const int kw = min(KC, K - kc);
+#pragma unroll
+    for (int u = 0; u < PA; ++u) {
+      const int e = tid + u * THREADS, m = e % TM, k = e / TM;
+      va[u] = (k < kw && rb + m < a.r1) ? F[(size_t)(a.k0 + kc + k) * fmax + rb + m] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int e = tid + u * THREADS, n = e % NT, k = e / NT;
+      vb[u] = (k < kw && cb + n < a.c1) ? F[(size_t)(cb + n) * fmax + a.k0 + kc + k] : make_float2(0.f, 0.f);
+    }
+  };
+  if (nchunk > 0) load(0);
+  int chunks = 0;
+  for (int ch = 0; ch < nchunk; ++ch, ++chunks) {
+    // ---- A' (TM x KP): element (m, 2k + p), hi and lo
+#pragma unroll
+    for (int u = 0; u < PA; ++u) {
+      const int e = tid + u * THREADS, m = e % TM, k = e / TM;
+      const float2 v = va[u];
+      const int kr = 2 * k;  // real k within the chunk
+      const int s = kr / KSTEP, kk = kr % KSTEP;
+      const uint32_t hx = to_tf32(v.x), hy = to_tf32(v.y);
+      const uint32_t lx = to_tf32(v.x - __uint_as_float(hx)), ly = to_tf32(v.y - __uint_as_float(hy));
+      const int o = s * A_SLICE + core_off(m, kk);
+      *reinterpret_cast<uint2*>(Ahi + o) = make_uint2(hx, hy);  // kk even: (2k, 2k+1) adjacent
+      *reinterpret_cast<uint2*>(Alo + o) = make_uint2(lx, ly);
+    }
+    // ---- B' (NP x KP, K-major): column n < NT: (Re B, -Im B); column NT + n: (Im B, Re B)
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int e = tid + u * THREADS, n = e % NT, k = e / NT;
+      const float re = vb[u].x, im = vb[u].y;
+      const int kr = 2 * k, s = kr / KSTEP, kk = kr % KSTEP;
+      const uint32_t hre = to_tf32(re), him = to_tf32(im), hnim = to_tf32(-im);
+      const uint32_t lre = to_tf32(re - __uint_as_float(hre)), lim = to_tf32(im - __uint_as_float(him));
+      const uint32_t lnim = to_tf32(-im - __uint_as_float(hnim));
+      const int o1 = s * B_SLICE + core_off(n, kk), o2 = s * B_SLICE + core_off(NT + n, kk);
+      *reinterpret_cast<uint2*>(Bhi + o1) = make_uint2(hre, hnim);
+      *reinterpret_cast<uint2*>(Blo + o1) = make_uint2(lre, lnim);
+      *reinterpret_cast<uint2*>(Bhi + o2) = make_uint2(him, hre);
+      *reinterpret_cast<uint2*>(Blo + o2) = make_uint2(lim, lre);
+    }
+    // generic-proxy writes -> visible to the tensor core's async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      for (int s = 0; s < NSTEP; ++s) {
+        const uint64_t ah = sdesc(smem_u32(Ahi + s * A_SLICE)), al = sdesc(smem_u32(Alo + s * A_SLICE));
+        const uint64_t bh = sdesc(smem_u32(Bhi + s * B_SLICE)), bl = sdesc(smem_u32(Blo + s * B_SLICE));
+        const int acc0 = (ch > 0 || s > 0) ? 1 : 0;
+        mma_tf32(tmem, ah, bh, acc0);
+        mma_tf32(tmem, ah, bl, 1);
+        mma_tf32(tmem, al, bh, 1);
+      }
+      mma_commit(mb);
+    }
+    if (ch + 1 < nchunk) load((ch + 1) * KC);
+    // the operands are overwritten by the next chunk: wait for these MMAs
+    if (!mbar_wait(mb, phase)) {
+      if (tid == 0) atomicExch(a.err, 2);
+      failed = 1;
+    }
+    phase ^= 1;
+    __syncthreads();
+    if (failed) break;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+  if (!failed && chunks > 0) {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .., columns of half w / 4 of the Re
+    // and the Im blocks, and subtracts from C
+    const int q = warp & 3, half = warp >> 2;
+    const int m = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    for (int cc = 0; cc < NT / 2; cc += 16) {
+      const int col = half * (NT / 2) + cc;
+      uint32_t re[16], im[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
+            "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]),
+            "=r"(re[15])
+          : "r"(tmem + lane_base + (uint32_t)col));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
+            "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]),
+            "=r"(im[15])
+          : "r"(tmem + lane_base + (uint32_t)(NT + col)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (rb + m < a.r1)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = cb + col + j;
+          if (c < a.c1) {
+            float2& x = F[(size_t)c * fmax + rb + m];
+            x.x -= __uint_as_float(re[j]);
+            x.y -= __uint_as_float(im[j]);
+          }
+        }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NP) : "memory");
+}
+
+bool tc_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LS_TC");
+    return !(e && std::strcmp(e, "0") == 0);
+  }();
+  return on;
+}
+
+// C -= A B on every front of a level (see the file comment); a no-op for empty ranges
+void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0, int c1, int k0, int k1, int* err,
+              cudaStream_t st) {
+  if (r1 <= r0 || c1 <= c0 || k1 <= k0 || nf <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    LS_CUDA(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    attr = true;
+  }
+  TcArgs a;
+  a.F = F;
+  a.fstride = fstride;
+  a.fmax = fmax;
+  a.r0 = r0; a.r1 = r1; a.c0 = c0; a.c1 = c1; a.k0 = k0; a.k1 = k1;
+  a.ntr = (r1 - r0 + tc::TM - 1) / tc::TM;
+  a.err = err;
+  const int ntc = (c1 - c0 + tc::NT - 1) / tc::NT;
+  LS_LAUNCH("nd_gemm_tc_c64", st, k_tc_cgemm<<<dim3(nf, a.ntr * ntc), tc::THREADS, tc::SMEM, st>>>(a));
+}
+
+}  // namespace ls
