@@ -95,6 +95,10 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
  * into the nested-dissection fronts and computes their partial LU factorizations (pivoting
  * restricted to the fully-summed rows of each front).  FP32 fronts under LS_PREC_MIXED,
  * FP64 under LS_PREC_FP64.  May be called again (e.g. to time it); LS_ESTATE if c is NULL.
+ * Asynchronous: the factorization is enqueued on the context's stream and the call returns;
+ * a later ls_rhs_plane_wave overlaps it.  The next ls_solve or ls_precond waits for it and
+ * reports its errors (LS_EINVAL for an exactly singular front, LS_ETIMEOUT if a bounded
+ * device wait expired); after such an error the context needs ls_factor again.
  */
 ls_status ls_factor(ls_ctx* c);
 

@@ -69,6 +69,9 @@ struct ls_ctx {
   std::vector<double2> alpha_h, cint_h;
   ls::NdPlan* nd = nullptr;
   bool factored = false;
+  bool factor_pending = false;  // enqueued, its error flag not read yet
+  cudaStream_t st2 = nullptr;   // side stream: right-hand sides that overlap the factorization
+  cudaEvent_t ev_factor = nullptr;  // recorded on st where the factorization's top levels begin
   std::map<std::string, DevBuf> bufs;
   std::vector<double2*> V;
   std::vector<void*> Z;
@@ -175,11 +178,25 @@ template <typename F> void run_graph(ls_ctx* c, const std::string& key, F&& body
 }
 
 // copy count complex doubles (or doubles) between a caller array and a device buffer
-void copy_in(ls_ctx* c, void* dst, const void* src, size_t bytes) {
-  LS_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+void copy_in(ls_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st = nullptr) {
+  LS_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          st ? st : c->st));
 }
-void copy_out(ls_ctx* c, void* dst, const void* src, size_t bytes) {
-  LS_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+void copy_out(ls_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st = nullptr) {
+  LS_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          st ? st : c->st));
+}
+
+// waits for an enqueued factorization and reads its error flag (throws on failure)
+void factor_wait(ls_ctx* c) {
+  if (!c->factor_pending) return;
+  c->factor_pending = false;
+  try {
+    ls::nd_factor_check(c->nd, c->st);
+  } catch (...) {
+    c->factored = false;
+    throw;
+  }
 }
 
 void ensure_basis(ls_ctx* c, int nvec, int nrhs, int z_elem) {
@@ -457,6 +474,8 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
       LS_CUDA(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
       c->own_stream = true;
     }
+    LS_CUDA(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    LS_CUDA(cudaEventCreateWithFlags(&c->ev_factor, cudaEventDisableTiming));
     // medium: checks on the host copy (Sec. 2.1: m vanishes within the buffer; 1 - m > 0)
     std::vector<double> mh(c->N);
     if (is_device_ptr(m)) LS_CUDA(cudaMemcpy(mh.data(), m, c->N * sizeof(double), cudaMemcpyDeviceToHost));
@@ -590,11 +609,11 @@ ls_status ls_factor(ls_ctx* c) {
     const bool mixed = c->prec == LS_PREC_MIXED;
     if (mixed ? ls::nd_prepare<float2>(c->nd, c->st) : ls::nd_prepare<double2>(c->nd, c->st)) ++c->gen;
     run_graph(c, "factor", [&] {
-      if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
-      else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st);
+      if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, c->ev_factor);
+      else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, c->ev_factor);
     });
-    ls::nd_factor_check(c->nd, c->st);
     c->factored = true;
+    c->factor_pending = true;
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -609,16 +628,25 @@ ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_o
     if (nrhs < 1 || !dirs || !g_out) throw Error{ls::EINVAL_, "bad arguments"};
     const size_t tot = (size_t)nrhs * c->N;
     double* dd = buf<double>(c, "dirs", (size_t)nrhs * c->d);
-    copy_in(c, dd, dirs, (size_t)nrhs * c->d * sizeof(double));
     double2* gd = buf<double2>(c, "rhs_out", tot);
     const size_t s1 = ls::conv_scratch1_elems(c->d, c->n, nrhs), s2 = ls::conv_scratch2_elems(c->d, c->n, nrhs);
     void* t1 = buf<double2>(c, "conv1_64", s1);
     void* t2 = s2 ? buf<double2>(c, "conv2_64", s2) : nullptr;
+    // With a factorization in flight, run on the side stream from the point where its top
+    // levels begin (they occupy few SMs; every earlier use of these buffers is before that
+    // point in stream order), so that the two overlap; it uses none of the factorization's
+    // data.
+    cudaStream_t st = c->st;
+    if (c->factor_pending) {
+      st = c->st2;
+      LS_CUDA(cudaStreamWaitEvent(st, c->ev_factor, 0));
+    }
+    copy_in(c, dd, dirs, (size_t)nrhs * c->d * sizeof(double), st);
     // float-float passes on the mixed path, FP64 on the plain path
-    if (c->prec == LS_PREC_MIXED) ls::conv_rhs_ff(c->plan, nrhs, dd, gd, t1, t2, c->st);
-    else ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, c->st);
-    copy_out(c, g_out, gd, tot * sizeof(double2));
-    LS_CUDA(cudaStreamSynchronize(c->st));
+    if (c->prec == LS_PREC_MIXED) ls::conv_rhs_ff(c->plan, nrhs, dd, gd, t1, t2, st);
+    else ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, st);
+    copy_out(c, g_out, gd, tot * sizeof(double2), st);
+    LS_CUDA(cudaStreamSynchronize(st));
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -629,6 +657,7 @@ ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u
   try {
     check_ctx(c);
     if (!c->factored) throw Error{ls::ESTATE_, "ls_solve before ls_factor"};
+    factor_wait(c);
     if (nrhs < 1 || !rhs || !u_out || !(tol > 0)) throw Error{ls::EINVAL_, "bad arguments"};
     const size_t tot = (size_t)nrhs * c->N;
     double2* g = buf<double2>(c, "solve_g", tot);
@@ -661,6 +690,7 @@ const char* ls_last_error(const ls_ctx* c) {
 void ls_free(ls_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->st2) cudaStreamSynchronize(c->st2);
   for (void* p : {(void*)c->w2m64, (void*)c->w2m32, (void*)c->tw32, (void*)c->tw64, (void*)c->ktq, (void*)c->sym32,
                   (void*)c->sym64, (void*)c->ffbuf, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ})
     if (p) ls::dev_free(p);
@@ -672,6 +702,8 @@ void ls_free(ls_ctx* c) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->nd) ls::nd_free(c->nd);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->ev_factor) cudaEventDestroy(c->ev_factor);
   cudaGetLastError();
   delete c;
 }
@@ -757,6 +789,7 @@ ls_status ls_precond(ls_ctx* c, int nrhs, const double* in, double* out) {
   try {
     check_ctx(c);
     if (!c->factored) throw Error{ls::ESTATE_, "ls_precond before ls_factor"};
+    factor_wait(c);
     if (nrhs < 1 || !in || !out) throw Error{ls::EINVAL_, "bad arguments"};
     const size_t tot = (size_t)nrhs * c->N;
     double2* x = buf<double2>(c, "io_in", tot);

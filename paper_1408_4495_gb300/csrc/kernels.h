@@ -114,7 +114,9 @@ template <typename C>
 void nd_factor(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
 template <typename C> bool nd_prepare(NdPlan* p, cudaStream_t st);
 template <typename C>
-void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
+// top_levels (may be null): recorded on st where the levels with at most 32 fronts begin
+void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st,
+                      cudaEvent_t top_levels);
 void nd_factor_check(NdPlan* p, cudaStream_t st);
 // x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);

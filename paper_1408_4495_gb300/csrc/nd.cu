@@ -1360,7 +1360,7 @@ template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* s
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
   nd_prepare<C>(p, st);
-  nd_factor_launch<C>(p, alpha64, cint64, w2m64, st);
+  nd_factor_launch<C>(p, alpha64, cint64, w2m64, st, nullptr);
   nd_factor_check(p, st);
 }
 
@@ -1372,8 +1372,17 @@ void nd_factor_check(NdPlan* p, cudaStream_t st) {
   if (err) LS_FAIL(EINVAL_, "nested-dissection factorization met an exactly singular front");
 }
 
+// an event other streams can wait on, also from inside a stream capture (as an event node)
+static void record_marker(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LS_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusActive) LS_CUDA(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  else LS_CUDA(cudaEventRecord(ev, st));
+}
+
 template <typename C>
-void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
+void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st,
+                      cudaEvent_t top_levels) {
   if (!p->F || p->F_bytes != (int)sizeof(C)) LS_FAIL(ESTATE_, "front storage not prepared for this precision");
   const bool f32 = sizeof(C) == 8;
   LS_CUDA(cudaMemsetAsync(p->F, 0, p->F_elems * sizeof(C), st));
@@ -1393,11 +1402,17 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     LS_CUDA(cudaFuncSetAttribute(k_gauss_jordan<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM_MAX));
     attr = true;
   }
+  bool marked = top_levels == nullptr;
   for (int l = depth - 1; l >= 0; --l) {
     prof_tag(l);
     LevelK<C> L = level_k<C>(p, l);
     const bool has_child = l + 1 < depth;
     LevelK<C> Ch = has_child ? level_k<C>(p, l + 1) : L;
+    if (!marked && L.nf <= 32) {
+      // the levels from here to the root run on few SMs: work on other streams may start
+      record_marker(top_levels, st);
+      marked = true;
+    }
     // own rows: [F11 | F12 | I] -> [* | H | F11^{-1}]
     const size_t gjm = gj_smem<C>(L.smax, L.ncols);
     // the children's Schur complements: by a GPU-wide kernel, or inside the Gauss-Jordan
@@ -1455,6 +1470,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     // ring rows: [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
     launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err);
   }
+  if (!marked) record_marker(top_levels, st);
   prof_tag(-1);
 }
 
@@ -1928,8 +1944,8 @@ template void nd_factor<float2>(NdPlan*, const void*, const void*, const void*, 
 template void nd_factor<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template bool nd_prepare<float2>(NdPlan*, cudaStream_t);
 template bool nd_prepare<double2>(NdPlan*, cudaStream_t);
-template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
-template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
+template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t);
+template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t);
 template void nd_solve<float2>(NdPlan*, int, const float2*, float2*, cudaStream_t);
 template void nd_solve<double2>(NdPlan*, int, const double2*, double2*, cudaStream_t);
 
