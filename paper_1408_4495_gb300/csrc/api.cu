@@ -302,6 +302,12 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
   std::vector<char> act(nrhs);
   std::vector<double2> Y((size_t)nrhs * R);
   const double inner = mixed ? 0.5 : 1.0;
+  // subsets of right-hand sides that are still iterating
+  std::vector<int> live_ix(nrhs);
+  int* dlive = buf<int>(c, "live_idx", nrhs);
+  double2* vlive = buf<double2>(c, "live_v", tot);
+  CZ* zlive = buf<CZ>(c, "live_z", tot);
+  void* wlive = buf<double2>(c, "live_w", tot);
 
   while (true) {
     bool any = false;
@@ -325,12 +331,37 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       if (!live) break;
       ensure_basis(c, k + 2, nrhs, sizeof(CZ));
       CZ* zk = (CZ*)c->Z[k];
-      // z_k = P v_k (stencil + nested-dissection solve), w = A z_k (FFT operator)
-      run_graph(c, "iter:" + std::to_string(k) + ":" + std::to_string(nrhs) + (mixed ? ":m" : ":d"), [&] {
-        precond_apply<CZ>(c, nrhs, c->V[k], zk);
-        if (mixed) op_apply<CZ>(c, nrhs, zk, wz);
-        else op_apply<double2>(c, nrhs, (const double2*)zk, w);
-      });
+      // right-hand sides still iterating; the others carry zero vectors (their scale was 0)
+      int nlive = 0;
+      for (int j = 0; j < nrhs; ++j)
+        if (act[j] && kdone[j] == 0) live_ix[nlive++] = j;
+      const bool compact = nlive < nrhs;
+      if (compact) LS_CUDA(cudaMemcpyAsync(dlive, live_ix.data(), nlive * sizeof(int), cudaMemcpyHostToDevice, c->st));
+      // z_k = P v_k (stencil + nested-dissection solve), w = A z_k (FFT operator), on the
+      // live right-hand sides only
+      run_graph(c, "iter:" + std::to_string(k) + ":" + std::to_string(nrhs) + ":" + std::to_string(nlive) +
+                       (mixed ? ":m" : ":d"),
+                [&] {
+                  if (!compact) {
+                    precond_apply<CZ>(c, nrhs, c->V[k], zk);
+                    if (mixed) op_apply<CZ>(c, nrhs, zk, wz);
+                    else op_apply<double2>(c, nrhs, (const double2*)zk, w);
+                    return;
+                  }
+                  ls::rhs_gather<double2>(c->V[k], vlive, dlive, nlive, N, c->st);
+                  precond_apply<CZ>(c, nlive, vlive, zlive);
+                  LS_CUDA(cudaMemsetAsync(zk, 0, tot * sizeof(CZ), c->st));
+                  ls::rhs_scatter<CZ>(zlive, zk, dlive, nlive, N, c->st);
+                  if (mixed) {
+                    op_apply<CZ>(c, nlive, zlive, (CZ*)wlive);
+                    LS_CUDA(cudaMemsetAsync(wz, 0, tot * sizeof(CZ), c->st));
+                    ls::rhs_scatter<CZ>((const CZ*)wlive, wz, dlive, nlive, N, c->st);
+                  } else {
+                    op_apply<double2>(c, nlive, (const double2*)zlive, (double2*)wlive);
+                    LS_CUDA(cudaMemsetAsync(w, 0, tot * sizeof(double2), c->st));
+                    ls::rhs_scatter<double2>((const double2*)wlive, w, dlive, nlive, N, c->st);
+                  }
+                });
       const double2* const* dV = c->dV;
       // CGS2 against V[0..k]
       if (mixed) {

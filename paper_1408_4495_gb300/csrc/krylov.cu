@@ -190,4 +190,29 @@ template void update_u<double2>(const double2* const*, int, const double2*, int,
 template void cast<double2, float2>(const double2*, float2*, long, cudaStream_t);
 template void cast<float2, double2>(const float2*, double2*, long, cudaStream_t);
 
+// ---- right-hand-side subsets (the ones still iterating)
+template <typename T, bool SCATTER>
+__global__ void k_rhs_move(const T* __restrict__ src, T* __restrict__ dst, const int* __restrict__ idx, int n, long N) {
+  const long tot = (long)n * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    const long i = e / N, k = e - i * N;
+    const long j = idx[i];
+    if (SCATTER) dst[j * N + k] = src[e];
+    else dst[e] = src[j * N + k];
+  }
+}
+
+template <typename T> void rhs_gather(const T* src, T* dst, const int* idx, int n, long N, cudaStream_t st) {
+  if (n <= 0) return;
+  LS_LAUNCH("kr_move", st, k_rhs_move<T, false><<<1024, 256, 0, st>>>(src, dst, idx, n, N));
+}
+template <typename T> void rhs_scatter(const T* src, T* dst, const int* idx, int n, long N, cudaStream_t st) {
+  if (n <= 0) return;
+  LS_LAUNCH("kr_move", st, k_rhs_move<T, true><<<1024, 256, 0, st>>>(src, dst, idx, n, N));
+}
+template void rhs_gather<double2>(const double2*, double2*, const int*, int, long, cudaStream_t);
+template void rhs_gather<float2>(const float2*, float2*, const int*, int, long, cudaStream_t);
+template void rhs_scatter<double2>(const double2*, double2*, const int*, int, long, cudaStream_t);
+template void rhs_scatter<float2>(const float2*, float2*, const int*, int, long, cudaStream_t);
+
 }  // namespace ls

@@ -22,5 +22,9 @@ template <typename Cz>
 void update_u(const Cz* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs, cudaStream_t st);
 void residual(const double2* g, const double2* Au, double2* r, long tot, cudaStream_t st);
 template <typename Cin, typename Cout> void cast(const Cin* in, Cout* out, long tot, cudaStream_t st);
+// dst[i] = src[idx[i]] (gather) or dst[idx[i]] = src[i] (scatter) for i < n right-hand
+// sides of N entries each; idx on the device
+template <typename T> void rhs_gather(const T* src, T* dst, const int* idx, int n, long N, cudaStream_t st);
+template <typename T> void rhs_scatter(const T* src, T* dst, const int* idx, int n, long N, cudaStream_t st);
 
 }  // namespace ls
