@@ -25,11 +25,13 @@
 #include "alloc.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "ffloat.cuh"
 #include "krylov.h"
 #include "ls.h"
 #include "prof.h"
 
 using ls::Error;
+using ls::ffc;
 using cd = std::complex<double>;
 
 struct DevBuf {
@@ -248,10 +250,11 @@ void op_apply_ff(ls_ctx* c, int nrhs, const double2* u, double2* y, const double
 }
 
 // z = M^{-1} [A;B] v for FP64 input v; z in the factor precision C
-template <typename C> void precond_apply(ls_ctx* c, int nrhs, const double2* v, C* z) {
+// z = M^{-1} [A;B] v for v in FP64 or FP32 pairs; z in the factor precision C
+template <typename C, typename Cv = double2> void precond_apply(ls_ctx* c, int nrhs, const Cv* v, C* z) {
   C* r = buf<C>(c, sizeof(C) == 8 ? "pre_r32" : "pre_r64", (size_t)nrhs * c->N);
   const void* alpha = sizeof(C) == 8 ? (const void*)c->alpha32 : (const void*)c->alpha64;
-  ls::stencil_apply<double2, C>(c->d, c->n, nrhs, v, r, 1, c->N, alpha, c->st);
+  ls::stencil_apply<Cv, C>(c->d, c->n, nrhs, v, r, 1, c->N, alpha, c->st);
   ls::nd_solve<C>(c->nd, nrhs, r, z, c->st);
 }
 
@@ -281,6 +284,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
   double2* partial = buf<double2>(c, "partial", (size_t)nrhs * (R + 2) * nblk);
   double2* hd = buf<double2>(c, "hcol", (size_t)nrhs * (R + 2) * 2);
   double* sd = buf<double>(c, "scale", nrhs);
+  ffc* hff = mixed ? buf<ffc>(c, "h_ff", (size_t)nrhs * (R + 2) * 2) : nullptr;
   double2* yd = buf<double2>(c, "ycoef", (size_t)nrhs * R);
 
   LS_CUDA(cudaMemsetAsync(u, 0, tot * sizeof(double2), c->st));
@@ -323,7 +327,8 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       s[(size_t)j * (R + 1)] = act[j] ? rn[j] : 0.0;
     }
     LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    ls::scale(r, c->V[0], sd, N, nrhs, c->st);
+    if (mixed) ls::scale_ff<double2>(r, (ffc*)c->V[0], sd, N, nrhs, c->st);
+    else ls::scale(r, c->V[0], sd, N, nrhs, c->st);
     int k = 0;
     for (; k < R; ++k) {
       bool live = false;
@@ -343,13 +348,15 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
                        (mixed ? ":m" : ":d"),
                 [&] {
                   if (!compact) {
-                    precond_apply<CZ>(c, nrhs, c->V[k], zk);
+                    if (mixed) precond_apply<CZ, ffc>(c, nrhs, (const ffc*)c->V[k], zk);
+                    else precond_apply<CZ>(c, nrhs, c->V[k], zk);
                     if (mixed) op_apply<CZ>(c, nrhs, zk, wz);
                     else op_apply<double2>(c, nrhs, (const double2*)zk, w);
                     return;
                   }
                   ls::rhs_gather<double2>(c->V[k], vlive, dlive, nlive, N, c->st);
-                  precond_apply<CZ>(c, nlive, vlive, zlive);
+                  if (mixed) precond_apply<CZ, ffc>(c, nlive, (const ffc*)vlive, zlive);
+                  else precond_apply<CZ>(c, nlive, vlive, zlive);
                   LS_CUDA(cudaMemsetAsync(zk, 0, tot * sizeof(CZ), c->st));
                   ls::rhs_scatter<CZ>(zlive, zk, dlive, nlive, N, c->st);
                   if (mixed) {
@@ -364,17 +371,23 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
                 });
       const double2* const* dV = c->dV;
       // CGS2 against V[0..k]
+      double2* hd2 = hd + (size_t)nrhs * (R + 2);
       if (mixed) {
-        ls::dots<CZ>(dV, k + 1, wz, N, nrhs, partial, hd, R + 2, false, c->st);
-        ls::sub_proj<CZ>(dV, k + 1, wz, w, hd, R + 2, N, nrhs, c->st);
+        // the basis and w as FP32 pairs: every product on the FP32 pipes
+        const ffc* const* dVf = reinterpret_cast<const ffc* const*>(dV);
+        ffc* wf = reinterpret_cast<ffc*>(w);
+        ls::dots_ff<CZ>(dVf, k + 1, wz, N, nrhs, partial, hd, R + 2, false, c->st);
+        ls::sub_proj_ff<CZ>(dVf, k + 1, wz, wf, hd, R + 2, N, nrhs, hff, c->st);
+        ls::dots_ff<ffc>(dVf, k + 1, wf, N, nrhs, partial, hd2, R + 2, false, c->st);
+        ls::sub_proj_ff<ffc>(dVf, k + 1, wf, wf, hd2, R + 2, N, nrhs, hff, c->st);
+        ls::norms2_ff(wf, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
       } else {
         ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd, R + 2, false, c->st);
         ls::sub_proj<double2>(dV, k + 1, w, w, hd, R + 2, N, nrhs, c->st);
+        ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd2, R + 2, false, c->st);
+        ls::sub_proj<double2>(dV, k + 1, w, w, hd2, R + 2, N, nrhs, c->st);
+        ls::norms2<double2>(w, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
       }
-      double2* hd2 = hd + (size_t)nrhs * (R + 2);
-      ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd2, R + 2, false, c->st);
-      ls::sub_proj<double2>(dV, k + 1, w, w, hd2, R + 2, N, nrhs, c->st);
-      ls::norms2<double2>(w, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
       LS_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
       LS_CUDA(cudaStreamSynchronize(c->st));
       for (int j = 0; j < nrhs; ++j) {
@@ -409,7 +422,8 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
         else sc[j] = 1.0 / beta;
       }
       LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
-      ls::scale(w, c->V[k + 1], sd, N, nrhs, c->st);
+      if (mixed) ls::scale_ff<ffc>((const ffc*)w, (ffc*)c->V[k + 1], sd, N, nrhs, c->st);
+      else ls::scale(w, c->V[k + 1], sd, N, nrhs, c->st);
     }
     // least squares: H(0:k, 0:k) y = s(0:k), per right-hand side
     int kmax = 0;

@@ -3,7 +3,10 @@
 // norms, scaling, the solution update u += Z y and the residual g - A u.  Every vector is
 // laid out [nrhs][N] (complex128); reductions are two-stage with a fixed summation order,
 // so results do not depend on scheduling.
+#include <type_traits>
+
 #include "common.cuh"
+#include "ffloat.cuh"
 #include "krylov.h"
 #include "prof.h"
 
@@ -214,5 +217,185 @@ template void rhs_gather<double2>(const double2*, double2*, const int*, int, lon
 template void rhs_gather<float2>(const float2*, float2*, const int*, int, long, cudaStream_t);
 template void rhs_scatter<double2>(const double2*, double2*, const int*, int, long, cudaStream_t);
 template void rhs_scatter<float2>(const float2*, float2*, const int*, int, long, cudaStream_t);
+
+// ---- float-float variants for the mixed path: the Arnoldi basis and the projected vector
+// are kept as FP32 pairs (ffc, 16 bytes per complex like FP64), and every product and sum
+// runs on the FP32 pipes (GB300 issues FP32 at 64 times its FP64 rate).  Partial sums leave
+// the blocks as FP64 for the ordered cross-block reduction.
+
+__device__ __forceinline__ ffc ff_of(float2 v) {
+  ffc r;
+  r.x = ff(v.x, 0.f);
+  r.y = ff(v.y, 0.f);
+  return r;
+}
+__device__ __forceinline__ ffc ff_of(ffc v) { return v; }
+__device__ __forceinline__ ffc ldff(const ffc* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  ffc r;
+  r.x = ff(v.x, v.y);
+  r.y = ff(v.z, v.w);
+  return r;
+}
+__device__ __forceinline__ void stff(ffc* p, ffc v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
+}
+template <typename Cw> __device__ __forceinline__ ffc ldw(const Cw* p) { return ff_of(*p); }
+template <> __device__ __forceinline__ ffc ldw<ffc>(const ffc* p) { return ldff(p); }
+
+// conj(a) * b
+__device__ __forceinline__ ffc ff_cconjmul(ffc a, ffc b) {
+  ffc r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.x * b.y - a.y * b.x;
+  return r;
+}
+__device__ __forceinline__ ffc ff_cmul(ffc a, ffc b) {
+  ffc r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+__device__ __forceinline__ ff ff_shfl_down(ff v, int o) {
+  return ff(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+}
+
+// sum of v over the CTA in FP64 (thread 0); FP32-pair adds within warps
+__device__ __forceinline__ double2 block_sum_ff(ffc v, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x = v.x + ff_shfl_down(v.x, o);
+    v.y = v.y + ff_shfl_down(v.y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = make_double2(ff_to(v.x), ff_to(v.y));
+  __syncthreads();
+  double2 r = make_double2(0, 0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { r.x += sh[i].x; r.y += sh[i].y; }
+  __syncthreads();
+  return r;
+}
+
+template <typename Cw>
+__global__ void __launch_bounds__(KT) k_dots_ff(const ffc* const* __restrict__ V, int nv, const Cw* __restrict__ w,
+                                                long N, double2* __restrict__ partial, int nblk) {
+  __shared__ double2 sh[KT / 32];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  const long chunk = (N + nblk - 1) / nblk;
+  const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
+  const Cw* wr = w + (size_t)rhs * N;
+  for (int j = 0; j < nv; ++j) {
+    const ffc* vr = V[j] + (size_t)rhs * N;
+    ffc acc;
+    acc.x = ff(0);
+    acc.y = ff(0);
+    for (long i = i0 + threadIdx.x; i < i1; i += KT) {
+      const ffc t = ff_cconjmul(ldff(vr + i), ldw(wr + i));
+      acc.x = acc.x + t.x;
+      acc.y = acc.y + t.y;
+    }
+    const double2 s = block_sum_ff(acc, sh);
+    if (threadIdx.x == 0) partial[((size_t)rhs * nv + j) * nblk + blk] = s;
+  }
+}
+
+// hf[i] = h[i] as FP32 pairs
+__global__ void k_h_to_ff(const double2* __restrict__ h, ffc* hf, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) stff(hf + i, ffc_from(h[i]));
+}
+
+// wout = win - sum_j V_j h[rhs][j]; one right-hand side per grid row, h as FP32 pairs
+template <typename Cw>
+__global__ void __launch_bounds__(256) k_sub_proj_ff(const ffc* const* __restrict__ V, int nv, const Cw* __restrict__ win,
+                                                     ffc* wout, const ffc* __restrict__ hf, int hstride, long N) {
+  const int rhs = blockIdx.y;
+  const ffc* hr = hf + (size_t)rhs * hstride;
+  const size_t base = (size_t)rhs * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    ffc acc = ldw(win + base + i);
+    for (int j = 0; j < nv; ++j) {
+      const ffc t = ff_cmul(ldff(V[j] + base + i), ldff(hr + j));
+      acc.x = acc.x - t.x;
+      acc.y = acc.y - t.y;
+    }
+    stff(wout + base + i, acc);
+  }
+}
+
+__global__ void __launch_bounds__(KT) k_norm2_ff(const ffc* __restrict__ w, long N, double2* partial, int nblk) {
+  __shared__ double2 sh[KT / 32];
+  const int rhs = blockIdx.y, blk = blockIdx.x;
+  const long chunk = (N + nblk - 1) / nblk;
+  const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
+  const ffc* wr = w + (size_t)rhs * N;
+  ffc acc;
+  acc.x = ff(0);
+  acc.y = ff(0);
+  for (long i = i0 + threadIdx.x; i < i1; i += KT) {
+    const ffc v = ldff(wr + i);
+    acc.x = acc.x + (v.x * v.x + v.y * v.y);
+  }
+  const double2 s = block_sum_ff(acc, sh);
+  if (threadIdx.x == 0) partial[(size_t)rhs * nblk + blk] = s;
+}
+
+// out[rhs] = in[rhs] * scale[rhs] as FP32 pairs; in FP64 (the residual) or FP32 pairs
+template <typename Cin>
+__global__ void k_scale_ff(const Cin* __restrict__ in, ffc* out, const double* __restrict__ scale, long N) {
+  const int rhs = blockIdx.y;
+  const ff s = ff_from(scale[rhs]);
+  const size_t base = (size_t)rhs * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    ffc v;
+    if constexpr (std::is_same<Cin, double2>::value) v = ffc_from(in[base + i]);
+    else v = ldff(in + base + i);
+    v.x = v.x * s;
+    v.y = v.y * s;
+    stff(out + base + i, v);
+  }
+}
+
+static dim3 grid_rows(long N, int nrhs) {
+  long b = (N + 255) / 256;
+  const long cap = (152L * 16 + nrhs - 1) / nrhs;
+  if (b > cap) b = cap;
+  return dim3((unsigned)(b < 1 ? 1 : b), nrhs);
+}
+
+template <typename Cw>
+void dots_ff(const ffc* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride,
+             bool accumulate, cudaStream_t st) {
+  const int nblk = dots_blocks(N);
+  LS_LAUNCH("kr_dots", st, k_dots_ff<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk));
+  LS_LAUNCH("kr_reduce", st,
+            k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, accumulate ? 1 : 0));
+}
+
+template <typename Cw>
+void sub_proj_ff(const ffc* const* V, int nv, const Cw* win, ffc* wout, const double2* h, int hstride, long N, int nrhs,
+                 ffc* hf, cudaStream_t st) {
+  const int count = nrhs * hstride;
+  LS_LAUNCH("kr_scale", st, k_h_to_ff<<<(count + 255) / 256, 256, 0, st>>>(h, hf, count));
+  LS_LAUNCH("kr_sub_proj", st, k_sub_proj_ff<Cw><<<grid_rows(N, nrhs), 256, 0, st>>>(V, nv, win, wout, hf, hstride, N));
+}
+
+void norms2_ff(const ffc* w, long N, int nrhs, double2* partial, double2* out, int ostride, cudaStream_t st) {
+  const int nblk = dots_blocks(N);
+  LS_LAUNCH("kr_norm2", st, k_norm2_ff<<<dim3(nblk, nrhs), KT, 0, st>>>(w, N, partial, nblk));
+  LS_LAUNCH("kr_reduce", st, k_reduce<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, 1, nrhs, nblk, out, ostride, 0));
+}
+
+template <typename Cin> void scale_ff(const Cin* in, ffc* out, const double* s, long N, int nrhs, cudaStream_t st) {
+  LS_LAUNCH("kr_scale", st, k_scale_ff<Cin><<<grid_rows(N, nrhs), 256, 0, st>>>(in, out, s, N));
+}
+
+template void dots_ff<float2>(const ffc* const*, int, const float2*, long, int, double2*, double2*, int, bool, cudaStream_t);
+template void dots_ff<ffc>(const ffc* const*, int, const ffc*, long, int, double2*, double2*, int, bool, cudaStream_t);
+template void sub_proj_ff<float2>(const ffc* const*, int, const float2*, ffc*, const double2*, int, long, int, ffc*,
+                                  cudaStream_t);
+template void sub_proj_ff<ffc>(const ffc* const*, int, const ffc*, ffc*, const double2*, int, long, int, ffc*,
+                               cudaStream_t);
+template void scale_ff<double2>(const double2*, ffc*, const double*, long, int, cudaStream_t);
+template void scale_ff<ffc>(const ffc*, ffc*, const double*, long, int, cudaStream_t);
 
 }  // namespace ls

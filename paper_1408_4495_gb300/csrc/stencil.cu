@@ -6,10 +6,18 @@
 // adjacent points are shared in L1.  The coefficient table (3^d classes x 3^d offsets)
 // is staged in shared memory.
 #include "common.cuh"
+#include "ffloat.cuh"
 #include "kernels.h"
 #include "prof.h"
 
 namespace ls {
+
+// one input entry in the output arithmetic (float-float input: its leading FP32 part)
+template <typename Cout, typename Cin> __device__ __forceinline__ Cout ld_in(const Cin* p) { return ccast<Cout>(__ldg(p)); }
+template <> __device__ __forceinline__ float2 ld_in<float2, ffc>(const ffc* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return make_float2(v.x, v.z);
+}
 
 template <typename Cin, typename Cout, int D>
 __global__ void __launch_bounds__(256) k_stencil(int n, int nrhs, const Cin* __restrict__ v, Cout* __restrict__ r,
@@ -40,7 +48,7 @@ __global__ void __launch_bounds__(256) k_stencil(int n, int nrhs, const Cin* __r
         for (int t1 = -1; t1 <= 1; ++t1) {
           const int a0 = c[0] + t0, a1 = c[1] + t1;
           if (a0 >= 0 && a0 < n && a1 >= 0 && a1 < n) {
-            const Cout x = ccast<Cout>(__ldg(&vr[(long)a0 * n + a1]));
+            const Cout x = ld_in<Cout>(&vr[(long)a0 * n + a1]);
             acc = cfma(acc, al[(t0 + 1) * 3 + (t1 + 1)], x);
           }
         }
@@ -53,7 +61,7 @@ __global__ void __launch_bounds__(256) k_stencil(int n, int nrhs, const Cin* __r
           for (int t2 = -1; t2 <= 1; ++t2) {
             const int a0 = c[0] + t0, a1 = c[1] + t1, a2 = c[2] + t2;
             if (a0 >= 0 && a0 < n && a1 >= 0 && a1 < n && a2 >= 0 && a2 < n) {
-              const Cout x = ccast<Cout>(__ldg(&vr[((long)a0 * n + a1) * n + a2]));
+              const Cout x = ld_in<Cout>(&vr[((long)a0 * n + a1) * n + a2]);
               acc = cfma(acc, al[((t0 + 1) * 3 + (t1 + 1)) * 3 + (t2 + 1)], x);
             }
           }
@@ -78,6 +86,7 @@ void stencil_apply(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, lon
 }
 
 template void stencil_apply<float2, float2>(int, int, int, const float2*, float2*, long, long, const void*, cudaStream_t);
+template void stencil_apply<ffc, float2>(int, int, int, const ffc*, float2*, long, long, const void*, cudaStream_t);
 template void stencil_apply<double2, float2>(int, int, int, const double2*, float2*, long, long, const void*, cudaStream_t);
 template void stencil_apply<double2, double2>(int, int, int, const double2*, double2*, long, long, const void*, cudaStream_t);
 
