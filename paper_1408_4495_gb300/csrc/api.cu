@@ -376,10 +376,11 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
         // the basis and w as FP32 pairs: every product on the FP32 pipes
         const ffc* const* dVf = reinterpret_cast<const ffc* const*>(dV);
         ffc* wf = reinterpret_cast<ffc*>(w);
-        ls::dots_ff<CZ>(dVf, k + 1, wz, N, nrhs, partial, hd, R + 2, false, c->st);
-        ls::sub_proj_ff<CZ>(dVf, k + 1, wz, wf, hd, R + 2, N, nrhs, hff, c->st);
-        ls::dots_ff<ffc>(dVf, k + 1, wf, N, nrhs, partial, hd2, R + 2, false, c->st);
-        ls::sub_proj_ff<ffc>(dVf, k + 1, wf, wf, hd2, R + 2, N, nrhs, hff, c->st);
+        ffc* hff2 = hff + (size_t)nrhs * (R + 2);
+        ls::dots_ff<CZ>(dVf, k + 1, wz, N, nrhs, partial, hd, hff, R + 2, c->st);
+        ls::sub_proj_ff<CZ>(dVf, k + 1, wz, wf, hff, R + 2, N, nrhs, c->st);
+        ls::dots_ff<ffc>(dVf, k + 1, wf, N, nrhs, partial, hd2, hff2, R + 2, c->st);
+        ls::sub_proj_ff<ffc>(dVf, k + 1, wf, wf, hff2, R + 2, N, nrhs, c->st);
         ls::norms2_ff(wf, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
       } else {
         ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd, R + 2, false, c->st);

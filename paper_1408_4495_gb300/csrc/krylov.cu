@@ -49,9 +49,13 @@ __global__ void __launch_bounds__(KT) k_dots(const double2* const* __restrict__ 
   }
 }
 
-// out[rhs * ostride + j] = sum_blk partial  (ordered), optionally accumulated into out
+struct ffc;
+__device__ void store_ff_pair(void* outf, size_t i, double2 v);
+
+// out[rhs * ostride + j] = sum_blk partial  (ordered), optionally accumulated into out; with
+// outf, also the result as FP32 pairs at the same index
 __global__ void k_reduce(const double2* __restrict__ partial, int nv, int nrhs, int nblk, double2* out, int ostride,
-                         int accumulate) {
+                         int accumulate, void* outf = nullptr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nv * nrhs) return;
   const int rhs = t / nv, j = t % nv;
@@ -61,6 +65,7 @@ __global__ void k_reduce(const double2* __restrict__ partial, int nv, int nrhs, 
   double2* o = out + (size_t)rhs * ostride + j;
   if (accumulate) { o->x += s.x; o->y += s.y; }
   else *o = s;
+  if (outf) store_ff_pair(outf, (size_t)rhs * ostride + j, *o);
 }
 
 // wout = win - sum_j V_j h[rhs][j]
@@ -240,6 +245,8 @@ __device__ __forceinline__ ffc ldff(const ffc* p) {
 __device__ __forceinline__ void stff(ffc* p, ffc v) {
   *reinterpret_cast<float4*>(p) = make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
 }
+__device__ void store_ff_pair(void* outf, size_t i, double2 v) { stff(reinterpret_cast<ffc*>(outf) + i, ffc_from(v)); }
+
 template <typename Cw> __device__ __forceinline__ ffc ldw(const Cw* p) { return ff_of(*p); }
 template <> __device__ __forceinline__ ffc ldw<ffc>(const ffc* p) { return ldff(p); }
 
@@ -297,11 +304,6 @@ __global__ void __launch_bounds__(KT) k_dots_ff(const ffc* const* __restrict__ V
     const double2 s = block_sum_ff(acc, sh);
     if (threadIdx.x == 0) partial[((size_t)rhs * nv + j) * nblk + blk] = s;
   }
-}
-
-// hf[i] = h[i] as FP32 pairs
-__global__ void k_h_to_ff(const double2* __restrict__ h, ffc* hf, int count) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) stff(hf + i, ffc_from(h[i]));
 }
 
 // wout = win - sum_j V_j h[rhs][j]; one right-hand side per grid row, h as FP32 pairs
@@ -363,19 +365,17 @@ static dim3 grid_rows(long N, int nrhs) {
 }
 
 template <typename Cw>
-void dots_ff(const ffc* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, int ostride,
-             bool accumulate, cudaStream_t st) {
+void dots_ff(const ffc* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, ffc* outf,
+             int ostride, cudaStream_t st) {
   const int nblk = dots_blocks(N);
   LS_LAUNCH("kr_dots", st, k_dots_ff<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk));
   LS_LAUNCH("kr_reduce", st,
-            k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, accumulate ? 1 : 0));
+            k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, 0, outf));
 }
 
 template <typename Cw>
-void sub_proj_ff(const ffc* const* V, int nv, const Cw* win, ffc* wout, const double2* h, int hstride, long N, int nrhs,
-                 ffc* hf, cudaStream_t st) {
-  const int count = nrhs * hstride;
-  LS_LAUNCH("kr_scale", st, k_h_to_ff<<<(count + 255) / 256, 256, 0, st>>>(h, hf, count));
+void sub_proj_ff(const ffc* const* V, int nv, const Cw* win, ffc* wout, const ffc* hf, int hstride, long N, int nrhs,
+                 cudaStream_t st) {
   LS_LAUNCH("kr_sub_proj", st, k_sub_proj_ff<Cw><<<grid_rows(N, nrhs), 256, 0, st>>>(V, nv, win, wout, hf, hstride, N));
 }
 
@@ -389,12 +389,11 @@ template <typename Cin> void scale_ff(const Cin* in, ffc* out, const double* s, 
   LS_LAUNCH("kr_scale", st, k_scale_ff<Cin><<<grid_rows(N, nrhs), 256, 0, st>>>(in, out, s, N));
 }
 
-template void dots_ff<float2>(const ffc* const*, int, const float2*, long, int, double2*, double2*, int, bool, cudaStream_t);
-template void dots_ff<ffc>(const ffc* const*, int, const ffc*, long, int, double2*, double2*, int, bool, cudaStream_t);
-template void sub_proj_ff<float2>(const ffc* const*, int, const float2*, ffc*, const double2*, int, long, int, ffc*,
-                                  cudaStream_t);
-template void sub_proj_ff<ffc>(const ffc* const*, int, const ffc*, ffc*, const double2*, int, long, int, ffc*,
-                               cudaStream_t);
+template void dots_ff<float2>(const ffc* const*, int, const float2*, long, int, double2*, double2*, ffc*, int,
+                              cudaStream_t);
+template void dots_ff<ffc>(const ffc* const*, int, const ffc*, long, int, double2*, double2*, ffc*, int, cudaStream_t);
+template void sub_proj_ff<float2>(const ffc* const*, int, const float2*, ffc*, const ffc*, int, long, int, cudaStream_t);
+template void sub_proj_ff<ffc>(const ffc* const*, int, const ffc*, ffc*, const ffc*, int, long, int, cudaStream_t);
 template void scale_ff<double2>(const double2*, ffc*, const double*, long, int, cudaStream_t);
 template void scale_ff<ffc>(const ffc*, ffc*, const double*, long, int, cudaStream_t);
 

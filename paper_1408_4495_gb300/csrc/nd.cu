@@ -1417,7 +1417,11 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     const size_t gjm = gj_smem<C>(L.smax, L.ncols);
     // the children's Schur complements: by a GPU-wide kernel, or inside the Gauss-Jordan
     // CTA when they are small (one CTA per front would serialise large ones)
-    const bool gj = gjm <= GJ_SMEM_MAX;
+    // Gauss-Jordan in one CTA for the small fronts (up to 16 own rows); the register sweeps,
+    // whose trailing updates spread over many CTAs, for the larger ones (measured on 2D
+    // n = 256: 1 % faster with the 32-row levels on the register path, 6 % slower with
+    // the 8- and 16-row levels there too)
+    const bool gj = gjm <= GJ_SMEM_MAX && (L.smax <= 16 || L.smax > 32 * reg_rpl_max<C>());
     const bool fused_ea = gj && has_child && Ch.bmax < 48;
     if (has_child && !fused_ea) {
       const long tot = (long)Ch.bmax * Ch.bmax;
