@@ -909,6 +909,109 @@ __global__ void __launch_bounds__(512) k_panel_rows(LevelK<C> L, int k0, int k1,
   if (t == 0) swp[(size_t)z * SWP_STRIDE] = cnt;
 }
 
+// Panel [k0, k1) on at most 256 own rows, one row per thread held in registers (the column
+// loops are unrolled, so every register index is a constant).  Per column one barrier: each
+// warp's best live row (largest |re| + |im|, lowest row on ties, as k_panel_rows) publishes
+// its key and its whole row to a parity-double-buffered slot before the barrier; after it
+// every thread picks the winning warp and updates its own row from the winner's slot with
+// broadcast shared-memory reads.  The panel rows are then written to their logical
+// positions (local to k0): pivot j to position j; the rows at positions < w that were not
+// chosen fill, in increasing order, the positions >= w whose rows were chosen.  Any
+// consistent row order is valid: the same permutation, recorded in swp, is applied to the
+// trailing columns and to the identity block.
+template <typename C>
+__global__ void __launch_bounds__(256) k_panel_reg(LevelK<C> L, int k0, int k1, int* __restrict__ swp, int* err) {
+  using Rl = typename RealOf<C>::T;
+  __shared__ __align__(16) C slot[2][8][NB];
+  __shared__ unsigned skey[2][8], sidx[2][8];
+  __shared__ int vac[NB];
+  __shared__ int wcnt[8];
+  __shared__ int cnt;
+  const int z = blockIdx.x, r = threadIdx.x, lane = r & 31, wid = r >> 5, nw = blockDim.x >> 5;
+  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
+  C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;  // local (r, c) at A[c * fmax + r]
+  const bool has = r < R;
+  C a[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) a[c] = (has && c < w) ? A[(size_t)c * fmax + r] : czero<C>();
+  if (r == 0) cnt = 0;
+  bool live = has;
+  int jp = -1;  // the column at which this row was chosen as pivot
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < w) {
+      const int par = j & 1;
+      const unsigned key = live ? __float_as_uint((float)(fabs(a[j].x) + fabs(a[j].y))) : 0u;
+      const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+      const unsigned iw = __reduce_min_sync(0xffffffffu, (live && key == kw) ? (unsigned)r : 0xffffffffu);
+      if (iw == (unsigned)r) {
+#pragma unroll
+        for (int c = j; c < NB; ++c) slot[par][wid][c] = a[c];
+      }
+      if (lane == 0) {
+        skey[par][wid] = kw;
+        sidx[par][wid] = iw;
+      }
+      __syncthreads();
+      const unsigned k2 = lane < nw ? skey[par][lane] : 0u;
+      const unsigned s2 = lane < nw ? sidx[par][lane] : 0xffffffffu;
+      const unsigned km = __reduce_max_sync(0xffffffffu, s2 != 0xffffffffu ? k2 : 0u);
+      const unsigned bw = __reduce_min_sync(0xffffffffu, (s2 != 0xffffffffu && k2 == km) ? (unsigned)lane : 0xffffffffu);
+      if (bw == 0xffffffffu) {  // no live row left (cannot happen while j < R)
+        if (r == 0) atomicExch(err, 1);
+        continue;
+      }
+      if (km == 0u && r == 0) atomicExch(err, 1);
+      const int bi = (int)sidx[par][bw];
+      if (r == bi) {
+        live = false;
+        jp = j;
+      }
+      if (live) {
+        const C* pr = slot[par][bw];
+        const C d = pr[j];
+        const Rl den = cabs2(d);
+        const Rl rden = den > 0 ? recip(den) : (Rl)0;
+        C inv;
+        inv.x = d.x * rden;
+        inv.y = -d.y * rden;
+        const C m = cmul(a[j], inv);
+        a[j] = m;
+#pragma unroll
+        for (int c = j + 1; c < NB; ++c) a[c] = cfms(a[c], m, pr[c]);
+      }
+    }
+  }
+  // positions >= w vacated by pivots, in increasing order
+  const bool vp = jp >= 0 && r >= w;
+  const unsigned bv = __ballot_sync(0xffffffffu, vp);
+  if (lane == 0) wcnt[wid] = __popc(bv);
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  if (vp) {
+    int before = 0;
+    for (int q = 0; q < wid; ++q) before += wcnt[q];
+    vac[before + __popc(bv & lt)] = r;
+  }
+  __syncthreads();
+  // rows at positions < w not chosen (all in warp 0) take the vacated positions in order
+  const bool dp = has && jp < 0 && r < w;
+  const unsigned bd = __ballot_sync(0xffffffffu, dp);
+  const int pos = jp >= 0 ? jp : (dp ? vac[__popc(bd & lt)] : r);
+  if (has) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < w) A[(size_t)c * fmax + pos] = a[c];
+    if (pos != r) {
+      const int q = atomicAdd(&cnt, 1);
+      swp[(size_t)z * SWP_STRIDE + 1 + 2 * q] = pos;
+      swp[(size_t)z * SWP_STRIDE + 2 + 2 * q] = r;
+    }
+  }
+  __syncthreads();
+  if (r == 0) swp[(size_t)z * SWP_STRIDE] = cnt;
+}
+
 // One warp per column c in [k1, ncols): local rows p = 32 q + lane of [k0, smax) in slot q,
 // loaded through the panel's permutation; x_p -= L_pi x_i for i < w, p > i (forward
 // substitution inside the block, update below it).  The panel L is staged in shared
@@ -1345,8 +1448,11 @@ template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* s
     const int G = 512 / r32 >= 4 ? 4 : (512 / r32 >= 2 ? 2 : 1);
     const int threads = r32 * G;
     const size_t psmem = (size_t)R * (NB + 1) * sizeof(C) + 2 * (size_t)R * sizeof(int);
-    LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-              k_panel_rows<C><<<L.nf, threads, psmem, st>>>(L, k0, k1, swp, err));
+    if (R <= 256)
+      LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st, k_panel_reg<C><<<L.nf, r32, 0, st>>>(L, k0, k1, swp, err));
+    else
+      LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                k_panel_rows<C><<<L.nf, threads, psmem, st>>>(L, k0, k1, swp, err));
     const int m = L.ncols - k1;
     const size_t smem = (size_t)(k1 - k0) * R * sizeof(C) + (size_t)R * sizeof(int);
     LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
