@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdio>
 #include <string>
 
@@ -43,12 +44,19 @@ template <typename C> __host__ __device__ __forceinline__ C cdiv(C a, C b) {
   typename RealOf<C>::T den = b.x * b.x + b.y * b.y;
   C r; r.x = (a.x * b.x + a.y * b.y) / den; r.y = (a.y * b.x - a.x * b.y) / den; return r;
 }
-// multiply-subtract: acc - a*b
+__host__ __device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+// multiply-subtract acc - a*b and multiply-add acc + a*b: each component is two chained
+// FMAs into the accumulator (four instructions per complex product instead of six)
 template <typename C> __host__ __device__ __forceinline__ C cfms(C acc, C a, C b) {
-  acc.x -= a.x * b.x - a.y * b.y; acc.y -= a.x * b.y + a.y * b.x; return acc;
+  acc.x = rfma(-a.x, b.x, acc.x); acc.x = rfma(a.y, b.y, acc.x);
+  acc.y = rfma(-a.x, b.y, acc.y); acc.y = rfma(-a.y, b.x, acc.y);
+  return acc;
 }
 template <typename C> __host__ __device__ __forceinline__ C cfma(C acc, C a, C b) {
-  acc.x += a.x * b.x - a.y * b.y; acc.y += a.x * b.y + a.y * b.x; return acc;
+  acc.x = rfma(a.x, b.x, acc.x); acc.x = rfma(-a.y, b.y, acc.x);
+  acc.y = rfma(a.x, b.y, acc.y); acc.y = rfma(a.y, b.x, acc.y);
+  return acc;
 }
 
 template <typename Cto, typename Cfrom> __host__ __device__ __forceinline__ Cto ccast(Cfrom a) {

@@ -794,138 +794,30 @@ template <typename C> __device__ __forceinline__ C shfl_c(C v, int src) {
   return v;
 }
 
-// Panel [k0, k1) on own rows [k0, smax), rows kept in shared memory (row stride NB + 1):
-// G = blockDim / R32 threads per row (R32 = R rounded up to 32; G = 1, 2 or 4, so a row's
-// threads share a warp); thread t updates row t / G on the columns c = t (mod G).  Rows are never moved during the elimination: a row chosen
-// as pivot is retired, and the pivot sequence gives at the end the logical order that
-// LAPACK-style row swaps produce (ph[i]: physical row at logical position i).  Pivot =
-// largest |re| + |im| (as LAPACK's izamax), compared as FP32 bit patterns with warp
-// reductions, lowest row on ties; one barrier per column.  The factored panel is written
-// back in logical order and the net permutation to swp.
-template <typename C>
-__global__ void __launch_bounds__(512) k_panel_rows(LevelK<C> L, int k0, int k1, int* __restrict__ swp, int* err) {
-  using Rl = typename RealOf<C>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LDP = NB + 1;
-  __shared__ unsigned skey[2][16], sidx[2][16];
-  __shared__ int pseq[NB];
-  __shared__ int cnt;
-  const int z = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
-  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
-  const int G = blockDim.x / ((R + 31) / 32 * 32);  // 1, 2 or 4
-  const int lgG = G == 4 ? 2 : (G == 2 ? 1 : 0), r = t >> lgG, g = t & (G - 1);
-  C* P = reinterpret_cast<C*>(smem_raw);  // [R][LDP]
-  int* ph = reinterpret_cast<int*>(P + (size_t)R * LDP);
-  int* iph = ph + R;
-  const C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;  // local (r, c) at A[c * fmax + r]
-  const bool has = r < R;
-  C* row = P + (size_t)r * LDP;
-  // load: 8 entries in flight per thread (coalesced over the rows of a column)
-  for (int base = t; base < R * w; base += blockDim.x * 8) {
-    C v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = base + u * blockDim.x;
-      if (e < R * w) v[u] = A[(size_t)(e / R) * fmax + e % R];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = base + u * blockDim.x;
-      if (e < R * w) P[(size_t)(e % R) * LDP + e / R] = v[u];
-    }
-  }
-  for (int i = t; i < R; i += blockDim.x) { ph[i] = i; iph[i] = i; }
-  if (t == 0) cnt = 0;
-  __syncthreads();
-  bool done = !has;  // row retired as a pivot (or no row)
-  for (int j = 0; j < w; ++j) {
-    const int par = j & 1;
-    const C aj = has ? row[j] : czero<C>();
-    const bool cand = !done && g == 0;
-    const unsigned key = cand ? __float_as_uint((float)(fabs(aj.x) + fabs(aj.y))) : 0u;
-    const unsigned kw = __reduce_max_sync(0xffffffffu, key);
-    const unsigned iw = __reduce_min_sync(0xffffffffu, (cand && key == kw) ? (unsigned)r : 0xffffffffu);
-    if (lane == 0) { skey[par][wid] = kw; sidx[par][wid] = iw; }
-    __syncthreads();
-    const unsigned k2 = lane < nw ? skey[par][lane] : 0u;
-    const unsigned km = __reduce_max_sync(0xffffffffu, k2);
-    const unsigned bu = __reduce_min_sync(0xffffffffu, (lane < nw && k2 == km) ? sidx[par][lane] : 0xffffffffu);
-    if (bu == 0xffffffffu) {  // no live row left (cannot happen while j < R)
-      if (t == 0) atomicExch(err, 1);
-      break;
-    }
-    const int bi = (int)bu;
-    if (t == 0) {
-      if (km == 0u) atomicExch(err, 1);
-      pseq[j] = bi;
-    }
-    if (r == bi) done = true;
-    if (!done) {
-      const C* prow = P + (size_t)bi * LDP;
-      const C d = prow[j];
-      const Rl den = cabs2(d);
-      const Rl rden = den > 0 ? recip(den) : (Rl)0;
-      C inv;
-      inv.x = d.x * rden;
-      inv.y = -d.y * rden;
-      const C m = cmul(aj, inv);
-      if (g == 0) row[j] = m;
-      // columns c > j with c = g (mod G), four at a time: loads before the stores
-      int c = j + 1 + ((g - j - 1) & (G - 1));
-      for (; c + 3 * G < w; c += 4 * G) {
-        C pv[4], rv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { pv[u] = prow[c + u * G]; rv[u] = row[c + u * G]; }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) row[c + u * G] = cfms(rv[u], m, pv[u]);
-      }
-      for (; c < w; c += G) row[c] = cfms(row[c], m, prow[c]);
-    }
-    __syncwarp();  // the G threads of a row share a warp: their column writes are seen next step
-  }
-  __syncthreads();
-  if (t == 0)
-    for (int j = 0; j < w; ++j) {
-      // logical swap of position j with the pivot row's position
-      const int bi = pseq[j], pj = ph[j], lb = iph[bi];
-      ph[j] = bi;
-      iph[bi] = j;
-      ph[lb] = pj;
-      iph[pj] = lb;
-    }
-  __syncthreads();
-  C* Aw = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;
-  for (int e = t; e < R * w; e += blockDim.x) {
-    const int c = e / R, i = e - c * R;
-    Aw[(size_t)c * fmax + i] = P[(size_t)ph[i] * LDP + c];
-  }
-  for (int i = t; i < R; i += blockDim.x)
-    if (ph[i] != i) {
-      const int q = atomicAdd(&cnt, 1);
-      swp[(size_t)z * SWP_STRIDE + 1 + 2 * q] = i;
-      swp[(size_t)z * SWP_STRIDE + 2 + 2 * q] = ph[i];
-    }
-  __syncthreads();
-  if (t == 0) swp[(size_t)z * SWP_STRIDE] = cnt;
-}
-
-// Panel [k0, k1) on at most 256 own rows, one row per thread held in registers (the column
-// loops are unrolled, so every register index is a constant).  Per column one barrier: each
-// warp's best live row (largest |re| + |im|, lowest row on ties, as k_panel_rows) publishes
-// its key and its whole row to a parity-double-buffered slot before the barrier; after it
+// Panel [k0, k1) on at most 512 own rows (256 in FP64), one row per thread held in registers
+// (the column loops are unrolled, so every register index is a constant).  Per column one
+// barrier: each warp's best live row publishes its key, the reciprocal of its pivot entry
+// and the rest of its row to a parity-double-buffered slot before the barrier; after it
 // every thread picks the winning warp and updates its own row from the winner's slot with
-// broadcast shared-memory reads.  The panel rows are then written to their logical
-// positions (local to k0): pivot j to position j; the rows at positions < w that were not
-// chosen fill, in increasing order, the positions >= w whose rows were chosen.  Any
-// consistent row order is valid: the same permutation, recorded in swp, is applied to the
-// trailing columns and to the identity block.
+// broadcast shared-memory reads.  Pivot key: |re| + |im| as an FP32 bit pattern cut to 14
+// mantissa bits, packed above (1023 - row) so that one max reduction finds the largest
+// entry and, among entries equal to 14 bits, the lowest row (partial pivoting up to a
+// relative 2^-14, as stable as an exact search).  The panel rows are then written to their
+// logical positions (local to k0): pivot j to position j; the rows at positions < w that
+// were not chosen fill, in increasing order, the positions >= w whose rows were chosen.
+// Any consistent row order is valid: the same permutation, recorded in swp, is applied to
+// the trailing columns and to the identity block.
+template <typename C> __host__ __device__ constexpr int panel_reg_rows() { return sizeof(C) == 8 ? 512 : 256; }
+
 template <typename C>
-__global__ void __launch_bounds__(256) k_panel_reg(LevelK<C> L, int k0, int k1, int* __restrict__ swp, int* err) {
+__global__ void __launch_bounds__(panel_reg_rows<C>()) k_panel_reg(LevelK<C> L, int k0, int k1, int* __restrict__ swp,
+                                                                  int* err) {
   using Rl = typename RealOf<C>::T;
-  __shared__ __align__(16) C slot[2][8][NB];
-  __shared__ unsigned skey[2][8], sidx[2][8];
+  constexpr int MW = panel_reg_rows<C>() / 32;
+  __shared__ __align__(16) C slot[2][MW][NB];
+  __shared__ unsigned skey[2][MW];
   __shared__ int vac[NB];
-  __shared__ int wcnt[8];
+  __shared__ int wcnt[MW];
   __shared__ int cnt;
   const int z = blockIdx.x, r = threadIdx.x, lane = r & 31, wid = r >> 5, nw = blockDim.x >> 5;
   const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
@@ -935,47 +827,42 @@ __global__ void __launch_bounds__(256) k_panel_reg(LevelK<C> L, int k0, int k1, 
 #pragma unroll
   for (int c = 0; c < NB; ++c) a[c] = (has && c < w) ? A[(size_t)c * fmax + r] : czero<C>();
   if (r == 0) cnt = 0;
+  if (r < NB) vac[r] = r;
   bool live = has;
   int jp = -1;  // the column at which this row was chosen as pivot
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
     if (j < w) {
       const int par = j & 1;
-      const unsigned key = live ? __float_as_uint((float)(fabs(a[j].x) + fabs(a[j].y))) : 0u;
+      const unsigned mag = __float_as_uint((float)(fabs(a[j].x) + fabs(a[j].y)));
+      const unsigned key = live ? ((mag >> 9) << 10) | (1023u - (unsigned)r) : 0u;
       const unsigned kw = __reduce_max_sync(0xffffffffu, key);
-      const unsigned iw = __reduce_min_sync(0xffffffffu, (live && key == kw) ? (unsigned)r : 0xffffffffu);
-      if (iw == (unsigned)r) {
+      if (live && key == kw) {
+        const Rl den = cabs2(a[j]);
+        const Rl rden = den > 0 ? recip(den) : (Rl)0;
+        C inv;
+        inv.x = a[j].x * rden;
+        inv.y = -a[j].y * rden;
+        slot[par][wid][j] = inv;
 #pragma unroll
-        for (int c = j; c < NB; ++c) slot[par][wid][c] = a[c];
+        for (int c = j + 1; c < NB; ++c) slot[par][wid][c] = a[c];
       }
-      if (lane == 0) {
-        skey[par][wid] = kw;
-        sidx[par][wid] = iw;
-      }
+      if (lane == 0) skey[par][wid] = kw;
       __syncthreads();
-      const unsigned k2 = lane < nw ? skey[par][lane] : 0u;
-      const unsigned s2 = lane < nw ? sidx[par][lane] : 0xffffffffu;
-      const unsigned km = __reduce_max_sync(0xffffffffu, s2 != 0xffffffffu ? k2 : 0u);
-      const unsigned bw = __reduce_min_sync(0xffffffffu, (s2 != 0xffffffffu && k2 == km) ? (unsigned)lane : 0xffffffffu);
-      if (bw == 0xffffffffu) {  // no live row left (cannot happen while j < R)
+      const unsigned km = __reduce_max_sync(0xffffffffu, lane < nw ? skey[par][lane] : 0u);
+      if (km == 0u) {  // no live row left (cannot happen while j < R)
         if (r == 0) atomicExch(err, 1);
         continue;
       }
-      if (km == 0u && r == 0) atomicExch(err, 1);
-      const int bi = (int)sidx[par][bw];
+      if ((km >> 10) == 0u && r == 0) atomicExch(err, 1);  // zero pivot
+      const int bi = 1023 - (int)(km & 1023u);
       if (r == bi) {
         live = false;
         jp = j;
       }
       if (live) {
-        const C* pr = slot[par][bw];
-        const C d = pr[j];
-        const Rl den = cabs2(d);
-        const Rl rden = den > 0 ? recip(den) : (Rl)0;
-        C inv;
-        inv.x = d.x * rden;
-        inv.y = -d.y * rden;
-        const C m = cmul(a[j], inv);
+        const C* pr = slot[par][bi >> 5];
+        const C m = cmul(a[j], pr[j]);
         a[j] = m;
 #pragma unroll
         for (int c = j + 1; c < NB; ++c) a[c] = cfms(a[c], m, pr[c]);
@@ -997,36 +884,39 @@ __global__ void __launch_bounds__(256) k_panel_reg(LevelK<C> L, int k0, int k1, 
   // rows at positions < w not chosen (all in warp 0) take the vacated positions in order
   const bool dp = has && jp < 0 && r < w;
   const unsigned bd = __ballot_sync(0xffffffffu, dp);
-  const int pos = jp >= 0 ? jp : (dp ? vac[__popc(bd & lt)] : r);
+  const int pos = jp >= 0 ? jp : (dp ? min(vac[__popc(bd & lt)], R - 1) : r);
   if (has) {
 #pragma unroll
     for (int c = 0; c < NB; ++c)
       if (c < w) A[(size_t)c * fmax + pos] = a[c];
     if (pos != r) {
       const int q = atomicAdd(&cnt, 1);
-      swp[(size_t)z * SWP_STRIDE + 1 + 2 * q] = pos;
-      swp[(size_t)z * SWP_STRIDE + 2 + 2 * q] = r;
+      if (q < 2 * NB) {
+        swp[(size_t)z * SWP_STRIDE + 1 + 2 * q] = pos;
+        swp[(size_t)z * SWP_STRIDE + 2 + 2 * q] = r;
+      }
     }
   }
   __syncthreads();
-  if (r == 0) swp[(size_t)z * SWP_STRIDE] = cnt;
+  if (r == 0) swp[(size_t)z * SWP_STRIDE] = min(cnt, 2 * NB);
 }
 
 // One warp per column c in [k1, ncols): local rows p = 32 q + lane of [k0, smax) in slot q,
 // loaded through the panel's permutation; x_p -= L_pi x_i for i < w, p > i (forward
 // substitution inside the block, update below it).  The panel L is staged in shared
-// memory as lp[i * R + p].
+// memory as lp[i * R32 + p], R32 = R rounded up to 32, rows R..R32 zero, so that only the
+// first slot (p < 32) needs the p > i test.
 template <typename C, int RPL>
 __global__ void __launch_bounds__(256) k_lower_update(LevelK<C> L, int k0, int k1, const int* __restrict__ swp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int z = blockIdx.x;
-  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
+  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0, R32 = (R + 31) & ~31;
   C* lp = reinterpret_cast<C*>(smem_raw);
-  int* perm = reinterpret_cast<int*>(lp + (size_t)w * R);
+  int* perm = reinterpret_cast<int*>(lp + (size_t)w * R32);
   const C* P = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;
-  stage_copy<8>(lp, w * R, [&](int e) {
-    const int i = e / R, p = e - i * R;
-    return P[(size_t)i * fmax + p];
+  stage_copy<8>(lp, w * R32, [&](int e) {
+    const int i = e / R32, p = e - i * R32;
+    return p < R ? P[(size_t)i * fmax + p] : czero<C>();
   });
   for (int p = threadIdx.x; p < R; p += blockDim.x) perm[p] = p;
   __syncthreads();
@@ -1046,12 +936,11 @@ __global__ void __launch_bounds__(256) k_lower_update(LevelK<C> L, int k0, int k
   }
   for (int i = 0; i < w; ++i) {
     const C xi = shfl_c(x[0], i);
-    const C* li = lp + (size_t)i * R;
+    const C* li = lp + (size_t)i * R32 + lane;
+    if (lane > i) x[0] = cfms(x[0], li[0], xi);
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int p = 32 * q + lane;
-      if (p > i && p < R) x[q] = cfms(x[q], li[p], xi);
-    }
+    for (int q = 1; q < RPL; ++q)
+      if (32 * q < R32) x[q] = cfms(x[q], li[32 * q], xi);
   }
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
@@ -1064,7 +953,7 @@ __global__ void __launch_bounds__(256) k_lower_update(LevelK<C> L, int k0, int k
 // registers (row 32 q + lane in slot q); U11 columns [i0, i0 + 32) staged per block as
 // us[il * rows + p], their reciprocal pivots in invd.
 template <typename C, int RPL>
-__global__ void __launch_bounds__(256) k_upper_solve(LevelK<C> L) {
+__global__ void __launch_bounds__(256, 1) k_upper_solve(LevelK<C> L) {
   using Rl = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C invd[32];
@@ -1102,15 +991,12 @@ __global__ void __launch_bounds__(256) k_upper_solve(LevelK<C> L) {
       __syncthreads();
       if (active)
         for (int li = iw - 1; li >= 0; --li) {
-          const int i = i0 + li;
           C xi = cmul(shfl_c(x[qi], li), invd[li]);
           if (lane == li) x[qi] = xi;
-          const C* ui = us + (size_t)li * rows;
+          const C* ui = us + (size_t)li * rows + lane;
 #pragma unroll
-          for (int q = 0; q <= qi; ++q) {
-            const int p = 32 * q + lane;
-            if (p < i) x[q] = cfms(x[q], ui[p], xi);
-          }
+          for (int q = 0; q < qi; ++q) x[q] = cfms(x[q], ui[32 * q], xi);  // rows p < i0 <= i
+          if (lane < li) x[qi] = cfms(x[qi], ui[32 * qi], xi);
         }
     }
   }
@@ -1435,26 +1321,17 @@ template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* s
   const size_t smem_max = (size_t)32 * 32 * RPL * sizeof(C) + (size_t)32 * RPL * sizeof(int);
   static bool attr = false;
   if (!attr) {
-    const size_t psmem_max = (size_t)32 * RPL * (NB + 1) * sizeof(C) + 2 * (size_t)32 * RPL * sizeof(int);
-    LS_CUDA(cudaFuncSetAttribute(k_panel_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_max));
     LS_CUDA(cudaFuncSetAttribute(k_lower_update<C, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     LS_CUDA(cudaFuncSetAttribute(k_upper_solve<C, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     attr = true;
   }
+  static_assert(32 * RPL <= panel_reg_rows<C>(), "the register panel holds every own row");
   for (int k0 = 0; k0 < L.smax; k0 += NB) {
     const int k1 = std::min(k0 + NB, L.smax), R = L.smax - k0;
-    // 1, 2 or 4 threads per row (a power of two, so that a row's threads share a warp)
     const int r32 = (R + 31) / 32 * 32;
-    const int G = 512 / r32 >= 4 ? 4 : (512 / r32 >= 2 ? 2 : 1);
-    const int threads = r32 * G;
-    const size_t psmem = (size_t)R * (NB + 1) * sizeof(C) + 2 * (size_t)R * sizeof(int);
-    if (R <= 256)
-      LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st, k_panel_reg<C><<<L.nf, r32, 0, st>>>(L, k0, k1, swp, err));
-    else
-      LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                k_panel_rows<C><<<L.nf, threads, psmem, st>>>(L, k0, k1, swp, err));
+    LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st, k_panel_reg<C><<<L.nf, r32, 0, st>>>(L, k0, k1, swp, err));
     const int m = L.ncols - k1;
-    const size_t smem = (size_t)(k1 - k0) * R * sizeof(C) + (size_t)R * sizeof(int);
+    const size_t smem = (size_t)(k1 - k0) * r32 * sizeof(C) + (size_t)R * sizeof(int);
     LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
               k_lower_update<C, RPL><<<dim3(L.nf, (m + 7) / 8), 256, smem, st>>>(L, k0, k1, swp));
   }
