@@ -27,6 +27,11 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   with n (``mie.py``).                                                          pinned
 * the sparsity claim A K ~ C (Sec. 2.2): reported ratio only, the paper prints
   no magnitude.                                                  parity unpinned
+* Laplace variant (Sec. 5, ``omega = 0`` in 3D, ``point_source``, ``laplace_solve``):
+  harmonicity and unit flux of 1/(4 pi r); k_0 = a^2/2 by ball quadrature and as the
+  omega -> 0 limit of the Helmholtz weight; the point-source right-hand side equals the
+  Green's function at the grid offsets; V = 0 gives u = g; dense solve of (I + K V) u = g;
+  stencil optimality for the Laplace kernel.                                  pinned
 """
 
 from .ls_oracle import *  # noqa: F401,F403

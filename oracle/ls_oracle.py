@@ -25,7 +25,7 @@ __all__ = [
     "dense_K", "apply_K_direct", "apply_K_fft", "apply_operator", "plane_wave", "rhs",
     "point_class", "class_mu", "class_far_set", "stencil", "all_stencils",
     "assemble", "nd_order", "Preconditioner", "gmres_right", "solve",
-    "check_buffer", "sparsity_ratio",
+    "check_buffer", "sparsity_ratio", "point_source", "laplace_solve",
 ]
 
 
@@ -46,9 +46,14 @@ def grid_coords(n: int, d: int):
 
 def green(d: int, omega: float, r):
     """Free-space Green's function of -(Delta + omega^2) at distance r > 0 (Sec. 1):
-    2D ``(i/4) H_0^(1)(omega r)``, 3D ``exp(i omega r) / (4 pi r)``."""
+    2D ``(i/4) H_0^(1)(omega r)``, 3D ``exp(i omega r) / (4 pi r)``.
+
+    omega = 0 in 3D is the Laplace Green's function 1 / (4 pi r) of Sec. 5 (the same
+    formula); the 2D Laplace kernel is not part of the paper and is refused."""
     r = np.asarray(r, dtype=np.float64)
     if d == 2:
+        if omega == 0:
+            raise ValueError("the Laplace variant (omega = 0) is three-dimensional (Sec. 5)")
         return 0.25j * sp.hankel1(0, omega * r)
     if d == 3:
         return np.exp(1j * omega * r) / (4.0 * np.pi * r)
@@ -66,12 +71,18 @@ def k0_weight(d: int, omega: float, h: float) -> complex:
         so k_0 = (i pi a / (2 omega)) H_1^(1)(omega a) - 1/omega^2.
     3D, a = h (3/(4 pi))^(1/3):  int_0^a r e^{i omega r} dr
         so k_0 = e^{i omega a}(1/omega^2 - i a/omega) - 1/omega^2.
+    3D Laplace (omega = 0, Sec. 5):  int_0^a (1/(4 pi r)) 4 pi r^2 dr = a^2 / 2, the
+        omega -> 0 limit of the 3D form.
     """
     if d == 2:
+        if omega == 0:
+            raise ValueError("the Laplace variant (omega = 0) is three-dimensional (Sec. 5)")
         a = h / math.sqrt(math.pi)
         return complex(1j * math.pi * a / (2.0 * omega) * sp.hankel1(1, omega * a) - 1.0 / omega**2)
     if d == 3:
         a = h * (3.0 / (4.0 * math.pi)) ** (1.0 / 3.0)
+        if omega == 0:
+            return complex(a * a / 2.0)
         return complex(np.exp(1j * omega * a) * (1.0 / omega**2 - 1j * a / omega) - 1.0 / omega**2)
     raise ValueError("d must be 2 or 3")
 
@@ -164,6 +175,15 @@ def rhs(ktab, omega: float, m: np.ndarray, direction, direct: bool = False,
     uI = plane_wave(n, d, omega, direction)
     v = -(omega**2) * m * uI
     return apply_K_direct(ktab, v) if direct else apply_K_fft(ktab, v, workers)
+
+
+def point_source(ktab, n: int, d: int, point, strength: complex = 1.0) -> np.ndarray:
+    """Right-hand side g = K f of Sec. 5 for a delta source of the given strength at the
+    grid point ``point`` (0-based multi-index): the discrete delta is f_j = strength / h^d
+    at j = point and 0 elsewhere (unit mass on the cell), so g_i = strength k_{i-point} / h^d."""
+    f = np.zeros((n,) * d, dtype=np.complex128)
+    f[tuple(point)] = strength / grid_h(n) ** d
+    return apply_K_fft(ktab, f)
 
 
 def check_buffer(m: np.ndarray, b: int) -> bool:
@@ -463,6 +483,44 @@ def solve(n: int, d: int, omega: float, m: np.ndarray, directions, b: int = 2,
     for dr in directions:
         g = rhs(ktab, omega, m, dr, workers=workers).reshape(-1)
         u, it, _ = gmres_right(A, Pf, g, tol, restart, max_iter)
+        gn = np.linalg.norm(g)
+        res.append(np.linalg.norm(g - A(u)) / gn if gn > 0 else 0.0)
+        us.append(u)
+        its.append(it)
+        gs.append(g)
+    return dict(u=np.array(us), iters=its, resid=res, g=np.array(gs), P=P, ktab=ktab,
+                sten=sten, cint=cint)
+
+
+def laplace_solve(n: int, V: np.ndarray, points, b: int = 2, tol: float = 1e-6,
+                  restart: int = 50, max_iter: int = 500, workers=None, strengths=None):
+    """Sec. 5: (I + K V) u = K f in 3D with the Laplace kernel k_t = h^3 / (4 pi h |t|),
+    k_0 = a^2 / 2, and delta sources f at the given grid points.
+
+    The sparsifying preconditioner is built exactly as in Secs. 2-3 from this kernel
+    (Sec. 5 applies it without modification): the stencils are the SVD minimisers of
+    K(mu, far) for the Laplace table, and M = [A + C V ; B].  The operator and M need only
+    the product omega^2 m of the Helmholtz case, which is V here; the functions above are
+    called with omega = 1 and m = V for those two steps and with omega = 0 for the kernel.
+    Returns dict with u (nsrc, n^3), iterations, true relative residuals, g."""
+    d = 3
+    V = np.asarray(V, dtype=np.float64)
+    if not check_buffer(V, b):
+        raise ValueError("V must vanish within b+1 layers of the boundary")
+    ktab = kernel_table(n, d, 0.0)
+    sten, cint = all_stencils(n, d, 0.0, b)
+    M, S = assemble(n, d, 1.0, V, sten, cint)
+    P = Preconditioner(M, S, n, d)
+    shape = (n,) * d
+
+    def A(x):
+        return apply_operator(ktab, 1.0, V, x.reshape(shape), workers=workers).reshape(-1)
+
+    us, its, res, gs = [], [], [], []
+    for k, pt in enumerate(points):
+        q = 1.0 if strengths is None else strengths[k]
+        g = point_source(ktab, n, d, pt, q).reshape(-1)
+        u, it, _ = gmres_right(A, P, g, tol, restart, max_iter)
         gn = np.linalg.norm(g)
         res.append(np.linalg.norm(g - A(u)) / gn if gn > 0 else 0.0)
         us.append(u)

@@ -14,6 +14,9 @@ stand-ins of the same shape:
 * ``bumps``: sum of Gaussian bumps A exp(-|x-c|^2 / (2 w^2)) times the cutoff.
 * ``smooth_noise``: white noise convolved with a Gaussian of width 4h, scaled to a given
   max |m|, times the cutoff.
+* ``laplace_3d``: the potentials of Sec. 5 (a negative Gaussian, or a smoothed indicator of
+  a ball, scaled so that max |V| = 1/h^2 as in the paper's tables) times the cutoff, and
+  delta sources near the top-left corner of the middle cross-section x_1 = 1/2.
 """
 
 from __future__ import annotations
@@ -148,3 +151,47 @@ def enforce_buffer(m: np.ndarray, b: int) -> np.ndarray:
         sl[a] = slice(n - w, n)
         m[tuple(sl)] = 0.0
     return m
+
+
+@dataclass
+class LaplaceWorkload:
+    name: str
+    n: int
+    V: np.ndarray = field(repr=False)
+    points: np.ndarray = field(repr=False)  # (nsrc, 3) 0-based grid indices of the sources
+    mixed: bool = True
+    buffer_b: int = 2
+    restart: int = 50
+    tol: float = 1e-6
+
+    @property
+    def nrhs(self) -> int:
+        return len(self.points)
+
+
+def laplace_3d(n: int = 64, nsrc: int = 8, shape: str = "gaussian", seed: int = 1005) -> LaplaceWorkload:
+    """Sec. 5 stand-in: V = -(1/h^2) S(x) times the cutoff with S a Gaussian bump
+    exp(-|x-c|^2 / (2 w^2)), w = 0.1, or a ball indicator smoothed over 0.05 (radius 0.25),
+    c = (1/2, 1/2, 1/2); sources: the first at the grid point nearest (1/2, 1/4, 3/4), the
+    others at seeded offsets of up to 4 grid steps in the cross-section, all distinct."""
+    X = np.meshgrid(*([grid_x(n)] * 3), indexing="ij")
+    r = np.sqrt(sum((X[a] - 0.5) ** 2 for a in range(3)))
+    if shape == "gaussian":
+        S = np.exp(-r * r / (2 * 0.1 * 0.1))
+    elif shape == "ball":
+        S = _smooth_step((0.25 - r) / 0.05 + 0.5)
+    else:
+        raise ValueError("shape must be 'gaussian' or 'ball'")
+    h = 1.0 / (n + 1)
+    V = -(1.0 / (h * h)) * S * cutoff(n, 3)
+    base = np.array([round(0.5 / h) - 1, round(0.25 / h) - 1, round(0.75 / h) - 1])
+    rng = np.random.default_rng(seed)
+    pts = [base]
+    seen = {tuple(base)}
+    while len(pts) < nsrc:
+        q = base + np.concatenate([[0], rng.integers(-4, 5, 2)])
+        q = np.clip(q, 0, n - 1)
+        if tuple(q) not in seen:
+            seen.add(tuple(q))
+            pts.append(q)
+    return LaplaceWorkload(f"3d_laplace_{shape}_n{n}", n, V, np.array(pts, dtype=np.int64))

@@ -1,0 +1,123 @@
+"""Pins of the oracle's Laplace variant (Sec. 5): (I + K V) u = K f in 3D with the Green's
+function 1 / (4 pi r), delta sources, and the sparsifying preconditioner built from the
+Laplace kernel without modification.
+
+Each check is fixed by the mathematics rather than by re-calling the oracle's routine: the
+Green's function is harmonic away from the source, k_0 is a quadrature over the ball and the
+omega -> 0 limit of the Helmholtz weight, the point-source right-hand side is the Green's
+function itself at the grid offsets, a zero potential makes both the operator and the
+preconditioner the identity, and the GMRES solve equals a dense solve of the system.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+
+import oracle as O
+from paper_1408_4495_gb300 import workloads as W
+
+
+def test_laplace_green_is_harmonic_with_unit_source():
+    # 4th-order central Laplacian of 1/(4 pi r) vanishes away from 0; flux of -grad G
+    # through a sphere is 1 (the source of -Delta G = delta has unit mass)
+    dl = 2e-3
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        x = rng.uniform(0.2, 0.8, 3) * rng.choice([-1, 1], 3)
+        lap = 0.0
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = dl
+            f = lambda y: float(np.real(O.green(3, 0.0, np.linalg.norm(y))))
+            lap += (-f(x + 2 * e) + 16 * f(x + e) - 30 * f(x) + 16 * f(x - e) - f(x - 2 * e)) / (12 * dl * dl)
+        assert abs(lap) < 1e-6 * abs(O.green(3, 0.0, np.linalg.norm(x))) / np.dot(x, x)
+    r, dr = 0.3, 1e-5
+    dG = (O.green(3, 0.0, r + dr) - O.green(3, 0.0, r - dr)) / (2 * dr)
+    assert abs(-dG * 4 * math.pi * r * r - 1.0) < 1e-8
+
+
+def test_laplace_green_refused_in_2d():
+    with pytest.raises(ValueError):
+        O.green(2, 0.0, 0.5)
+    with pytest.raises(ValueError):
+        O.k0_weight(2, 0.0, 0.1)
+
+
+@pytest.mark.parametrize("h", [1 / 17, 1 / 65, 0.1])
+def test_laplace_k0_is_the_integral_over_the_equal_volume_ball(h):
+    # the reading of k_0: integral of G over the ball of volume h^3, by radial quadrature
+    a = (3 * h**3 / (4 * math.pi)) ** (1 / 3)
+    ref = si.quad(lambda r: 4 * math.pi * r * r / (4 * math.pi * r), 0, a, epsabs=0, epsrel=1e-13)[0]
+    assert abs(O.k0_weight(3, 0.0, h) - ref) < 1e-13 * ref
+    # and the omega -> 0 limit of the Helmholtz weight (first-order term i omega a^3 / 3)
+    w = 1e-2
+    hz = O.k0_weight(3, w, h)
+    assert abs(hz.real - ref) < 1e-6 * ref
+    assert abs(hz.imag - w * a**3 / 3) < 1e-6 * w * a**3
+
+
+@pytest.mark.parametrize("n,point", [(8, (3, 1, 6)), (16, (7, 3, 12)), (16, (0, 15, 5))])
+def test_point_source_is_the_green_function_at_the_grid_offsets(n, point):
+    # g = K f for a unit-mass discrete delta: g_i = G(h |i - p|) away from p, k_0 / h^3 at p
+    h = O.grid_h(n)
+    kt = O.kernel_table(n, 3, 0.0)
+    g = O.point_source(kt, n, 3, point, 2.5 - 1j)
+    idx = np.stack(np.meshgrid(*([np.arange(n)] * 3), indexing="ij"), axis=-1)
+    r = h * np.linalg.norm(idx - np.array(point), axis=-1)
+    ref = np.where(r > 0, 1.0 / (4 * math.pi * np.where(r > 0, r, 1.0)),
+                   (3 / (4 * math.pi)) ** (2 / 3) / (2 * h))  # a^2 / 2 / h^3
+    ref = (2.5 - 1j) * ref
+    assert np.max(np.abs(g - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_laplace_zero_potential_gives_u_equals_g():
+    # V = 0: A = I and M = [A;B] = S, so P = I; one iteration reaches the tolerance
+    n = 16
+    w = W.laplace_3d(n, 2)
+    r = O.laplace_solve(n, np.zeros((n,) * 3), w.points, tol=1e-10)
+    assert r["iters"] == [1, 1]
+    assert np.max(np.abs(r["u"] - r["g"])) < 1e-11 * np.max(np.abs(r["g"]))
+
+
+def test_laplace_solve_equals_dense_solve():
+    n = 10
+    h = O.grid_h(n)
+    w = W.laplace_3d(n, 2, seed=7)
+    V = W.enforce_buffer(w.V, 2)
+    assert np.min(V) < -0.5 / h**2
+    r = O.laplace_solve(n, V, w.points, tol=1e-12)
+    K = O.dense_K(O.kernel_table(n, 3, 0.0), n, 3)
+    A = np.eye(n**3) + K * V.reshape(-1)[None, :]
+    for j in range(2):
+        u = np.linalg.solve(A, r["g"][j])
+        assert np.linalg.norm(r["u"][j] - u) < 1e-9 * np.linalg.norm(u)
+        assert r["resid"][j] < 1e-11
+
+
+@pytest.mark.parametrize("cls", [(0, 0, 0), (1, 0, 0), (1, -1, 1)])
+def test_laplace_stencil_is_unit_and_optimal(cls):
+    n, d, b = 8, 3, 2
+    mu, alpha, S = O.stencil(n, d, 0.0, b, cls, return_sigma=True)
+    far = O.class_far_set(n, b, cls)
+    K = O.kernel_value(d, 0.0, O.grid_h(n), np.array(mu)[:, None, :] - far[None, :, :])
+    assert abs(np.linalg.norm(alpha) - 1) < 1e-14
+    assert abs(np.linalg.norm(alpha @ K) - S[-1]) < 1e-12 * S[0]
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        beta = rng.standard_normal(len(mu)) + 1j * rng.standard_normal(len(mu))
+        beta /= np.linalg.norm(beta)
+        assert np.linalg.norm(beta @ K) >= np.linalg.norm(alpha @ K) * (1 - 1e-12)
+    # the Laplace kernel is real, so the minimiser is real once the centre is made positive
+    assert np.max(np.abs(alpha.imag)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", ["gaussian", "ball"])
+def test_laplace_iterations_stay_in_the_papers_band(shape):
+    # Sec. 5 tables: 5-7 iterations with max|V| = 1/h^2 (qualitative band, not a value)
+    n = 16
+    w = W.laplace_3d(n, 2, shape)
+    r = O.laplace_solve(n, W.enforce_buffer(w.V, 2), w.points, tol=1e-6)
+    assert all(1 <= it <= 10 for it in r["iters"])
+    assert all(res <= 1e-6 for res in r["resid"])
