@@ -276,9 +276,10 @@ def run_gpu(args):
         _, info = s.solve(g, TOL, out=u)
         return info
 
-    def timed(s, steps, warmup, prof_class=None, clocks=False):
+    def timed(s, steps, warmup, prof_class=None, clocks=False, step_fn=None):
+        step_fn = step_fn or step
         for _ in range(warmup):
-            step(s)
+            step_fn(s)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -294,7 +295,7 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            infos.append(step(s))
+            infos.append(step_fn(s))
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -355,6 +356,45 @@ def run_gpu(args):
     its64 = [i.iters for inf in infos64 for i in inf]
     s64.close()
 
+    # ---- Sec. 5 Laplace variant beside it: 3D n = 64, Gaussian potential with max|V| ~ 1/h^2,
+    # 8 delta sources; one step = ls_factor + ls_rhs_point_source + ls_solve
+    from paper_1408_4495_gb300 import workloads as W
+    lw = W.laplace_3d(64, 8, "gaussian", 1005)
+    V_dev = torch.tensor(W.enforce_buffer(lw.V, 2), device=dev)
+    pts_dev = torch.tensor(lw.points.astype(np.int32), device=dev)
+    lshape = (lw.nrhs,) + (lw.n,) * 3
+    gl = torch.empty(lshape, dtype=torch.complex128, device=dev)
+    ul = torch.empty(lshape, dtype=torch.complex128, device=dev)
+    s_lap = ls.Solver(V_dev, dim=3, buffer_b=lw.buffer_b, restart=lw.restart, mixed=True, stream=stream, laplace=True)
+
+    def lap_step(s):
+        s.factor()
+        s.rhs_point_source(pts_dev, out=gl)
+        _, info = s.solve(gl, TOL, out=ul)
+        return info
+
+    kl = max(2, min(args.steps, 5))
+    ms_l, infos_l, _, _ = timed(s_lap, kl, 2, step_fn=lap_step)
+    nd_l = s_lap.nd_stats()
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_lap.solve(gl, TOL, out=ul)  # completes any pending factorization before the events
+    fe0.record(stream)
+    s_lap.factor()
+    fe1.record(stream)
+    s_lap.precond(gl[:1].clone())  # waits for the factorization (it reports its errors)
+    torch.cuda.synchronize()
+    fac_ms = fe0.elapsed_time(fe1)
+    s_lap.close()
+    lap = {"workload": f"{lw.name}_{lw.nrhs}src", "value": job_rate(lw.nrhs * kl, world, ms_l / 1e3),
+           "unit": "solves/s", "ms_per_step": ms_l / kl, "steps": kl, "warmup": 2,
+           "step": "ls_factor + ls_rhs_point_source + ls_solve (all sources), mixed precision",
+           "iters": {"min": min(i.iters for inf in infos_l for i in inf),
+                     "max": max(i.iters for inf in infos_l for i in inf)},
+           "max_rel_resid": max(i.rel_resid for inf in infos_l for i in inf),
+           "all_converged": all(i.converged for inf in infos_l for i in inf),
+           "factor_ms": fac_ms, "factor_flops": nd_l["factor_flops"],
+           "factor_tflops": nd_l["factor_flops"] / (fac_ms / 1e3) / 1e12, "max_front": nd_l["max_front"]}
+
     # ---- end to end through the public API with host buffers (pinned)
     m_host = torch.tensor(w.m).pin_memory()
     dirs_host = torch.tensor(w.directions).pin_memory()
@@ -403,7 +443,7 @@ def run_gpu(args):
                 "max_rel_resid": max(res), "all_converged": conv,
                 "plain_fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / k64, "steps": k64,
                                "iters": {"min": min(its64), "max": max(its64)}},
-                "mixed_over_fp64": value / value64,
+                "mixed_over_fp64": value / value64, "laplace_3d": lap,
                 "setup_ms": setup_s * 1e3, "nd": nd,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "launches_by_class": prof["counts"], "device_time_shares": shares, "clocks": clocks}

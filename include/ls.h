@@ -4,6 +4,8 @@
  *   L. Ying, "Sparsifying Preconditioner for the Lippmann-Schwinger Equation", arXiv:1408.4495.
  *
  * Problem (Sec. 1, eq. ls; Sec. 2.1, eqs. lsd/lso):  (I + K omega^2 m) u = g on the grid
+ * (Sec. 5, ls_setup_laplace: (I + K V) u = g with the Laplace kernel; wherever omega^2 m
+ * appears below, read V for such a context)
  * x_i = i h, i in {1..n}^d, h = 1/(n+1), d in {2, 3}, K(i,j) = k_{i-j} the Nystrom weights
  * of the Green's function.  Preconditioner (Sec. 2.2, eq. PC): u <= M^{-1} [A;B] g with
  * M = [A + C omega^2 m ; B], factored by nested dissection (Sec. 2.2, Sec. 3.2).
@@ -89,6 +91,22 @@ typedef struct {
  *   out     receives the context; *out is NULL on failure.
  */
 ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream, ls_ctx** out);
+/*
+ * ls_setup_laplace -- Sec. 5: the 3D Laplace equation with a compactly supported potential,
+ * (-Delta + V) u = f, in Lippmann-Schwinger form (I + K V) u = K f with the Green's function
+ * 1 / (4 pi r): k_t = h^3 / (4 pi h |t|), k_0 = a^2 / 2 (a = h (3 / (4 pi))^(1/3), the integral
+ * of G over the ball of volume h^3, the omega -> 0 limit of the Helmholtz weight).  Every
+ * later step is the Helmholtz one with V in place of omega^2 m: the stencils are built from
+ * this kernel (Sec. 5: the preconditioner applies without modification), M = [A + C V; B],
+ * and ls_solve / ls_apply / ls_precond work on (I + K V).  ls_rhs_plane_wave is refused
+ * (LS_ESTATE); right-hand sides come from ls_rhs_point_source or the caller.
+ *   g       grid description (copied); g->dim must be 3 (else LS_EINVAL).
+ *   V       n^3 real doubles, C order: the potential V(x_i).  Host or device pointer; copied.
+ *           Must be finite (else LS_EINVAL) and vanish on the b+1 outermost layers (else
+ *           LS_EBUFFER); any sign (Sec. 5 takes V negative and of order 1/h^2).
+ *   stream, out   as for ls_setup.
+ */
+ls_status ls_setup_laplace(const ls_grid* g, const double* V, void* stream, ls_ctx** out);
 
 /*
  * ls_factor -- Sec. 2.2 eq. PC, Sec. 3.1 eq. ABop, Sec. 3.2: assembles M = [A + C omega^2 m; B]
@@ -110,6 +128,17 @@ ls_status ls_factor(ls_ctx* c);
  *   g_out  nrhs x n^d complex doubles, host or device, written.
  */
 ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_out);
+/*
+ * ls_rhs_point_source -- Sec. 5: g = K f for delta sources, f = q delta(x - x_p) discretised
+ * as q / h^d at the grid point p (unit mass on the cell), i.e. g_r(i) = q_r k_{i - p_r} / h^d,
+ * computed on the device in FP64 from the kernel table.  Either kernel.
+ *   nrhs       number of sources, >= 1.
+ *   points     nrhs x d ints, 0-based grid indices (i_0, .., i_{d-1}) in C order, each in
+ *              [0, n) (else LS_EINVAL); host or device.
+ *   strengths  nrhs complex doubles q_r (interleaved re, im), host or device, or NULL for 1.
+ *   g_out      nrhs x n^d complex doubles, host or device, written.
+ */
+ls_status ls_rhs_point_source(ls_ctx* c, int nrhs, const int* points, const double* strengths, double* g_out);
 
 /*
  * ls_solve -- Sec. 3.3: right-preconditioned GMRES(restart) on (I + K omega^2 m) u = g with

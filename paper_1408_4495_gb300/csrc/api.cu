@@ -53,6 +53,7 @@ struct ls_ctx {
   int d = 0, n = 0, L = 0, b = 2, restart = 50, max_iter = 500;
   long N = 0;
   double omega = 0, h = 0;
+  bool laplace = false;  // Sec. 5 kernel 1/(4 pi r), potential V in place of omega^2 m
   ls_prec prec = LS_PREC_MIXED;
   cudaStream_t st = nullptr;
   bool own_stream = false;
@@ -487,17 +488,21 @@ bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 // =======================================================================================
 extern "C" {
 
-ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream, ls_ctx** out) {
+// Shared by ls_setup (Helmholtz kernel, medium m, potential omega^2 m) and ls_setup_laplace
+// (Sec. 5: Laplace kernel, potential V given directly; omega = 0 selects the kernel).
+static ls_status setup_common(const ls_grid* g, double omega, const double* m, bool laplace, void* stream,
+                              ls_ctx** out) {
   if (out) *out = nullptr;
   ls_ctx* c = nullptr;
   try {
     if (!g || !m || !out) throw Error{ls::EINVAL_, "NULL argument"};
     if (g->dim != 2 && g->dim != 3) throw Error{ls::EINVAL_, "dim must be 2 or 3"};
+    if (laplace && g->dim != 3) throw Error{ls::EINVAL_, "the Laplace variant is three-dimensional (Sec. 5)"};
     const int n = g->n;
     if (!pow2(2 * n)) throw Error{ls::EINVAL_, "2n must be a power of two"};
     if (g->dim == 2 && (n < 16 || n > 2048)) throw Error{ls::EINVAL_, "2D needs 16 <= n <= 2048"};
     if (g->dim == 3 && (n < 8 || n > 128)) throw Error{ls::EINVAL_, "3D needs 8 <= n <= 128"};
-    if (!(omega > 0) || !std::isfinite(omega)) throw Error{ls::EINVAL_, "omega must be positive"};
+    if (!laplace && (!(omega > 0) || !std::isfinite(omega))) throw Error{ls::EINVAL_, "omega must be positive"};
     const int b = g->buffer_b > 0 ? g->buffer_b : 2;
     if (n <= 2 * (b + 1)) throw Error{ls::EINVAL_, "n too small for the buffer layers"};
     if (g->prec != LS_PREC_FP64 && g->prec != LS_PREC_MIXED) throw Error{ls::EINVAL_, "unknown precision"};
@@ -511,7 +516,8 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
     c->max_iter = g->max_iter > 0 ? g->max_iter : 500;
     c->prec = g->prec;
     c->N = c->d == 2 ? (long)n * n : (long)n * n * n;
-    c->omega = omega;
+    c->laplace = laplace;
+    c->omega = laplace ? 0.0 : omega;
     c->h = 1.0 / (n + 1);
     // LS_GRAPHS=0 runs every launch eagerly (for debugging and per-launch timing)
     if (const char* e = std::getenv("LS_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
@@ -528,7 +534,8 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
     else std::memcpy(mh.data(), m, c->N * sizeof(double));
     const int wl = b + 1;
     for (long i = 0; i < c->N; ++i) {
-      if (!std::isfinite(mh[i]) || !(1.0 - mh[i] > 0)) throw Error{ls::EINVAL_, "m must be finite with 1 - m > 0"};
+      if (!std::isfinite(mh[i])) throw Error{ls::EINVAL_, "the medium must be finite"};
+      if (!laplace && !(1.0 - mh[i] > 0)) throw Error{ls::EINVAL_, "m must satisfy 1 - m > 0"};
       long q = i;
       bool edge = false;
       for (int a = 0; a < c->d; ++a) {
@@ -536,12 +543,12 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
         q /= n;
         if (ia < wl || ia >= n - wl) edge = true;
       }
-      if (edge && mh[i] != 0.0) throw Error{ls::EBUFFER_, "m must vanish within b+1 layers of the boundary"};
+      if (edge && mh[i] != 0.0) throw Error{ls::EBUFFER_, "the medium must vanish within b+1 layers of the boundary"};
     }
     std::vector<double> w64(c->N);
     std::vector<float> w32(c->N);
     for (long i = 0; i < c->N; ++i) {
-      w64[i] = omega * omega * mh[i];
+      w64[i] = laplace ? mh[i] : omega * omega * mh[i];
       w32[i] = (float)w64[i];
     }
     c->w2m64 = dalloc<double>(c->N);
@@ -567,10 +574,10 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
     c->ktq = dalloc<double2>(nq);
     c->sym64 = dalloc<double2>(nq);
     c->sym32 = dalloc<float2>(nq);
-    ls::build_kernel_table(c->d, n, omega, c->h, c->ktq, c->st);
+    ls::build_kernel_table(c->d, n, c->omega, c->h, c->ktq, c->st);
     c->plan.d = c->d;
     c->plan.n = n;
-    c->plan.omega = omega;
+    c->plan.omega = c->omega;
     c->plan.h = c->h;
     c->plan.tw32 = c->tw32;
     c->plan.tw64 = c->tw64;
@@ -600,9 +607,9 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
       c->plan.symff = c->ffbuf + ntw;
       c->plan.w2mff = c->ffbuf + ntw + nsy;
     }
-    // stencils (Sec. 3.1), cached per (d, n, b, omega)
+    // stencils (Sec. 3.1), cached per (d, n, b, omega); omega = 0 is the Laplace kernel
     {
-      StencilKey key{c->d, n, b, omega};
+      StencilKey key{c->d, n, b, c->omega};
       bool hit = false;
       {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -648,6 +655,14 @@ ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream
   }
 }
 
+ls_status ls_setup(const ls_grid* g, double omega, const double* m, void* stream, ls_ctx** out) {
+  return setup_common(g, omega, m, false, stream, out);
+}
+
+ls_status ls_setup_laplace(const ls_grid* g, const double* V, void* stream, ls_ctx** out) {
+  return setup_common(g, 0.0, V, true, stream, out);
+}
+
 ls_status ls_factor(ls_ctx* c) {
   try {
     check_ctx(c);
@@ -671,6 +686,7 @@ ls_status ls_factor(ls_ctx* c) {
 ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_out) {
   try {
     check_ctx(c);
+    if (c->laplace) throw Error{ls::ESTATE_, "plane waves need the Helmholtz kernel (omega > 0)"};
     if (nrhs < 1 || !dirs || !g_out) throw Error{ls::EINVAL_, "bad arguments"};
     const size_t tot = (size_t)nrhs * c->N;
     double* dd = buf<double>(c, "dirs", (size_t)nrhs * c->d);
@@ -691,6 +707,37 @@ ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_o
     // float-float passes on the mixed path, FP64 on the plain path
     if (c->prec == LS_PREC_MIXED) ls::conv_rhs_ff(c->plan, nrhs, dd, gd, t1, t2, st);
     else ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, st);
+    copy_out(c, g_out, gd, tot * sizeof(double2), st);
+    LS_CUDA(cudaStreamSynchronize(st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_rhs_point_source(ls_ctx* c, int nrhs, const int* points, const double* strengths, double* g_out) {
+  try {
+    check_ctx(c);
+    if (nrhs < 1 || !points || !g_out) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t np = (size_t)nrhs * c->d;
+    std::vector<int> ph(np);
+    if (is_device_ptr(points)) LS_CUDA(cudaMemcpy(ph.data(), points, np * sizeof(int), cudaMemcpyDeviceToHost));
+    else std::memcpy(ph.data(), points, np * sizeof(int));
+    for (size_t i = 0; i < np; ++i)
+      if (ph[i] < 0 || ph[i] >= c->n) throw Error{ls::EINVAL_, "source point outside the grid"};
+    const size_t tot = (size_t)nrhs * c->N;
+    int* pd = buf<int>(c, "src_points", np);
+    double2* qd = strengths ? buf<double2>(c, "src_strengths", nrhs) : nullptr;
+    double2* gd = buf<double2>(c, "rhs_out", tot);
+    // with a factorization in flight, on the side stream (it reads only the kernel table)
+    cudaStream_t st = c->st;
+    if (c->factor_pending) {
+      st = c->st2;
+      LS_CUDA(cudaStreamWaitEvent(st, c->ev_factor, 0));
+    }
+    LS_CUDA(cudaMemcpyAsync(pd, ph.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (qd) copy_in(c, qd, strengths, (size_t)nrhs * sizeof(double2), st);
+    ls::point_source(c->d, c->n, nrhs, pd, qd, c->ktq, c->h, gd, st);
     copy_out(c, g_out, gd, tot * sizeof(double2), st);
     LS_CUDA(cudaStreamSynchronize(st));
     return LS_OK;

@@ -562,6 +562,7 @@ size_t conv_scratch2_elems(int d, int n, int nrhs) {
 // k_t for t in [0, n]^d (the table is even in every component).  2D: G = (i/4) H0(omega r),
 // 3D: G = exp(i omega r) / (4 pi r); k_t = G(h|t|) h^d; k_0 = integral of G over the disk /
 // ball of area / volume h^d (closed form, see the oracle docstring for the derivation).
+// omega = 0 in 3D is the Laplace kernel of Sec. 5: G = 1 / (4 pi r), k_0 = a^2 / 2.
 __global__ void k_kernel_quadrant(double2* ktq, int d, int n, double omega, double h) {
   const long n1 = n + 1;
   const long total = d == 2 ? n1 * n1 : n1 * n1 * n1;
@@ -591,7 +592,11 @@ __global__ void k_kernel_quadrant(double2* ktq, int d, int n, double omega, doub
       }
     } else {
       const double hd = h * h * h;
-      if (r2 == 0) {
+      if (omega == 0.0) {
+        const double a = h * cbrt(3.0 / (4.0 * M_PI));
+        k.x = r2 == 0 ? 0.5 * a * a : hd / (4.0 * M_PI * h * sqrt(r2));
+        k.y = 0.0;
+      } else if (r2 == 0) {
         const double a = h * cbrt(3.0 / (4.0 * M_PI));
         double sn, cs;
         sincos(omega * a, &sn, &cs);
@@ -663,6 +668,34 @@ __global__ void k_to_ff(const double* __restrict__ src, float2* __restrict__ dst
 void to_ff(const double* src, void* dst, long count, cudaStream_t st) {
   if (count <= 0) return;
   LS_LAUNCH("to_ff", st, k_to_ff<<<512, 256, 0, st>>>(src, reinterpret_cast<float2*>(dst), count));
+}
+
+// Sec. 5 right-hand side g = K f for delta sources: f_j = q_r / h^d at the source point p_r
+// (unit mass on the cell), so g_r(i) = q_r k_{i - p_r} / h^d, read from the quadrant table
+// at |i - p_r| (componentwise).  One thread per output entry, r outermost.
+__global__ void k_point_source(double2* g, const int* __restrict__ pts, const double2* __restrict__ q,
+                               const double2* __restrict__ ktq, int d, int n, int nrhs, double inv_hd) {
+  const long N = d == 2 ? (long)n * n : (long)n * n * n, n1 = n + 1;
+  const long total = N * nrhs;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / N);
+    long i = e - (long)r * N, src = 0, mul = 1;
+    for (int a = d - 1; a >= 0; --a) {  // C order: the last index is the fastest
+      const long ia = i % n;
+      i /= n;
+      const long t = ia - pts[(size_t)r * d + a];
+      src += (t < 0 ? -t : t) * mul;
+      mul *= n1;
+    }
+    const double2 k = ktq[src], s = q ? q[r] : make_double2(1.0, 0.0);
+    g[e] = make_double2((k.x * s.x - k.y * s.y) * inv_hd, (k.x * s.y + k.y * s.x) * inv_hd);
+  }
+}
+
+void point_source(int d, int n, int nrhs, const int* pts, const double2* q, const double2* ktq, double h, double2* g,
+                  cudaStream_t st) {
+  const double hd = d == 2 ? h * h : h * h * h;
+  LS_LAUNCH("point_source", st, k_point_source<<<1024, 256, 0, st>>>(g, pts, q, ktq, d, n, nrhs, 1.0 / hd));
 }
 
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st) {

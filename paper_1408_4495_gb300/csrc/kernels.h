@@ -77,6 +77,10 @@ void to_ff(const double* src, void* dst, long count, cudaStream_t st);
 size_t conv_scratch1_elems(int d, int n, int nrhs);
 size_t conv_scratch2_elems(int d, int n, int nrhs);
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st);
+// Sec. 5: g_r = q_r K delta_{p_r} / h^d for nrhs point sources (pts: nrhs x d grid indices;
+// q: nrhs complex strengths or null for 1), from the quadrant table ktq.
+void point_source(int d, int n, int nrhs, const int* pts, const double2* q, const double2* ktq, double h, double2* g,
+                  cudaStream_t st);
 void build_symbol(const ConvPlan& p, const double2* ktq, double2* sym64, float2* sym32, double2* work,
                   cudaStream_t st);
 

@@ -25,7 +25,8 @@ LS_PREC_FP64, LS_PREC_MIXED, LS_PREC_FF = 0, 1, 2
 STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS_ESTATE", "LS_ETIMEOUT", "LS_EBUFFER"]
 
 # every entry point declared in include/ls.h
-EXPORTS = ["ls_setup", "ls_factor", "ls_rhs_plane_wave", "ls_solve", "ls_last_error", "ls_free",
+EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
+           "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
 
@@ -69,6 +70,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_setup.argtypes = [ctypes.POINTER(LsGrid), dp, vp, vp, ctypes.POINTER(vp)]
     lib.ls_factor.argtypes = [vp]
     lib.ls_rhs_plane_wave.argtypes = [vp, ip, vp, vp]
+    lib.ls_setup_laplace.argtypes = [ctypes.POINTER(LsGrid), vp, vp, ctypes.POINTER(vp)]
+    lib.ls_rhs_point_source.argtypes = [vp, ip, vp, vp, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -133,21 +136,28 @@ class SolveInfo:
 
 
 class Solver:
-    """One medium on one grid: ``ls_setup`` at construction, ``ls_free`` on close."""
+    """One medium on one grid: ``ls_setup`` at construction, ``ls_free`` on close.
 
-    def __init__(self, m, omega: float, dim: int | None = None, buffer_b: int = 2, restart: int = 50,
-                 max_iter: int = 500, mixed: bool = True, stream=None):
+    ``laplace=True`` selects the Laplace variant (``ls_setup_laplace``, Sec. 5): ``m`` is then
+    the potential V and ``omega`` is ignored."""
+
+    def __init__(self, m, omega: float = 0.0, dim: int | None = None, buffer_b: int = 2, restart: int = 50,
+                 max_iter: int = 500, mixed: bool = True, stream=None, laplace: bool = False):
         self.lib = load()
         if isinstance(m, np.ndarray):
             m = np.ascontiguousarray(m, dtype=np.float64)
         self.d = dim if dim is not None else m.ndim
         self.n = int(m.shape[0])
         self.N = self.n ** self.d
-        self.omega = float(omega)
+        self.omega = 0.0 if laplace else float(omega)
+        self.laplace = laplace
         self.mixed = mixed
         g = LsGrid(self.d, self.n, buffer_b, restart, max_iter, LS_PREC_MIXED if mixed else LS_PREC_FP64)
         h = ctypes.c_void_p()
-        st = self.lib.ls_setup(ctypes.byref(g), self.omega, _ptr(m), _stream_ptr(stream), ctypes.byref(h))
+        if laplace:
+            st = self.lib.ls_setup_laplace(ctypes.byref(g), _ptr(m), _stream_ptr(stream), ctypes.byref(h))
+        else:
+            st = self.lib.ls_setup(ctypes.byref(g), self.omega, _ptr(m), _stream_ptr(stream), ctypes.byref(h))
         if st != LS_OK:
             raise LsError(st, self.lib.ls_last_error(None).decode())
         self.h = h
@@ -189,6 +199,24 @@ class Solver:
                 import torch
                 out = torch.empty(shape, dtype=torch.complex128, device=dirs_np.device)
         self._check(self.lib.ls_rhs_plane_wave(self.h, nrhs, _ptr(dirs_np), _ptr(out)))
+        return out
+
+    def rhs_point_source(self, points, strengths=None, out=None):
+        """g = K f for delta sources at the (nrhs, d) 0-based grid indices ``points``."""
+        pts = points if not isinstance(points, np.ndarray) else np.ascontiguousarray(points, dtype=np.int32)
+        nrhs = int(pts.shape[0])
+        q = strengths
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.complex128)
+        if out is None:
+            shape = (nrhs,) + (self.n,) * self.d
+            if isinstance(pts, np.ndarray):
+                out = np.empty(shape, dtype=np.complex128)
+            else:
+                import torch
+                out = torch.empty(shape, dtype=torch.complex128, device=pts.device)
+        self._check(self.lib.ls_rhs_point_source(self.h, nrhs, _ptr(pts), _ptr(q) if q is not None else None,
+                                                 _ptr(out)))
         return out
 
     def solve(self, rhs, tol: float = 1e-6, out=None, raise_on_noconv: bool = True):
