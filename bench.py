@@ -228,10 +228,10 @@ def algorithmic_bytes(cls, w, nd, counts, steps):
 # ncu DRAM traffic per launch of a kernel class, valid while the class's source file is
 # unchanged (sha1 of the file at capture time); see profiles/.
 TRAFFIC = {
-    "nd_fwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "258dc65474791ca701789d6b24e9ceb8a9ab4e8b",
-                   "bytes": 5847414},
-    "nd_bwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "258dc65474791ca701789d6b24e9ceb8a9ab4e8b",
-                   "bytes": 8078789},
+    "nd_fwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "4acda65409d8d01e40fddc9b1ed7f35c2a80287c",
+                   "bytes": 5848418},
+    "nd_bwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "4acda65409d8d01e40fddc9b1ed7f35c2a80287c",
+                   "bytes": 8079419},
 }
 
 
