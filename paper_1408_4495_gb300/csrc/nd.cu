@@ -28,6 +28,8 @@
 //   backward (root to leaves): x_own = F11^{-1} w_own - H x_ring
 // two batched multi-right-hand-side matrix-vector products per level, every factor entry
 // read once per sweep.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -901,6 +903,204 @@ __global__ void __launch_bounds__(panel_reg_rows<C>()) k_panel_reg(LevelK<C> L, 
   if (r == 0) swp[(size_t)z * SWP_STRIDE] = min(cnt, 2 * NB);
 }
 
+// Panel [k0, k1) of a front with up to PC_CTAS * 512 own rows (FP32): the register panel
+// spread over a thread-block cluster, one own row per thread, 512 rows per CTA.  Per column:
+// each warp's best live row publishes its key, reciprocal pivot and row to its CTA's
+// parity-double-buffered slot (as in k_panel_reg), the CTA reduces its warps' keys, one
+// cluster barrier makes every CTA's best key and slots visible, and each warp reads the
+// CTAs' keys and then the winning row through distributed shared memory.  Keys carry the
+// magnitude |re| + |im| cut to 12 mantissa bits above (4095 - row).  At the end CTA 0 gathers the pivot
+// sequence from every CTA and places the rows above w that were not chosen; the rows are
+// written to their logical positions and swp holds, per front, the pairs (position, source)
+// local to k0: pivot j in pair j, the displaced rows in pairs w.. (count = w + displaced).
+constexpr int PC_ROWS = 512, PC_CTAS = 8;
+template <typename C>
+__global__ void __launch_bounds__(PC_ROWS) k_panel_cluster(LevelK<C> L, int k0, int k1, int* __restrict__ swp,
+                                                          int* err) {
+  namespace cg = cooperative_groups;
+  using Rl = typename RealOf<C>::T;
+  constexpr int MW = PC_ROWS / 32;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ __align__(16) C slot[2][MW][NB];
+  __shared__ unsigned wkey[2][MW];
+  __shared__ unsigned ckey[2];
+  __shared__ int pivrow[NB];  // the row chosen at each step when it lives in this CTA, else -1
+  __shared__ int pseq[NB], vac[NB];
+  const int q = (int)cl.block_rank(), ncta = (int)cl.num_blocks();
+  const int z = blockIdx.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int fmax = L.fmax, R = L.smax - k0, w = k1 - k0;
+  const int r = q * PC_ROWS + t;  // own row, local to k0
+  C* A = L.F + (size_t)z * fmax * L.ncols + (size_t)k0 * fmax + k0;  // local (r, c) at A[c * fmax + r]
+  const bool has = r < R;
+  C a[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) a[c] = (has && c < w) ? A[(size_t)c * fmax + r] : czero<C>();
+  if (t < NB) pivrow[t] = -1;
+  bool live = has;
+  int jp = -1;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < w) {
+      const int par = j & 1;
+      const unsigned mag = __float_as_uint((float)(fabs(a[j].x) + fabs(a[j].y)));
+      const unsigned key = live ? ((mag >> 11) << 12) | (4095u - (unsigned)r) : 0u;
+      const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+      if (live && key == kw) {
+        const Rl den = cabs2(a[j]);
+        const Rl rden = den > 0 ? recip(den) : (Rl)0;
+        C inv;
+        inv.x = a[j].x * rden;
+        inv.y = -a[j].y * rden;
+        slot[par][wid][j] = inv;
+#pragma unroll
+        for (int c = j + 1; c < NB; ++c) slot[par][wid][c] = a[c];
+      }
+      if (lane == 0) wkey[par][wid] = kw;
+      __syncthreads();
+      if (wid == 0) {
+        const unsigned kc = __reduce_max_sync(0xffffffffu, lane < MW ? wkey[par][lane] : 0u);
+        if (lane == 0) ckey[par] = kc;
+      }
+      cl.sync();
+      const unsigned km = __reduce_max_sync(0xffffffffu, lane < ncta ? *cl.map_shared_rank(&ckey[par], lane) : 0u);
+      if (km == 0u) {  // no live row left (cannot happen while j < R)
+        if (t == 0 && q == 0) atomicExch(err, 1);
+        continue;
+      }
+      if ((km >> 12) == 0u && t == 0 && q == 0) atomicExch(err, 1);  // zero pivot
+      const int bi = 4095 - (int)(km & 4095u);
+      if (r == bi) {
+        live = false;
+        jp = j;
+        pivrow[j] = r;
+      }
+      if (live) {
+        const C* pr = cl.map_shared_rank(&slot[par][(bi % PC_ROWS) >> 5][0], bi / PC_ROWS);
+        const C m = cmul(a[j], pr[j]);
+        a[j] = m;
+#pragma unroll
+        for (int c = j + 1; c < NB; ++c) a[c] = cfms(a[c], m, pr[c]);
+      }
+    }
+  }
+  cl.sync();  // every CTA's pivrow is final
+  if (q == 0 && wid == 0) {
+    int pj = -1;
+    if (lane < w)
+      for (int p = 0; p < ncta; ++p) {
+        const int v = *cl.map_shared_rank(&pivrow[lane], p);
+        if (v >= 0) pj = v;
+      }
+    pseq[lane] = pj;
+    // positions >= w vacated by pivots, in increasing order (rank among the vacated rows)
+    const bool vp = lane < w && pj >= w;
+    int rank = 0;
+    for (int i = 0; i < 32; ++i) {
+      const int o = __shfl_sync(0xffffffffu, pj, i);
+      const bool ov = __shfl_sync(0xffffffffu, vp ? 1 : 0, i) != 0;
+      if (ov && o < pj) ++rank;
+    }
+    vac[lane] = lane;  // unused entries stay in range
+    __syncwarp();
+    if (vp) vac[rank] = pj;
+  }
+  __syncthreads();
+  cl.sync();  // CTA 0 has finished reading the other CTAs' shared memory
+  int pos = r;
+  if (jp >= 0) pos = jp;
+  int* sw = swp + (size_t)z * SWP_STRIDE;
+  if (q == 0 && wid == 0) {
+    // rows at positions < w that were not chosen (all in warp 0 of CTA 0)
+    const bool dp = has && jp < 0 && r < w;
+    const unsigned bd = __ballot_sync(0xffffffffu, dp);
+    const int k = __popc(bd & ((1u << lane) - 1u));
+    if (dp) {
+      pos = min(vac[k], R - 1);
+      sw[1 + 2 * (w + k)] = pos;
+      sw[2 + 2 * (w + k)] = r;
+    }
+    // a step without a pivot (singular front, flagged in err) keeps its position
+    if (lane < w && pseq[lane] < 0) {
+      sw[1 + 2 * lane] = lane;
+      sw[2 + 2 * lane] = lane;
+    }
+    if (lane == 0) sw[0] = w + __popc(bd);
+  }
+  if (jp >= 0) {
+    sw[1 + 2 * jp] = jp;
+    sw[2 + 2 * jp] = r;
+  }
+  if (has) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < w) A[(size_t)c * fmax + pos] = a[c];
+  }
+}
+
+// Columns c in [k1, ncols): apply the panel's row permutation given as (position, source)
+// pairs local to k0 (k_panel_reg / k_panel_cluster), then F[k0:k1, c] = L_kk^{-1} F[k0:k1, c].
+template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(LevelK<C> L, int k0, int k1,
+                                                                              const int* __restrict__ swp) {
+  const int z = blockIdx.x;
+  const int fmax = L.fmax, w = k1 - k0, R = L.smax - k0;
+  C* A = L.F + (size_t)z * fmax * L.ncols;
+  __shared__ C Ld[NB][NB + 1];
+  __shared__ int stop[NB], bpos[NB], bsrc[NB], nb;
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, l = idx / w;
+    Ld[i][l] = A[(size_t)(k0 + l) * fmax + k0 + i];
+  }
+  if (threadIdx.x < NB) stop[threadIdx.x] = threadIdx.x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int* sw = swp + (size_t)z * SWP_STRIDE;
+    const int cnt = min(sw[0], 2 * NB);
+    int m = 0;
+    for (int qq = 0; qq < cnt; ++qq) {
+      const int ps = sw[1 + 2 * qq], sr = sw[2 + 2 * qq];
+      if (ps < 0 || ps >= R || sr < 0 || sr >= R) continue;
+      if (ps < w) stop[ps] = sr;
+      else if (m < NB) {
+        bpos[m] = ps;
+        bsrc[m] = sr;
+        ++m;
+      }
+    }
+    nb = m;
+  }
+  __syncthreads();
+  const int c = k1 + blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= L.ncols) return;
+  C* col = A + (size_t)c * fmax + k0;
+  const int np = nb;
+  C x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < w) x[i] = col[stop[i]];
+  {
+    C extra[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i < np) extra[i] = col[bsrc[i]];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i < np) col[bpos[i]] = extra[i];
+  }
+#pragma unroll
+  for (int i = 1; i < NB; ++i) {
+    if (i < w) {
+      C acc = x[i];
+#pragma unroll
+      for (int l = 0; l < NB; ++l)
+        if (l < i) acc = cfms(acc, Ld[i][l], x[l]);
+      x[i] = acc;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < w) col[i] = x[i];
+}
+
 // One warp per column c in [k1, ncols): local rows p = 32 q + lane of [k0, smax) in slot q,
 // loaded through the panel's permutation; x_p -= L_pi x_i for i < w, p > i (forward
 // substitution inside the block, update below it).  The panel L is staged in shared
@@ -1431,17 +1631,43 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
       // them), the block rows of [F12 | I] carried along
       for (int k0 = 0; k0 < L.smax; k0 += NB) {
-        const int k1 = std::min(k0 + NB, L.smax);
-        const size_t psm = (size_t)(L.smax - k0) * (k1 - k0) * sizeof(C);
-        if (psm <= PANEL_SMEM_MAX)
-          LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                    k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
-        else
-          LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                    k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
+        const int k1 = std::min(k0 + NB, L.smax), R = L.smax - k0;
         const int m = L.ncols - k1;
-        LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                  k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
+        // register panels (one CTA up to panel_reg_rows, a cluster of up to PC_CTAS CTAs of
+        // PC_ROWS rows in FP32) record the row permutation as pairs in swp; the shared- or
+        // global-memory panel records LAPACK-style swaps in piv
+        const int ncta = (R + PC_ROWS - 1) / PC_ROWS;
+        if (R <= panel_reg_rows<C>() || (f32 && ncta <= PC_CTAS)) {
+          if (R <= panel_reg_rows<C>()) {
+            LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                      k_panel_reg<C><<<L.nf, (R + 31) / 32 * 32, 0, st>>>(L, k0, k1, p->swp, p->d_err));
+          } else if constexpr (sizeof(C) == 8) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(ncta, L.nf);
+            cfg.blockDim = dim3(PC_ROWS);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = ncta;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            LS_LAUNCH("nd_panel_c64", st, LS_CUDA(cudaLaunchKernelEx(&cfg, k_panel_cluster<C>, L, k0, k1, p->swp, p->d_err)));
+          }
+          LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                    k_trsm_lower_swp<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1, p->swp));
+        } else {
+          const size_t psm = (size_t)R * (k1 - k0) * sizeof(C);
+          if (psm <= PANEL_SMEM_MAX)
+            LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                      k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
+          else
+            LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                      k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
+          LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                    k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
+        }
         launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
       }
       // sweep 2: backward substitution with U11 on the own rows of [F12 | I]

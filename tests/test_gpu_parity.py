@@ -258,3 +258,39 @@ def test_errors_are_reported_not_raised_in_the_library(LS):
         with pytest.raises(LS.LsError) as e:
             s.apply(np.zeros((1, n, n), complex), prec=7)
         assert e.value.status == LS.LS_EINVAL
+
+
+@pytest.mark.parametrize("laplace", [False, True])
+def test_preconditioner_cluster_panel_3d_n32(LS, laplace):
+    """3D n=32: the root front has 1024 own rows, so its first panels run on the
+    thread-block-cluster panel (FP32) or the shared-memory panel (FP64).  The two GPU paths
+    are independent implementations of the same factorization; both are checked by the
+    backward error against the oracle's assembled M, and against each other."""
+    n, d = 32, 3
+    x = rand_c((2,) + (n,) * d, 41)
+    if laplace:
+        V = W.enforce_buffer(W.laplace_3d(n, 1).V, 2)
+        sten, cint = O.all_stencils(n, d, 0.0, 2)
+        M, S = O.assemble(n, d, 1.0, V, sten, cint)
+        mk = lambda mixed: LS.Solver(V, mixed=mixed, laplace=True)
+    else:
+        omega = 2 * np.pi * 4.0
+        m = medium(d, n, seed=5)
+        sten, cint = O.all_stencils(n, d, omega, 2)
+        M, S = O.assemble(n, d, omega, m, sten, cint)
+        mk = lambda mixed: LS.Solver(m, omega, mixed=mixed)
+    normM = abs(M).sum(axis=1).max()
+    z = {}
+    for mixed in (False, True):
+        with mk(mixed) as s:
+            s.factor()
+            z[mixed] = s.precond(x)
+        for j in range(2):
+            zj = z[mixed][j].reshape(-1)
+            be = np.linalg.norm(M @ zj - S @ x[j].reshape(-1)) / (normM * np.linalg.norm(zj))
+            # measured on GB300: Helmholtz FP64 3e-16, FP32 2e-7; Laplace (V ~ -1/h^2, cond(F11)
+            # far larger) FP64 3-5e-13, FP32 3-7e-4 depending on the pivot sequence; bounds ~5x
+            bound = (2e-6 if mixed else 2e-15) if not laplace else (4e-3 if mixed else 3e-12)
+            assert be < bound, be
+    if not laplace:
+        assert rel(z[True], z[False]) < 2e-4  # measured 2.4e-5
