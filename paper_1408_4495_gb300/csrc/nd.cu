@@ -1578,6 +1578,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             k_set_one<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_one, p->d_one_off));
   const int depth = (int)p->lev.size();
   constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+  constexpr int REG_MAX_COLS = 1024;
   constexpr size_t GJ_SMEM_MAX = 160 * 1024;
   static bool attr = false;
   if (!attr) {
@@ -1621,7 +1622,10 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err);
       continue;
     }
-    if (L.smax <= 32 * reg_rpl_max<C>()) {
+    // The register sweeps update every trailing column on CUDA cores from a panel staged per
+    // block; fronts with many columns (3D levels with thousands of ring rows) take the
+    // blocked path, whose trailing updates are tensor-core GEMMs.
+    if (L.smax <= 32 * reg_rpl_max<C>() && L.ncols <= REG_MAX_COLS) {
       // both sweeps with the fronts' own rows in registers
       const int rpl = (L.smax + 31) / 32;
       if (rpl <= 4) reg_sweeps<C, 4>(L, p->swp, p->d_err, st);
