@@ -32,6 +32,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   omega -> 0 limit of the Helmholtz weight; the point-source right-hand side equals the
   Green's function at the grid offsets; V = 0 gives u = g; dense solve of (I + K V) u = g;
   stencil optimality for the Laplace kernel.                                  pinned
+* ``far_field`` (exterior evaluation): equals the direct exterior sum of the Green's
+  function at a distant point (constant and sign), zero for m = 0, and reciprocity
+  u_inf(theta; d) = u_inf(-d; -theta) of the discrete solution.               pinned
 """
 
 from .ls_oracle import *  # noqa: F401,F403

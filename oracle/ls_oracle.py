@@ -25,7 +25,7 @@ __all__ = [
     "dense_K", "apply_K_direct", "apply_K_fft", "apply_operator", "plane_wave", "rhs",
     "point_class", "class_mu", "class_far_set", "stencil", "all_stencils",
     "assemble", "nd_order", "Preconditioner", "gmres_right", "solve",
-    "check_buffer", "sparsity_ratio", "point_source", "laplace_solve",
+    "check_buffer", "sparsity_ratio", "point_source", "laplace_solve", "far_field",
 ]
 
 
@@ -184,6 +184,26 @@ def point_source(ktab, n: int, d: int, point, strength: complex = 1.0) -> np.nda
     f = np.zeros((n,) * d, dtype=np.complex128)
     f[tuple(point)] = strength / grid_h(n) ** d
     return apply_K_fft(ktab, f)
+
+
+def far_field(n: int, d: int, omega: float, m: np.ndarray, u_total: np.ndarray, obs) -> np.ndarray:
+    """Far-field pattern of the scattered field in the observation directions ``obs``
+    (shape (k, d), unit vectors).  The scattered field is u_s = -K(omega^2 m u) (eq. ls with
+    u the total field) and G(x - y) ~ c_d e^{i omega r} r^{-(d-1)/2} e^{-i omega theta . y}
+    as r = |x| -> infinity in direction theta, so
+        u_s(x) ~ e^{i omega r} r^{-(d-1)/2} u_inf(theta),
+        u_inf(theta) = -c_d h^d sum_i e^{-i omega theta . x_i} omega^2 m_i u_i,
+    c_2 = e^{i pi/4} / sqrt(8 pi omega) (large-argument form of (i/4) H_0^(1)),
+    c_3 = 1 / (4 pi).  The discrete sum replaces the integral by the same quadrature as K."""
+    X = grid_coords(n, d)
+    h = grid_h(n)
+    c = np.exp(1j * math.pi / 4) / math.sqrt(8 * math.pi * omega) if d == 2 else 1.0 / (4 * math.pi)
+    v = (omega**2 * m * u_total).reshape(-1)
+    out = np.empty(len(obs), dtype=np.complex128)
+    for k, th in enumerate(obs):
+        phase = sum(X[a] * float(th[a]) for a in range(d)).reshape(-1)
+        out[k] = -c * h**d * np.sum(np.exp(-1j * omega * phase) * v)
+    return out
 
 
 def check_buffer(m: np.ndarray, b: int) -> bool:
