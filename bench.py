@@ -340,6 +340,21 @@ def run_gpu(args):
                 "launches_timed": nlaunch, "steps_timed": k_roof,
                 "share_of_kernel_time": by_cls[cls] / tot_cls}
 
+    # exterior evaluation after the step: far-field pattern of the 16 solutions in 64 directions
+    obs_dev = torch.tensor(np.array([[math.cos(2 * math.pi * k / 64), math.sin(2 * math.pi * k / 64)] for k in range(64)])
+                           if w.d == 2 else np.eye(3), device=dev)
+    ff_out = torch.empty((w.nrhs, obs_dev.shape[0]), dtype=torch.complex128, device=dev)
+    s_mix.far_field(dirs_dev, u, obs_dev, out=ff_out)
+    torch.cuda.synchronize()
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fe0.record(stream)
+    for _ in range(5):
+        s_mix.far_field(dirs_dev, u, obs_dev, out=ff_out)
+    fe1.record(stream)
+    torch.cuda.synchronize()
+    far = {"ms": fe0.elapsed_time(fe1) / 5, "nrhs": w.nrhs, "nobs": int(obs_dev.shape[0]),
+           "includes": "ls_far_field with device buffers (copies of its inputs, one FP64 kernel)"}
+
     if args.only_mixed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "only_mixed": True,
@@ -443,7 +458,7 @@ def run_gpu(args):
                 "max_rel_resid": max(res), "all_converged": conv,
                 "plain_fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / k64, "steps": k64,
                                "iters": {"min": min(its64), "max": max(its64)}},
-                "mixed_over_fp64": value / value64, "laplace_3d": lap,
+                "mixed_over_fp64": value / value64, "laplace_3d": lap, "far_field": far,
                 "setup_ms": setup_s * 1e3, "nd": nd,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "launches_by_class": prof["counts"], "device_time_shares": shares, "clocks": clocks}

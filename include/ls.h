@@ -153,6 +153,25 @@ ls_status ls_rhs_point_source(ls_ctx* c, int nrhs, const int* points, const doub
  */
 ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u_out, ls_info* info);
 
+/*
+ * ls_far_field -- exterior evaluation after the solve.  With u = u_I + u_s the total field
+ * (u_I the plane wave of direction dir, u_s the scattered field that ls_solve returns for
+ * g = ls_rhs_plane_wave(dir)), the scattered field outside the domain is
+ * u_s(x) = -int G(x - y) omega^2 m(y) u(y) dy (Sec. 1, eq. ls), and as r = |x| -> infinity
+ * in the direction theta, u_s(x) ~ e^{i omega r} r^{-(d-1)/2} u_inf(theta) with
+ *   u_inf(theta) = -c_d h^d sum_i e^{-i omega theta . x_i} omega^2 m_i u(x_i),
+ *   c_2 = e^{i pi/4} / sqrt(8 pi omega), c_3 = 1 / (4 pi)   (FP64 on the device).
+ * Helmholtz contexts only (LS_ESTATE for ls_setup_laplace).
+ *   nrhs   number of incident waves, >= 1.
+ *   dirs   nrhs x d doubles: the incident directions the scattered fields belong to.
+ *   us     nrhs x n^d complex doubles: the scattered fields (ls_solve's u_out).
+ *   nobs   number of observation directions, >= 1.
+ *   obs    nobs x d doubles: observation directions theta (unit vectors).
+ *   out    nrhs x nobs complex doubles, written: out[r * nobs + k] = u_inf(theta_k) of wave r.
+ * Host or device pointers.
+ */
+ls_status ls_far_field(ls_ctx* c, int nrhs, const double* dirs, const double* us, int nobs, const double* obs,
+                       double* out);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

@@ -746,6 +746,29 @@ ls_status ls_rhs_point_source(ls_ctx* c, int nrhs, const int* points, const doub
   }
 }
 
+ls_status ls_far_field(ls_ctx* c, int nrhs, const double* dirs, const double* us, int nobs, const double* obs,
+                       double* out) {
+  try {
+    check_ctx(c);
+    if (c->laplace) throw Error{ls::ESTATE_, "the far-field pattern needs the Helmholtz kernel (omega > 0)"};
+    if (nrhs < 1 || nobs < 1 || !dirs || !us || !obs || !out) throw Error{ls::EINVAL_, "bad arguments"};
+    const size_t tot = (size_t)nrhs * c->N;
+    double* dd = buf<double>(c, "ff_dirs", (size_t)nrhs * c->d);
+    double* od = buf<double>(c, "ff_obs", (size_t)nobs * c->d);
+    double2* ud = buf<double2>(c, "ff_u", tot);
+    double2* fd = buf<double2>(c, "ff_out", (size_t)nrhs * nobs);
+    copy_in(c, dd, dirs, (size_t)nrhs * c->d * sizeof(double));
+    copy_in(c, od, obs, (size_t)nobs * c->d * sizeof(double));
+    copy_in(c, ud, us, tot * sizeof(double2));
+    ls::far_field(c->d, c->n, nrhs, nobs, ud, dd, od, c->w2m64, c->omega, c->h, fd, c->st);
+    copy_out(c, out, fd, (size_t)nrhs * nobs * sizeof(double2));
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
 ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u_out, ls_info* info) {
   try {
     check_ctx(c);

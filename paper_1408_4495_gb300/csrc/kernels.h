@@ -79,6 +79,10 @@ size_t conv_scratch2_elems(int d, int n, int nrhs);
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st);
 // Sec. 5: g_r = q_r K delta_{p_r} / h^d for nrhs point sources (pts: nrhs x d grid indices;
 // q: nrhs complex strengths or null for 1), from the quadrant table ktq.
+// far-field pattern u_inf(theta_k; r) of the scattered fields us (nrhs x N) of the plane waves
+// dirs (nrhs x d) in the directions obs (nobs x d); out: nrhs x nobs
+void far_field(int d, int n, int nrhs, int nobs, const double2* us, const double* dirs, const double* obs,
+               const double* w, double omega, double h, double2* out, cudaStream_t st);
 void point_source(int d, int n, int nrhs, const int* pts, const double2* q, const double2* ktq, double h, double2* g,
                   cudaStream_t st);
 void build_symbol(const ConvPlan& p, const double2* ktq, double2* sym64, float2* sym32, double2* work,

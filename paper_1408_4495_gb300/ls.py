@@ -26,7 +26,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
-           "ls_last_error", "ls_free",
+           "ls_far_field", "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
 
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_rhs_plane_wave.argtypes = [vp, ip, vp, vp]
     lib.ls_setup_laplace.argtypes = [ctypes.POINTER(LsGrid), vp, vp, ctypes.POINTER(vp)]
     lib.ls_rhs_point_source.argtypes = [vp, ip, vp, vp, vp]
+    lib.ls_far_field.argtypes = [vp, ip, vp, vp, ip, vp, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -217,6 +218,23 @@ class Solver:
                 out = torch.empty(shape, dtype=torch.complex128, device=pts.device)
         self._check(self.lib.ls_rhs_point_source(self.h, nrhs, _ptr(pts), _ptr(q) if q is not None else None,
                                                  _ptr(out)))
+        return out
+
+    def far_field(self, dirs, us, obs, out=None):
+        """Far-field pattern u_inf(obs_k) of the scattered fields ``us`` of the plane waves
+        ``dirs``: an (nrhs, nobs) complex array (see ls_far_field in include/ls.h)."""
+        d = dirs if not isinstance(dirs, np.ndarray) else np.ascontiguousarray(dirs, dtype=np.float64)
+        o = obs if not isinstance(obs, np.ndarray) else np.ascontiguousarray(obs, dtype=np.float64)
+        if isinstance(us, np.ndarray):
+            us = np.ascontiguousarray(us, dtype=np.complex128)
+        nrhs, nobs = int(d.shape[0]), int(o.shape[0])
+        if out is None:
+            if isinstance(us, np.ndarray):
+                out = np.empty((nrhs, nobs), dtype=np.complex128)
+            else:
+                import torch
+                out = torch.empty((nrhs, nobs), dtype=torch.complex128, device=us.device)
+        self._check(self.lib.ls_far_field(self.h, nrhs, _ptr(d), _ptr(us), nobs, _ptr(o), _ptr(out)))
         return out
 
     def solve(self, rhs, tol: float = 1e-6, out=None, raise_on_noconv: bool = True):
