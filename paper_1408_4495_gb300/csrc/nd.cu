@@ -767,6 +767,7 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
 // its column in registers, the U11 columns staged in shared memory 32 at a time.
 // ---------------------------------------------------------------------------------------
 constexpr int SWP_STRIDE = 1 + 4 * NB;  // per front: count, then (position, source) pairs
+constexpr int OB_PANELS = 4;            // panels per outer block of the blocked path
 
 // dst[e] = src(e) for e < n over the CTA's threads, B loads in flight per thread before the
 // first store (the loads do not wait on the stores of earlier iterations)
@@ -1037,10 +1038,11 @@ __global__ void __launch_bounds__(PC_ROWS) k_panel_cluster(LevelK<C> L, int k0, 
   }
 }
 
-// Columns c in [k1, ncols): apply the panel's row permutation given as (position, source)
-// pairs local to k0 (k_panel_reg / k_panel_cluster), then F[k0:k1, c] = L_kk^{-1} F[k0:k1, c].
-template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(LevelK<C> L, int k0, int k1,
-                                                                              const int* __restrict__ swp) {
+// Columns c in [c0, c1): apply the panel's row permutation given as (position, source)
+// pairs local to k0 (k_panel_reg / k_panel_cluster; none when swp is null), then
+// F[k0:k1, c] = L_kk^{-1} F[k0:k1, c].
+template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(LevelK<C> L, int k0, int k1, int c0,
+                                                                              int c1, const int* __restrict__ swp) {
   const int z = blockIdx.x;
   const int fmax = L.fmax, w = k1 - k0, R = L.smax - k0;
   C* A = L.F + (size_t)z * fmax * L.ncols;
@@ -1053,8 +1055,8 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(Le
   if (threadIdx.x < NB) stop[threadIdx.x] = threadIdx.x;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int* sw = swp + (size_t)z * SWP_STRIDE;
-    const int cnt = min(sw[0], 2 * NB);
+    const int* sw = swp ? swp + (size_t)z * SWP_STRIDE : nullptr;
+    const int cnt = sw ? min(sw[0], 2 * NB) : 0;
     int m = 0;
     for (int qq = 0; qq < cnt; ++qq) {
       const int ps = sw[1 + 2 * qq], sr = sw[2 + 2 * qq];
@@ -1069,8 +1071,8 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(Le
     nb = m;
   }
   __syncthreads();
-  const int c = k1 + blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= L.ncols) return;
+  const int c = c0 + blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   C* col = A + (size_t)c * fmax + k0;
   const int np = nb;
   C x[NB];
@@ -1099,6 +1101,39 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(Le
 #pragma unroll
   for (int i = 0; i < NB; ++i)
     if (i < w) col[i] = x[i];
+}
+
+// Row permutations of nrec panels applied in order to the columns [c0, c1) (no solve): record
+// q holds (position, source) pairs local to k0 + q NB, as written by k_panel_reg /
+// k_panel_cluster.  A block takes AP_COLS columns; a thread moves one entry of one column.
+constexpr int AP_COLS = 4;
+template <typename C>
+__global__ void __launch_bounds__(256) k_apply_swp(LevelK<C> L, int k0, int c0, int c1, const int* __restrict__ swp,
+                                                   int nrec, long rec_stride) {
+  __shared__ C v[AP_COLS][2 * NB];
+  __shared__ int sp[2 * NB], ss[2 * NB], cnt;
+  const int z = blockIdx.x, R = L.smax - k0;
+  C* A = L.F + (size_t)z * L.fmax * L.ncols;
+  const int u = threadIdx.x / (2 * NB), e = threadIdx.x % (2 * NB);
+  const int c = c0 + blockIdx.y * AP_COLS + u;
+  for (int q = 0; q < nrec; ++q) {
+    const int kq = k0 + q * NB;
+    __syncthreads();
+    if (threadIdx.x == 0) cnt = min(swp[q * rec_stride + (size_t)z * SWP_STRIDE], 2 * NB);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      const int* sw = swp + q * rec_stride + (size_t)z * SWP_STRIDE;
+      const int ps = sw[1 + 2 * threadIdx.x], sr = sw[2 + 2 * threadIdx.x];
+      const bool ok = ps >= 0 && sr >= 0 && kq + ps < k0 + R && kq + sr < k0 + R;
+      sp[threadIdx.x] = ok ? kq + ps : -1;
+      ss[threadIdx.x] = ok ? kq + sr : -1;
+    }
+    __syncthreads();
+    const bool act = u < AP_COLS && c < c1 && e < cnt && sp[e] >= 0;
+    if (act) v[u][e] = A[(size_t)c * L.fmax + ss[e]];
+    __syncthreads();
+    if (act) A[(size_t)c * L.fmax + sp[e]] = v[u][e];
+  }
 }
 
 // One warp per column c in [k1, ncols): local rows p = 32 q + lane of [k0, smax) in slot q,
@@ -1478,7 +1513,7 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes, cudaStream_t st) {
   LS_CUDA(cudaMemsetAsync(p->cnt, 0, items * sizeof(unsigned), st));
   p->part_elems = part;
   if (p->swp) { dev_free(p->swp); p->swp = nullptr; }
-  p->swp = static_cast<int*>(dev_alloc((size_t)nf_max * SWP_STRIDE * sizeof(int)));
+  p->swp = static_cast<int*>(dev_alloc((size_t)OB_PANELS * nf_max * SWP_STRIDE * sizeof(int)));
   p->F_bytes = p->W_bytes = elem_bytes;
   return true;
 }
@@ -1633,19 +1668,46 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       else reg_sweeps<C, reg_rpl_max<C>()>(L, p->swp, p->d_err, st);
     } else {
       // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
-      // them), the block rows of [F12 | I] carried along
-      for (int k0 = 0; k0 < L.smax; k0 += NB) {
-        const int k1 = std::min(k0 + NB, L.smax), R = L.smax - k0;
-        const int m = L.ncols - k1;
-        // register panels (one CTA up to panel_reg_rows, a cluster of up to PC_CTAS CTAs of
-        // PC_ROWS rows in FP32) record the row permutation as pairs in swp; the shared- or
-        // global-memory panel records LAPACK-style swaps in piv
-        const int ncta = (R + PC_ROWS - 1) / PC_ROWS;
-        if (R <= panel_reg_rows<C>() || (f32 && ncta <= PC_CTAS)) {
+      // them), the block rows of [F12 | I] carried along.  Outer blocks of OB_PANELS panels:
+      // when the block's panels record their permutations as pairs (register panel up to
+      // panel_reg_rows rows, cluster panel up to PC_CTAS * PC_ROWS rows in FP32), the columns
+      // right of the block receive all the block's permutations, then the triangular solve
+      // with the block's unit lower L11 panel by panel, then one trailing GEMM with
+      // K = OB_PANELS * NB (a quarter of the passes over the trailing matrix); otherwise
+      // (the shared- or global-memory panel with LAPACK-style swaps) every panel updates
+      // all trailing columns.
+      const long rs = (long)L.nf * SWP_STRIDE;  // one swp record per panel of an outer block
+      for (int K0 = 0; K0 < L.smax; K0 += OB_PANELS * NB) {
+        const int K1 = std::min(K0 + OB_PANELS * NB, L.smax), R0 = L.smax - K0;
+        const bool pairs = R0 <= panel_reg_rows<C>() || (f32 && (R0 + PC_ROWS - 1) / PC_ROWS <= PC_CTAS);
+        if (!pairs) {
+          for (int k0 = K0; k0 < K1; k0 += NB) {
+            const int k1 = std::min(k0 + NB, L.smax), R = L.smax - k0, m = L.ncols - k1;
+            const size_t psm = (size_t)R * (k1 - k0) * sizeof(C);
+            if (psm <= PANEL_SMEM_MAX)
+              LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                        k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
+            else
+              LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
+                        k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
+            LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                      k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
+            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
+          }
+          continue;
+        }
+        // two levels only where the trailing matrix is large: below about 8 M entries per
+        // level the extra launches cost more than the passes they save (2D n = 1024)
+        const bool two = (double)L.nf * R0 * (L.ncols - K0) >= 8.0e6;
+        int np = 0;
+        for (int k0 = K0; k0 < K1; k0 += NB, ++np) {
+          const int k1 = std::min(k0 + NB, K1), R = L.smax - k0;
+          int* rec = p->swp + (two ? np : 0) * rs;
           if (R <= panel_reg_rows<C>()) {
             LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                      k_panel_reg<C><<<L.nf, (R + 31) / 32 * 32, 0, st>>>(L, k0, k1, p->swp, p->d_err));
+                      k_panel_reg<C><<<L.nf, (R + 31) / 32 * 32, 0, st>>>(L, k0, k1, rec, p->d_err));
           } else if constexpr (sizeof(C) == 8) {
+            const int ncta = (R + PC_ROWS - 1) / PC_ROWS;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(ncta, L.nf);
             cfg.blockDim = dim3(PC_ROWS);
@@ -1657,31 +1719,58 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             at[0].val.clusterDim.z = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            LS_LAUNCH("nd_panel_c64", st, LS_CUDA(cudaLaunchKernelEx(&cfg, k_panel_cluster<C>, L, k0, k1, p->swp, p->d_err)));
+            LS_LAUNCH("nd_panel_c64", st, LS_CUDA(cudaLaunchKernelEx(&cfg, k_panel_cluster<C>, L, k0, k1, rec, p->d_err)));
           }
-          LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                    k_trsm_lower_swp<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1, p->swp));
-        } else {
-          const size_t psm = (size_t)R * (k1 - k0) * sizeof(C);
-          if (psm <= PANEL_SMEM_MAX)
-            LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                      k_panel<C, true><<<L.nf, 512, psm, st>>>(L, k0, k1, p->d_err));
-          else
-            LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
-                      k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
-          LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                    k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
+          if (!two) {
+            // one level: permutation and forward substitution of every trailing column, then
+            // the trailing GEMM with K = NB
+            LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                      k_trsm_lower_swp<C><<<dim3(L.nf, (L.ncols - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1,
+                                                                                                 L.ncols, rec));
+            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
+            continue;
+          }
+          // the block's earlier L columns follow this panel's permutation
+          if (k0 > K0)
+            LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                      k_apply_swp<C><<<dim3(L.nf, (k0 - K0 + AP_COLS - 1) / AP_COLS), 256, 0, st>>>(L, k0, K0, k0, rec,
+                                                                                                    1, rs));
+          // the rest of the block: permutation, forward substitution, update below
+          if (k1 < K1) {
+            LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                      k_trsm_lower_swp<C><<<dim3(L.nf, (K1 - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1, K1, rec));
+            launch_gemm<C>(L, k1, L.smax, k1, K1, k0, k1, st, p->d_err);
+          }
         }
-        launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
+        if (two && K1 < L.ncols) {
+          const int m = L.ncols - K1;
+          LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                    k_apply_swp<C><<<dim3(L.nf, (m + AP_COLS - 1) / AP_COLS), 256, 0, st>>>(L, K0, K1, L.ncols, p->swp,
+                                                                                             np, rs));
+          for (int q = 0; q < np; ++q) {
+            const int k0 = K0 + q * NB, k1 = std::min(k0 + NB, K1);
+            LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                      k_trsm_lower_swp<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1, K1, L.ncols,
+                                                                                       (const int*)nullptr));
+            launch_gemm<C>(L, k1, K1, K1, L.ncols, k0, k1, st, p->d_err);
+          }
+          launch_gemm<C>(L, K1, L.smax, K1, L.ncols, K0, K1, st, p->d_err);
+        }
       }
-      // sweep 2: backward substitution with U11 on the own rows of [F12 | I]
+      // sweep 2: backward substitution with U11 on the own rows of [F12 | I], in outer
+      // blocks of OB_PANELS row blocks: inside a block each 32-row solve updates the block's
+      // rows above it, then one GEMM with K = OB_PANELS * NB updates the rows above the block
       const int nblk = (L.smax + NB - 1) / NB;
-      for (int jb = nblk - 1; jb >= 0; --jb) {
-        const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
-        const int m = L.ncols - L.smax;
-        LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
-                  k_trsm_upper<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, j0, j1));
-        launch_gemm<C>(L, 0, j0, L.smax, L.ncols, j0, j1, st, p->d_err);
+      const int m2 = L.ncols - L.smax;
+      for (int ob = (nblk - 1) / OB_PANELS; ob >= 0; --ob) {
+        const int J0 = ob * OB_PANELS * NB, J1 = std::min(J0 + OB_PANELS * NB, L.smax);
+        for (int jb = (J1 - 1) / NB; jb >= J0 / NB; --jb) {
+          const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
+          LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+                    k_trsm_upper<C><<<dim3(L.nf, (m2 + 127) / 128), 128, 0, st>>>(L, j0, j1));
+          launch_gemm<C>(L, J0, j0, L.smax, L.ncols, j0, j1, st, p->d_err);
+        }
+        launch_gemm<C>(L, 0, J0, L.smax, L.ncols, J0, J1, st, p->d_err);
       }
     }
     // ring rows: [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
