@@ -225,24 +225,40 @@ def algorithmic_bytes(cls, w, nd, counts, steps):
     raise ValueError(cls)
 
 
-# ncu DRAM traffic per launch of a kernel class, valid while the class's source file is
-# unchanged (sha1 of the file at capture time); see profiles/.
+# ncu DRAM traffic per launch of a kernel class, valid while the kernel's source is unchanged:
+# the sha1 of its source region (the text between two markers of the file) and of the
+# header it includes for its arithmetic, taken when the counters were captured; see profiles/.
+SWEEP_SRC = [("paper_1408_4495_gb300/csrc/nd.cu", "template <typename C> struct SweepK {",
+              "// r[rhs][N] -> T[group][N][RC]"),
+             ("paper_1408_4495_gb300/csrc/common.cuh", None, None)]
 TRAFFIC = {
-    "nd_fwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "4acda65409d8d01e40fddc9b1ed7f35c2a80287c",
-                   "bytes": 5848418},
-    "nd_bwd_c64": {"file": "paper_1408_4495_gb300/csrc/nd.cu", "sha1": "4acda65409d8d01e40fddc9b1ed7f35c2a80287c",
-                   "bytes": 8079419},
+    "nd_fwd_c64": {"src": SWEEP_SRC, "sha1": "2dfd35c36927992687d1a8cf6d3ebbad7a7353a0", "bytes": 5847217},
+    "nd_bwd_c64": {"src": SWEEP_SRC, "sha1": "2dfd35c36927992687d1a8cf6d3ebbad7a7353a0", "bytes": 8079202},
 }
 
 
-def recorded_traffic(cls):
+def source_sha1(src):
     import hashlib
+    h = hashlib.sha1()
+    for path, begin, end in src:
+        with open(os.path.join(ROOT, path), encoding="utf-8") as f:
+            text = f.read()
+        if begin is not None:
+            i = text.find(begin)
+            j = text.find(end, i + 1) if i >= 0 else -1
+            if i < 0 or j < 0:
+                return None
+            text = text[i:j]
+        h.update(text.encode())
+    return h.hexdigest()
+
+
+def recorded_traffic(cls):
     rec = TRAFFIC.get(cls)
     if not rec or not rec["sha1"]:
         return None
-    with open(os.path.join(ROOT, rec["file"]), "rb") as f:
-        if hashlib.sha1(f.read()).hexdigest() != rec["sha1"]:
-            return None
+    if source_sha1(rec["src"]) != rec["sha1"]:
+        return None
     return rec["bytes"]
 
 

@@ -759,12 +759,13 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
 // ---------------------------------------------------------------------------------------
 // Register-resident blocked factorization for fronts with at most 32 * RPL own rows.
 // Sweep 1 (LU of F11 with partial pivoting over the own rows, [F12 | I] carried along):
-// per panel of NB columns one CTA factors the panel with one own row per thread (rows in
-// shared memory), then one warp per trailing column (in registers) applies the panel's
-// row permutation, the forward substitution with the unit lower L_kk and the update of
-// the rows below.  Sweep 2 (U11 X = B on the
-// own rows of [F12 | I]): one warp per column runs the whole backward substitution with
-// its column in registers, the U11 columns staged in shared memory 32 at a time.
+// per panel of NB columns one CTA factors the panel with one own row per thread held in
+// registers (k_panel_reg), then one warp per trailing column (in registers) applies the
+// panel's row permutation, the forward substitution with the unit lower L_kk and the update
+// of the rows below.  Sweep 2 (U11 X = B on the own rows of [F12 | I]): one warp per column
+// runs the whole backward substitution with its column in registers, the U11 columns staged
+// in shared memory 32 at a time.  The blocked path of larger fronts uses the same panels
+// (and, from 513 to 4096 rows, their cluster form) with tensor-core trailing GEMMs.
 // ---------------------------------------------------------------------------------------
 constexpr int SWP_STRIDE = 1 + 4 * NB;  // per front: count, then (position, source) pairs
 constexpr int OB_PANELS = 4;            // panels per outer block of the blocked path
@@ -1319,8 +1320,6 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
   using Rl = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* B = reinterpret_cast<C*>(smem_raw);  // column major, ld = smax
-  __shared__ Rl sv[32];
-  __shared__ int si[32];
   const int z = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
   const int s = L.smax, fmax = L.fmax, nc = L.ncols;
   C* A = L.F + (size_t)z * fmax * nc;
