@@ -121,3 +121,24 @@ def test_laplace_iterations_stay_in_the_papers_band(shape):
     r = O.laplace_solve(n, W.enforce_buffer(w.V, 2), w.points, tol=1e-6)
     assert all(1 <= it <= 10 for it in r["iters"])
     assert all(res <= 1e-6 for res in r["resid"])
+
+
+def test_laplace_first_row_of_the_papers_tables():
+    """Figs. L31 / L32, first row: N = 1.2e4 = 23^3 and max|V| = 5.8e2 = 1/h^2 with h = 1/24,
+    n_p = 5 for both potentials.  The stand-in potentials match the printed N and max|V| (the
+    grid and the scaling of reading 12) but not the unprinted widths, so the iteration count
+    is checked against the printed one within a band, not for equality."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_laplace_np.json")) as f:
+        tab = {t["figure"]: t for t in json.load(f)["tables"]}
+    n = 23
+    h = O.grid_h(n)
+    assert abs(n**3 - tab["L31"]["N"][0]) / tab["L31"]["N"][0] < 0.02
+    assert abs(1 / h**2 - tab["L31"]["max_V"][0]) / tab["L31"]["max_V"][0] < 0.01
+    for fig, shape in (("L31", "gaussian"), ("L32", "ball")):
+        w = W.laplace_3d(n, 1, shape)
+        V = W.enforce_buffer(w.V, 2)
+        r = O.laplace_solve(n, V, w.points, tol=1e-6)
+        assert abs(r["iters"][0] - tab[fig]["n_p"][0]) <= 3, (fig, r["iters"])
+        assert r["resid"][0] <= 1e-6
