@@ -35,6 +35,11 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 * ``far_field`` (exterior evaluation): equals the direct exterior sum of the Green's
   function at a distant point (constant and sign), zero for m = 0, and reciprocity
   u_inf(theta; d) = u_inf(-d; -theta) of the discrete solution.               pinned
+* general domains (Sec. 4: ``general_support``, ``general_stencils``, ``general_assemble``,
+  ``general_solve``): the restricted solution equals the full-grid solution on Omega, the
+  support is supp(m) with its buffer, boundary stencils attain sigma_min of T(mu(i), :)
+  (recomputed by the direct sum), interior rows equal the rectangular ones, iteration
+  counts in the band of the Sec. 4 tables and stable under the random draw.   pinned
 """
 
 from .ls_oracle import *  # noqa: F401,F403

@@ -14,6 +14,9 @@ stand-ins of the same shape:
 * ``bumps``: sum of Gaussian bumps A exp(-|x-c|^2 / (2 w^2)) times the cutoff.
 * ``smooth_noise``: white noise convolved with a Gaussian of width 4h, scaled to a given
   max |m|, times the cutoff.
+* ``cavity``: the media of Sec. 4 (general domains): a smoothed cavity of an l2 or l1 ball,
+  m = A s((rho - |x - c|_p) / delta) with the C-infinity step s, so that supp(m) is the open
+  ball of radius rho (the unknowns of the general-domain method) and m = A inside rho - delta.
 * ``laplace_3d``: the potentials of Sec. 5 (a negative Gaussian, or a smoothed indicator of
   a ball, scaled so that max |V| = 1/h^2 as in the paper's tables) times the cutoff, and
   delta sources near the top-left corner of the middle cross-section x_1 = 1/2.
@@ -195,3 +198,17 @@ def laplace_3d(n: int = 64, nsrc: int = 8, shape: str = "gaussian", seed: int = 
             seen.add(tuple(q))
             pts.append(q)
     return LaplaceWorkload(f"3d_laplace_{shape}_n{n}", n, V, np.array(pts, dtype=np.int64))
+
+
+def cavity(n: int, d: int, norm: str = "l2", rho: float = 0.4, delta: float = 0.1, amp: float = -0.3,
+           centre=None) -> np.ndarray:
+    """Sec. 4 stand-in: smoothed cavity of an l2 (norm="l2") or l1 (norm="l1") ball."""
+    X = np.meshgrid(*([grid_x(n)] * d), indexing="ij")
+    c = centre if centre is not None else [0.5] * d
+    if norm == "l2":
+        r = np.sqrt(sum((X[a] - c[a]) ** 2 for a in range(d)))
+    elif norm == "l1":
+        r = sum(np.abs(X[a] - c[a]) for a in range(d))
+    else:
+        raise ValueError("norm must be 'l2' or 'l1'")
+    return amp * _smooth_step((rho - r) / delta)
