@@ -17,6 +17,9 @@ stand-ins of the same shape:
 * ``cavity``: the media of Sec. 4 (general domains): a smoothed cavity of an l2 or l1 ball,
   m = A s((rho - |x - c|_p) / delta) with the C-infinity step s, so that supp(m) is the open
   ball of radius rho (the unknowns of the general-domain method) and m = A inside rho - delta.
+* ``serving_stream``: a seeded Poisson stream of requests of the serving mix: 2D and 3D grids,
+  omega / 2 pi = n / 8, 4-8 Gaussian bumps per medium rescaled to max|m| <= 0.3, 1..k plane
+  waves per request; media drawn from a pool so that some requests share a medium.
 * ``laplace_3d``: the potentials of Sec. 5 (a negative Gaussian, or a smoothed indicator of
   a ball, scaled so that max |V| = 1/h^2 as in the paper's tables) times the cutoff, and
   delta sources near the top-left corner of the middle cross-section x_1 = 1/2.
@@ -212,3 +215,31 @@ def cavity(n: int, d: int, norm: str = "l2", rho: float = 0.4, delta: float = 0.
     else:
         raise ValueError("norm must be 'l2' or 'l1'")
     return amp * _smooth_step((rho - r) / delta)
+
+
+def serving_stream(count: int, rate: float, seed: int = 1006, grids=((2, 128), (2, 256), (3, 16), (3, 32)),
+                   weights=(0.35, 0.35, 0.15, 0.15), max_dirs: int = 32, pool: int | None = None):
+    """Seeded serving mix: ``count`` requests with exponential inter-arrival times of mean
+    1 / rate seconds.  Each entry is (d, n, omega, m, directions, arrival).  With ``pool`` set,
+    each grid draws its medium from ``pool`` seeded media, so requests can share a medium."""
+    rng = np.random.default_rng(seed)
+    media = {}
+    out = []
+    t = 0.0
+    for _ in range(count):
+        t += rng.exponential(1.0 / rate)
+        d, n = grids[rng.choice(len(grids), p=np.asarray(weights) / np.sum(weights))]
+        mseed = int(rng.integers(0, pool)) if pool else int(rng.integers(0, 2**31))
+        key = (d, n, mseed)
+        if key not in media:
+            mr = np.random.default_rng(mseed)
+            nb = int(mr.integers(4, 9))
+            m = bumps(n, d, mr.uniform(-0.3, 0.3, nb), mr.uniform(0.05, 0.12, nb), mr.uniform(0.25, 0.75, (nb, d)))
+            peak = np.max(np.abs(m))
+            if peak > 0.3:
+                m *= 0.3 / peak
+            media[key] = enforce_buffer(m, 2)
+        k = int(rng.integers(1, max_dirs + 1))
+        dirs = directions_circle(k) if d == 2 else directions_sphere(k, int(rng.integers(0, 2**31)))
+        out.append((d, n, 2 * math.pi * n / 8, media[key], dirs, t))
+    return out
