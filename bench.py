@@ -202,12 +202,28 @@ def run_reference(args):
 MODELED = ("fft_row_fwd", "fft_col_sym", "fft_row_inv", "stencil", "nd_fwd", "nd_bwd")
 
 
-def algorithmic_bytes(cls, w, nd, counts, steps):
+def live_rhs(infos):
+    """Average number of right-hand sides a GMRES iteration's launches carry: converged
+    right-hand sides are compacted out, so over one cycle the iterations move sum_j iters_j
+    right-hand sides in max_j iters_j launch sets (per step; ``infos`` holds one list of
+    per-right-hand-side iteration counts per step)."""
+    tot = sum(sum(step) for step in infos)
+    sets = sum(max(step) for step in infos if step)
+    return tot / sets if sets else 0.0
+
+
+# classes launched once per GMRES iteration on the live right-hand sides only; the others
+# (float-float residual and right-hand-side passes) carry every right-hand side
+PER_ITERATION = ("fft_row_fwd_c64", "fft_col_sym_c64", "fft_row_inv_c64", "stencil", "nd_fwd", "nd_bwd")
+
+
+def algorithmic_bytes(cls, w, nd, counts, steps, rhs=None):
     """Average bytes one launch of a kernel class must move (reads + writes), from the pass
     design: FP32 complex = 8 B, FP64 complex = 16 B, lines of n (grid) or L = 2n (padded).
     The nested-dissection sweeps read every factor block once and move the front vectors;
-    one launch per level, so the per-launch figure is a sweep's bytes / its launches."""
-    n, N, R = w.n, w.n ** w.d, w.nrhs
+    one launch per level, so the per-launch figure is a sweep's bytes / its launches.
+    ``rhs``: right-hand sides per launch (default: all of the workload's)."""
+    n, N, R = w.n, w.n ** w.d, (w.nrhs if rhs is None else rhs)
     c = 8 if cls.endswith("_c64") else 16
     wb = 4 if c == 8 else 8
     if cls.startswith("fft_row_fwd"):      # read u (n per line), weights once; write L per line
@@ -337,7 +353,8 @@ def run_gpu(args):
     # stream (graphs are bypassed while launches are timed); per-class device time shares
     roof = None
     k_roof = max(3, min(args.steps, 10))
-    roof_ms, _, rprof, _ = timed(s_mix, k_roof, 1, "*")
+    roof_ms, rinfos, rprof, _ = timed(s_mix, k_roof, 1, "*")
+    r_live = live_rhs([[i.iters for i in inf] for inf in rinfos])
     by_cls = rprof.get("ms_by_class", {})
     tot_cls = sum(by_cls.values()) or 1.0
     shares = {k: round(v / tot_cls, 4) for k, v in sorted(by_cls.items(), key=lambda x: -x[1])}
@@ -347,14 +364,25 @@ def run_gpu(args):
     if by_cls.get(cls, 0) > 0 and rprof["counts"].get(cls, 0) > 0:
         nlaunch = rprof["counts"][cls]
         avg_ms = by_cls[cls] / nlaunch
-        abytes = algorithmic_bytes(cls, w, nd, rprof["counts"], k_roof)
+        abytes = algorithmic_bytes(cls, w, nd, rprof["counts"], k_roof,
+                                   rhs=r_live if cls.startswith(PER_ITERATION) else None)
         achieved = abytes / (avg_ms / 1e3) / 1e9
         peak, peak_src = measured_hbm_peak()
         roof = {"kernel": cls, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(cls), "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_ms * 1e3,
                 "launches_timed": nlaunch, "steps_timed": k_roof,
-                "share_of_kernel_time": by_cls[cls] / tot_cls}
+                "share_of_kernel_time": by_cls[cls] / tot_cls, "live_rhs_per_iteration": r_live}
+    # the same model for every class that has one (HBM-bound passes and sweeps)
+    by_model = {}
+    for c2 in sorted(by_cls):
+        if c2.startswith(MODELED) and rprof["counts"].get(c2, 0) > 0:
+            avg2 = by_cls[c2] / rprof["counts"][c2]
+            ab2 = algorithmic_bytes(c2, w, nd, rprof["counts"], k_roof,
+                                    rhs=r_live if c2.startswith(PER_ITERATION) else None)
+            pk, _ = measured_hbm_peak()
+            by_model[c2] = {"achieved_gbs": ab2 / (avg2 / 1e3) / 1e9, "frac": ab2 / (avg2 / 1e3) / 1e9 / pk,
+                            "avg_launch_us": avg2 * 1e3, "algorithmic_bytes_per_launch": ab2}
 
     # exterior evaluation after the step: far-field pattern of the 16 solutions in 64 directions
     obs_dev = torch.tensor(np.array([[math.cos(2 * math.pi * k / 64), math.sin(2 * math.pi * k / 64)] for k in range(64)])
@@ -486,7 +514,8 @@ def run_gpu(args):
                                "iters": {"min": min(its64), "max": max(its64)}},
                 "mixed_over_fp64": value / value64, "laplace_3d": lap, "far_field": far, "serving": serving,
                 "setup_ms": setup_s * 1e3, "nd": nd,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "roofline_by_class": by_model, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
                 "launches_by_class": prof["counts"], "device_time_shares": shares, "clocks": clocks}
         print(json.dumps(line), flush=True)
     s_mix.close()

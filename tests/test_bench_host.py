@@ -1,0 +1,29 @@
+"""Host-side arithmetic of bench.py's roofline model (no GPU): the live right-hand-side count
+of the GMRES iterations and the per-launch algorithmic bytes."""
+
+import numpy as np
+
+import bench
+from paper_1408_4495_gb300 import workloads as W
+
+
+def test_live_rhs_counts_compacted_iterations():
+    # 16 right-hand sides, 12 converge after 3 iterations and 4 after 4: the first three
+    # iterations carry 16, the fourth carries 4, i.e. 52 right-hand sides in 4 launch sets
+    step = [3] * 12 + [4] * 4
+    assert bench.live_rhs([step]) == 52 / 4
+    assert bench.live_rhs([step, [2] * 16]) == (52 + 32) / (4 + 2)
+    assert bench.live_rhs([]) == 0.0
+
+
+def test_algorithmic_bytes_scale_with_the_right_hand_sides():
+    w = W.bumps_2d(64, 8.0, 3, 16, 1)
+    nd = {"fwd_factor_bytes": 1e6, "bwd_factor_bytes": 2e6, "fwd_bytes_per_rhs": 1e4,
+          "bwd_bytes_per_rhs": 2e4, "levels": 10}
+    n, N = 64, 64 * 64
+    assert bench.algorithmic_bytes("fft_row_fwd_c64", w, nd, None, None) == 16 * N * 8 * 3 + N * 4
+    assert bench.algorithmic_bytes("fft_row_fwd_c64", w, nd, None, None, rhs=8) == 8 * N * 8 * 3 + N * 4
+    assert bench.algorithmic_bytes("fft_col_sym_cff", w, nd, None, None) == 16 * 2 * (n * 2 * n) * 16 + (n + 1) ** 2 * 16
+    assert bench.algorithmic_bytes("nd_fwd_c64", w, nd, None, None, rhs=4) == (1e6 + 4 * 1e4) / 10
+    assert "stencil_c64".startswith(bench.PER_ITERATION)
+    assert not "fft_row_fwd_cff".startswith(bench.PER_ITERATION)
