@@ -35,6 +35,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 * ``far_field`` (exterior evaluation): equals the direct exterior sum of the Green's
   function at a distant point (constant and sign), zero for m = 0, and reciprocity
   u_inf(theta; d) = u_inf(-d; -theta) of the discrete solution.               pinned
+* ``k0_corrected`` (higher-order weight of the singular point, Sec. 2.1): the discrete
+  convolution of a smooth field converges with order ~4 (against ~2 for the ball weight),
+  checked against an independent radial quadrature; independent of the fitting width. pinned
 * general domains (Sec. 4: ``general_support``, ``general_stencils``, ``general_assemble``,
   ``general_solve``): the restricted solution equals the full-grid solution on Omega, the
   support is supp(m) with its buffer, boundary stencils attain sigma_min of T(mu(i), :)

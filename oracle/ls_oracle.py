@@ -21,7 +21,7 @@ import scipy.sparse.linalg as spla
 import scipy.special as sp
 
 __all__ = [
-    "grid_h", "grid_coords", "green", "k0_weight", "kernel_value", "kernel_table",
+    "grid_h", "grid_coords", "green", "k0_weight", "k0_corrected", "kernel_value", "kernel_table",
     "dense_K", "apply_K_direct", "apply_K_fft", "apply_operator", "plane_wave", "rhs",
     "point_class", "class_mu", "class_far_set", "stencil", "all_stencils",
     "assemble", "nd_order", "Preconditioner", "gmres_right", "solve",
@@ -88,26 +88,60 @@ def k0_weight(d: int, omega: float, h: float) -> complex:
     raise ValueError("d must be 2 or 3")
 
 
-def kernel_value(d: int, omega: float, h: float, t) -> np.ndarray:
+def _radial_integral_G_gauss(d: int, omega: float, s: float) -> complex:
+    """int over R^d of G(x) exp(-|x|^2 / (2 s^2)) dx, as a radial quadrature."""
+    import scipy.integrate as si
+    if d == 2:
+        g = lambda r: 2 * math.pi * r * 0.25 * complex(-sp.y0(omega * r), sp.j0(omega * r))
+    else:
+        g = lambda r: r * complex(math.cos(omega * r), math.sin(omega * r))  # 4 pi r^2 / (4 pi r)
+    w = lambda r: math.exp(-r * r / (2 * s * s))
+    pts = [s * q for q in (0.25, 0.5, 1, 2, 4)]
+    re = si.quad(lambda r: g(r).real * w(r), 0, 12 * s, points=pts, limit=500, epsabs=0, epsrel=1e-11)[0]
+    im = si.quad(lambda r: g(r).imag * w(r), 0, 12 * s, points=pts, limit=500, epsabs=0, epsrel=1e-11)[0]
+    return complex(re, im)
+
+
+def k0_corrected(d: int, omega: float, h: float, width: float = 8.0) -> complex:
+    """One-point correction of the trapezoidal rule at the singular point (Sec. 2.1: accuracy
+    O(h^4 log(1/h)) in 2D, citing Duan and Rokhlin; the weight is not printed).
+
+    Reading: the corrected rule sum_{j != 0} G(h j) h^d f(h j) + k_0 f(0) must integrate
+    G f for smooth f; its error for the plain trapezoidal sum is f(0) times a constant
+    (depending on h, omega) plus O(h^4 log h) terms, so requiring exactness for one smooth
+    radial f fixes k_0 to that order.  Here f is the Gaussian of width ``width`` h, the
+    integral a radial quadrature and the lattice sum runs over |j| <= 11 width."""
+    s = width * h
+    M = int(math.ceil(11 * width))
+    ax = np.arange(-M, M + 1)
+    J = np.stack(np.meshgrid(*([ax] * d), indexing="ij"), -1).reshape(-1, d)
+    J = J[np.any(J != 0, axis=1)]
+    r = h * np.linalg.norm(J, axis=1)
+    lattice = np.sum(green(d, omega, r) * h**d * np.exp(-r * r / (2 * s * s)))
+    return complex(_radial_integral_G_gauss(d, omega, s) - lattice)
+
+
+def kernel_value(d: int, omega: float, h: float, t, k0=None) -> np.ndarray:
     """k_t = G(h t) h^d for t != 0 and k_0 at t = 0 (Sec. 2.1, 2D and 3D forms).
 
-    ``t`` is an integer array of shape (..., d)."""
+    ``t`` is an integer array of shape (..., d); ``k0`` overrides the weight of the singular
+    point (default: the ball integral of k0_weight; k0_corrected for the higher-order rule)."""
     t = np.asarray(t, dtype=np.float64)
     r = h * np.sqrt(np.sum(t * t, axis=-1))
     out = np.empty(r.shape, dtype=np.complex128)
     nz = r > 0
     out[nz] = green(d, omega, r[nz]) * h**d
-    out[~nz] = k0_weight(d, omega, h)
+    out[~nz] = k0_weight(d, omega, h) if k0 is None else k0
     return out
 
 
-def kernel_table(n: int, d: int, omega: float) -> np.ndarray:
+def kernel_table(n: int, d: int, omega: float, k0=None) -> np.ndarray:
     """Table of k_t for every t in (-n, n)^d, shape (2n-1,)*d, entry t stored at t + n - 1.
 
     These are all the offsets i - j between two grid points (Sec. 2.1, eq. lsd)."""
     t1 = np.arange(-(n - 1), n)
     T = np.stack(np.meshgrid(*([t1] * d), indexing="ij"), axis=-1)
-    return kernel_value(d, omega, grid_h(n), T)
+    return kernel_value(d, omega, grid_h(n), T, k0)
 
 
 # ----------------------------------------------------------------------------------------
