@@ -172,6 +172,19 @@ ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u
  */
 ls_status ls_far_field(ls_ctx* c, int nrhs, const double* dirs, const double* us, int nobs, const double* obs,
                        double* out);
+/*
+ * ls_k0_weight -- Sec. 2.1: the weight k_0 of the singular point of the Nystrom table, on the
+ * host in FP64 (no context, no device work).
+ *   rule LS_K0_BALL:      the integral of G over the disk / ball of area / volume h^d (the
+ *                         weight every context uses; second-order accurate).
+ *   rule LS_K0_CORRECTED: the one-point correction of the trapezoidal rule (fourth order up
+ *                         to a log, as Sec. 2.1 states): the weight for which the corrected
+ *                         rule integrates G f exactly for a Gaussian f of width 8 h.
+ *   dim 2 or 3; omega >= 0 (0 is the 3D Laplace kernel of Sec. 5; 2D needs omega > 0);
+ *   h > 0.  out: 2 doubles (re, im).  LS_EINVAL on bad arguments.
+ */
+typedef enum { LS_K0_BALL = 0, LS_K0_CORRECTED = 1 } ls_k0_rule;
+ls_status ls_k0_weight(int dim, double omega, double h, int rule, double* out);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

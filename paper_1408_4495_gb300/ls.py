@@ -22,11 +22,12 @@ LIB_PATH = os.path.join(HERE, "_lib", "libls.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ENOCONV, LS_ESTATE, LS_ETIMEOUT, LS_EBUFFER = range(8)
 LS_PREC_FP64, LS_PREC_MIXED, LS_PREC_FF = 0, 1, 2
+LS_K0_BALL, LS_K0_CORRECTED = 0, 1
 STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS_ESTATE", "LS_ETIMEOUT", "LS_EBUFFER"]
 
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
-           "ls_far_field", "ls_last_error", "ls_free",
+           "ls_far_field", "ls_k0_weight", "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
 
@@ -73,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_setup_laplace.argtypes = [ctypes.POINTER(LsGrid), vp, vp, ctypes.POINTER(vp)]
     lib.ls_rhs_point_source.argtypes = [vp, ip, vp, vp, vp]
     lib.ls_far_field.argtypes = [vp, ip, vp, vp, ip, vp, vp]
+    lib.ls_k0_weight.argtypes = [ip, dp, dp, ip, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -126,6 +128,16 @@ def profile_stop() -> dict:
     buf = ctypes.create_string_buffer(1 << 16)
     load().ls_profile_stop(buf, len(buf))
     return json.loads(buf.value.decode())
+
+
+def k0_weight(dim: int, omega: float, h: float, rule: int = LS_K0_BALL) -> complex:
+    """ls_k0_weight: the weight of the singular point (host computation, no device)."""
+    lib = load()
+    out = (ctypes.c_double * 2)()
+    st = lib.ls_k0_weight(int(dim), float(omega), float(h), int(rule), out)
+    if st != LS_OK:
+        raise LsError(st, "ls_k0_weight: bad arguments")
+    return complex(out[0], out[1])
 
 
 @dataclass
