@@ -8,7 +8,7 @@ the method of L. Ying, "Sparsifying Preconditioner for the Lippmann-Schwinger Eq
 imports it; inputs (media, directions) are passed in as arrays.
 
 Every function cites the passage of the paper it follows (section / equation).  Readings
-taken where the paper is silent are stated in the docstrings and listed in the design doc.
+taken where the paper is silent are stated in the docstrings.
 
 Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 

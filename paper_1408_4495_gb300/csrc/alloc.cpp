@@ -63,7 +63,7 @@ void* dev_alloc(size_t bytes) {
   void* p = nullptr;
   if (cudaMalloc(&p, cls) != cudaSuccess) {
     cudaGetLastError();
-    // give the cached blocks of this device back to the driver and retry once
+    // free the cached blocks of this device (cudaFree) and retry once
     std::multimap<std::pair<int, size_t>, void*> drop;
     {
       std::lock_guard<std::mutex> lk(P.mu);
