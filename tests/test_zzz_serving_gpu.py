@@ -22,7 +22,7 @@ def LS():
 
 
 def test_served_results_equal_results_alone(LS):
-    stream = W.serving_stream(12, 200.0, seed=11, grids=((2, 64), (2, 128), (3, 16)), weights=(0.4, 0.4, 0.2),
+    stream = W.serving_stream(12, 1000.0, seed=11, grids=((2, 64), (2, 128), (3, 16)), weights=(0.4, 0.4, 0.2),
                               max_dirs=6, pool=3)
     reqs = [S.Request(i, d, n, om, m, dirs, t) for i, (d, n, om, m, dirs, t) in enumerate(stream)]
     be = S.LibBackend(mixed=True, tol=1e-6)
