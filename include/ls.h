@@ -185,6 +185,26 @@ ls_status ls_far_field(ls_ctx* c, int nrhs, const double* dirs, const double* us
  */
 typedef enum { LS_K0_BALL = 0, LS_K0_CORRECTED = 1 } ls_k0_rule;
 ls_status ls_k0_weight(int dim, double omega, double h, int rule, double* out);
+/*
+ * Sec. 4, general domains (host computations in FP64, no context, no device work).
+ * ls_general_support: the unknowns of the general-domain method, the grid points within
+ *   infinity distance b + 1 of supp(m) (the support with the buffer that the rectangular
+ *   method keeps at the box boundary).  m: n^d doubles (C order), mask: n^d bytes written
+ *   (1 = unknown).
+ * ls_general_boundary_stencils: the stencils of the boundary points of the unknowns (those
+ *   with a neighbour, at infinity distance 1, that is not an unknown): alpha = the unit
+ *   minimiser of |alpha T(mu(i), :)|, mu(i) the neighbours among the unknowns, T the sketch
+ *   (K omega^2 m) R of the rows of K omega^2 m by r >= 3^d Gaussian columns.
+ *   mask: n^d bytes as written by ls_general_support; T: (number of unknowns) x r complex
+ *   doubles, rows in increasing flat index of the unknowns; alpha: (number of unknowns) x 3^d
+ *   complex doubles written (offset index sum_a (t_a + 1) 3^(d-1-a); zero for interior points
+ *   and for offsets that are not unknowns; the coefficient at offset 0 real positive);
+ *   boundary: (number of unknowns) ints written, 1 for boundary points.
+ *   LS_EINVAL on bad arguments or when a smallest singular value is not simple.
+ */
+ls_status ls_general_support(int dim, int n, const double* m, int b, unsigned char* mask);
+ls_status ls_general_boundary_stencils(int dim, int n, const unsigned char* mask, const double* T, int r,
+                                       double* alpha, int* boundary);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

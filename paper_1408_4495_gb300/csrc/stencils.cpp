@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "ls.h"
 
 namespace ls {
 
@@ -115,6 +116,31 @@ void jacobi_svd(const std::vector<cd>& R, int c, std::vector<double>& sig, std::
     for (int i = 0; i < c; ++i) s += std::norm(X[(size_t)i * c + j]);
     sig[j] = std::sqrt(s);
   }
+}
+
+// alpha = U(:, end)^* for K = U S V^* given as c rows of length r (row-major K[i * r + j]),
+// r >= c: the tall-skinny route of solve_class on a single chunk.  Returns false when the
+// smallest singular value is not simple (alpha undetermined).
+bool min_left_singular(const cd* K, int c, int r, std::vector<cd>& alpha) {
+  std::vector<cd> A((size_t)r * c);  // column-major r x c: K^*
+  for (int col = 0; col < c; ++col)
+    for (int row = 0; row < r; ++row) A[(size_t)col * r + row] = std::conj(K[(size_t)col * r + row]);
+  householder_r(A.data(), r, c);
+  std::vector<cd> R((size_t)c * c);
+  for (int i = 0; i < c; ++i)
+    for (int j = 0; j < c; ++j) R[(size_t)i * c + j] = j >= i ? A[(size_t)j * r + i] : cd(0, 0);
+  std::vector<double> sig;
+  std::vector<cd> V;
+  jacobi_svd(R, c, sig, V);
+  int jmin = 0, j2 = -1;
+  for (int j = 1; j < c; ++j)
+    if (sig[j] < sig[jmin]) jmin = j;
+  for (int j = 0; j < c; ++j)
+    if (j != jmin && (j2 < 0 || sig[j] < sig[j2])) j2 = j;
+  if (j2 >= 0 && sig[jmin] > 0 && sig[j2] / sig[jmin] < 1.0 + 1e-8) return false;
+  alpha.resize(c);
+  for (int i = 0; i < c; ++i) alpha[i] = std::conj(V[(size_t)i * c + jmin]);
+  return true;
 }
 
 struct ClassGeom {
@@ -306,3 +332,112 @@ void compute_stencils(int d, int n, int b, const std::vector<double2>& ktq, std:
 }
 
 }  // namespace ls
+
+// ---------------------------------------------------------------------------------------
+// Sec. 4, general domains (host, FP64).  The unknowns are the grid points within infinity
+// distance b + 1 of supp(m): the support with the buffer that the rectangular method keeps
+// at the box boundary, so that a boundary point's objective only sees columns where m
+// vanishes nearby, as in the far sets of Sec. 3.1.  A point is interior when all 3^d
+// neighbours are unknowns; a boundary point i takes the unit alpha minimising
+// |alpha T(mu(i), :)| with T = (K omega^2 m) R the sketch of the rows of K omega^2 m by r
+// Gaussian columns and mu(i) its neighbours among the unknowns: alpha = U(:, end)^* of
+// T(mu(i), :) = U S V^*, the coefficient at offset 0 made real and positive.
+// ---------------------------------------------------------------------------------------
+
+extern "C" ls_status ls_general_support(int dim, int n, const double* m, int b, unsigned char* mask) {
+  if ((dim != 2 && dim != 3) || n < 1 || b < 0 || !m || !mask) return LS_EINVAL;
+  const long N = dim == 2 ? (long)n * n : (long)n * n * n;
+  std::vector<unsigned char> cur(N), nxt(N);
+  for (long i = 0; i < N; ++i) cur[i] = m[i] != 0.0;
+  const long stride[3] = {dim == 2 ? (long)n : (long)n * n, dim == 2 ? 1L : (long)n, 1L};
+  const int w = b + 1;
+  // infinity-norm dilation = a running maximum along each axis in turn
+  for (int a = 0; a < dim; ++a) {
+    for (long i = 0; i < N; ++i) {
+      const long c = (i / stride[a]) % n;
+      unsigned char v = 0;
+      for (int t = -w; t <= w && !v; ++t) {
+        const long cc = c + t;
+        if (cc >= 0 && cc < n) v = cur[i + t * stride[a]];
+      }
+      nxt[i] = v;
+    }
+    cur.swap(nxt);
+  }
+  std::copy(cur.begin(), cur.end(), mask);
+  return LS_OK;
+}
+
+extern "C" ls_status ls_general_boundary_stencils(int dim, int n, const unsigned char* mask, const double* T, int r,
+                                                  double* alpha, int* boundary) {
+  using namespace ls;
+  if ((dim != 2 && dim != 3) || n < 1 || !mask || !T || !alpha || !boundary || r < 1) return LS_EINVAL;
+  const long N = dim == 2 ? (long)n * n : (long)n * n * n;
+  const int P3 = dim == 2 ? 9 : 27;
+  if (r < P3) return LS_EINVAL;  // the sketch needs at least as many columns as a stencil has points
+  std::vector<long> pos(N, -1), pts;
+  for (long i = 0; i < N; ++i)
+    if (mask[i]) {
+      pos[i] = (long)pts.size();
+      pts.push_back(i);
+    }
+  const long NO = (long)pts.size();
+  const cd* Tc = reinterpret_cast<const cd*>(T);
+  cd* Ac = reinterpret_cast<cd*>(alpha);
+  std::fill(Ac, Ac + (size_t)NO * P3, cd(0, 0));
+  const int nthreads = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  std::vector<int> bad(nthreads, 0);
+  auto work = [&](int tid) {
+    std::vector<cd> K;
+    std::vector<cd> al;
+    for (long k = tid; k < NO; k += nthreads) {
+      const long i = pts[k];
+      int c[3] = {0, 0, 0};
+      long q = i;
+      for (int a = dim - 1; a >= 0; --a) {
+        c[a] = (int)(q % n);
+        q /= n;
+      }
+      std::vector<int> toff;
+      std::vector<long> rows;
+      for (int t = 0; t < P3; ++t) {
+        int tt = t;
+        long j = 0;
+        bool in = true;
+        int y[3] = {0, 0, 0};
+        for (int a = dim - 1; a >= 0; --a) {
+          y[a] = c[a] + (tt % 3) - 1;
+          tt /= 3;
+          if (y[a] < 0 || y[a] >= n) in = false;
+        }
+        if (!in) continue;
+        for (int a = 0; a < dim; ++a) j = j * n + y[a];
+        if (pos[j] < 0) continue;
+        toff.push_back(t);
+        rows.push_back(pos[j]);
+      }
+      const int cnt = (int)toff.size();
+      boundary[k] = cnt < P3 ? 1 : 0;
+      if (cnt == P3) continue;
+      K.resize((size_t)cnt * r);
+      for (int u = 0; u < cnt; ++u)
+        for (int j = 0; j < r; ++j) K[(size_t)u * r + j] = Tc[(size_t)rows[u] * r + j];
+      if (!min_left_singular(K.data(), cnt, r, al)) {
+        bad[tid] = 1;
+        continue;
+      }
+      int ci = -1;
+      for (int u = 0; u < cnt; ++u)
+        if (toff[u] == (P3 - 1) / 2) ci = u;
+      const cd ph = std::abs(al[ci]) > 0 ? al[ci] / std::abs(al[ci]) : cd(1, 0);
+      for (int u = 0; u < cnt; ++u) Ac[(size_t)k * P3 + toff[u]] = al[u] / ph;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto& t : th) t.join();
+  for (int b : bad)
+    if (b) return LS_EINVAL;
+  return LS_OK;
+}

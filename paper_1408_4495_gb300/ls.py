@@ -27,7 +27,8 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
-           "ls_far_field", "ls_k0_weight", "ls_last_error", "ls_free",
+           "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
+           "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
 
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_rhs_point_source.argtypes = [vp, ip, vp, vp, vp]
     lib.ls_far_field.argtypes = [vp, ip, vp, vp, ip, vp, vp]
     lib.ls_k0_weight.argtypes = [ip, dp, dp, ip, vp]
+    lib.ls_general_support.argtypes = [ip, ip, vp, ip, vp]
+    lib.ls_general_boundary_stencils.argtypes = [ip, ip, vp, vp, ip, vp, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -138,6 +141,31 @@ def k0_weight(dim: int, omega: float, h: float, rule: int = LS_K0_BALL) -> compl
     if st != LS_OK:
         raise LsError(st, "ls_k0_weight: bad arguments")
     return complex(out[0], out[1])
+
+
+def general_support(m: np.ndarray, b: int = 2) -> np.ndarray:
+    """ls_general_support: boolean mask of the general-domain unknowns (Sec. 4)."""
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    mask = np.empty(m.shape, dtype=np.uint8)
+    st = load().ls_general_support(m.ndim, m.shape[0], _ptr(m), int(b), _ptr(mask))
+    if st != LS_OK:
+        raise LsError(st, "ls_general_support: bad arguments")
+    return mask.astype(bool)
+
+
+def general_boundary_stencils(mask: np.ndarray, T: np.ndarray):
+    """ls_general_boundary_stencils: (alpha (unknowns x 3^d), boundary flags) from the sketch T
+    (unknowns x r, rows in increasing flat index of the unknowns)."""
+    mk = np.ascontiguousarray(mask, dtype=np.uint8)
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    no, r = T.shape
+    d = mk.ndim
+    alpha = np.empty((no, 3**d), dtype=np.complex128)
+    bnd = np.empty(no, dtype=np.int32)
+    st = load().ls_general_boundary_stencils(d, mk.shape[0], _ptr(mk), _ptr(T), int(r), _ptr(alpha), _ptr(bnd))
+    if st != LS_OK:
+        raise LsError(st, "ls_general_boundary_stencils: bad arguments or an undetermined stencil")
+    return alpha, bnd.astype(bool)
 
 
 @dataclass

@@ -1,0 +1,65 @@
+"""The library's host steps of the general-domain method (Sec. 4) against the oracle: the
+unknowns (supp(m) with its b + 1 buffer) and the boundary stencils from a sketch T.  T is an
+input of the library step (on the GPU path it comes from the operator passes applied to R);
+here the test forms it with the oracle's FFT apply from a seeded R."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1408_4495_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def LS():
+    from paper_1408_4495_gb300 import build, ls
+    build.build()
+    return ls
+
+
+CASES = [(2, 32, 4.0, "l2", 0.35), (2, 32, 4.0, "l1", 0.38), (3, 12, 1.0, "l2", 0.25)]
+
+
+@pytest.mark.parametrize("d,n,freq,norm,rho", CASES)
+def test_general_support_matches_the_oracle(LS, d, n, freq, norm, rho):
+    m = W.cavity(n, d, norm, rho=rho)
+    mask = LS.general_support(m, 2)
+    ref = np.zeros(n**d, dtype=bool)
+    ref[O.general_support(m, 2)] = True
+    assert np.array_equal(mask.reshape(-1), ref)
+
+
+@pytest.mark.parametrize("d,n,freq,norm,rho", CASES)
+def test_general_boundary_stencils_match_the_oracle(LS, d, n, freq, norm, rho):
+    omega = 2 * math.pi * freq
+    m = W.cavity(n, d, norm, rho=rho)
+    idx = O.general_support(m, 2)
+    R = np.random.default_rng(5).standard_normal((len(idx), 2 * 3**d))
+    kt = O.kernel_table(n, d, omega)
+    T = np.empty((len(idx), R.shape[1]), dtype=np.complex128)
+    for q in range(R.shape[1]):
+        full = np.zeros(n**d, dtype=np.complex128)
+        full[idx] = R[:, q]
+        T[:, q] = O.apply_K_fft(kt, (omega**2 * m.reshape(-1) * full).reshape((n,) * d)).reshape(-1)[idx]
+    mask = np.zeros(n**d, dtype=np.uint8)
+    mask[idx] = 1
+    alpha, bnd = LS.general_boundary_stencils(mask.reshape((n,) * d), T)
+    _, interior, ref, _, _ = O.general_stencils(n, d, omega, m, R)
+    assert np.array_equal(bnd, ~interior)
+    for k, i in enumerate(idx):
+        if interior[k]:
+            assert np.all(alpha[k] == 0)
+            continue
+        offs, a = ref[int(i)]
+        row = np.zeros(3**d, dtype=np.complex128)
+        for t, v in zip(offs, a):
+            row[sum((t[x] + 1) * 3 ** (d - 1 - x) for x in range(d))] = v
+        assert np.max(np.abs(alpha[k] - row)) < 1e-9, (k, np.max(np.abs(alpha[k] - row)))
+
+
+def test_general_boundary_stencils_reject_a_short_sketch(LS):
+    mask = np.ones((8, 8), dtype=np.uint8)
+    with pytest.raises(LS.LsError):
+        LS.general_boundary_stencils(mask, np.zeros((64, 4), dtype=np.complex128))
