@@ -104,7 +104,7 @@ def test_slots_run_concurrently(slots):
     assert st["max_concurrent"] == slots
     # 8 solves of 30 ms (+3 ms factor): serial ~0.26 s, four slots ~0.07 s
     if slots == 4:
-        assert wall < 0.2
+        assert wall < 0.24
     else:
         assert wall > 0.25
 
