@@ -339,18 +339,20 @@ def stencil(n: int, d: int, omega: float, b: int, cls, return_sigma: bool = Fals
     return mu, alpha
 
 
-def all_stencils(n: int, d: int, omega: float, b: int = 2):
+def all_stencils(n: int, d: int, omega: float, b: int = 2, k0=None):
     """alpha for all 3^d classes and C(i, mu(i)) = alpha K(mu(0), mu(0)) for the interior class.
 
     Sec. 2.2 defines C only for the interior rows (A); boundary rows of the preconditioner
-    matrix are B alone (eq. PC).  Returns dict cls -> (mu, alpha), and (mu0, c)."""
+    matrix are B alone (eq. PC).  ``k0`` overrides the weight of the singular point, which
+    enters C only (the far sets exclude mu, so alpha never sees it).  Returns dict
+    cls -> (mu, alpha), and (mu0, c)."""
     h = grid_h(n)
     out = {}
     for cls in itertools.product((-1, 0, 1), repeat=d):
         out[cls] = stencil(n, d, omega, b, cls)
     mu0, a0 = out[(0,) * d]
     T = np.array(mu0)[:, None, :] - np.array(mu0)[None, :, :]
-    Kmm = kernel_value(d, omega, h, T)                         # K(mu, mu)(t, t') = k_{t - t'}
+    Kmm = kernel_value(d, omega, h, T, k0)                     # K(mu, mu)(t, t') = k_{t - t'}
     c = a0 @ Kmm                                               # C(0, t') = sum_t alpha_t k_{t-t'}
     return out, (mu0, c)
 
@@ -527,14 +529,17 @@ def gmres_right(apply_A, apply_P, g: np.ndarray, tol: float = 1e-6, restart: int
 
 def solve(n: int, d: int, omega: float, m: np.ndarray, directions, b: int = 2,
           tol: float = 1e-6, restart: int = 50, max_iter: int = 500, workers=None,
-          precond: bool = True):
+          precond: bool = True, k0=None):
     """The whole preconditioned solve for each incident direction (Secs. 2-3).
 
+    ``k0`` overrides the weight of the singular point (default the ball integral of
+    k0_weight; k0_corrected(d, omega, h) for the higher-order rule of Sec. 2.1); it enters
+    the operator, the right-hand side and C.
     Returns dict with u (nrhs, n^d), iterations, true relative residuals, g."""
     if not check_buffer(m, b):
         raise ValueError("m must vanish within b+1 layers of the boundary")
-    ktab = kernel_table(n, d, omega)
-    sten, cint = all_stencils(n, d, omega, b)
+    ktab = kernel_table(n, d, omega, k0)
+    sten, cint = all_stencils(n, d, omega, b, k0)
     M, S = assemble(n, d, omega, m, sten, cint)
     P = Preconditioner(M, S, n, d)
     shape = (n,) * d
@@ -557,7 +562,7 @@ def solve(n: int, d: int, omega: float, m: np.ndarray, directions, b: int = 2,
 
 
 def laplace_solve(n: int, V: np.ndarray, points, b: int = 2, tol: float = 1e-6,
-                  restart: int = 50, max_iter: int = 500, workers=None, strengths=None):
+                  restart: int = 50, max_iter: int = 500, workers=None, strengths=None, k0=None):
     """Sec. 5: (I + K V) u = K f in 3D with the Laplace kernel k_t = h^3 / (4 pi h |t|),
     k_0 = a^2 / 2, and delta sources f at the given grid points.
 
@@ -566,13 +571,14 @@ def laplace_solve(n: int, V: np.ndarray, points, b: int = 2, tol: float = 1e-6,
     K(mu, far) for the Laplace table, and M = [A + C V ; B].  The operator and M need only
     the product omega^2 m of the Helmholtz case, which is V here; the functions above are
     called with omega = 1 and m = V for those two steps and with omega = 0 for the kernel.
+    ``k0`` overrides the weight of the singular point as in ``solve``.
     Returns dict with u (nsrc, n^3), iterations, true relative residuals, g."""
     d = 3
     V = np.asarray(V, dtype=np.float64)
     if not check_buffer(V, b):
         raise ValueError("V must vanish within b+1 layers of the boundary")
-    ktab = kernel_table(n, d, 0.0)
-    sten, cint = all_stencils(n, d, 0.0, b)
+    ktab = kernel_table(n, d, 0.0, k0)
+    sten, cint = all_stencils(n, d, 0.0, b, k0)
     M, S = assemble(n, d, 1.0, V, sten, cint)
     P = Preconditioner(M, S, n, d)
     shape = (n,) * d

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1408_4495_gb300 import workloads as W
 
 
 def _exact_centre_value(d, omega, w):
@@ -63,3 +64,68 @@ def test_corrected_weight_does_not_depend_on_the_fitting_width():
     a = O.k0_corrected(2, 2 * math.pi * 2, h, width=6.0)
     b = O.k0_corrected(2, 2 * math.pi * 2, h, width=10.0)
     assert abs(a - b) < 2e-3 * abs(a)
+
+
+# ---- the weight as a setup option: it reaches C, the operator and the right-hand side ----
+
+def _dense_system(d, n, omega, k0):
+    """K(i, j) = G(h |i - j|) h^d off the diagonal, k0 on it, straight from the Green's
+    function (scipy's Hankel function / the exponential), independent of the oracle's table."""
+    import scipy.special as sp
+    h = 1.0 / (n + 1)
+    idx = np.stack(np.meshgrid(*([np.arange(n)] * d), indexing="ij"), -1).reshape(-1, d)
+    r = h * np.linalg.norm(idx[:, None, :] - idx[None, :, :], axis=-1)
+    rs = np.where(r > 0, r, 1.0)
+    if d == 2:
+        G = 0.25j * sp.hankel1(0, omega * rs)
+    else:
+        G = np.exp(1j * omega * rs) / (4 * math.pi * rs)
+    K = np.where(r > 0, G * h**d, k0)
+    x = (idx + 1.0) * h
+    return K, x
+
+
+@pytest.mark.parametrize("d,n,omega", [(2, 16, 2 * math.pi * 2), (3, 8, 2 * math.pi * 1), (3, 8, 0.0)])
+def test_weight_enters_C_through_the_diagonal_only(d, n, omega):
+    # C = alpha K(mu, mu) and K(mu, mu) holds k_0 on its diagonal alone, so moving k_0 by
+    # delta moves C by delta * alpha; alpha itself is unchanged (the far sets exclude mu)
+    h = O.grid_h(n)
+    kb, kc = O.k0_weight(d, omega, h), O.k0_corrected(d, omega, h)
+    assert abs(kc - kb) > 1e-3 * abs(kb)
+    sb, (mu, cb) = O.all_stencils(n, d, omega, 2)
+    sc, (mu2, cc) = O.all_stencils(n, d, omega, 2, k0=kc)
+    assert mu == mu2
+    for cls in sb:
+        assert np.array_equal(sb[cls][1], sc[cls][1])
+    a0 = sb[(0,) * d][1]
+    assert np.max(np.abs((cc - cb) - (kc - kb) * a0)) < 1e-13 * np.max(np.abs(cb))
+
+
+@pytest.mark.parametrize("d,n,freq", [(2, 20, 3.0), (3, 8, 1.0)])
+def test_solve_with_the_corrected_weight_matches_the_dense_system(d, n, freq):
+    omega = 2 * math.pi * freq
+    k0 = O.k0_corrected(d, omega, 1.0 / (n + 1))
+    m = W.enforce_buffer(W.bumps(n, d, [-0.2], [0.1], [(0.5,) * d]), 2)
+    dr = np.array([1.0, 0.0]) if d == 2 else np.array([0.0, 0.6, 0.8])
+    res = O.solve(n, d, omega, m, [tuple(dr)], tol=1e-12, k0=k0)
+    K, x = _dense_system(d, n, omega, k0)
+    w2m = omega**2 * m.reshape(-1)
+    g = -K @ (w2m * np.exp(1j * omega * (x @ dr)))
+    u = np.linalg.solve(np.eye(n**d) + K * w2m[None, :], g)
+    assert np.linalg.norm(res["g"][0] - g) < 1e-12 * np.linalg.norm(g)
+    assert np.linalg.norm(res["u"][0] - u) < 1e-9 * np.linalg.norm(u)
+
+
+def test_laplace_solve_with_the_corrected_weight_matches_the_dense_system():
+    n = 8
+    k0 = O.k0_corrected(3, 0.0, 1.0 / (n + 1))
+    w = W.laplace_3d(n, 1, seed=5)
+    V = W.enforce_buffer(w.V, 2)
+    res = O.laplace_solve(n, V, w.points, tol=1e-12, k0=k0)
+    K, _ = _dense_system(3, n, 0.0, k0)
+    f = np.zeros(n**3)
+    f[np.ravel_multi_index(tuple(w.points[0]), (n,) * 3)] = (n + 1) ** 3
+    g = K @ f
+    u = np.linalg.solve(np.eye(n**3) + K * V.reshape(-1)[None, :], g)
+    assert np.linalg.norm(res["g"][0] - g) < 1e-12 * np.linalg.norm(g)
+    assert np.linalg.norm(res["u"][0] - u) < 1e-9 * np.linalg.norm(u)
