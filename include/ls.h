@@ -65,6 +65,10 @@ typedef struct {
   int restart;   /* GMRES restart length; 0 selects 50 */
   int max_iter;  /* cap on GMRES iterations per right-hand side; 0 selects 500 */
   ls_prec prec;  /* arithmetic of the path, see ls_prec */
+  int k0_rule;   /* weight k_0 of the singular point of the Nystrom table (Sec. 2.1), an
+                    ls_k0_rule below: 0 = LS_K0_BALL (the default of a zero-initialised
+                    struct), 1 = LS_K0_CORRECTED (fourth order up to a log); it enters the
+                    operator, the symbol, C = alpha K(mu, mu) and the point sources */
 } ls_grid;
 
 typedef struct ls_ctx ls_ctx; /* opaque */
@@ -81,8 +85,8 @@ typedef struct {
  * Builds the Nystrom table k_t, the Fourier symbol of its (2n)^d circulant embedding, the
  * 3^d stencils alpha (eqs. Fmin, Emin, Cmin; the centre coefficient made real positive) and
  * C = alpha K(mu, mu), and the nested-dissection structure.  Tables that depend only on
- * (d, n, omega, b) are cached inside the library and reused by later contexts.
- *   g       grid description (copied).
+ * (d, n, omega, b, k0_rule) are cached inside the library and reused by later contexts.
+ *   g       grid description (copied); an unknown prec or k0_rule gives LS_EINVAL.
  *   omega   angular frequency, > 0.
  *   m       n^d real doubles, C order: the medium m(x_i) (index of refraction 1 - m).  Host or
  *           device pointer; copied.  Must vanish on the b+1 outermost layers (else LS_EBUFFER)
@@ -175,8 +179,8 @@ ls_status ls_far_field(ls_ctx* c, int nrhs, const double* dirs, const double* us
 /*
  * ls_k0_weight -- Sec. 2.1: the weight k_0 of the singular point of the Nystrom table, on the
  * host in FP64 (no context, no device work).
- *   rule LS_K0_BALL:      the integral of G over the disk / ball of area / volume h^d (the
- *                         weight every context uses; second-order accurate).
+ *   rule LS_K0_BALL:      the integral of G over the disk / ball of area / volume h^d
+ *                         (second-order accurate; the default of ls_grid.k0_rule).
  *   rule LS_K0_CORRECTED: the one-point correction of the trapezoidal rule (fourth order up
  *                         to a log, as Sec. 2.1 states): the weight for which the corrected
  *                         rule integrates G f exactly for a Gaussian f of width 8 h.

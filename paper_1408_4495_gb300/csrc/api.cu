@@ -96,7 +96,10 @@ std::string g_setup_err;
 struct StencilKey {
   int d, n, b;
   double omega;
-  bool operator<(const StencilKey& o) const { return std::tie(d, n, b, omega) < std::tie(o.d, o.n, o.b, o.omega); }
+  int k0_rule;  // C = alpha K(mu, mu) holds k_0
+  bool operator<(const StencilKey& o) const {
+    return std::tie(d, n, b, omega, k0_rule) < std::tie(o.d, o.n, o.b, o.omega, o.k0_rule);
+  }
 };
 std::map<StencilKey, std::pair<std::vector<double2>, std::vector<double2>>> g_stencil_cache;
 
@@ -506,6 +509,7 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     const int b = g->buffer_b > 0 ? g->buffer_b : 2;
     if (n <= 2 * (b + 1)) throw Error{ls::EINVAL_, "n too small for the buffer layers"};
     if (g->prec != LS_PREC_FP64 && g->prec != LS_PREC_MIXED) throw Error{ls::EINVAL_, "unknown precision"};
+    if (g->k0_rule != LS_K0_BALL && g->k0_rule != LS_K0_CORRECTED) throw Error{ls::EINVAL_, "unknown k0_rule"};
     c = new ls_ctx;
     c->g = *g;
     c->d = g->dim;
@@ -575,6 +579,14 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     c->sym64 = dalloc<double2>(nq);
     c->sym32 = dalloc<float2>(nq);
     ls::build_kernel_table(c->d, n, c->omega, c->h, c->ktq, c->st);
+    // the higher-order weight of the singular point replaces k_0 = ktq[0] (Sec. 2.1); the
+    // stream is synchronised below, before k0w goes out of scope
+    double k0w[2] = {0.0, 0.0};
+    if (g->k0_rule == LS_K0_CORRECTED) {
+      if (ls_k0_weight(c->d, c->omega, c->h, LS_K0_CORRECTED, k0w) != LS_OK)
+        throw Error{ls::EINVAL_, "k_0 weight undefined for these arguments"};
+      LS_CUDA(cudaMemcpyAsync(c->ktq, k0w, sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    }
     c->plan.d = c->d;
     c->plan.n = n;
     c->plan.omega = c->omega;
@@ -609,7 +621,7 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     }
     // stencils (Sec. 3.1), cached per (d, n, b, omega); omega = 0 is the Laplace kernel
     {
-      StencilKey key{c->d, n, b, c->omega};
+      StencilKey key{c->d, n, b, c->omega, g->k0_rule};
       bool hit = false;
       {
         std::lock_guard<std::mutex> lk(g_mu);

@@ -35,7 +35,8 @@ EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls
 
 class LsGrid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("buffer_b", ctypes.c_int),
-                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
+                ("k0_rule", ctypes.c_int)]
 
 
 class LsInfo(ctypes.Structure):
@@ -180,10 +181,12 @@ class Solver:
     """One medium on one grid: ``ls_setup`` at construction, ``ls_free`` on close.
 
     ``laplace=True`` selects the Laplace variant (``ls_setup_laplace``, Sec. 5): ``m`` is then
-    the potential V and ``omega`` is ignored."""
+    the potential V and ``omega`` is ignored.  ``k0_rule`` picks the weight of the singular
+    point (``LS_K0_BALL`` or ``LS_K0_CORRECTED``, Sec. 2.1)."""
 
     def __init__(self, m, omega: float = 0.0, dim: int | None = None, buffer_b: int = 2, restart: int = 50,
-                 max_iter: int = 500, mixed: bool = True, stream=None, laplace: bool = False):
+                 max_iter: int = 500, mixed: bool = True, stream=None, laplace: bool = False,
+                 k0_rule: int = LS_K0_BALL):
         self.lib = load()
         if isinstance(m, np.ndarray):
             m = np.ascontiguousarray(m, dtype=np.float64)
@@ -193,7 +196,9 @@ class Solver:
         self.omega = 0.0 if laplace else float(omega)
         self.laplace = laplace
         self.mixed = mixed
-        g = LsGrid(self.d, self.n, buffer_b, restart, max_iter, LS_PREC_MIXED if mixed else LS_PREC_FP64)
+        self.k0_rule = k0_rule
+        g = LsGrid(self.d, self.n, buffer_b, restart, max_iter, LS_PREC_MIXED if mixed else LS_PREC_FP64,
+                   k0_rule)
         h = ctypes.c_void_p()
         if laplace:
             st = self.lib.ls_setup_laplace(ctypes.byref(g), _ptr(m), _stream_ptr(stream), ctypes.byref(h))

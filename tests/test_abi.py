@@ -35,11 +35,37 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_structs_match_header_sizes():
-    # ls_grid: 6 ints; ls_info: int, int, double, int (padded to 24);
+    # ls_grid: 7 ints; ls_info: int, int, double, int (padded to 24);
     # ls_nd_stats: 3 ints (+pad) + int64 + 6 doubles
-    assert ctypes.sizeof(LS.LsGrid) == 24
+    assert ctypes.sizeof(LS.LsGrid) == 28
     assert ctypes.sizeof(LS.LsInfo) == 24
     assert ctypes.sizeof(LS.LsNdStats) == 72
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    # sizeof / offsetof of every field as the C compiler lays out include/ls.h
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ls_grid": LS.LsGrid, "ls_info": LS.LsInfo, "ls_nd_stats": LS.LsNdStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ls.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                   text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
 
 
 def test_binding_refuses_without_library(tmp_path):

@@ -26,7 +26,7 @@ def test_k0_weight_matches_the_oracle(LS, d, omega, h):
     assert abs(ball - ref) < 1e-13 * abs(ref)
     corr = LS.k0_weight(d, omega, h, LS.LS_K0_CORRECTED)
     refc = O.k0_corrected(d, omega, h)
-    assert abs(corr - refc) < 1e-9 * abs(refc)
+    assert abs(corr - refc) < 1e-12 * abs(refc)
 
 
 def test_k0_weight_rejects_bad_arguments(LS):
