@@ -9,6 +9,7 @@
 // the integral replaced by the Nystrom quadrature of K.  Both exponentials factor over the
 // axes, so each block tabulates e^{-i omega theta_a x} and e^{i omega (d_a - theta_a) x} per
 // axis in shared memory (FP64) and a grid point costs d - 1 complex products per factor.
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -78,10 +79,10 @@ void far_field(int d, int n, int nrhs, int nobs, const double2* us, const double
   const double2 cd = d == 2 ? make_double2(cos(M_PI / 4) / sqrt(8 * M_PI * omega), sin(M_PI / 4) / sqrt(8 * M_PI * omega))
                             : make_double2(1.0 / (4 * M_PI), 0.0);
   const size_t smem = 2 * (size_t)d * n * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_far_field, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 2 * 2048 * 16));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   LS_LAUNCH("far_field", st,
             k_far_field<<<dim3(nobs, nrhs), 256, smem, st>>>(d, n, nobs, us, dirs, obs, w, omega, h, cd, out));

@@ -16,6 +16,7 @@
 //        P3 rows(axis 1) inv, crop -> n, + u
 //   3D:  P1 axis 2 fwd [scale, pad] -> P2 axis 1 fwd [pad] -> P3 axis 0 fwd * s_hat inv
 //        -> P4 axis 1 inv [crop] -> P5 axis 2 inv [crop, + u]
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -407,10 +408,10 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
 template <typename C, int L, int SIGN> static void launch_row_L(const RowPassArgs& a, cudaStream_t st) {
   constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL;
   const size_t smem = (size_t)NL * Lay<L>::LS * sizeof(C);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_row_pass<C, L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   const long blocks = (a.lines + NL - 1) / NL;
   if (blocks == 0) return;
@@ -421,10 +422,10 @@ template <typename C, int L, int SIGN> static void launch_row_L(const RowPassArg
 template <typename C, int L, int MODE> static void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
   constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
   const size_t smem = (size_t)TC * Lay<L>::LS * sizeof(C);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_col_pass<C, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   const long tiles = (a.inner + TC - 1) / TC;
   const long blocks = tiles * a.outer;

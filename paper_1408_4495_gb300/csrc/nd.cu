@@ -28,6 +28,7 @@
 //   backward (root to leaves): x_own = F11^{-1} w_own - H x_ring
 // two batched multi-right-hand-side matrix-vector products per level, every factor entry
 // read once per sweep.
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -1553,11 +1554,11 @@ template <typename C> constexpr int reg_rpl_max() { return sizeof(C) == 8 ? 16 :
 template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* swp, int* err, cudaStream_t st) {
   const bool f32 = sizeof(C) == 8;
   const size_t smem_max = (size_t)32 * 32 * RPL * sizeof(C) + (size_t)32 * RPL * sizeof(int);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_lower_update<C, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     LS_CUDA(cudaFuncSetAttribute(k_upper_solve<C, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   static_assert(32 * RPL <= panel_reg_rows<C>(), "the register panel holds every own row");
   for (int k0 = 0; k0 < L.smax; k0 += NB) {
@@ -1614,11 +1615,11 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
   constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
   constexpr int REG_MAX_COLS = 1024;
   constexpr size_t GJ_SMEM_MAX = 160 * 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_panel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
     LS_CUDA(cudaFuncSetAttribute(k_gauss_jordan<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM_MAX));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   bool marked = top_levels == nullptr;
   for (int l = depth - 1; l >= 0; --l) {
@@ -2167,11 +2168,11 @@ static void launch_sweep_tr(NdPlan* p, int l, C* T, int ng, const SweepPlan& q, 
   const int depth = (int)p->lev.size();
   const SweepShape sh = sweep_shape<C, RC, TR, MODE>(q.ksz, 0);
   if (sh.smem > SWEEP_SMEM_MAX) LS_FAIL(EINVAL_, "front too large for the solve kernels (%zu bytes of shared memory)", sh.smem);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_sweep<C, RC, TR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SWEEP_SMEM_MAX));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   SweepK<C> S;
   S.F = reinterpret_cast<const C*>(p->F) + D.F_off;

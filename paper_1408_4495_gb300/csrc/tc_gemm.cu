@@ -14,6 +14,7 @@
 // (M = 128, N = 128, K = 8 per instruction) from K-major operands in shared memory
 // (no-swizzle canonical layout: 8-row x 16-byte core matrices).  One thread issues the MMAs
 // and commits them to an mbarrier; all waits are bounded and set *err on expiry.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -274,10 +275,10 @@ bool tc_enabled() {
 void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0, int c1, int k0, int k1, int* err,
               cudaStream_t st) {
   if (r1 <= r0 || c1 <= c0 || k1 <= k0 || nf <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   TcArgs a;
   a.F = F;
