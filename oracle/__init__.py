@@ -38,8 +38,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 * ``k0_corrected`` (higher-order weight of the singular point, Sec. 2.1): the discrete
   convolution of a smooth field converges with order ~4 (against ~2 for the ball weight),
   checked against an independent radial quadrature; independent of the fitting width. pinned
-* general domains (Sec. 4: ``general_support``, ``general_stencils``, ``general_assemble``,
-  ``general_solve``): the restricted solution equals the full-grid solution on Omega, the
+* general domains (Sec. 4: ``general_support``, ``general_sketch``, ``general_stencils``,
+  ``general_assemble``, ``general_solve``): the sketch equals the direct O(N^2) sum of its
+  definition, the restricted solution equals the full-grid solution on Omega, the
   support is supp(m) with its buffer, boundary stencils attain sigma_min of T(mu(i), :)
   (recomputed by the direct sum), interior rows equal the rectangular ones, iteration
   counts in the band of the Sec. 4 tables and stable under the random draw.   pinned

@@ -26,7 +26,8 @@ __all__ = [
     "point_class", "class_mu", "class_far_set", "stencil", "all_stencils",
     "assemble", "nd_order", "Preconditioner", "gmres_right", "solve",
     "check_buffer", "sparsity_ratio", "point_source", "laplace_solve", "far_field",
-    "general_support", "general_apply", "general_rhs", "general_stencils", "general_assemble", "general_solve",
+    "general_support", "general_apply", "general_rhs", "general_sketch", "general_stencils", "general_assemble",
+    "general_solve",
 ]
 
 
@@ -636,6 +637,21 @@ def general_rhs(ktab, omega: float, m: np.ndarray, omega_idx, direction) -> np.n
     return rhs(ktab, omega, m, direction).reshape(-1)[omega_idx]
 
 
+def general_sketch(n: int, d: int, omega: float, m: np.ndarray, R: np.ndarray, b: int = 2) -> np.ndarray:
+    """The sketch T = (K omega^2 m) R of Sec. 4.1 on the unknowns Omega: R is |Omega| x r
+    (rows in the order of general_support, zero outside Omega), one convolution of the
+    definition per column, the rows of Omega kept.  Returns |Omega| x r."""
+    idx = general_support(m, b)
+    ktab = kernel_table(n, d, omega)
+    T = np.empty((len(idx), R.shape[1]), dtype=np.complex128)
+    for q in range(R.shape[1]):
+        full = np.zeros(n**d, dtype=np.complex128)
+        full[idx] = R[:, q]
+        v = (omega**2 * m.reshape(-1) * full).reshape((n,) * d)
+        T[:, q] = apply_K_fft(ktab, v).reshape(-1)[idx]
+    return T
+
+
 def general_stencils(n: int, d: int, omega: float, m: np.ndarray, R: np.ndarray, b: int = 2):
     """Stencils of Sec. 4.1.  Interior points of Omega (all 3^d neighbours in Omega) take the
     rectangular interior stencil alpha and C = alpha K(mu, mu) (Sec. 2.2 / 3.1, eq. Fmin).
@@ -651,14 +667,7 @@ def general_stencils(n: int, d: int, omega: float, m: np.ndarray, R: np.ndarray,
     idx = general_support(m, b)
     pos = -np.ones(n**d, dtype=np.int64)
     pos[idx] = np.arange(len(idx))
-    ktab = kernel_table(n, d, omega)
-    # T = (K omega^2 m) R on Omega: one convolution per column of R
-    T = np.empty((len(idx), R.shape[1]), dtype=np.complex128)
-    for q in range(R.shape[1]):
-        full = np.zeros(n**d, dtype=np.complex128)
-        full[idx] = R[:, q]
-        v = (omega**2 * m.reshape(-1) * full).reshape((n,) * d)
-        T[:, q] = apply_K_fft(ktab, v).reshape(-1)[idx]
+    T = general_sketch(n, d, omega, m, R, b)
     mu_all = [t for t in itertools.product((-1, 0, 1), repeat=d)]
     coords = np.stack(np.unravel_index(idx, (n,) * d), axis=-1)
     interior = np.zeros(len(idx), dtype=bool)

@@ -59,6 +59,22 @@ def test_general_support_is_supp_m_with_its_buffer():
             assert m[tuple(x)] == 0
 
 
+@pytest.mark.parametrize("d,n,freq,rho", [(2, 24, 3.0, 0.35), (3, 10, 1.0, 0.25)])
+def test_general_sketch_equals_the_direct_sum(d, n, freq, rho):
+    # T = (K omega^2 m) R on Omega by the O(N^2) sum of the definition (dense K)
+    omega = 2 * math.pi * freq
+    m = W.cavity(n, d, "l2", rho=rho)
+    R = _R(m, d, 4) + 1j * _R(m, d, 5)
+    idx = O.general_support(m)
+    T = O.general_sketch(n, d, omega, m, R)
+    K = O.dense_K(O.kernel_table(n, d, omega), n, d)
+    full = np.zeros((n**d, R.shape[1]), dtype=np.complex128)
+    full[idx] = R
+    ref = (K @ ((omega**2 * m.reshape(-1))[:, None] * full))[idx]
+    assert T.shape == (len(idx), R.shape[1])
+    assert np.linalg.norm(T - ref) < 1e-12 * np.linalg.norm(ref)
+
+
 def test_general_boundary_stencils_attain_sigma_min():
     n, d, omega = 32, 2, 2 * math.pi * 4
     m = W.cavity(n, d, "l2", rho=0.35)
