@@ -209,6 +209,22 @@ ls_status ls_k0_weight(int dim, double omega, double h, int rule, double* out);
 ls_status ls_general_support(int dim, int n, const double* m, int b, unsigned char* mask);
 ls_status ls_general_boundary_stencils(int dim, int n, const unsigned char* mask, const double* T, int r,
                                        double* alpha, int* boundary);
+/*
+ * ls_general_sketch -- Sec. 4.1: the sketch T = (K omega^2 m) R on the unknowns of a general
+ * domain, computed with the context's FP64 operator apply on the device (the potential V in
+ * place of omega^2 m for a Laplace context).  Column q of R, extended by zero off the
+ * unknowns, is convolved; row k of T is the result at the k-th unknown.
+ *   c     a context of the full grid (ls_setup / ls_setup_laplace; no factorization needed).
+ *   mask  n^d bytes (C order, nonzero = unknown), as written by ls_general_support.
+ *   r     number of columns, >= 1.
+ *   R     (number of unknowns) x r complex doubles (row-major, rows in increasing flat index
+ *         of the unknowns), read.
+ *   T     (number of unknowns) x r complex doubles, same layout, written; the input of
+ *         ls_general_boundary_stencils.
+ * mask, R and T are host arrays (LS_EINVAL for device pointers).  With no unknowns nothing is
+ * written.  Works on the context's stream and returns when T is written.
+ */
+ls_status ls_general_sketch(ls_ctx* c, const unsigned char* mask, int r, const double* R, double* T);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

@@ -890,6 +890,54 @@ ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec p
   }
 }
 
+// Sec. 4.1: the sketch T = (K omega^2 m) R on the unknowns of a general domain.  The columns
+// of R go through the FP64 operator apply in groups of up to 16 (y = x + K omega^2 m x on the
+// device), and T = y - x is read off at the unknowns on the host.
+ls_status ls_general_sketch(ls_ctx* c, const unsigned char* mask, int r, const double* R, double* T) {
+  try {
+    check_ctx(c);
+    if (r < 1 || !mask || !R || !T) throw Error{ls::EINVAL_, "bad arguments"};
+    if (is_device_ptr(mask) || is_device_ptr(R) || is_device_ptr(T))
+      throw Error{ls::EINVAL_, "mask, R and T are host arrays"};
+    const long N = c->N;
+    std::vector<long> idx;
+    for (long i = 0; i < N; ++i)
+      if (mask[i]) idx.push_back(i);
+    const long nu = (long)idx.size();
+    if (nu == 0) return LS_OK;
+    constexpr int GROUP = 16;
+    const int g = std::min(r, GROUP);
+    const size_t tot = (size_t)g * N;
+    std::vector<double2> x(tot), y(tot);
+    double2* xd = buf<double2>(c, "io_in", tot);
+    double2* yd = buf<double2>(c, "io_out", tot);
+    for (int q0 = 0; q0 < r; q0 += GROUP) {
+      const int w = std::min(GROUP, r - q0);
+      std::fill(x.begin(), x.end(), make_double2(0.0, 0.0));
+      for (long k = 0; k < nu; ++k)
+        for (int q = 0; q < w; ++q) {
+          const size_t s = 2 * ((size_t)k * r + q0 + q);
+          x[(size_t)q * N + idx[k]] = make_double2(R[s], R[s + 1]);
+        }
+      LS_CUDA(cudaMemcpyAsync(xd, x.data(), (size_t)w * N * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+      op_apply<double2>(c, w, xd, yd);
+      LS_CUDA(cudaMemcpyAsync(y.data(), yd, (size_t)w * N * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+      LS_CUDA(cudaStreamSynchronize(c->st));
+      for (long k = 0; k < nu; ++k)
+        for (int q = 0; q < w; ++q) {
+          const size_t e = (size_t)q * N + idx[k], t = 2 * ((size_t)k * r + q0 + q);
+          T[t] = y[e].x - x[e].x;
+          T[t + 1] = y[e].y - x[e].y;
+        }
+    }
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::bad_alloc&) {
+    return fail(c, Error{ls::ENOMEM_, "host allocation failed"});
+  }
+}
+
 ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec) {
   try {
     check_ctx(c);

@@ -28,6 +28,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
            "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
+           "ls_general_sketch",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_k0_weight.argtypes = [ip, dp, dp, ip, vp]
     lib.ls_general_support.argtypes = [ip, ip, vp, ip, vp]
     lib.ls_general_boundary_stencils.argtypes = [ip, ip, vp, vp, ip, vp, vp]
+    lib.ls_general_sketch.argtypes = [vp, vp, ip, vp, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -292,6 +294,17 @@ class Solver:
         return out, [SolveInfo(i.iters, i.refinements, i.rel_resid, bool(i.converged)) for i in infos]
 
     # ---- inspection entry points
+    def general_sketch(self, mask: np.ndarray, R: np.ndarray) -> np.ndarray:
+        """ls_general_sketch: T = (K omega^2 m) R on the unknowns of ``mask`` (Sec. 4.1); R is
+        (unknowns x r), rows in increasing flat index of the unknowns."""
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        R = np.ascontiguousarray(R, dtype=np.complex128)
+        if R.ndim != 2 or R.shape[0] != int(np.count_nonzero(mk)):
+            raise ValueError("R must be (number of unknowns) x r")
+        T = np.empty_like(R)
+        self._check(self.lib.ls_general_sketch(self.h, _ptr(mk), int(R.shape[1]), _ptr(R), _ptr(T)))
+        return T
+
     def kernel_table(self):
         out = np.empty((self.n + 1,) * self.d, dtype=np.complex128)
         self._check(self.lib.ls_kernel_table(self.h, _ptr(out)))
