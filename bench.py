@@ -190,7 +190,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(w, {"precision": "FP64 (CPU oracle)"}),
+            "data": "synthetic", "config": config(w, {"precision": "FP64 (CPU oracle)",
+                                                                 "l2": "not applicable (host run, no device)"}),
             "iters": {"min": min(its), "max": max(its)},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
