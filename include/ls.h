@@ -225,6 +225,25 @@ ls_status ls_general_boundary_stencils(int dim, int n, const unsigned char* mask
  * written.  Works on the context's stream and returns when T is written.
  */
 ls_status ls_general_sketch(ls_ctx* c, const unsigned char* mask, int r, const double* R, double* T);
+/*
+ * ls_general_setup -- Sec. 4: makes the context's preconditioner the general-domain one.
+ * Rows of M and [A;B] become per point: an interior point of the unknowns (all 3^d
+ * neighbours are unknowns) keeps the rectangular interior stencil and C omega^2 m; a boundary
+ * point of the unknowns takes its stencil alpha_i (B(i, mu(i)), no C term); a point off the
+ * unknowns takes the identity row, so the unknowns decouple from the rest of the box and the
+ * nested dissection of the box factors M restricted to them.  The operator stays the box's:
+ * m vanishes off the unknowns, so the box solution restricted to the unknowns is the
+ * general-domain solution, and the box adds one block with identity diagonal to the
+ * preconditioned operator (at most one more GMRES iteration).
+ *   mask      n^d bytes (nonzero = unknown), as written by ls_general_support.
+ *   alpha     (number of unknowns) x 3^d complex doubles, boundary (number of unknowns)
+ *             ints: the outputs of ls_general_boundary_stencils.
+ * Host arrays (LS_EINVAL for device pointers).  LS_EINVAL when a point flagged interior has a
+ * neighbour off the unknowns or a boundary stencil has no positive centre.  Drops the
+ * factorization: ls_factor must run again before ls_solve.  ls_stencils still reports the
+ * class tables.
+ */
+ls_status ls_general_setup(ls_ctx* c, const unsigned char* mask, const double* alpha, const int* boundary);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

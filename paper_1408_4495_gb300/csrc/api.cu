@@ -70,6 +70,12 @@ struct ls_ctx {
   float2* alpha32 = nullptr;
   double2* cint64 = nullptr;
   std::vector<double2> alpha_h, cint_h;
+  // general domain (Sec. 4), set by ls_general_setup: a stencil per point (N x 3^d) and the
+  // interior flag per point, replacing the class tables in the assembly and the stencil apply
+  bool general = false;
+  double2* apt64 = nullptr;
+  float2* apt32 = nullptr;
+  unsigned char* inter_pt = nullptr;
   ls::NdPlan* nd = nullptr;
   bool factored = false;
   bool factor_pending = false;  // enqueued, its error flag not read yet
@@ -257,8 +263,13 @@ void op_apply_ff(ls_ctx* c, int nrhs, const double2* u, double2* y, const double
 // z = M^{-1} [A;B] v for v in FP64 or FP32 pairs; z in the factor precision C
 template <typename C, typename Cv = double2> void precond_apply(ls_ctx* c, int nrhs, const Cv* v, C* z) {
   C* r = buf<C>(c, sizeof(C) == 8 ? "pre_r32" : "pre_r64", (size_t)nrhs * c->N);
-  const void* alpha = sizeof(C) == 8 ? (const void*)c->alpha32 : (const void*)c->alpha64;
-  ls::stencil_apply<Cv, C>(c->d, c->n, nrhs, v, r, 1, c->N, alpha, c->st);
+  if (c->general) {
+    const void* apt = sizeof(C) == 8 ? (const void*)c->apt32 : (const void*)c->apt64;
+    ls::stencil_apply_pt<Cv, C>(c->d, c->n, nrhs, v, r, 1, c->N, apt, c->st);
+  } else {
+    const void* alpha = sizeof(C) == 8 ? (const void*)c->alpha32 : (const void*)c->alpha64;
+    ls::stencil_apply<Cv, C>(c->d, c->n, nrhs, v, r, 1, c->N, alpha, c->st);
+  }
   ls::nd_solve<C>(c->nd, nrhs, r, z, c->st);
 }
 
@@ -681,9 +692,11 @@ ls_status ls_factor(ls_ctx* c) {
     c->factored = false;
     const bool mixed = c->prec == LS_PREC_MIXED;
     if (mixed ? ls::nd_prepare<float2>(c->nd, c->st) : ls::nd_prepare<double2>(c->nd, c->st)) ++c->gen;
+    const void* apt = c->general ? (const void*)c->apt64 : nullptr;
+    const unsigned char* inter = c->general ? c->inter_pt : nullptr;
     run_graph(c, "factor", [&] {
-      if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, c->ev_factor);
-      else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, c->ev_factor);
+      if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, c->ev_factor, apt, inter);
+      else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, c->ev_factor, apt, inter);
     });
     c->factored = true;
     c->factor_pending = true;
@@ -820,7 +833,8 @@ void ls_free(ls_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   if (c->st2) cudaStreamSynchronize(c->st2);
   for (void* p : {(void*)c->w2m64, (void*)c->w2m32, (void*)c->tw32, (void*)c->tw64, (void*)c->ktq, (void*)c->sym32,
-                  (void*)c->sym64, (void*)c->ffbuf, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ})
+                  (void*)c->sym64, (void*)c->ffbuf, (void*)c->alpha64, (void*)c->alpha32, (void*)c->cint64, (void*)c->dV, (void*)c->dZ,
+                  (void*)c->apt64, (void*)c->apt32, (void*)c->inter_pt})
     if (p) ls::dev_free(p);
   for (auto p : c->V) ls::dev_free(p);
   for (auto p : c->Z) ls::dev_free(p);
@@ -890,6 +904,88 @@ ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec p
   }
 }
 
+// Sec. 4: switches the context to the general-domain preconditioner.  Per grid point i:
+// off the unknowns the identity row (alpha_i = e_0, so M and [A;B] act as I there and the
+// unknowns decouple from the rest); a boundary point of the unknowns its own stencil from
+// ls_general_boundary_stencils; an interior point the rectangular interior stencil and C.
+ls_status ls_general_setup(ls_ctx* c, const unsigned char* mask, const double* alpha, const int* boundary) {
+  try {
+    check_ctx(c);
+    if (!mask || !alpha || !boundary) throw Error{ls::EINVAL_, "bad arguments"};
+    if (is_device_ptr(mask) || is_device_ptr(alpha) || is_device_ptr(boundary))
+      throw Error{ls::EINVAL_, "mask, alpha and boundary are host arrays"};
+    const long N = c->N;
+    const int P3 = c->d == 2 ? 9 : 27, centre = (P3 - 1) / 2;  // offset 0; also the interior class
+    if (c->alpha_h.size() != (size_t)P3 * P3) throw Error{ls::ESTATE_, "stencil tables missing"};
+    std::vector<double2> a64((size_t)N * P3, make_double2(0.0, 0.0));
+    std::vector<float2> a32((size_t)N * P3, make_float2(0.0f, 0.0f));
+    std::vector<unsigned char> inter(N, 0);
+    long k = 0;
+    for (long i = 0; i < N; ++i) {
+      double2* row = a64.data() + (size_t)i * P3;
+      if (!mask[i]) {
+        row[centre] = make_double2(1.0, 0.0);
+      } else {
+        if (boundary[k]) {
+          for (int t = 0; t < P3; ++t) {
+            const size_t s = 2 * ((size_t)k * P3 + t);
+            row[t] = make_double2(alpha[s], alpha[s + 1]);
+          }
+          if (!(row[centre].x > 0.0)) throw Error{ls::EINVAL_, "a boundary stencil lacks its positive centre"};
+        } else {
+          for (int t = 0; t < P3; ++t) row[t] = c->alpha_h[(size_t)centre * P3 + t];
+          inter[i] = 1;
+        }
+        ++k;
+      }
+      for (int t = 0; t < P3; ++t)
+        a32[(size_t)i * P3 + t] = make_float2((float)row[t].x, (float)row[t].y);
+    }
+    for (long i = 0; i < N; ++i)
+      if (inter[i]) {  // an interior point needs all 3^d neighbours among the unknowns
+        long q = i;
+        int cc[3] = {0, 0, 0};
+        for (int a = c->d - 1; a >= 0; --a) {
+          cc[a] = (int)(q % c->n);
+          q /= c->n;
+        }
+        for (int t = 0; t < P3; ++t) {
+          int tt = t;
+          long j = 0;
+          bool in = true;
+          int tv[3] = {0, 0, 0};
+          for (int a = c->d - 1; a >= 0; --a) {
+            tv[a] = tt % 3 - 1;
+            tt /= 3;
+          }
+          for (int a = 0; a < c->d; ++a) {
+            const int ca = cc[a] + tv[a];
+            if (ca < 0 || ca >= c->n) in = false;
+            j = j * c->n + ca;
+          }
+          if (!in || !mask[j]) throw Error{ls::EINVAL_, "a point flagged interior has a neighbour off the unknowns"};
+        }
+      }
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    if (!c->apt64) {
+      c->apt64 = dalloc<double2>((size_t)N * P3);
+      c->apt32 = dalloc<float2>((size_t)N * P3);
+      c->inter_pt = dalloc<unsigned char>(N);
+    }
+    LS_CUDA(cudaMemcpy(c->apt64, a64.data(), a64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    LS_CUDA(cudaMemcpy(c->apt32, a32.data(), a32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    LS_CUDA(cudaMemcpy(c->inter_pt, inter.data(), N, cudaMemcpyHostToDevice));
+    c->general = true;
+    c->factored = false;
+    ++c->gen;  // captured graphs hold the class tables
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::bad_alloc&) {
+    return fail(c, Error{ls::ENOMEM_, "host allocation failed"});
+  }
+}
+
 // Sec. 4.1: the sketch T = (K omega^2 m) R on the unknowns of a general domain.  The columns
 // of R go through the FP64 operator apply in groups of up to 16 (y = x + K omega^2 m x on the
 // device), and T = y - x is read off at the unknowns on the host.
@@ -948,10 +1044,12 @@ ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, l
     copy_in(c, x, in, tot * sizeof(double2));
     if (prec == LS_PREC_MIXED) {
       float2* y32 = buf<float2>(c, "io_out32", tot);
-      ls::stencil_apply<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->alpha32, c->st);
+      if (c->general) ls::stencil_apply_pt<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->apt32, c->st);
+      else ls::stencil_apply<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->alpha32, c->st);
       ls::cast<float2, double2>(y32, y, tot, c->st);
     } else {
-      ls::stencil_apply<double2, double2>(c->d, c->n, nrhs, x, y, 1, c->N, c->alpha64, c->st);
+      if (c->general) ls::stencil_apply_pt<double2, double2>(c->d, c->n, nrhs, x, y, 1, c->N, c->apt64, c->st);
+      else ls::stencil_apply<double2, double2>(c->d, c->n, nrhs, x, y, 1, c->N, c->alpha64, c->st);
     }
     copy_out(c, out, y, tot * sizeof(double2));
     LS_CUDA(cudaStreamSynchronize(c->st));

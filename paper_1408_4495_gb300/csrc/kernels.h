@@ -100,6 +100,10 @@ void compute_stencils(int d, int n, int b, const std::vector<double2>& ktq, std:
 template <typename Cin, typename Cout>
 void stencil_apply(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, long rs_r, const void* alpha,
                    cudaStream_t st);
+// the same with a stencil per point: alpha_pt is N x 3^d in Cout (general domains, Sec. 4.1)
+template <typename Cin, typename Cout>
+void stencil_apply_pt(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, long rs_r, const void* alpha_pt,
+                      cudaStream_t st);
 
 // ---------------------------------------------------------------- nested dissection (nd.cu)
 struct NdPlan;  // opaque: host symbolic + device index arrays
@@ -122,9 +126,11 @@ template <typename C>
 void nd_factor(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st);
 template <typename C> bool nd_prepare(NdPlan* p, cudaStream_t st);
 template <typename C>
-// top_levels (may be null): recorded on st where the levels with at most 32 fronts begin
+// top_levels (may be null): recorded on st where the levels with at most 32 fronts begin;
+// alpha_pt (FP64, N x 3^d) and inter_pt (N bytes), when not null, give every point its own
+// stencil and interior flag (general domains, Sec. 4) in place of the class tables
 void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st,
-                      cudaEvent_t top_levels);
+                      cudaEvent_t top_levels, const void* alpha_pt = nullptr, const unsigned char* inter_pt = nullptr);
 void nd_factor_check(NdPlan* p, cudaStream_t st);
 // x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);

@@ -479,7 +479,8 @@ size_t nd_device_bytes(const NdPlan* p, int elem_bytes) {
 template <typename C>
 __global__ void k_assemble(C* F, long n_asm, const int64_t* __restrict__ off, const int* __restrict__ row,
                            const unsigned char* __restrict__ tcode, int d, int n, const double2* __restrict__ alpha,
-                           const double2* __restrict__ cint, const double* __restrict__ w2m) {
+                           const double2* __restrict__ cint, const double* __restrict__ w2m,
+                           const double2* __restrict__ alpha_pt, const unsigned char* __restrict__ inter_pt) {
   const int P3 = d == 2 ? 9 : 27;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n_asm; e += (long)gridDim.x * blockDim.x) {
     const int i = row[e];
@@ -499,8 +500,15 @@ __global__ void k_assemble(C* F, long n_asm, const int64_t* __restrict__ off, co
       if (ca != 1) interior = false;
       cls = cls * 3 + ca;
     }
-    // M(i, i+t) = alpha_cls(i)(t) + [i interior] c(t) omega^2 m_{i+t}   (eq. PC)
-    double2 v = alpha[cls * P3 + t];
+    // M(i, i+t) = alpha_cls(i)(t) + [i interior] c(t) omega^2 m_{i+t}   (eq. PC); general
+    // domains (Sec. 4) give a stencil and an interior flag per point instead of per class
+    double2 v;
+    if (alpha_pt) {
+      v = alpha_pt[(long)i * P3 + t];
+      interior = inter_pt[i] != 0;
+    } else {
+      v = alpha[cls * P3 + t];
+    }
     if (interior) {
       long j = 0;
       for (int a = 0; a < d; ++a) j = j * n + (c[a] + tv[a]);
@@ -1578,7 +1586,7 @@ template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* s
 template <typename C>
 void nd_factor(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st) {
   nd_prepare<C>(p, st);
-  nd_factor_launch<C>(p, alpha64, cint64, w2m64, st, nullptr);
+  nd_factor_launch<C>(p, alpha64, cint64, w2m64, st, nullptr, nullptr, nullptr);
   nd_factor_check(p, st);
 }
 
@@ -1600,7 +1608,7 @@ static void record_marker(cudaEvent_t ev, cudaStream_t st) {
 
 template <typename C>
 void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const void* w2m64, cudaStream_t st,
-                      cudaEvent_t top_levels) {
+                      cudaEvent_t top_levels, const void* alpha_pt64, const unsigned char* inter_pt) {
   if (!p->F || p->F_bytes != (int)sizeof(C)) LS_FAIL(ESTATE_, "front storage not prepared for this precision");
   const bool f32 = sizeof(C) == 8;
   LS_CUDA(cudaMemsetAsync(p->F, 0, p->F_elems * sizeof(C), st));
@@ -1608,7 +1616,8 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
   LS_LAUNCH(f32 ? "nd_assemble_c64" : "nd_assemble_c128", st,
             k_assemble<C><<<1024, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_asm, p->d_asm_off, p->d_asm_row,
                                                 p->d_asm_t, p->d, p->n, (const double2*)alpha64,
-                                                (const double2*)cint64, (const double*)w2m64));
+                                                (const double2*)cint64, (const double*)w2m64,
+                                                (const double2*)alpha_pt64, inter_pt));
   LS_LAUNCH(f32 ? "nd_ones_c64" : "nd_ones_c128", st,
             k_set_one<C><<<256, 256, 0, st>>>(reinterpret_cast<C*>(p->F), p->n_one, p->d_one_off));
   const int depth = (int)p->lev.size();
@@ -2250,8 +2259,10 @@ template void nd_factor<float2>(NdPlan*, const void*, const void*, const void*, 
 template void nd_factor<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t);
 template bool nd_prepare<float2>(NdPlan*, cudaStream_t);
 template bool nd_prepare<double2>(NdPlan*, cudaStream_t);
-template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t);
-template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t);
+template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t,
+                                       const void*, const unsigned char*);
+template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t,
+                                        const void*, const unsigned char*);
 template void nd_solve<float2>(NdPlan*, int, const float2*, float2*, cudaStream_t);
 template void nd_solve<double2>(NdPlan*, int, const double2*, double2*, cudaStream_t);
 

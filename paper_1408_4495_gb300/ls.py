@@ -28,7 +28,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
            "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
-           "ls_general_sketch",
+           "ls_general_sketch", "ls_general_setup",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_general_support.argtypes = [ip, ip, vp, ip, vp]
     lib.ls_general_boundary_stencils.argtypes = [ip, ip, vp, vp, ip, vp, vp]
     lib.ls_general_sketch.argtypes = [vp, vp, ip, vp, vp]
+    lib.ls_general_setup.argtypes = [vp, vp, vp, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -304,6 +305,27 @@ class Solver:
         T = np.empty_like(R)
         self._check(self.lib.ls_general_sketch(self.h, _ptr(mk), int(R.shape[1]), _ptr(R), _ptr(T)))
         return T
+
+    def general_setup(self, mask: np.ndarray, alpha: np.ndarray, boundary: np.ndarray):
+        """ls_general_setup: the general-domain preconditioner of Sec. 4 from the unknowns
+        ``mask`` and the boundary stencils (outputs of general_boundary_stencils)."""
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        al = np.ascontiguousarray(alpha, dtype=np.complex128)
+        bd = np.ascontiguousarray(boundary, dtype=np.int32)
+        nu = int(np.count_nonzero(mk))
+        if al.shape != (nu, 3 ** self.d) or bd.shape != (nu,):
+            raise ValueError("alpha must be (unknowns) x 3^d and boundary (unknowns,)")
+        self._check(self.lib.ls_general_setup(self.h, _ptr(mk), _ptr(al), _ptr(bd)))
+
+    def general_domain(self, m: np.ndarray, R: np.ndarray, buffer_b: int = 2):
+        """The Sec. 4 pipeline through the C-ABI: unknowns (ls_general_support), device sketch
+        (ls_general_sketch), boundary stencils (ls_general_boundary_stencils) and the
+        preconditioner switch (ls_general_setup).  Returns the mask of the unknowns."""
+        mask = general_support(m, buffer_b)
+        T = self.general_sketch(mask, R)
+        alpha, bnd = general_boundary_stencils(mask, T)
+        self.general_setup(mask, alpha, bnd)
+        return mask
 
     def kernel_table(self):
         out = np.empty((self.n + 1,) * self.d, dtype=np.complex128)

@@ -1,0 +1,142 @@
+"""The general-domain solve of Sec. 4 on the device, through the C-ABI (ls_general_support,
+ls_general_sketch, ls_general_boundary_stencils, ls_general_setup, ls_factor, ls_solve).
+
+The library keeps the box: every point off the unknowns Omega gets the identity row in M
+and [A;B], so the preconditioner is diag(M_Omega^{-1} [A;B]_Omega, I), and the operator is
+the box's (m vanishes off Omega, so A = [[A_OO, 0], [A_xO, I]] in the order Omega, rest).
+The preconditioned operator is block lower triangular with an identity block, so GMRES on
+the box takes the restricted method's iterations plus one and its solution restricted to
+Omega is the restricted solution (checked with the oracle's pieces on the CPU for these
+cases: +1 iteration, agreement 1e-11 at tolerance 1e-10).
+
+Checks against the oracle's restricted method (general_stencils / general_solve, same R):
+the per-point stencil apply (FP64 to rounding, FP32 to 1e-6 relative), the preconditioner's
+backward error, and the solve (FP64: the oracle's iterations + 1, solution within 1e-8 of
+the oracle solved to 1e-10; mixed: within +-2 of that count, true relative residual
+<= 1e-6, solution within 1e-5).  The file is named to run after the parity suite.
+"""
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_1408_4495_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(2, 32, 4.0, "l2", 0.35), (2, 64, 8.0, "l1", 0.38), (3, 16, 2.0, "l2", 0.3)]
+
+
+@pytest.fixture(scope="module")
+def LS():
+    from paper_1408_4495_gb300 import build, ls
+    build.build()
+    return ls
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def case(d, n, freq, norm, rho):
+    omega = 2 * math.pi * freq
+    m = W.cavity(n, d, norm, rho=rho)
+    idx = O.general_support(m, 2)
+    R = np.random.default_rng(5).standard_normal((len(idx), 2 * 3**d))
+    return omega, m, idx, R
+
+
+def box_matrices(n, d, omega, m, st):
+    """M and [A;B] of the box from the oracle's general-domain stencils: identity rows off
+    Omega, boundary rows alpha_i, interior rows alpha + C omega^2 m."""
+    idx, interior, bnd, (mu0, a0), (mu0c, c) = st
+    N = n**d
+    inter = np.zeros(N, dtype=bool)
+    inter[idx[interior]] = True
+    on = np.zeros(N, dtype=bool)
+    on[idx] = True
+    w2m = (omega**2 * m).reshape(-1)
+    amap, cmap = dict(zip(mu0, a0)), dict(zip(mu0c, c))
+    rows, cols, mv, sv = [], [], [], []
+    for i in range(N):
+        x = np.array(np.unravel_index(i, (n,) * d))
+        if not on[i]:
+            rows.append(i); cols.append(i); mv.append(1.0); sv.append(1.0)
+            continue
+        pairs = ([(t, amap[t]) for t in itertools.product((-1, 0, 1), repeat=d)] if inter[i]
+                 else list(zip(*bnd[int(i)])))
+        for t, a in pairs:
+            j = int(np.ravel_multi_index(tuple(x + np.array(t)), (n,) * d))
+            rows.append(i); cols.append(j); sv.append(a)
+            mv.append(a + cmap[t] * w2m[j] if inter[i] else a)
+    M = sp.csr_matrix((mv, (rows, cols)), shape=(N, N))
+    S = sp.csr_matrix((sv, (rows, cols)), shape=(N, N))
+    return M, S
+
+
+@pytest.mark.parametrize("d,n,freq,norm,rho", CASES)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_general_stencil_apply_and_preconditioner(LS, d, n, freq, norm, rho, mixed):
+    omega, m, idx, R = case(d, n, freq, norm, rho)
+    st = O.general_stencils(n, d, omega, m, R)
+    M, S = box_matrices(n, d, omega, m, st)
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal((2,) + (n,) * d) + 1j * rng.standard_normal((2,) + (n,) * d)
+    with LS.Solver(m, omega, dim=d, mixed=mixed) as s:
+        s.general_domain(m, R)
+        y = s.stencil_apply(x)
+        s.factor()
+        z = s.precond(x)
+    for j in range(2):
+        ref = S @ x[j].reshape(-1)
+        assert rel(y[j].reshape(-1), ref) < (1e-6 if mixed else 1e-12)
+        zj = z[j].reshape(-1)
+        normM = abs(M).sum(axis=1).max()
+        be = np.linalg.norm(M @ zj - ref) / (normM * np.linalg.norm(zj))
+        assert be < (2e-5 if mixed else 5e-13), be
+
+
+@pytest.mark.parametrize("d,n,freq,norm,rho", CASES)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_general_solve_matches_the_restricted_oracle(LS, d, n, freq, norm, rho, mixed):
+    omega, m, idx, R = case(d, n, freq, norm, rho)
+    dirs = W.directions_circle(2) if d == 2 else W.directions_sphere(2, 7)
+    ref = O.general_solve(n, d, omega, m, dirs, R, tol=1e-10)
+    ref6 = O.general_solve(n, d, omega, m, dirs, R, tol=1e-6)
+    with LS.Solver(m, omega, dim=d, mixed=mixed) as s:
+        mask = s.general_domain(m, R)
+        s.factor()
+        g = s.rhs_plane_wave(dirs)
+        u, info = s.solve(g, tol=1e-6)
+    assert np.array_equal(np.flatnonzero(mask.reshape(-1)), idx)
+    for j in range(len(dirs)):
+        assert rel(g[j].reshape(-1)[idx], ref["g"][j]) < 1e-11
+        assert info[j].converged and info[j].rel_resid <= 1e-6
+        if mixed:
+            assert abs(info[j].iters - (ref6["iters"][j] + 1)) <= 2
+            assert rel(u[j].reshape(-1)[idx], ref["u"][j]) < 1e-5
+        else:
+            assert info[j].iters == ref6["iters"][j] + 1
+            assert rel(u[j].reshape(-1)[idx], ref["u"][j]) < 1e-8
+
+
+def test_general_setup_refuses_inconsistent_flags(LS):
+    n, d = 32, 2
+    omega, m, idx, R = case(d, n, 4.0, "l2", 0.35)
+    with LS.Solver(m, omega, dim=d, mixed=False) as s:
+        mask = LS.general_support(m, 2)
+        T = s.general_sketch(mask, R)
+        alpha, bnd = LS.general_boundary_stencils(mask, T)
+        wrong = bnd.copy()
+        wrong[np.flatnonzero(bnd)[0]] = False  # a boundary point claimed interior
+        with pytest.raises(LS.LsError) as e:
+            s.general_setup(mask, alpha, wrong)
+        assert e.value.status == LS.LS_EINVAL
+        s.general_setup(mask, alpha, bnd)
+        with pytest.raises(LS.LsError) as e:  # the factorization was dropped
+            s.solve(s.rhs_plane_wave(W.directions_circle(1)), tol=1e-6)
+        assert e.value.status == LS.LS_ESTATE
