@@ -244,6 +244,19 @@ ls_status ls_general_sketch(ls_ctx* c, const unsigned char* mask, int r, const d
  * class tables.
  */
 ls_status ls_general_setup(ls_ctx* c, const unsigned char* mask, const double* alpha, const int* boundary);
+/*
+ * ls_general_rows -- the host step of ls_general_setup (no context, no device work): the
+ * stencil of every grid point in the box embedding of Sec. 4.
+ *   mask, alpha, boundary  as for ls_general_setup; alpha_interior: 3^d complex doubles, the
+ *                          rectangular interior stencil (row (3^d - 1) / 2 of ls_stencils).
+ *   rows      n^d x 3^d complex doubles written (offset index as for ls_stencils): e_0 off the
+ *             unknowns, alpha_i at boundary points, alpha_interior at interior points.
+ *   interior  n^d bytes written, 1 at interior points (the rows that carry C omega^2 m).
+ * LS_EINVAL on bad arguments, when a point flagged interior has a neighbour off the unknowns
+ * or off the grid, or when a boundary stencil's centre is not positive.
+ */
+ls_status ls_general_rows(int dim, int n, const unsigned char* mask, const double* alpha, const int* boundary,
+                          const double* alpha_interior, double* rows, unsigned char* interior);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

@@ -917,55 +917,15 @@ ls_status ls_general_setup(ls_ctx* c, const unsigned char* mask, const double* a
     const long N = c->N;
     const int P3 = c->d == 2 ? 9 : 27, centre = (P3 - 1) / 2;  // offset 0; also the interior class
     if (c->alpha_h.size() != (size_t)P3 * P3) throw Error{ls::ESTATE_, "stencil tables missing"};
-    std::vector<double2> a64((size_t)N * P3, make_double2(0.0, 0.0));
-    std::vector<float2> a32((size_t)N * P3, make_float2(0.0f, 0.0f));
+    std::vector<double2> a64((size_t)N * P3);
+    std::vector<float2> a32((size_t)N * P3);
     std::vector<unsigned char> inter(N, 0);
-    long k = 0;
-    for (long i = 0; i < N; ++i) {
-      double2* row = a64.data() + (size_t)i * P3;
-      if (!mask[i]) {
-        row[centre] = make_double2(1.0, 0.0);
-      } else {
-        if (boundary[k]) {
-          for (int t = 0; t < P3; ++t) {
-            const size_t s = 2 * ((size_t)k * P3 + t);
-            row[t] = make_double2(alpha[s], alpha[s + 1]);
-          }
-          if (!(row[centre].x > 0.0)) throw Error{ls::EINVAL_, "a boundary stencil lacks its positive centre"};
-        } else {
-          for (int t = 0; t < P3; ++t) row[t] = c->alpha_h[(size_t)centre * P3 + t];
-          inter[i] = 1;
-        }
-        ++k;
-      }
-      for (int t = 0; t < P3; ++t)
-        a32[(size_t)i * P3 + t] = make_float2((float)row[t].x, (float)row[t].y);
-    }
-    for (long i = 0; i < N; ++i)
-      if (inter[i]) {  // an interior point needs all 3^d neighbours among the unknowns
-        long q = i;
-        int cc[3] = {0, 0, 0};
-        for (int a = c->d - 1; a >= 0; --a) {
-          cc[a] = (int)(q % c->n);
-          q /= c->n;
-        }
-        for (int t = 0; t < P3; ++t) {
-          int tt = t;
-          long j = 0;
-          bool in = true;
-          int tv[3] = {0, 0, 0};
-          for (int a = c->d - 1; a >= 0; --a) {
-            tv[a] = tt % 3 - 1;
-            tt /= 3;
-          }
-          for (int a = 0; a < c->d; ++a) {
-            const int ca = cc[a] + tv[a];
-            if (ca < 0 || ca >= c->n) in = false;
-            j = j * c->n + ca;
-          }
-          if (!in || !mask[j]) throw Error{ls::EINVAL_, "a point flagged interior has a neighbour off the unknowns"};
-        }
-      }
+    if (ls_general_rows(c->d, c->n, mask, alpha, boundary,
+                        reinterpret_cast<const double*>(c->alpha_h.data() + (size_t)centre * P3),
+                        reinterpret_cast<double*>(a64.data()), inter.data()) != LS_OK)
+      throw Error{ls::EINVAL_, "inconsistent general-domain stencils (an interior point with a neighbour off the "
+                               "unknowns, or a boundary stencil without its positive centre)"};
+    for (size_t e = 0; e < a64.size(); ++e) a32[e] = make_float2((float)a64[e].x, (float)a64[e].y);
     LS_CUDA(cudaStreamSynchronize(c->st));
     if (!c->apt64) {
       c->apt64 = dalloc<double2>((size_t)N * P3);

@@ -441,3 +441,55 @@ extern "C" ls_status ls_general_boundary_stencils(int dim, int n, const unsigned
     if (b) return LS_EINVAL;
   return LS_OK;
 }
+
+// Sec. 4: the rows of M and [A;B] per grid point for the general-domain solve in the box
+// (identity off the unknowns, alpha_i on their boundary, the interior stencil inside), with
+// the checks that an interior point has all 3^d neighbours among the unknowns and that a
+// boundary stencil has its positive centre.
+extern "C" ls_status ls_general_rows(int dim, int n, const unsigned char* mask, const double* alpha,
+                                     const int* boundary, const double* alpha_interior, double* rows,
+                                     unsigned char* interior) {
+  if ((dim != 2 && dim != 3) || n < 1 || !mask || !alpha || !boundary || !alpha_interior || !rows || !interior)
+    return LS_EINVAL;
+  const long N = dim == 2 ? (long)n * n : (long)n * n * n;
+  const int P3 = dim == 2 ? 9 : 27, centre = (P3 - 1) / 2;
+  long k = 0;
+  for (long i = 0; i < N; ++i) {
+    double* row = rows + 2 * (size_t)i * P3;
+    std::fill(row, row + 2 * P3, 0.0);
+    interior[i] = 0;
+    if (!mask[i]) {
+      row[2 * centre] = 1.0;
+      continue;
+    }
+    const double* src = boundary[k] ? alpha + 2 * (size_t)k * P3 : alpha_interior;
+    std::copy(src, src + 2 * P3, row);
+    if (boundary[k]) {
+      if (!(row[2 * centre] > 0.0)) return LS_EINVAL;
+    } else {
+      interior[i] = 1;
+      long q = i;
+      int c[3] = {0, 0, 0};
+      for (int a = dim - 1; a >= 0; --a) {
+        c[a] = (int)(q % n);
+        q /= n;
+      }
+      for (int t = 0; t < P3; ++t) {
+        int tt = t, tv[3] = {0, 0, 0};
+        for (int a = dim - 1; a >= 0; --a) {
+          tv[a] = tt % 3 - 1;
+          tt /= 3;
+        }
+        long j = 0;
+        for (int a = 0; a < dim; ++a) {
+          const int ca = c[a] + tv[a];
+          if (ca < 0 || ca >= n) return LS_EINVAL;
+          j = j * n + ca;
+        }
+        if (!mask[j]) return LS_EINVAL;
+      }
+    }
+    ++k;
+  }
+  return LS_OK;
+}

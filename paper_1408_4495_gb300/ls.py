@@ -28,7 +28,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
            "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
-           "ls_general_sketch", "ls_general_setup",
+           "ls_general_sketch", "ls_general_setup", "ls_general_rows",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_general_boundary_stencils.argtypes = [ip, ip, vp, vp, ip, vp, vp]
     lib.ls_general_sketch.argtypes = [vp, vp, ip, vp, vp]
     lib.ls_general_setup.argtypes = [vp, vp, vp, vp]
+    lib.ls_general_rows.argtypes = [ip, ip, vp, vp, vp, vp, vp, vp]
     lib.ls_solve.argtypes = [vp, ip, vp, dp, vp, ctypes.POINTER(LsInfo)]
     lib.ls_last_error.argtypes = [vp]
     lib.ls_last_error.restype = ctypes.c_char_p
@@ -170,6 +171,25 @@ def general_boundary_stencils(mask: np.ndarray, T: np.ndarray):
     if st != LS_OK:
         raise LsError(st, "ls_general_boundary_stencils: bad arguments or an undetermined stencil")
     return alpha, bnd.astype(bool)
+
+
+def general_rows(mask: np.ndarray, alpha: np.ndarray, boundary: np.ndarray, alpha_interior: np.ndarray):
+    """ls_general_rows: (rows (n^d x 3^d), interior flags (n^d,)) of the box embedding of the
+    general-domain preconditioner (Sec. 4), on the host."""
+    mk = np.ascontiguousarray(mask, dtype=np.uint8)
+    d = mk.ndim
+    al = np.ascontiguousarray(alpha, dtype=np.complex128)
+    bd = np.ascontiguousarray(boundary, dtype=np.int32)
+    ai = np.ascontiguousarray(alpha_interior, dtype=np.complex128)
+    nu = int(np.count_nonzero(mk))
+    if al.shape != (nu, 3**d) or bd.shape != (nu,) or ai.shape != (3**d,):
+        raise ValueError("alpha (unknowns x 3^d), boundary (unknowns,), alpha_interior (3^d,)")
+    rows = np.empty((mk.size, 3**d), dtype=np.complex128)
+    inter = np.empty(mk.size, dtype=np.uint8)
+    st = load().ls_general_rows(d, mk.shape[0], _ptr(mk), _ptr(al), _ptr(bd), _ptr(ai), _ptr(rows), _ptr(inter))
+    if st != LS_OK:
+        raise LsError(st, "ls_general_rows: bad arguments or inconsistent stencils")
+    return rows, inter.astype(bool)
 
 
 @dataclass

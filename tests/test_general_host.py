@@ -63,3 +63,60 @@ def test_general_boundary_stencils_reject_a_short_sketch(LS):
     mask = np.ones((8, 8), dtype=np.uint8)
     with pytest.raises(LS.LsError):
         LS.general_boundary_stencils(mask, np.zeros((64, 4), dtype=np.complex128))
+
+
+def _oracle_T(n, d, omega, m, R):
+    return O.general_sketch(n, d, omega, m, R)
+
+
+@pytest.mark.parametrize("d,n,freq,norm,rho", CASES)
+def test_general_rows_embed_the_oracle_stencils_in_the_box(LS, d, n, freq, norm, rho):
+    # the host step of ls_general_setup: identity rows off Omega, the oracle's boundary
+    # stencils on the boundary of Omega, the rectangular interior stencil inside
+    omega = 2 * math.pi * freq
+    m = W.cavity(n, d, norm, rho=rho)
+    idx = O.general_support(m, 2)
+    R = np.random.default_rng(5).standard_normal((len(idx), 2 * 3**d))
+    mask = LS.general_support(m, 2)
+    alpha, bnd = LS.general_boundary_stencils(mask, _oracle_T(n, d, omega, m, R))
+    _, interior, ref, (mu0, a0), _ = O.general_stencils(n, d, omega, m, R)
+    code = lambda t: sum((t[x] + 1) * 3 ** (d - 1 - x) for x in range(d))
+    a_int = np.zeros(3**d, dtype=np.complex128)
+    for t, v in zip(mu0, a0):
+        a_int[code(t)] = v
+    rows, inter = LS.general_rows(mask, alpha, bnd, a_int)
+    on = np.zeros(n**d, dtype=bool)
+    on[idx] = True
+    e0 = np.zeros(3**d)
+    e0[(3**d - 1) // 2] = 1
+    assert np.all(rows[~on] == e0)
+    assert not np.any(inter[~on])
+    assert np.array_equal(np.flatnonzero(inter), idx[interior])
+    assert np.all(rows[idx[interior]] == a_int)
+    for i in idx[~interior]:
+        offs, a = ref[int(i)]
+        want = np.zeros(3**d, dtype=np.complex128)
+        for t, v in zip(offs, a):
+            want[code(t)] = v
+        assert np.max(np.abs(rows[i] - want)) < 1e-9
+
+
+def test_general_rows_refuse_inconsistent_flags(LS):
+    n, d, omega = 32, 2, 2 * math.pi * 4
+    m = W.cavity(n, d, "l2", rho=0.35)
+    idx = O.general_support(m, 2)
+    R = np.random.default_rng(5).standard_normal((len(idx), 18))
+    mask = LS.general_support(m, 2)
+    alpha, bnd = LS.general_boundary_stencils(mask, _oracle_T(n, d, omega, m, R))
+    a_int = np.zeros(9, dtype=np.complex128)
+    a_int[4] = 1
+    wrong = bnd.copy()
+    wrong[np.flatnonzero(bnd)[0]] = False  # a boundary point claimed interior
+    with pytest.raises(LS.LsError) as e:
+        LS.general_rows(mask, alpha, wrong, a_int)
+    assert e.value.status == LS.LS_EINVAL
+    neg = alpha.copy()
+    k = np.flatnonzero(bnd)[0]
+    neg[k] = -neg[k]  # centre no longer positive
+    with pytest.raises(LS.LsError):
+        LS.general_rows(mask, neg, bnd, a_int)
