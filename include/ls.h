@@ -20,6 +20,9 @@
  *  - Any array argument may be a host pointer or a device pointer of the current device;
  *    the library tells them apart with cudaPointerGetAttributes.  Host arrays are copied
  *    inside the call; device arrays are read / written in place on the context's stream.
+ *    Exceptions: the host computations ls_k0_weight, ls_general_support,
+ *    ls_general_boundary_stencils and ls_general_rows, and the arrays of ls_general_sketch
+ *    and ls_general_setup, take host arrays only.
  *  - The caller owns every array it passes; the library keeps no pointer to them after the
  *    call returns.  The context owns all device memory it allocates.
  *  - A context is not thread-safe; distinct contexts may be used from distinct threads.
@@ -42,7 +45,8 @@ typedef enum {
   LS_ECUDA = 3,     /* a CUDA call failed; message has the CUDA error string */
   LS_ENOCONV = 4,   /* GMRES did not reach the tolerance within max_iter; outputs are filled */
   LS_ESTATE = 5,    /* call out of order (e.g. ls_solve before ls_factor) */
-  LS_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up */
+  LS_ETIMEOUT = 6,  /* a bounded device wait gave up (the tensor-core front update of
+                       ls_factor); the context stays usable */
   LS_EBUFFER = 7    /* m is not zero within b+1 layers of the boundary (Sec. 2.1, Sec. 3.1) */
 } ls_status;
 
