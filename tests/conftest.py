@@ -10,3 +10,14 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libls")
+    config.addinivalue_line("markers", "late(rank): runs after every unmarked test, in increasing rank, so "
+                                       "that a run stopping at its first failure has run the others first")
+
+
+def pytest_collection_modifyitems(session, config, items):
+    def key(item):
+        mk = item.get_closest_marker("late")
+        if mk is None:
+            return (0, 0)
+        return (1, mk.args[0] if mk.args else 0)
+    items.sort(key=key)  # stable: file and definition order within a group

@@ -13,7 +13,7 @@ Checks against the oracle's restricted method (general_stencils / general_solve,
 the per-point stencil apply (FP64 to rounding, FP32 to 1e-6 relative), the preconditioner's
 backward error, and the solve (FP64: the oracle's iterations + 1, solution within 1e-8 of
 the oracle solved to 1e-10; mixed: within +-2 of that count, true relative residual
-<= 1e-6, solution within 1e-5).  The file is named to run after the parity suite.
+<= 1e-6, solution within 1e-5).  It runs after the established GPU tests (marker late).
 """
 
 import itertools
@@ -26,7 +26,7 @@ import scipy.sparse as sp
 import oracle as O
 from paper_1408_4495_gb300 import workloads as W
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late(3)]
 
 CASES = [(2, 32, 4.0, "l2", 0.35), (2, 64, 8.0, "l1", 0.38), (3, 16, 2.0, "l2", 0.3)]
 

@@ -16,7 +16,7 @@ import pytest
 import oracle as O
 from paper_1408_4495_gb300 import workloads as W
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late(1)]
 
 
 def rel(a, b):

@@ -11,7 +11,7 @@ import pytest
 from paper_1408_4495_gb300 import serving as S
 from paper_1408_4495_gb300 import workloads as W
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late(4)]
 
 
 @pytest.fixture(scope="module")
