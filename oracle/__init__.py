@@ -33,8 +33,10 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   Green's function at the grid offsets; V = 0 gives u = g; dense solve of (I + K V) u = g;
   stencil optimality for the Laplace kernel.                                  pinned
 * ``far_field`` (exterior evaluation): equals the direct exterior sum of the Green's
-  function at a distant point (constant and sign), zero for m = 0, and reciprocity
-  u_inf(theta; d) = u_inf(-d; -theta) of the discrete solution.               pinned
+  function at a distant point (constant and sign), zero for m = 0, reciprocity
+  u_inf(theta; d) = u_inf(-d; -theta) of the discrete solution, and convergence to the
+  Mie series' far field of a constant-contrast disk (``mie.mie_disk_far_field``, itself
+  checked as the limit of the Mie field).                                      pinned
 * ``k0_corrected`` (higher-order weight of the singular point, Sec. 2.1): the discrete
   convolution of a smooth field converges with order ~4 (against ~2 for the ball weight),
   checked against an independent radial quadrature; independent of the fitting width. pinned

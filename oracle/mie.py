@@ -47,3 +47,29 @@ def mie_disk_scattered(X1, X2, omega: float, m0: float, R: float, centre=(0.5, 0
         inn_field = an * sp.jv(n, k1 * r[inside]) - inn * sp.jv(n, k0 * r[inside])
         u[inside] += pref * inn_field * e[inside]
     return u
+
+
+def mie_disk_far_field(theta, omega: float, m0: float, R: float, centre=(0.5, 0.5), nmax=None):
+    """Far-field pattern of the scattered field of the same disk, in the convention
+    u_s(x) ~ e^{i omega |x|} |x|^{-1/2} u_inf(theta) as |x| -> infinity in direction theta.
+
+    Outside the disk u_s = pref sum_n c_n H_n(k0 r) e^{i n phi} with (r, phi) about the centre
+    c; with r = |x| - theta . c + o(1) and H_n(z) ~ sqrt(2 / (pi z)) e^{i (z - n pi/2 - pi/4)},
+        u_inf(theta) = pref sqrt(2 / (pi omega)) e^{-i pi/4} e^{-i omega theta . c}
+                       sum_n c_n (-i)^n e^{i n theta}."""
+    theta = np.asarray(theta, dtype=np.float64)
+    k0 = omega
+    k1 = omega * np.sqrt(1.0 - m0)
+    if nmax is None:
+        nmax = int(k1 * R + 4.0 * (k1 * R) ** (1.0 / 3.0) + 20)
+    pref = np.exp(1j * omega * centre[0])
+    s = np.zeros(theta.shape, dtype=np.complex128)
+    for n in range(-nmax, nmax + 1):
+        jn0, jn1 = sp.jv(n, k0 * R), sp.jv(n, k1 * R)
+        djn0, djn1 = sp.jvp(n, k0 * R), sp.jvp(n, k1 * R)
+        hn0, dhn0 = sp.hankel1(n, k0 * R), sp.h1vp(n, k0 * R)
+        inn = 1j ** (n % 4)
+        cn = inn * (k1 * djn1 * jn0 - k0 * djn0 * jn1) / (k0 * dhn0 * jn1 - k1 * djn1 * hn0)
+        s += cn * (-1j) ** (n % 4) * np.exp(1j * n * theta)
+    phase = np.exp(-1j * omega * (np.cos(theta) * centre[0] + np.sin(theta) * centre[1]))
+    return pref * np.sqrt(2.0 / (np.pi * omega)) * np.exp(-1j * np.pi / 4) * phase * s
