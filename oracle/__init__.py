@@ -31,7 +31,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   harmonicity and unit flux of 1/(4 pi r); k_0 = a^2/2 by ball quadrature and as the
   omega -> 0 limit of the Helmholtz weight; the point-source right-hand side equals the
   Green's function at the grid offsets; V = 0 gives u = g; dense solve of (I + K V) u = g;
-  stencil optimality for the Laplace kernel.                                  pinned
+  stencil optimality for the Laplace kernel; convergence to the radial solution of a
+  delta source at the centre of a constant ball potential.                    pinned
 * ``far_field`` (exterior evaluation): equals the direct exterior sum of the Green's
   function at a distant point (constant and sign), zero for m = 0, reciprocity
   u_inf(theta; d) = u_inf(-d; -theta) of the discrete solution, and convergence to the

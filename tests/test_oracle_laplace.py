@@ -142,3 +142,31 @@ def test_laplace_first_row_of_the_papers_tables():
         r = O.laplace_solve(n, V, w.points, tol=1e-6)
         assert abs(r["iters"][0] - tab[fig]["n_p"][0]) <= 3, (fig, r["iters"])
         assert r["resid"][0] <= 1e-6
+
+
+def test_laplace_solve_converges_to_the_radial_solution_of_a_ball_potential():
+    """(-Delta + V) u = delta at the centre of a ball with V = V0 inside, 0 outside (Sec. 5
+    form).  With kappa = sqrt(V0) the radial solution is (a e^{-kappa r} + b e^{kappa r}) / r
+    inside and c / r outside: the source fixes a + b = 1 / (4 pi), continuity of u and u' at
+    R gives b = a e^{-2 kappa R} and c = a e^{-kappa R} + b e^{kappa R}.  The discrete solution
+    (V jumps, so no fixed order) approaches it away from the source: measured 4.0e-2, 1.1e-2,
+    8.0e-3 at n = 15, 31, 47."""
+    V0, R = 64.0, 0.25
+    kap = math.sqrt(V0)
+    a = 1 / (4 * math.pi * (1 + math.exp(-2 * kap * R)))
+    b = a * math.exp(-2 * kap * R)
+    c = a * math.exp(-kap * R) + b * math.exp(kap * R)
+    errs = []
+    for n in (15, 31):
+        p = (n + 1) // 2 - 1  # the grid point at x = 1/2
+        X = O.grid_coords(n, 3)
+        r = np.sqrt((X[0] - 0.5) ** 2 + (X[1] - 0.5) ** 2 + (X[2] - 0.5) ** 2)
+        V = np.where(r < R, V0, 0.0)
+        res = O.laplace_solve(n, V, [(p, p, p)], tol=1e-10)
+        u = res["u"][0].reshape((n,) * 3)
+        sel = r > 0.1
+        rs = r[sel]
+        ex = np.where(rs < R, (a * np.exp(-kap * rs) + b * np.exp(kap * rs)) / rs, c / rs)
+        errs.append(np.linalg.norm(u[sel] - ex) / np.linalg.norm(ex))
+    assert errs[0] < 0.06
+    assert errs[1] < 0.4 * errs[0]
