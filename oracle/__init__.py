@@ -23,8 +23,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   sparse LU equals a dense solve of M; ND order is a permutation whose separators
   disconnect the two halves.                                                    pinned
 * ``gmres_right``: dense solve of (I + K omega^2 m) u = g at n <= 32.          pinned
-* whole discrete solve: Mie series of a constant-contrast disk, error decreasing
-  with n (``mie.py``).                                                          pinned
+* whole discrete solve: Mie series of a constant-contrast disk (2D) and ball (3D), error
+  decreasing with n (``mie.py``; the series checked by their interface conditions and
+  the Helmholtz equation on both sides).                                        pinned
 * the sparsity claim A K ~ C (Sec. 2.2): reported ratio only, the paper prints
   no magnitude.                                                  parity unpinned
 * Laplace variant (Sec. 5, ``omega = 0`` in 3D, ``point_source``, ``laplace_solve``):

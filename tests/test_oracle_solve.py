@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from oracle.mie import mie_disk_scattered
+from oracle.mie import mie_disk_scattered, mie_sphere_scattered
 from paper_1408_4495_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -184,3 +184,42 @@ def test_M_approximates_stencil_times_operator(d, n):
     Sx = S @ x.reshape(-1)
     part = np.linalg.norm(SAx - Sx)
     assert np.linalg.norm(SAx - Mx) < 0.05 * part
+
+
+def test_sphere_mie_series_satisfies_interface_conditions():
+    # continuity of the total field and of its radial derivative at r = R, and Helmholtz
+    # inside (k1^2 = omega^2 (1 - m0)) and outside (omega^2), by finite differences
+    omega, m0, R = 9.0, -0.3, 0.25
+    eps = 1e-6
+
+    def tot(x):
+        return mie_sphere_scattered(*[np.array([v]) for v in x], omega, m0, R)[0] + np.exp(1j * omega * x[0])
+
+    for t, p in ((0.3, 0.2), (1.4, 2.1), (2.7, 4.0)):
+        e = np.array([np.cos(t), np.sin(t) * np.cos(p), np.sin(t) * np.sin(p)])
+        at = lambda rr: tot(0.5 + rr * e)
+        assert abs(at(R - eps) - at(R + eps)) < 1e-4
+        dm = (at(R - eps) - at(R - 3 * eps)) / (2 * eps)
+        dp = (at(R + 3 * eps) - at(R + eps)) / (2 * eps)
+        assert abs(dm - dp) < 1e-2 * (1 + abs(dm))
+    dl = 1e-3
+    for x0, k2 in ((np.array([0.55, 0.47, 0.52]), omega**2 * (1 - m0)), (np.array([0.9, 0.3, 0.6]), omega**2)):
+        lap = sum(tot(x0 + dl * np.eye(3)[a]) + tot(x0 - dl * np.eye(3)[a]) for a in range(3)) - 6 * tot(x0)
+        lap /= dl**2
+        assert abs(lap + k2 * tot(x0)) < 1e-3 * omega**2
+
+
+def test_3d_discrete_solution_converges_to_the_sphere_mie_series():
+    """Constant-contrast ball: the relative L2 error of the 3D solve against the Mie series
+    decreases under refinement (measured 5.8e-2 at n = 15, 1.8e-2 at n = 31)."""
+    omega = 2 * np.pi * 1.5
+    errs = []
+    for n in (15, 31):
+        X = O.grid_coords(n, 3)
+        r = np.sqrt(sum((X[a] - 0.5) ** 2 for a in range(3)))
+        m = np.where(r < 0.25, -0.3, 0.0)
+        res = O.solve(n, 3, omega, m, [(1.0, 0.0, 0.0)], tol=1e-10)
+        ue = mie_sphere_scattered(X[0], X[1], X[2], omega, -0.3, 0.25)
+        errs.append(np.linalg.norm(res["u"][0].reshape((n,) * 3) - ue) / np.linalg.norm(ue))
+    assert errs[0] < 0.08
+    assert errs[1] < 0.45 * errs[0]
