@@ -108,3 +108,18 @@ def test_sparsity_ratio_decreases_as_the_grid_resolves_the_wave():
         r = [O.sparsity_ratio(n, d, 2 * np.pi * freq) for n in ns]
         assert all(a > b for a, b in zip(r, r[1:])), r
         assert r[-1] < 1e-3
+
+
+@pytest.mark.parametrize("d,n,omega", [(2, 64, 0.01), (3, 16, 0.1)])
+def test_small_omega_interior_stencil_is_a_discrete_laplacian(d, n, omega):
+    """As omega h -> 0 the kernel's far field is harmonic with a slowly decaying monopole, so
+    the minimiser must annihilate constants: the interior alpha becomes (up to scale) a
+    symmetric zero-sum stencil, i.e. a 3^d-point discrete -Laplacian (positive centre,
+    negative neighbours), real up to O(omega h)."""
+    mu, a = O.stencil(n, d, omega, 2, (0,) * d)
+    A = dict(zip(mu, a))
+    c = A[(0,) * d]
+    assert c.real > 0
+    assert abs(sum(a)) < 1e-3 * abs(c)
+    assert np.max(np.abs(np.imag(a))) < 1e-6 * abs(c)
+    assert all(v.real < 0 for t, v in A.items() if any(t))
