@@ -76,3 +76,47 @@ def test_binding_refuses_without_library(tmp_path):
             LS.load(str(tmp_path / "missing.so"))
     finally:
         LS._lib = saved
+
+
+def test_host_entry_points_from_a_c_program(tmp_path, lib):
+    # the C-ABI used from C: a program compiled against include/ls.h and linked with libls
+    # calls the host computations (no device needed) and reports status and values
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "ls.h"
+int main(void) {
+  double k[2];
+  if (ls_k0_weight(3, 6.283185307179586, 1.0 / 17.0, LS_K0_BALL, k) != LS_OK) return 1;
+  printf("%.17g %.17g\n", k[0], k[1]);
+  if (ls_k0_weight(4, 1.0, 0.1, LS_K0_BALL, k) != LS_EINVAL) return 2;
+  const int n = 16;
+  double* m = calloc((size_t)n * n, sizeof(double));
+  unsigned char* mask = calloc((size_t)n * n, 1);
+  m[8 * n + 8] = -0.2;
+  if (ls_general_support(2, n, m, 2, mask) != LS_OK) return 3;
+  int cnt = 0;
+  for (int i = 0; i < n * n; ++i) cnt += mask[i] != 0;
+  printf("%d\n", cnt);
+  printf("%s\n", ls_last_error(NULL) ? "ok" : "null");
+  free(m);
+  free(mask);
+  return 0;
+}
+""")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(B.LIB)
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lls",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    re_, im_ = (float(v) for v in out[0].split())
+    ref = LS.k0_weight(3, 6.283185307179586, 1.0 / 17.0, LS.LS_K0_BALL)
+    assert re_ == ref.real and im_ == ref.imag
+    assert int(out[1]) == 7 * 7  # the point and its b + 1 = 3 layers
+    assert out[2] == "ok"
