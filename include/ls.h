@@ -127,6 +127,16 @@ ls_status ls_setup_laplace(const ls_grid* g, const double* V, void* stream, ls_c
  * device wait expired); after such an error the context needs ls_factor again.
  */
 ls_status ls_factor(ls_ctx* c);
+/*
+ * ls_set_medium -- a new medium m (n^d doubles, C order, host or device; V for a Laplace
+ * context) on the context's grid, frequency and kernel, with the checks of ls_setup
+ * (LS_EINVAL, LS_EBUFFER; the context is unchanged on failure).  The tables that depend only
+ * on (d, n, omega, b, k0_rule) -- symbol, stencils, nested-dissection structure -- and the
+ * device buffers are kept, so a sequence of media on one grid costs no setup.  Drops the
+ * factorization (ls_factor must run again before ls_solve) and a general-domain
+ * preconditioner (ls_general_setup must run again).
+ */
+ls_status ls_set_medium(ls_ctx* c, const double* m);
 
 /*
  * ls_rhs_plane_wave -- Sec. 1 eq. ls, Sec. 2.1 eq. lsd: g = K(-omega^2 m u_I) with the

@@ -500,6 +500,37 @@ bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 // =======================================================================================
 // C-ABI
 // =======================================================================================
+// Medium of a context (Sec. 2.1): the host copy of m (host or device pointer) is checked --
+// finite, 1 - m > 0 (Helmholtz), zero within b + 1 layers of the boundary -- and turned into
+// the potential omega^2 m (V itself for a Laplace context) in FP64 and FP32.
+static void medium_weights(const ls_ctx* c, const double* m, std::vector<double>& w64, std::vector<float>& w32) {
+  const long N = c->N;
+  const int n = c->n;
+  std::vector<double> mh(N);
+  if (is_device_ptr(m)) LS_CUDA(cudaMemcpy(mh.data(), m, N * sizeof(double), cudaMemcpyDeviceToHost));
+  else std::memcpy(mh.data(), m, N * sizeof(double));
+  const int wl = c->b + 1;
+  for (long i = 0; i < N; ++i) {
+    if (!std::isfinite(mh[i])) throw Error{ls::EINVAL_, "the medium must be finite"};
+    if (!c->laplace && !(1.0 - mh[i] > 0)) throw Error{ls::EINVAL_, "m must satisfy 1 - m > 0"};
+    long q = i;
+    bool edge = false;
+    for (int a = 0; a < c->d; ++a) {
+      const long ia = q % n;
+      q /= n;
+      if (ia < wl || ia >= n - wl) edge = true;
+    }
+    if (edge && mh[i] != 0.0) throw Error{ls::EBUFFER_, "the medium must vanish within b+1 layers of the boundary"};
+  }
+  w64.resize(N);
+  w32.resize(N);
+  const double w2 = c->laplace ? 1.0 : c->omega * c->omega;
+  for (long i = 0; i < N; ++i) {
+    w64[i] = c->laplace ? mh[i] : w2 * mh[i];
+    w32[i] = (float)w64[i];
+  }
+}
+
 extern "C" {
 
 // Shared by ls_setup (Helmholtz kernel, medium m, potential omega^2 m) and ls_setup_laplace
@@ -543,29 +574,9 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     }
     LS_CUDA(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
     LS_CUDA(cudaEventCreateWithFlags(&c->ev_factor, cudaEventDisableTiming));
-    // medium: checks on the host copy (Sec. 2.1: m vanishes within the buffer; 1 - m > 0)
-    std::vector<double> mh(c->N);
-    if (is_device_ptr(m)) LS_CUDA(cudaMemcpy(mh.data(), m, c->N * sizeof(double), cudaMemcpyDeviceToHost));
-    else std::memcpy(mh.data(), m, c->N * sizeof(double));
-    const int wl = b + 1;
-    for (long i = 0; i < c->N; ++i) {
-      if (!std::isfinite(mh[i])) throw Error{ls::EINVAL_, "the medium must be finite"};
-      if (!laplace && !(1.0 - mh[i] > 0)) throw Error{ls::EINVAL_, "m must satisfy 1 - m > 0"};
-      long q = i;
-      bool edge = false;
-      for (int a = 0; a < c->d; ++a) {
-        const long ia = q % n;
-        q /= n;
-        if (ia < wl || ia >= n - wl) edge = true;
-      }
-      if (edge && mh[i] != 0.0) throw Error{ls::EBUFFER_, "the medium must vanish within b+1 layers of the boundary"};
-    }
-    std::vector<double> w64(c->N);
-    std::vector<float> w32(c->N);
-    for (long i = 0; i < c->N; ++i) {
-      w64[i] = laplace ? mh[i] : omega * omega * mh[i];
-      w32[i] = (float)w64[i];
-    }
+    std::vector<double> w64;
+    std::vector<float> w32;
+    medium_weights(c, m, w64, w32);
     c->w2m64 = dalloc<double>(c->N);
     c->w2m32 = dalloc<float>(c->N);
     LS_CUDA(cudaMemcpyAsync(c->w2m64, w64.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, c->st));
@@ -901,6 +912,40 @@ ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec p
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);
+  }
+}
+
+// A new medium on the context's grid, frequency and kernel: the potential tables (FP64,
+// FP32, float-float) are rewritten in place, so the stencils, the symbol, the
+// nested-dissection structure, the buffers and the captured graphs stay valid; the
+// factorization and a general-domain preconditioner (whose stencils depend on the medium)
+// are dropped.
+ls_status ls_set_medium(ls_ctx* c, const double* m) {
+  try {
+    check_ctx(c);
+    if (!m) throw Error{ls::EINVAL_, "NULL medium"};
+    std::vector<double> w64;
+    std::vector<float> w32;
+    medium_weights(c, m, w64, w32);
+    LS_CUDA(cudaStreamSynchronize(c->st));  // nothing in flight reads the old tables
+    c->factor_pending = false;
+    c->factored = false;
+    if (c->general) {
+      c->general = false;
+      ++c->gen;  // captured graphs hold the per-point tables
+    }
+    const long n1 = c->n + 1;
+    const size_t nq = c->d == 2 ? (size_t)(n1 * n1) : (size_t)(n1 * n1 * n1);
+    const size_t ntw = 2 * (size_t)c->L, nsy = 2 * nq;
+    LS_CUDA(cudaMemcpyAsync(c->w2m64, w64.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    LS_CUDA(cudaMemcpyAsync(c->w2m32, w32.data(), c->N * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    ls::to_ff(c->w2m64, c->ffbuf + ntw + nsy, c->N, c->st);
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::bad_alloc&) {
+    return fail(c, Error{ls::ENOMEM_, "host allocation failed"});
   }
 }
 

@@ -28,7 +28,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
            "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
-           "ls_general_sketch", "ls_general_setup", "ls_general_rows",
+           "ls_general_sketch", "ls_general_setup", "ls_general_rows", "ls_set_medium",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.ls_setup.argtypes = [ctypes.POINTER(LsGrid), dp, vp, vp, ctypes.POINTER(vp)]
     lib.ls_factor.argtypes = [vp]
+    lib.ls_set_medium.argtypes = [vp, vp]
     lib.ls_rhs_plane_wave.argtypes = [vp, ip, vp, vp]
     lib.ls_setup_laplace.argtypes = [ctypes.POINTER(LsGrid), vp, vp, ctypes.POINTER(vp)]
     lib.ls_rhs_point_source.argtypes = [vp, ip, vp, vp, vp]
@@ -256,6 +257,12 @@ class Solver:
     # ---- the path
     def factor(self):
         self._check(self.lib.ls_factor(self.h))
+
+    def set_medium(self, m):
+        """ls_set_medium: a new medium on this grid (drops the factorization)."""
+        if isinstance(m, np.ndarray):
+            m = np.ascontiguousarray(m, dtype=np.float64)
+        self._check(self.lib.ls_set_medium(self.h, _ptr(m)))
 
     def rhs_plane_wave(self, dirs, out=None):
         dirs_np = dirs if not isinstance(dirs, np.ndarray) else np.ascontiguousarray(dirs, dtype=np.float64)
