@@ -562,7 +562,7 @@ def run_serving(np, torch, count=64, seed=1006):
     return {"requests": st["requests"], "errors": st["errors"], "solves": st["solves"],
             "value": st["solves_per_s"], "unit": "solves/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "arrival_rate_per_s": rate, "slots": 4, "budget_bytes": budget, "cache_hits": st["cache_hits"],
-            "evictions": st["evictions"], "max_concurrent": st["max_concurrent"],
+            "evictions": st["evictions"], "retargets": st.get("retargets", 0), "max_concurrent": st["max_concurrent"],
             "max_used_bytes": st["max_used_bytes"], "all_converged": st["all_converged"],
             "mix_vs_alone_max_rel_l2": worst,
             "fp64_one_at_a_time": {"requests": st64["requests"], "value": st64["solves_per_s"], "unit": "solves/s",

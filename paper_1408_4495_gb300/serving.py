@@ -9,6 +9,11 @@ requests concurrently: every context owns its CUDA stream, so one request's fact
 overlaps another's FFTs and sweeps on the device.  Each result is the same as the request
 solved alone: contexts share no mutable state on the device.
 
+When memory must be freed for a new medium and an idle context of the same grid and
+frequency is resident, the engine gives that context the new medium (``retarget``:
+ls_set_medium, which keeps the stencils, the symbol, the nested-dissection structure and the
+buffers) instead of closing it and setting up a new one.
+
 The engine itself is host logic (threads, a condition variable, the admission queue); the
 device work goes through a backend, ``LibBackend`` for libls.  Latency is arrival to result
 on the host; the run reports p50 / p99 and the throughput in solves/s (incident directions
@@ -86,6 +91,9 @@ class LibBackend:
     def factor(self, ctx):
         ctx.factor()
 
+    def retarget(self, ctx, req: Request):
+        ctx.set_medium(req.m)
+
     def solve(self, ctx, req: Request):
         g = ctx.rhs_plane_wave(np.ascontiguousarray(req.dirs, dtype=np.float64))
         u, info = ctx.solve(g, self.tol, raise_on_noconv=False)
@@ -109,10 +117,10 @@ class Engine:
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         cv = threading.Condition()
         pending = collections.deque()
-        cache = collections.OrderedDict()  # key -> [ctx, bytes, busy, factored]
+        cache = collections.OrderedDict()  # key -> [ctx, bytes, busy, factored, grid]
         jobs = collections.deque()
         results = {}
-        stats = {"max_used_bytes": 0, "max_concurrent": 0, "evictions": 0, "cache_hits": 0}
+        stats = {"max_used_bytes": 0, "max_concurrent": 0, "evictions": 0, "cache_hits": 0, "retargets": 0}
         state = {"used": 0, "running": 0, "done": 0, "stop": False}
         t0 = clock()
 
@@ -160,9 +168,26 @@ class Engine:
                     if ent is not None and ent[2]:
                         break  # the medium's context is in use: keep FIFO order
                     if ent is None:
+                        grid = (req.d, req.n, req.omega)
+                        ctx = None
                         try:
-                            ctx = self.backend.open(req)
-                            need = self.backend.footprint(ctx, req)
+                            cand = self._idle_same_grid(cache, grid)
+                            if cand is not None:
+                                need = self.backend.footprint(cand[1][0], req)
+                                if need <= self.budget and state["used"] + need > self.budget:
+                                    # room must be made anyway: the idle context takes the medium
+                                    del cache[cand[0]]
+                                    state["used"] -= cand[1][1]
+                                    try:
+                                        self.backend.retarget(cand[1][0], req)
+                                    except Exception:
+                                        self.backend.close(cand[1][0])
+                                        raise
+                                    ctx = cand[1][0]
+                                    stats["retargets"] += 1
+                            if ctx is None:
+                                ctx = self.backend.open(req)
+                                need = self.backend.footprint(ctx, req)
                         except Exception as e:
                             res.error = f"{type(e).__name__}: {e}"
                             res.end = clock() - t0
@@ -183,7 +208,7 @@ class Engine:
                         if state["used"] + need > self.budget:
                             self.backend.close(ctx)
                             break  # wait for running requests to release memory
-                        ent = [ctx, need, False, False]
+                        ent = [ctx, need, False, False, grid]
                         cache[req.key] = ent
                         state["used"] += need
                         stats["max_used_bytes"] = max(stats["max_used_bytes"], state["used"])
@@ -223,6 +248,16 @@ class Engine:
             "all_converged": all(r.converged for r in ok),
         })
         return out, stats
+
+    def _idle_same_grid(self, cache, grid):
+        """The least recently used idle entry of this grid and frequency, if the backend can
+        give a context a new medium."""
+        if not hasattr(self.backend, "retarget"):
+            return None
+        for key, ent in cache.items():
+            if not ent[2] and ent[4] == grid:
+                return key, ent
+        return None
 
     def _evict_one(self, cache, state, stats) -> bool:
         for key, ent in cache.items():  # least recently used first

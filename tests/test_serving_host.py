@@ -121,3 +121,47 @@ def test_latency_statistics_follow_the_schedule():
     assert abs(st["p50_ms"] - np.percentile(lat, 50) * 1e3) < 1e-6
     assert st["p99_ms"] >= st["p50_ms"]
     assert st["solves"] == 10 and st["solves_per_s"] > 0
+
+
+class RetargetBackend(FakeBackend):
+    """Fake backend that can give an open context a new medium (as ls_set_medium does)."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.opened = 0
+        self.retargeted = 0
+
+    def open(self, req):
+        with self.lock:
+            self.opened += 1
+        return {"key": req.key, "grid": (req.d, req.n, req.omega)}
+
+    def retarget(self, ctx, req):
+        assert ctx["grid"] == (req.d, req.n, req.omega)
+        with self.lock:
+            self.retargeted += 1
+        ctx["key"] = req.key
+
+    def solve(self, ctx, req):
+        assert ctx["key"] == req.key  # the context holds this request's medium
+        return super().solve(ctx, req)
+
+
+def test_idle_contexts_of_the_same_grid_take_new_media():
+    be = RetargetBackend()
+    reqs = requests(40, 2000.0)  # every medium unique
+    budget = 2 * 32 * 32 * 1000  # two large media at a time
+    res, st = S.Engine(be, slots=2, budget_bytes=budget).run(reqs)
+    assert st["errors"] == 0 and st["all_converged"]
+    assert st["max_used_bytes"] <= budget
+    assert st["retargets"] > 0 and be.retargeted == st["retargets"]
+    assert be.opened + be.retargeted == len(reqs)  # no cache hits: every request got a context
+    for q, r in zip(sorted(reqs, key=lambda q: q.arrival), res):
+        assert np.array_equal(r.u, be.solve({"key": q.key}, q)[0])
+
+
+def test_no_retarget_while_memory_fits():
+    be = RetargetBackend()
+    reqs = requests(10, 2000.0)
+    res, st = S.Engine(be, slots=2, budget_bytes=1 << 30).run(reqs)
+    assert st["errors"] == 0 and st["retargets"] == 0 and be.opened == len(reqs)
