@@ -492,6 +492,37 @@ def run_gpu(args):
            "includes": "ls_setup (medium from pinned host) + ls_factor + ls_rhs_plane_wave + ls_solve "
                        "(solution to pinned host) + ls_free, wall clock"}
 
+    # ---- the same on one context that takes a new medium every step (ls_set_medium), the
+    # form a serving loop uses for a sequence of media on one grid
+    sg_local, sg_err = 0.0, None
+    try:
+        with ls.Solver(m_host.numpy(), w.omega, dim=w.d, buffer_b=w.buffer_b, restart=w.restart, mixed=True,
+                       stream=stream) as s:
+            def same_grid_step():
+                s.set_medium(m_host.numpy())
+                s.factor()
+                s.rhs_plane_wave(dirs_host.numpy(), out=g)
+                s.solve(g, TOL, out=u_host.numpy())
+                return float(np.abs(u_host.numpy()).max())
+
+            same_grid_step()
+            same_grid_step()  # graphs are captured on the second run
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                same_grid_step()
+            torch.cuda.synchronize()
+            sg_local = time.perf_counter() - t0
+    except Exception as e:  # reported in the line instead of losing the headline
+        sg_err = f"{type(e).__name__}: {e}"
+    sg_s = max_over_ranks(sg_local, dev, world)
+    e2e["same_grid"] = ({"error": sg_err} if sg_err else
+                        {"value": job_rate(w.nrhs * e2e_steps, world, sg_s), "unit": "solves/s",
+                         "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                         "d2h_bytes_per_step": e2e["d2h_bytes_per_step"],
+                         "includes": "ls_set_medium (medium from pinned host) + ls_factor + ls_rhs_plane_wave + "
+                                     "ls_solve (solution to pinned host) on one context, wall clock"})
+
     # ---- CPU oracle on the host cores (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
