@@ -28,449 +28,6 @@
 
 namespace ls {
 
-template <> struct RealOf<ffc> { using T = ff; };
-
-// read-only cached load of one complex entry
-template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
-template <> __device__ __forceinline__ ffc ldg_c<ffc>(const ffc* p) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-  ffc r;
-  r.x = ff(v.x, v.y);
-  r.y = ff(v.z, v.w);
-  return r;
-}
-
-// kernel-class names of the three arithmetics
-template <typename C> constexpr const char* arith_tag();
-template <> constexpr const char* arith_tag<float2>() { return "c64"; }
-template <> constexpr const char* arith_tag<double2>() { return "c128"; }
-template <> constexpr const char* arith_tag<ffc>() { return "cff"; }
-
-// Padded shared-memory index: one spare slot every 8 complex entries keeps the strided
-// Stockham writes (stride R = 8 in the first pass) free of bank conflicts.
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
-template <int L> struct Lay { static constexpr int LS = L + L / 8 + 1; };
-
-template <int SIGN, typename C> __device__ __forceinline__ C rot_i(C a) {
-  C r;
-  if (SIGN > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
-  return r;
-}
-
-// In-register R-point DFT, out[q] = sum_r v[r] exp(SIGN 2 pi i r q / R).
-template <int R, int SIGN, typename C> __device__ __forceinline__ void dft(C* v);
-template <> __device__ __forceinline__ void dft<2, -1, float2>(float2* v) { float2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
-template <> __device__ __forceinline__ void dft<2, 1, float2>(float2* v) { float2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
-template <> __device__ __forceinline__ void dft<2, -1, double2>(double2* v) { double2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
-template <> __device__ __forceinline__ void dft<2, 1, double2>(double2* v) { double2 a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
-template <> __device__ __forceinline__ void dft<2, -1, ffc>(ffc* v) { ffc a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
-template <> __device__ __forceinline__ void dft<2, 1, ffc>(ffc* v) { ffc a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
-
-template <int SIGN, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-  C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = rot_i<SIGN>(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
-}
-
-template <int SIGN, typename C> __device__ __forceinline__ void dft4v(C* v) { dft4<SIGN>(v[0], v[1], v[2], v[3]); }
-
-template <typename Rl> __device__ __forceinline__ Rl cos_pi4() { return (Rl)0.70710678118654752440; }
-// cos(pi/4) as an FP32 pair: 0.70710677 + 1.21016175e-8
-template <> __device__ __forceinline__ ff cos_pi4<ff>() { return ff(0.70710677f, 1.21016175e-8f); }
-
-template <int SIGN, typename C> __device__ __forceinline__ void dft8v(C* v) {
-  using Rl = typename RealOf<C>::T;
-  const Rl c = cos_pi4<Rl>();
-  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-  dft4<SIGN>(e0, e1, e2, e3);
-  dft4<SIGN>(o0, o1, o2, o3);
-  // o_q *= W8^q, W8 = exp(SIGN 2 pi i / 8)
-  C t;
-  t.x = c * (o1.x - SIGN * o1.y); t.y = c * (SIGN * o1.x + o1.y); o1 = t;
-  o2 = rot_i<SIGN>(o2);
-  t.x = c * (-o3.x - SIGN * o3.y); t.y = c * (SIGN * o3.x - o3.y); o3 = t;
-  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
-  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
-  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
-}
-
-template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR(C* v) {
-  if constexpr (R == 8) dft8v<SIGN>(v);
-  else if constexpr (R == 4) dft4v<SIGN>(v);
-  else dft<2, SIGN, C>(v);
-}
-
-// One radix-R Stockham pass over NLINES lines of length L held in shared memory.
-// Pass input: sub-transforms of length NS; output: sub-transforms of length NS * R.
-// Butterfly j of a line reads entries j + r L/R, multiplies by w^{r k} with
-// w = exp(SIGN 2 pi i / (NS R)), k = j mod NS, and writes (j / NS) NS R + k + r NS.
-template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT>
-__device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
-  constexpr int LS = Lay<L>::LS;
-  constexpr int BPL = L / R;
-  constexpr int BF = NLINES * BPL;
-  constexpr int PER = (BF + NT - 1) / NT;
-  C v[PER][R];
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int b = threadIdx.x + q * NT;
-    if (BF % NT == 0 || b < BF) {
-      const int line = b / BPL, j = b - line * BPL;
-      const C* sl = s + line * LS;
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = sl[pidx(j + r * BPL)];
-      if constexpr (NS > 1) {
-        const int k = j & (NS - 1);
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C w = ldg_c(&tw[r * k * (L / (NS * R))]);
-          if (SIGN > 0) w.y = -w.y;
-          v[q][r] = cmul(v[q][r], w);
-        }
-      }
-      dftR<R, SIGN>(v[q]);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int b = threadIdx.x + q * NT;
-    if (BF % NT == 0 || b < BF) {
-      const int line = b / BPL, j = b - line * BPL;
-      C* sl = s + line * LS;
-      const int k = j & (NS - 1);
-      const int base = (j / NS) * NS * R + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) sl[pidx(base + r * NS)] = v[q][r];
-    }
-  }
-  __syncthreads();
-}
-
-template <typename C, int L, int NS, int SIGN, int NLINES, int NT>
-__device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw) {
-  if constexpr (NS < L) {
-    constexpr int REM = L / NS;
-    constexpr int R = REM >= 8 ? 8 : REM;
-    fft_pass<C, L, R, NS, SIGN, NLINES, NT>(s, tw);
-    fft_lines<C, L, NS * R, SIGN, NLINES, NT>(s, tw);
-  }
-}
-
-// ------------------------------------------------------------------------------------
-// Launch shapes
-// ------------------------------------------------------------------------------------
-template <int L> struct RowShape {
-  static constexpr int NT = (L / 8 > 256) ? L / 8 : 256;
-  static constexpr int NL = NT * 8 / L;
-};
-// TC adjacent lines per CTA (about 64 KB of shared memory); FP32 lines of 512 and more
-// take 8 lines and 2 butterflies per thread, so that two CTAs fit an SM's registers
-template <typename C, int L> struct ColShape {
-  static constexpr int raw = 65536 / (L * (int)sizeof(C));
-  static constexpr bool f32_long = sizeof(C) == 8 && L >= 512;
-  static constexpr int TC = f32_long ? 8 : (raw < 2 ? 2 : (raw > 16 ? 16 : raw));
-  static constexpr int t = f32_long ? TC * L / 16 : TC * L / 8;
-  static constexpr int NT = t > 512 ? 512 : (t < 64 ? 64 : t);
-};
-
-// ------------------------------------------------------------------------------------
-// Row pass: lines contiguous in memory.
-// ------------------------------------------------------------------------------------
-template <typename C, int L, int SIGN>
-__global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
-  constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL, LS = Lay<L>::LS;
-  using Rl = typename RealOf<C>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* s = reinterpret_cast<C*>(smem_raw);
-  const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
-  const long line0 = (long)blockIdx.x * NL;
-  const int n_in = a.n_in;
-
-  // load n_in entries of NL lines (coalesced), apply the prologue
-  if (a.plane_dirs == nullptr) {
-    // LB independent loads in flight per thread before the first shared-memory store
-    constexpr int LB = 4;
-    const int tot = NL * n_in;
-    const C* __restrict__ in = reinterpret_cast<const C*>(a.in);
-    const Rl* __restrict__ pw = reinterpret_cast<const Rl*>(a.pw);
-    for (int base = threadIdx.x; base < tot; base += NT * LB) {
-      C v[LB];
-      Rl wv[LB];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = base + u * NT;
-        v[u] = czero<C>();
-        wv[u] = (Rl)1;
-        if (idx < tot) {
-          const int li = idx / n_in, e = idx - li * n_in;
-          const long line = line0 + li;
-          if (line < a.lines) {
-            if constexpr (std::is_same<C, ffc>::value) {
-              v[u] = a.in64 ? ffc_from(reinterpret_cast<const double2*>(a.in)[line * a.in_ls + e])
-                            : in[line * a.in_ls + e];
-            } else {
-              v[u] = in[line * a.in_ls + e];
-            }
-            if (pw != nullptr) wv[u] = pw[(line % a.pw_lines) * n_in + e];
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = base + u * NT;
-        if (idx < tot) {
-          const int li = idx / n_in, e = idx - li * n_in;
-          C x = v[u];
-          x.x *= wv[u];
-          x.y *= wv[u];
-          s[li * LS + pidx(e)] = x;
-        }
-      }
-    }
-  } else
-  for (int idx = threadIdx.x; idx < NL * n_in; idx += NT) {
-    const int li = idx / n_in, e = idx - li * n_in;
-    const long line = line0 + li;
-    C v = czero<C>();
-    if (line < a.lines) {
-      if (a.plane_dirs != nullptr) {
-        if constexpr (std::is_same<C, double2>::value || std::is_same<C, ffc>::value) {
-          // v = -omega^2 m(x) exp(i omega x . dir) (right-hand side, eq. ls), in FP64
-          const long q = line % a.pw_lines;      // row within the grid
-          const long rhs = line / a.pw_lines;
-          const double* dir = a.plane_dirs + rhs * a.d;
-          double ph = (double)(e + 1) * dir[a.d - 1];
-          long qq = q;
-          for (int ax = a.d - 2; ax >= 0; --ax) {
-            const long ia = qq % a.n;
-            qq /= a.n;
-            ph += (double)(ia + 1) * dir[ax];
-          }
-          ph *= a.omega * a.h;
-          double sn, cs;
-          sincos(ph, &sn, &cs);
-          const double w = a.pw64[q * n_in + e];
-          if constexpr (std::is_same<C, ffc>::value) v = ffc_from(make_double2(-w * cs, -w * sn));
-          else v = make_double2(-w * cs, -w * sn);
-        }
-      } else {
-        v = reinterpret_cast<const C*>(a.in)[line * a.in_ls + e];
-        if (a.pw != nullptr) {
-          const Rl w = reinterpret_cast<const Rl*>(a.pw)[(line % a.pw_lines) * n_in + e];
-          v.x *= w;
-          v.y *= w;
-        }
-      }
-    }
-    s[li * LS + pidx(e)] = v;
-  }
-  if (n_in < L) {
-    const int padn = L - n_in;
-    for (int idx = threadIdx.x; idx < NL * padn; idx += NT) {
-      const int li = idx / padn, e = n_in + (idx - li * padn);
-      s[li * LS + pidx(e)] = czero<C>();
-    }
-  }
-  __syncthreads();
-  fft_lines<C, L, 1, SIGN, NL, NT>(s, tw);
-  const int n_out = a.n_out;
-  C* out = reinterpret_cast<C*>(a.out);
-  const C* addv = reinterpret_cast<const C*>(a.addv);
-  for (int idx = threadIdx.x; idx < NL * n_out; idx += NT) {
-    const int li = idx / n_out, e = idx - li * n_out;
-    const long line = line0 + li;
-    if (line < a.lines) {
-      C v = s[li * LS + pidx(e)];
-      if constexpr (std::is_same<C, ffc>::value) {
-        if (a.out64) {
-          // FP64 epilogue: y = v + addv, or y = subv - (v + addv)
-          double2 o = ffc_to(v);
-          if (a.addv != nullptr) o = cadd(o, reinterpret_cast<const double2*>(a.addv)[line * a.add_ls + e]);
-          if (a.subv != nullptr) o = csub(reinterpret_cast<const double2*>(a.subv)[line * a.add_ls + e], o);
-          reinterpret_cast<double2*>(a.out)[line * a.out_ls + e] = o;
-          continue;
-        }
-      }
-      if (addv != nullptr) v = cadd(v, addv[line * a.add_ls + e]);
-      out[line * a.out_ls + e] = v;
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------------
-// Column pass: lines strided (element stride es), TC adjacent lines per CTA.
-// MODE 0: forward; 1: inverse; 2: forward, multiply by the symbol, inverse.
-// ------------------------------------------------------------------------------------
-template <typename C, int L, int MODE>
-__global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) {
-  constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC, LS = Lay<L>::LS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* s = reinterpret_cast<C*>(smem_raw);
-  const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
-  const long tiles = (a.inner + TC - 1) / TC;
-  const long o = blockIdx.x / tiles;
-  const long c0 = (blockIdx.x - o * tiles) * TC;
-  const C* in = reinterpret_cast<const C*>(a.in) + o * a.in_os + c0;
-  const int n_in = a.n_in;
-  {
-    // LB independent loads in flight per thread before the first shared-memory store
-    constexpr int LB = 4;
-    const int tot = n_in * TC;
-    for (int base = threadIdx.x; base < tot; base += NT * LB) {
-      C v[LB];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = base + u * NT;
-        v[u] = czero<C>();
-        if (idx < tot) {
-          const int e = idx / TC, c = idx - e * TC;
-          if (c0 + c < a.inner) v[u] = in[(long)e * a.in_es + c];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = base + u * NT;
-        if (idx < tot) {
-          const int e = idx / TC, c = idx - e * TC;
-          s[c * LS + pidx(e)] = v[u];
-        }
-      }
-    }
-  }
-  if (n_in < L) {
-    const int padn = L - n_in;
-    for (int idx = threadIdx.x; idx < padn * TC; idx += NT) {
-      const int e = n_in + idx / TC, c = idx % TC;
-      s[c * LS + pidx(e)] = czero<C>();
-    }
-  }
-  __syncthreads();
-  if constexpr (MODE == 0) {
-    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
-  } else if constexpr (MODE == 1) {
-    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
-  } else {
-    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
-    const C* __restrict__ sym = reinterpret_cast<const C*>(a.sym);
-    const int n1 = a.n + 1;
-    // symbol values of SB entries loaded together, then applied
-    constexpr int SB = 8;
-    for (int base = threadIdx.x; base < L * TC; base += NT * SB) {
-      C sv[SB];
-#pragma unroll
-      for (int u = 0; u < SB; ++u) {
-        const int idx = base + u * NT;
-        const int e = idx / TC, c = idx - e * TC;
-        const long cc = c0 + c;
-        sv[u] = czero<C>();
-        if (idx < L * TC && cc < a.inner) {
-          const int q0 = e <= L - e ? e : L - e;
-          long si;
-          if (a.d == 2) {
-            const int k1 = (int)cc;
-            si = (long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1);
-          } else {
-            const int k1 = (int)(cc / L), k2 = (int)(cc - (long)k1 * L);
-            si = ((long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1)) * n1 + (k2 <= L - k2 ? k2 : L - k2);
-          }
-          sv[u] = ldg_c(&sym[si]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < SB; ++u) {
-        const int idx = base + u * NT;
-        const int e = idx / TC, c = idx - e * TC;
-        if (idx < L * TC && c0 + c < a.inner) {
-          C& v = s[c * LS + pidx(e)];
-          v = cmul(v, sv[u]);
-        }
-      }
-    }
-    __syncthreads();
-    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
-  }
-  C* out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
-  const int n_out = a.n_out;
-  for (int idx = threadIdx.x; idx < n_out * TC; idx += NT) {
-    const int e = idx / TC, c = idx - e * TC;
-    if (c0 + c < a.inner) out[(long)e * a.out_es + c] = s[c * LS + pidx(e)];
-  }
-}
-
-// ------------------------------------------------------------------------------------
-// Host dispatch
-// ------------------------------------------------------------------------------------
-template <typename C, int L, int SIGN> static void launch_row_L(const RowPassArgs& a, cudaStream_t st) {
-  constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL;
-  const size_t smem = (size_t)NL * Lay<L>::LS * sizeof(C);
-  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
-  if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_row_pass<C, L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr.store(true, std::memory_order_release);
-  }
-  const long blocks = (a.lines + NL - 1) / NL;
-  if (blocks == 0) return;
-  static const std::string cls = std::string(SIGN < 0 ? "fft_row_fwd_" : "fft_row_inv_") + arith_tag<C>();
-  LS_LAUNCH(cls.c_str(), st, k_row_pass<C, L, SIGN><<<(unsigned)blocks, NT, smem, st>>>(a));
-}
-
-template <typename C, int L, int MODE> static void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
-  constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
-  const size_t smem = (size_t)TC * Lay<L>::LS * sizeof(C);
-  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
-  if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_col_pass<C, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr.store(true, std::memory_order_release);
-  }
-  const long tiles = (a.inner + TC - 1) / TC;
-  const long blocks = tiles * a.outer;
-  if (blocks == 0) return;
-  static const std::string cls =
-      std::string(MODE == 0 ? "fft_col_fwd_" : MODE == 1 ? "fft_col_inv_" : "fft_col_sym_") + arith_tag<C>();
-  LS_LAUNCH(cls.c_str(), st, k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a));
-}
-
-#define LS_FOR_L(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
-
-template <typename C> void row_pass(int L, int sign, const RowPassArgs& a, cudaStream_t st) {
-  switch (L) {
-#define CASE(LL)                                                     \
-  case LL:                                                           \
-    if (sign < 0) launch_row_L<C, LL, -1>(a, st);                    \
-    else launch_row_L<C, LL, 1>(a, st);                              \
-    return;
-    LS_FOR_L(CASE)
-#undef CASE
-  }
-  LS_FAIL(EINVAL_, "unsupported FFT length %d", L);
-}
-
-template <typename C> void col_pass(int L, int mode, const ColPassArgs& a, cudaStream_t st) {
-  switch (L) {
-#define CASE(LL)                                                     \
-  case LL:                                                           \
-    if (mode == 0) launch_col_L<C, LL, 0>(a, st);                    \
-    else if (mode == 1) launch_col_L<C, LL, 1>(a, st);               \
-    else launch_col_L<C, LL, 2>(a, st);                              \
-    return;
-    LS_FOR_L(CASE)
-#undef CASE
-  }
-  LS_FAIL(EINVAL_, "unsupported FFT length %d", L);
-}
-
-template void row_pass<float2>(int, int, const RowPassArgs&, cudaStream_t);
-template void row_pass<double2>(int, int, const RowPassArgs&, cudaStream_t);
-template void col_pass<float2>(int, int, const ColPassArgs&, cudaStream_t);
-template void col_pass<double2>(int, int, const ColPassArgs&, cudaStream_t);
-template void row_pass<ffc>(int, int, const RowPassArgs&, cudaStream_t);
-template void col_pass<ffc>(int, int, const ColPassArgs&, cudaStream_t);
-
 // ------------------------------------------------------------------------------------
 // Operator-level sequences
 // ------------------------------------------------------------------------------------

@@ -1,0 +1,9 @@
+// The FFT passes in FP32 arithmetic (see fft_passes.cuh).
+#include "fft_passes.cuh"
+
+namespace ls {
+
+template void row_pass<float2>(int, int, const RowPassArgs&, cudaStream_t);
+template void col_pass<float2>(int, int, const ColPassArgs&, cudaStream_t);
+
+}  // namespace ls
