@@ -165,3 +165,23 @@ def test_no_retarget_while_memory_fits():
     reqs = requests(10, 2000.0)
     res, st = S.Engine(be, slots=2, budget_bytes=1 << 30).run(reqs)
     assert st["errors"] == 0 and st["retargets"] == 0 and be.opened == len(reqs)
+
+
+def test_a_failed_retarget_is_reported_and_the_engine_keeps_serving():
+    class Flaky(RetargetBackend):
+        def retarget(self, ctx, req):
+            if req.rid % 3 == 0:
+                raise RuntimeError("set_medium refused")
+            super().retarget(ctx, req)
+
+    be = Flaky()
+    reqs = requests(30, 2000.0)
+    budget = 2 * 32 * 32 * 1000
+    res, st = S.Engine(be, slots=2, budget_bytes=budget).run(reqs)
+    assert st["requests"] == 30 and st["max_used_bytes"] <= budget
+    failed = [r for r in res if r.error]
+    assert failed and all("set_medium refused" in r.error for r in failed)
+    assert all(r.rid % 3 == 0 for r in failed)
+    for q, r in zip(sorted(reqs, key=lambda q: q.arrival), res):
+        if not r.error:
+            assert np.array_equal(r.u, be.solve({"key": q.key}, q)[0])
