@@ -29,6 +29,7 @@
 #include "krylov.h"
 #include "ls.h"
 #include "prof.h"
+#include "trace.h"
 
 using ls::Error;
 using ls::ffc;
@@ -329,6 +330,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
   void* wlive = buf<double2>(c, "live_w", tot);
 
   while (true) {
+    ls::Range cycle_range("gmres_cycle");
     bool any = false;
     for (int j = 0; j < nrhs; ++j) {
       act[j] = !conv[j] && iters[j] < c->max_iter;
@@ -464,6 +466,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
     }
     // residual r = g - A u in FP64 storage; the operator in float-float arithmetic on the
     // mixed path (GB300's FP64 rate is a small fraction of its FP32 rate), FP64 otherwise
+    ls::Range resid_range("true_residual");
     run_graph(c, "resid:" + std::to_string(nrhs), [&] {
       if (mixed) {
         op_apply_ff(c, nrhs, u, r, g);
@@ -539,6 +542,7 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
                               ls_ctx** out) {
   if (out) *out = nullptr;
   ls_ctx* c = nullptr;
+  ls::Range range(laplace ? "ls_setup_laplace" : "ls_setup");
   try {
     if (!g || !m || !out) throw Error{ls::EINVAL_, "NULL argument"};
     if (g->dim != 2 && g->dim != 3) throw Error{ls::EINVAL_, "dim must be 2 or 3"};
@@ -698,6 +702,7 @@ ls_status ls_setup_laplace(const ls_grid* g, const double* V, void* stream, ls_c
 }
 
 ls_status ls_factor(ls_ctx* c) {
+  ls::Range range("ls_factor");
   try {
     check_ctx(c);
     c->factored = false;
@@ -720,6 +725,7 @@ ls_status ls_factor(ls_ctx* c) {
 }
 
 ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_out) {
+  ls::Range range("ls_rhs_plane_wave");
   try {
     check_ctx(c);
     if (c->laplace) throw Error{ls::ESTATE_, "plane waves need the Helmholtz kernel (omega > 0)"};
@@ -806,6 +812,7 @@ ls_status ls_far_field(ls_ctx* c, int nrhs, const double* dirs, const double* us
 }
 
 ls_status ls_solve(ls_ctx* c, int nrhs, const double* rhs, double tol, double* u_out, ls_info* info) {
+  ls::Range range("ls_solve");
   try {
     check_ctx(c);
     if (!c->factored) throw Error{ls::ESTATE_, "ls_solve before ls_factor"};
