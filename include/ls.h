@@ -271,6 +271,14 @@ ls_status ls_general_setup(ls_ctx* c, const unsigned char* mask, const double* a
  */
 ls_status ls_general_rows(int dim, int n, const unsigned char* mask, const double* alpha, const int* boundary,
                           const double* alpha_interior, double* rows, unsigned char* interior);
+/*
+ * ls_fault_alloc -- host-side fault injection for tests of the error paths (no GPU fault is
+ * ever induced): the k-th device allocation of the library after this call (k >= 1,
+ * process-wide, counted before the caching allocator is consulted) fails as if the device
+ * were out of memory, so the call that made it returns LS_ENOMEM with the word "injected"
+ * in its message.  k = 0 disarms.  LS_EINVAL for k < 0.
+ */
+ls_status ls_fault_alloc(long k);
 /* Message of the last failed call on c (or of the last failed ls_setup when c is NULL).
  * Valid until the next call on c. */
 const char* ls_last_error(const ls_ctx* c);

@@ -8,11 +8,13 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <unordered_map>
 
 #include "common.cuh"
+#include "ls.h"
 
 namespace ls {
 
@@ -42,9 +44,19 @@ size_t size_class(size_t bytes) {
   return (bytes + g - 1) / g * g;
 }
 
+// Host-side fault injection (ls_fault_alloc): the number of device allocations still to
+// pass before one is refused; 0 = disarmed.
+std::atomic<long> fault_countdown{0};
+
 }  // namespace
 
 void* dev_alloc(size_t bytes) {
+  for (long k = fault_countdown.load(); k > 0;) {
+    if (fault_countdown.compare_exchange_weak(k, k - 1)) {
+      if (k == 1) LS_FAIL(ENOMEM_, "device allocation of %zu bytes refused (injected by ls_fault_alloc)", bytes);
+      break;
+    }
+  }
   int dev = 0;
   LS_CUDA(cudaGetDevice(&dev));
   const size_t cls = size_class(bytes == 0 ? 1 : bytes);
@@ -108,3 +120,9 @@ void dev_free(void* p) {
 }
 
 }  // namespace ls
+
+extern "C" ls_status ls_fault_alloc(long k) {
+  if (k < 0) return LS_EINVAL;
+  ls::fault_countdown.store(k);
+  return LS_OK;
+}

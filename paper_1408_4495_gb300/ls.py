@@ -28,7 +28,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 # every entry point declared in include/ls.h
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
            "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
-           "ls_general_sketch", "ls_general_setup", "ls_general_rows", "ls_set_medium",
+           "ls_general_sketch", "ls_general_setup", "ls_general_rows", "ls_set_medium", "ls_fault_alloc",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_setup.argtypes = [ctypes.POINTER(LsGrid), dp, vp, vp, ctypes.POINTER(vp)]
     lib.ls_factor.argtypes = [vp]
     lib.ls_set_medium.argtypes = [vp, vp]
+    lib.ls_fault_alloc.argtypes = [ctypes.c_long]
     lib.ls_rhs_plane_wave.argtypes = [vp, ip, vp, vp]
     lib.ls_setup_laplace.argtypes = [ctypes.POINTER(LsGrid), vp, vp, ctypes.POINTER(vp)]
     lib.ls_rhs_point_source.argtypes = [vp, ip, vp, vp, vp]
@@ -172,6 +173,13 @@ def general_boundary_stencils(mask: np.ndarray, T: np.ndarray):
     if st != LS_OK:
         raise LsError(st, "ls_general_boundary_stencils: bad arguments or an undetermined stencil")
     return alpha, bnd.astype(bool)
+
+
+def fault_alloc(k: int):
+    """ls_fault_alloc: the k-th device allocation from now fails with LS_ENOMEM (0 disarms)."""
+    st = load().ls_fault_alloc(int(k))
+    if st != LS_OK:
+        raise LsError(st, "ls_fault_alloc: k must be >= 0")
 
 
 def general_rows(mask: np.ndarray, alpha: np.ndarray, boundary: np.ndarray, alpha_interior: np.ndarray):

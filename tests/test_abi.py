@@ -120,3 +120,13 @@ int main(void) {
     assert re_ == ref.real and im_ == ref.imag
     assert int(out[1]) == 7 * 7  # the point and its b + 1 = 3 layers
     assert out[2] == "ok"
+
+
+def test_fault_injection_arms_and_disarms_on_the_host(lib):
+    # arming touches no device; the injected failure itself is exercised by the GPU tests
+    assert lib.ls_fault_alloc(ctypes.c_long(3)) == LS.LS_OK
+    assert lib.ls_fault_alloc(ctypes.c_long(0)) == LS.LS_OK
+    assert lib.ls_fault_alloc(ctypes.c_long(-1)) == LS.LS_EINVAL
+    LS.fault_alloc(0)
+    with pytest.raises(LS.LsError):
+        LS.fault_alloc(-2)
