@@ -56,7 +56,7 @@ def test_table_and_C_take_the_corrected_weight(LS, d, n, freq):
     with LS.Solver(m, omega, mixed=False, laplace=lap, k0_rule=LS.LS_K0_CORRECTED) as s:
         kc = s.kernel_table()
         Ac, Cc = s.stencils()
-    assert abs(kc.flat[0] - k0) < 1e-12 * abs(k0)
+    assert abs(kc.flat[0] - k0) < 1e-11 * abs(k0)  # two independent quadratures (~2e-13 here)
     assert np.array_equal(kc.flat[1:], kb.flat[1:])
     assert np.max(np.abs(Ac - Ab)) < 1e-14
     _, (mu0, c) = O.all_stencils(n, d, omega, 2, k0=k0)
