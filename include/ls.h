@@ -73,7 +73,19 @@ typedef struct {
                     ls_k0_rule below: 0 = LS_K0_BALL (the default of a zero-initialised
                     struct), 1 = LS_K0_CORRECTED (fourth order up to a log); it enters the
                     operator, the symbol, C = alpha K(mu, mu) and the point sources */
+  int front_fmt; /* arithmetic of the fronts' Schur products under LS_PREC_MIXED, an
+                    ls_front_fmt below: 0 = LS_FRONT_3XTF32 (the default of a zero-initialised
+                    struct), 1 = LS_FRONT_FP32; ignored under LS_PREC_FP64 */
 } ls_grid;
+
+/* Fronts under LS_PREC_MIXED are stored in FP32.  LS_FRONT_3XTF32: the Schur-complement
+ * products with >= 64 rows and >= 16 inner columns run on the tensor cores (tcgen05
+ * kind::tf32) with each operand split into two TF32 parts (hi*hi + hi*lo + lo*hi), which
+ * keeps FP32 accuracy; LS_FRONT_FP32: every product on the CUDA cores.  Single-TF32 and BF16
+ * fronts (LS_FRONT_TF32, LS_FRONT_BF16) are not built: their 1e-3 / 1e-2 relative error
+ * would loosen the preconditioner that the iteration counts rely on; setup returns
+ * LS_EINVAL for them. */
+typedef enum { LS_FRONT_3XTF32 = 0, LS_FRONT_FP32 = 1, LS_FRONT_TF32 = 2, LS_FRONT_BF16 = 3 } ls_front_fmt;
 
 typedef struct ls_ctx ls_ctx; /* opaque */
 
@@ -90,7 +102,8 @@ typedef struct {
  * 3^d stencils alpha (eqs. Fmin, Emin, Cmin; the centre coefficient made real positive) and
  * C = alpha K(mu, mu), and the nested-dissection structure.  Tables that depend only on
  * (d, n, omega, b, k0_rule) are cached inside the library and reused by later contexts.
- *   g       grid description (copied); an unknown prec or k0_rule gives LS_EINVAL.
+ *   g       grid description (copied); an unknown prec, k0_rule or front_fmt, or a front
+ *           format that is not built, gives LS_EINVAL.
  *   omega   angular frequency, > 0.
  *   m       n^d real doubles, C order: the medium m(x_i) (index of refraction 1 - m).  Host or
  *           device pointer; copied.  Must vanish on the b+1 outermost layers (else LS_EBUFFER)

@@ -556,6 +556,9 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     if (n <= 2 * (b + 1)) throw Error{ls::EINVAL_, "n too small for the buffer layers"};
     if (g->prec != LS_PREC_FP64 && g->prec != LS_PREC_MIXED) throw Error{ls::EINVAL_, "unknown precision"};
     if (g->k0_rule != LS_K0_BALL && g->k0_rule != LS_K0_CORRECTED) throw Error{ls::EINVAL_, "unknown k0_rule"};
+    if (g->front_fmt == LS_FRONT_TF32 || g->front_fmt == LS_FRONT_BF16)
+      throw Error{ls::EINVAL_, "TF32 and BF16 fronts are not built (LS_FRONT_3XTF32 or LS_FRONT_FP32)"};
+    if (g->front_fmt != LS_FRONT_3XTF32 && g->front_fmt != LS_FRONT_FP32) throw Error{ls::EINVAL_, "unknown front_fmt"};
     c = new ls_ctx;
     c->g = *g;
     c->d = g->dim;
@@ -677,6 +680,7 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     LS_CUDA(cudaMemcpyAsync(c->cint64, c->cint_h.data(), c->cint_h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
     // nested-dissection structure (Sec. 3.2)
     c->nd = ls::nd_build(c->d, n, c->st);
+    ls::nd_set_tensor_cores(c->nd, g->front_fmt == LS_FRONT_3XTF32);
     LS_CUDA(cudaStreamSynchronize(c->st));
     *out = c;
     return LS_OK;

@@ -132,6 +132,8 @@ template <typename C>
 void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const void* w2m_T, cudaStream_t st,
                       cudaEvent_t top_levels, const void* alpha_pt = nullptr, const unsigned char* inter_pt = nullptr);
 void nd_factor_check(NdPlan* p, cudaStream_t st);
+// FP32 Schur-complement products on the tensor cores (3xTF32, the default) or on the CUDA cores
+void nd_set_tensor_cores(NdPlan* p, bool on);
 // x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);
 size_t nd_device_bytes(const NdPlan* p, int elem_bytes);

@@ -95,6 +95,7 @@ struct NdPlan {
   size_t part_elems = 0;
   unsigned* cnt = nullptr;  // solve: per-item arrival counters
   int* d_err = nullptr;
+  bool use_tc = true;  // FP32 Schur products on the tensor cores (3xTF32) where they qualify
   void* blob = nullptr;  // every index array of the plan, one device allocation
   NdInfo info{};
 };
@@ -1541,10 +1542,10 @@ template <typename C> static size_t gj_smem(int s, int nc) {
 constexpr int TC_MIN_ROWS = 64, TC_MIN_K = 16;
 
 template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
-                                              cudaStream_t st, int* err) {
+                                              cudaStream_t st, int* err, bool tc) {
   if (r1 <= r0 || c1 <= c0 || k1 <= k0) return;
   if constexpr (sizeof(C) == 8) {
-    if (r1 - r0 >= TC_MIN_ROWS && k1 - k0 >= TC_MIN_K && tc_enabled()) {
+    if (tc && r1 - r0 >= TC_MIN_ROWS && k1 - k0 >= TC_MIN_K && tc_enabled()) {
       tc_cgemm(reinterpret_cast<float2*>(L.F), (long)L.fmax * L.ncols, L.fmax, L.nf, r0, r1, c0, c1, k0, k1, err, st);
       return;
     }
@@ -1555,6 +1556,8 @@ template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1
 }
 
 template <typename C> bool nd_prepare(NdPlan* p, cudaStream_t st) { return ensure_buffers(p, sizeof(C), st); }
+
+void nd_set_tensor_cores(NdPlan* p, bool on) { p->use_tc = on; }
 
 // own rows per lane of the register sweeps (32 * this many own rows at most)
 template <typename C> constexpr int reg_rpl_max() { return sizeof(C) == 8 ? 16 : 8; }
@@ -1663,7 +1666,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
                 k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, fused_ea ? 1 : 0,
                                                                                    p->d_err));
-      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err);
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, p->use_tc);
       continue;
     }
     // The register sweeps update every trailing column on CUDA cores from a panel staged per
@@ -1701,7 +1704,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
                         k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
-            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
+            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
           }
           continue;
         }
@@ -1736,7 +1739,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (L.ncols - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1,
                                                                                                  L.ncols, rec));
-            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err);
+            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
             continue;
           }
           // the block's earlier L columns follow this panel's permutation
@@ -1748,7 +1751,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
           if (k1 < K1) {
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (K1 - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1, K1, rec));
-            launch_gemm<C>(L, k1, L.smax, k1, K1, k0, k1, st, p->d_err);
+            launch_gemm<C>(L, k1, L.smax, k1, K1, k0, k1, st, p->d_err, p->use_tc);
           }
         }
         if (two && K1 < L.ncols) {
@@ -1761,9 +1764,9 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1, K1, L.ncols,
                                                                                        (const int*)nullptr));
-            launch_gemm<C>(L, k1, K1, K1, L.ncols, k0, k1, st, p->d_err);
+            launch_gemm<C>(L, k1, K1, K1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
           }
-          launch_gemm<C>(L, K1, L.smax, K1, L.ncols, K0, K1, st, p->d_err);
+          launch_gemm<C>(L, K1, L.smax, K1, L.ncols, K0, K1, st, p->d_err, p->use_tc);
         }
       }
       // sweep 2: backward substitution with U11 on the own rows of [F12 | I], in outer
@@ -1777,13 +1780,13 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
           const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
           LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                     k_trsm_upper<C><<<dim3(L.nf, (m2 + 127) / 128), 128, 0, st>>>(L, j0, j1));
-          launch_gemm<C>(L, J0, j0, L.smax, L.ncols, j0, j1, st, p->d_err);
+          launch_gemm<C>(L, J0, j0, L.smax, L.ncols, j0, j1, st, p->d_err, p->use_tc);
         }
-        launch_gemm<C>(L, 0, J0, L.smax, L.ncols, J0, J1, st, p->d_err);
+        launch_gemm<C>(L, 0, J0, L.smax, L.ncols, J0, J1, st, p->d_err, p->use_tc);
       }
     }
     // ring rows: [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
-    launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err);
+    launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, p->use_tc);
   }
   if (!marked) record_marker(top_levels, st);
   prof_tag(-1);

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libls.so")
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ENOCONV, LS_ESTATE, LS_ETIMEOUT, LS_EBUFFER = range(8)
 LS_PREC_FP64, LS_PREC_MIXED, LS_PREC_FF = 0, 1, 2
 LS_K0_BALL, LS_K0_CORRECTED = 0, 1
+LS_FRONT_3XTF32, LS_FRONT_FP32, LS_FRONT_TF32, LS_FRONT_BF16 = 0, 1, 2, 3
 STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS_ESTATE", "LS_ETIMEOUT", "LS_EBUFFER"]
 
 # every entry point declared in include/ls.h
@@ -37,7 +38,7 @@ EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls
 class LsGrid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("buffer_b", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
-                ("k0_rule", ctypes.c_int)]
+                ("k0_rule", ctypes.c_int), ("front_fmt", ctypes.c_int)]
 
 
 class LsInfo(ctypes.Structure):
@@ -214,11 +215,12 @@ class Solver:
 
     ``laplace=True`` selects the Laplace variant (``ls_setup_laplace``, Sec. 5): ``m`` is then
     the potential V and ``omega`` is ignored.  ``k0_rule`` picks the weight of the singular
-    point (``LS_K0_BALL`` or ``LS_K0_CORRECTED``, Sec. 2.1)."""
+    point (``LS_K0_BALL`` or ``LS_K0_CORRECTED``, Sec. 2.1); ``front_fmt`` the arithmetic of the
+    fronts' Schur products on the mixed path (``LS_FRONT_3XTF32`` or ``LS_FRONT_FP32``)."""
 
     def __init__(self, m, omega: float = 0.0, dim: int | None = None, buffer_b: int = 2, restart: int = 50,
                  max_iter: int = 500, mixed: bool = True, stream=None, laplace: bool = False,
-                 k0_rule: int = LS_K0_BALL):
+                 k0_rule: int = LS_K0_BALL, front_fmt: int = LS_FRONT_3XTF32):
         self.lib = load()
         if isinstance(m, np.ndarray):
             m = np.ascontiguousarray(m, dtype=np.float64)
@@ -230,7 +232,7 @@ class Solver:
         self.mixed = mixed
         self.k0_rule = k0_rule
         g = LsGrid(self.d, self.n, buffer_b, restart, max_iter, LS_PREC_MIXED if mixed else LS_PREC_FP64,
-                   k0_rule)
+                   k0_rule, front_fmt)
         h = ctypes.c_void_p()
         if laplace:
             st = self.lib.ls_setup_laplace(ctypes.byref(g), _ptr(m), _stream_ptr(stream), ctypes.byref(h))

@@ -35,9 +35,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_structs_match_header_sizes():
-    # ls_grid: 7 ints; ls_info: int, int, double, int (padded to 24);
+    # ls_grid: 8 ints; ls_info: int, int, double, int (padded to 24);
     # ls_nd_stats: 3 ints (+pad) + int64 + 6 doubles
-    assert ctypes.sizeof(LS.LsGrid) == 28
+    assert ctypes.sizeof(LS.LsGrid) == 32
     assert ctypes.sizeof(LS.LsInfo) == 24
     assert ctypes.sizeof(LS.LsNdStats) == 72
 
