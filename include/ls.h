@@ -32,6 +32,7 @@
 #ifndef LS_H_
 #define LS_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -150,6 +151,21 @@ ls_status ls_factor(ls_ctx* c);
  * preconditioner (ls_general_setup must run again).
  */
 ls_status ls_set_medium(ls_ctx* c, const double* m);
+/*
+ * ls_export_factors / ls_import_factors -- checkpoint of a factorization, e.g. a serving
+ * cache spilled to host memory.  The blob is a 64-byte header (grid, b, precision, k0_rule,
+ * front_fmt, kernel, omega, a 64-bit hash of the FP64 potential) followed by the factored
+ * fronts, the whole state the solves read.
+ *   ls_export_factors: *size receives the blob's size; with out != NULL and capacity >= *size
+ *     the blob is written to out (host array).  LS_ESTATE before ls_factor (or for a
+ *     general-domain context), LS_EINVAL for a short capacity or a device pointer; reports
+ *     the errors of a factorization still in flight.
+ *   ls_import_factors: in (host array, size bytes) must come from a context with the same
+ *     grid, b, precision, k0_rule, front_fmt, kernel, omega and medium (LS_EINVAL otherwise);
+ *     the context is then factored, as if ls_factor had run, without repeating the work.
+ */
+ls_status ls_export_factors(ls_ctx* c, void* out, size_t capacity, size_t* size);
+ls_status ls_import_factors(ls_ctx* c, const void* in, size_t size);
 
 /*
  * ls_rhs_plane_wave -- Sec. 1 eq. ls, Sec. 2.1 eq. lsd: g = K(-omega^2 m u_I) with the

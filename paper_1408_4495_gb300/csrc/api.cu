@@ -91,6 +91,7 @@ struct ls_ctx {
   void** dZ = nullptr;
   ls::ConvPlan plan{};
   uint64_t gen = 1;  // bumped whenever a device buffer is (re)allocated
+  uint64_t medium_hash = 0;  // FNV-1a of the FP64 potential, the identity of exported factors
   bool use_graphs = true;
   std::map<std::string, GraphEntry> graphs;
 };
@@ -503,6 +504,17 @@ bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 // =======================================================================================
 // C-ABI
 // =======================================================================================
+// FNV-1a (64 bit) of a byte array
+static uint64_t fnv1a(const void* data, size_t bytes) {
+  const unsigned char* q = static_cast<const unsigned char*>(data);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= q[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
 // Medium of a context (Sec. 2.1): the host copy of m (host or device pointer) is checked --
 // finite, 1 - m > 0 (Helmholtz), zero within b + 1 layers of the boundary -- and turned into
 // the potential omega^2 m (V itself for a Laplace context) in FP64 and FP32.
@@ -584,6 +596,7 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     std::vector<double> w64;
     std::vector<float> w32;
     medium_weights(c, m, w64, w32);
+    c->medium_hash = fnv1a(w64.data(), w64.size() * sizeof(double));
     c->w2m64 = dalloc<double>(c->N);
     c->w2m32 = dalloc<float>(c->N);
     LS_CUDA(cudaMemcpyAsync(c->w2m64, w64.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, c->st));
@@ -939,6 +952,7 @@ ls_status ls_set_medium(ls_ctx* c, const double* m) {
     std::vector<float> w32;
     medium_weights(c, m, w64, w32);
     LS_CUDA(cudaStreamSynchronize(c->st));  // nothing in flight reads the old tables
+    c->medium_hash = fnv1a(w64.data(), w64.size() * sizeof(double));
     c->factor_pending = false;
     c->factored = false;
     if (c->general) {
@@ -957,6 +971,83 @@ ls_status ls_set_medium(ls_ctx* c, const double* m) {
     return fail(c, e);
   } catch (const std::bad_alloc&) {
     return fail(c, Error{ls::ENOMEM_, "host allocation failed"});
+  }
+}
+
+// Checkpoint of a factorization (the serving cache spilled to host memory): a header that
+// identifies grid, frequency, kernel, formats and medium, then the factored fronts.
+struct FactorHeader {
+  char magic[8];
+  int32_t d, n, b, prec, k0_rule, front_fmt, laplace, reserved;
+  double omega;
+  uint64_t medium_hash, bytes;
+};
+static const char FACTOR_MAGIC[8] = {'L', 'S', 'F', 'A', 'C', 'T', '1', '\0'};
+
+static FactorHeader factor_header(const ls_ctx* c) {
+  FactorHeader h{};
+  std::memcpy(h.magic, FACTOR_MAGIC, sizeof h.magic);
+  h.d = c->d;
+  h.n = c->n;
+  h.b = c->b;
+  h.prec = (int32_t)c->prec;
+  h.k0_rule = c->g.k0_rule;
+  h.front_fmt = c->g.front_fmt;
+  h.laplace = c->laplace ? 1 : 0;
+  h.omega = c->omega;
+  h.medium_hash = c->medium_hash;
+  h.bytes = ls::nd_factor_bytes(c->nd);
+  return h;
+}
+
+ls_status ls_export_factors(ls_ctx* c, void* out, size_t capacity, size_t* size) {
+  try {
+    check_ctx(c);
+    if (!size) throw Error{ls::EINVAL_, "NULL size"};
+    if (!c->factored) throw Error{ls::ESTATE_, "no factorization to export"};
+    if (c->general) throw Error{ls::ESTATE_, "general-domain factorizations are not exported"};
+    factor_wait(c);
+    const FactorHeader h = factor_header(c);
+    *size = sizeof(FactorHeader) + h.bytes;
+    if (!out) return LS_OK;
+    if (capacity < *size) throw Error{ls::EINVAL_, "capacity below the exported size"};
+    if (is_device_ptr(out)) throw Error{ls::EINVAL_, "out is a host array"};
+    std::memcpy(out, &h, sizeof h);
+    ls::nd_copy_factors(c->nd, static_cast<unsigned char*>(out) + sizeof h, true, c->st);
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_import_factors(ls_ctx* c, const void* in, size_t size) {
+  try {
+    check_ctx(c);
+    if (!in || size < sizeof(FactorHeader)) throw Error{ls::EINVAL_, "bad arguments"};
+    if (is_device_ptr(in)) throw Error{ls::EINVAL_, "in is a host array"};
+    if (c->general) throw Error{ls::ESTATE_, "general-domain factorizations are not imported"};
+    FactorHeader h;
+    std::memcpy(&h, in, sizeof h);
+    if (std::memcmp(h.magic, FACTOR_MAGIC, sizeof h.magic) != 0)
+      throw Error{ls::EINVAL_, "not an exported factorization"};
+    const FactorHeader mine = factor_header(c);
+    if (h.d != mine.d || h.n != mine.n || h.b != mine.b || h.prec != mine.prec || h.k0_rule != mine.k0_rule ||
+        h.front_fmt != mine.front_fmt || h.laplace != mine.laplace || h.omega != mine.omega)
+      throw Error{ls::EINVAL_, "factorization of another grid, frequency, kernel or format"};
+    if (h.medium_hash != mine.medium_hash) throw Error{ls::EINVAL_, "factorization of another medium"};
+    LS_CUDA(cudaStreamSynchronize(c->st));
+    c->factored = false;
+    c->factor_pending = false;
+    const bool mixed = c->prec == LS_PREC_MIXED;
+    if (mixed ? ls::nd_prepare<float2>(c->nd, c->st) : ls::nd_prepare<double2>(c->nd, c->st)) ++c->gen;
+    if (h.bytes != ls::nd_factor_bytes(c->nd) || size < sizeof h + h.bytes)
+      throw Error{ls::EINVAL_, "size of the exported factorization does not match"};
+    ls::nd_copy_factors(c->nd, const_cast<unsigned char*>(static_cast<const unsigned char*>(in)) + sizeof h, false,
+                        c->st);
+    c->factored = true;
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
   }
 }
 

@@ -137,5 +137,9 @@ void nd_set_tensor_cores(NdPlan* p, bool on);
 // x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);
 size_t nd_device_bytes(const NdPlan* p, int elem_bytes);
+// bytes of the factored fronts (the factorization's whole state), and their copy to / from a
+// host array of that size (synchronous on st)
+size_t nd_factor_bytes(const NdPlan* p);
+void nd_copy_factors(NdPlan* p, void* host, bool to_host, cudaStream_t st);
 
 }  // namespace ls

@@ -473,6 +473,19 @@ size_t nd_device_bytes(const NdPlan* p, int elem_bytes) {
   return (p->F_elems + p->W_elems + (size_t)p->N * SOLVE_CHUNK) * (size_t)elem_bytes;
 }
 
+// The factorization's whole state is the front storage F: the solve reads the factored
+// fronts and the static index arrays only (the panel pivots are consumed inside the
+// factorization).  0 when F is not allocated.
+size_t nd_factor_bytes(const NdPlan* p) { return p->F ? p->F_elems * (size_t)p->F_bytes : 0; }
+
+void nd_copy_factors(NdPlan* p, void* host, bool to_host, cudaStream_t st) {
+  const size_t bytes = nd_factor_bytes(p);
+  if (!bytes) LS_FAIL(ESTATE_, "front storage not prepared");
+  if (to_host) LS_CUDA(cudaMemcpyAsync(host, p->F, bytes, cudaMemcpyDeviceToHost, st));
+  else LS_CUDA(cudaMemcpyAsync(p->F, host, bytes, cudaMemcpyHostToDevice, st));
+  LS_CUDA(cudaStreamSynchronize(st));
+}
+
 // ---------------------------------------------------------------------------------------
 // factorization kernels
 // ---------------------------------------------------------------------------------------

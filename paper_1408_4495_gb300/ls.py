@@ -30,6 +30,7 @@ STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ENOCONV", "LS
 EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls_rhs_point_source", "ls_solve",
            "ls_far_field", "ls_k0_weight", "ls_general_support", "ls_general_boundary_stencils",
            "ls_general_sketch", "ls_general_setup", "ls_general_rows", "ls_set_medium", "ls_fault_alloc",
+           "ls_export_factors", "ls_import_factors",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
            "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_setup.argtypes = [ctypes.POINTER(LsGrid), dp, vp, vp, ctypes.POINTER(vp)]
     lib.ls_factor.argtypes = [vp]
     lib.ls_set_medium.argtypes = [vp, vp]
+    lib.ls_export_factors.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    lib.ls_import_factors.argtypes = [vp, vp, ctypes.c_size_t]
     lib.ls_fault_alloc.argtypes = [ctypes.c_long]
     lib.ls_rhs_plane_wave.argtypes = [vp, ip, vp, vp]
     lib.ls_setup_laplace.argtypes = [ctypes.POINTER(LsGrid), vp, vp, ctypes.POINTER(vp)]
@@ -267,6 +270,19 @@ class Solver:
     # ---- the path
     def factor(self):
         self._check(self.lib.ls_factor(self.h))
+
+    def export_factors(self) -> np.ndarray:
+        """ls_export_factors: the factorization as a host byte array (header + fronts)."""
+        size = ctypes.c_size_t(0)
+        self._check(self.lib.ls_export_factors(self.h, None, 0, ctypes.byref(size)))
+        blob = np.empty(size.value, dtype=np.uint8)
+        self._check(self.lib.ls_export_factors(self.h, _ptr(blob), blob.size, ctypes.byref(size)))
+        return blob
+
+    def import_factors(self, blob: np.ndarray):
+        """ls_import_factors: a factorization exported by a context of the same grid and medium."""
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        self._check(self.lib.ls_import_factors(self.h, _ptr(blob), blob.size))
 
     def set_medium(self, m):
         """ls_set_medium: a new medium on this grid (drops the factorization)."""
