@@ -12,7 +12,10 @@ solved alone: contexts share no mutable state on the device.
 When memory must be freed for a new medium and an idle context of the same grid and
 frequency is resident, the engine gives that context the new medium (``retarget``:
 ls_set_medium, which keeps the stencils, the symbol, the nested-dissection structure and the
-buffers) instead of closing it and setting up a new one.
+buffers) instead of closing it and setting up a new one.  With ``host_cache_bytes`` the
+factorization of a context that leaves the device is kept in host memory
+(ls_export_factors, least recently used out) and imported when its medium returns, so that
+request skips the factorization.
 
 The engine itself is host logic (threads, a condition variable, the admission queue); the
 device work goes through a backend, ``LibBackend`` for libls.  Latency is arrival to result
@@ -94,6 +97,12 @@ class LibBackend:
     def retarget(self, ctx, req: Request):
         ctx.set_medium(req.m)
 
+    def export_factors(self, ctx):
+        return ctx.export_factors()
+
+    def import_factors(self, ctx, blob):
+        ctx.import_factors(blob)
+
     def solve(self, ctx, req: Request):
         g = ctx.rhs_plane_wave(np.ascontiguousarray(req.dirs, dtype=np.float64))
         u, info = ctx.solve(g, self.tol, raise_on_noconv=False)
@@ -107,11 +116,15 @@ class Engine:
     """Admission by free slot and device-memory budget, FIFO order, factor cache, concurrent
     execution on ``slots`` worker threads."""
 
-    def __init__(self, backend, slots: int = 4, budget_bytes: int = 16 << 30, keep_factors: bool = True):
+    def __init__(self, backend, slots: int = 4, budget_bytes: int = 16 << 30, keep_factors: bool = True,
+                 host_cache_bytes: int = 0):
         self.backend = backend
         self.slots = slots
         self.budget = budget_bytes
         self.keep = keep_factors
+        # second level of the factor cache: factorizations of evicted contexts kept in host
+        # memory (ls_export_factors) and imported when their medium comes back
+        self.host_cache = host_cache_bytes if hasattr(backend, "export_factors") else 0
 
     def run(self, requests, clock=time.perf_counter):
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
@@ -120,7 +133,10 @@ class Engine:
         cache = collections.OrderedDict()  # key -> [ctx, bytes, busy, factored, grid]
         jobs = collections.deque()
         results = {}
-        stats = {"max_used_bytes": 0, "max_concurrent": 0, "evictions": 0, "cache_hits": 0, "retargets": 0}
+        stats = {"max_used_bytes": 0, "max_concurrent": 0, "evictions": 0, "cache_hits": 0, "retargets": 0,
+                 "spills": 0, "host_hits": 0}
+        spill = collections.OrderedDict()  # key -> exported factorization (host bytes)
+        self._spill_store = spill
         state = {"used": 0, "running": 0, "done": 0, "stop": False}
         t0 = clock()
 
@@ -178,6 +194,7 @@ class Engine:
                                     # room must be made anyway: the idle context takes the medium
                                     del cache[cand[0]]
                                     state["used"] -= cand[1][1]
+                                    self._spill(cand[0], cand[1], stats)
                                     try:
                                         self.backend.retarget(cand[1][0], req)
                                     except Exception:
@@ -209,6 +226,14 @@ class Engine:
                             self.backend.close(ctx)
                             break  # wait for running requests to release memory
                         ent = [ctx, need, False, False, grid]
+                        blob = spill.pop(req.key, None)
+                        if blob is not None:
+                            try:
+                                self.backend.import_factors(ctx, blob)
+                                ent[3] = True
+                                stats["host_hits"] += 1
+                            except Exception:
+                                pass  # factored afresh by the worker
                         cache[req.key] = ent
                         state["used"] += need
                         stats["max_used_bytes"] = max(stats["max_used_bytes"], state["used"])
@@ -259,9 +284,27 @@ class Engine:
                 return key, ent
         return None
 
+    def _spill(self, key, ent, stats):
+        """Keeps the factorization of an idle context that leaves the device in host memory."""
+        if not self.host_cache or not ent[3]:
+            return
+        try:
+            blob = self.backend.export_factors(ent[0])
+        except Exception:
+            return
+        if len(blob) > self.host_cache:
+            return
+        spill = self._spill_store
+        spill[key] = blob
+        spill.move_to_end(key)
+        while sum(len(b) for b in spill.values()) > self.host_cache:
+            spill.popitem(last=False)
+        stats["spills"] += 1
+
     def _evict_one(self, cache, state, stats) -> bool:
         for key, ent in cache.items():  # least recently used first
             if not ent[2]:
+                self._spill(key, ent, stats)
                 self.backend.close(ent[0])
                 state["used"] -= ent[1]
                 del cache[key]

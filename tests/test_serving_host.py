@@ -185,3 +185,55 @@ def test_a_failed_retarget_is_reported_and_the_engine_keeps_serving():
     for q, r in zip(sorted(reqs, key=lambda q: q.arrival), res):
         if not r.error:
             assert np.array_equal(r.u, be.solve({"key": q.key}, q)[0])
+
+
+class SpillBackend(FakeBackend):
+    """Fake backend whose contexts can export and import their factorization."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.imported = 0
+
+    def open(self, req):
+        return {"key": req.key, "factored": False}
+
+    def factor(self, ctx):
+        super().factor(ctx)
+        ctx["factored"] = True
+
+    def export_factors(self, ctx):
+        assert ctx["factored"]
+        return ("blob:" + ctx["key"]).encode()
+
+    def import_factors(self, ctx, blob):
+        assert blob == ("blob:" + ctx["key"]).encode()  # the medium's own factorization
+        with self.lock:
+            self.imported += 1
+        ctx["factored"] = True
+
+    def solve(self, ctx, req):
+        assert ctx["factored"] and ctx["key"] == req.key
+        return super().solve(ctx, req)
+
+
+def test_evicted_factorizations_come_back_from_host_memory():
+    be = SpillBackend()
+    reqs = requests(40, 2000.0, pool=4)
+    budget = 32 * 32 * 1000  # one large medium at a time on the device
+    res, st = S.Engine(be, slots=2, budget_bytes=budget, host_cache_bytes=1 << 20).run(reqs)
+    assert st["errors"] == 0 and st["all_converged"] and st["max_used_bytes"] <= budget
+    assert st["spills"] > 0 and st["host_hits"] > 0 and be.imported == st["host_hits"]
+    # every request is a device hit, a host hit or a fresh factorization
+    assert be.factored + st["host_hits"] + st["cache_hits"] == len(reqs)
+    for q, r in zip(sorted(reqs, key=lambda q: q.arrival), res):
+        assert np.array_equal(r.u, be.solve({"key": q.key, "factored": True}, q)[0])
+
+
+def test_host_cache_is_bounded():
+    be = SpillBackend()
+    reqs = requests(40, 2000.0, pool=6)
+    blob = len(be.export_factors({"key": reqs[0].key, "factored": True}))
+    eng = S.Engine(be, slots=1, budget_bytes=32 * 32 * 1000, host_cache_bytes=2 * blob + 1)
+    res, st = eng.run(reqs)
+    assert st["errors"] == 0
+    assert sum(len(b) for b in eng._spill_store.values()) <= 2 * blob + 1
