@@ -122,52 +122,58 @@ def test_general_rows_refuse_inconsistent_flags(LS):
         LS.general_rows(mask, neg, bnd, a_int)
 
 
-def test_box_embedding_of_the_library_rows_gives_the_restricted_solution(LS):
+@pytest.mark.parametrize("d,n,freq,rho", [(2, 32, 4.0, 0.35), (3, 12, 1.0, 0.25)])
+def test_box_embedding_of_the_library_rows_gives_the_restricted_solution(LS, d, n, freq, rho):
     """The reading behind ls_general_setup, checked on the CPU with the library's own rows:
     M and [A;B] of the box built from ls_general_rows (identity off Omega), GMRES on the GPU machine
-    operator, compared with the oracle's restricted method: same solution on Omega, one more
-    iteration (the identity block of the block lower triangular preconditioned operator)."""
+    operator, compared with the oracle's restricted method: same solution on Omega, at most one
+    more iteration (the identity block of the block lower triangular preconditioned operator
+    raises the degree of its minimal polynomial by at most one)."""
+    import itertools
+
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
-    n, d, omega = 32, 2, 2 * math.pi * 4
-    m = W.cavity(n, d, "l2", rho=0.35)
+    omega = 2 * math.pi * freq
+    P3, shape = 3**d, (n,) * d
+    m = W.cavity(n, d, "l2", rho=rho)
     idx = O.general_support(m, 2)
-    R = np.random.default_rng(5).standard_normal((len(idx), 18))
+    R = np.random.default_rng(5).standard_normal((len(idx), 2 * P3))
     mask = LS.general_support(m, 2)
     alpha, bnd = LS.general_boundary_stencils(mask, _oracle_T(n, d, omega, m, R))
     sten, (mu0c, c) = O.all_stencils(n, d, omega, 2)
     code = lambda t: sum((t[x] + 1) * 3 ** (d - 1 - x) for x in range(d))
-    a_int = np.zeros(9, dtype=np.complex128)
-    for t, v in zip(*sten[(0, 0)]):
+    a_int = np.zeros(P3, dtype=np.complex128)
+    for t, v in zip(*sten[(0,) * d]):
         a_int[code(t)] = v
-    c_int = np.zeros(9, dtype=np.complex128)
+    c_int = np.zeros(P3, dtype=np.complex128)
     for t, v in zip(mu0c, c):
         c_int[code(t)] = v
     rows, inter = LS.general_rows(mask, alpha, bnd, a_int)
     w2m = (omega**2 * m).reshape(-1)
+    offs = [np.array(t) for t in itertools.product((-1, 0, 1), repeat=d)]
     ri, ci, mv, sv = [], [], [], []
-    for i in range(n * n):
-        x = np.array(np.unravel_index(i, (n, n)))
-        for t in range(9):
-            tv = np.array([t // 3 - 1, t % 3 - 1])
+    for i in range(n**d):
+        x = np.array(np.unravel_index(i, shape))
+        for t, tv in enumerate(offs):
             y = x + tv
             if np.any(y < 0) or np.any(y >= n):
                 continue
-            j = int(np.ravel_multi_index(tuple(y), (n, n)))
+            j = int(np.ravel_multi_index(tuple(y), shape))
             a = rows[i, t]
             v = a + (c_int[t] * w2m[j] if inter[i] else 0)
             if a != 0 or v != 0:
                 ri.append(i); ci.append(j); sv.append(a); mv.append(v)
-    M = sp.csc_matrix((mv, (ri, ci)), shape=(n * n, n * n))
-    S = sp.csr_matrix((sv, (ri, ci)), shape=(n * n, n * n))
+    M = sp.csc_matrix((mv, (ri, ci)), shape=(n**d, n**d))
+    S = sp.csr_matrix((sv, (ri, ci)), shape=(n**d, n**d))
     lu = spla.splu(M)
     kt = O.kernel_table(n, d, omega)
-    A = lambda v: O.apply_operator(kt, omega, m, v.reshape(n, n)).reshape(-1)
+    A = lambda v: O.apply_operator(kt, omega, m, v.reshape(shape)).reshape(-1)
     P = lambda v: lu.solve(S @ v)
-    ref = O.general_solve(n, d, omega, m, [(1.0, 0.0)], R, tol=1e-10)
-    ref6 = O.general_solve(n, d, omega, m, [(1.0, 0.0)], R, tol=1e-6)
-    g = O.rhs(kt, omega, m, (1.0, 0.0)).reshape(-1)
+    dr = (1.0, 0.0) if d == 2 else (0.0, 0.6, 0.8)
+    ref = O.general_solve(n, d, omega, m, [dr], R, tol=1e-10)
+    ref6 = O.general_solve(n, d, omega, m, [dr], R, tol=1e-6)
+    g = O.rhs(kt, omega, m, dr).reshape(-1)
     u, it, _ = O.gmres_right(A, P, g, 1e-10, 50, 500)
     _, it6, _ = O.gmres_right(A, P, g, 1e-6, 50, 500)
     assert np.linalg.norm(u[idx] - ref["u"][0]) < 1e-8 * np.linalg.norm(ref["u"][0])
-    assert it6 == ref6["iters"][0] + 1
+    assert ref6["iters"][0] <= it6 <= ref6["iters"][0] + 1

@@ -5,13 +5,13 @@ The library keeps the box: every point off the unknowns Omega gets the identity 
 and [A;B], so the preconditioner is diag(M_Omega^{-1} [A;B]_Omega, I), and the operator is
 the box's (m vanishes off Omega, so A = [[A_OO, 0], [A_xO, I]] in the order Omega, rest).
 The preconditioned operator is block lower triangular with an identity block, so GMRES on
-the box takes the restricted method's iterations plus one and its solution restricted to
-Omega is the restricted solution (checked with the oracle's pieces on the CPU for these
-cases: +1 iteration, agreement 1e-11 at tolerance 1e-10).
+the box takes at most one iteration more than the restricted method and its solution
+restricted to Omega is the restricted solution (checked with the oracle's pieces on the CPU
+for these cases: +1 iteration, agreement 1e-11 at tolerance 1e-10).
 
 Checks against the oracle's restricted method (general_stencils / general_solve, same R):
 the per-point stencil apply (FP64 to rounding, FP32 to 1e-6 relative), the preconditioner's
-backward error, and the solve (FP64: the oracle's iterations + 1, solution within 1e-8 of
+backward error, and the solve (FP64: the oracle's iterations or one more, solution within 1e-8 of
 the oracle solved to 1e-10; mixed: within +-2 of that count, true relative residual
 <= 1e-6, solution within 1e-5).  It runs after the established GPU tests (marker late).
 """
@@ -120,7 +120,7 @@ def test_general_solve_matches_the_restricted_oracle(LS, d, n, freq, norm, rho, 
             assert abs(info[j].iters - (ref6["iters"][j] + 1)) <= 2
             assert rel(u[j].reshape(-1)[idx], ref["u"][j]) < 1e-5
         else:
-            assert info[j].iters == ref6["iters"][j] + 1
+            assert ref6["iters"][j] <= info[j].iters <= ref6["iters"][j] + 1
             assert rel(u[j].reshape(-1)[idx], ref["u"][j]) < 1e-8
 
 
