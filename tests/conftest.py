@@ -16,6 +16,9 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(session, config, items):
     def key(item):
+        # the allocation-free entry point's file comes after everything else, late ones included
+        if os.path.basename(str(item.fspath)).startswith("test_zz_"):
+            return (2, 0)
         mk = item.get_closest_marker("late")
         if mk is None:
             return (0, 0)
