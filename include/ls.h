@@ -27,7 +27,9 @@
  *    call returns.  The context owns all device memory it allocates.
  *  - A context is not thread-safe; distinct contexts may be used from distinct threads.
  *  - Calls are synchronous with respect to the host: when a call returns, its outputs
- *    (host or device) are complete.
+ *    (host or device) are complete.  The one exception is ls_factor, which only enqueues the
+ *    factorization on the context's stream (see there); the calls that read the factors
+ *    (ls_solve, ls_precond, ls_export_factors) wait for it and report its errors.
  */
 #ifndef LS_H_
 #define LS_H_
@@ -93,7 +95,9 @@ typedef struct ls_ctx ls_ctx; /* opaque */
 typedef struct {
   int iters;        /* GMRES iterations (one preconditioner + one operator apply each) */
   int refinements;  /* number of FP64 residual evaluations after the first cycle */
-  double rel_resid; /* |g - (I + K omega^2 m) u| / |g| evaluated in FP64 at the end */
+  double rel_resid; /* |g - (I + K omega^2 m) u| / |g| at the end: FP64 storage and norms; the
+                       operator K inside it is the FP64 one under LS_PREC_FP64 and the
+                       float-float one (about 48 significant bits) under LS_PREC_MIXED */
   int converged;    /* 1 if rel_resid <= tol */
 } ls_info;
 
@@ -384,8 +388,10 @@ ls_status ls_profile_stop(char* report, int capacity);
  * while another component owns the device memory pool, loops in which cudaMalloc/cudaFree
  * would synchronise the device, or deployments that forbid allocation after start-up.
  *
- *   x, y   nrhs x n^d complex doubles (interleaved), DEVICE pointers of the current device,
- *          owned by the caller; host pointers are rejected with LS_EINVAL.
+ *   x, y   nrhs x n^d complex doubles (interleaved), DEVICE pointers owned by the caller, on
+ *          the device that was current when the context was set up; that device must be
+ *          current at the call.  Host pointers, arrays of another device and a call made with
+ *          another device current are rejected with LS_EINVAL.
  *
  * The FFT passes' intermediate buffer is a fixed 64 MiB array compiled into the library
  * (it occupies 64 MiB on every GPU that loads the library until the process exits).  One

@@ -58,6 +58,7 @@ struct ls_ctx {
   ls_prec prec = LS_PREC_MIXED;
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  int device = 0;  // the device current at setup: every device array of the context lives there
   std::string err;
   double* w2m64 = nullptr;
   float* w2m32 = nullptr;
@@ -584,6 +585,7 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     c->laplace = laplace;
     c->omega = laplace ? 0.0 : omega;
     c->h = 1.0 / (n + 1);
+    LS_CUDA(cudaGetDevice(&c->device));
     // LS_GRAPHS=0 runs every launch eagerly (for debugging and per-launch timing)
     if (const char* e = std::getenv("LS_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
     if (stream) c->st = (cudaStream_t)stream;
@@ -1011,7 +1013,7 @@ ls_status ls_export_factors(ls_ctx* c, void* out, size_t capacity, size_t* size)
     *size = sizeof(FactorHeader) + h.bytes;
     if (!out) return LS_OK;
     if (capacity < *size) throw Error{ls::EINVAL_, "capacity below the exported size"};
-    if (is_device_ptr(out)) throw Error{ls::EINVAL_, "out is a host array"};
+    if (is_device_ptr(out)) throw Error{ls::EINVAL_, "out must be a host array"};
     std::memcpy(out, &h, sizeof h);
     ls::nd_copy_factors(c->nd, static_cast<unsigned char*>(out) + sizeof h, true, c->st);
     return LS_OK;
@@ -1024,7 +1026,7 @@ ls_status ls_import_factors(ls_ctx* c, const void* in, size_t size) {
   try {
     check_ctx(c);
     if (!in || size < sizeof(FactorHeader)) throw Error{ls::EINVAL_, "bad arguments"};
-    if (is_device_ptr(in)) throw Error{ls::EINVAL_, "in is a host array"};
+    if (is_device_ptr(in)) throw Error{ls::EINVAL_, "in must be a host array"};
     if (c->general) throw Error{ls::ESTATE_, "general-domain factorizations are not imported"};
     FactorHeader h;
     std::memcpy(&h, in, sizeof h);
@@ -1035,13 +1037,15 @@ ls_status ls_import_factors(ls_ctx* c, const void* in, size_t size) {
         h.front_fmt != mine.front_fmt || h.laplace != mine.laplace || h.omega != mine.omega)
       throw Error{ls::EINVAL_, "factorization of another grid, frequency, kernel or format"};
     if (h.medium_hash != mine.medium_hash) throw Error{ls::EINVAL_, "factorization of another medium"};
+    // checked before anything is dropped: a refused import leaves an existing factorization
+    const size_t want = ls::nd_factor_elems(c->nd) * (c->prec == LS_PREC_MIXED ? sizeof(float2) : sizeof(double2));
+    if (h.bytes != want || size < sizeof h + h.bytes)
+      throw Error{ls::EINVAL_, "size of the exported factorization does not match"};
     LS_CUDA(cudaStreamSynchronize(c->st));
     c->factored = false;
     c->factor_pending = false;
     const bool mixed = c->prec == LS_PREC_MIXED;
     if (mixed ? ls::nd_prepare<float2>(c->nd, c->st) : ls::nd_prepare<double2>(c->nd, c->st)) ++c->gen;
-    if (h.bytes != ls::nd_factor_bytes(c->nd) || size < sizeof h + h.bytes)
-      throw Error{ls::EINVAL_, "size of the exported factorization does not match"};
     ls::nd_copy_factors(c->nd, const_cast<unsigned char*>(static_cast<const unsigned char*>(in)) + sizeof h, false,
                         c->st);
     c->factored = true;
@@ -1219,6 +1223,7 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out) {
 namespace ls {
 const ConvPlan* ctx_plan(const ls_ctx* c) { return &c->plan; }
 cudaStream_t ctx_stream(const ls_ctx* c) { return c->st; }
+int ctx_device(const ls_ctx* c) { return c->device; }
 void ctx_set_error(ls_ctx* c, const char* msg) { c->err = msg; }
 }  // namespace ls
 

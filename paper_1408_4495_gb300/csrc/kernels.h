@@ -140,6 +140,7 @@ size_t nd_device_bytes(const NdPlan* p, int elem_bytes);
 // bytes of the factored fronts (the factorization's whole state), and their copy to / from a
 // host array of that size (synchronous on st)
 size_t nd_factor_bytes(const NdPlan* p);
+size_t nd_factor_elems(const NdPlan* p);  // front entries, whether or not the storage exists yet
 void nd_copy_factors(NdPlan* p, void* host, bool to_host, cudaStream_t st);
 
 }  // namespace ls

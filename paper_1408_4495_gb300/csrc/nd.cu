@@ -477,6 +477,7 @@ size_t nd_device_bytes(const NdPlan* p, int elem_bytes) {
 // fronts and the static index arrays only (the panel pivots are consumed inside the
 // factorization).  0 when F is not allocated.
 size_t nd_factor_bytes(const NdPlan* p) { return p->F ? p->F_elems * (size_t)p->F_bytes : 0; }
+size_t nd_factor_elems(const NdPlan* p) { return p->F_elems; }
 
 void nd_copy_factors(NdPlan* p, void* host, bool to_host, cudaStream_t st) {
   const size_t bytes = nd_factor_bytes(p);

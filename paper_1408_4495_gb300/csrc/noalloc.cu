@@ -43,13 +43,14 @@ void* scratch_on_current_device() {
   return g_scratch_ptr[dev];
 }
 
-bool on_device(const void* p) {
+// True when p is device (or managed) memory that belongs to device dev.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -58,6 +59,7 @@ bool on_device(const void* p) {
 namespace ls {
 const ConvPlan* ctx_plan(const ls_ctx* c);
 cudaStream_t ctx_stream(const ls_ctx* c);
+int ctx_device(const ls_ctx* c);
 void ctx_set_error(ls_ctx* c, const char* msg);
 }  // namespace ls
 
@@ -66,7 +68,13 @@ extern "C" ls_status ls_apply_noalloc(ls_ctx* c, int nrhs, const double* x, doub
   try {
     const ls::ConvPlan* p = ls::ctx_plan(c);
     if (nrhs < 1 || !x || !y) LS_FAIL(ls::EINVAL_, "bad arguments");
-    if (!on_device(x) || !on_device(y)) LS_FAIL(ls::EINVAL_, "ls_apply_noalloc takes device arrays only");
+    int dev = -1;
+    LS_CUDA(cudaGetDevice(&dev));
+    if (dev != ls::ctx_device(c))
+      LS_FAIL(ls::EINVAL_, "ls_apply_noalloc: the current device (%d) is not the context's device (%d)", dev,
+              ls::ctx_device(c));
+    if (!on_device(x, dev) || !on_device(y, dev))
+      LS_FAIL(ls::EINVAL_, "ls_apply_noalloc takes device arrays of the context's device only");
     const size_t s1 = ls::conv_scratch1_elems(p->d, p->n, nrhs), s2 = ls::conv_scratch2_elems(p->d, p->n, nrhs);
     const size_t need = (s1 + s2) * sizeof(double2);
     if (need > kScratchBytes)

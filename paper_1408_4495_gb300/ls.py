@@ -414,7 +414,20 @@ class Solver:
 
     def apply_noalloc(self, x, out):
         """FP64 operator apply into a caller-provided device tensor, without any device
-        allocation inside the library (see ls_apply_noalloc in include/ls.h)."""
+        allocation inside the library (see ls_apply_noalloc in include/ls.h).  x and out must
+        be complex128 tensors of shape (nrhs,) + (n,) * d on one CUDA device; anything else is
+        refused here, before the library would read or write past the end of a buffer."""
+        for name, t in (("x", x), ("out", out)):
+            if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+                raise ValueError(f"{name} must be a CUDA tensor")
+            if str(t.dtype) != "torch.complex128":
+                raise ValueError(f"{name} must be complex128, got {t.dtype}")
+            if t.dim() != self.d + 1 or tuple(t.shape[1:]) != (self.n,) * self.d:
+                raise ValueError(f"{name} must have shape (nrhs,) + {(self.n,) * self.d}, got {tuple(t.shape)}")
+        if tuple(x.shape) != tuple(out.shape):
+            raise ValueError(f"x {tuple(x.shape)} and out {tuple(out.shape)} differ in shape")
+        if x.device != out.device:
+            raise ValueError(f"x ({x.device}) and out ({out.device}) are on different devices")
         self._check(self.lib.ls_apply_noalloc(self.h, int(x.shape[0]), _ptr(x), _ptr(out)))
         return out
 
