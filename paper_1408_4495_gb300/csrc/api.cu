@@ -346,7 +346,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       s[(size_t)j * (R + 1)] = act[j] ? rn[j] : 0.0;
     }
     LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    if (mixed) ls::scale_ff<double2>(r, (ffc*)c->V[0], sd, N, nrhs, c->st);
+    if (mixed) ls::scale_f<double2>(r, (float2*)c->V[0], sd, N, nrhs, c->st);
     else ls::scale(r, c->V[0], sd, N, nrhs, c->st);
     int k = 0;
     for (; k < R; ++k) {
@@ -367,15 +367,19 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
                        (mixed ? ":m" : ":d"),
                 [&] {
                   if (!compact) {
-                    if (mixed) precond_apply<CZ, ffc>(c, nrhs, (const ffc*)c->V[k], zk);
+                    if (mixed) precond_apply<CZ, float2>(c, nrhs, (const float2*)c->V[k], zk);
                     else precond_apply<CZ>(c, nrhs, c->V[k], zk);
                     if (mixed) op_apply<CZ>(c, nrhs, zk, wz);
                     else op_apply<double2>(c, nrhs, (const double2*)zk, w);
                     return;
                   }
-                  ls::rhs_gather<double2>(c->V[k], vlive, dlive, nlive, N, c->st);
-                  if (mixed) precond_apply<CZ, ffc>(c, nlive, (const ffc*)vlive, zlive);
-                  else precond_apply<CZ>(c, nlive, vlive, zlive);
+                  if (mixed) {
+                    ls::rhs_gather<float2>((const float2*)c->V[k], (float2*)vlive, dlive, nlive, N, c->st);
+                    precond_apply<CZ, float2>(c, nlive, (const float2*)vlive, zlive);
+                  } else {
+                    ls::rhs_gather<double2>(c->V[k], vlive, dlive, nlive, N, c->st);
+                    precond_apply<CZ>(c, nlive, vlive, zlive);
+                  }
                   LS_CUDA(cudaMemsetAsync(zk, 0, tot * sizeof(CZ), c->st));
                   ls::rhs_scatter<CZ>(zlive, zk, dlive, nlive, N, c->st);
                   if (mixed) {
@@ -392,15 +396,15 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       // CGS2 against V[0..k]
       double2* hd2 = hd + (size_t)nrhs * (R + 2);
       if (mixed) {
-        // the basis and w as FP32 pairs: every product on the FP32 pipes
-        const ffc* const* dVf = reinterpret_cast<const ffc* const*>(dV);
-        ffc* wf = reinterpret_cast<ffc*>(w);
+        // the basis and w stored as FP32 complex, every product and sum in float-float on
+        // the FP32 pipes; the second projection also gives |w|^2
+        const float2* const* dVf = reinterpret_cast<const float2* const*>(dV);
+        float2* wf = reinterpret_cast<float2*>(w);
         ffc* hff2 = hff + (size_t)nrhs * (R + 2);
-        ls::dots_ff<CZ>(dVf, k + 1, wz, N, nrhs, partial, hd, hff, R + 2, c->st);
-        ls::sub_proj_ff<CZ>(dVf, k + 1, wz, wf, hff, R + 2, N, nrhs, c->st);
-        ls::dots_ff<ffc>(dVf, k + 1, wf, N, nrhs, partial, hd2, hff2, R + 2, c->st);
-        ls::sub_proj_ff<ffc>(dVf, k + 1, wf, wf, hff2, R + 2, N, nrhs, c->st);
-        ls::norms2_ff(wf, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
+        ls::dots_f(dVf, k + 1, (const float2*)wz, N, nrhs, partial, hd, hff, R + 2, c->st);
+        ls::sub_proj_f(dVf, k + 1, (const float2*)wz, wf, hff, R + 2, N, nrhs, partial, nullptr, 0, c->st);
+        ls::dots_f(dVf, k + 1, wf, N, nrhs, partial, hd2, hff2, R + 2, c->st);
+        ls::sub_proj_f(dVf, k + 1, wf, wf, hff2, R + 2, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
       } else {
         ls::dots<double2>(dV, k + 1, w, N, nrhs, partial, hd, R + 2, false, c->st);
         ls::sub_proj<double2>(dV, k + 1, w, w, hd, R + 2, N, nrhs, c->st);
@@ -442,7 +446,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
         else sc[j] = 1.0 / beta;
       }
       LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
-      if (mixed) ls::scale_ff<ffc>((const ffc*)w, (ffc*)c->V[k + 1], sd, N, nrhs, c->st);
+      if (mixed) ls::scale_f<float2>((const float2*)w, (float2*)c->V[k + 1], sd, N, nrhs, c->st);
       else ls::scale(w, c->V[k + 1], sd, N, nrhs, c->st);
     }
     // least squares: H(0:k, 0:k) y = s(0:k), per right-hand side

@@ -223,51 +223,39 @@ template void rhs_gather<float2>(const float2*, float2*, const int*, int, long, 
 template void rhs_scatter<double2>(const double2*, double2*, const int*, int, long, cudaStream_t);
 template void rhs_scatter<float2>(const float2*, float2*, const int*, int, long, cudaStream_t);
 
-// ---- float-float variants for the mixed path: the Arnoldi basis and the projected vector
-// are kept as FP32 pairs (ffc, 16 bytes per complex like FP64), and every product and sum
-// runs on the FP32 pipes (GB300 issues FP32 at 64 times its FP64 rate).  Partial sums leave
-// the blocks as FP64 for the ordered cross-block reduction.
+// ---- mixed path: the Arnoldi basis and the projected vector are stored as FP32 complex
+// (float2: the precision of the FP32 preconditioner and operator that produce them), and
+// every dot product, projection, norm and scaling runs in float-float arithmetic on the FP32
+// pipes (GB300 issues FP32 at 64 times its FP64 rate).  Partial sums leave the blocks as
+// FP64 for the ordered cross-block reduction.
 
-__device__ __forceinline__ ffc ff_of(float2 v) {
+__device__ __forceinline__ ffc ffc_of(float2 v) {
   ffc r;
   r.x = ff(v.x, 0.f);
   r.y = ff(v.y, 0.f);
   return r;
 }
-__device__ __forceinline__ ffc ff_of(ffc v) { return v; }
-__device__ __forceinline__ ffc ldff(const ffc* p) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  ffc r;
-  r.x = ff(v.x, v.y);
-  r.y = ff(v.z, v.w);
-  return r;
-}
-__device__ __forceinline__ void stff(ffc* p, ffc v) {
-  *reinterpret_cast<float4*>(p) = make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
-}
-__device__ void store_ff_pair(void* outf, size_t i, double2 v) { stff(reinterpret_cast<ffc*>(outf) + i, ffc_from(v)); }
+__device__ __forceinline__ ffc ffc_of(double2 v) { return ffc_from(v); }
 
-template <typename Cw> __device__ __forceinline__ ffc ldw(const Cw* p) { return ff_of(*p); }
-template <> __device__ __forceinline__ ffc ldw<ffc>(const ffc* p) { return ldff(p); }
-
-// conj(a) * b
-__device__ __forceinline__ ffc ff_cconjmul(ffc a, ffc b) {
-  ffc r;
-  r.x = a.x * b.x + a.y * b.y;
-  r.y = a.x * b.y - a.y * b.x;
-  return r;
+// the exact product of two FP32 numbers as a float-float (FMA TwoProduct)
+__device__ __forceinline__ ff ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return ff(p, __fmaf_rn(a, b, -p));
 }
-__device__ __forceinline__ ffc ff_cmul(ffc a, ffc b) {
-  ffc r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
+// a * b for a float-float a and an FP32 b (relative error about 2 u^2)
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  const float s = __fadd_rn(p, e);
+  return ff(s, __fsub_rn(e, __fsub_rn(s, p)));
 }
+__device__ __forceinline__ float2 rnd(ffc v) { return make_float2(v.x.hi, v.y.hi); }
 __device__ __forceinline__ ff ff_shfl_down(ff v, int o) {
   return ff(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
 }
 
-// sum of v over the CTA in FP64 (thread 0); FP32-pair adds within warps
+// sum of v over the CTA in FP64 (thread 0); float-float adds within warps
 __device__ __forceinline__ double2 block_sum_ff(ffc v, double2* sh) {
   for (int o = 16; o > 0; o >>= 1) {
     v.x = v.x + ff_shfl_down(v.x, o);
@@ -283,77 +271,89 @@ __device__ __forceinline__ double2 block_sum_ff(ffc v, double2* sh) {
   return r;
 }
 
-template <typename Cw>
-__global__ void __launch_bounds__(KT) k_dots_ff(const ffc* const* __restrict__ V, int nv, const Cw* __restrict__ w,
-                                                long N, double2* __restrict__ partial, int nblk) {
+__device__ void store_ff_pair(void* outf, size_t i, double2 v) {
+  const ffc f = ffc_from(v);
+  *reinterpret_cast<float4*>(reinterpret_cast<ffc*>(outf) + i) = make_float4(f.x.hi, f.x.lo, f.y.hi, f.y.lo);
+}
+
+constexpr int JB = 4;  // basis vectors per pass over w
+
+// partial[(rhs * nv + j) * nblk + blk] = sum over the block's chunk of conj(V_j) w, JB
+// vectors per pass over the chunk
+__global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__ V, int nv, const float2* __restrict__ w,
+                                               long N, double2* __restrict__ partial, int nblk) {
   __shared__ double2 sh[KT / 32];
   const int rhs = blockIdx.y, blk = blockIdx.x;
   const long chunk = (N + nblk - 1) / nblk;
   const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
-  const Cw* wr = w + (size_t)rhs * N;
-  for (int j = 0; j < nv; ++j) {
-    const ffc* vr = V[j] + (size_t)rhs * N;
-    ffc acc;
-    acc.x = ff(0);
-    acc.y = ff(0);
-    for (long i = i0 + threadIdx.x; i < i1; i += KT) {
-      const ffc t = ff_cconjmul(ldff(vr + i), ldw(wr + i));
-      acc.x = acc.x + t.x;
-      acc.y = acc.y + t.y;
-    }
-    const double2 s = block_sum_ff(acc, sh);
-    if (threadIdx.x == 0) partial[((size_t)rhs * nv + j) * nblk + blk] = s;
-  }
-}
-
-// wout = win - sum_j V_j h[rhs][j]; one right-hand side per grid row, h as FP32 pairs
-template <typename Cw>
-__global__ void __launch_bounds__(256) k_sub_proj_ff(const ffc* const* __restrict__ V, int nv, const Cw* __restrict__ win,
-                                                     ffc* wout, const ffc* __restrict__ hf, int hstride, long N) {
-  const int rhs = blockIdx.y;
-  const ffc* hr = hf + (size_t)rhs * hstride;
   const size_t base = (size_t)rhs * N;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-    ffc acc = ldw(win + base + i);
-    for (int j = 0; j < nv; ++j) {
-      const ffc t = ff_cmul(ldff(V[j] + base + i), ldff(hr + j));
-      acc.x = acc.x - t.x;
-      acc.y = acc.y - t.y;
+  for (int jg = 0; jg < nv; jg += JB) {
+    const int nj = min(JB, nv - jg);
+    ffc acc[JB];
+#pragma unroll
+    for (int q = 0; q < JB; ++q) acc[q].x = acc[q].y = ff(0);
+    for (long i = i0 + threadIdx.x; i < i1; i += KT) {
+      const float2 b = w[base + i];
+#pragma unroll
+      for (int q = 0; q < JB; ++q)
+        if (q < nj) {
+          const float2 a = V[jg + q][base + i];
+          acc[q].x = acc[q].x + (ff_prod(a.x, b.x) + ff_prod(a.y, b.y));
+          acc[q].y = acc[q].y + (ff_prod(a.x, b.y) - ff_prod(a.y, b.x));
+        }
     }
-    stff(wout + base + i, acc);
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+      if (q < nj) {
+        const double2 s = block_sum_ff(acc[q], sh);
+        if (threadIdx.x == 0) partial[((size_t)rhs * nv + jg + q) * nblk + blk] = s;
+      }
   }
 }
 
-__global__ void __launch_bounds__(KT) k_norm2_ff(const ffc* __restrict__ w, long N, double2* partial, int nblk) {
+// wout = win - sum_j V_j h[rhs][j] (h as FP32 pairs), rounded to FP32; with NORM, also the
+// partial sums of |wout|^2 (as stored) in the layout of k_dots_f
+template <bool NORM>
+__global__ void __launch_bounds__(KT) k_sub_proj_f(const float2* const* __restrict__ V, int nv, const float2* win,
+                                                   float2* wout, const ffc* __restrict__ hf, int hstride, long N,
+                                                   double2* __restrict__ partial, int nblk) {
   __shared__ double2 sh[KT / 32];
   const int rhs = blockIdx.y, blk = blockIdx.x;
   const long chunk = (N + nblk - 1) / nblk;
   const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
-  const ffc* wr = w + (size_t)rhs * N;
-  ffc acc;
-  acc.x = ff(0);
-  acc.y = ff(0);
+  const size_t base = (size_t)rhs * N;
+  const ffc* hr = hf + (size_t)rhs * hstride;
+  ffc nacc;
+  nacc.x = nacc.y = ff(0);
   for (long i = i0 + threadIdx.x; i < i1; i += KT) {
-    const ffc v = ldff(wr + i);
-    acc.x = acc.x + (v.x * v.x + v.y * v.y);
+    ffc acc = ffc_of(win[base + i]);
+    for (int j = 0; j < nv; ++j) {
+      const float2 a = V[j][base + i];
+      const ffc h = hr[j];
+      acc.x = acc.x - (ff_mul_f(h.x, a.x) - ff_mul_f(h.y, a.y));
+      acc.y = acc.y - (ff_mul_f(h.y, a.x) + ff_mul_f(h.x, a.y));
+    }
+    const float2 o = rnd(acc);
+    wout[base + i] = o;
+    if (NORM) nacc.x = nacc.x + (ff_prod(o.x, o.x) + ff_prod(o.y, o.y));
   }
-  const double2 s = block_sum_ff(acc, sh);
-  if (threadIdx.x == 0) partial[(size_t)rhs * nblk + blk] = s;
+  if (NORM) {
+    const double2 s = block_sum_ff(nacc, sh);
+    if (threadIdx.x == 0) partial[(size_t)rhs * nblk + blk] = s;
+  }
 }
 
-// out[rhs] = in[rhs] * scale[rhs] as FP32 pairs; in FP64 (the residual) or FP32 pairs
+// out[rhs] = in[rhs] * scale[rhs] rounded to FP32; in FP64 (the residual) or FP32
 template <typename Cin>
-__global__ void k_scale_ff(const Cin* __restrict__ in, ffc* out, const double* __restrict__ scale, long N) {
+__global__ void k_scale_f(const Cin* __restrict__ in, float2* out, const double* __restrict__ scale, long N) {
   const int rhs = blockIdx.y;
   const ff s = ff_from(scale[rhs]);
   const size_t base = (size_t)rhs * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-    ffc v;
-    if constexpr (std::is_same<Cin, double2>::value) v = ffc_from(in[base + i]);
-    else v = ldff(in + base + i);
+    ffc v = ffc_of(in[base + i]);
     v.x = v.x * s;
     v.y = v.y * s;
-    stff(out + base + i, v);
+    out[base + i] = rnd(v);
   }
 }
 
@@ -364,37 +364,33 @@ static dim3 grid_rows(long N, int nrhs) {
   return dim3((unsigned)(b < 1 ? 1 : b), nrhs);
 }
 
-template <typename Cw>
-void dots_ff(const ffc* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, ffc* outf,
-             int ostride, cudaStream_t st) {
+void dots_f(const float2* const* V, int nv, const float2* w, long N, int nrhs, double2* partial, double2* out,
+            ffc* outf, int ostride, cudaStream_t st) {
   const int nblk = dots_blocks(N);
-  LS_LAUNCH("kr_dots", st, k_dots_ff<Cw><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk));
+  LS_LAUNCH("kr_dots", st, k_dots_f<<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, w, N, partial, nblk));
   LS_LAUNCH("kr_reduce", st,
             k_reduce<<<(nv * nrhs + 127) / 128, 128, 0, st>>>(partial, nv, nrhs, nblk, out, ostride, 0, outf));
 }
 
-template <typename Cw>
-void sub_proj_ff(const ffc* const* V, int nv, const Cw* win, ffc* wout, const ffc* hf, int hstride, long N, int nrhs,
-                 cudaStream_t st) {
-  LS_LAUNCH("kr_sub_proj", st, k_sub_proj_ff<Cw><<<grid_rows(N, nrhs), 256, 0, st>>>(V, nv, win, wout, hf, hstride, N));
-}
-
-void norms2_ff(const ffc* w, long N, int nrhs, double2* partial, double2* out, int ostride, cudaStream_t st) {
+void sub_proj_f(const float2* const* V, int nv, const float2* win, float2* wout, const ffc* hf, int hstride, long N,
+                int nrhs, double2* partial, double2* norm_out, int ostride, cudaStream_t st) {
   const int nblk = dots_blocks(N);
-  LS_LAUNCH("kr_norm2", st, k_norm2_ff<<<dim3(nblk, nrhs), KT, 0, st>>>(w, N, partial, nblk));
-  LS_LAUNCH("kr_reduce", st, k_reduce<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, 1, nrhs, nblk, out, ostride, 0));
+  if (norm_out) {
+    LS_LAUNCH("kr_sub_proj", st,
+              k_sub_proj_f<true><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, win, wout, hf, hstride, N, partial, nblk));
+    LS_LAUNCH("kr_reduce", st,
+              k_reduce<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, 1, nrhs, nblk, norm_out, ostride, 0));
+  } else {
+    LS_LAUNCH("kr_sub_proj", st,
+              k_sub_proj_f<false><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, win, wout, hf, hstride, N, partial, nblk));
+  }
 }
 
-template <typename Cin> void scale_ff(const Cin* in, ffc* out, const double* s, long N, int nrhs, cudaStream_t st) {
-  LS_LAUNCH("kr_scale", st, k_scale_ff<Cin><<<grid_rows(N, nrhs), 256, 0, st>>>(in, out, s, N));
+template <typename Cin> void scale_f(const Cin* in, float2* out, const double* s, long N, int nrhs, cudaStream_t st) {
+  LS_LAUNCH("kr_scale", st, k_scale_f<Cin><<<grid_rows(N, nrhs), 256, 0, st>>>(in, out, s, N));
 }
 
-template void dots_ff<float2>(const ffc* const*, int, const float2*, long, int, double2*, double2*, ffc*, int,
-                              cudaStream_t);
-template void dots_ff<ffc>(const ffc* const*, int, const ffc*, long, int, double2*, double2*, ffc*, int, cudaStream_t);
-template void sub_proj_ff<float2>(const ffc* const*, int, const float2*, ffc*, const ffc*, int, long, int, cudaStream_t);
-template void sub_proj_ff<ffc>(const ffc* const*, int, const ffc*, ffc*, const ffc*, int, long, int, cudaStream_t);
-template void scale_ff<double2>(const double2*, ffc*, const double*, long, int, cudaStream_t);
-template void scale_ff<ffc>(const ffc*, ffc*, const double*, long, int, cudaStream_t);
+template void scale_f<double2>(const double2*, float2*, const double*, long, int, cudaStream_t);
+template void scale_f<float2>(const float2*, float2*, const double*, long, int, cudaStream_t);
 
 }  // namespace ls

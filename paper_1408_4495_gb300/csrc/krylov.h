@@ -24,17 +24,15 @@ template <typename Cz>
 void update_u(const Cz* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs, cudaStream_t st);
 void residual(const double2* g, const double2* Au, double2* r, long tot, cudaStream_t st);
 template <typename Cin, typename Cout> void cast(const Cin* in, Cout* out, long tot, cudaStream_t st);
-// Float-float variants (mixed path): V and the projected vector as FP32 pairs (ffc).
-// dots_ff also writes the coefficients as FP32 pairs (outf, same indexing as out), which
-// sub_proj_ff reads.
-template <typename Cw>
-void dots_ff(const ffc* const* V, int nv, const Cw* w, long N, int nrhs, double2* partial, double2* out, ffc* outf,
-             int ostride, cudaStream_t st);
-template <typename Cw>
-void sub_proj_ff(const ffc* const* V, int nv, const Cw* win, ffc* wout, const ffc* hf, int hstride, long N, int nrhs,
-                 cudaStream_t st);
-void norms2_ff(const ffc* w, long N, int nrhs, double2* partial, double2* out, int ostride, cudaStream_t st);
-template <typename Cin> void scale_ff(const Cin* in, ffc* out, const double* s, long N, int nrhs, cudaStream_t st);
+// Mixed path: V and the projected vector stored as FP32 complex, arithmetic in float-float.
+// dots_f also writes the coefficients as FP32 pairs (outf, same indexing as out), which
+// sub_proj_f reads; sub_proj_f with norm_out != NULL also writes |wout|^2 to
+// norm_out[rhs * ostride].x.  win may equal wout.
+void dots_f(const float2* const* V, int nv, const float2* w, long N, int nrhs, double2* partial, double2* out,
+            ffc* outf, int ostride, cudaStream_t st);
+void sub_proj_f(const float2* const* V, int nv, const float2* win, float2* wout, const ffc* hf, int hstride, long N,
+                int nrhs, double2* partial, double2* norm_out, int ostride, cudaStream_t st);
+template <typename Cin> void scale_f(const Cin* in, float2* out, const double* s, long N, int nrhs, cudaStream_t st);
 // dst[i] = src[idx[i]] (gather) or dst[idx[i]] = src[i] (scatter) for i < n right-hand
 // sides of N entries each; idx on the device
 template <typename T> void rhs_gather(const T* src, T* dst, const int* idx, int n, long N, cudaStream_t st);

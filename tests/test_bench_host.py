@@ -24,6 +24,16 @@ def test_algorithmic_bytes_scale_with_the_right_hand_sides():
     assert bench.algorithmic_bytes("fft_row_fwd_c64", w, nd, None, None) == 16 * N * 8 * 3 + N * 4
     assert bench.algorithmic_bytes("fft_row_fwd_c64", w, nd, None, None, rhs=8) == 8 * N * 8 * 3 + N * 4
     assert bench.algorithmic_bytes("fft_col_sym_cff", w, nd, None, None) == 16 * 2 * (n * 2 * n) * 16 + (n + 1) ** 2 * 16
-    assert bench.algorithmic_bytes("nd_fwd_c64", w, nd, None, None, rhs=4) == (1e6 + 4 * 1e4) / 10
+    # sweeps: every factor block once + each live right-hand side's vector read and written once
+    assert bench.algorithmic_bytes("nd_fwd_c64", w, nd, None, None, rhs=4) == (1e6 + 4 * N * 8 * 2) / 10
+    assert bench.algorithmic_bytes("stencil_c64", w, nd, None, None, rhs=2) == 2 * N * 8 * 2
     assert "stencil_c64".startswith(bench.PER_ITERATION)
     assert not "fft_row_fwd_cff".startswith(bench.PER_ITERATION)
+    assert "fft_col_sym_cff" not in bench.HBM_CLASSES and "nd_bwd_c64" in bench.HBM_CLASSES
+
+
+def test_3d_pass_bytes():
+    w = W.bumps_3d(16, 2.0, 2, 4, 1)
+    N = 16**3
+    assert bench.algorithmic_bytes("fft_col_fwd_c64", w, {}, None, None) == 4 * N * 8 * 6
+    assert bench.algorithmic_bytes("fft_col_sym_c64", w, {}, None, None) == 4 * N * 8 * 8 + 17**3 * 8
