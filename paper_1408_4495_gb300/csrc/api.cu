@@ -9,6 +9,7 @@
 // convergence and restarts the next cycle (iterative refinement).  Under LS_PREC_FP64 the
 // same loop runs with FP64 everywhere.
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include <algorithm>
 #include <cmath>
@@ -94,6 +95,11 @@ struct ls_ctx {
   uint64_t gen = 1;  // bumped whenever a device buffer is (re)allocated
   uint64_t medium_hash = 0;  // FNV-1a of the FP64 potential, the identity of exported factors
   bool use_graphs = true;
+  // one step of iterative refinement inside each FP32 preconditioner application of the
+  // GMRES iterations: -1 = not yet known for this factorization (measured in its first
+  // iteration), 0 = off, 1 = on
+  int pre_refine = -1;
+  double pre_err = 0.0;  // |[A;B] v - M z| / |[A;B] v| of the first application after a factorization
   std::map<std::string, GraphEntry> graphs;
 };
 
@@ -274,6 +280,27 @@ template <typename C, typename Cv = double2> void precond_apply(ls_ctx* c, int n
     ls::stencil_apply<Cv, C>(c->d, c->n, nrhs, v, r, 1, c->N, alpha, c->st);
   }
   ls::nd_solve<C>(c->nd, nrhs, r, z, c->st);
+  if constexpr (sizeof(C) == 8 && std::is_same<Cv, float2>::value) {
+    if (c->pre_refine == 1 && !c->general) {
+      // one step of iterative refinement of z = M^{-1} [A;B] v with the FP32 factors:
+      // z += M^{-1} ([A;B] v - M z)
+      C* r2 = buf<C>(c, "pre_r2", (size_t)nrhs * c->N);
+      C* z2 = buf<C>(c, "pre_z2", (size_t)nrhs * c->N);
+      ls::pre_resid(c->d, c->n, nrhs, v, z, r2, c->alpha32, c->cint64, c->w2m32, c->st);
+      ls::nd_solve<C>(c->nd, nrhs, r2, z2, c->st);
+      ls::add_to(z, z2, (long)nrhs * c->N, c->st);
+    }
+  }
+}
+
+// |[A;B] v - M z|^2 and |[A;B] v|^2 of the first right-hand side of the last preconditioner
+// application (FP32 path), into out[0].x and out[1].x
+void precond_error(ls_ctx* c, const float2* v, const float2* z, double2* partial, double2* out) {
+  const float2* sv = buf<float2>(c, "pre_r32", (size_t)c->N);  // [A;B] v of that application
+  float2* r2 = buf<float2>(c, "pre_est", (size_t)c->N);
+  ls::pre_resid(c->d, c->n, 1, v, z, r2, c->alpha32, c->cint64, c->w2m32, c->st);
+  ls::norms2<float2>(r2, c->N, 1, partial, out, 1, c->st);
+  ls::norms2<float2>(sv, c->N, 1, partial, out + 1, 1, c->st);
 }
 
 ls_status fail(ls_ctx* c, const Error& e) {
@@ -288,6 +315,15 @@ void check_ctx(ls_ctx* c) {
 // ---------------------------------------------------------------------------------------
 // GMRES cycles (Sec. 3.3), batched over right-hand sides
 // ---------------------------------------------------------------------------------------
+// FP32 preconditioner residual |[A;B] v - M z| / |[A;B] v| above which every application is
+// refined once.  GMRES contracts the residual by about max(rho, e) per iteration (rho: the
+// rate of the exact preconditioner, e this residual), so e = 0.1 costs about twice the
+// iterations of e < 0.01, while a refined application (e^2) costs one more forward and
+// backward sweep (about a quarter of an iteration on the 2D workloads).  Measured on GB300:
+// 2D n = 1024, omega = 2 pi 128: 0.13 (6 iterations, 3-4 refined; FP64: 3); 2D n = 256 and
+// 3D n = 64 Helmholtz: 1e-5 (no refinement).
+constexpr double PRE_REFINE_ABOVE = 0.02;
+
 template <typename CZ>
 void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, ls_info* info) {
   const long N = c->N, tot = N * nrhs;
@@ -304,6 +340,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
   double* sd = buf<double>(c, "scale", nrhs);
   ffc* hff = mixed ? buf<ffc>(c, "h_ff", (size_t)nrhs * (R + 2) * 2) : nullptr;
   double2* yd = buf<double2>(c, "ycoef", (size_t)nrhs * R);
+  double2* est = mixed ? buf<double2>(c, "pre_err", 2) : nullptr;
 
   LS_CUDA(cudaMemsetAsync(u, 0, tot * sizeof(double2), c->st));
   std::vector<double2> hh((size_t)nrhs * (R + 2) * 2);
@@ -363,12 +400,18 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       if (compact) LS_CUDA(cudaMemcpyAsync(dlive, live_ix.data(), nlive * sizeof(int), cudaMemcpyHostToDevice, c->st));
       // z_k = P v_k (stencil + nested-dissection solve), w = A z_k (FFT operator), on the
       // live right-hand sides only
+      // the FP32 path measures its preconditioner's residual in the first iteration after a
+      // factorization and refines every later application when it is large (FGMRES allows
+      // the preconditioner to change from one iteration to the next)
+      const bool estimate = mixed && c->pre_refine < 0 && !c->general;
       run_graph(c, "iter:" + std::to_string(k) + ":" + std::to_string(nrhs) + ":" + std::to_string(nlive) +
-                       (mixed ? ":m" : ":d"),
+                       (mixed ? ":m" : ":d") + (estimate ? ":e" : (c->pre_refine == 1 ? ":r" : "")),
                 [&] {
                   if (!compact) {
                     if (mixed) precond_apply<CZ, float2>(c, nrhs, (const float2*)c->V[k], zk);
                     else precond_apply<CZ>(c, nrhs, c->V[k], zk);
+                    if constexpr (sizeof(CZ) == 8)
+                      if (estimate) precond_error(c, (const float2*)c->V[k], zk, partial, est);
                     if (mixed) op_apply<CZ>(c, nrhs, zk, wz);
                     else op_apply<double2>(c, nrhs, (const double2*)zk, w);
                     return;
@@ -376,6 +419,8 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
                   if (mixed) {
                     ls::rhs_gather<float2>((const float2*)c->V[k], (float2*)vlive, dlive, nlive, N, c->st);
                     precond_apply<CZ, float2>(c, nlive, (const float2*)vlive, zlive);
+                    if constexpr (sizeof(CZ) == 8)
+                      if (estimate) precond_error(c, (const float2*)vlive, zlive, partial, est);
                   } else {
                     ls::rhs_gather<double2>(c->V[k], vlive, dlive, nlive, N, c->st);
                     precond_apply<CZ>(c, nlive, vlive, zlive);
@@ -413,7 +458,13 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
         ls::norms2<double2>(w, N, nrhs, partial, hd2 + (k + 1), R + 2, c->st);
       }
       LS_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+      double2 est_h[2] = {};
+      if (estimate) LS_CUDA(cudaMemcpyAsync(est_h, est, sizeof est_h, cudaMemcpyDeviceToHost, c->st));
       LS_CUDA(cudaStreamSynchronize(c->st));
+      if (estimate) {
+        c->pre_err = est_h[1].x > 0 ? std::sqrt(est_h[0].x / est_h[1].x) : 0.0;
+        c->pre_refine = c->pre_err > PRE_REFINE_ABOVE ? 1 : 0;
+      }
       for (int j = 0; j < nrhs; ++j) {
         sc[j] = 0.0;
         if (!act[j] || kdone[j]) continue;
@@ -739,6 +790,7 @@ ls_status ls_factor(ls_ctx* c) {
     });
     c->factored = true;
     c->factor_pending = true;
+    c->pre_refine = -1;
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -1053,6 +1105,7 @@ ls_status ls_import_factors(ls_ctx* c, const void* in, size_t size) {
     ls::nd_copy_factors(c->nd, const_cast<unsigned char*>(static_cast<const unsigned char*>(in)) + sizeof h, false,
                         c->st);
     c->factored = true;
+    c->pre_refine = -1;
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);

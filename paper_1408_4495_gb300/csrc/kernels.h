@@ -104,6 +104,11 @@ void stencil_apply(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, lon
 template <typename Cin, typename Cout>
 void stencil_apply_pt(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, long rs_r, const void* alpha_pt,
                       cudaStream_t st);
+// r2 = [A;B] v - M z (FP32), the residual of a preconditioner application (class stencils)
+void pre_resid(int d, int n, int nrhs, const float2* v, const float2* z, float2* r2, const float2* alpha32,
+               const double2* cint64, const float* w2m32, cudaStream_t st);
+// z += dz
+void add_to(float2* z, const float2* dz, long tot, cudaStream_t st);
 
 // ---------------------------------------------------------------- nested dissection (nd.cu)
 struct NdPlan;  // opaque: host symbolic + device index arrays

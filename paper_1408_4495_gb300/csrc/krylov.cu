@@ -193,6 +193,7 @@ template void dots<double2>(const double2* const*, int, const double2*, long, in
 template void sub_proj<float2>(const double2* const*, int, const float2*, double2*, const double2*, int, long, int, cudaStream_t);
 template void sub_proj<double2>(const double2* const*, int, const double2*, double2*, const double2*, int, long, int, cudaStream_t);
 template void norms2<double2>(const double2*, long, int, double2*, double2*, int, cudaStream_t);
+template void norms2<float2>(const float2*, long, int, double2*, double2*, int, cudaStream_t);
 template void update_u<float2>(const float2* const*, int, const double2*, int, double2*, long, int, cudaStream_t);
 template void update_u<double2>(const double2* const*, int, const double2*, int, double2*, long, int, cudaStream_t);
 template void cast<double2, float2>(const double2*, float2*, long, cudaStream_t);

@@ -17,10 +17,16 @@
 //       [ F11  F12  I ]        own rows (s)
 //       [ F21  F22  0 ]        ring rows (b)
 // and eliminated in two sweeps:
-//   1. blocked right-looking LU of the own columns (pivot rows restricted to the own rows;
-//      panel / row-swap + unit-lower TRSM of the block row / GEMM of the trailing block),
-//      which leaves the Schur complement S = F22 - F21 F11^{-1} F12 in the ring block and
-//      Y = -F21 F11^{-1} in the ring rows of the identity columns;
+//   1. blocked right-looking partial LU of the whole front over the own columns (pivot rows
+//      restricted to the own rows; panel / row-swap + unit-lower TRSM of the block row / GEMM
+//      of the trailing block), the ring rows included: their panel entries become the
+//      multipliers L21 = F21 U11^{-1} (forward substitution with each panel's U block) and
+//      one GEMM with them leaves the Schur complement S = F22 - L21 U12 in the ring block and
+//      Y = -L21 L11^{-1} P = -F21 F11^{-1} in the ring rows of the identity columns -- the
+//      backward-stable LU form (forming them as F21 [H | F11^{-1}] from the explicit inverse
+//      amplifies rounding by cond(F11), which weakened the FP32 preconditioner on large
+//      fronts); the small fronts (up to 16 own rows) eliminate Gauss-Jordan style in shared
+//      memory and form [S | Y] from the inverse;
 //   2. blocked backward substitution with U11 on the own rows of [F12 I] (Gauss-Jordan),
 //      which leaves H = F11^{-1} F12 and F11^{-1} there.
 // S is extend-added into the parent.  The solve then needs no triangular recurrences:
@@ -778,6 +784,61 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
 #pragma unroll
   for (int i = 0; i < NB; ++i)
     if (i < w) col[j0 + i] = x[i];
+}
+
+// Ring rows r in [smax, fmax) of every front, panel columns [k0, k1): the multipliers
+// L21 = F21 U_kk^{-1}, by forward substitution along the panel with its upper triangle U_kk
+// (rows k0..k1 of the panel after the panel kernel; the ring rows are never permuted).  With
+// the ring rows also in the trailing updates, the forward elimination of the own columns is
+// the partial LU of the whole front, so the Schur complement S = F22 - L21 U12 and
+// Y = -L21 L11^{-1} P are formed backward stably (the product F21 [H | F11^{-1}] of the
+// explicit inverse would amplify rounding by cond(F11)).  One thread per ring row; U_kk and
+// its reciprocal pivots in shared memory.
+template <typename C> __global__ void __launch_bounds__(256) k_ring_trsm(LevelK<C> L, int k0, int k1) {
+  using Rl = typename RealOf<C>::T;
+  __shared__ C u[NB][NB + 1];  // u[j][i] = U_kk(i, j)
+  __shared__ C invd[NB];
+  const int z = blockIdx.x, w = k1 - k0, fmax = L.fmax;
+  C* A = L.F + (size_t)z * fmax * L.ncols;
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    const int i = e % w, j = e / w;
+    u[j][i] = A[(size_t)(k0 + j) * fmax + k0 + i];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+    const C dg = u[j][j];
+    const Rl den = cabs2(dg);
+    C inv;
+    inv.x = den > 0 ? dg.x / den : (Rl)0;
+    inv.y = den > 0 ? -dg.y / den : (Rl)0;
+    invd[j] = inv;
+  }
+  __syncthreads();
+  const int r = L.smax + blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= fmax) return;
+  C* row = A + (size_t)k0 * fmax + r;
+  C f[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) f[c] = c < w ? row[(size_t)c * fmax] : czero<C>();
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (c < w) {
+      C acc = f[c];
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < c) acc = cfms(acc, f[i], u[c][i]);
+      f[c] = cmul(acc, invd[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    if (c < w) row[(size_t)c * fmax] = f[c];
+}
+
+template <typename C> static void launch_ring_trsm(const LevelK<C>& L, int k0, int k1, cudaStream_t st) {
+  if (L.bmax <= 0) return;
+  LS_LAUNCH(sizeof(C) == 8 ? "nd_trsm_c64" : "nd_trsm_c128", st,
+            k_ring_trsm<C><<<dim3(L.nf, (L.bmax + 255) / 256), 256, 0, st>>>(L, k0, k1));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1576,7 +1637,8 @@ void nd_set_tensor_cores(NdPlan* p, bool on) { p->use_tc = on; }
 // own rows per lane of the register sweeps (32 * this many own rows at most)
 template <typename C> constexpr int reg_rpl_max() { return sizeof(C) == 8 ? 16 : 8; }
 
-template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* swp, int* err, cudaStream_t st) {
+template <typename C, int RPL>
+static void reg_sweeps(const LevelK<C>& L, int* swp, int* err, bool tc, cudaStream_t st) {
   const bool f32 = sizeof(C) == 8;
   const size_t smem_max = (size_t)32 * 32 * RPL * sizeof(C) + (size_t)32 * RPL * sizeof(int);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
@@ -1590,11 +1652,17 @@ template <typename C, int RPL> static void reg_sweeps(const LevelK<C>& L, int* s
     const int k1 = std::min(k0 + NB, L.smax), R = L.smax - k0;
     const int r32 = (R + 31) / 32 * 32;
     LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st, k_panel_reg<C><<<L.nf, r32, 0, st>>>(L, k0, k1, swp, err));
+    launch_ring_trsm<C>(L, k0, k1, st);
     const int m = L.ncols - k1;
     const size_t smem = (size_t)(k1 - k0) * r32 * sizeof(C) + (size_t)R * sizeof(int);
     LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
               k_lower_update<C, RPL><<<dim3(L.nf, (m + 7) / 8), 256, smem, st>>>(L, k0, k1, swp));
+    // the ring rows' own-column entries right of the panel (the later panels' multipliers)
+    launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, err, tc);
   }
+  // ring rows: [S | Y] = [F22 | 0] - L21 [U12 | L11^{-1} P], before sweep 2 overwrites the own
+  // rows of [F12 | I]
+  launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, err, tc);
   const int m = L.ncols - L.smax;
   const size_t smem = (size_t)32 * L.smax * sizeof(C);
   LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st, k_upper_solve<C, RPL><<<dim3(L.nf, (m + 7) / 8), 256, smem, st>>>(L));
@@ -1689,9 +1757,9 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     if (L.smax <= 32 * reg_rpl_max<C>() && L.ncols <= REG_MAX_COLS) {
       // both sweeps with the fronts' own rows in registers
       const int rpl = (L.smax + 31) / 32;
-      if (rpl <= 4) reg_sweeps<C, 4>(L, p->swp, p->d_err, st);
-      else if (rpl <= 8) reg_sweeps<C, 8>(L, p->swp, p->d_err, st);
-      else reg_sweeps<C, reg_rpl_max<C>()>(L, p->swp, p->d_err, st);
+      if (rpl <= 4) reg_sweeps<C, 4>(L, p->swp, p->d_err, p->use_tc, st);
+      else if (rpl <= 8) reg_sweeps<C, 8>(L, p->swp, p->d_err, p->use_tc, st);
+      else reg_sweeps<C, reg_rpl_max<C>()>(L, p->swp, p->d_err, p->use_tc, st);
     } else {
       // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
       // them), the block rows of [F12 | I] carried along.  Outer blocks of OB_PANELS panels:
@@ -1716,9 +1784,11 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             else
               LS_LAUNCH(f32 ? "nd_panel_c64" : "nd_panel_c128", st,
                         k_panel<C, false><<<L.nf, 512, 0, st>>>(L, k0, k1, p->d_err));
+            launch_ring_trsm<C>(L, k0, k1, st);
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
             launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, p->d_err, p->use_tc);
           }
           continue;
         }
@@ -1747,6 +1817,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             cfg.numAttrs = 1;
             LS_LAUNCH("nd_panel_c64", st, LS_CUDA(cudaLaunchKernelEx(&cfg, k_panel_cluster<C>, L, k0, k1, rec, p->d_err)));
           }
+          launch_ring_trsm<C>(L, k0, k1, st);
           if (!two) {
             // one level: permutation and forward substitution of every trailing column, then
             // the trailing GEMM with K = NB
@@ -1754,6 +1825,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
                       k_trsm_lower_swp<C><<<dim3(L.nf, (L.ncols - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1,
                                                                                                  L.ncols, rec));
             launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, p->d_err, p->use_tc);
             continue;
           }
           // the block's earlier L columns follow this panel's permutation
@@ -1765,7 +1837,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
           if (k1 < K1) {
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (K1 - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1, K1, rec));
-            launch_gemm<C>(L, k1, L.smax, k1, K1, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, k1, L.fmax, k1, K1, k0, k1, st, p->d_err, p->use_tc);
           }
         }
         if (two && K1 < L.ncols) {
@@ -1781,8 +1853,12 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             launch_gemm<C>(L, k1, K1, K1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
           }
           launch_gemm<C>(L, K1, L.smax, K1, L.ncols, K0, K1, st, p->d_err, p->use_tc);
+          launch_gemm<C>(L, L.smax, L.fmax, K1, L.smax, K0, K1, st, p->d_err, p->use_tc);
         }
       }
+      // ring rows: [S | Y] = [F22 | 0] - L21 [U12 | L11^{-1} P], before sweep 2 overwrites the
+      // own rows of [F12 | I]
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, p->use_tc);
       // sweep 2: backward substitution with U11 on the own rows of [F12 | I], in outer
       // blocks of OB_PANELS row blocks: inside a block each 32-row solve updates the block's
       // rows above it, then one GEMM with K = OB_PANELS * NB updates the rows above the block
@@ -1799,8 +1875,6 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
         launch_gemm<C>(L, 0, J0, L.smax, L.ncols, J0, J1, st, p->d_err, p->use_tc);
       }
     }
-    // ring rows: [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
-    launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, p->use_tc);
   }
   if (!marked) record_marker(top_levels, st);
   prof_tag(-1);

@@ -108,6 +108,83 @@ void stencil_apply_pt(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, 
     LS_LAUNCH(cls, st, k_stencil<Cin, Cout, 3, true><<<blocks, 256, 0, st>>>(n, nrhs, v, r, rs_i, rs_r, (const Cout*)alpha_pt));
 }
 
+// Residual of a preconditioner application, r2 = [A;B] v - M z with
+// M(i, i+t) = alpha_cls(i)(t) + c(t) omega^2 m_{i+t} (eq. PC; the c term vanishes on the
+// boundary rows because m is zero on the b+1 outermost layers):
+//   r2_i = sum_t alpha_cls(i)(t) (v - z)_{i+t} - sum_t c(t) (omega^2 m z)_{i+t}.
+// FP32; same line-wise thread layout as k_stencil.
+template <int D>
+__global__ void __launch_bounds__(256) k_pre_resid(int n, int nrhs, const float2* __restrict__ v,
+                                                   const float2* __restrict__ z, float2* __restrict__ r2,
+                                                   const float2* __restrict__ alpha, const double2* __restrict__ cint,
+                                                   const float* __restrict__ w2m) {
+  constexpr int P3 = D == 2 ? 9 : 27;
+  __shared__ float2 sa[P3 * P3];
+  __shared__ float2 sc[P3];
+  for (int i = threadIdx.x; i < P3 * P3; i += blockDim.x) sa[i] = alpha[i];
+  for (int i = threadIdx.x; i < P3; i += blockDim.x) sc[i] = make_float2((float)cint[i].x, (float)cint[i].y);
+  __syncthreads();
+  const int width = n < (int)blockDim.x ? n : (int)blockDim.x;
+  const int lpb = (int)blockDim.x / width;
+  const int sub = threadIdx.x / width, lane = threadIdx.x - sub * width;
+  if (sub >= lpb) return;
+  const long lines = (D == 2 ? (long)n : (long)n * n);
+  const long N = lines * n;
+  for (long line = (long)blockIdx.x * lpb + sub; line < lines * nrhs; line += (long)gridDim.x * lpb) {
+    const long rhs = line / lines, l = line - rhs * lines;
+    const int c0 = D == 2 ? (int)l : (int)(l / n);
+    const int c1 = D == 2 ? 0 : (int)(l - (long)c0 * n);
+    const int k0 = c0 == 0 ? 0 : (c0 == n - 1 ? 2 : 1);
+    const int k1 = c1 == 0 ? 0 : (c1 == n - 1 ? 2 : 1);
+    const float2* vr = v + rhs * N;
+    const float2* zr = z + rhs * N;
+    for (int c2 = lane; c2 < n; c2 += width) {
+      const int k2 = c2 == 0 ? 0 : (c2 == n - 1 ? 2 : 1);
+      const long i = l * n + c2;
+      float2 acc = make_float2(0.f, 0.f);
+      const int cls = D == 2 ? k0 * 3 + k2 : (k0 * 3 + k1) * 3 + k2;
+      const float2* al = sa + cls * P3;
+#pragma unroll
+      for (int t = 0; t < P3; ++t) {
+        const int t0 = D == 2 ? t / 3 - 1 : t / 9 - 1;
+        const int t1 = D == 2 ? 0 : (t / 3) % 3 - 1;
+        const int t2 = t % 3 - 1;
+        const int a0 = c0 + t0, a1 = c1 + t1, a2 = c2 + t2;
+        if (a0 < 0 || a0 >= n || a2 < 0 || a2 >= n || (D == 3 && (a1 < 0 || a1 >= n))) continue;
+        const long j = D == 2 ? (long)a0 * n + a2 : ((long)a0 * n + a1) * n + a2;
+        const float2 zv = __ldg(&zr[j]);
+        const float2 d = csub(__ldg(&vr[j]), zv);
+        acc = cfma(acc, al[t], d);
+        const float w = __ldg(&w2m[j]);
+        acc = cfms(acc, sc[t], make_float2(w * zv.x, w * zv.y));
+      }
+      r2[rhs * N + i] = acc;
+    }
+  }
+}
+
+__global__ void k_add_to(float2* __restrict__ z, const float2* __restrict__ dz, long tot) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    z[e] = cadd(z[e], dz[e]);
+}
+
+void pre_resid(int d, int n, int nrhs, const float2* v, const float2* z, float2* r2, const float2* alpha32,
+               const double2* cint64, const float* w2m32, cudaStream_t st) {
+  const unsigned blocks = stencil_blocks(d, n, nrhs);
+  if (blocks == 0) return;
+  if (d == 2)
+    LS_LAUNCH("stencil_c64", st, k_pre_resid<2><<<blocks, 256, 0, st>>>(n, nrhs, v, z, r2, alpha32, cint64, w2m32));
+  else
+    LS_LAUNCH("stencil_c64", st, k_pre_resid<3><<<blocks, 256, 0, st>>>(n, nrhs, v, z, r2, alpha32, cint64, w2m32));
+}
+
+void add_to(float2* z, const float2* dz, long tot, cudaStream_t st) {
+  long b = (tot + 255) / 256;
+  if (b > 152L * 32) b = 152L * 32;
+  if (b < 1) return;
+  LS_LAUNCH("kr_update_u", st, k_add_to<<<(unsigned)b, 256, 0, st>>>(z, dz, tot));
+}
+
 template void stencil_apply<float2, float2>(int, int, int, const float2*, float2*, long, long, const void*, cudaStream_t);
 template void stencil_apply<double2, float2>(int, int, int, const double2*, float2*, long, long, const void*, cudaStream_t);
 template void stencil_apply<double2, double2>(int, int, int, const double2*, double2*, long, long, const void*, cudaStream_t);
