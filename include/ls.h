@@ -65,8 +65,8 @@ typedef enum {
 
 typedef struct {
   int dim;       /* d: 2 or 3 */
-  int n;         /* points per dimension; 2n must be a power of two, 16 <= n <= 2048 (2D),
-                    8 <= n <= 128 (3D) */
+  int n;         /* points per dimension; 2n (the FFT length) must be a power of two, 48 or 96
+                    (n = 24, 48: radix-3 passes); 16 <= n <= 2048 (2D), 8 <= n <= 128 (3D) */
   int buffer_b;  /* b of Sec. 3.1: width (in grid steps) of the layer where m vanishes, >= 1;
                     0 selects the default 2 */
   int restart;   /* GMRES restart length; 0 selects 50 */
@@ -378,6 +378,29 @@ ls_status ls_get_nd_stats(ls_ctx* c, ls_nd_stats* out);
  * --------------------------------------------------------------------------------------- */
 ls_status ls_profile_start(const char* timed_class);
 ls_status ls_profile_stop(char* report, int capacity);
+
+/* ---------------------------------------------------------------------------------------
+ * Autotuner (the paper has no counterpart: launch shapes of this implementation).
+ *
+ * ls_autotune -- times, on this context's factorization and solve, the alternatives of the
+ * launch-shape choices that have no single best value across grids: the trailing-matrix size
+ * from which the blocked front LU updates in two levels, the smallest FP32 Schur product
+ * (rows) given to the tensor cores, the largest front factored Gauss-Jordan style in one CTA,
+ * and how many CTAs per SM the split of a solve sweep level aims at.  A coordinate search
+ * keeps each alternative that is more than 2 % faster (the fastest of 2 factorizations / 3
+ * solves of nrhs right-hand sides, CUDA events).  The choice is applied to c, kept for every
+ * later context of the same (dim, n, prec, kernel) in this process, and, when the
+ * environment variable LS_TUNE_FILE names a file, written there (one JSON object per line)
+ * and read back by the first ls_setup of a later process.  Leaves c factored (with the
+ * chosen shapes).  FFT radices (8, 4, 2, 3) and the right-hand-side batch widths (16 per
+ * item, 64 per launch) are fixed.
+ *   nrhs     right-hand sides of the timed solves, >= 1.
+ *   report   NUL-terminated JSON: the choice and every timing (truncated to capacity bytes;
+ *            may be NULL).
+ * ls_tune_info -- the context's current choices as a JSON object (no device work).
+ * --------------------------------------------------------------------------------------- */
+ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity);
+ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free operator apply (the paper has no counterpart: this is a deployment aid).

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <complex>
 #include <cstdlib>
 #include <cstring>
@@ -604,6 +605,84 @@ static void medium_weights(const ls_ctx* c, const double* m, std::vector<double>
 
 extern "C" {
 
+// ---------------------------------------------------------------------------------------
+// Autotuner: the launch-shape choices of the factorization and of the solve sweeps (ls::NdTune)
+// per (d, n, precision, kernel), timed on a context and kept process-wide; with LS_TUNE_FILE
+// set, the table is read from that file at the first setup and rewritten after each tuning.
+// ---------------------------------------------------------------------------------------
+struct TuneKey {
+  int d, n, prec, laplace;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(d, n, prec, laplace) < std::tie(o.d, o.n, o.prec, o.laplace);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, ls::NdTune> g_tune;
+static bool g_tune_loaded = false;
+
+static TuneKey tune_key(const ls_ctx* c) { return TuneKey{c->d, c->n, (int)c->prec, c->laplace ? 1 : 0}; }
+
+// one line per entry, the format tune_save writes
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("LS_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    TuneKey k{};
+    ls::NdTune t;
+    if (std::sscanf(line,
+                    "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %lf, "
+                    "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d}",
+                    &k.d, &k.n, &k.prec, &k.laplace, &t.two_level_min, &t.tc_min_rows, &t.sweep_ctas,
+                    &t.gj_max_own) == 8)
+      g_tune[k] = t;
+  }
+  std::fclose(f);
+}
+
+static void tune_save_locked() {
+  const char* path = std::getenv("LS_TUNE_FILE");
+  if (!path || !*path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  for (const auto& kv : g_tune)
+    std::fprintf(f,
+                 "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %.17g, "
+                 "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d}\n",
+                 kv.first.d, kv.first.n, kv.first.prec, kv.first.laplace, kv.second.two_level_min,
+                 kv.second.tc_min_rows, kv.second.sweep_ctas, kv.second.gj_max_own);
+  std::fclose(f);
+  std::rename(tmp.c_str(), path);
+}
+
+static bool tune_lookup(const TuneKey& k, ls::NdTune* t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *t = it->second;
+  return true;
+}
+
+static std::string tune_json(const ls::NdTune& t) {
+  char b[256];
+  std::snprintf(b, sizeof b, "{\"two_level_min\": %.6g, \"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d}",
+                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own);
+  return b;
+}
+
+static void write_report(const std::string& r, char* out, int capacity) {
+  if (!out || capacity <= 0) return;
+  const size_t n = std::min(r.size(), (size_t)capacity - 1);
+  std::memcpy(out, r.data(), n);
+  out[n] = '\0';
+}
+
 // Shared by ls_setup (Helmholtz kernel, medium m, potential omega^2 m) and ls_setup_laplace
 // (Sec. 5: Laplace kernel, potential V given directly; omega = 0 selects the kernel).
 static ls_status setup_common(const ls_grid* g, double omega, const double* m, bool laplace, void* stream,
@@ -616,7 +695,8 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     if (g->dim != 2 && g->dim != 3) throw Error{ls::EINVAL_, "dim must be 2 or 3"};
     if (laplace && g->dim != 3) throw Error{ls::EINVAL_, "the Laplace variant is three-dimensional (Sec. 5)"};
     const int n = g->n;
-    if (!pow2(2 * n)) throw Error{ls::EINVAL_, "2n must be a power of two"};
+    if (!pow2(2 * n) && 2 * n != 48 && 2 * n != 96)
+      throw Error{ls::EINVAL_, "2n must be a power of two, 48 or 96 (the FFT lengths of the passes)"};
     if (g->dim == 2 && (n < 16 || n > 2048)) throw Error{ls::EINVAL_, "2D needs 16 <= n <= 2048"};
     if (g->dim == 3 && (n < 8 || n > 128)) throw Error{ls::EINVAL_, "3D needs 8 <= n <= 128"};
     if (!laplace && (!(omega > 0) || !std::isfinite(omega))) throw Error{ls::EINVAL_, "omega must be positive"};
@@ -750,6 +830,10 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     LS_CUDA(cudaMemcpyAsync(c->cint64, c->cint_h.data(), c->cint_h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
     // nested-dissection structure (Sec. 3.2)
     c->nd = ls::nd_build(c->d, n, c->st);
+    {
+      ls::NdTune t;
+      if (tune_lookup(tune_key(c), &t)) ls::nd_set_tune(c->nd, t);
+    }
     ls::nd_set_tensor_cores(c->nd, g->front_fmt == LS_FRONT_3XTF32);
     LS_CUDA(cudaStreamSynchronize(c->st));
     *out = c;
@@ -1285,6 +1369,128 @@ void ctx_set_error(ls_ctx* c, const char* msg) { c->err = msg; }
 }  // namespace ls
 
 extern "C" {
+
+// ls_autotune: see include/ls.h.  Coordinate search: each choice in turn takes the candidate
+// that beats the current best by more than 2 %, the factorization choices timed on
+// ls_factor's launches (no graph, no overlap), the sweep choice on preconditioner solves of
+// nrhs right-hand sides; every timing is the fastest of its repeats (CUDA events).
+ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
+  try {
+    check_ctx(c);
+    if (nrhs < 1) throw Error{ls::EINVAL_, "nrhs must be >= 1"};
+    factor_wait(c);
+    const bool mixed = c->prec == LS_PREC_MIXED;
+    if (mixed ? ls::nd_prepare<float2>(c->nd, c->st) : ls::nd_prepare<double2>(c->nd, c->st)) ++c->gen;
+    const void* apt = c->general ? (const void*)c->apt64 : nullptr;
+    const unsigned char* inter = c->general ? c->inter_pt : nullptr;
+    cudaEvent_t e0, e1;
+    LS_CUDA(cudaEventCreate(&e0));
+    LS_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto&& body, int reps) {
+      float best = 1e30f;
+      for (int r = 0; r < reps; ++r) {
+        LS_CUDA(cudaEventRecord(e0, c->st));
+        body();
+        LS_CUDA(cudaEventRecord(e1, c->st));
+        LS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        LS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+      }
+      return (double)best;
+    };
+    auto factor_ms = [&](const ls::NdTune& t) {
+      ls::nd_set_tune(c->nd, t);
+      const double ms = timed([&] {
+        if (mixed) ls::nd_factor_launch<float2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, nullptr, apt, inter);
+        else ls::nd_factor_launch<double2>(c->nd, c->alpha64, c->cint64, c->w2m64, c->st, nullptr, apt, inter);
+      }, 2);
+      ls::nd_factor_check(c->nd, c->st);
+      return ms;
+    };
+    const size_t tot = (size_t)nrhs * c->N;
+    void* rb = mixed ? (void*)buf<float2>(c, "tune_r", tot) : (void*)buf<double2>(c, "tune_r", tot);
+    void* zb = mixed ? (void*)buf<float2>(c, "tune_z", tot) : (void*)buf<double2>(c, "tune_z", tot);
+    LS_CUDA(cudaMemsetAsync(rb, 0x3c, tot * (mixed ? sizeof(float2) : sizeof(double2)), c->st));
+    auto solve_ms = [&](const ls::NdTune& t) {
+      ls::nd_set_tune(c->nd, t);
+      return timed([&] {
+        if (mixed) ls::nd_solve<float2>(c->nd, nrhs, (const float2*)rb, (float2*)zb, c->st);
+        else ls::nd_solve<double2>(c->nd, nrhs, (const double2*)rb, (double2*)zb, c->st);
+      }, 3);
+    };
+    std::string log = "{\"factor_ms\": [";
+    ls::NdTune best = ls::nd_get_tune(c->nd);
+    double fb = factor_ms(best);
+    log += "[" + tune_json(best) + ", " + std::to_string(fb) + "]";
+    auto try_factor = [&](ls::NdTune t) {
+      const double f = factor_ms(t);
+      log += ", [" + tune_json(t) + ", " + std::to_string(f) + "]";
+      if (f < 0.98 * fb) {
+        best = t;
+        fb = f;
+      }
+    };
+    for (double v : {2.0e6, 3.2e7, 1e30}) {
+      ls::NdTune t = best;
+      t.two_level_min = v;
+      try_factor(t);
+    }
+    if (mixed)
+      for (int v : {128, 256}) {
+        ls::NdTune t = best;
+        t.tc_min_rows = v;
+        try_factor(t);
+      }
+    {
+      ls::NdTune t = best;
+      t.gj_max_own = best.gj_max_own == 16 ? 32 : 16;
+      try_factor(t);
+    }
+    // the factors the sweeps read: those of the chosen factorization
+    factor_ms(best);
+    log += "], \"solve_ms\": [";
+    double sb = solve_ms(best);
+    log += "[" + std::to_string(best.sweep_ctas) + ", " + std::to_string(sb) + "]";
+    for (int v : {1, 2, 4}) {
+      if (v == best.sweep_ctas) continue;
+      ls::NdTune t = best;
+      t.sweep_ctas = v;
+      const double sm = solve_ms(t);
+      log += ", [" + std::to_string(v) + ", " + std::to_string(sm) + "]";
+      if (sm < 0.98 * sb) {
+        best = t;
+        sb = sm;
+      }
+    }
+    ls::nd_set_tune(c->nd, best);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ++c->gen;  // the captured graphs hold the old launch sequences
+    c->factored = true;
+    c->factor_pending = false;
+    c->pre_refine = -1;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load_locked();
+      g_tune[tune_key(c)] = best;
+      tune_save_locked();
+    }
+    char head[160];
+    std::snprintf(head, sizeof head, "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"nrhs\": %d, ", c->d, c->n,
+                  (int)c->prec, c->laplace ? 1 : 0, nrhs);
+    write_report(std::string(head) + "\"choice\": " + tune_json(best) + ", " + log.substr(1) + "]}", report, capacity);
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity) {
+  if (!c) return LS_ESTATE;
+  write_report(tune_json(ls::nd_get_tune(c->nd)), report, capacity);
+  return LS_OK;
+}
 
 ls_status ls_profile_start(const char* timed_class) {
   ls::prof_start(timed_class);

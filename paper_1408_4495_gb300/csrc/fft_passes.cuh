@@ -87,9 +87,33 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft8v(C* v) {
   v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
+template <typename Rl> __device__ __forceinline__ Rl sin_pi3() { return (Rl)0.86602540378443864676; }
+// sin(pi/3) = sqrt(3)/2 as an FP32 pair: 0.8660254 + 1.5543625e-8
+template <> __device__ __forceinline__ ff sin_pi3<ff>() { return ff(0.8660254f, 1.5543625e-8f); }
+template <typename Rl> __device__ __forceinline__ Rl one_half() { return (Rl)0.5; }
+template <> __device__ __forceinline__ ff one_half<ff>() { return ff(0.5f, 0.f); }
+
+// 3-point DFT with w = exp(SIGN 2 pi i / 3) = -1/2 + SIGN i sqrt(3)/2:
+// X0 = a + (b + c), X1 = a - (b + c)/2 + SIGN i sqrt(3)/2 (b - c), X2 = the same with - for +
+template <int SIGN, typename C> __device__ __forceinline__ void dft3v(C* v) {
+  using Rl = typename RealOf<C>::T;
+  const Rl s3 = sin_pi3<Rl>(), half = one_half<Rl>();
+  const C a = v[0], t = cadd(v[1], v[2]);
+  C m, d = csub(v[1], v[2]);
+  m.x = a.x - half * t.x;
+  m.y = a.y - half * t.y;
+  d.x = s3 * d.x;
+  d.y = s3 * d.y;
+  const C r = rot_i<SIGN>(d);
+  v[0] = cadd(a, t);
+  v[1] = cadd(m, r);
+  v[2] = csub(m, r);
+}
+
 template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR(C* v) {
   if constexpr (R == 8) dft8v<SIGN>(v);
   else if constexpr (R == 4) dft4v<SIGN>(v);
+  else if constexpr (R == 3) dft3v<SIGN>(v);
   else dft<2, SIGN, C>(v);
 }
 
@@ -113,7 +137,7 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q][r] = sl[pidx(j + r * BPL)];
       if constexpr (NS > 1) {
-        const int k = j & (NS - 1);
+        const int k = j % NS;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
           C w = ldg_c(&tw[r * k * (L / (NS * R))]);
@@ -131,7 +155,7 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
     if (BF % NT == 0 || b < BF) {
       const int line = b / BPL, j = b - line * BPL;
       C* sl = s + line * LS;
-      const int k = j & (NS - 1);
+      const int k = j % NS;
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) sl[pidx(base + r * NS)] = v[q][r];
@@ -140,11 +164,13 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
   __syncthreads();
 }
 
+// Radices 8, then 4 or 2 for the rest of the power of two, then 3 for L = 3 * 2^k.
 template <typename C, int L, int NS, int SIGN, int NLINES, int NT>
 __device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw) {
   if constexpr (NS < L) {
     constexpr int REM = L / NS;
-    constexpr int R = REM >= 8 ? 8 : REM;
+    constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
+    static_assert(REM % R == 0, "FFT length must be 2^k or 3 * 2^k");
     fft_pass<C, L, R, NS, SIGN, NLINES, NT>(s, tw);
     fft_lines<C, L, NS * R, SIGN, NLINES, NT>(s, tw);
   }
@@ -424,7 +450,7 @@ template <typename C, int L, int MODE> void launch_col_L(const ColPassArgs& a, c
   LS_LAUNCH(cls.c_str(), st, k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a));
 }
 
-#define LS_FOR_L(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+#define LS_FOR_L(X) X(16) X(32) X(48) X(64) X(96) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
 // Explicit instantiation (PREFIX empty) or instantiation declaration (PREFIX extern) of the
 // five launchers of one arithmetic C and one length LL: the float-float passes spread their

@@ -139,6 +139,20 @@ void nd_factor_launch(NdPlan* p, const void* alpha_T, const void* cint_T, const 
 void nd_factor_check(NdPlan* p, cudaStream_t st);
 // FP32 Schur-complement products on the tensor cores (3xTF32, the default) or on the CUDA cores
 void nd_set_tensor_cores(NdPlan* p, bool on);
+// Launch-shape choices of the factorization and of the solve sweeps.  The defaults were
+// chosen by measurement on 2D n = 256; ls_autotune times the alternatives per grid and
+// precision and keeps the fastest.
+struct NdTune {
+  double two_level_min = 8.0e6;  // trailing-matrix entries of a level from which the blocked
+                                 // LU updates in two levels (outer blocks of 4 panels)
+  int tc_min_rows = 64;          // FP32 Schur products with at least this many rows (and 16
+                                 // inner columns) run on the tensor cores
+  int sweep_ctas = 2;            // CTAs per SM that the split of a sweep level's columns aims at
+  int gj_max_own = 16;           // fronts with at most this many own rows: Gauss-Jordan in one CTA
+};
+constexpr int SWEEP_CTAS_MAX = 4;  // the solve's partial-sum buffers are sized for this target
+void nd_set_tune(NdPlan* p, const NdTune& t);
+NdTune nd_get_tune(const NdPlan* p);
 // x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
 template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);
 size_t nd_device_bytes(const NdPlan* p, int elem_bytes);

@@ -102,6 +102,7 @@ struct NdPlan {
   unsigned* cnt = nullptr;  // solve: per-item arrival counters
   int* d_err = nullptr;
   bool use_tc = true;  // FP32 Schur products on the tensor cores (3xTF32) where they qualify
+  NdTune tune{};       // launch-shape choices (defaults, or the autotuner's)
   void* blob = nullptr;  // every index array of the plan, one device allocation
   NdInfo info{};
 };
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(512) k_panel(LevelK<C> L, int k0, int k1, int*
     if (bi == 0x7fffffff) bi = j;
     if (tid == 0) {
       L.piv[(size_t)z * smax + k0 + j] = k0 + bi;
-      if (!(best > 0)) atomicExch(err, 1);
+      if (!(best > 0)) atomicCAS(err, 0, 1);
     }
     if (bi != j)
       for (int c = tid; c < w; c += NT) {
@@ -940,10 +941,10 @@ __global__ void __launch_bounds__(panel_reg_rows<C>()) k_panel_reg(LevelK<C> L, 
       __syncthreads();
       const unsigned km = __reduce_max_sync(0xffffffffu, lane < nw ? skey[par][lane] : 0u);
       if (km == 0u) {  // no live row left (cannot happen while j < R)
-        if (r == 0) atomicExch(err, 1);
+        if (r == 0) atomicCAS(err, 0, 1);
         continue;
       }
-      if ((km >> 10) == 0u && r == 0) atomicExch(err, 1);  // zero pivot
+      if ((km >> 10) == 0u && r == 0) atomicCAS(err, 0, 1);  // zero pivot
       const int bi = 1023 - (int)(km & 1023u);
       if (r == bi) {
         live = false;
@@ -1051,10 +1052,10 @@ __global__ void __launch_bounds__(PC_ROWS) k_panel_cluster(LevelK<C> L, int k0, 
       cl.sync();
       const unsigned km = __reduce_max_sync(0xffffffffu, lane < ncta ? *cl.map_shared_rank(&ckey[par], lane) : 0u);
       if (km == 0u) {  // no live row left (cannot happen while j < R)
-        if (t == 0 && q == 0) atomicExch(err, 1);
+        if (t == 0 && q == 0) atomicCAS(err, 0, 1);
         continue;
       }
-      if ((km >> 12) == 0u && t == 0 && q == 0) atomicExch(err, 1);  // zero pivot
+      if ((km >> 12) == 0u && t == 0 && q == 0) atomicCAS(err, 0, 1);  // zero pivot
       const int bi = 4095 - (int)(km & 4095u);
       if (r == bi) {
         live = false;
@@ -1486,7 +1487,7 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
     const unsigned bu = __reduce_min_sync(0xffffffffu, (lane < nw && k2 == km) ? sidx[par][lane] : 0xffffffffu);
     const int bi = bu == 0xffffffffu ? 0 : (int)bu;
     if (tid == 0) {
-      if (km == 0u || bu == 0xffffffffu) atomicExch(err, 1);
+      if (km == 0u || bu == 0xffffffffu) atomicCAS(err, 0, 1);
       pseq_s[j] = bi;
     }
     if (live && r == bi) live = false;
@@ -1557,7 +1558,7 @@ template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
 struct SweepPlan {
   int K, tr, ntile, nsplit, ksz;
 };
-static SweepPlan sweep_plan(const LevelDev& D, int mode, int ng) {
+static SweepPlan sweep_plan(const LevelDev& D, int mode, int ng, int ctas_per_sm) {
   SweepPlan q;
   q.K = mode == 0 ? D.smax : D.bmax + D.smax;
   const int nrows = mode == 0 ? D.bmax : D.smax;
@@ -1566,7 +1567,7 @@ static SweepPlan sweep_plan(const LevelDev& D, int mode, int ng) {
   const long base = (long)D.nf * q.ntile * ng;
   q.nsplit = 1;
   if (nrows > 0)
-    while (base * q.nsplit < 2 * 152 && q.K / (q.nsplit * 2) >= 64) q.nsplit *= 2;
+    while (base * q.nsplit < (long)ctas_per_sm * 152 && q.K / (q.nsplit * 2) >= 64) q.nsplit *= 2;
   q.ksz = q.K > 0 ? (q.K + q.nsplit - 1) / q.nsplit : 0;
   return q;
 }
@@ -1586,7 +1587,7 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes, cudaStream_t st) {
   for (const LevelDev& D : p->lev)
     for (int mode = 0; mode < 2; ++mode)
       for (int ng = 1; ng <= SOLVE_CHUNK / 16; ++ng) {
-        const SweepPlan q = sweep_plan(D, mode, ng);
+        const SweepPlan q = sweep_plan(D, mode, ng, SWEEP_CTAS_MAX);
         items = std::max(items, (size_t)D.nf * q.ntile * ng);
         if (q.nsplit > 1) part = std::max(part, (size_t)D.nf * q.ntile * q.nsplit * q.tr * 16 * ng);
       }
@@ -1616,11 +1617,12 @@ template <typename C> static size_t gj_smem(int s, int nc) {
 // FP32 products with at least this many rows and k go to the tensor cores (3xTF32)
 constexpr int TC_MIN_ROWS = 64, TC_MIN_K = 16;
 
+// tc: the launch-shape choices when the tensor cores may take the product, else null
 template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
-                                              cudaStream_t st, int* err, bool tc) {
+                                              cudaStream_t st, int* err, const NdTune* tc) {
   if (r1 <= r0 || c1 <= c0 || k1 <= k0) return;
   if constexpr (sizeof(C) == 8) {
-    if (tc && r1 - r0 >= TC_MIN_ROWS && k1 - k0 >= TC_MIN_K && tc_enabled()) {
+    if (tc && r1 - r0 >= std::max(tc->tc_min_rows, TC_MIN_ROWS) && k1 - k0 >= TC_MIN_K && tc_enabled()) {
       tc_cgemm(reinterpret_cast<float2*>(L.F), (long)L.fmax * L.ncols, L.fmax, L.nf, r0, r1, c0, c1, k0, k1, err, st);
       return;
     }
@@ -1633,12 +1635,14 @@ template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1
 template <typename C> bool nd_prepare(NdPlan* p, cudaStream_t st) { return ensure_buffers(p, sizeof(C), st); }
 
 void nd_set_tensor_cores(NdPlan* p, bool on) { p->use_tc = on; }
+void nd_set_tune(NdPlan* p, const NdTune& t) { p->tune = t; }
+NdTune nd_get_tune(const NdPlan* p) { return p->tune; }
 
 // own rows per lane of the register sweeps (32 * this many own rows at most)
 template <typename C> constexpr int reg_rpl_max() { return sizeof(C) == 8 ? 16 : 8; }
 
 template <typename C, int RPL>
-static void reg_sweeps(const LevelK<C>& L, int* swp, int* err, bool tc, cudaStream_t st) {
+static void reg_sweeps(const LevelK<C>& L, int* swp, int* err, const NdTune* tc, cudaStream_t st) {
   const bool f32 = sizeof(C) == 8;
   const size_t smem_max = (size_t)32 * 32 * RPL * sizeof(C) + (size_t)32 * RPL * sizeof(int);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
@@ -1679,6 +1683,9 @@ void nd_factor_check(NdPlan* p, cudaStream_t st) {
   int err = 0;
   LS_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA(cudaStreamSynchronize(st));
+  // a singular pivot only claims the flag while it is clear (atomicCAS), an expired wait
+  // always takes it (atomicExch): a timeout is reported even when the fronts it left
+  // unupdated later give a zero pivot
   if (err == 2) LS_FAIL(ETIMEOUT_, "a bounded wait of the tensor-core front update expired");
   if (err) LS_FAIL(EINVAL_, "nested-dissection factorization met an exactly singular front");
 }
@@ -1716,6 +1723,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     attr.store(true, std::memory_order_release);
   }
   bool marked = top_levels == nullptr;
+  const NdTune* tcp = p->use_tc ? &p->tune : nullptr;
   for (int l = depth - 1; l >= 0; --l) {
     prof_tag(l);
     LevelK<C> L = level_k<C>(p, l);
@@ -1734,7 +1742,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     // whose trailing updates spread over many CTAs, for the larger ones (measured on 2D
     // n = 256: 1 % faster with the 32-row levels on the register path, 6 % slower with
     // the 8- and 16-row levels there too)
-    const bool gj = gjm <= GJ_SMEM_MAX && (L.smax <= 16 || L.smax > 32 * reg_rpl_max<C>());
+    const bool gj = gjm <= GJ_SMEM_MAX && (L.smax <= p->tune.gj_max_own || L.smax > 32 * reg_rpl_max<C>());
     const bool fused_ea = gj && has_child && Ch.bmax < 48;
     if (has_child && !fused_ea) {
       const long tot = (long)Ch.bmax * Ch.bmax;
@@ -1748,7 +1756,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
       LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
                 k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, fused_ea ? 1 : 0,
                                                                                    p->d_err));
-      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, p->use_tc);
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, tcp);
       continue;
     }
     // The register sweeps update every trailing column on CUDA cores from a panel staged per
@@ -1757,9 +1765,9 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
     if (L.smax <= 32 * reg_rpl_max<C>() && L.ncols <= REG_MAX_COLS) {
       // both sweeps with the fronts' own rows in registers
       const int rpl = (L.smax + 31) / 32;
-      if (rpl <= 4) reg_sweeps<C, 4>(L, p->swp, p->d_err, p->use_tc, st);
-      else if (rpl <= 8) reg_sweeps<C, 8>(L, p->swp, p->d_err, p->use_tc, st);
-      else reg_sweeps<C, reg_rpl_max<C>()>(L, p->swp, p->d_err, p->use_tc, st);
+      if (rpl <= 4) reg_sweeps<C, 4>(L, p->swp, p->d_err, tcp, st);
+      else if (rpl <= 8) reg_sweeps<C, 8>(L, p->swp, p->d_err, tcp, st);
+      else reg_sweeps<C, reg_rpl_max<C>()>(L, p->swp, p->d_err, tcp, st);
     } else {
       // sweep 1: blocked LU of the own columns on the own rows (pivot rows restricted to
       // them), the block rows of [F12 | I] carried along.  Outer blocks of OB_PANELS panels:
@@ -1787,14 +1795,14 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             launch_ring_trsm<C>(L, k0, k1, st);
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1));
-            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
-            launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, tcp);
+            launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, p->d_err, tcp);
           }
           continue;
         }
         // two levels only where the trailing matrix is large: below about 8 M entries per
         // level the extra launches cost more than the passes they save (2D n = 1024)
-        const bool two = (double)L.nf * R0 * (L.ncols - K0) >= 8.0e6;
+        const bool two = (double)L.nf * R0 * (L.ncols - K0) >= p->tune.two_level_min;
         int np = 0;
         for (int k0 = K0; k0 < K1; k0 += NB, ++np) {
           const int k1 = std::min(k0 + NB, K1), R = L.smax - k0;
@@ -1824,8 +1832,8 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (L.ncols - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1,
                                                                                                  L.ncols, rec));
-            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
-            launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, k1, L.smax, k1, L.ncols, k0, k1, st, p->d_err, tcp);
+            launch_gemm<C>(L, L.smax, L.fmax, k1, L.smax, k0, k1, st, p->d_err, tcp);
             continue;
           }
           // the block's earlier L columns follow this panel's permutation
@@ -1837,7 +1845,7 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
           if (k1 < K1) {
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (K1 - k1 + 127) / 128), 128, 0, st>>>(L, k0, k1, k1, K1, rec));
-            launch_gemm<C>(L, k1, L.fmax, k1, K1, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, k1, L.fmax, k1, K1, k0, k1, st, p->d_err, tcp);
           }
         }
         if (two && K1 < L.ncols) {
@@ -1850,15 +1858,15 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
             LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                       k_trsm_lower_swp<C><<<dim3(L.nf, (m + 127) / 128), 128, 0, st>>>(L, k0, k1, K1, L.ncols,
                                                                                        (const int*)nullptr));
-            launch_gemm<C>(L, k1, K1, K1, L.ncols, k0, k1, st, p->d_err, p->use_tc);
+            launch_gemm<C>(L, k1, K1, K1, L.ncols, k0, k1, st, p->d_err, tcp);
           }
-          launch_gemm<C>(L, K1, L.smax, K1, L.ncols, K0, K1, st, p->d_err, p->use_tc);
-          launch_gemm<C>(L, L.smax, L.fmax, K1, L.smax, K0, K1, st, p->d_err, p->use_tc);
+          launch_gemm<C>(L, K1, L.smax, K1, L.ncols, K0, K1, st, p->d_err, tcp);
+          launch_gemm<C>(L, L.smax, L.fmax, K1, L.smax, K0, K1, st, p->d_err, tcp);
         }
       }
       // ring rows: [S | Y] = [F22 | 0] - L21 [U12 | L11^{-1} P], before sweep 2 overwrites the
       // own rows of [F12 | I]
-      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, p->use_tc);
+      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, tcp);
       // sweep 2: backward substitution with U11 on the own rows of [F12 | I], in outer
       // blocks of OB_PANELS row blocks: inside a block each 32-row solve updates the block's
       // rows above it, then one GEMM with K = OB_PANELS * NB updates the rows above the block
@@ -1870,9 +1878,9 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
           const int j0 = jb * NB, j1 = std::min(j0 + NB, L.smax);
           LS_LAUNCH(f32 ? "nd_trsm_c64" : "nd_trsm_c128", st,
                     k_trsm_upper<C><<<dim3(L.nf, (m2 + 127) / 128), 128, 0, st>>>(L, j0, j1));
-          launch_gemm<C>(L, J0, j0, L.smax, L.ncols, j0, j1, st, p->d_err, p->use_tc);
+          launch_gemm<C>(L, J0, j0, L.smax, L.ncols, j0, j1, st, p->d_err, tcp);
         }
-        launch_gemm<C>(L, 0, J0, L.smax, L.ncols, J0, J1, st, p->d_err, p->use_tc);
+        launch_gemm<C>(L, 0, J0, L.smax, L.ncols, J0, J1, st, p->d_err, tcp);
       }
     }
   }
@@ -2304,7 +2312,7 @@ static void launch_sweep_tr(NdPlan* p, int l, C* T, int ng, const SweepPlan& q, 
 }
 
 template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int l, C* T, int ng, cudaStream_t st) {
-  const SweepPlan q = sweep_plan(p->lev[l], MODE, ng);
+  const SweepPlan q = sweep_plan(p->lev[l], MODE, ng, std::min(std::max(p->tune.sweep_ctas, 1), SWEEP_CTAS_MAX));
   if (q.K <= 0) return;
   if (q.nsplit > 1 && (size_t)p->lev[l].nf * q.ntile * q.nsplit * q.tr * RC * ng > p->part_elems)
     LS_FAIL(EINVAL_, "solve partial-sum buffer too small");

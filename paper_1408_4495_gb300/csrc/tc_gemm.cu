@@ -12,8 +12,14 @@
 // accuracy of the FP32 fronts).  A CTA owns a 128-row tile of C and NT = 64 complex columns:
 // D = 128 x 128 FP32 accumulators in tensor memory, filled by tcgen05.mma kind::tf32
 // (M = 128, N = 128, K = 8 per instruction) from K-major operands in shared memory
-// (no-swizzle canonical layout: 8-row x 16-byte core matrices).  One thread issues the MMAs
-// and commits them to an mbarrier; all waits are bounded and set *err on expiry.
+// (no-swizzle canonical layout: 8-row x 16-byte core matrices).  The K loop is a two-stage
+// pipeline over chunks of KC complex k: while the tensor core runs the MMAs of one chunk, the
+// threads convert the next chunk (held in registers) into the other operand stage (3xTF32
+// split, canonical layout) and load the chunk after it from global memory (coalesced:
+// consecutive threads on consecutive entries of a column).  One thread issues the MMAs and
+// commits each chunk to its stage's mbarrier; 65 KB of shared memory, three CTAs per SM.  All
+// waits are bounded and set *err on expiry, and the tensor memory is freed only after the
+// last commit has been awaited.
 #include <atomic>
 #include <cuda_runtime.h>
 
@@ -32,7 +38,7 @@ namespace tc {
 constexpr int TM = 128;        // rows of C per CTA
 constexpr int NT = 64;         // complex columns of C per CTA
 constexpr int NP = 2 * NT;     // real columns (Re | Im)
-constexpr int KC = 16;         // complex k per chunk
+constexpr int KC = 8;          // complex k per chunk
 constexpr int KP = 2 * KC;     // real k per chunk
 constexpr int KSTEP = 8;       // tf32 k per instruction
 constexpr int NSTEP = KP / KSTEP;
@@ -40,10 +46,12 @@ constexpr int THREADS = 256;
 // one operand slice of KSTEP real k: rows x 32 bytes
 constexpr int A_SLICE = TM * KSTEP * 4;   // 4 KB
 constexpr int B_SLICE = NP * KSTEP * 4;   // 4 KB
-constexpr int A_BYTES = NSTEP * A_SLICE;  // 16 KB (hi or lo)
-constexpr int B_BYTES = NSTEP * B_SLICE;  // 16 KB
-constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES + 1024;  // + barrier and TMEM address
+constexpr int A_BYTES = NSTEP * A_SLICE;  // 8 KB (hi or lo)
+constexpr int B_BYTES = NSTEP * B_SLICE;  // 8 KB
+constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of A' and B': 32 KB
+constexpr int SMEM = 2 * STAGE + 1024;            // two stages + barriers and TMEM address: three CTAs per SM
 constexpr long WAIT_LIMIT = 1L << 26;
+constexpr long TEST_WAIT_LIMIT = 1L << 10;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -93,8 +101,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
 }
 
 // waits for the given phase of the barrier; false if the bound expired
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (long it = 0; it < WAIT_LIMIT; ++it)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long limit) {
+  for (long it = 0; it < limit; ++it)
     if (mbar_try_wait(mbar, phase)) return true;
   return false;
 }
@@ -108,17 +116,15 @@ struct TcArgs {
   int r0, r1, c0, c1, k0, k1;
   int ntr;           // row tiles (grid.y = ntr * column tiles)
   int* err;
+  int test_no_mma;   // test hook: issue no MMA and no commit, so that the bounded waits expire
+  long wait_limit;   // iterations of a bounded mbarrier wait
 };
 
 __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* Ahi = smem_raw;
-  unsigned char* Alo = Ahi + A_BYTES;
-  unsigned char* Bhi = Alo + A_BYTES;
-  unsigned char* Blo = Bhi + B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + B_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + 2 * STAGE);  // one per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   __shared__ int failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -131,6 +137,7 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
   if (tid == 0) {
     failed = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -143,13 +150,12 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t mb = smem_u32(mbar);
 
-  uint32_t phase = 0;
   const int K = a.k1 - a.k0;
   const int nchunk = (K + KC - 1) / KC;
-  // global loads of one chunk into registers: A 128 x KC (8 per thread), B KC x 64 (4 per
-  // thread); the next chunk's loads are issued while the tensor core works on this one
+  // global loads of one chunk into registers: A 128 x KC (4 per thread, consecutive threads
+  // on consecutive rows of a column), B KC x 64 (2 per thread, consecutive threads on
+  // consecutive k of a column); issued one chunk ahead, while the tensor core works
   constexpr int PA = TM * KC / THREADS, PB = NT * KC / THREADS;
   float2 va[PA], vb[PB];
   auto load = [&](int kc) {
@@ -161,14 +167,18 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
     }
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
-      const int e = tid + u * THREADS, n = e % NT, k = e / NT;
+      const int e = tid + u * THREADS, k = e % KC, n = e / KC;
       vb[u] = (k < kw && cb + n < a.c1) ? F[(size_t)(cb + n) * fmax + a.k0 + kc + k] : make_float2(0.f, 0.f);
     }
   };
-  if (nchunk > 0) load(0);
-  int chunks = 0;
-  for (int ch = 0; ch < nchunk; ++ch, ++chunks) {
-    // ---- A' (TM x KP): element (m, 2k + p), hi and lo
+  // the registers of one chunk -> stage st: A' (TM x KP): element (m, 2k + p); B' (NP x KP,
+  // K-major): column n < NT holds (Re B, -Im B), column NT + n holds (Im B, Re B); each as
+  // the TF32 pair hi, lo = x - hi
+  auto convert = [&](int st) {
+    unsigned char* Ahi = smem_raw + st * STAGE;
+    unsigned char* Alo = Ahi + A_BYTES;
+    unsigned char* Bhi = Alo + A_BYTES;
+    unsigned char* Blo = Bhi + B_BYTES;
 #pragma unroll
     for (int u = 0; u < PA; ++u) {
       const int e = tid + u * THREADS, m = e % TM, k = e / TM;
@@ -181,10 +191,9 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
       *reinterpret_cast<uint2*>(Ahi + o) = make_uint2(hx, hy);  // kk even: (2k, 2k+1) adjacent
       *reinterpret_cast<uint2*>(Alo + o) = make_uint2(lx, ly);
     }
-    // ---- B' (NP x KP, K-major): column n < NT: (Re B, -Im B); column NT + n: (Im B, Re B)
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
-      const int e = tid + u * THREADS, n = e % NT, k = e / NT;
+      const int e = tid + u * THREADS, k = e % KC, n = e / KC;
       const float re = vb[u].x, im = vb[u].y;
       const int kr = 2 * k, s = kr / KSTEP, kk = kr % KSTEP;
       const uint32_t hre = to_tf32(re), him = to_tf32(im), hnim = to_tf32(-im);
@@ -196,34 +205,65 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
       *reinterpret_cast<uint2*>(Bhi + o2) = make_uint2(him, hre);
       *reinterpret_cast<uint2*>(Blo + o2) = make_uint2(lim, lre);
     }
+  };
+  // one thread: the chunk's MMAs on stage st (3 per K step: hi hi, hi lo, lo hi), committed
+  // to the stage's barrier
+  auto issue = [&](int st, bool first) {
+    const unsigned char* Ahi = smem_raw + st * STAGE;
+    const unsigned char* Alo = Ahi + A_BYTES;
+    const unsigned char* Bhi = Alo + A_BYTES;
+    const unsigned char* Blo = Bhi + B_BYTES;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (a.test_no_mma) return;
+    for (int s = 0; s < NSTEP; ++s) {
+      const uint64_t ah = sdesc(smem_u32(Ahi + s * A_SLICE)), al = sdesc(smem_u32(Alo + s * A_SLICE));
+      const uint64_t bh = sdesc(smem_u32(Bhi + s * B_SLICE)), bl = sdesc(smem_u32(Blo + s * B_SLICE));
+      mma_tf32(tmem, ah, bh, (!first || s > 0) ? 1 : 0);
+      mma_tf32(tmem, ah, bl, 1);
+      mma_tf32(tmem, al, bh, 1);
+    }
+    mma_commit(smem_u32(mbar + st));
+  };
+
+  // two-stage pipeline: the registers of chunk ch + 1 load while the MMAs of chunk ch - 1 run
+  // and chunk ch is converted into the stage the MMAs of chunk ch - 2 have released
+  uint32_t phase[2] = {0u, 0u};
+  int last = -1;  // last chunk whose MMAs were issued
+  if (nchunk > 0) load(0);
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int st = ch & 1;
+    if (ch >= 2) {
+      if (!tc::mbar_wait(smem_u32(mbar + st), phase[st], a.wait_limit)) {
+        if (tid == 0) atomicExch(a.err, 2);
+        failed = 1;
+      }
+      phase[st] ^= 1u;
+      __syncthreads();
+      if (failed) break;
+    }
+    convert(st);
+    if (ch + 1 < nchunk) load((ch + 1) * KC);
     // generic-proxy writes -> visible to the tensor core's async proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      for (int s = 0; s < NSTEP; ++s) {
-        const uint64_t ah = sdesc(smem_u32(Ahi + s * A_SLICE)), al = sdesc(smem_u32(Alo + s * A_SLICE));
-        const uint64_t bh = sdesc(smem_u32(Bhi + s * B_SLICE)), bl = sdesc(smem_u32(Blo + s * B_SLICE));
-        const int acc0 = (ch > 0 || s > 0) ? 1 : 0;
-        mma_tf32(tmem, ah, bh, acc0);
-        mma_tf32(tmem, ah, bl, 1);
-        mma_tf32(tmem, al, bh, 1);
-      }
-      mma_commit(mb);
-    }
-    if (ch + 1 < nchunk) load((ch + 1) * KC);
-    // the operands are overwritten by the next chunk: wait for these MMAs
-    if (!mbar_wait(mb, phase)) {
+    if (tid == 0) issue(st, ch == 0);
+    last = ch;
+  }
+  // the last commit covers every MMA issued before it.  If it does not arrive within the
+  // bound, the error is set and it is awaited once more (bounded) before the tensor memory
+  // is freed, so that no MMA issued here can still be writing it
+  if (last >= 0) {
+    const int st = last & 1;
+    if (!tc::mbar_wait(smem_u32(mbar + st), phase[st], a.wait_limit)) {
       if (tid == 0) atomicExch(a.err, 2);
       failed = 1;
+      tc::mbar_wait(smem_u32(mbar + st), phase[st], a.wait_limit);
     }
-    phase ^= 1;
-    __syncthreads();
-    if (failed) break;
   }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
-  if (!failed && chunks > 0) {
+  if (!failed && last >= 0) {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .., columns of half w / 4 of the Re
     // and the Im blocks, and subtracts from C
     const int q = warp & 3, half = warp >> 2;
@@ -281,6 +321,11 @@ void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0,
     attr.store(true, std::memory_order_release);
   }
   TcArgs a;
+  // test hook (off unless LS_TEST_TC_TIMEOUT=1): no MMA is issued and the waits are short,
+  // so that the bounded waits expire with nothing in flight and ls_factor reports LS_ETIMEOUT
+  const char* hook = std::getenv("LS_TEST_TC_TIMEOUT");
+  a.test_no_mma = (hook && hook[0] == '1') ? 1 : 0;
+  a.wait_limit = a.test_no_mma ? tc::TEST_WAIT_LIMIT : tc::WAIT_LIMIT;
   a.F = F;
   a.fstride = fstride;
   a.fmax = fmax;

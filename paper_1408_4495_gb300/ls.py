@@ -33,7 +33,7 @@ EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls
            "ls_export_factors", "ls_import_factors",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
-           "ls_profile_start", "ls_profile_stop", "ls_apply_noalloc"]
+           "ls_profile_start", "ls_profile_stop", "ls_autotune", "ls_tune_info", "ls_apply_noalloc"]
 
 
 class LsGrid(ctypes.Structure):
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_precond.argtypes = [vp, ip, vp, vp]
     lib.ls_get_nd_stats.argtypes = [vp, ctypes.POINTER(LsNdStats)]
     lib.ls_apply_noalloc.argtypes = [vp, ip, vp, vp]
+    lib.ls_autotune.argtypes = [vp, ip, ctypes.c_char_p, ip]
+    lib.ls_tune_info.argtypes = [vp, ctypes.c_char_p, ip]
     lib.ls_profile_start.argtypes = [ctypes.c_char_p]
     lib.ls_profile_stop.argtypes = [ctypes.c_char_p, ip]
     for name in EXPORTS:
@@ -430,6 +432,21 @@ class Solver:
             raise ValueError(f"x ({x.device}) and out ({out.device}) are on different devices")
         self._check(self.lib.ls_apply_noalloc(self.h, int(x.shape[0]), _ptr(x), _ptr(out)))
         return out
+
+    def autotune(self, nrhs: int) -> dict:
+        """ls_autotune: time the launch-shape alternatives on this context (factorization and
+        solves of nrhs right-hand sides), apply and keep the fastest; returns the report."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.lib.ls_autotune(self.h, int(nrhs), buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def tune(self) -> dict:
+        """ls_tune_info: the context's launch-shape choices."""
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        self._check(self.lib.ls_tune_info(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def nd_stats(self) -> dict:
         s = LsNdStats()

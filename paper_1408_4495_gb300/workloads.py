@@ -14,6 +14,7 @@ stand-ins of the same shape:
 * ``bumps``: sum of Gaussian bumps A exp(-|x-c|^2 / (2 w^2)) times the cutoff.
 * ``smooth_noise``: white noise convolved with a Gaussian of width 4h, scaled to a given
   max |m|, times the cutoff.
+* ``box_cavity``: the smoothed square (2D) and cubic (3D) cavities of Sec. 3.3.
 * ``cavity``: the media of Sec. 4 (general domains): a smoothed cavity of an l2 or l1 ball,
   m = A s((rho - |x - c|_p) / delta) with the C-infinity step s, so that supp(m) is the open
   ball of radius rho (the unknowns of the general-domain method) and m = A inside rho - delta.
@@ -217,8 +218,28 @@ def cavity(n: int, d: int, norm: str = "l2", rho: float = 0.4, delta: float = 0.
     return amp * _smooth_step((rho - r) / delta)
 
 
-def serving_stream(count: int, rate: float, seed: int = 1006, grids=((2, 128), (2, 256), (3, 16), (3, 32)),
-                   weights=(0.35, 0.35, 0.15, 0.15), max_dirs: int = 32, pool: int | None = None):
+# the serving mix: 70 % 2D n in {128, 256, 512}, 30 % 3D n in {32, 48}
+SERVING_GRIDS = ((2, 128), (2, 256), (2, 512), (3, 32), (3, 48))
+SERVING_WEIGHTS = (0.7 / 3, 0.7 / 3, 0.7 / 3, 0.15, 0.15)
+
+
+def box_cavity(n: int, d: int, amp: float = -1.25, half: float = 0.2, delta: float = 0.1) -> np.ndarray:
+    """Secs. 3.3 stand-in for the smoothed square (2D, Fig. R22) and cubic (3D, Fig. R32)
+    cavities: amp times a smoothed indicator of the box |x_a - 1/2| < half on every axis,
+    product over the axes of s((half - |x_a - 1/2|) / delta + 1/2) with the C-infinity step s
+    (so m = amp on |x_a - 1/2| < half - delta/2 and 0 beyond half + delta/2), times the cutoff.
+    amp = -1.25 gives the velocity c = (1 - m)^(-1/2) = 2/3 inside and 1 outside, the range
+    the paper states for its examples."""
+    x = grid_x(n)
+    s1 = _smooth_step((half - np.abs(x - 0.5)) / delta + 0.5)
+    out = s1
+    for _ in range(d - 1):
+        out = np.multiply.outer(out, s1)
+    return amp * out * cutoff(n, d)
+
+
+def serving_stream(count: int, rate: float, seed: int = 1006, grids=SERVING_GRIDS, weights=SERVING_WEIGHTS,
+                   max_dirs: int = 32, pool: int | None = None):
     """Seeded serving mix: ``count`` requests with exponential inter-arrival times of mean
     1 / rate seconds.  Each entry is (d, n, omega, m, directions, arrival).  With ``pool`` set,
     each grid draws its medium from ``pool`` seeded media, so requests can share a medium."""

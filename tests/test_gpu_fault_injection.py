@@ -49,3 +49,27 @@ def test_failed_solve_leaves_the_context_usable(LS):
         assert e.value.status == LS.LS_ENOMEM
         u, info = s.solve(g, tol=1e-6)
         assert all(i.converged for i in info)
+
+
+def test_expired_tensor_core_wait_reports_etimeout_and_the_context_recovers(LS, monkeypatch):
+    """The bounded mbarrier waits of the tensor-core front update: under the test hook
+    LS_TEST_TC_TIMEOUT=1 no MMA is issued and the waits are short, so every wait expires with
+    nothing in flight; the kernels free their tensor memory and return, the factorization
+    reports LS_ETIMEOUT at the next call that reads it, and a factorization without the hook
+    on the same context then solves normally.  No GPU fault is induced."""
+    n = 128
+    rng = np.random.default_rng(9)
+    m = W.enforce_buffer(W.bumps(n, 2, rng.uniform(-0.2, 0.2, 3), rng.uniform(0.06, 0.1, 3),
+                                 rng.uniform(0.35, 0.65, (3, 2))), 2)
+    omega = 2 * np.pi * 16
+    with LS.Solver(m, omega, mixed=True) as s:
+        g = s.rhs_plane_wave(W.directions_circle(2))
+        monkeypatch.setenv("LS_TEST_TC_TIMEOUT", "1")
+        s.factor()
+        with pytest.raises(LS.LsError) as e:
+            s.solve(g, tol=1e-6)
+        assert e.value.status == LS.LS_ETIMEOUT
+        monkeypatch.delenv("LS_TEST_TC_TIMEOUT")
+        s.factor()
+        u, info = s.solve(g, tol=1e-6)
+    assert all(i.converged and i.rel_resid <= 1e-6 for i in info)

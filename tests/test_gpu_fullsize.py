@@ -115,18 +115,22 @@ def test_large_2d_n1024(LS):
 
 
 def test_3d_n64(LS):
-    """3D n=64, omega = 2 pi 8, six bumps, 8 directions on the sphere."""
+    """3D n=64, omega = 2 pi 8, six bumps, 8 directions on the sphere, in the bench's
+    configuration; against the oracle's stored iterations and 1e-10 solutions (its SuperLU
+    factorization of this grid takes about half an hour on the host)."""
     w = W.bumps_3d(64, 8.0, 6, 8, 1004)
     w.m = W.enforce_buffer(w.m, 2)
     with LS.Solver(w.m, w.omega, mixed=True) as s:
         assert _sampled_apply_check(s, w, 4, 3) < 1e-11
-        s.factor()
-        g = s.rhs_plane_wave(w.directions)
-        u, info = s.solve(g, tol=1e-6)
+        for _ in range(3):  # eager, captured, replayed
+            s.factor()
+            g = s.rhs_plane_wave(w.directions)
+            u, info = s.solve(g, tol=1e-6)
     assert all(i.converged and i.rel_resid <= 1e-6 for i in info)
-    assert max(i.iters for i in info) <= 20
-    for j in (0, 5):
+    gold = _golden("3d_n64")
+    for j in gold["directions"]:
         assert _true_resid(w, u[j], g[j]) < 1.01e-6
+    _check_against_golden(gold, u, info)
 
 
 def test_3d_n64_preconditioner_backward_error(LS):

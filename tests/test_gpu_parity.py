@@ -42,7 +42,8 @@ def LS():
     return ls
 
 
-CASES = [(2, 16, 2.0), (2, 32, 4.0), (2, 64, 6.0), (3, 8, 1.0), (3, 16, 2.0)]
+# n = 48 (2D) and n = 24 (3D): FFT lengths 96 and 48 (radix-8/4/2 passes and one radix-3 pass)
+CASES = [(2, 16, 2.0), (2, 32, 4.0), (2, 64, 6.0), (2, 48, 5.0), (3, 8, 1.0), (3, 16, 2.0), (3, 24, 3.0)]
 
 
 @pytest.mark.parametrize("d,n,freq", CASES)
@@ -185,7 +186,7 @@ def test_plain_fp64_solve_matches_oracle_iterates():
     assert rel(u.reshape(1, -1), ref["u"]) < 1e-8
 
 
-@pytest.mark.parametrize("d,n,freq,nrhs", [(2, 64, 8.0, 4), (2, 128, 16.0, 3), (3, 16, 2.0, 3)])
+@pytest.mark.parametrize("d,n,freq,nrhs", [(2, 64, 8.0, 4), (2, 128, 16.0, 3), (3, 16, 2.0, 3), (3, 24, 3.0, 2)])
 @pytest.mark.parametrize("mixed", [False, True])
 def test_batched_solve(LS, d, n, freq, nrhs, mixed):
     omega = 2 * np.pi * freq
@@ -244,7 +245,7 @@ def test_errors_are_reported_not_raised_in_the_library(LS):
         LS.Solver(m, 10.0)
     assert e.value.status == LS.LS_EBUFFER
     with pytest.raises(LS.LsError) as e:
-        LS.Solver(np.zeros((24, 24)), 10.0)
+        LS.Solver(np.zeros((40, 40)), 10.0)  # 2n = 80: no FFT length of the library
     assert e.value.status == LS.LS_EINVAL
     m2 = np.zeros((n, n))
     m2[10, 10] = 1.5  # 1 - m <= 0

@@ -22,8 +22,9 @@ def LS():
 
 
 def test_served_results_equal_results_alone(LS):
-    stream = W.serving_stream(12, 1000.0, seed=11, grids=((2, 64), (2, 128), (3, 16)), weights=(0.4, 0.4, 0.2),
-                              max_dirs=6, pool=3)
+    # 3D n = 24 takes the radix-3 FFT passes (2n = 48), like the n = 48 grid of the bench's mix
+    stream = W.serving_stream(14, 1000.0, seed=11, grids=((2, 64), (2, 128), (3, 16), (3, 24)),
+                              weights=(0.35, 0.35, 0.15, 0.15), max_dirs=6, pool=3)
     reqs = [S.Request(i, d, n, om, m, dirs, t) for i, (d, n, om, m, dirs, t) in enumerate(stream)]
     be = S.LibBackend(mixed=True, tol=1e-6)
     res, st = S.Engine(be, slots=3, budget_bytes=2 << 30).run(reqs)

@@ -223,3 +223,29 @@ def test_3d_discrete_solution_converges_to_the_sphere_mie_series():
         errs.append(np.linalg.norm(res["u"][0].reshape((n,) * 3) - ue) / np.linalg.norm(ue))
     assert errs[0] < 0.08
     assert errs[1] < 0.45 * errs[0]
+
+
+def test_box_cavity_medium_and_its_iteration_counts():
+    """The smoothed square / cubic cavities of Sec. 3.3 (Figs. R22, R32): the velocity
+    c = (1 - m)^(-1/2) spans [2/3, 1] as the paper states, m is symmetric about the centre and
+    vanishes outside the smoothed box, and at 6 points per wavelength of the homogeneous
+    region the oracle's preconditioned GMRES stays within the band of the paper's tables and
+    does not grow with omega (qualitative, as for the bump)."""
+    with open(os.path.join(GOLDEN, "paper_rectangular_np.json")) as f:
+        tab = json.load(f)
+    hi = max(max(r["n_p"]) for r in tab["tables"])
+    for d, n in ((2, 64), (3, 12)):
+        m = W.box_cavity(n, d)
+        c = (1 - m) ** -0.5
+        assert abs(c.min() - 2 / 3) < 1e-12 and abs(c.max() - 1) < 1e-12
+        assert np.allclose(m, np.flip(m, axis=0)) and np.allclose(m, np.swapaxes(m, 0, d - 1))
+        x = W.grid_x(n)
+        outside = np.abs(x - 0.5) > 0.2 + 0.05
+        assert np.all(m[outside] == 0)
+    its = []
+    for n in (32, 64):
+        m = W.enforce_buffer(W.box_cavity(n, 2), 2)
+        res = O.solve(n, 2, 2 * np.pi * (n + 1) / 6, m, [(0.0, -1.0)])
+        its += res["iters"]
+    assert all(1 <= i <= hi + 4 for i in its), its
+    assert max(its) - min(its) <= 2, its
