@@ -659,8 +659,13 @@ def run_gpu(args):
     w = workload()
     step, dirs_dev, g, u = B.plane_wave_step(w)
 
-    # ---- mixed precision on the headline workload
+    # ---- mixed precision on the headline workload; the autotuner picks the launch shapes of
+    # its factorization and sweeps first (untimed; the choice also serves the later contexts
+    # of this grid and precision, e.g. the end-to-end ones)
     s_mix, setup_s = B.solver(w, True)
+    t0 = time.perf_counter()
+    tune = s_mix.autotune(w.nrhs)
+    tune_s = time.perf_counter() - t0
     nd = s_mix.nd_stats()
     # headline region: launches counted, replayed through the library's CUDA graphs
     total_ms, infos, prof, clocks = B.timed(s_mix, args.steps, args.warmup, step, clocks=True)
@@ -735,6 +740,8 @@ def run_gpu(args):
                                "iters": {"min": min(its64), "max": max(its64)}},
                 "mixed_over_fp64": value / value64, "configs": others, "laplace_3d": lap, "far_field": far,
                 "cufft": cufft, "serving": serving, "setup_ms": setup_s * 1e3, "nd": nd,
+                "autotune": {"choice": tune["choice"], "seconds": tune_s, "factor_ms": tune["factor_ms"],
+                             "solve_ms": tune["solve_ms"]},
                 "roofline": roof, "roofline_by_class": by_model, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
                 "launches_by_class": prof["counts"], "device_time_shares": shares, "clocks": clocks}

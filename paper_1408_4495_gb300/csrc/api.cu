@@ -520,7 +520,8 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
     }
     if (kmax > 0) {
       LS_CUDA(cudaMemcpyAsync(yd, Y.data(), Y.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
-      ls::update_u<CZ>((const CZ* const*)c->dZ, kmax, yd, R, u, N, nrhs, c->st);
+      if (mixed) ls::update_u_f((const float2* const*)c->dZ, kmax, yd, R, u, N, nrhs, c->st);
+      else ls::update_u<CZ>((const CZ* const*)c->dZ, kmax, yd, R, u, N, nrhs, c->st);
     }
     // residual r = g - A u in FP64 storage; the operator in float-float arithmetic on the
     // mixed path (GB300's FP64 rate is a small fraction of its FP32 rate), FP64 otherwise

@@ -358,6 +358,30 @@ __global__ void k_scale_f(const Cin* __restrict__ in, float2* out, const double*
   }
 }
 
+// u[rhs] += sum_j Z_j[rhs] y[rhs][j] for FP32 Z (mixed path): the sum in float-float on the
+// FP32 pipes, one FP64 add per component into u (the FP64 form of k_update_u spends four
+// FP64 FMAs per basis vector and component, at GB300's small FP64 rate)
+__global__ void k_update_u_f(const float2* const* __restrict__ Z, int nz, const double2* __restrict__ y, int ystride,
+                             double2* u, long N) {
+  const int rhs = blockIdx.y;
+  const double2* yr = y + (size_t)rhs * ystride;
+  const size_t base = (size_t)rhs * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    ffc acc;
+    acc.x = acc.y = ff(0);
+    for (int j = 0; j < nz; ++j) {
+      const float2 zv = Z[j][base + i];
+      const ffc h = ffc_from(yr[j]);
+      acc.x = acc.x + (ff_mul_f(h.x, zv.x) - ff_mul_f(h.y, zv.y));
+      acc.y = acc.y + (ff_mul_f(h.y, zv.x) + ff_mul_f(h.x, zv.y));
+    }
+    double2 v = u[base + i];
+    v.x += ff_to(acc.x);
+    v.y += ff_to(acc.y);
+    u[base + i] = v;
+  }
+}
+
 static dim3 grid_rows(long N, int nrhs) {
   long b = (N + 255) / 256;
   const long cap = (152L * 16 + nrhs - 1) / nrhs;
@@ -385,6 +409,11 @@ void sub_proj_f(const float2* const* V, int nv, const float2* win, float2* wout,
     LS_LAUNCH("kr_sub_proj", st,
               k_sub_proj_f<false><<<dim3(nblk, nrhs), KT, 0, st>>>(V, nv, win, wout, hf, hstride, N, partial, nblk));
   }
+}
+
+void update_u_f(const float2* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs,
+                cudaStream_t st) {
+  LS_LAUNCH("kr_update_u", st, k_update_u_f<<<grid_rows(N, nrhs), 256, 0, st>>>(Z, nz, y, ystride, u, N));
 }
 
 template <typename Cin> void scale_f(const Cin* in, float2* out, const double* s, long N, int nrhs, cudaStream_t st) {

@@ -33,6 +33,9 @@ void dots_f(const float2* const* V, int nv, const float2* w, long N, int nrhs, d
 void sub_proj_f(const float2* const* V, int nv, const float2* win, float2* wout, const ffc* hf, int hstride, long N,
                 int nrhs, double2* partial, double2* norm_out, int ostride, cudaStream_t st);
 template <typename Cin> void scale_f(const Cin* in, float2* out, const double* s, long N, int nrhs, cudaStream_t st);
+// u += sum_j Z_j y_j with FP32 Z, the sum in float-float
+void update_u_f(const float2* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs,
+                cudaStream_t st);
 // dst[i] = src[idx[i]] (gather) or dst[idx[i]] = src[i] (scatter) for i < n right-hand
 // sides of N entries each; idx on the device
 template <typename T> void rhs_gather(const T* src, T* dst, const int* idx, int n, long N, cudaStream_t st);
