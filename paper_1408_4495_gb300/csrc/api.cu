@@ -1453,8 +1453,9 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
     log += "], \"solve_ms\": [";
     double sb = solve_ms(best);
     log += "[" + std::to_string(best.sweep_ctas) + ", " + std::to_string(sb) + "]";
+    const int sweep_base = best.sweep_ctas;
     for (int v : {1, 2, 4}) {
-      if (v == best.sweep_ctas) continue;
+      if (v == sweep_base) continue;
       ls::NdTune t = best;
       t.sweep_ctas = v;
       const double sm = solve_ms(t);

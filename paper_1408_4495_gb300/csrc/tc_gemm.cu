@@ -15,8 +15,8 @@
 // (no-swizzle canonical layout: 8-row x 16-byte core matrices).  The K loop is a two-stage
 // pipeline over chunks of KC complex k: while the tensor core runs the MMAs of one chunk, the
 // threads convert the next chunk (held in registers) into the other operand stage (3xTF32
-// split, canonical layout) and load the chunk after it from global memory (coalesced:
-// consecutive threads on consecutive entries of a column).  One thread issues the MMAs and
+// split, canonical layout, conflict-free stores) and load the chunk after it from global
+// memory.  One thread issues the MMAs and
 // commits each chunk to its stage's mbarrier; 65 KB of shared memory, three CTAs per SM.  All
 // waits are bounded and set *err on expiry, and the tensor memory is freed only after the
 // last commit has been awaited.
@@ -153,21 +153,36 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
 
   const int K = a.k1 - a.k0;
   const int nchunk = (K + KC - 1) / KC;
-  // global loads of one chunk into registers: A 128 x KC (4 per thread, consecutive threads
-  // on consecutive rows of a column), B KC x 64 (2 per thread, consecutive threads on
-  // consecutive k of a column); issued one chunk ahead, while the tensor core works
+  // global loads of one chunk into registers.  Element u of a thread: idx = u * THREADS + tid,
+  // group idx / 32 of 32 entries = 8 consecutive rows (or B columns) x 4 consecutive k, lane
+  // bits 0-2 the row, bits 3-4 the k.  Its 32 shared-memory stores (8 bytes each) then fill
+  // 8 rows x 16 bytes of two neighbouring core matrices, 256 distinct bytes: no bank
+  // conflict; the global loads are 8-row (64-byte) runs of a column of A and 4-entry
+  // (32-byte) runs of a column of B
   constexpr int PA = TM * KC / THREADS, PB = NT * KC / THREADS;
   float2 va[PA], vb[PB];
+  auto a_of = [&](int u, int& m, int& k) {
+    const int idx = u * THREADS + tid, grp = idx >> 5, ln = idx & 31;
+    m = (grp >> 1) * 8 + (ln & 7);
+    k = (grp & 1) * 4 + (ln >> 3);
+  };
+  auto b_of = [&](int u, int& n, int& k) {
+    const int idx = u * THREADS + tid, grp = idx >> 5, ln = idx & 31;
+    n = (grp >> 1) * 8 + (ln & 7);
+    k = (grp & 1) * 4 + (ln >> 3);
+  };
   auto load = [&](int kc) {
     const int kw = min(KC, K - kc);
 #pragma unroll
     for (int u = 0; u < PA; ++u) {
-      const int e = tid + u * THREADS, m = e % TM, k = e / TM;
+      int m, k;
+      a_of(u, m, k);
       va[u] = (k < kw && rb + m < a.r1) ? F[(size_t)(a.k0 + kc + k) * fmax + rb + m] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
-      const int e = tid + u * THREADS, k = e % KC, n = e / KC;
+      int n, k;
+      b_of(u, n, k);
       vb[u] = (k < kw && cb + n < a.c1) ? F[(size_t)(cb + n) * fmax + a.k0 + kc + k] : make_float2(0.f, 0.f);
     }
   };
@@ -181,7 +196,8 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
     unsigned char* Blo = Bhi + B_BYTES;
 #pragma unroll
     for (int u = 0; u < PA; ++u) {
-      const int e = tid + u * THREADS, m = e % TM, k = e / TM;
+      int m, k;
+      a_of(u, m, k);
       const float2 v = va[u];
       const int kr = 2 * k;  // real k within the chunk
       const int s = kr / KSTEP, kk = kr % KSTEP;
@@ -193,7 +209,8 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
     }
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
-      const int e = tid + u * THREADS, k = e % KC, n = e / KC;
+      int n, k;
+      b_of(u, n, k);
       const float re = vb[u].x, im = vb[u].y;
       const int kr = 2 * k, s = kr / KSTEP, kk = kr % KSTEP;
       const uint32_t hre = to_tf32(re), him = to_tf32(im), hnim = to_tf32(-im);
