@@ -1948,6 +1948,9 @@ template <typename C> struct SweepK {
                      // order by the CTA that finishes last
   int ksz;           // columns per range
   int kv;            // items of the vector operand held in shared memory at once
+  int ng;            // groups of RC right-hand sides: the CTAs of one front's groups are
+                     // adjacent in the grid (x = front * ng + group), so that its factor tile
+                     // is read from DRAM once and from L2 by the other groups
   C* part;           // nsplit > 1: partial sums [item][nsplit][tile rows x RC]
   unsigned* cnt;     // nsplit > 1: CTAs finished per item (the last one resets it)
   long N;
@@ -2037,8 +2040,8 @@ __device__ __forceinline__ void sweep_gather(const SweepK<C>& S, int z, int g, i
   }
 }
 
-// One level of either sweep.  grid (fronts, row tiles x column ranges, groups of RC
-// right-hand sides); the kg warps split the columns of each chunk and add their partial
+// One level of either sweep.  grid (fronts x groups of RC right-hand sides, row tiles x
+// column ranges); the kg warps split the columns of each chunk and add their partial
 // sums in a fixed order.  Forward rows are the ring rows of Y (the identity columns of the
 // augmented front); backward rows are the own rows of [H | F11^{-1}].
 template <typename C, int RC, int TR, int MODE> __global__ void __launch_bounds__(256) k_sweep(SweepK<C> S) {
@@ -2046,7 +2049,7 @@ template <typename C, int RC, int TR, int MODE> __global__ void __launch_bounds_
   __shared__ int last_s;
   constexpr int KA = sweep_ka<C>();
   constexpr int RCT = RC * TR / 32;
-  const int z = blockIdx.x, g = blockIdx.z;
+  const int z = blockIdx.x / S.ng, g = blockIdx.x - (blockIdx.x / S.ng) * S.ng;
   const int tile = blockIdx.y / S.nsplit, sp = blockIdx.y - tile * S.nsplit;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, kg = blockDim.x >> 5, NT = blockDim.x;
   const int row = TR == 32 ? lane : (lane & 15);
@@ -2302,10 +2305,11 @@ static void launch_sweep_tr(NdPlan* p, int l, C* T, int ng, const SweepPlan& q, 
   S.nsplit = q.nsplit;
   S.ksz = q.ksz;
   S.kv = sh.kv;
+  S.ng = ng;
   S.part = reinterpret_cast<C*>(p->part);
   S.cnt = p->cnt;
   S.N = p->N;
-  const dim3 grid(D.nf, q.ntile * q.nsplit, ng);
+  const dim3 grid((unsigned)((long)D.nf * ng), q.ntile * q.nsplit, 1);
   const bool f32 = sizeof(C) == 8;
   LS_LAUNCH(MODE == 0 ? (f32 ? "nd_fwd_c64" : "nd_fwd_c128") : (f32 ? "nd_bwd_c64" : "nd_bwd_c128"), st,
             launch_pdl(k_sweep<C, RC, TR, MODE>, grid, dim3(32 * sh.kg), sh.smem, st, S));
