@@ -323,9 +323,17 @@ def algorithmic_bytes(cls, w, nd, counts, steps, rhs=None):
 
 # ncu DRAM traffic per launch of a kernel class on the headline workload, valid while the
 # kernel's source is unchanged: the sha1 of its source region (the text between two markers
-# of the file) and of the headers it includes, taken when the counters were captured (see
-# profiles/); empty until such a capture exists
-TRAFFIC = {}
+# of the file) and of the header it includes for its arithmetic, taken when the counters
+# were captured (profiles/nd_sweep_2d_n1024_64rhs.md).  "rhs": the right-hand sides per launch
+# of the capture; the line scales the bytes to the live count of the timed launches with the
+# byte model's ratio (factor bytes fixed, vector bytes in proportion).
+SWEEP_SRC = [("paper_1408_4495_gb300/csrc/nd.cu", "template <typename C> struct SweepK {",
+              "// r[rhs][N] -> T[group][N][RC]"),
+             ("paper_1408_4495_gb300/csrc/common.cuh", None, None)]
+TRAFFIC = {
+    "nd_fwd_c64": {"src": SWEEP_SRC, "sha1": "585ffbaf4171a5971b2ff24b4904261772a51999", "bytes": 345.26e6, "rhs": 64},
+    "nd_bwd_c64": {"src": SWEEP_SRC, "sha1": "585ffbaf4171a5971b2ff24b4904261772a51999", "bytes": 207.37e6, "rhs": 64},
+}
 
 
 def source_sha1(src):
@@ -344,13 +352,18 @@ def source_sha1(src):
     return h.hexdigest()
 
 
-def recorded_traffic(cls):
+def recorded_traffic(cls, w=None, nd=None, rhs=None):
+    """Recorded DRAM bytes per launch of a class, scaled to ``rhs`` right-hand sides per
+    launch by the byte model; None when there is no record or the kernel changed since."""
     rec = TRAFFIC.get(cls)
     if not rec or not rec["sha1"]:
         return None
     if source_sha1(rec["src"]) != rec["sha1"]:
         return None
-    return rec["bytes"]
+    if w is None or rhs is None:
+        return rec["bytes"]
+    return rec["bytes"] * algorithmic_bytes(cls, w, nd, None, None, rhs=rhs) / \
+        algorithmic_bytes(cls, w, nd, None, None, rhs=rec["rhs"])
 
 
 class GpuBench:
@@ -447,7 +460,10 @@ class GpuBench:
         if cls and cls in by_model:
             bm = by_model[cls]
             roof = {"kernel": cls, "bound": "hbm", "achieved": bm["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                    "frac": bm["achieved_gbs"] / peak, "traffic": recorded_traffic(cls), "peak_source": peak_src,
+                    "frac": bm["achieved_gbs"] / peak, "traffic": recorded_traffic(cls, w, nd, r_live),
+                    "traffic_note": "ncu dram__bytes_read + write per launch, captured with 64 right-hand sides per "
+                                    "launch and scaled to the live count by the byte model",
+                    "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": bm["algorithmic_bytes_per_launch"],
                     "avg_launch_us": bm["avg_launch_us"], "launches_timed": bm["launches"], "steps_timed": steps,
                     "share_of_kernel_time": bm["share"], "live_rhs_per_iteration": r_live,

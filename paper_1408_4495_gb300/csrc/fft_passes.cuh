@@ -38,7 +38,13 @@ template <> constexpr const char* arith_tag<ffc>() { return "cff"; }
 // Padded shared-memory index: one spare slot every 8 complex entries keeps the strided
 // Stockham writes (stride R = 8 in the first pass) free of bank conflicts.
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
-template <int L> struct Lay { static constexpr int LS = L + L / 8 + 1; };
+template <int L> struct Lay {
+  static constexpr int LS = L + L / 8 + 1;
+  // column passes: TC lines side by side, filled and drained by warps that cover 4 entries
+  // of 8 lines; a stride of 2 (mod 16) complex entries puts those 8 lines 4 banks apart, so
+  // that the 16 entries of a half-warp fall on distinct banks
+  static constexpr int LSC = L + L / 8 + ((L + L / 8) % 16 == 0 ? 2 : 1);
+};
 
 template <int SIGN, typename C> __device__ __forceinline__ C rot_i(C a) {
   C r;
@@ -121,9 +127,8 @@ template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR(C* v
 // Pass input: sub-transforms of length NS; output: sub-transforms of length NS * R.
 // Butterfly j of a line reads entries j + r L/R, multiplies by w^{r k} with
 // w = exp(SIGN 2 pi i / (NS R)), k = j mod NS, and writes (j / NS) NS R + k + r NS.
-template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT>
+template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT, int LS = Lay<L>::LS>
 __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
-  constexpr int LS = Lay<L>::LS;
   constexpr int BPL = L / R;
   constexpr int BF = NLINES * BPL;
   constexpr int PER = (BF + NT - 1) / NT;
@@ -165,14 +170,14 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
 }
 
 // Radices 8, then 4 or 2 for the rest of the power of two, then 3 for L = 3 * 2^k.
-template <typename C, int L, int NS, int SIGN, int NLINES, int NT>
+template <typename C, int L, int NS, int SIGN, int NLINES, int NT, int LS = Lay<L>::LS>
 __device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw) {
   if constexpr (NS < L) {
     constexpr int REM = L / NS;
     constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
     static_assert(REM % R == 0, "FFT length must be 2^k or 3 * 2^k");
-    fft_pass<C, L, R, NS, SIGN, NLINES, NT>(s, tw);
-    fft_lines<C, L, NS * R, SIGN, NLINES, NT>(s, tw);
+    fft_pass<C, L, R, NS, SIGN, NLINES, NT, LS>(s, tw);
+    fft_lines<C, L, NS * R, SIGN, NLINES, NT, LS>(s, tw);
   }
 }
 
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
 // ------------------------------------------------------------------------------------
 template <typename C, int L, int MODE>
 __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) {
-  constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC, LS = Lay<L>::LS;
+  constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC, LS = Lay<L>::LSC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
@@ -367,11 +372,11 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
   }
   __syncthreads();
   if constexpr (MODE == 0) {
-    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT, LS>(s, tw);
   } else if constexpr (MODE == 1) {
-    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT, LS>(s, tw);
   } else {
-    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT, LS>(s, tw);
     const C* __restrict__ sym = reinterpret_cast<const C*>(a.sym);
     const int n1 = a.n + 1;
     // symbol values of SB entries loaded together, then applied
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
       }
     }
     __syncthreads();
-    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT, LS>(s, tw);
   }
   C* out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
   const int n_out = a.n_out;
@@ -437,7 +442,7 @@ template <typename C, int L, int SIGN> void launch_row_L(const RowPassArgs& a, c
 
 template <typename C, int L, int MODE> void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
   constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
-  const size_t smem = (size_t)TC * Lay<L>::LS * sizeof(C);
+  const size_t smem = (size_t)TC * Lay<L>::LSC * sizeof(C);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_col_pass<C, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
