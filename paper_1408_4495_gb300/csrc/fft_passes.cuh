@@ -19,6 +19,60 @@ namespace ls {
 
 template <> struct RealOf<ffc> { using T = ff; };
 
+// Float-float arithmetic inside the passes, with renormalisation deferred: an add keeps the
+// exact TwoSum of the leading parts and adds the trailing parts without the final
+// fast-TwoSum (8 FP32 operations instead of 11), a product keeps the FMA TwoProduct and the
+// cross terms without it (4 instead of 7).  The pair then is an exact unevaluated sum whose
+// trailing part may exceed half an ulp of the leading one; every value is renormalised when a
+// pass stores it to shared memory, so within one radix pass the trailing part stays below
+// about 2^-21 of the leading one and the dropped lo * lo term below 2^-42 relative.
+__device__ __forceinline__ ff lz_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff lz_neg(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff lz_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff(p, e);
+}
+__device__ __forceinline__ ff lz_norm(ff a) { return ff_fast_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ ffc cadd(ffc a, ffc b) {
+  ffc r;
+  r.x = lz_add(a.x, b.x);
+  r.y = lz_add(a.y, b.y);
+  return r;
+}
+__device__ __forceinline__ ffc csub(ffc a, ffc b) {
+  ffc r;
+  r.x = lz_add(a.x, lz_neg(b.x));
+  r.y = lz_add(a.y, lz_neg(b.y));
+  return r;
+}
+__device__ __forceinline__ ffc cmul(ffc a, ffc b) {
+  ffc r;
+  r.x = lz_add(lz_mul(a.x, b.x), lz_neg(lz_mul(a.y, b.y)));
+  r.y = lz_add(lz_mul(a.x, b.y), lz_mul(a.y, b.x));
+  return r;
+}
+// real helpers of the butterflies: plain arithmetic, deferred float-float for ff
+template <typename Rl> __device__ __forceinline__ Rl r_mul(Rl a, Rl b) { return a * b; }
+template <> __device__ __forceinline__ ff r_mul<ff>(ff a, ff b) { return lz_mul(a, b); }
+template <typename Rl> __device__ __forceinline__ Rl r_add(Rl a, Rl b) { return a + b; }
+template <> __device__ __forceinline__ ff r_add<ff>(ff a, ff b) { return lz_add(a, b); }
+template <typename Rl> __device__ __forceinline__ Rl r_sub(Rl a, Rl b) { return a - b; }
+template <> __device__ __forceinline__ ff r_sub<ff>(ff a, ff b) { return lz_add(a, lz_neg(b)); }
+template <typename Rl> __device__ __forceinline__ Rl r_neg(Rl a) { return -a; }
+template <> __device__ __forceinline__ ff r_neg<ff>(ff a) { return lz_neg(a); }
+template <typename C> __device__ __forceinline__ C c_norm(C v) { return v; }
+template <> __device__ __forceinline__ ffc c_norm<ffc>(ffc v) {
+  v.x = lz_norm(v.x);
+  v.y = lz_norm(v.y);
+  return v;
+}
+
 // read-only cached load of one complex entry
 template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
 template <> __device__ __forceinline__ ffc ldg_c<ffc>(const ffc* p) {
@@ -84,9 +138,17 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft8v(C* v) {
   dft4<SIGN>(o0, o1, o2, o3);
   // o_q *= W8^q, W8 = exp(SIGN 2 pi i / 8)
   C t;
-  t.x = c * (o1.x - SIGN * o1.y); t.y = c * (SIGN * o1.x + o1.y); o1 = t;
+  if (SIGN > 0) {
+    t.x = r_mul(c, r_sub(o1.x, o1.y)); t.y = r_mul(c, r_add(o1.x, o1.y)); o1 = t;
+  } else {
+    t.x = r_mul(c, r_add(o1.x, o1.y)); t.y = r_mul(c, r_sub(o1.y, o1.x)); o1 = t;
+  }
   o2 = rot_i<SIGN>(o2);
-  t.x = c * (-o3.x - SIGN * o3.y); t.y = c * (SIGN * o3.x - o3.y); o3 = t;
+  if (SIGN > 0) {
+    t.x = r_neg(r_mul(c, r_add(o3.x, o3.y))); t.y = r_mul(c, r_sub(o3.x, o3.y)); o3 = t;
+  } else {
+    t.x = r_mul(c, r_sub(o3.y, o3.x)); t.y = r_neg(r_mul(c, r_add(o3.x, o3.y))); o3 = t;
+  }
   v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
   v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
   v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
@@ -106,10 +168,10 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft3v(C* v) {
   const Rl s3 = sin_pi3<Rl>(), half = one_half<Rl>();
   const C a = v[0], t = cadd(v[1], v[2]);
   C m, d = csub(v[1], v[2]);
-  m.x = a.x - half * t.x;
-  m.y = a.y - half * t.y;
-  d.x = s3 * d.x;
-  d.y = s3 * d.y;
+  m.x = r_sub(a.x, r_mul(half, t.x));
+  m.y = r_sub(a.y, r_mul(half, t.y));
+  d.x = r_mul(s3, d.x);
+  d.y = r_mul(s3, d.y);
   const C r = rot_i<SIGN>(d);
   v[0] = cadd(a, t);
   v[1] = cadd(m, r);
@@ -163,7 +225,7 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
       const int k = j % NS;
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sl[pidx(base + r * NS)] = v[q][r];
+      for (int r = 0; r < R; ++r) sl[pidx(base + r * NS)] = c_norm(v[q][r]);
     }
   }
   __syncthreads();
