@@ -91,4 +91,57 @@ __host__ __device__ __forceinline__ ffc ffc_from(double2 v) {
 }
 __host__ __device__ __forceinline__ double2 ffc_to(ffc v) { return make_double2(ff_to(v.x), ff_to(v.y)); }
 
+// Conversions between FP64 and FP32 pairs on the integer and FP32 pipes.  GB300 runs FP64
+// instructions (conversions to and from FP64 among them) at a small fraction of its FP32
+// rate, so a streaming kernel that converts every element through FP64 is bound by them.
+// Both are written from the IEEE 754 binary32 / binary64 layouts (1 sign, 8 / 11 exponent
+// and 23 / 52 fraction bits, exponent biases 127 / 1023).
+
+// the exact FP64 value of an FP32 number: normal numbers by moving the fields, zeros, FP32
+// subnormals, infinities and NaNs by the FP64 conversion
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long exp = (unsigned long long)(e + (1023u - 127u)) << 52;
+    const unsigned long long frac = (unsigned long long)(b & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(sign | exp | frac));
+  }
+  if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)(b >> 31) << 63));
+  return (double)f;
+}
+// hi + lo of a float-float as FP64: one FP64 add (exact when the pair is normalized)
+__device__ __forceinline__ double ff_to_f64(ff a) { return f64_of(a.hi) + f64_of(a.lo); }
+__device__ __forceinline__ double2 ffc_to_f64(ffc v) { return make_double2(ff_to_f64(v.x), ff_to_f64(v.y)); }
+
+// an FP64 number as a float-float: hi = its leading 24 significant bits (truncated), lo =
+// the next 23 bits (truncated), so |x - (hi + lo)| < 2^-46 |x|; lo is built as an exact
+// FP32 integer (the magic-number form) scaled by a power of two.  Outside
+// 2^-74 <= |x| < 2^128 (where lo or hi would leave the FP32 normal range) and for
+// infinities and NaNs the FP64 conversion is used; zeros stay zeros.  |lo| may reach
+// ulp(hi) rather than ulp(hi) / 2: the operations above take such pairs as they are.
+__device__ __forceinline__ ff ff_of_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  if (e == 0u) return ff(__uint_as_float(sign), 0.f);
+  if (e - 949u < 1150u - 949u + 1u) {
+    const unsigned hi = sign | ((e - (1023u - 127u)) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+    const unsigned r = (unsigned)(b >> 6) & 0x7fffffu;  // fraction bits 28..6
+    // r as an FP32 integer: 2^23 + r has the exponent field of 2^23 and fraction r
+    const float rf = __fsub_rn(__uint_as_float(0x4b000000u | r), 8388608.0f);
+    // lo = r * 2^(E - 46), E = e - 1023 the unbiased exponent of x
+    const float scale = __uint_as_float((e - (1023u + 46u - 127u)) << 23);
+    return ff(__uint_as_float(hi), __uint_as_float(__float_as_uint(__fmul_rn(rf, scale)) | sign));
+  }
+  return ff_from(x);
+}
+__device__ __forceinline__ ffc ffc_of_f64(double2 v) {
+  ffc r;
+  r.x = ff_of_f64(v.x);
+  r.y = ff_of_f64(v.y);
+  return r;
+}
+
 }  // namespace ls

@@ -89,15 +89,40 @@ template <> constexpr const char* arith_tag<float2>() { return "c64"; }
 template <> constexpr const char* arith_tag<double2>() { return "c128"; }
 template <> constexpr const char* arith_tag<ffc>() { return "cff"; }
 
-// Padded shared-memory index: one spare slot every 8 complex entries keeps the strided
-// Stockham writes (stride R = 8 in the first pass) free of bank conflicts.
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
-template <int L> struct Lay {
-  static constexpr int LS = L + L / 8 + 1;
-  // column passes: TC lines side by side, filled and drained by warps that cover 4 entries
-  // of 8 lines; a stride of 2 (mod 16) complex entries puts those 8 lines 4 banks apart, so
-  // that the 16 entries of a half-warp fall on distinct banks
-  static constexpr int LSC = L + L / 8 + ((L + L / 8) % 16 == 0 ? 2 : 1);
+// Shared-memory layout of the LINES lines of a CTA: line-major without padding; inside
+// each 128-byte row of E entries (E = 16 FP32 complex or 8 16-byte entries) the entry
+// position is XORed with a function h of the row index and the line (a bank swizzle).  A
+// warp's accesses then fall on distinct banks in every pass (modelled per half-warp for
+// 8-byte and per quarter-warp for 16-byte entries, the units in which shared memory serves
+// them):
+//   - loads of consecutive entries, and stores at Stockham strides NS >= E, stay inside
+//     whole rows, which the XOR permutes;
+//   - the stride-R stores of the first pass (NS = 1) spread over R rows: h's low bits
+//     follow the row index, so they land on distinct positions;
+//   - the NS = 8 stores (8-byte entries) take two rows R / 2 or 4 apart for the two halves
+//     of a half-warp: h's bit 3 carries the parity of the row's low three bits, so the
+//     halves differ in it;
+//   - h depends on the row's low three bits only, so entries 8 E apart (multiples of whole
+//     8-row blocks) share it: a thread's R accesses at such strides take one swizzle and
+//     constant offsets, which keeps the address arithmetic (and registers) of the long
+//     passes at the level of a plain layout;
+//   - column fill, symbol multiply and drain touch E / LINES entries of each line at once:
+//     the line term shifts the lines E / LINES positions apart.
+// Padding one entry in every 8 instead keeps the first pass's strided stores apart but
+// makes every run of 16 consecutive 8-byte entries wrap onto its own banks (67 % extra
+// shared-memory wavefronts in the FP32 column pass of L = 2048, measured with ncu).
+template <typename C, int L, int LINES> struct SLay {
+  static constexpr int E = 128 / (int)sizeof(C);
+  static constexpr int KC = E / LINES > 1 ? E / LINES : 1;
+  static constexpr int SIZE = LINES * L;  // entries
+  static_assert(L % E == 0, "line length must be a multiple of the swizzle row");
+  __host__ __device__ static constexpr bool shift_free(int stride) { return stride % (8 * E) == 0; }
+  __device__ static __forceinline__ int off(int line, int i) {
+    const int row = (i / E) & 7;
+    int h = row ^ (line * KC);
+    if constexpr (E == 16) h ^= ((row ^ (row >> 1) ^ (row >> 2)) & 1) << 3;
+    return line * L + (i & ~(E - 1)) + ((i ^ h) & (E - 1));
+  }
 };
 
 template <int SIGN, typename C> __device__ __forceinline__ C rot_i(C a) {
@@ -189,8 +214,9 @@ template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR(C* v
 // Pass input: sub-transforms of length NS; output: sub-transforms of length NS * R.
 // Butterfly j of a line reads entries j + r L/R, multiplies by w^{r k} with
 // w = exp(SIGN 2 pi i / (NS R)), k = j mod NS, and writes (j / NS) NS R + k + r NS.
-template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT, int LS = Lay<L>::LS>
+template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT>
 __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
+  using SL = SLay<C, L, NLINES>;
   constexpr int BPL = L / R;
   constexpr int BF = NLINES * BPL;
   constexpr int PER = (BF + NT - 1) / NT;
@@ -200,9 +226,14 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
     const int b = threadIdx.x + q * NT;
     if (BF % NT == 0 || b < BF) {
       const int line = b / BPL, j = b - line * BPL;
-      const C* sl = s + line * LS;
+      if constexpr (SL::shift_free(BPL)) {
+        const int o = SL::off(line, j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = sl[pidx(j + r * BPL)];
+        for (int r = 0; r < R; ++r) v[q][r] = s[o + r * BPL];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = s[SL::off(line, j + r * BPL)];
+      }
       if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -221,25 +252,30 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
     const int b = threadIdx.x + q * NT;
     if (BF % NT == 0 || b < BF) {
       const int line = b / BPL, j = b - line * BPL;
-      C* sl = s + line * LS;
       const int k = j % NS;
       const int base = (j / NS) * NS * R + k;
+      if constexpr (SL::shift_free(NS)) {
+        const int o = SL::off(line, base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) sl[pidx(base + r * NS)] = c_norm(v[q][r]);
+        for (int r = 0; r < R; ++r) s[o + r * NS] = c_norm(v[q][r]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[SL::off(line, base + r * NS)] = c_norm(v[q][r]);
+      }
     }
   }
   __syncthreads();
 }
 
 // Radices 8, then 4 or 2 for the rest of the power of two, then 3 for L = 3 * 2^k.
-template <typename C, int L, int NS, int SIGN, int NLINES, int NT, int LS = Lay<L>::LS>
+template <typename C, int L, int NS, int SIGN, int NLINES, int NT>
 __device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw) {
   if constexpr (NS < L) {
     constexpr int REM = L / NS;
     constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
     static_assert(REM % R == 0, "FFT length must be 2^k or 3 * 2^k");
-    fft_pass<C, L, R, NS, SIGN, NLINES, NT, LS>(s, tw);
-    fft_lines<C, L, NS * R, SIGN, NLINES, NT, LS>(s, tw);
+    fft_pass<C, L, R, NS, SIGN, NLINES, NT>(s, tw);
+    fft_lines<C, L, NS * R, SIGN, NLINES, NT>(s, tw);
   }
 }
 
@@ -250,13 +286,13 @@ template <int L> struct RowShape {
   static constexpr int NT = (L / 8 > 256) ? L / 8 : 256;
   static constexpr int NL = NT * 8 / L;
 };
-// TC adjacent lines per CTA (about 64 KB of shared memory); FP32 lines of 512 and more
-// take 8 lines (64-byte runs of each row) and 2 butterflies per thread (measured on 2D
-// n = 1024: 4 lines, 32-byte runs and three CTAs per SM, is 30 % slower)
+// TC adjacent lines per CTA (about 64 KB of shared memory); FP32 lines of 512 to 2048
+// take 8 lines (64-byte runs of each row; measured on 2D n = 1024: 4 lines, 32-byte runs
+// and three CTAs per SM, is 30 % slower), lines of 4096 take 4 (8 would need 256 KB)
 template <typename C, int L> struct ColShape {
   static constexpr int raw = 65536 / (L * (int)sizeof(C));
   static constexpr bool f32_long = sizeof(C) == 8 && L >= 512;
-  static constexpr int TC = f32_long ? 8 : (raw < 2 ? 2 : (raw > 16 ? 16 : raw));
+  static constexpr int TC = f32_long ? (L <= 2048 ? 8 : 4) : (raw < 2 ? 2 : (raw > 16 ? 16 : raw));
   static constexpr int t = f32_long ? TC * L / 16 : TC * L / 8;
   static constexpr int NT = t > 512 ? 512 : (t < 64 ? 64 : t);
 };
@@ -266,7 +302,8 @@ template <typename C, int L> struct ColShape {
 // ------------------------------------------------------------------------------------
 template <typename C, int L, int SIGN>
 __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
-  constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL, LS = Lay<L>::LS;
+  constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL;
+  using SL = SLay<C, L, NL>;
   using Rl = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -294,7 +331,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
           const long line = line0 + li;
           if (line < a.lines) {
             if constexpr (std::is_same<C, ffc>::value) {
-              v[u] = a.in64 ? ffc_from(reinterpret_cast<const double2*>(a.in)[line * a.in_ls + e])
+              v[u] = a.in64 ? ffc_of_f64(reinterpret_cast<const double2*>(a.in)[line * a.in_ls + e])
                             : in[line * a.in_ls + e];
             } else {
               v[u] = in[line * a.in_ls + e];
@@ -311,7 +348,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
           C x = v[u];
           x.x *= wv[u];
           x.y *= wv[u];
-          s[li * LS + pidx(e)] = x;
+          s[SL::off(li, e)] = x;
         }
       }
     }
@@ -350,13 +387,13 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
         }
       }
     }
-    s[li * LS + pidx(e)] = v;
+    s[SL::off(li, e)] = v;
   }
   if (n_in < L) {
     const int padn = L - n_in;
     for (int idx = threadIdx.x; idx < NL * padn; idx += NT) {
       const int li = idx / padn, e = n_in + (idx - li * padn);
-      s[li * LS + pidx(e)] = czero<C>();
+      s[SL::off(li, e)] = czero<C>();
     }
   }
   __syncthreads();
@@ -368,11 +405,11 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
     const int li = idx / n_out, e = idx - li * n_out;
     const long line = line0 + li;
     if (line < a.lines) {
-      C v = s[li * LS + pidx(e)];
+      C v = s[SL::off(li, e)];
       if constexpr (std::is_same<C, ffc>::value) {
         if (a.out64) {
           // FP64 epilogue: y = v + addv, or y = subv - (v + addv)
-          double2 o = ffc_to(v);
+          double2 o = ffc_to_f64(v);
           if (a.addv != nullptr) o = cadd(o, reinterpret_cast<const double2*>(a.addv)[line * a.add_ls + e]);
           if (a.subv != nullptr) o = csub(reinterpret_cast<const double2*>(a.subv)[line * a.add_ls + e], o);
           reinterpret_cast<double2*>(a.out)[line * a.out_ls + e] = o;
@@ -391,7 +428,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
 // ------------------------------------------------------------------------------------
 template <typename C, int L, int MODE>
 __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) {
-  constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC, LS = Lay<L>::LSC;
+  constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
+  using SL = SLay<C, L, TC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
@@ -420,7 +458,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
         const int idx = base + u * NT;
         if (idx < tot) {
           const int e = idx / TC, c = idx - e * TC;
-          s[c * LS + pidx(e)] = v[u];
+          s[SL::off(c, e)] = v[u];
         }
       }
     }
@@ -429,16 +467,16 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
     const int padn = L - n_in;
     for (int idx = threadIdx.x; idx < padn * TC; idx += NT) {
       const int e = n_in + idx / TC, c = idx % TC;
-      s[c * LS + pidx(e)] = czero<C>();
+      s[SL::off(c, e)] = czero<C>();
     }
   }
   __syncthreads();
   if constexpr (MODE == 0) {
-    fft_lines<C, L, 1, -1, TC, NT, LS>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
   } else if constexpr (MODE == 1) {
-    fft_lines<C, L, 1, 1, TC, NT, LS>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
   } else {
-    fft_lines<C, L, 1, -1, TC, NT, LS>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
     const C* __restrict__ sym = reinterpret_cast<const C*>(a.sym);
     const int n1 = a.n + 1;
     // symbol values of SB entries loaded together, then applied
@@ -469,19 +507,19 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
         const int idx = base + u * NT;
         const int e = idx / TC, c = idx - e * TC;
         if (idx < L * TC && c0 + c < a.inner) {
-          C& v = s[c * LS + pidx(e)];
+          C& v = s[SL::off(c, e)];
           v = cmul(v, sv[u]);
         }
       }
     }
     __syncthreads();
-    fft_lines<C, L, 1, 1, TC, NT, LS>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
   }
   C* out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
   const int n_out = a.n_out;
   for (int idx = threadIdx.x; idx < n_out * TC; idx += NT) {
     const int e = idx / TC, c = idx - e * TC;
-    if (c0 + c < a.inner) out[(long)e * a.out_es + c] = s[c * LS + pidx(e)];
+    if (c0 + c < a.inner) out[(long)e * a.out_es + c] = s[SL::off(c, e)];
   }
 }
 
@@ -490,7 +528,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) 
 // ------------------------------------------------------------------------------------
 template <typename C, int L, int SIGN> void launch_row_L(const RowPassArgs& a, cudaStream_t st) {
   constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL;
-  const size_t smem = (size_t)NL * Lay<L>::LS * sizeof(C);
+  const size_t smem = (size_t)SLay<C, L, NL>::SIZE * sizeof(C);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_row_pass<C, L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -504,7 +542,7 @@ template <typename C, int L, int SIGN> void launch_row_L(const RowPassArgs& a, c
 
 template <typename C, int L, int MODE> void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
   constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
-  const size_t smem = (size_t)TC * Lay<L>::LSC * sizeof(C);
+  const size_t smem = (size_t)SLay<C, L, TC>::SIZE * sizeof(C);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_col_pass<C, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

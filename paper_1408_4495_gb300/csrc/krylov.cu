@@ -236,7 +236,7 @@ __device__ __forceinline__ ffc ffc_of(float2 v) {
   r.y = ff(v.y, 0.f);
   return r;
 }
-__device__ __forceinline__ ffc ffc_of(double2 v) { return ffc_from(v); }
+__device__ __forceinline__ ffc ffc_of(double2 v) { return ffc_of_f64(v); }
 
 // the exact product of two FP32 numbers as a float-float (FMA TwoProduct)
 __device__ __forceinline__ ff ff_prod(float a, float b) {
@@ -277,10 +277,17 @@ __device__ void store_ff_pair(void* outf, size_t i, double2 v) {
   *reinterpret_cast<float4*>(reinterpret_cast<ffc*>(outf) + i) = make_float4(f.x.hi, f.x.lo, f.y.hi, f.y.lo);
 }
 
-constexpr int JB = 4;  // basis vectors per pass over w
+constexpr int JB = 4;   // basis vectors per pass over w
+constexpr int RUN = 4;  // elements per thread summed in FP32 before a float-float add
 
 // partial[(rhs * nv + j) * nblk + blk] = sum over the block's chunk of conj(V_j) w, JB
-// vectors per pass over the chunk
+// vectors per pass over the chunk.  Each thread sums the products of RUN of its elements
+// with FP32 FMAs (error at most about RUN u times the sum of their magnitudes, u = 2^-24)
+// and adds the run into a float-float accumulator, so that the error of a coefficient
+// stays near RUN u |V_j| |w| however long the vectors are.  Such an error only leaves a
+// component of that size along V_j in the projected vector, which CGS2's second pass
+// removes; the Arnoldi relation holds with the coefficients as computed, because the
+// projection itself (k_sub_proj_f) runs in float-float.
 __global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__ V, int nv, const float2* __restrict__ w,
                                                long N, double2* __restrict__ partial, int nblk) {
   __shared__ double2 sh[KT / 32];
@@ -293,14 +300,29 @@ __global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__
     ffc acc[JB];
 #pragma unroll
     for (int q = 0; q < JB; ++q) acc[q].x = acc[q].y = ff(0);
-    for (long i = i0 + threadIdx.x; i < i1; i += KT) {
-      const float2 b = w[base + i];
+    for (long i = i0 + threadIdx.x; i < i1; i += (long)KT * RUN) {
+      float2 sr[JB];
+#pragma unroll
+      for (int q = 0; q < JB; ++q) sr[q] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) {
+        const long e = i + (long)u * KT;
+        if (e < i1) {
+          const float2 b = w[base + e];
+#pragma unroll
+          for (int q = 0; q < JB; ++q)
+            if (q < nj) {
+              const float2 a = V[jg + q][base + e];
+              sr[q].x = __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, sr[q].x));
+              sr[q].y = __fmaf_rn(a.x, b.y, __fmaf_rn(-a.y, b.x, sr[q].y));
+            }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < JB; ++q)
         if (q < nj) {
-          const float2 a = V[jg + q][base + i];
-          acc[q].x = acc[q].x + (ff_prod(a.x, b.x) + ff_prod(a.y, b.y));
-          acc[q].y = acc[q].y + (ff_prod(a.x, b.y) - ff_prod(a.y, b.x));
+          acc[q].x = acc[q].x + ff(sr[q].x, 0.f);
+          acc[q].y = acc[q].y + ff(sr[q].y, 0.f);
         }
     }
 #pragma unroll
@@ -348,7 +370,7 @@ __global__ void __launch_bounds__(KT) k_sub_proj_f(const float2* const* __restri
 template <typename Cin>
 __global__ void k_scale_f(const Cin* __restrict__ in, float2* out, const double* __restrict__ scale, long N) {
   const int rhs = blockIdx.y;
-  const ff s = ff_from(scale[rhs]);
+  const ff s = ff_of_f64(scale[rhs]);
   const size_t base = (size_t)rhs * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
     ffc v = ffc_of(in[base + i]);
@@ -359,25 +381,30 @@ __global__ void k_scale_f(const Cin* __restrict__ in, float2* out, const double*
 }
 
 // u[rhs] += sum_j Z_j[rhs] y[rhs][j] for FP32 Z (mixed path): the sum in float-float on the
-// FP32 pipes, one FP64 add per component into u (the FP64 form of k_update_u spends four
-// FP64 FMAs per basis vector and component, at GB300's small FP64 rate)
-__global__ void k_update_u_f(const float2* const* __restrict__ Z, int nz, const double2* __restrict__ y, int ystride,
-                             double2* u, long N) {
+// FP32 pipes, the coefficients converted once per CTA, and two FP64 adds per component into
+// u (the FP64 form of k_update_u spends four FP64 FMAs per basis vector and component, at
+// GB300's small FP64 rate).  At most UPD_MAXZ vectors per launch.
+constexpr int UPD_MAXZ = 64;
+__global__ void __launch_bounds__(256) k_update_u_f(const float2* const* __restrict__ Z, int nz,
+                                                   const double2* __restrict__ y, int ystride, double2* u, long N) {
+  __shared__ ffc hy[UPD_MAXZ];
   const int rhs = blockIdx.y;
   const double2* yr = y + (size_t)rhs * ystride;
+  for (int j = threadIdx.x; j < nz; j += blockDim.x) hy[j] = ffc_of_f64(yr[j]);
+  __syncthreads();
   const size_t base = (size_t)rhs * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
     ffc acc;
     acc.x = acc.y = ff(0);
     for (int j = 0; j < nz; ++j) {
       const float2 zv = Z[j][base + i];
-      const ffc h = ffc_from(yr[j]);
+      const ffc h = hy[j];
       acc.x = acc.x + (ff_mul_f(h.x, zv.x) - ff_mul_f(h.y, zv.y));
       acc.y = acc.y + (ff_mul_f(h.y, zv.x) + ff_mul_f(h.x, zv.y));
     }
     double2 v = u[base + i];
-    v.x += ff_to(acc.x);
-    v.y += ff_to(acc.y);
+    v.x += ff_to_f64(acc.x);
+    v.y += ff_to_f64(acc.y);
     u[base + i] = v;
   }
 }
@@ -413,7 +440,10 @@ void sub_proj_f(const float2* const* V, int nv, const float2* win, float2* wout,
 
 void update_u_f(const float2* const* Z, int nz, const double2* y, int ystride, double2* u, long N, int nrhs,
                 cudaStream_t st) {
-  LS_LAUNCH("kr_update_u", st, k_update_u_f<<<grid_rows(N, nrhs), 256, 0, st>>>(Z, nz, y, ystride, u, N));
+  for (int j0 = 0; j0 < nz; j0 += UPD_MAXZ)
+    LS_LAUNCH("kr_update_u", st,
+              k_update_u_f<<<grid_rows(N, nrhs), 256, 0, st>>>(Z + j0, std::min(UPD_MAXZ, nz - j0), y + j0, ystride,
+                                                               u, N));
 }
 
 template <typename Cin> void scale_f(const Cin* in, float2* out, const double* s, long N, int nrhs, cudaStream_t st) {
