@@ -907,7 +907,8 @@ ls_status ls_rhs_plane_wave(ls_ctx* c, int nrhs, const double* dirs, double* g_o
     }
     copy_in(c, dd, dirs, (size_t)nrhs * c->d * sizeof(double), st);
     // float-float passes on the mixed path, FP64 on the plain path
-    if (c->prec == LS_PREC_MIXED) ls::conv_rhs_ff(c->plan, nrhs, dd, gd, t1, t2, st);
+    if (c->prec == LS_PREC_MIXED)
+      ls::conv_rhs_ff(c->plan, nrhs, dd, gd, t1, t2, buf<ffc>(c, "rhs_phase", (size_t)nrhs * c->d * c->n), st);
     else ls::conv_apply<double2>(c->plan, nrhs, (const double2*)nullptr, gd, dd, false, t1, t2, st);
     copy_out(c, g_out, gd, tot * sizeof(double2), st);
     LS_CUDA(cudaStreamSynchronize(st));

@@ -91,6 +91,30 @@ __host__ __device__ __forceinline__ ffc ffc_from(double2 v) {
 }
 __host__ __device__ __forceinline__ double2 ffc_to(ffc v) { return make_double2(ff_to(v.x), ff_to(v.y)); }
 
+// Renormalisation deferred: an add keeps the exact TwoSum of the leading parts and adds the
+// trailing parts without the final fast-TwoSum (8 FP32 operations instead of 11), a product
+// keeps the FMA TwoProduct and the cross terms without it (4 instead of 7; 3 for an FP32
+// factor).  The pair then is an exact unevaluated sum whose trailing part may exceed half an
+// ulp of the leading one; a chain of k such operations adds about k u^2 of its operands'
+// magnitudes in error before the final lz_norm.
+__device__ __forceinline__ ff lz_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff lz_neg(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff lz_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff(p, e);
+}
+__device__ __forceinline__ ff lz_mul_f(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  return ff(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+__device__ __forceinline__ ff lz_norm(ff a) { return ff_fast_two_sum(a.hi, a.lo); }
+
 // Conversions between FP64 and FP32 pairs on the integer and FP32 pipes.  GB300 runs FP64
 // instructions (conversions to and from FP64 among them) at a small fraction of its FP32
 // rate, so a streaming kernel that converts every element through FP64 is bound by them.

@@ -39,7 +39,7 @@ namespace ls {
 template <typename C>
 static void conv_run(const ConvPlan& p, int nrhs, const void* u, void* y, const double* plane_dirs, bool add_u,
                      const void* sub, int in64, int out64, const void* tw, const void* sym, const void* w2m,
-                     void* scratch1, void* scratch2, cudaStream_t st) {
+                     void* scratch1, void* scratch2, cudaStream_t st, const void* phase = nullptr) {
   const int n = p.n, L = 2 * n, d = p.d;
   const long rows = (d == 2) ? (long)n : (long)n * n;  // lines of one grid along the last axis
   C* T1 = reinterpret_cast<C*>(scratch1);
@@ -47,7 +47,7 @@ static void conv_run(const ConvPlan& p, int nrhs, const void* u, void* y, const 
   r.in = u; r.out = T1; r.lines = (long)nrhs * rows; r.n_in = n; r.n_out = L;
   r.in_ls = n; r.out_ls = L; r.pw = w2m; r.pw_lines = rows; r.tw = tw;
   r.plane_dirs = plane_dirs; r.d = d; r.n = n; r.omega = p.omega; r.h = p.h; r.in64 = in64;
-  r.pw64 = p.w2m64;
+  r.pw64 = p.w2m64; r.phase = phase;
   row_pass<C>(L, -1, r, st);
   if (d == 2) {
     ColPassArgs c{};
@@ -94,11 +94,30 @@ void conv_apply_ff(const ConvPlan& p, int nrhs, const double2* u, double2* y, co
   conv_run<ffc>(p, nrhs, u, y, nullptr, true, sub, 1, 1, p.twff, p.symff, p.w2mff, scratch1, scratch2, st);
 }
 
+// phase[(rhs * d + a) * n + k] = exp(i omega h (k + 1) dir_a) as float-float complex (FP64
+// sincos, once per right-hand side, axis and index): the plane wave exp(i omega x . dir) at
+// x = h (i + 1) is the product of one factor per axis
+__global__ void k_phase_table(const double* __restrict__ dirs, int nrhs, int d, int n, double omega, double h,
+                              ffc* __restrict__ phase) {
+  const long tot = (long)nrhs * d * n;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
+    const long ra = t / n;
+    const int k = (int)(t - ra * n);
+    double sn, cs;
+    sincos(omega * h * ((double)(k + 1) * dirs[ra]), &sn, &cs);
+    phase[t] = ffc_from(make_double2(cs, sn));
+  }
+}
+
 void conv_rhs_ff(const ConvPlan& p, int nrhs, const double* plane_dirs, double2* g, void* scratch1, void* scratch2,
-                 cudaStream_t st) {
+                 void* phase, cudaStream_t st) {
   if (!p.twff || !p.symff) LS_FAIL(ESTATE_, "float-float operator tables missing");
+  const long tot = (long)nrhs * p.d * p.n;
+  LS_LAUNCH("rhs_phase", st,
+            k_phase_table<<<(unsigned)std::min<long>((tot + 255) / 256, 1024), 256, 0, st>>>(
+                plane_dirs, nrhs, p.d, p.n, p.omega, p.h, reinterpret_cast<ffc*>(phase)));
   conv_run<ffc>(p, nrhs, nullptr, g, plane_dirs, false, nullptr, 0, 1, p.twff, p.symff, p.w2mff, scratch1, scratch2,
-                st);
+                st, phase);
 }
 
 template void conv_apply<float2>(const ConvPlan&, int, const float2*, float2*, const double*, bool, void*, void*, cudaStream_t);

@@ -19,26 +19,10 @@ namespace ls {
 
 template <> struct RealOf<ffc> { using T = ff; };
 
-// Float-float arithmetic inside the passes, with renormalisation deferred: an add keeps the
-// exact TwoSum of the leading parts and adds the trailing parts without the final
-// fast-TwoSum (8 FP32 operations instead of 11), a product keeps the FMA TwoProduct and the
-// cross terms without it (4 instead of 7).  The pair then is an exact unevaluated sum whose
-// trailing part may exceed half an ulp of the leading one; every value is renormalised when a
-// pass stores it to shared memory, so within one radix pass the trailing part stays below
-// about 2^-21 of the leading one and the dropped lo * lo term below 2^-42 relative.
-__device__ __forceinline__ ff lz_add(ff a, ff b) {
-  const ff s = ff_two_sum(a.hi, b.hi);
-  return ff(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ ff lz_neg(ff a) { return ff(-a.hi, -a.lo); }
-__device__ __forceinline__ ff lz_mul(ff a, ff b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return ff(p, e);
-}
-__device__ __forceinline__ ff lz_norm(ff a) { return ff_fast_two_sum(a.hi, a.lo); }
+// Float-float arithmetic inside the passes: the deferred-renormalisation forms of
+// ffloat.cuh (lz_add, lz_mul, lz_norm); every value is renormalised when a pass stores it to
+// shared memory, so within one radix pass the trailing part stays below about 2^-21 of the
+// leading one and the dropped lo * lo term below 2^-42 relative.
 __device__ __forceinline__ ffc cadd(ffc a, ffc b) {
   ffc r;
   r.x = lz_add(a.x, b.x);
@@ -286,15 +270,22 @@ template <int L> struct RowShape {
   static constexpr int NT = (L / 8 > 256) ? L / 8 : 256;
   static constexpr int NL = NT * 8 / L;
 };
-// TC adjacent lines per CTA (about 64 KB of shared memory); FP32 lines of 512 to 2048
-// take 8 lines (64-byte runs of each row; measured on 2D n = 1024: 4 lines, 32-byte runs
-// and three CTAs per SM, is 30 % slower), lines of 4096 take 4 (8 would need 256 KB)
+// TC adjacent lines per CTA (about 64 KB of shared memory).  FP32 lines of 1024 and more:
+// 4 lines (32-byte runs of each row), L / 8 threads with 4 butterflies each and two CTAs
+// per SM, so that one CTA's global loads and stores overlap the other's passes (measured on
+// 2D n = 1024, L = 2048: 8 % faster than 8 lines and one 512-thread CTA per SM, which
+// leaves the SM idle while a CTA loads; 1024 threads of 2 butterflies each is 16 % slower).
+// FP32 lines of 512: 8 lines, 256 threads.  Float-float lines of 2048: 2 lines, 512
+// threads, two CTAs per SM (64 registers suffice; lines of 4096 need more).
 template <typename C, int L> struct ColShape {
   static constexpr int raw = 65536 / (L * (int)sizeof(C));
   static constexpr bool f32_long = sizeof(C) == 8 && L >= 512;
-  static constexpr int TC = f32_long ? (L <= 2048 ? 8 : 4) : (raw < 2 ? 2 : (raw > 16 ? 16 : raw));
-  static constexpr int t = f32_long ? TC * L / 16 : TC * L / 8;
+  static constexpr int TC = f32_long ? (L >= 1024 ? 4 : 8) : (raw < 2 ? 2 : (raw > 16 ? 16 : raw));
+  static constexpr int t = f32_long ? TC * L / (L >= 1024 ? 32 : 16) : TC * L / 8;
   static constexpr int NT = t > 512 ? 512 : (t < 64 ? 64 : t);
+  // resident CTAs per SM the register allocation must allow
+  static constexpr int MINB =
+      f32_long && L >= 1024 && NT < 512 ? 512 / NT : (std::is_same<C, ffc>::value && L <= 2048 && NT == 512 ? 2 : 1);
 };
 
 // ------------------------------------------------------------------------------------
@@ -363,6 +354,24 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
           // v = -omega^2 m(x) exp(i omega x . dir) (right-hand side, eq. ls), in FP64
           const long q = line % a.pw_lines;      // row within the grid
           const long rhs = line / a.pw_lines;
+          if constexpr (std::is_same<C, ffc>::value) {
+            if (a.phase != nullptr) {
+              // float-float: the product of the per-axis phase factors
+              const ffc* ph = reinterpret_cast<const ffc*>(a.phase) + rhs * a.d * a.n;
+              ffc x = ph[(long)(a.d - 1) * a.n + e];
+              long qq = q;
+              for (int ax = a.d - 2; ax >= 0; --ax) {
+                const long ia = qq % a.n;
+                qq /= a.n;
+                x = c_norm(cmul(x, ph[(long)ax * a.n + ia]));
+              }
+              const ff w = lz_neg(ff_of_f64(a.pw64[q * n_in + e]));
+              x.x = lz_norm(lz_mul(w, x.x));
+              x.y = lz_norm(lz_mul(w, x.y));
+              s[SL::off(li, e)] = x;
+              continue;
+            }
+          }
           const double* dir = a.plane_dirs + rhs * a.d;
           double ph = (double)(e + 1) * dir[a.d - 1];
           long qq = q;
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
 // MODE 0: forward; 1: inverse; 2: forward, multiply by the symbol, inverse.
 // ------------------------------------------------------------------------------------
 template <typename C, int L, int MODE>
-__global__ void __launch_bounds__(ColShape<C, L>::NT) k_col_pass(ColPassArgs a) {
+__global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_col_pass(ColPassArgs a) {
   constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
   using SL = SLay<C, L, TC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];

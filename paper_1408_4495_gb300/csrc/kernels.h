@@ -20,6 +20,8 @@ struct RowPassArgs {
   const void* tw;      // twiddles exp(-2 pi i m / L), m < L
   const double* plane_dirs;  // right-hand-side prologue (FP64 and float-float passes), or null
   const double* pw64;  // omega^2 m in FP64 for that prologue
+  const void* phase;   // float-float passes: the prologue's phase factors as float-float
+                       // complex [rhs][axis][k] = exp(i omega h (k + 1) dir_axis), or null
   int d, n;
   double omega, h;
   const void* addv;    // epilogue: out += addv[line * add_ls + e], or null
@@ -63,8 +65,9 @@ void conv_apply(const ConvPlan& p, int nrhs, const C* u, C* y, const double* pla
 void conv_apply_ff(const ConvPlan& p, int nrhs, const double2* u, double2* y, const double2* sub, void* scratch1,
                    void* scratch2, cudaStream_t st);
 // g = K(-omega^2 m u_inc) for plane waves (the right-hand side), float-float passes, FP64 g
+// phase: scratch of nrhs * d * n float-float complex entries (4 floats each)
 void conv_rhs_ff(const ConvPlan& p, int nrhs, const double* plane_dirs, double2* g, void* scratch1, void* scratch2,
-                 cudaStream_t st);
+                 void* phase, cudaStream_t st);
 // C -= A B on the complex FP32 fronts of a level on the tensor cores (tc_gemm.cu): A, B, C
 // are the blocks [r0,r1)x[k0,k1), [k0,k1)x[c0,c1), [r0,r1)x[c0,c1) of each column-major
 // front (ld = fmax, fstride elements apart); *err = 2 if a bounded wait expired

@@ -298,8 +298,12 @@ __global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__
   for (int jg = 0; jg < nv; jg += JB) {
     const int nj = min(JB, nv - jg);
     ffc acc[JB];
+    const float2* vp[JB];  // the vectors' base pointers, loaded once (not per element)
 #pragma unroll
-    for (int q = 0; q < JB; ++q) acc[q].x = acc[q].y = ff(0);
+    for (int q = 0; q < JB; ++q) {
+      acc[q].x = acc[q].y = ff(0);
+      vp[q] = q < nj ? V[jg + q] + base : w + base;
+    }
     for (long i = i0 + threadIdx.x; i < i1; i += (long)KT * RUN) {
       float2 sr[JB];
 #pragma unroll
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__
 #pragma unroll
           for (int q = 0; q < JB; ++q)
             if (q < nj) {
-              const float2 a = V[jg + q][base + e];
+              const float2 a = vp[q][e];
               sr[q].x = __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, sr[q].x));
               sr[q].y = __fmaf_rn(a.x, b.y, __fmaf_rn(-a.y, b.x, sr[q].y));
             }
@@ -335,30 +339,66 @@ __global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__
 }
 
 // wout = win - sum_j V_j h[rhs][j] (h as FP32 pairs), rounded to FP32; with NORM, also the
-// partial sums of |wout|^2 (as stored) in the layout of k_dots_f
+// partial sums of |wout|^2 (as stored) in the layout of k_dots_f.  The sum runs in
+// float-float with deferred renormalisation (one lz_norm per element before the rounding),
+// RUN elements per thread at a time so that their loads are in flight together; the
+// coefficients sit in shared memory (up to SP_MAXV of them, else they are read from global
+// memory).  |wout|^2 sums FP32 runs of RUN squares (positive terms: relative error about
+// RUN u) into float-float.  win may equal wout.
+constexpr int SP_MAXV = 64;
 template <bool NORM>
 __global__ void __launch_bounds__(KT) k_sub_proj_f(const float2* const* __restrict__ V, int nv, const float2* win,
                                                    float2* wout, const ffc* __restrict__ hf, int hstride, long N,
                                                    double2* __restrict__ partial, int nblk) {
   __shared__ double2 sh[KT / 32];
+  __shared__ ffc hs[SP_MAXV];
+  __shared__ const float2* vps[SP_MAXV];
   const int rhs = blockIdx.y, blk = blockIdx.x;
   const long chunk = (N + nblk - 1) / nblk;
   const long i0 = blk * chunk, i1 = min(N, i0 + chunk);
   const size_t base = (size_t)rhs * N;
   const ffc* hr = hf + (size_t)rhs * hstride;
+  const bool staged = nv <= SP_MAXV;
+  if (staged)
+    for (int j = threadIdx.x; j < nv; j += KT) {
+      hs[j] = hr[j];
+      vps[j] = V[j];
+    }
+  __syncthreads();
+  const ffc* hc = staged ? hs : hr;
   ffc nacc;
   nacc.x = nacc.y = ff(0);
-  for (long i = i0 + threadIdx.x; i < i1; i += KT) {
-    ffc acc = ffc_of(win[base + i]);
-    for (int j = 0; j < nv; ++j) {
-      const float2 a = V[j][base + i];
-      const ffc h = hr[j];
-      acc.x = acc.x - (ff_mul_f(h.x, a.x) - ff_mul_f(h.y, a.y));
-      acc.y = acc.y - (ff_mul_f(h.y, a.x) + ff_mul_f(h.x, a.y));
+  for (long i = i0 + threadIdx.x; i < i1; i += (long)KT * RUN) {
+    ffc acc[RUN];
+#pragma unroll
+    for (int u = 0; u < RUN; ++u) {
+      const long e = i + (long)u * KT;
+      acc[u] = ffc_of(e < i1 ? win[base + e] : make_float2(0.f, 0.f));
     }
-    const float2 o = rnd(acc);
-    wout[base + i] = o;
-    if (NORM) nacc.x = nacc.x + (ff_prod(o.x, o.x) + ff_prod(o.y, o.y));
+    for (int j = 0; j < nv; ++j) {
+      const ffc h = hc[j];
+      const float2* vj = (staged ? vps[j] : V[j]) + base;
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) {
+        const long e = i + (long)u * KT;
+        if (e < i1) {
+          const float2 a = vj[e];
+          acc[u].x = lz_add(acc[u].x, lz_neg(lz_add(lz_mul_f(h.x, a.x), lz_neg(lz_mul_f(h.y, a.y)))));
+          acc[u].y = lz_add(acc[u].y, lz_neg(lz_add(lz_mul_f(h.y, a.x), lz_mul_f(h.x, a.y))));
+        }
+      }
+    }
+    float nr = 0.f;
+#pragma unroll
+    for (int u = 0; u < RUN; ++u) {
+      const long e = i + (long)u * KT;
+      if (e < i1) {
+        const float2 o = make_float2(lz_norm(acc[u].x).hi, lz_norm(acc[u].y).hi);
+        wout[base + e] = o;
+        if (NORM) nr = __fmaf_rn(o.x, o.x, __fmaf_rn(o.y, o.y, nr));
+      }
+    }
+    if (NORM) nacc.x = nacc.x + ff(nr, 0.f);
   }
   if (NORM) {
     const double2 s = block_sum_ff(nacc, sh);
@@ -388,16 +428,20 @@ constexpr int UPD_MAXZ = 64;
 __global__ void __launch_bounds__(256) k_update_u_f(const float2* const* __restrict__ Z, int nz,
                                                    const double2* __restrict__ y, int ystride, double2* u, long N) {
   __shared__ ffc hy[UPD_MAXZ];
+  __shared__ const float2* zps[UPD_MAXZ];
   const int rhs = blockIdx.y;
   const double2* yr = y + (size_t)rhs * ystride;
-  for (int j = threadIdx.x; j < nz; j += blockDim.x) hy[j] = ffc_of_f64(yr[j]);
+  for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+    hy[j] = ffc_of_f64(yr[j]);
+    zps[j] = Z[j];
+  }
   __syncthreads();
   const size_t base = (size_t)rhs * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
     ffc acc;
     acc.x = acc.y = ff(0);
     for (int j = 0; j < nz; ++j) {
-      const float2 zv = Z[j][base + i];
+      const float2 zv = zps[j][base + i];
       const ffc h = hy[j];
       acc.x = acc.x + (ff_mul_f(h.x, zv.x) - ff_mul_f(h.y, zv.y));
       acc.y = acc.y + (ff_mul_f(h.y, zv.x) + ff_mul_f(h.x, zv.y));

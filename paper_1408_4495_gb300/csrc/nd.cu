@@ -1977,7 +1977,9 @@ template <typename C, int RC, int TR, int MODE> __host__ __device__ SweepShape s
   s.nbuf = ksz > KA ? 2 : 1;
   s.kv = (size_t)ksz * RC * sizeof(C) <= SWEEP_VS_MAX ? ksz : KA;
   if (kg_in > 0) s.kg = kg_in;
-  else s.kg = ksz > KA ? 8 : (ksz / 16 < 1 ? 1 : (ksz / 16 > 8 ? 8 : ksz / 16));
+  // one warp up to 32 columns (its sums are final, no cross-warp reduction), else about
+  // 16 columns per warp up to 8 warps
+  else s.kg = ksz > KA ? 8 : (ksz <= 32 ? 1 : (ksz / 16 > 8 ? 8 : ksz / 16));
   const size_t a = (size_t)s.nbuf * s.kc0 * TR + (size_t)s.kv * RC;
   const size_t red = (size_t)s.kg * 32 * (RCT + 1);
   s.region0 = a > red ? a : red;
@@ -2173,6 +2175,33 @@ template <typename C, int RC, int TR, int MODE> __global__ void __launch_bounds_
     __syncthreads();
   }
   if (rvalid <= 0) return;
+  if (kg == 1 && S.nsplit == 1) {
+    // one warp over all columns: every thread holds the finished sums of its row and
+    // right-hand sides and stores them directly (RCT consecutive entries of one item)
+    __syncthreads();  // wt complete when no column chunk ran
+    if (row >= rvalid) return;
+    C* dst;
+    if (MODE == 0) {
+      dst = S.W + ((size_t)g * S.nf * fmax + (size_t)z * fmax + smax + t0 + row) * RC + j0;
+      if (sp == 0) {
+#pragma unroll
+        for (int j = 0; j < RCT; ++j) acc[j] = cadd(acc[j], wt[row * RC + j0 + j]);
+      }
+    } else {
+      const int pt = ixs[kv + row];
+      if (pt < 0) return;
+      dst = S.T + ((size_t)g * S.N + pt) * RC + j0;
+    }
+    if constexpr (sizeof(C) == 8 && RCT % 2 == 0) {
+#pragma unroll
+      for (int j = 0; j < RCT; j += 2)
+        reinterpret_cast<float4*>(dst)[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < RCT; ++j) dst[j] = acc[j];
+    }
+    return;
+  }
   C* red = reinterpret_cast<C*>(smem_raw);
 #pragma unroll
   for (int j = 0; j < RCT; ++j) red[((size_t)w * 32 + lane) * (RCT + 1) + j] = acc[j];

@@ -10,6 +10,8 @@ first run warms up) and exits; graphs are off, so every launch is a separate ker
     python -m paper_1408_4495_gb300.profile_cases factor --d 3 --n 48
         ls_factor once (the front kernels, the tensor-core Schur products); prints the number
         of tensor-core GEMM launches of one factorization
+    python -m paper_1408_4495_gb300.profile_cases solve --d 2 --n 1024 --nrhs 8
+        ls_factor + ls_rhs_plane_wave + ls_solve at tolerance 1e-6 (the GMRES kernels)
 """
 
 from __future__ import annotations
@@ -30,7 +32,7 @@ def _medium(W, d, n):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["precond", "apply", "factor"])
+    ap.add_argument("case", choices=["precond", "apply", "factor", "solve"])
     ap.add_argument("--d", type=int, default=2)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=16)
@@ -53,6 +55,12 @@ def main(argv=None) -> int:
         for _ in range(2):
             s.apply(x, prec=ls.LS_PREC_MIXED)
             s.apply(x, prec=ls.LS_PREC_FF)
+    elif a.case == "solve":
+        dirs = W.directions_circle(a.nrhs) if a.d == 2 else W.directions_sphere(a.nrhs, 1004)
+        for _ in range(2):
+            s.factor()
+            u, info = s.solve(s.rhs_plane_wave(dirs), tol=1e-6)
+        out["iters"] = [i.iters for i in info]
     else:
         ls.profile_start(None)
         s.factor()
