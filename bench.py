@@ -289,7 +289,10 @@ def algorithmic_bytes(cls, w, nd, counts, steps, rhs=None):
                  row inv 2N + N -> N (per right-hand side, times c)
       stencil: read v N c, write r N c
       nested-dissection sweeps: every factor block once per sweep + each right-hand side's vector
-                 read and written once (N c each), spread over the sweep's launches (one per level).
+                 read and written once (N c each), spread over the sweep's launches (one per level
+                 on the CUDA cores, three -- gather, tensor-core product, scatter -- per level on
+                 the tensor cores: the launches per sweep come from ``counts``, one application
+                 being the two nd_items launches around its sweeps; one per level without counts).
     ``rhs``: right-hand sides per launch (default: all of the workload's)."""
     n, N, R = w.n, w.n ** w.d, (w.nrhs if rhs is None else rhs)
     c = 8 if cls.endswith("_c64") else 16
@@ -315,24 +318,40 @@ def algorithmic_bytes(cls, w, nd, counts, steps, rhs=None):
     if cls.startswith("stencil"):
         return R * N * c * 2
     if cls.startswith("nd_fwd") or cls.startswith("nd_bwd"):
-        key = "fwd" if cls.startswith("nd_fwd") else "bwd"
-        per_sweep = nd[f"{key}_factor_bytes"] + R * N * c * 2
-        return per_sweep / nd["levels"]  # one launch per level in both sweeps
+        return sweep_bytes(cls, w, nd, rhs) / sweep_launches(cls, nd, counts)
     raise ValueError(cls)
 
 
-# ncu DRAM traffic per launch of a kernel class on the headline workload, valid while the
-# kernel's source is unchanged: the sha1 of its source region (the text between two markers
-# of the file) and of the header it includes for its arithmetic, taken when the counters
-# were captured (profiles/nd_sweep_2d_n1024_64rhs.md).  "rhs": the right-hand sides per launch
-# of the capture; the line scales the bytes to the live count of the timed launches with the
-# byte model's ratio (factor bytes fixed, vector bytes in proportion).
+def sweep_bytes(cls, w, nd, rhs=None):
+    """Algorithmic bytes of one forward or backward sweep (see algorithmic_bytes)."""
+    N, R = w.n ** w.d, (w.nrhs if rhs is None else rhs)
+    c = 8 if cls.endswith("_c64") else 16
+    key = "fwd" if cls.startswith("nd_fwd") else "bwd"
+    return nd[f"{key}_factor_bytes"] + R * N * c * 2
+
+
+def sweep_launches(cls, nd, counts):
+    """Launches per sweep: from the class counts when they include the applications' item
+    launches, else one per level."""
+    items = (counts or {}).get("nd_items" + cls[6:], 0)
+    if items and (counts or {}).get(cls, 0):
+        return counts[cls] / (items / 2)
+    return nd["levels"]
+
+
+# ncu DRAM traffic of one sweep (all its launches) on the headline workload, valid while the
+# kernels' sources are unchanged: the sha1 of their source regions (the text between two
+# markers of a file, or the whole file) taken when the counters were captured
+# (profiles/nd_sweep_2d_n1024_64rhs.md).  "rhs": the right-hand sides of the capture; the
+# line scales the bytes to the live count of the timed launches with the byte model's ratio
+# (factor bytes fixed, vector bytes in proportion) and divides them over the sweep's launches.
 SWEEP_SRC = [("paper_1408_4495_gb300/csrc/nd.cu", "template <typename C> struct SweepK {",
-              "// r[rhs][N] -> T[group][N][RC]"),
+              "template <typename C, int RC>\nstatic void solve_chunk"),
+             ("paper_1408_4495_gb300/csrc/tc_gemm.cu", None, None),
              ("paper_1408_4495_gb300/csrc/common.cuh", None, None)]
 TRAFFIC = {
-    "nd_fwd_c64": {"src": SWEEP_SRC, "sha1": "585ffbaf4171a5971b2ff24b4904261772a51999", "bytes": 345.26e6, "rhs": 64},
-    "nd_bwd_c64": {"src": SWEEP_SRC, "sha1": "585ffbaf4171a5971b2ff24b4904261772a51999", "bytes": 207.37e6, "rhs": 64},
+    "nd_fwd_c64": {"src": SWEEP_SRC, "sha1": None, "bytes_per_sweep": None, "rhs": 64},
+    "nd_bwd_c64": {"src": SWEEP_SRC, "sha1": None, "bytes_per_sweep": None, "rhs": 64},
 }
 
 
@@ -352,18 +371,19 @@ def source_sha1(src):
     return h.hexdigest()
 
 
-def recorded_traffic(cls, w=None, nd=None, rhs=None):
-    """Recorded DRAM bytes per launch of a class, scaled to ``rhs`` right-hand sides per
-    launch by the byte model; None when there is no record or the kernel changed since."""
+def recorded_traffic(cls, w=None, nd=None, rhs=None, counts=None):
+    """Recorded DRAM bytes per launch of a sweep class: the sweep's bytes scaled to ``rhs``
+    right-hand sides by the byte model, over its launches; None when there is no record or a
+    kernel changed since."""
     rec = TRAFFIC.get(cls)
-    if not rec or not rec["sha1"]:
+    if not rec or not rec["sha1"] or not rec["bytes_per_sweep"]:
         return None
     if source_sha1(rec["src"]) != rec["sha1"]:
         return None
-    if w is None or rhs is None:
-        return rec["bytes"]
-    return rec["bytes"] * algorithmic_bytes(cls, w, nd, None, None, rhs=rhs) / \
-        algorithmic_bytes(cls, w, nd, None, None, rhs=rec["rhs"])
+    per_sweep = rec["bytes_per_sweep"]
+    if w is not None and rhs is not None:
+        per_sweep *= sweep_bytes(cls, w, nd, rhs) / sweep_bytes(cls, w, nd, rec["rhs"])
+    return per_sweep / sweep_launches(cls, nd, counts) if nd is not None else per_sweep
 
 
 class GpuBench:
@@ -460,9 +480,10 @@ class GpuBench:
         if cls and cls in by_model:
             bm = by_model[cls]
             roof = {"kernel": cls, "bound": "hbm", "achieved": bm["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                    "frac": bm["achieved_gbs"] / peak, "traffic": recorded_traffic(cls, w, nd, r_live),
-                    "traffic_note": "ncu dram__bytes_read + write per launch, captured with 64 right-hand sides per "
-                                    "launch and scaled to the live count by the byte model",
+                    "frac": bm["achieved_gbs"] / peak,
+                    "traffic": recorded_traffic(cls, w, nd, r_live, rprof["counts"]),
+                    "traffic_note": "ncu dram__bytes_read + write of whole sweeps (64 right-hand sides), scaled to "
+                                    "the live count by the byte model, per launch of the sweep",
                     "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": bm["algorithmic_bytes_per_launch"],
                     "avg_launch_us": bm["avg_launch_us"], "launches_timed": bm["launches"], "steps_timed": steps,

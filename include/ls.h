@@ -386,7 +386,8 @@ ls_status ls_profile_stop(char* report, int capacity);
  * launch-shape choices that have no single best value across grids: the trailing-matrix size
  * from which the blocked front LU updates in two levels, the smallest FP32 Schur product
  * (rows) given to the tensor cores, the largest front factored Gauss-Jordan style in one CTA,
- * and how many CTAs per SM the split of a solve sweep level aims at.  A coordinate search
+ * how many CTAs per SM the split of a solve sweep level aims at, and the smallest FP32 solve
+ * level (rows of its product, at least 64) run on the tensor cores.  A coordinate search
  * keeps each alternative that is more than 2 % faster (the fastest of 2 factorizations / 3
  * solves of nrhs right-hand sides, CUDA events).  The choice is applied to c, kept for every
  * later context of the same (dim, n, prec, kernel) in this process, and, when the
@@ -398,9 +399,17 @@ ls_status ls_profile_stop(char* report, int capacity);
  *   report   NUL-terminated JSON: the choice and every timing (truncated to capacity bytes;
  *            may be NULL).
  * ls_tune_info -- the context's current choices as a JSON object (no device work).
+ * ls_set_tune -- applies choices given as a JSON object with any of the keys of
+ *   ls_tune_info (other keys are ignored; missing keys keep their values) to c only, e.g. to
+ *   pin a shape or to compare two.  A factorization in flight is awaited first; the next
+ *   ls_factor uses the factorization choices, the next solve the solve choices (a change of
+ *   a factorization choice needs a new ls_factor to take effect).  LS_EINVAL when a value is
+ *   out of range (two_level_min <= 0, tc_min_rows < 1, sweep_ctas outside 1..4,
+ *   gj_max_own outside 1..32, tcs_min_rows < 1).
  * --------------------------------------------------------------------------------------- */
 ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity);
 ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity);
+ls_status ls_set_tune(ls_ctx* c, const char* json);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free operator apply (the paper has no counterpart: this is a deployment aid).

@@ -637,9 +637,9 @@ static void tune_load_locked() {
     ls::NdTune t;
     if (std::sscanf(line,
                     "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %lf, "
-                    "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d}",
+                    "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d}",
                     &k.d, &k.n, &k.prec, &k.laplace, &t.two_level_min, &t.tc_min_rows, &t.sweep_ctas,
-                    &t.gj_max_own) == 8)
+                    &t.gj_max_own, &t.tcs_min_rows) == 9)
       g_tune[k] = t;
   }
   std::fclose(f);
@@ -654,9 +654,9 @@ static void tune_save_locked() {
   for (const auto& kv : g_tune)
     std::fprintf(f,
                  "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %.17g, "
-                 "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d}\n",
+                 "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d}\n",
                  kv.first.d, kv.first.n, kv.first.prec, kv.first.laplace, kv.second.two_level_min,
-                 kv.second.tc_min_rows, kv.second.sweep_ctas, kv.second.gj_max_own);
+                 kv.second.tc_min_rows, kv.second.sweep_ctas, kv.second.gj_max_own, kv.second.tcs_min_rows);
   std::fclose(f);
   std::rename(tmp.c_str(), path);
 }
@@ -672,8 +672,10 @@ static bool tune_lookup(const TuneKey& k, ls::NdTune* t) {
 
 static std::string tune_json(const ls::NdTune& t) {
   char b[256];
-  std::snprintf(b, sizeof b, "{\"two_level_min\": %.6g, \"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d}",
-                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own);
+  std::snprintf(b, sizeof b,
+                "{\"two_level_min\": %.6g, \"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, "
+                "\"tcs_min_rows\": %d}",
+                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own, t.tcs_min_rows);
   return b;
 }
 
@@ -1314,6 +1316,7 @@ ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, l
 }
 
 ls_status ls_precond(ls_ctx* c, int nrhs, const double* in, double* out) {
+  ls::Range range("ls_precond");
   try {
     check_ctx(c);
     if (!c->factored) throw Error{ls::ESTATE_, "ls_precond before ls_factor"};
@@ -1453,17 +1456,30 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
     factor_ms(best);
     log += "], \"solve_ms\": [";
     double sb = solve_ms(best);
-    log += "[" + std::to_string(best.sweep_ctas) + ", " + std::to_string(sb) + "]";
+    log += "[" + tune_json(best) + ", " + std::to_string(sb) + "]";
+    auto try_solve = [&](ls::NdTune t) {
+      const double sm = solve_ms(t);
+      log += ", [" + tune_json(t) + ", " + std::to_string(sm) + "]";
+      if (sm < 0.98 * sb) {
+        best = t;
+        sb = sm;
+      }
+    };
     const int sweep_base = best.sweep_ctas;
     for (int v : {1, 2, 4}) {
       if (v == sweep_base) continue;
       ls::NdTune t = best;
       t.sweep_ctas = v;
-      const double sm = solve_ms(t);
-      log += ", [" + std::to_string(v) + ", " + std::to_string(sm) + "]";
-      if (sm < 0.98 * sb) {
-        best = t;
-        sb = sm;
+      try_solve(t);
+    }
+    if (mixed) {
+      // solve levels on the tensor cores from 64 rows (the default), from 128 or 256, or none
+      const int tcs_base = best.tcs_min_rows;
+      for (int v : {64, 128, 256, 1 << 30}) {
+        if (v == tcs_base) continue;
+        ls::NdTune t = best;
+        t.tcs_min_rows = v;
+        try_solve(t);
       }
     }
     ls::nd_set_tune(c->nd, best);
@@ -1493,6 +1509,48 @@ ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity) {
   if (!c) return LS_ESTATE;
   write_report(tune_json(ls::nd_get_tune(c->nd)), report, capacity);
   return LS_OK;
+}
+
+// the number after "key": in a flat JSON object, if the key is present
+static bool json_number(const char* js, const char* key, double* v) {
+  const std::string k = std::string("\"") + key + "\"";
+  const char* p = std::strstr(js, k.c_str());
+  if (!p) return false;
+  p = std::strchr(p + k.size(), ':');
+  if (!p) return false;
+  char* end = nullptr;
+  const double x = std::strtod(p + 1, &end);
+  if (end == p + 1) return false;
+  *v = x;
+  return true;
+}
+
+ls_status ls_set_tune(ls_ctx* c, const char* json) {
+  try {
+    check_ctx(c);
+    if (!json) throw Error{ls::EINVAL_, "NULL tune object"};
+    ls::NdTune t = ls::nd_get_tune(c->nd);
+    double v;
+    if (json_number(json, "two_level_min", &v)) {
+      if (!(v > 0)) throw Error{ls::EINVAL_, "two_level_min must be > 0"};
+      t.two_level_min = v;
+    }
+    auto int_key = [&](const char* key, int lo, int hi, int* dst) {
+      if (!json_number(json, key, &v)) return;
+      if (!(v >= lo && v <= hi) || v != std::floor(v)) throw Error{ls::EINVAL_, std::string(key) + " out of range"};
+      *dst = (int)v;
+    };
+    int_key("tc_min_rows", 1, 1 << 30, &t.tc_min_rows);
+    int_key("sweep_ctas", 1, ls::SWEEP_CTAS_MAX, &t.sweep_ctas);
+    int_key("gj_max_own", 1, 32, &t.gj_max_own);
+    int_key("tcs_min_rows", 1, 1 << 30, &t.tcs_min_rows);
+    factor_wait(c);
+    ls::nd_set_tune(c->nd, t);
+    ++c->gen;  // the captured graphs hold the old launch sequences
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
 }
 
 ls_status ls_profile_start(const char* timed_class) {

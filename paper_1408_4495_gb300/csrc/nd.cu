@@ -98,6 +98,11 @@ struct NdPlan {
   void* T = nullptr;  // grid-point items of the solve (N x SOLVE_CHUNK)
   int* swp = nullptr;  // per-front row permutation of the current panel (register sweeps)
   void* part = nullptr;  // solve: partial sums of split column ranges
+  // solve levels on the tensor cores (FP32): the gathered vector operands and the products,
+  // sized for every level with at least TCS_MIN_ROWS rows
+  float2* tcs_B = nullptr;
+  float2* tcs_C = nullptr;
+  size_t tcs_B_elems = 0, tcs_C_elems = 0;
   size_t part_elems = 0;
   unsigned* cnt = nullptr;  // solve: per-item arrival counters
   int* d_err = nullptr;
@@ -471,13 +476,32 @@ void nd_free(NdPlan* p) {
   if (p->swp) dev_free(p->swp);
   if (p->part) dev_free(p->part);
   if (p->cnt) dev_free(p->cnt);
+  if (p->tcs_B) dev_free(p->tcs_B);
+  if (p->tcs_C) dev_free(p->tcs_C);
   delete p;
 }
 
 NdInfo nd_info(const NdPlan* p) { return p->info; }
 
+// rows of a sweep level's product from which it may run on the tensor cores, and its
+// operand sizes for SOLVE_CHUNK right-hand sides (mode 0 forward, 1 backward)
+constexpr int TCS_MIN_ROWS = 64;
+static int tcs_rows(const LevelDev& D, int mode) { return mode == 0 ? D.bmax : D.smax; }
+static int tcs_k(const LevelDev& D, int mode) { return mode == 0 ? D.smax : D.bmax + D.smax; }
+static void tcs_sizes(const std::vector<LevelDev>& lev, size_t* b, size_t* c) {
+  *b = *c = 0;
+  for (const LevelDev& D : lev)
+    for (int mode = 0; mode < 2; ++mode)
+      if (tcs_rows(D, mode) >= TCS_MIN_ROWS) {
+        *b = std::max(*b, (size_t)D.nf * tcs_k(D, mode) * SOLVE_CHUNK);
+        *c = std::max(*c, (size_t)D.nf * tcs_rows(D, mode) * SOLVE_CHUNK);
+      }
+}
+
 size_t nd_device_bytes(const NdPlan* p, int elem_bytes) {
-  return (p->F_elems + p->W_elems + (size_t)p->N * SOLVE_CHUNK) * (size_t)elem_bytes;
+  size_t b = 0, c = 0;
+  if (elem_bytes == 8) tcs_sizes(p->lev, &b, &c);
+  return (p->F_elems + p->W_elems + (size_t)p->N * SOLVE_CHUNK + b + c) * (size_t)elem_bytes;
 }
 
 // The factorization's whole state is the front storage F: the solve reads the factored
@@ -1595,6 +1619,14 @@ static bool ensure_buffers(NdPlan* p, int elem_bytes, cudaStream_t st) {
   if (p->cnt) { dev_free(p->cnt); p->cnt = nullptr; }
   p->part = dev_alloc(part * elem_bytes);
   p->cnt = static_cast<unsigned*>(dev_alloc(items * sizeof(unsigned)));
+  if (p->tcs_B) { dev_free(p->tcs_B); p->tcs_B = nullptr; }
+  if (p->tcs_C) { dev_free(p->tcs_C); p->tcs_C = nullptr; }
+  p->tcs_B_elems = p->tcs_C_elems = 0;
+  if (elem_bytes == 8) {
+    tcs_sizes(p->lev, &p->tcs_B_elems, &p->tcs_C_elems);
+    if (p->tcs_B_elems) p->tcs_B = static_cast<float2*>(dev_alloc(p->tcs_B_elems * sizeof(float2)));
+    if (p->tcs_C_elems) p->tcs_C = static_cast<float2*>(dev_alloc(p->tcs_C_elems * sizeof(float2)));
+  }
   LS_CUDA(cudaMemsetAsync(p->cnt, 0, items * sizeof(unsigned), st));
   p->part_elems = part;
   if (p->swp) { dev_free(p->swp); p->swp = nullptr; }
@@ -2344,7 +2376,113 @@ static void launch_sweep_tr(NdPlan* p, int l, C* T, int ng, const SweepPlan& q, 
             launch_pdl(k_sweep<C, RC, TR, MODE>, grid, dim3(32 * sh.kg), sh.smem, st, S));
 }
 
+// ---- sweep levels on the tensor cores (FP32, 16 right-hand sides per group): the level's
+// product of k_sweep as one batched GEMM (tc_sweep_gemm, 3xTF32) between a gather of the
+// vector operand into B[z][k][n] and a scatter of C[z][row][n], n = group * 16 + j < ncols
+//   forward:  B = w_own (r at the own points + the children's updates, also stored to W),
+//             C = Y w_own, stored to the ring part of W with the children's ring updates added;
+//   backward: B = [-x_ring; w_own], C = [H | F11^-1] B = x_own, stored to T at the own points.
+// One thread moves two right-hand sides (16 bytes) of one k or row.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_tcs_gather(SweepK<float2> S, float2* __restrict__ B, int K, int ncols) {
+  const int z = blockIdx.x, pairs = ncols / 2;
+  float2* Bz = B + (size_t)z * K * ncols;
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < K * pairs; t += gridDim.y * blockDim.x) {
+    const int k = t / pairs, n = 2 * (t - k * pairs), g = n >> 4, j = n & 15;
+    const size_t wrow = (size_t)g * S.nf * S.fmax + (size_t)z * S.fmax;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MODE == 0) {
+      const int pt = __ldg(S.own + (size_t)z * S.smax + k);
+      const int s0 = __ldg(S.fsrc + ((size_t)z * S.fmax + k) * 2), s1 = __ldg(S.fsrc + ((size_t)z * S.fmax + k) * 2 + 1);
+      const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+      if (pt >= 0) v = padd(v, __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16 + j)));
+      if (s0 >= 0) v = padd(v, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16 + j)));
+      if (s1 >= 0) v = padd(v, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16 + j)));
+      *reinterpret_cast<float4*>(S.W + (wrow + k) * 16 + j) = v;
+    } else if (k < S.bmax) {
+      const int pt = __ldg(S.ring + (size_t)z * S.bmax + k);
+      if (pt >= 0) {
+        v = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16 + j));
+        v = make_float4(-v.x, -v.y, -v.z, -v.w);
+      }
+    } else {
+      v = __ldcg(reinterpret_cast<const float4*>(S.W + (wrow + k - S.bmax) * 16 + j));
+    }
+    *reinterpret_cast<float4*>(Bz + (size_t)k * ncols + n) = v;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const float2* __restrict__ Cm, int rows,
+                                                     int ncols) {
+  const int z = blockIdx.x, pairs = ncols / 2;
+  const float2* Cz = Cm + (size_t)z * rows * ncols;
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < rows * pairs; t += gridDim.y * blockDim.x) {
+    const int i = t / pairs, n = 2 * (t - i * pairs), g = n >> 4, j = n & 15;
+    float4 v = __ldcg(reinterpret_cast<const float4*>(Cz + (size_t)i * ncols + n));
+    if (MODE == 0) {
+      const int p0 = S.smax + i;
+      const int s0 = __ldg(S.fsrc + ((size_t)z * S.fmax + p0) * 2), s1 = __ldg(S.fsrc + ((size_t)z * S.fmax + p0) * 2 + 1);
+      const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+      if (s0 >= 0) v = padd(v, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16 + j)));
+      if (s1 >= 0) v = padd(v, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16 + j)));
+      *reinterpret_cast<float4*>(S.W + ((size_t)g * S.nf * S.fmax + (size_t)z * S.fmax + p0) * 16 + j) = v;
+    } else {
+      const int pt = __ldg(S.own + (size_t)z * S.smax + i);
+      if (pt >= 0) *reinterpret_cast<float4*>(S.T + ((size_t)g * S.N + pt) * 16 + j) = v;
+    }
+  }
+}
+
+// whether level l's sweep product of this mode runs on the tensor cores
+static bool tcs_level(const NdPlan* p, int l, int mode, int ng) {
+  const LevelDev& D = p->lev[l];
+  const int rows = tcs_rows(D, mode);
+  return p->use_tc && tc_enabled() && p->tcs_B && p->tcs_C && rows >= std::max(TCS_MIN_ROWS, p->tune.tcs_min_rows) &&
+         tcs_k(D, mode) >= TC_MIN_K && (size_t)D.nf * tcs_k(D, mode) * ng * 16 <= p->tcs_B_elems &&
+         (size_t)D.nf * rows * ng * 16 <= p->tcs_C_elems;
+}
+
+template <int MODE> static void launch_sweep_tc(NdPlan* p, int l, float2* T, int ng, cudaStream_t st) {
+  const LevelDev& D = p->lev[l];
+  const int depth = (int)p->lev.size();
+  SweepK<float2> S{};
+  S.F = reinterpret_cast<const float2*>(p->F) + D.F_off;
+  S.W = reinterpret_cast<float2*>(p->W) + D.W_off;
+  const bool has_child = l + 1 < depth;
+  S.Wc = has_child ? reinterpret_cast<const float2*>(p->W) + p->lev[l + 1].W_off : S.W;
+  S.T = T;
+  S.own = D.own;
+  S.ring = D.ring;
+  S.fsrc = D.fsrc;
+  S.nf = D.nf;
+  S.smax = D.smax;
+  S.bmax = D.bmax;
+  S.fmax = D.fmax;
+  S.ncols = D.ncols;
+  S.nf_c = has_child ? p->lev[l + 1].nf : 0;
+  S.fmax_c = has_child ? p->lev[l + 1].fmax : 0;
+  S.N = p->N;
+  const int K = tcs_k(D, MODE), rows = tcs_rows(D, MODE), ncols = ng * 16;
+  const char* cls = MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64";
+  const int gy_b = std::min(64, (K * ncols / 2 + 255) / 256), gy_c = std::min(64, (rows * ncols / 2 + 255) / 256);
+  LS_LAUNCH(cls, st, k_tcs_gather<MODE><<<dim3(D.nf, gy_b), 256, 0, st>>>(S, p->tcs_B, K, ncols));
+  // forward: A = Y (ring rows smax.., identity columns fmax..); backward: A = [H | F11^-1]
+  // (own rows, columns smax..ncols)
+  const int r0 = MODE == 0 ? D.smax : 0, k0 = MODE == 0 ? D.fmax : D.smax;
+  tc_sweep_gemm(reinterpret_cast<const float2*>(p->F) + D.F_off, (long)D.fmax * D.ncols, D.fmax, D.nf, r0, r0 + rows,
+                k0, k0 + K, p->tcs_B, (long)K * ncols, ncols, p->tcs_C, (long)rows * ncols, ncols, ncols, p->d_err, st,
+                cls);
+  LS_LAUNCH(cls, st, k_tcs_scatter<MODE><<<dim3(D.nf, gy_c), 256, 0, st>>>(S, p->tcs_C, rows, ncols));
+}
+
 template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int l, C* T, int ng, cudaStream_t st) {
+  if constexpr (sizeof(C) == 8 && RC == 16) {
+    if (tcs_level(p, l, MODE, ng)) {
+      launch_sweep_tc<MODE>(p, l, reinterpret_cast<float2*>(T), ng, st);
+      return;
+    }
+  }
   const SweepPlan q = sweep_plan(p->lev[l], MODE, ng, std::min(std::max(p->tune.sweep_ctas, 1), SWEEP_CTAS_MAX));
   if (q.K <= 0) return;
   if (q.nsplit > 1 && (size_t)p->lev[l].nf * q.ntile * q.nsplit * q.tr * RC * ng > p->part_elems)

@@ -20,6 +20,12 @@
 // commits each chunk to its stage's mbarrier; 65 KB of shared memory, three CTAs per SM.  All
 // waits are bounded and set *err on expiry, and the tensor memory is freed only after the
 // last commit has been awaited.
+//
+// The same kernel, instantiated with EXT, runs the multi-right-hand-side products of the
+// solve sweeps on the large fronts: C[z] = A[z] B[z] with A a block of front z (Y on its ring
+// rows for the forward sweep, [H | F11^-1] on its own rows for the backward one), B[z] the
+// gathered vector operand (k x right-hand side, right-hand sides contiguous) and C[z] a
+// dense result (row x right-hand side), both outside the fronts.
 #include <atomic>
 #include <cuda_runtime.h>
 
@@ -118,8 +124,17 @@ struct TcArgs {
   int* err;
   int test_no_mma;   // test hook: issue no MMA and no commit, so that the bounded waits expire
   long wait_limit;   // iterations of a bounded mbarrier wait
+  // EXT: B[z][k][n] = Bx[z * bstride + (k - k0) * ldb + n], C[z][r][n] = Cx[z * cstride +
+  // (r - r0) * ldc + n] (written, not accumulated); columns n in [c0, c1)
+  const float2* Bx;
+  long bstride;
+  int ldb;
+  float2* Cx;
+  long cstride;
+  int ldc;
 };
 
+template <bool EXT>
 __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -183,7 +198,11 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
     for (int u = 0; u < PB; ++u) {
       int n, k;
       b_of(u, n, k);
-      vb[u] = (k < kw && cb + n < a.c1) ? F[(size_t)(cb + n) * fmax + a.k0 + kc + k] : make_float2(0.f, 0.f);
+      if constexpr (EXT)
+        vb[u] = (k < kw && cb + n < a.c1) ? a.Bx[(size_t)z * a.bstride + (size_t)(kc + k) * a.ldb + cb + n]
+                                          : make_float2(0.f, 0.f);
+      else
+        vb[u] = (k < kw && cb + n < a.c1) ? F[(size_t)(cb + n) * fmax + a.k0 + kc + k] : make_float2(0.f, 0.f);
     }
   };
   // the registers of one chunk -> stage st: A' (TM x KP): element (m, 2k + p); B' (NP x KP,
@@ -302,7 +321,22 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
             "=r"(im[15])
           : "r"(tmem + lane_base + (uint32_t)(NT + col)));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (rb + m < a.r1)
+      if constexpr (EXT) {
+        // 16 consecutive right-hand sides of one row: 8 16-byte stores
+        if (rb + m < a.r1) {
+          float2* cr = a.Cx + (size_t)z * a.cstride + (size_t)(rb + m - a.r0) * a.ldc + cb + col;
+          if (cb + col + 16 <= a.c1) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2)
+              reinterpret_cast<float4*>(cr)[j / 2] = make_float4(__uint_as_float(re[j]), __uint_as_float(im[j]),
+                                                                 __uint_as_float(re[j + 1]), __uint_as_float(im[j + 1]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (cb + col + j < a.c1) cr[j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+          }
+        }
+      } else if (rb + m < a.r1) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = cb + col + j;
@@ -312,6 +346,7 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
             x.y -= __uint_as_float(im[j]);
           }
         }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -328,16 +363,20 @@ bool tc_enabled() {
   return on;
 }
 
+template <bool EXT> static void tc_smem_attr() {
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
+    LS_CUDA(cudaFuncSetAttribute(k_tc_cgemm<EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    attr.store(true, std::memory_order_release);
+  }
+}
+
 // C -= A B on every front of a level (see the file comment); a no-op for empty ranges
 void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0, int c1, int k0, int k1, int* err,
               cudaStream_t st) {
   if (r1 <= r0 || c1 <= c0 || k1 <= k0 || nf <= 0) return;
-  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
-  if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
-    attr.store(true, std::memory_order_release);
-  }
-  TcArgs a;
+  tc_smem_attr<false>();
+  TcArgs a{};
   // test hook (off unless LS_TEST_TC_TIMEOUT=1): no MMA is issued and the waits are short,
   // so that the bounded waits expire with nothing in flight and ls_factor reports LS_ETIMEOUT
   const char* hook = std::getenv("LS_TEST_TC_TIMEOUT");
@@ -350,7 +389,30 @@ void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0,
   a.ntr = (r1 - r0 + tc::TM - 1) / tc::TM;
   a.err = err;
   const int ntc = (c1 - c0 + tc::NT - 1) / tc::NT;
-  LS_LAUNCH("nd_gemm_tc_c64", st, k_tc_cgemm<<<dim3(nf, a.ntr * ntc), tc::THREADS, tc::SMEM, st>>>(a));
+  LS_LAUNCH("nd_gemm_tc_c64", st, k_tc_cgemm<false><<<dim3(nf, a.ntr * ntc), tc::THREADS, tc::SMEM, st>>>(a));
+}
+
+// C[z] = A[z] B[z] for the sweeps (see the file comment): A = rows [r0, r1) x columns
+// [k0, k1) of front z, B[z] (k1 - k0) x ncols at B + z * bstride (ld ldb), C[z]
+// (r1 - r0) x ncols at C + z * cstride (ld ldc)
+void tc_sweep_gemm(const float2* F, long fstride, int fmax, int nf, int r0, int r1, int k0, int k1, const float2* B,
+                   long bstride, int ldb, float2* C, long cstride, int ldc, int ncols, int* err, cudaStream_t st,
+                   const char* cls) {
+  if (r1 <= r0 || ncols <= 0 || k1 <= k0 || nf <= 0) return;
+  tc_smem_attr<true>();
+  TcArgs a{};
+  a.test_no_mma = 0;
+  a.wait_limit = tc::WAIT_LIMIT;
+  a.F = const_cast<float2*>(F);
+  a.fstride = fstride;
+  a.fmax = fmax;
+  a.r0 = r0; a.r1 = r1; a.c0 = 0; a.c1 = ncols; a.k0 = k0; a.k1 = k1;
+  a.ntr = (r1 - r0 + tc::TM - 1) / tc::TM;
+  a.err = err;
+  a.Bx = B; a.bstride = bstride; a.ldb = ldb;
+  a.Cx = C; a.cstride = cstride; a.ldc = ldc;
+  const int ntc = (ncols + tc::NT - 1) / tc::NT;
+  LS_LAUNCH(cls, st, k_tc_cgemm<true><<<dim3(nf, a.ntr * ntc), tc::THREADS, tc::SMEM, st>>>(a));
 }
 
 }  // namespace ls

@@ -33,7 +33,7 @@ EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls
            "ls_export_factors", "ls_import_factors",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
-           "ls_profile_start", "ls_profile_stop", "ls_autotune", "ls_tune_info", "ls_apply_noalloc"]
+           "ls_profile_start", "ls_profile_stop", "ls_autotune", "ls_tune_info", "ls_set_tune", "ls_apply_noalloc"]
 
 
 class LsGrid(ctypes.Structure):
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_apply_noalloc.argtypes = [vp, ip, vp, vp]
     lib.ls_autotune.argtypes = [vp, ip, ctypes.c_char_p, ip]
     lib.ls_tune_info.argtypes = [vp, ctypes.c_char_p, ip]
+    lib.ls_set_tune.argtypes = [vp, ctypes.c_char_p]
     lib.ls_profile_start.argtypes = [ctypes.c_char_p]
     lib.ls_profile_stop.argtypes = [ctypes.c_char_p, ip]
     for name in EXPORTS:
@@ -447,6 +448,11 @@ class Solver:
         buf = ctypes.create_string_buffer(1024)
         self._check(self.lib.ls_tune_info(self.h, buf, len(buf)))
         return json.loads(buf.value.decode())
+
+    def set_tune(self, choices: dict) -> None:
+        """ls_set_tune: apply launch-shape choices (any keys of tune()) to this context."""
+        import json
+        self._check(self.lib.ls_set_tune(self.h, json.dumps(choices).encode()))
 
     def nd_stats(self) -> dict:
         s = LsNdStats()

@@ -36,6 +36,7 @@ def main(argv=None) -> int:
     ap.add_argument("--d", type=int, default=2)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--tune", default=None, help="launch-shape choices to apply (JSON object, as ls_set_tune takes)")
     a = ap.parse_args(argv)
     os.environ["LS_GRAPHS"] = "0"  # read by ls_setup: every launch stays a separate kernel
     import torch
@@ -44,6 +45,8 @@ def main(argv=None) -> int:
 
     m, omega = _medium(W, a.d, a.n)
     s = ls.Solver(torch.tensor(m, device="cuda"), omega, dim=a.d, mixed=True)
+    if a.tune:
+        s.set_tune(json.loads(a.tune))
     shape = (a.nrhs,) + (a.n,) * a.d
     x = torch.randn(shape, dtype=torch.complex128, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     out = {"case": a.case, "d": a.d, "n": a.n, "nrhs": a.nrhs}

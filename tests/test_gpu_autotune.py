@@ -36,7 +36,8 @@ def test_autotune_applies_keeps_and_persists_its_choice(LS, tmp_path, monkeypatc
         choice = rep["choice"]
         assert s.tune() == choice
         assert len(rep["factor_ms"]) >= 4 and all(ms > 0 for _, ms in rep["factor_ms"])
-        assert len(rep["solve_ms"]) == 3 and all(ms > 0 for _, ms in rep["solve_ms"])
+        # sweep split: the base and 2 alternatives; solve levels on the tensor cores: 3 more
+        assert len(rep["solve_ms"]) == 6 and all(ms > 0 for _, ms in rep["solve_ms"])
         # left factored with the chosen shapes
         g = s.rhs_plane_wave(dirs)
         u, info = s.solve(g, tol=1e-6)
@@ -53,3 +54,20 @@ def test_autotune_applies_keeps_and_persists_its_choice(LS, tmp_path, monkeypatc
         assert s2.tune() == choice
     with LS.Solver(m, omega, mixed=False) as s3:  # another precision keeps the defaults
         assert s3.tune()["sweep_ctas"] == 2
+
+
+def test_set_tune_validates_and_applies(LS):
+    n, d = 32, 2
+    m = W.enforce_buffer(W.bumps(n, d, [0.1], [0.1], [[0.5, 0.5]]), 2)
+    with LS.Solver(m, 2 * np.pi * 4, mixed=True) as s:
+        base = s.tune()
+        s.set_tune({"tcs_min_rows": 128, "sweep_ctas": 4, "unknown": 1})
+        t = s.tune()
+        assert t["tcs_min_rows"] == 128 and t["sweep_ctas"] == 4
+        assert {k: v for k, v in t.items() if k not in ("tcs_min_rows", "sweep_ctas")} == \
+            {k: v for k, v in base.items() if k not in ("tcs_min_rows", "sweep_ctas")}
+        for bad in ({"sweep_ctas": 5}, {"gj_max_own": 0}, {"two_level_min": -1}, {"tcs_min_rows": 1.5}):
+            with pytest.raises(LS.LsError) as e:
+                s.set_tune(bad)
+            assert e.value.status == LS.LS_EINVAL
+        assert s.tune() == t
