@@ -386,8 +386,9 @@ ls_status ls_profile_stop(char* report, int capacity);
  * launch-shape choices that have no single best value across grids: the trailing-matrix size
  * from which the blocked front LU updates in two levels, the smallest FP32 Schur product
  * (rows) given to the tensor cores, the largest front factored Gauss-Jordan style in one CTA,
- * how many CTAs per SM the split of a solve sweep level aims at, and the smallest FP32 solve
- * level (rows of its product, at least 64) run on the tensor cores.  A coordinate search
+ * how many CTAs per SM the split of a solve sweep level aims at, and the smallest FP32
+ * forward and backward solve levels (rows of their products, at least 64) run on the tensor
+ * cores.  A coordinate search
  * keeps each alternative that is more than 2 % faster (the fastest of 2 factorizations / 3
  * solves of nrhs right-hand sides, CUDA events).  The choice is applied to c, kept for every
  * later context of the same (dim, n, prec, kernel) in this process, and, when the
@@ -405,7 +406,7 @@ ls_status ls_profile_stop(char* report, int capacity);
  *   ls_factor uses the factorization choices, the next solve the solve choices (a change of
  *   a factorization choice needs a new ls_factor to take effect).  LS_EINVAL when a value is
  *   out of range (two_level_min <= 0, tc_min_rows < 1, sweep_ctas outside 1..4,
- *   gj_max_own outside 1..32, tcs_min_rows < 1).
+ *   gj_max_own outside 1..32, tcs_min_rows or tcs_bwd_min_rows < 1).
  * --------------------------------------------------------------------------------------- */
 ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity);
 ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity);

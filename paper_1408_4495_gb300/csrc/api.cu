@@ -637,9 +637,10 @@ static void tune_load_locked() {
     ls::NdTune t;
     if (std::sscanf(line,
                     "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %lf, "
-                    "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d}",
+                    "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d, "
+                    "\"tcs_bwd_min_rows\": %d}",
                     &k.d, &k.n, &k.prec, &k.laplace, &t.two_level_min, &t.tc_min_rows, &t.sweep_ctas,
-                    &t.gj_max_own, &t.tcs_min_rows) == 9)
+                    &t.gj_max_own, &t.tcs_min_rows, &t.tcs_bwd_min_rows) == 10)
       g_tune[k] = t;
   }
   std::fclose(f);
@@ -654,9 +655,11 @@ static void tune_save_locked() {
   for (const auto& kv : g_tune)
     std::fprintf(f,
                  "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %.17g, "
-                 "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d}\n",
+                 "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d, "
+                 "\"tcs_bwd_min_rows\": %d}\n",
                  kv.first.d, kv.first.n, kv.first.prec, kv.first.laplace, kv.second.two_level_min,
-                 kv.second.tc_min_rows, kv.second.sweep_ctas, kv.second.gj_max_own, kv.second.tcs_min_rows);
+                 kv.second.tc_min_rows, kv.second.sweep_ctas, kv.second.gj_max_own, kv.second.tcs_min_rows,
+                 kv.second.tcs_bwd_min_rows);
   std::fclose(f);
   std::rename(tmp.c_str(), path);
 }
@@ -674,8 +677,8 @@ static std::string tune_json(const ls::NdTune& t) {
   char b[256];
   std::snprintf(b, sizeof b,
                 "{\"two_level_min\": %.6g, \"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, "
-                "\"tcs_min_rows\": %d}",
-                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own, t.tcs_min_rows);
+                "\"tcs_min_rows\": %d, \"tcs_bwd_min_rows\": %d}",
+                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own, t.tcs_min_rows, t.tcs_bwd_min_rows);
   return b;
 }
 
@@ -1473,13 +1476,16 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
       try_solve(t);
     }
     if (mixed) {
-      // solve levels on the tensor cores from 64 rows (the default), from 128 or 256, or none
-      const int tcs_base = best.tcs_min_rows;
-      for (int v : {64, 128, 256, 1 << 30}) {
-        if (v == tcs_base) continue;
-        ls::NdTune t = best;
-        t.tcs_min_rows = v;
-        try_solve(t);
+      // forward and backward solve levels on the tensor cores from 64 rows (the default),
+      // from 128 or 256, or none
+      for (int bwd = 0; bwd < 2; ++bwd) {
+        const int base = bwd ? best.tcs_bwd_min_rows : best.tcs_min_rows;
+        for (int v : {64, 128, 256, 1 << 30}) {
+          if (v == base) continue;
+          ls::NdTune t = best;
+          (bwd ? t.tcs_bwd_min_rows : t.tcs_min_rows) = v;
+          try_solve(t);
+        }
       }
     }
     ls::nd_set_tune(c->nd, best);
@@ -1544,6 +1550,7 @@ ls_status ls_set_tune(ls_ctx* c, const char* json) {
     int_key("sweep_ctas", 1, ls::SWEEP_CTAS_MAX, &t.sweep_ctas);
     int_key("gj_max_own", 1, 32, &t.gj_max_own);
     int_key("tcs_min_rows", 1, 1 << 30, &t.tcs_min_rows);
+    int_key("tcs_bwd_min_rows", 1, 1 << 30, &t.tcs_bwd_min_rows);
     factor_wait(c);
     ls::nd_set_tune(c->nd, t);
     ++c->gen;  // the captured graphs hold the old launch sequences

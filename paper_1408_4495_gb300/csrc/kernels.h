@@ -75,9 +75,10 @@ void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0,
               cudaStream_t st);
 // C[z] = A[z] B[z] on every front z of a level, A = rows [r0, r1) x columns [k0, k1) of the
 // front, B and C dense per front outside it (tc_gemm.cu); launches counted under cls
+// (k range split nsplit ways, ksz columns each, partial products split_stride apart)
 void tc_sweep_gemm(const float2* F, long fstride, int fmax, int nf, int r0, int r1, int k0, int k1, const float2* B,
-                   long bstride, int ldb, float2* C, long cstride, int ldc, int ncols, int* err, cudaStream_t st,
-                   const char* cls);
+                   long bstride, int ldb, float2* C, long cstride, int ldc, int ncols, int nsplit, int ksz,
+                   long split_stride, int* err, cudaStream_t st, const char* cls);
 // tensor-core products on (LS_TC=0 in the environment turns them off, for comparisons)
 bool tc_enabled();
 // float-float copy of count FP64 reals (dst: 2 * count floats)
@@ -157,8 +158,9 @@ struct NdTune {
                                  // inner columns) run on the tensor cores
   int sweep_ctas = 2;            // CTAs per SM that the split of a sweep level's columns aims at
   int gj_max_own = 16;           // fronts with at most this many own rows: Gauss-Jordan in one CTA
-  int tcs_min_rows = 64;         // FP32 solve levels whose products have at least this many rows
-                                 // (and 16 inner columns) run on the tensor cores
+  int tcs_min_rows = 64;         // FP32 forward-sweep levels whose products have at least this
+                                 // many rows (and 16 inner columns) run on the tensor cores
+  int tcs_bwd_min_rows = 64;     // the same for the backward sweep
 };
 constexpr int SWEEP_CTAS_MAX = 4;  // the solve's partial-sum buffers are sized for this target
 void nd_set_tune(NdPlan* p, const NdTune& t);

@@ -488,13 +488,26 @@ NdInfo nd_info(const NdPlan* p) { return p->info; }
 constexpr int TCS_MIN_ROWS = 64;
 static int tcs_rows(const LevelDev& D, int mode) { return mode == 0 ? D.bmax : D.smax; }
 static int tcs_k(const LevelDev& D, int mode) { return mode == 0 ? D.smax : D.bmax + D.smax; }
+// split of a level's k range over CTAs: enough CTAs for three per SM (the tensor-core GEMM's
+// residency) with at least 64 columns (8 chunks) per split
+struct TcsSplit {
+  int nsplit, ksz;
+};
+static TcsSplit tcs_split(const LevelDev& D, int mode) {
+  const int K = tcs_k(D, mode), rows = tcs_rows(D, mode);
+  const long base = (long)D.nf * ((rows + 127) / 128);
+  int ns = 1;
+  while (base * ns < 3L * 152 && (K + 2 * ns - 1) / (2 * ns) >= 64) ns *= 2;
+  const int ksz = ((K + ns - 1) / ns + 7) / 8 * 8;
+  return {(K + ksz - 1) / ksz, ksz};
+}
 static void tcs_sizes(const std::vector<LevelDev>& lev, size_t* b, size_t* c) {
   *b = *c = 0;
   for (const LevelDev& D : lev)
     for (int mode = 0; mode < 2; ++mode)
       if (tcs_rows(D, mode) >= TCS_MIN_ROWS) {
         *b = std::max(*b, (size_t)D.nf * tcs_k(D, mode) * SOLVE_CHUNK);
-        *c = std::max(*c, (size_t)D.nf * tcs_rows(D, mode) * SOLVE_CHUNK);
+        *c = std::max(*c, (size_t)D.nf * tcs_rows(D, mode) * SOLVE_CHUNK * tcs_split(D, mode).nsplit);
       }
 }
 
@@ -2412,14 +2425,18 @@ __global__ void __launch_bounds__(256) k_tcs_gather(SweepK<float2> S, float2* __
   }
 }
 
+// the k-range splits' partial products are added in split order (nsplit arrays split_stride
+// apart)
 template <int MODE>
 __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const float2* __restrict__ Cm, int rows,
-                                                     int ncols) {
+                                                     int ncols, int nsplit, long split_stride) {
   const int z = blockIdx.x, pairs = ncols / 2;
   const float2* Cz = Cm + (size_t)z * rows * ncols;
   for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < rows * pairs; t += gridDim.y * blockDim.x) {
     const int i = t / pairs, n = 2 * (t - i * pairs), g = n >> 4, j = n & 15;
     float4 v = __ldcg(reinterpret_cast<const float4*>(Cz + (size_t)i * ncols + n));
+    for (int sp = 1; sp < nsplit; ++sp)
+      v = padd(v, __ldcg(reinterpret_cast<const float4*>(Cz + sp * split_stride + (size_t)i * ncols + n)));
     if (MODE == 0) {
       const int p0 = S.smax + i;
       const int s0 = __ldg(S.fsrc + ((size_t)z * S.fmax + p0) * 2), s1 = __ldg(S.fsrc + ((size_t)z * S.fmax + p0) * 2 + 1);
@@ -2438,9 +2455,10 @@ __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const flo
 static bool tcs_level(const NdPlan* p, int l, int mode, int ng) {
   const LevelDev& D = p->lev[l];
   const int rows = tcs_rows(D, mode);
-  return p->use_tc && tc_enabled() && p->tcs_B && p->tcs_C && rows >= std::max(TCS_MIN_ROWS, p->tune.tcs_min_rows) &&
+  const int min_rows = mode == 0 ? p->tune.tcs_min_rows : p->tune.tcs_bwd_min_rows;
+  return p->use_tc && tc_enabled() && p->tcs_B && p->tcs_C && rows >= std::max(TCS_MIN_ROWS, min_rows) &&
          tcs_k(D, mode) >= TC_MIN_K && (size_t)D.nf * tcs_k(D, mode) * ng * 16 <= p->tcs_B_elems &&
-         (size_t)D.nf * rows * ng * 16 <= p->tcs_C_elems;
+         (size_t)D.nf * rows * ng * 16 * tcs_split(D, mode).nsplit <= p->tcs_C_elems;
 }
 
 template <int MODE> static void launch_sweep_tc(NdPlan* p, int l, float2* T, int ng, cudaStream_t st) {
@@ -2470,10 +2488,13 @@ template <int MODE> static void launch_sweep_tc(NdPlan* p, int l, float2* T, int
   // forward: A = Y (ring rows smax.., identity columns fmax..); backward: A = [H | F11^-1]
   // (own rows, columns smax..ncols)
   const int r0 = MODE == 0 ? D.smax : 0, k0 = MODE == 0 ? D.fmax : D.smax;
+  const TcsSplit sp = tcs_split(D, MODE);
+  const long split_stride = (long)D.nf * rows * ncols;
   tc_sweep_gemm(reinterpret_cast<const float2*>(p->F) + D.F_off, (long)D.fmax * D.ncols, D.fmax, D.nf, r0, r0 + rows,
-                k0, k0 + K, p->tcs_B, (long)K * ncols, ncols, p->tcs_C, (long)rows * ncols, ncols, ncols, p->d_err, st,
-                cls);
-  LS_LAUNCH(cls, st, k_tcs_scatter<MODE><<<dim3(D.nf, gy_c), 256, 0, st>>>(S, p->tcs_C, rows, ncols));
+                k0, k0 + K, p->tcs_B, (long)K * ncols, ncols, p->tcs_C, (long)rows * ncols, ncols, ncols, sp.nsplit,
+                sp.ksz, split_stride, p->d_err, st, cls);
+  LS_LAUNCH(cls, st,
+            k_tcs_scatter<MODE><<<dim3(D.nf, gy_c), 256, 0, st>>>(S, p->tcs_C, rows, ncols, sp.nsplit, split_stride));
 }
 
 template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int l, C* T, int ng, cudaStream_t st) {

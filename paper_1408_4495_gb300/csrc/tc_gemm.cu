@@ -125,13 +125,17 @@ struct TcArgs {
   int test_no_mma;   // test hook: issue no MMA and no commit, so that the bounded waits expire
   long wait_limit;   // iterations of a bounded mbarrier wait
   // EXT: B[z][k][n] = Bx[z * bstride + (k - k0) * ldb + n], C[z][r][n] = Cx[z * cstride +
-  // (r - r0) * ldc + n] (written, not accumulated); columns n in [c0, c1)
+  // (r - r0) * ldc + n] (written, not accumulated); columns n in [c0, c1).  The k range may be
+  // split over grid.z: split s takes k in [k0 + s ksz, k0 + (s + 1) ksz) and writes its
+  // partial product to Cx + s * split_stride
   const float2* Bx;
   long bstride;
   int ldb;
   float2* Cx;
   long cstride;
   int ldc;
+  int ksz;
+  long split_stride;
 };
 
 template <bool EXT>
@@ -166,7 +170,8 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  const int K = a.k1 - a.k0;
+  const int kbeg = EXT ? (int)blockIdx.z * a.ksz : 0;
+  const int K = EXT ? min(a.k1 - a.k0 - kbeg, a.ksz) : a.k1 - a.k0;
   const int nchunk = (K + KC - 1) / KC;
   // global loads of one chunk into registers.  Element u of a thread: idx = u * THREADS + tid,
   // group idx / 32 of 32 entries = 8 consecutive rows (or B columns) x 4 consecutive k, lane
@@ -192,14 +197,14 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
     for (int u = 0; u < PA; ++u) {
       int m, k;
       a_of(u, m, k);
-      va[u] = (k < kw && rb + m < a.r1) ? F[(size_t)(a.k0 + kc + k) * fmax + rb + m] : make_float2(0.f, 0.f);
+      va[u] = (k < kw && rb + m < a.r1) ? F[(size_t)(a.k0 + kbeg + kc + k) * fmax + rb + m] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
       int n, k;
       b_of(u, n, k);
       if constexpr (EXT)
-        vb[u] = (k < kw && cb + n < a.c1) ? a.Bx[(size_t)z * a.bstride + (size_t)(kc + k) * a.ldb + cb + n]
+        vb[u] = (k < kw && cb + n < a.c1) ? a.Bx[(size_t)z * a.bstride + (size_t)(kbeg + kc + k) * a.ldb + cb + n]
                                           : make_float2(0.f, 0.f);
       else
         vb[u] = (k < kw && cb + n < a.c1) ? F[(size_t)(cb + n) * fmax + a.k0 + kc + k] : make_float2(0.f, 0.f);
@@ -324,7 +329,8 @@ __global__ void __launch_bounds__(tc::THREADS) k_tc_cgemm(TcArgs a) {
       if constexpr (EXT) {
         // 16 consecutive right-hand sides of one row: 8 16-byte stores
         if (rb + m < a.r1) {
-          float2* cr = a.Cx + (size_t)z * a.cstride + (size_t)(rb + m - a.r0) * a.ldc + cb + col;
+          float2* cr = a.Cx + (size_t)blockIdx.z * a.split_stride + (size_t)z * a.cstride +
+                       (size_t)(rb + m - a.r0) * a.ldc + cb + col;
           if (cb + col + 16 <= a.c1) {
 #pragma unroll
             for (int j = 0; j < 16; j += 2)
@@ -394,11 +400,15 @@ void tc_cgemm(float2* F, long fstride, int fmax, int nf, int r0, int r1, int c0,
 
 // C[z] = A[z] B[z] for the sweeps (see the file comment): A = rows [r0, r1) x columns
 // [k0, k1) of front z, B[z] (k1 - k0) x ncols at B + z * bstride (ld ldb), C[z]
-// (r1 - r0) x ncols at C + z * cstride (ld ldc)
+// (r1 - r0) x ncols at C + z * cstride (ld ldc); with nsplit > 1 split s of the k range
+// (ksz columns each, a multiple of the chunk) writes its partial product at
+// C + s * split_stride (the caller adds them)
 void tc_sweep_gemm(const float2* F, long fstride, int fmax, int nf, int r0, int r1, int k0, int k1, const float2* B,
-                   long bstride, int ldb, float2* C, long cstride, int ldc, int ncols, int* err, cudaStream_t st,
-                   const char* cls) {
+                   long bstride, int ldb, float2* C, long cstride, int ldc, int ncols, int nsplit, int ksz,
+                   long split_stride, int* err, cudaStream_t st, const char* cls) {
   if (r1 <= r0 || ncols <= 0 || k1 <= k0 || nf <= 0) return;
+  if (nsplit < 1 || ksz % tc::KC != 0 || (long)(nsplit - 1) * ksz >= k1 - k0 || (long)nsplit * ksz < k1 - k0)
+    LS_FAIL(EINVAL_, "tensor-core sweep: bad split of the k range");
   tc_smem_attr<true>();
   TcArgs a{};
   a.test_no_mma = 0;
@@ -411,8 +421,9 @@ void tc_sweep_gemm(const float2* F, long fstride, int fmax, int nf, int r0, int 
   a.err = err;
   a.Bx = B; a.bstride = bstride; a.ldb = ldb;
   a.Cx = C; a.cstride = cstride; a.ldc = ldc;
+  a.ksz = ksz; a.split_stride = split_stride;
   const int ntc = (ncols + tc::NT - 1) / tc::NT;
-  LS_LAUNCH(cls, st, k_tc_cgemm<true><<<dim3(nf, a.ntr * ntc), tc::THREADS, tc::SMEM, st>>>(a));
+  LS_LAUNCH(cls, st, k_tc_cgemm<true><<<dim3(nf, a.ntr * ntc, nsplit), tc::THREADS, tc::SMEM, st>>>(a));
 }
 
 }  // namespace ls

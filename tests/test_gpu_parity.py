@@ -324,7 +324,7 @@ def test_tensor_core_sweep_levels(LS, d, n, freq, nrhs, bound):
     with LS.Solver(m, omega, mixed=True) as s:
         s.factor()
         for tcs in (64, off):
-            s.set_tune({"tcs_min_rows": tcs})
+            s.set_tune({"tcs_min_rows": tcs, "tcs_bwd_min_rows": tcs})
             LS.profile_start(None)
             z[tcs] = s.precond(x)
             counts = LS.profile_stop()["counts"]
