@@ -387,7 +387,7 @@ ls_status ls_profile_stop(char* report, int capacity);
  * from which the blocked front LU updates in two levels, the smallest FP32 Schur product
  * (rows) given to the tensor cores, the largest front factored Gauss-Jordan style in one CTA,
  * how many CTAs per SM the split of a solve sweep level aims at, and the smallest FP32
- * forward and backward solve levels (rows of their products, at least 64) run on the tensor
+ * forward and backward solve levels (rows of their products, at least 32) run on the tensor
  * cores.  A coordinate search
  * keeps each alternative that is more than 2 % faster (the fastest of 2 factorizations / 3
  * solves of nrhs right-hand sides, CUDA events).  The choice is applied to c, kept for every

@@ -1477,10 +1477,10 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
     }
     if (mixed) {
       // forward and backward solve levels on the tensor cores from 64 rows (the default),
-      // from 128 or 256, or none
+      // from 32, 128 or 256, or none
       for (int bwd = 0; bwd < 2; ++bwd) {
         const int base = bwd ? best.tcs_bwd_min_rows : best.tcs_min_rows;
-        for (int v : {64, 128, 256, 1 << 30}) {
+        for (int v : {32, 64, 128, 256, 1 << 30}) {
           if (v == base) continue;
           ls::NdTune t = best;
           (bwd ? t.tcs_bwd_min_rows : t.tcs_min_rows) = v;

@@ -485,7 +485,7 @@ NdInfo nd_info(const NdPlan* p) { return p->info; }
 
 // rows of a sweep level's product from which it may run on the tensor cores, and its
 // operand sizes for SOLVE_CHUNK right-hand sides (mode 0 forward, 1 backward)
-constexpr int TCS_MIN_ROWS = 64;
+constexpr int TCS_MIN_ROWS = 32;
 static int tcs_rows(const LevelDev& D, int mode) { return mode == 0 ? D.bmax : D.smax; }
 static int tcs_k(const LevelDev& D, int mode) { return mode == 0 ? D.smax : D.bmax + D.smax; }
 // split of a level's k range over CTAs: enough CTAs for three per SM (the tensor-core GEMM's

@@ -37,8 +37,8 @@ def test_autotune_applies_keeps_and_persists_its_choice(LS, tmp_path, monkeypatc
         assert s.tune() == choice
         assert len(rep["factor_ms"]) >= 4 and all(ms > 0 for _, ms in rep["factor_ms"])
         # sweep split: the base and 2 alternatives; forward and backward solve levels on the
-        # tensor cores: 3 more each
-        assert len(rep["solve_ms"]) == 9 and all(ms > 0 for _, ms in rep["solve_ms"])
+        # tensor cores: 4 more each
+        assert len(rep["solve_ms"]) == 11 and all(ms > 0 for _, ms in rep["solve_ms"])
         # left factored with the chosen shapes
         g = s.rhs_plane_wave(dirs)
         u, info = s.solve(g, tol=1e-6)

@@ -303,8 +303,9 @@ TCS_CASES = [(2, 128, 16.0, 40, 2e-5), (2, 256, 32.0, 16, 2e-3), (3, 32, 4.0, 24
 
 @pytest.mark.parametrize("d,n,freq,nrhs,bound", TCS_CASES)
 def test_tensor_core_sweep_levels(LS, d, n, freq, nrhs, bound):
-    """FP32 solve levels whose products have at least 64 rows run as one batched tcgen05
-    GEMM (3xTF32) between a gather of the vector operand and a scatter of the result, when
+    """FP32 solve levels whose products have at least 64 rows (the default threshold) run
+    as one batched tcgen05 GEMM (3xTF32) between a gather of the vector operand and a
+    scatter of the result, when
     16 right-hand sides share an item (more than 4 right-hand sides).  The same application
     with every level on the CUDA-core sweep kernel (tcs_min_rows above every level) is the
     comparison: both meet the backward-error bound against the oracle's assembled M, the
