@@ -638,9 +638,9 @@ static void tune_load_locked() {
     if (std::sscanf(line,
                     "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %lf, "
                     "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d, "
-                    "\"tcs_bwd_min_rows\": %d}",
+                    "\"tcs_bwd_min_rows\": %d, \"small_max_k\": %d}",
                     &k.d, &k.n, &k.prec, &k.laplace, &t.two_level_min, &t.tc_min_rows, &t.sweep_ctas,
-                    &t.gj_max_own, &t.tcs_min_rows, &t.tcs_bwd_min_rows) == 10)
+                    &t.gj_max_own, &t.tcs_min_rows, &t.tcs_bwd_min_rows, &t.small_max_k) == 11)
       g_tune[k] = t;
   }
   std::fclose(f);
@@ -656,10 +656,10 @@ static void tune_save_locked() {
     std::fprintf(f,
                  "{\"d\": %d, \"n\": %d, \"prec\": %d, \"laplace\": %d, \"two_level_min\": %.17g, "
                  "\"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, \"tcs_min_rows\": %d, "
-                 "\"tcs_bwd_min_rows\": %d}\n",
+                 "\"tcs_bwd_min_rows\": %d, \"small_max_k\": %d}\n",
                  kv.first.d, kv.first.n, kv.first.prec, kv.first.laplace, kv.second.two_level_min,
                  kv.second.tc_min_rows, kv.second.sweep_ctas, kv.second.gj_max_own, kv.second.tcs_min_rows,
-                 kv.second.tcs_bwd_min_rows);
+                 kv.second.tcs_bwd_min_rows, kv.second.small_max_k);
   std::fclose(f);
   std::rename(tmp.c_str(), path);
 }
@@ -677,8 +677,9 @@ static std::string tune_json(const ls::NdTune& t) {
   char b[256];
   std::snprintf(b, sizeof b,
                 "{\"two_level_min\": %.6g, \"tc_min_rows\": %d, \"sweep_ctas\": %d, \"gj_max_own\": %d, "
-                "\"tcs_min_rows\": %d, \"tcs_bwd_min_rows\": %d}",
-                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own, t.tcs_min_rows, t.tcs_bwd_min_rows);
+                "\"tcs_min_rows\": %d, \"tcs_bwd_min_rows\": %d, \"small_max_k\": %d}",
+                t.two_level_min, t.tc_min_rows, t.sweep_ctas, t.gj_max_own, t.tcs_min_rows, t.tcs_bwd_min_rows,
+                t.small_max_k);
   return b;
 }
 
@@ -1487,6 +1488,14 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
           try_solve(t);
         }
       }
+      // the bottom levels one warp per front up to 64 columns (the default), up to 32, or none
+      const int small_base = best.small_max_k;
+      for (int v : {0, 32, 64}) {
+        if (v == small_base) continue;
+        ls::NdTune t = best;
+        t.small_max_k = v;
+        try_solve(t);
+      }
     }
     ls::nd_set_tune(c->nd, best);
     cudaEventDestroy(e0);
@@ -1551,6 +1560,7 @@ ls_status ls_set_tune(ls_ctx* c, const char* json) {
     int_key("gj_max_own", 1, 32, &t.gj_max_own);
     int_key("tcs_min_rows", 1, 1 << 30, &t.tcs_min_rows);
     int_key("tcs_bwd_min_rows", 1, 1 << 30, &t.tcs_bwd_min_rows);
+    int_key("small_max_k", 0, 64, &t.small_max_k);
     factor_wait(c);
     ls::nd_set_tune(c->nd, t);
     ++c->gen;  // the captured graphs hold the old launch sequences

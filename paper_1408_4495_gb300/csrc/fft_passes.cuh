@@ -194,16 +194,94 @@ template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR(C* v
   else dft<2, SIGN, C>(v);
 }
 
+// Pruned butterflies for the zero-padded transforms: every forward transform of the
+// operator reads n = L / 2 entries (the rest is zero padding) and every inverse one keeps
+// n = L / 2 outputs (the crop).
+// 4-point DFT of (a0, a1, 0, 0): X0 = a0 + a1, X1 = a0 + rot(a1), X2 = a0 - a1, X3 = a0 - rot(a1)
+template <int SIGN, typename C> __device__ __forceinline__ void dft4_lo(C& a0, C& a1, C& a2, C& a3) {
+  const C b = a1, r = rot_i<SIGN>(a1);
+  a1 = cadd(a0, r);
+  a2 = csub(a0, b);
+  a3 = csub(a0, r);
+  a0 = cadd(a0, b);
+}
+// 8-point DFT of (v0, v1, v2, v3, 0, 0, 0, 0) (the first pass of a padded transform)
+template <int SIGN, typename C> __device__ __forceinline__ void dft8v_lo(C* v) {
+  using Rl = typename RealOf<C>::T;
+  const Rl c = cos_pi4<Rl>();
+  C e0 = v[0], e1 = v[2], e2, e3;
+  C o0 = v[1], o1 = v[3], o2, o3;
+  dft4_lo<SIGN>(e0, e1, e2, e3);
+  dft4_lo<SIGN>(o0, o1, o2, o3);
+  C t;
+  if (SIGN > 0) {
+    t.x = r_mul(c, r_sub(o1.x, o1.y)); t.y = r_mul(c, r_add(o1.x, o1.y)); o1 = t;
+  } else {
+    t.x = r_mul(c, r_add(o1.x, o1.y)); t.y = r_mul(c, r_sub(o1.y, o1.x)); o1 = t;
+  }
+  o2 = rot_i<SIGN>(o2);
+  if (SIGN > 0) {
+    t.x = r_neg(r_mul(c, r_add(o3.x, o3.y))); t.y = r_mul(c, r_sub(o3.x, o3.y)); o3 = t;
+  } else {
+    t.x = r_mul(c, r_sub(o3.y, o3.x)); t.y = r_neg(r_mul(c, r_add(o3.x, o3.y))); o3 = t;
+  }
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+// outputs 0 .. R/2 - 1 only (the last pass of a cropped transform; R even)
+template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR_hi_cut(C* v) {
+  if constexpr (R == 8) {
+    using Rl = typename RealOf<C>::T;
+    const Rl c = cos_pi4<Rl>();
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<SIGN>(e0, e1, e2, e3);
+    dft4<SIGN>(o0, o1, o2, o3);
+    C t;
+    if (SIGN > 0) {
+      t.x = r_mul(c, r_sub(o1.x, o1.y)); t.y = r_mul(c, r_add(o1.x, o1.y)); o1 = t;
+    } else {
+      t.x = r_mul(c, r_add(o1.x, o1.y)); t.y = r_mul(c, r_sub(o1.y, o1.x)); o1 = t;
+    }
+    o2 = rot_i<SIGN>(o2);
+    if (SIGN > 0) {
+      t.x = r_neg(r_mul(c, r_add(o3.x, o3.y))); t.y = r_mul(c, r_sub(o3.x, o3.y)); o3 = t;
+    } else {
+      t.x = r_mul(c, r_sub(o3.y, o3.x)); t.y = r_neg(r_mul(c, r_add(o3.x, o3.y))); o3 = t;
+    }
+    v[0] = cadd(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[3] = cadd(e3, o3);
+  } else if constexpr (R == 4) {
+    const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]), t2 = cadd(v[1], v[3]);
+    const C t3 = rot_i<SIGN>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[1] = cadd(t1, t3);
+  } else {
+    static_assert(R == 2, "cropped last pass: even radix");
+    v[0] = cadd(v[0], v[1]);
+  }
+}
+
 // One radix-R Stockham pass over NLINES lines of length L held in shared memory.
 // Pass input: sub-transforms of length NS; output: sub-transforms of length NS * R.
 // Butterfly j of a line reads entries j + r L/R, multiplies by w^{r k} with
 // w = exp(SIGN 2 pi i / (NS R)), k = j mod NS, and writes (j / NS) NS R + k + r NS.
-template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT>
+// PRUNE 1: the first pass of a zero-padded transform (entries L/2.. are zero: inputs
+// r >= R/2 are neither read nor used); PRUNE 2: the last pass of a cropped transform
+// (outputs L/2.. are not needed: r >= R/2 neither computed nor stored).
+template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT, int PRUNE = 0>
 __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
   using SL = SLay<C, L, NLINES>;
   constexpr int BPL = L / R;
   constexpr int BF = NLINES * BPL;
   constexpr int PER = (BF + NT - 1) / NT;
+  static_assert(PRUNE != 1 || (NS == 1 && R == 8), "padded first pass: radix 8");
+  static_assert(PRUNE != 2 || (NS * R == L && R % 2 == 0), "cropped last pass: even radix");
+  constexpr int RIN = PRUNE == 1 ? R / 2 : R, ROUT = PRUNE == 2 ? R / 2 : R;
   C v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -213,10 +291,10 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
       if constexpr (SL::shift_free(BPL)) {
         const int o = SL::off(line, j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = s[o + r * BPL];
+        for (int r = 0; r < RIN; ++r) v[q][r] = s[o + r * BPL];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = s[SL::off(line, j + r * BPL)];
+        for (int r = 0; r < RIN; ++r) v[q][r] = s[SL::off(line, j + r * BPL)];
       }
       if constexpr (NS > 1) {
         const int k = j % NS;
@@ -227,7 +305,9 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
           v[q][r] = cmul(v[q][r], w);
         }
       }
-      dftR<R, SIGN>(v[q]);
+      if constexpr (PRUNE == 1) dft8v_lo<SIGN>(v[q]);
+      else if constexpr (PRUNE == 2) dftR_hi_cut<R, SIGN>(v[q]);
+      else dftR<R, SIGN>(v[q]);
     }
   }
   __syncthreads();
@@ -241,10 +321,10 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
       if constexpr (SL::shift_free(NS)) {
         const int o = SL::off(line, base);
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[o + r * NS] = c_norm(v[q][r]);
+        for (int r = 0; r < ROUT; ++r) s[o + r * NS] = c_norm(v[q][r]);
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[SL::off(line, base + r * NS)] = c_norm(v[q][r]);
+        for (int r = 0; r < ROUT; ++r) s[SL::off(line, base + r * NS)] = c_norm(v[q][r]);
       }
     }
   }
@@ -252,14 +332,18 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
 }
 
 // Radices 8, then 4 or 2 for the rest of the power of two, then 3 for L = 3 * 2^k.
-template <typename C, int L, int NS, int SIGN, int NLINES, int NT>
+// HIN: the upper half of every line is zero padding (the first pass reads the lower half);
+// HOUT: only the lower half of the result is needed (the last pass stores only it, when its
+// radix is even)
+template <typename C, int L, int NS, int SIGN, int NLINES, int NT, bool HIN = false, bool HOUT = false>
 __device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw) {
   if constexpr (NS < L) {
     constexpr int REM = L / NS;
     constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
     static_assert(REM % R == 0, "FFT length must be 2^k or 3 * 2^k");
-    fft_pass<C, L, R, NS, SIGN, NLINES, NT>(s, tw);
-    fft_lines<C, L, NS * R, SIGN, NLINES, NT>(s, tw);
+    constexpr int PRUNE = (HIN && NS == 1 && R == 8) ? 1 : ((HOUT && NS * R == L && R % 2 == 0) ? 2 : 0);
+    fft_pass<C, L, R, NS, SIGN, NLINES, NT, PRUNE>(s, tw);
+    fft_lines<C, L, NS * R, SIGN, NLINES, NT, false, HOUT>(s, tw);
   }
 }
 
@@ -291,7 +375,9 @@ template <typename C, int L> struct ColShape {
 // ------------------------------------------------------------------------------------
 // Row pass: lines contiguous in memory.
 // ------------------------------------------------------------------------------------
-template <typename C, int L, int SIGN>
+// PR: the operator's half-length form (forward: n_in = L/2, the padding not stored; inverse:
+// n_out = L/2, the cropped half not computed)
+template <typename C, int L, int SIGN, bool PR>
 __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
   constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL;
   using SL = SLay<C, L, NL>;
@@ -398,7 +484,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
     }
     s[SL::off(li, e)] = v;
   }
-  if (n_in < L) {
+  if (!(PR && SIGN < 0) && n_in < L) {
     const int padn = L - n_in;
     for (int idx = threadIdx.x; idx < NL * padn; idx += NT) {
       const int li = idx / padn, e = n_in + (idx - li * padn);
@@ -406,7 +492,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
     }
   }
   __syncthreads();
-  fft_lines<C, L, 1, SIGN, NL, NT>(s, tw);
+  fft_lines<C, L, 1, SIGN, NL, NT, (PR && SIGN < 0), (PR && SIGN > 0)>(s, tw);
   const int n_out = a.n_out;
   C* out = reinterpret_cast<C*>(a.out);
   const C* addv = reinterpret_cast<const C*>(a.addv);
@@ -435,7 +521,9 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
 // Column pass: lines strided (element stride es), TC adjacent lines per CTA.
 // MODE 0: forward; 1: inverse; 2: forward, multiply by the symbol, inverse.
 // ------------------------------------------------------------------------------------
-template <typename C, int L, int MODE>
+// PR: the operator's half-length form (MODE 0 and 2: n_in = L/2, the padding not stored;
+// MODE 1 and 2: n_out = L/2, the cropped half not computed)
+template <typename C, int L, int MODE, bool PR>
 __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_col_pass(ColPassArgs a) {
   constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
   using SL = SLay<C, L, TC>;
@@ -472,7 +560,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
       }
     }
   }
-  if (n_in < L) {
+  if (!(PR && MODE != 1) && n_in < L) {
     const int padn = L - n_in;
     for (int idx = threadIdx.x; idx < padn * TC; idx += NT) {
       const int e = n_in + idx / TC, c = idx % TC;
@@ -481,11 +569,11 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
   }
   __syncthreads();
   if constexpr (MODE == 0) {
-    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT, PR, false>(s, tw);
   } else if constexpr (MODE == 1) {
-    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT, false, PR>(s, tw);
   } else {
-    fft_lines<C, L, 1, -1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT, PR, false>(s, tw);
     const C* __restrict__ sym = reinterpret_cast<const C*>(a.sym);
     const int n1 = a.n + 1;
     // symbol values of SB entries loaded together, then applied
@@ -522,7 +610,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
       }
     }
     __syncthreads();
-    fft_lines<C, L, 1, 1, TC, NT>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT, false, PR>(s, tw);
   }
   C* out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
   const int n_out = a.n_out;
@@ -535,26 +623,37 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
 // ------------------------------------------------------------------------------------
 // Host dispatch
 // ------------------------------------------------------------------------------------
-template <typename C, int L, int SIGN> void launch_row_L(const RowPassArgs& a, cudaStream_t st) {
+// the half-length form when the lengths are the operator's (L/2 in or out); the full form
+// (the symbol's transforms, FP64 only) otherwise
+template <typename C, int L, int SIGN, bool PR> void launch_row_LP(const RowPassArgs& a, cudaStream_t st) {
   constexpr int NT = RowShape<L>::NT, NL = RowShape<L>::NL;
   const size_t smem = (size_t)SLay<C, L, NL>::SIZE * sizeof(C);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_row_pass<C, L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LS_CUDA(cudaFuncSetAttribute(k_row_pass<C, L, SIGN, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr.store(true, std::memory_order_release);
   }
   const long blocks = (a.lines + NL - 1) / NL;
   if (blocks == 0) return;
   static const std::string cls = std::string(SIGN < 0 ? "fft_row_fwd_" : "fft_row_inv_") + arith_tag<C>();
-  LS_LAUNCH(cls.c_str(), st, k_row_pass<C, L, SIGN><<<(unsigned)blocks, NT, smem, st>>>(a));
+  LS_LAUNCH(cls.c_str(), st, k_row_pass<C, L, SIGN, PR><<<(unsigned)blocks, NT, smem, st>>>(a));
+}
+template <typename C, int L, int SIGN> void launch_row_L(const RowPassArgs& a, cudaStream_t st) {
+  const bool half = SIGN < 0 ? a.n_in * 2 == L : a.n_out * 2 == L;
+  if (half) {
+    launch_row_LP<C, L, SIGN, true>(a, st);
+  } else {
+    if constexpr (std::is_same<C, double2>::value) launch_row_LP<C, L, SIGN, false>(a, st);
+    else LS_FAIL(EINVAL_, "row pass: only the half-length form in this arithmetic");
+  }
 }
 
-template <typename C, int L, int MODE> void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
+template <typename C, int L, int MODE, bool PR> void launch_col_LP(const ColPassArgs& a, cudaStream_t st) {
   constexpr int NT = ColShape<C, L>::NT, TC = ColShape<C, L>::TC;
   const size_t smem = (size_t)SLay<C, L, TC>::SIZE * sizeof(C);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_col_pass<C, L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LS_CUDA(cudaFuncSetAttribute(k_col_pass<C, L, MODE, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr.store(true, std::memory_order_release);
   }
   const long tiles = (a.inner + TC - 1) / TC;
@@ -562,7 +661,17 @@ template <typename C, int L, int MODE> void launch_col_L(const ColPassArgs& a, c
   if (blocks == 0) return;
   static const std::string cls =
       std::string(MODE == 0 ? "fft_col_fwd_" : MODE == 1 ? "fft_col_inv_" : "fft_col_sym_") + arith_tag<C>();
-  LS_LAUNCH(cls.c_str(), st, k_col_pass<C, L, MODE><<<(unsigned)blocks, NT, smem, st>>>(a));
+  LS_LAUNCH(cls.c_str(), st, k_col_pass<C, L, MODE, PR><<<(unsigned)blocks, NT, smem, st>>>(a));
+}
+template <typename C, int L, int MODE> void launch_col_L(const ColPassArgs& a, cudaStream_t st) {
+  const bool in_half = a.n_in * 2 == L, out_half = a.n_out * 2 == L;
+  const bool half = MODE == 0 ? in_half : (MODE == 1 ? out_half : in_half && out_half);
+  if (half) {
+    launch_col_LP<C, L, MODE, true>(a, st);
+  } else {
+    if constexpr (std::is_same<C, double2>::value) launch_col_LP<C, L, MODE, false>(a, st);
+    else LS_FAIL(EINVAL_, "column pass: only the half-length form in this arithmetic");
+  }
 }
 
 #define LS_FOR_L(X) X(16) X(32) X(48) X(64) X(96) X(128) X(256) X(512) X(1024) X(2048) X(4096)

@@ -375,16 +375,27 @@ __global__ void __launch_bounds__(KT) k_sub_proj_f(const float2* const* __restri
       const long e = i + (long)u * KT;
       acc[u] = ffc_of(e < i1 ? win[base + e] : make_float2(0.f, 0.f));
     }
-    for (int j = 0; j < nv; ++j) {
-      const ffc h = hc[j];
+    // two basis vectors per step: their 2 RUN loads are issued before the arithmetic
+    for (int j = 0; j < nv; j += 2) {
+      const bool two = j + 1 < nv;
       const float2* vj = (staged ? vps[j] : V[j]) + base;
+      const float2* vk = two ? (staged ? vps[j + 1] : V[j + 1]) + base : vj;
+      float2 a[RUN], b[RUN];
 #pragma unroll
       for (int u = 0; u < RUN; ++u) {
         const long e = i + (long)u * KT;
-        if (e < i1) {
-          const float2 a = vj[e];
-          acc[u].x = lz_add(acc[u].x, lz_neg(lz_add(lz_mul_f(h.x, a.x), lz_neg(lz_mul_f(h.y, a.y)))));
-          acc[u].y = lz_add(acc[u].y, lz_neg(lz_add(lz_mul_f(h.y, a.x), lz_mul_f(h.x, a.y))));
+        a[u] = e < i1 ? vj[e] : make_float2(0.f, 0.f);
+        b[u] = e < i1 && two ? vk[e] : make_float2(0.f, 0.f);
+      }
+      const ffc h = hc[j];
+      const ffc g = two ? hc[j + 1] : h;
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) {
+        acc[u].x = lz_add(acc[u].x, lz_neg(lz_add(lz_mul_f(h.x, a[u].x), lz_neg(lz_mul_f(h.y, a[u].y)))));
+        acc[u].y = lz_add(acc[u].y, lz_neg(lz_add(lz_mul_f(h.y, a[u].x), lz_mul_f(h.x, a[u].y))));
+        if (two) {
+          acc[u].x = lz_add(acc[u].x, lz_neg(lz_add(lz_mul_f(g.x, b[u].x), lz_neg(lz_mul_f(g.y, b[u].y)))));
+          acc[u].y = lz_add(acc[u].y, lz_neg(lz_add(lz_mul_f(g.y, b[u].x), lz_mul_f(g.x, b[u].y))));
         }
       }
     }

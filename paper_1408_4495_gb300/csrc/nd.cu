@@ -2451,6 +2451,149 @@ __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const flo
   }
 }
 
+// ---- small sweep levels (the bottom of the tree: at most 32 product rows and SMALL_MAX_K
+// columns, FP32, 16 right-hand sides per item): one warp per (front, group), FPC warps per
+// CTA, no block barrier.  The warp stages the vector operand (K x 16 right-hand sides) in its
+// shared-memory slice, reads its factor rows straight from global memory (coalesced 8-byte
+// loads through L1), and every lane stores its finished sums: 16 right-hand sides of one row
+// when the level has more than 16 rows, else 8 (lanes 16-31 take the second half).
+// Forward: rows are the ring rows of Y, the children's ring updates added at the store.
+constexpr int SMALL_FPC = 4;
+template <int MODE>
+__global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S, int nitems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int item = blockIdx.x * SMALL_FPC + wp;
+  const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
+  const int K = MODE == 0 ? smax : bmax + smax;
+  const int rows = MODE == 0 ? bmax : smax;
+  float2* vs = reinterpret_cast<float2*>(smem_raw) + (size_t)wp * K * 16;
+  pdl_wait();
+  pdl_trigger();
+  if (item >= nitems) return;
+  const int z = item / S.ng, g = item - z * S.ng;
+  const size_t wrow = (size_t)g * S.nf * fmax + (size_t)z * fmax;
+  const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+  // vector operand: K items of 16 right-hand sides = 8 float4 each
+  for (int p = lane; p < K * 8; p += 32) {
+    const int c = p >> 3, v = p & 7;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MODE == 0) {
+      const int pt = __ldg(S.own + (size_t)z * smax + c);
+      const int s0 = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2), s1 = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
+      if (pt >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v));
+      if (s0 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16) + v));
+      if (s1 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16) + v));
+      reinterpret_cast<float4*>(S.W + (wrow + c) * 16)[v] = x;
+    } else if (c < bmax) {
+      const int pt = __ldg(S.ring + (size_t)z * bmax + c);
+      if (pt >= 0) {
+        x = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v);
+        x = make_float4(-x.x, -x.y, -x.z, -x.w);  // the H columns enter with a minus sign
+      }
+    } else {
+      x = __ldcg(reinterpret_cast<const float4*>(S.W + (wrow + c - bmax) * 16) + v);
+    }
+    reinterpret_cast<float4*>(vs)[p] = x;
+  }
+  __syncwarp();
+  // rows > 16: lane = row, all 16 right-hand sides; else row = lane & 15, half lane >> 4
+  const bool wide = rows > 16;
+  const int row = wide ? lane : (lane & 15), j0 = wide ? 0 : (lane >> 4) * 8;
+  if (row >= rows) return;
+  const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
+                    (MODE == 0 ? smax : 0) + row;
+  float2 acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+  if (wide) {
+    for (int k = 0; k < K; ++k) {
+      const float2 a = __ldg(A + (size_t)k * fmax);
+      const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 b = vv[j];
+        acc[2 * j] = cfma(acc[2 * j], a, make_float2(b.x, b.y));
+        acc[2 * j + 1] = cfma(acc[2 * j + 1], a, make_float2(b.z, b.w));
+      }
+    }
+  } else {
+    for (int k = 0; k < K; ++k) {
+      const float2 a = __ldg(A + (size_t)k * fmax);
+      const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16 + j0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 b = vv[j];
+        acc[2 * j] = cfma(acc[2 * j], a, make_float2(b.x, b.y));
+        acc[2 * j + 1] = cfma(acc[2 * j + 1], a, make_float2(b.z, b.w));
+      }
+    }
+  }
+  const int nj = wide ? 16 : 8;
+  float2* dst;
+  if (MODE == 0) {
+    const int p0 = smax + row;
+    const int s0 = __ldg(S.fsrc + ((size_t)z * fmax + p0) * 2), s1 = __ldg(S.fsrc + ((size_t)z * fmax + p0) * 2 + 1);
+    for (int j = 0; j < nj; j += 2) {
+      float4 x = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+      if (s0 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16 + j0 + j)));
+      if (s1 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16 + j0 + j)));
+      acc[j] = make_float2(x.x, x.y);
+      acc[j + 1] = make_float2(x.z, x.w);
+    }
+    dst = S.W + (wrow + p0) * 16 + j0;
+  } else {
+    const int pt = __ldg(S.own + (size_t)z * smax + row);
+    if (pt < 0) return;
+    dst = S.T + ((size_t)g * S.N + pt) * 16 + j0;
+  }
+#pragma unroll
+  for (int j = 0; j < 16; j += 2)
+    if (j < nj) reinterpret_cast<float4*>(dst)[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+}
+
+constexpr int SMALL_MAX_K = 64;
+static bool small_level(const NdPlan* p, int l, int mode) {
+  const LevelDev& D = p->lev[l];
+  const int rows = mode == 0 ? D.bmax : D.smax, K = mode == 0 ? D.smax : D.bmax + D.smax;
+  return rows > 0 && rows <= 32 && K > 0 && K <= std::min(SMALL_MAX_K, p->tune.small_max_k);
+}
+
+template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, int ng, cudaStream_t st) {
+  const LevelDev& D = p->lev[l];
+  const int depth = (int)p->lev.size();
+  SweepK<float2> S{};
+  S.F = reinterpret_cast<const float2*>(p->F) + D.F_off;
+  S.W = reinterpret_cast<float2*>(p->W) + D.W_off;
+  const bool has_child = l + 1 < depth;
+  S.Wc = has_child ? reinterpret_cast<const float2*>(p->W) + p->lev[l + 1].W_off : S.W;
+  S.T = T;
+  S.own = D.own;
+  S.ring = D.ring;
+  S.fsrc = D.fsrc;
+  S.nf = D.nf;
+  S.smax = D.smax;
+  S.bmax = D.bmax;
+  S.fmax = D.fmax;
+  S.ncols = D.ncols;
+  S.nf_c = has_child ? p->lev[l + 1].nf : 0;
+  S.fmax_c = has_child ? p->lev[l + 1].fmax : 0;
+  S.ng = ng;
+  S.N = p->N;
+  const int K = MODE == 0 ? D.smax : D.bmax + D.smax;
+  const int nitems = D.nf * ng;
+  const size_t smem = (size_t)SMALL_FPC * K * 16 * sizeof(float2);
+  static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
+  if (!attr.load(std::memory_order_acquire)) {
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(SMALL_FPC * SMALL_MAX_K * 16 * sizeof(float2))));
+    attr.store(true, std::memory_order_release);
+  }
+  LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st,
+            launch_pdl(k_sweep_small<MODE>, dim3((unsigned)((nitems + SMALL_FPC - 1) / SMALL_FPC)),
+                       dim3(32 * SMALL_FPC), smem, st, S, nitems));
+}
+
 // whether level l's sweep product of this mode runs on the tensor cores
 static bool tcs_level(const NdPlan* p, int l, int mode, int ng) {
   const LevelDev& D = p->lev[l];
@@ -2501,6 +2644,10 @@ template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int 
   if constexpr (sizeof(C) == 8 && RC == 16) {
     if (tcs_level(p, l, MODE, ng)) {
       launch_sweep_tc<MODE>(p, l, reinterpret_cast<float2*>(T), ng, st);
+      return;
+    }
+    if (small_level(p, l, MODE)) {
+      launch_sweep_small<MODE>(p, l, reinterpret_cast<float2*>(T), ng, st);
       return;
     }
   }

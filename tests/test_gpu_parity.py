@@ -299,21 +299,27 @@ def test_preconditioner_cluster_panel_3d_n32(LS, laplace):
 
 # (d, n, freq, right-hand sides, FP32 backward-error bound of test_preconditioner)
 TCS_CASES = [(2, 128, 16.0, 40, 2e-5), (2, 256, 32.0, 16, 2e-3), (3, 32, 4.0, 24, 2e-6)]
+OFF = 1 << 30
+GENERIC = {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 0}
+SWEEP_VARIANTS = {"tensor_core": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 0},
+                  "one_warp": {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 64},
+                  "default": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 64}}
 
 
+@pytest.mark.parametrize("variant", sorted(SWEEP_VARIANTS))
 @pytest.mark.parametrize("d,n,freq,nrhs,bound", TCS_CASES)
-def test_tensor_core_sweep_levels(LS, d, n, freq, nrhs, bound):
-    """FP32 solve levels whose products have at least 64 rows (the default threshold) run
-    as one batched tcgen05 GEMM (3xTF32) between a gather of the vector operand and a
-    scatter of the result, when
-    16 right-hand sides share an item (more than 4 right-hand sides).  The same application
-    with every level on the CUDA-core sweep kernel (tcs_min_rows above every level) is the
-    comparison: both meet the backward-error bound against the oracle's assembled M, the
-    tensor-core one within 5x of the other (3xTF32 products carry about 2^-22 relative
-    error against 2^-24 for FP32 FMAs; measured 1-3.6x), and the launch counts show which
-    path ran (a
-    tensor-core level adds the gather and the scatter).  40 right-hand sides leave the last
-    group of 16 and the GEMM's 64-column tile partly empty."""
+def test_sweep_level_kernels(LS, d, n, freq, nrhs, bound, variant):
+    """The solve-level kernels other than the general k_sweep, when 16 right-hand sides share
+    an item (more than 4 right-hand sides): FP32 levels whose products have at least 64 rows
+    as one batched tcgen05 GEMM (3xTF32) between a gather of the vector operand and a scatter
+    of the result ("tensor_core"); the bottom levels (at most 32 rows, 64 columns) one warp
+    per front ("one_warp"); both ("default").  The comparison is the same application with
+    every level on k_sweep: both meet the backward-error bound against the oracle's
+    assembled M, the variant within 5x of k_sweep (3xTF32 products carry about 2^-22
+    relative error against 2^-24 for FP32 FMAs; measured 1-3.6x), and with the tensor-core
+    levels the launch counts show that path ran (a tensor-core level adds the gather and the
+    scatter).  40 right-hand sides leave the last group of 16 and the GEMM's 64-column tile
+    partly empty."""
     omega = 2 * np.pi * freq
     m = medium(d, n, seed=5 if d == 3 else 0)
     x = rand_c((nrhs,) + (n,) * d, 17)
@@ -321,19 +327,19 @@ def test_tensor_core_sweep_levels(LS, d, n, freq, nrhs, bound):
     M, S = O.assemble(n, d, omega, m, sten, cint)
     normM = abs(M).sum(axis=1).max()
     z, launches, be = {}, {}, {}
-    off = 1 << 30
     with LS.Solver(m, omega, mixed=True) as s:
         s.factor()
-        for tcs in (64, off):
-            s.set_tune({"tcs_min_rows": tcs, "tcs_bwd_min_rows": tcs})
+        for key, tune in (("variant", SWEEP_VARIANTS[variant]), ("generic", GENERIC)):
+            s.set_tune(tune)
             LS.profile_start(None)
-            z[tcs] = s.precond(x)
+            z[key] = s.precond(x)
             counts = LS.profile_stop()["counts"]
-            launches[tcs] = counts.get("nd_fwd_c64", 0) + counts.get("nd_bwd_c64", 0)
-            be[tcs] = max(np.linalg.norm(M @ z[tcs][j].reshape(-1) - S @ x[j].reshape(-1))
-                          / (normM * np.linalg.norm(z[tcs][j].reshape(-1))) for j in (0, nrhs - 1))
-    print(f"d={d} n={n}: launches {launches}, backward errors {be}, relative difference "
-          f"{rel(z[64], z[off]):.3g}")
-    assert launches[64] > launches[off]
-    assert be[off] < bound and be[64] < bound
-    assert be[64] < 5 * be[off] + 1e-8
+            launches[key] = counts.get("nd_fwd_c64", 0) + counts.get("nd_bwd_c64", 0)
+            be[key] = max(np.linalg.norm(M @ z[key][j].reshape(-1) - S @ x[j].reshape(-1))
+                          / (normM * np.linalg.norm(z[key][j].reshape(-1))) for j in (0, nrhs - 1))
+    print(f"d={d} n={n} {variant}: launches {launches}, backward errors {be}, relative difference "
+          f"{rel(z['variant'], z['generic']):.3g}")
+    if SWEEP_VARIANTS[variant]["tcs_min_rows"] < OFF:
+        assert launches["variant"] > launches["generic"]
+    assert be["generic"] < bound and be["variant"] < bound
+    assert be["variant"] < 5 * be["generic"] + 1e-8
