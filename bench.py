@@ -703,7 +703,13 @@ def run_gpu(args):
     # of this grid and precision, e.g. the end-to-end ones)
     s_mix, setup_s = B.solver(w, True)
     t0 = time.perf_counter()
-    tune = s_mix.autotune(w.nrhs)
+    if args.tune:
+        # fixed launch shapes (profiling runs: timings under a profiler would mislead the tuner)
+        s_mix.set_tune(json.loads(args.tune))
+        s_mix.factor()
+        tune = {"choice": s_mix.tune(), "factor_ms": [], "solve_ms": []}
+    else:
+        tune = s_mix.autotune(w.nrhs)
     tune_s = time.perf_counter() - t0
     nd = s_mix.nd_stats()
     # headline region: launches counted, replayed through the library's CUDA graphs
@@ -877,6 +883,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time the mixed-precision steps only (short runs under a profiler)")
+    ap.add_argument("--tune", default=None,
+                    help="apply these launch shapes (JSON object, as ls_set_tune takes) instead of autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
