@@ -308,20 +308,23 @@ __global__ void __launch_bounds__(KT) k_dots_f(const float2* const* __restrict__
       float2 sr[JB];
 #pragma unroll
       for (int q = 0; q < JB; ++q) sr[q] = make_float2(0.f, 0.f);
+      // every load of the run issued before the arithmetic
+      float2 b[RUN], a[RUN][JB];
 #pragma unroll
       for (int u = 0; u < RUN; ++u) {
         const long e = i + (long)u * KT;
-        if (e < i1) {
-          const float2 b = w[base + e];
+        const bool in = e < i1;
+        b[u] = in ? w[base + e] : make_float2(0.f, 0.f);
 #pragma unroll
-          for (int q = 0; q < JB; ++q)
-            if (q < nj) {
-              const float2 a = vp[q][e];
-              sr[q].x = __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, sr[q].x));
-              sr[q].y = __fmaf_rn(a.x, b.y, __fmaf_rn(-a.y, b.x, sr[q].y));
-            }
-        }
+        for (int q = 0; q < JB; ++q) a[u][q] = in && q < nj ? vp[q][e] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int u = 0; u < RUN; ++u)
+#pragma unroll
+        for (int q = 0; q < JB; ++q) {
+          sr[q].x = __fmaf_rn(a[u][q].x, b[u].x, __fmaf_rn(a[u][q].y, b[u].y, sr[q].x));
+          sr[q].y = __fmaf_rn(a[u][q].x, b[u].y, __fmaf_rn(-a[u][q].y, b[u].x, sr[q].y));
+        }
 #pragma unroll
       for (int q = 0; q < JB; ++q)
         if (q < nj) {
@@ -448,19 +451,44 @@ __global__ void __launch_bounds__(256) k_update_u_f(const float2* const* __restr
   }
   __syncthreads();
   const size_t base = (size_t)rhs * N;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-    ffc acc;
-    acc.x = acc.y = ff(0);
-    for (int j = 0; j < nz; ++j) {
-      const float2 zv = zps[j][base + i];
-      const ffc h = hy[j];
-      acc.x = acc.x + (ff_mul_f(h.x, zv.x) - ff_mul_f(h.y, zv.y));
-      acc.y = acc.y + (ff_mul_f(h.y, zv.x) + ff_mul_f(h.x, zv.y));
+  const long stride = (long)gridDim.x * blockDim.x;
+  // UR elements per thread at a time, two basis vectors per step: their loads (and those of
+  // u) issued before the arithmetic
+  constexpr int UR = 2;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += stride * UR) {
+    ffc acc[UR];
+    double2 uv[UR];
+#pragma unroll
+    for (int r = 0; r < UR; ++r) {
+      acc[r].x = acc[r].y = ff(0);
+      const long e = i + r * stride;
+      uv[r] = e < N ? u[base + e] : make_double2(0.0, 0.0);
     }
-    double2 v = u[base + i];
-    v.x += ff_to_f64(acc.x);
-    v.y += ff_to_f64(acc.y);
-    u[base + i] = v;
+    for (int j = 0; j < nz; j += 2) {
+      const bool two = j + 1 < nz;
+      float2 za[UR], zb[UR];
+#pragma unroll
+      for (int r = 0; r < UR; ++r) {
+        const long e = i + r * stride;
+        za[r] = e < N ? zps[j][base + e] : make_float2(0.f, 0.f);
+        zb[r] = e < N && two ? zps[j + 1][base + e] : make_float2(0.f, 0.f);
+      }
+      const ffc h = hy[j], q = two ? hy[j + 1] : hy[j];
+#pragma unroll
+      for (int r = 0; r < UR; ++r) {
+        acc[r].x = acc[r].x + (ff_mul_f(h.x, za[r].x) - ff_mul_f(h.y, za[r].y));
+        acc[r].y = acc[r].y + (ff_mul_f(h.y, za[r].x) + ff_mul_f(h.x, za[r].y));
+        if (two) {
+          acc[r].x = acc[r].x + (ff_mul_f(q.x, zb[r].x) - ff_mul_f(q.y, zb[r].y));
+          acc[r].y = acc[r].y + (ff_mul_f(q.y, zb[r].x) + ff_mul_f(q.x, zb[r].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < UR; ++r) {
+      const long e = i + r * stride;
+      if (e < N) u[base + e] = make_double2(uv[r].x + ff_to_f64(acc[r].x), uv[r].y + ff_to_f64(acc[r].y));
+    }
   }
 }
 

@@ -1438,8 +1438,12 @@ __global__ void __launch_bounds__(256) k_gemm(LevelK<C> L, int r0, int r1, int c
 // children's Schur complements, then Gauss-Jordan elimination with partial pivoting over
 // the own rows of [F11 | F12 | I] held in shared memory, which leaves [I | H | F11^{-1}]
 // with H = F11^{-1} F12; the ring rows are updated by the tiled GEMM afterwards.
+// With ring != 0 the CTA also forms the ring rows' [S | Y] = [F22 | 0] - F21 [H | F11^{-1}]
+// (what the level's ring GEMM does otherwise): F21 read from global memory, [H | F11^{-1}]
+// from the shared-memory block.
 template <typename C>
-__global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch, int has_child, int* err) {
+__global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch, int has_child, int* err,
+                                                     int ring) {
   using Rl = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* B = reinterpret_cast<C*>(smem_raw);  // column major, ld = smax
@@ -1576,6 +1580,17 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(LevelK<C> L, LevelK<C> Ch,
     const int src = ph[r];
     for (int c = s + g; c < nc; c += G) A[(size_t)c * fmax + r] = B[(size_t)c * s + src];
   }
+  if (ring) {
+    // ring row i, column c: consecutive threads take consecutive ring rows (coalesced F21
+    // and F22 accesses); own row k of [H | F11^{-1}] is row ph[k] of the block
+    const int b = fmax - s, nco = nc - s;
+    for (int t = tid; t < b * nco; t += NT) {
+      const int i = s + t % b, c = s + t / b;
+      C acc = A[(size_t)c * fmax + i];
+      for (int k = 0; k < s; ++k) acc = cfms(acc, A[(size_t)k * fmax + i], B[(size_t)c * s + ph[k]]);
+      A[(size_t)c * fmax + i] = acc;
+    }
+  }
 }
 
 template <typename C> LevelK<C> level_k(NdPlan* p, int l) {
@@ -1663,11 +1678,16 @@ template <typename C> static size_t gj_smem(int s, int nc) {
 constexpr int TC_MIN_ROWS = 64, TC_MIN_K = 16;
 
 // tc: the launch-shape choices when the tensor cores may take the product, else null
+// whether a Schur product of this many rows and inner columns runs on the tensor cores
+template <typename C> static bool gemm_on_tc(int rows, int k, const NdTune* tc) {
+  return sizeof(C) == 8 && tc && rows >= std::max(tc->tc_min_rows, TC_MIN_ROWS) && k >= TC_MIN_K && tc_enabled();
+}
+
 template <typename C> static void launch_gemm(const LevelK<C>& L, int r0, int r1, int c0, int c1, int k0, int k1,
                                               cudaStream_t st, int* err, const NdTune* tc) {
   if (r1 <= r0 || c1 <= c0 || k1 <= k0) return;
   if constexpr (sizeof(C) == 8) {
-    if (tc && r1 - r0 >= std::max(tc->tc_min_rows, TC_MIN_ROWS) && k1 - k0 >= TC_MIN_K && tc_enabled()) {
+    if (gemm_on_tc<C>(r1 - r0, k1 - k0, tc)) {
       tc_cgemm(reinterpret_cast<float2*>(L.F), (long)L.fmax * L.ncols, L.fmax, L.nf, r0, r1, c0, c1, k0, k1, err, st);
       return;
     }
@@ -1797,11 +1817,13 @@ void nd_factor_launch(NdPlan* p, const void* alpha64, const void* cint64, const 
                   k_extend_add<C><<<dim3(Ch.nf, bx), 256, 0, st>>>(L, Ch, k));
     }
     if (gj) {
-      // one CTA per front: Gauss-Jordan in shared memory (with the extend-add if fused)
+      // one CTA per front: Gauss-Jordan in shared memory (with the extend-add if fused), and
+      // the ring rows' product in the same CTA unless it goes to the tensor cores
+      const bool ring_tc = gemm_on_tc<C>(L.bmax, L.smax, tcp);
       LS_LAUNCH(f32 ? "nd_gauss_jordan_c64" : "nd_gauss_jordan_c128", st,
                 k_gauss_jordan<C><<<L.nf, gj_threads(L.smax, L.ncols), gjm, st>>>(L, Ch, fused_ea ? 1 : 0,
-                                                                                   p->d_err));
-      launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, tcp);
+                                                                                   p->d_err, ring_tc ? 0 : 1));
+      if (ring_tc) launch_gemm<C>(L, L.smax, L.fmax, L.smax, L.ncols, 0, L.smax, st, p->d_err, tcp);
       continue;
     }
     // The register sweeps update every trailing column on CUDA cores from a panel staged per
