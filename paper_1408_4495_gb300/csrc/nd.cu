@@ -2496,27 +2496,51 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
   const int z = item / S.ng, g = item - z * S.ng;
   const size_t wrow = (size_t)g * S.nf * fmax + (size_t)z * fmax;
   const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
-  // vector operand: K items of 16 right-hand sides = 8 float4 each
-  for (int p = lane; p < K * 8; p += 32) {
-    const int c = p >> 3, v = p & 7;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (MODE == 0) {
-      const int pt = __ldg(S.own + (size_t)z * smax + c);
-      const int s0 = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2), s1 = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
-      if (pt >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v));
-      if (s0 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16) + v));
-      if (s1 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16) + v));
-      reinterpret_cast<float4*>(S.W + (wrow + c) * 16)[v] = x;
-    } else if (c < bmax) {
-      const int pt = __ldg(S.ring + (size_t)z * bmax + c);
-      if (pt >= 0) {
-        x = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v);
-        x = make_float4(-x.x, -x.y, -x.z, -x.w);  // the H columns enter with a minus sign
+  // vector operand: K items of 16 right-hand sides = 8 float4 each; GB pieces per lane at a
+  // time, their index loads and then their data loads in flight together
+  constexpr int GB = 4;
+  for (int p0 = lane; p0 < K * 8; p0 += 32 * GB) {
+    int i0[GB], i1[GB], i2[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int p = p0 + 32 * u, c = p >> 3;
+      i0[u] = i1[u] = i2[u] = -1;
+      if (p < K * 8) {
+        if (MODE == 0) {
+          i0[u] = __ldg(S.own + (size_t)z * smax + c);
+          i1[u] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
+          i2[u] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
+        } else if (c < bmax) {
+          i0[u] = __ldg(S.ring + (size_t)z * bmax + c);
+        }
       }
-    } else {
-      x = __ldcg(reinterpret_cast<const float4*>(S.W + (wrow + c - bmax) * 16) + v);
     }
-    reinterpret_cast<float4*>(vs)[p] = x;
+    float4 x[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int p = p0 + 32 * u, c = p >> 3, v = p & 7;
+      x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p >= K * 8) continue;
+      if (MODE == 0) {
+        if (i0[u] >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + i0[u]) * 16) + v));
+        if (i1[u] >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + i1[u]) * 16) + v));
+        if (i2[u] >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + i2[u]) * 16) + v));
+      } else if (c < bmax) {
+        if (i0[u] >= 0) {
+          const float4 t = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + i0[u]) * 16) + v);
+          x[u] = make_float4(-t.x, -t.y, -t.z, -t.w);  // the H columns enter with a minus sign
+        }
+      } else {
+        x[u] = __ldcg(reinterpret_cast<const float4*>(S.W + (wrow + c - bmax) * 16) + v);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int p = p0 + 32 * u, c = p >> 3, v = p & 7;
+      if (p >= K * 8) continue;
+      if (MODE == 0) reinterpret_cast<float4*>(S.W + (wrow + c) * 16)[v] = x[u];
+      reinterpret_cast<float4*>(vs)[p] = x[u];
+    }
   }
   __syncwarp();
   // rows > 16: lane = row, all 16 right-hand sides; else row = lane & 15, half lane >> 4
@@ -2529,6 +2553,7 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
 #pragma unroll
   for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
   if (wide) {
+#pragma unroll 4
     for (int k = 0; k < K; ++k) {
       const float2 a = __ldg(A + (size_t)k * fmax);
       const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16);
@@ -2540,6 +2565,7 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
       }
     }
   } else {
+#pragma unroll 4
     for (int k = 0; k < K; ++k) {
       const float2 a = __ldg(A + (size_t)k * fmax);
       const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16 + j0);
