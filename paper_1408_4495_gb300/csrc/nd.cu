@@ -2474,47 +2474,72 @@ __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const flo
 }
 
 // ---- small sweep levels (the bottom of the tree: at most 32 product rows and SMALL_MAX_K
-// columns, FP32, 16 right-hand sides per item): one warp per (front, group), FPC warps per
-// CTA, no block barrier.  The warp stages the vector operand (K x 16 right-hand sides) in its
-// shared-memory slice, reads its factor rows straight from global memory (coalesced 8-byte
-// loads through L1), and every lane stores its finished sums: 16 right-hand sides of one row
-// when the level has more than 16 rows, else 8 (lanes 16-31 take the second half).
-// Forward: rows are the ring rows of Y, the children's ring updates added at the store.
+// columns, FP32, 16 right-hand sides per item): one warp per (front, group), SMALL_FPC warps
+// per CTA, no block barrier.  Before the programmatic-dependent wait the warp stages its
+// item's indices and copies its factor tile (rows x K) into its shared-memory slice with
+// cp.async, overlapping the previous level's tail; after it, it gathers the vector operand
+// (K x 16 right-hand sides; index and data loads of four pieces in flight) and every lane
+// stores its finished sums: 16 right-hand sides of one row when WIDE (more than 16 rows),
+// else 8 (lanes 16-31 take the second half).  Forward: rows are the ring rows of Y, the
+// children's ring updates added at the store.
 constexpr int SMALL_FPC = 4;
-template <int MODE>
+// bytes of one warp's shared-memory slice: factor tile (RP x K complex, RP = 16 or 32 rows),
+// vector operand (K x 16 complex), indices (3 K + 2 RP ints), rounded up to 16 bytes so that
+// every slice's float4 accesses stay aligned
+__host__ __device__ constexpr size_t small_slice_bytes(int K, int rp) {
+  return (((size_t)rp * K + (size_t)K * 16) * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
+}
+template <int MODE, bool WIDE>
 __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S, int nitems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int RP = WIDE ? 32 : 16, NJ = WIDE ? 16 : 8;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int item = blockIdx.x * SMALL_FPC + wp;
   const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
   const int K = MODE == 0 ? smax : bmax + smax;
   const int rows = MODE == 0 ? bmax : smax;
-  float2* vs = reinterpret_cast<float2*>(smem_raw) + (size_t)wp * K * 16;
-  pdl_wait();
-  pdl_trigger();
-  if (item >= nitems) return;
-  const int z = item / S.ng, g = item - z * S.ng;
-  const size_t wrow = (size_t)g * S.nf * fmax + (size_t)z * fmax;
-  const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
-  // vector operand: K items of 16 right-hand sides = 8 float4 each; GB pieces per lane at a
-  // time, their index loads and then their data loads in flight together
-  constexpr int GB = 4;
-  for (int p0 = lane; p0 < K * 8; p0 += 32 * GB) {
-    int i0[GB], i1[GB], i2[GB];
-#pragma unroll
-    for (int u = 0; u < GB; ++u) {
-      const int p = p0 + 32 * u, c = p >> 3;
-      i0[u] = i1[u] = i2[u] = -1;
-      if (p < K * 8) {
-        if (MODE == 0) {
-          i0[u] = __ldg(S.own + (size_t)z * smax + c);
-          i1[u] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
-          i2[u] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
-        } else if (c < bmax) {
-          i0[u] = __ldg(S.ring + (size_t)z * bmax + c);
-        }
+  unsigned char* base = smem_raw + (size_t)wp * small_slice_bytes(K, RP);
+  float2* As = reinterpret_cast<float2*>(base);  // [K][RP]
+  float2* vs = As + (size_t)RP * K;              // [K][16]
+  int* ix = reinterpret_cast<int*>(vs + (size_t)K * 16);  // [3 K] item sources, [2 RP] row indices
+  const bool on = item < nitems;
+  const int z = on ? item / S.ng : 0, g = on ? item - z * S.ng : 0;
+  // ---- prologue: static data only
+  if (on) {
+    const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
+                      (MODE == 0 ? smax : 0);
+    for (int e = lane; e < K * RP; e += 32) {
+      const int k = e / RP, r = e - k * RP;
+      cp_async_elem<8>(As + e, r < rows ? A + (size_t)k * fmax + r : A, r < rows);
+    }
+    cp_async_commit();
+    for (int c = lane; c < K; c += 32) {
+      if (MODE == 0) {
+        ix[3 * c] = __ldg(S.own + (size_t)z * smax + c);
+        ix[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
+        ix[3 * c + 2] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
+      } else {
+        ix[3 * c] = c < bmax ? __ldg(S.ring + (size_t)z * bmax + c) : -1;
       }
     }
+    for (int r = lane; r < RP; r += 32) {
+      if (MODE == 0) {
+        const bool rv = r < rows;
+        ix[3 * K + 2 * r] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2) : -1;
+        ix[3 * K + 2 * r + 1] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2 + 1) : -1;
+      } else {
+        ix[3 * K + 2 * r] = r < rows ? __ldg(S.own + (size_t)z * smax + r) : -1;
+      }
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (!on) return;
+  __syncwarp();
+  const size_t wrow = (size_t)g * S.nf * fmax + (size_t)z * fmax;
+  const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
+  constexpr int GB = 4;
+  for (int p0 = lane; p0 < K * 8; p0 += 32 * GB) {
     float4 x[GB];
 #pragma unroll
     for (int u = 0; u < GB; ++u) {
@@ -2522,12 +2547,14 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
       x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (p >= K * 8) continue;
       if (MODE == 0) {
-        if (i0[u] >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + i0[u]) * 16) + v));
-        if (i1[u] >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + i1[u]) * 16) + v));
-        if (i2[u] >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + i2[u]) * 16) + v));
+        const int pt = ix[3 * c], s0 = ix[3 * c + 1], s1 = ix[3 * c + 2];
+        if (pt >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v));
+        if (s0 >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16) + v));
+        if (s1 >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16) + v));
       } else if (c < bmax) {
-        if (i0[u] >= 0) {
-          const float4 t = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + i0[u]) * 16) + v);
+        const int pt = ix[3 * c];
+        if (pt >= 0) {
+          const float4 t = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v);
           x[u] = make_float4(-t.x, -t.y, -t.z, -t.w);  // the H columns enter with a minus sign
         }
       } else {
@@ -2542,62 +2569,44 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
       reinterpret_cast<float4*>(vs)[p] = x[u];
     }
   }
+  cp_async_wait<0>();
   __syncwarp();
-  // rows > 16: lane = row, all 16 right-hand sides; else row = lane & 15, half lane >> 4
-  const bool wide = rows > 16;
-  const int row = wide ? lane : (lane & 15), j0 = wide ? 0 : (lane >> 4) * 8;
+  const int row = WIDE ? lane : (lane & 15), j0 = WIDE ? 0 : (lane >> 4) * 8;
   if (row >= rows) return;
-  const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
-                    (MODE == 0 ? smax : 0) + row;
-  float2 acc[16];
+  float2 acc[NJ];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
-  if (wide) {
+  for (int j = 0; j < NJ; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      const float2 a = __ldg(A + (size_t)k * fmax);
-      const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16);
+  for (int k = 0; k < K; ++k) {
+    const float2 a = As[k * RP + row];
+    const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16 + j0);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float4 b = vv[j];
-        acc[2 * j] = cfma(acc[2 * j], a, make_float2(b.x, b.y));
-        acc[2 * j + 1] = cfma(acc[2 * j + 1], a, make_float2(b.z, b.w));
-      }
-    }
-  } else {
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      const float2 a = __ldg(A + (size_t)k * fmax);
-      const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16 + j0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 b = vv[j];
-        acc[2 * j] = cfma(acc[2 * j], a, make_float2(b.x, b.y));
-        acc[2 * j + 1] = cfma(acc[2 * j + 1], a, make_float2(b.z, b.w));
-      }
+    for (int j = 0; j < NJ / 2; ++j) {
+      const float4 b = vv[j];
+      acc[2 * j] = cfma(acc[2 * j], a, make_float2(b.x, b.y));
+      acc[2 * j + 1] = cfma(acc[2 * j + 1], a, make_float2(b.z, b.w));
     }
   }
-  const int nj = wide ? 16 : 8;
   float2* dst;
   if (MODE == 0) {
-    const int p0 = smax + row;
-    const int s0 = __ldg(S.fsrc + ((size_t)z * fmax + p0) * 2), s1 = __ldg(S.fsrc + ((size_t)z * fmax + p0) * 2 + 1);
-    for (int j = 0; j < nj; j += 2) {
+    const int s0 = ix[3 * K + 2 * row], s1 = ix[3 * K + 2 * row + 1];
+#pragma unroll
+    for (int j = 0; j < NJ; j += 2) {
       float4 x = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
       if (s0 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16 + j0 + j)));
       if (s1 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16 + j0 + j)));
       acc[j] = make_float2(x.x, x.y);
       acc[j + 1] = make_float2(x.z, x.w);
     }
-    dst = S.W + (wrow + p0) * 16 + j0;
+    dst = S.W + (wrow + smax + row) * 16 + j0;
   } else {
-    const int pt = __ldg(S.own + (size_t)z * smax + row);
+    const int pt = ix[3 * K + 2 * row];
     if (pt < 0) return;
     dst = S.T + ((size_t)g * S.N + pt) * 16 + j0;
   }
 #pragma unroll
-  for (int j = 0; j < 16; j += 2)
-    if (j < nj) reinterpret_cast<float4*>(dst)[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+  for (int j = 0; j < NJ; j += 2)
+    reinterpret_cast<float4*>(dst)[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
 }
 
 constexpr int SMALL_MAX_K = 64;
@@ -2630,16 +2639,25 @@ template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, 
   S.N = p->N;
   const int K = MODE == 0 ? D.smax : D.bmax + D.smax;
   const int nitems = D.nf * ng;
-  const size_t smem = (size_t)SMALL_FPC * K * 16 * sizeof(float2);
+  const int rows = MODE == 0 ? D.bmax : D.smax;
+  const bool wide = rows > 16;
+  const size_t smem = (size_t)SMALL_FPC * small_slice_bytes(K, wide ? 32 : 16);
+  const size_t smem_max = (size_t)SMALL_FPC * small_slice_bytes(SMALL_MAX_K, 32);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(SMALL_FPC * SMALL_MAX_K * 16 * sizeof(float2))));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_max));
     attr.store(true, std::memory_order_release);
   }
-  LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st,
-            launch_pdl(k_sweep_small<MODE>, dim3((unsigned)((nitems + SMALL_FPC - 1) / SMALL_FPC)),
-                       dim3(32 * SMALL_FPC), smem, st, S, nitems));
+  const dim3 grid((unsigned)((nitems + SMALL_FPC - 1) / SMALL_FPC)), block(32 * SMALL_FPC);
+  if (wide)
+    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st,
+              launch_pdl(k_sweep_small<MODE, true>, grid, block, smem, st, S, nitems));
+  else
+    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st,
+              launch_pdl(k_sweep_small<MODE, false>, grid, block, smem, st, S, nitems));
 }
 
 // whether level l's sweep product of this mode runs on the tensor cores
