@@ -101,6 +101,15 @@ template <typename C, int L, int LINES> struct SLay {
   static constexpr int SIZE = LINES * L;  // entries
   static_assert(L % E == 0, "line length must be a multiple of the swizzle row");
   __host__ __device__ static constexpr bool shift_free(int stride) { return stride % (8 * E) == 0; }
+  // entries i0 + r, r < 8, of one line with i0 a multiple of 8 share a row and its swizzle:
+  // their offsets are rb + (q ^ r)
+  __device__ static __forceinline__ void group8(int line, int i0, int& rb, int& q) {
+    const int row = (i0 / E) & 7;
+    int h = row ^ (line * KC);
+    if constexpr (E == 16) h ^= ((row ^ (row >> 1) ^ (row >> 2)) & 1) << 3;
+    rb = line * L + (i0 & ~(E - 1));
+    q = (i0 ^ h) & (E - 1);
+  }
   __device__ static __forceinline__ int off(int line, int i) {
     const int row = (i / E) & 7;
     int h = row ^ (line * KC);
@@ -322,6 +331,12 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
         const int o = SL::off(line, base);
 #pragma unroll
         for (int r = 0; r < ROUT; ++r) s[o + r * NS] = c_norm(v[q][r]);
+      } else if constexpr (NS == 1 && R <= 8) {
+        // the first pass writes R consecutive entries from a multiple of R
+        int rb, qq;
+        SL::group8(line, base, rb, qq);
+#pragma unroll
+        for (int r = 0; r < ROUT; ++r) s[rb + (qq ^ r)] = c_norm(v[q][r]);
       } else {
 #pragma unroll
         for (int r = 0; r < ROUT; ++r) s[SL::off(line, base + r * NS)] = c_norm(v[q][r]);
@@ -386,7 +401,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
   C* s = reinterpret_cast<C*>(smem_raw);
   const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
   const long line0 = (long)blockIdx.x * NL;
-  const int n_in = a.n_in;
+  // the half-length forms' lengths are compile-time constants (index divisions by constants)
+  const int n_in = (PR && SIGN < 0) ? L / 2 : a.n_in;
 
   // load n_in entries of NL lines (coalesced), apply the prologue
   if (a.plane_dirs == nullptr) {
@@ -395,6 +411,10 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
     const int tot = NL * n_in;
     const C* __restrict__ in = reinterpret_cast<const C*>(a.in);
     const Rl* __restrict__ pw = reinterpret_cast<const Rl*>(a.pw);
+    // row of the weights of each of the CTA's lines (one division per line, not per entry)
+    __shared__ int pwrow[NL];
+    if (pw != nullptr && threadIdx.x < NL) pwrow[threadIdx.x] = (int)((line0 + threadIdx.x) % a.pw_lines);
+    __syncthreads();
     for (int base = threadIdx.x; base < tot; base += NT * LB) {
       C v[LB];
       Rl wv[LB];
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
             } else {
               v[u] = in[line * a.in_ls + e];
             }
-            if (pw != nullptr) wv[u] = pw[(line % a.pw_lines) * n_in + e];
+            if (pw != nullptr) wv[u] = pw[(long)pwrow[li] * n_in + e];
           }
         }
       }
@@ -493,7 +513,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT) k_row_pass(RowPassArgs a) {
   }
   __syncthreads();
   fft_lines<C, L, 1, SIGN, NL, NT, (PR && SIGN < 0), (PR && SIGN > 0)>(s, tw);
-  const int n_out = a.n_out;
+  const int n_out = (PR && SIGN > 0) ? L / 2 : a.n_out;
   C* out = reinterpret_cast<C*>(a.out);
   const C* addv = reinterpret_cast<const C*>(a.addv);
   for (int idx = threadIdx.x; idx < NL * n_out; idx += NT) {
@@ -534,7 +554,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
   const long o = blockIdx.x / tiles;
   const long c0 = (blockIdx.x - o * tiles) * TC;
   const C* in = reinterpret_cast<const C*>(a.in) + o * a.in_os + c0;
-  const int n_in = a.n_in;
+  const int n_in = (PR && MODE != 1) ? L / 2 : a.n_in;
   {
     // LB independent loads in flight per thread before the first shared-memory store
     constexpr int LB = 4;
@@ -613,7 +633,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
     fft_lines<C, L, 1, 1, TC, NT, false, PR>(s, tw);
   }
   C* out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
-  const int n_out = a.n_out;
+  const int n_out = (PR && MODE != 0) ? L / 2 : a.n_out;
   for (int idx = threadIdx.x; idx < n_out * TC; idx += NT) {
     const int e = idx / TC, c = idx - e * TC;
     if (c0 + c < a.inner) out[(long)e * a.out_es + c] = s[SL::off(c, e)];
