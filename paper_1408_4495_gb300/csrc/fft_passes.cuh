@@ -101,6 +101,12 @@ template <typename C, int L, int LINES> struct SLay {
   static constexpr int SIZE = LINES * L;  // entries
   static_assert(L % E == 0, "line length must be a multiple of the swizzle row");
   __host__ __device__ static constexpr bool shift_free(int stride) { return stride % (8 * E) == 0; }
+  // entries 4 E apart (an odd multiple): their rows' low three bits differ by 4, which flips
+  // bit 2 of the swizzle and the parity bit: h alternates between h0 and h0 ^ HALF_FLIP
+  __host__ __device__ static constexpr bool half_shift(int stride) {
+    return stride % (4 * E) == 0 && stride % (8 * E) != 0;
+  }
+  static constexpr int HALF_FLIP = E == 16 ? 12 : 4;
   // entries i0 + r, r < 8, of one line with i0 a multiple of 8 share a row and its swizzle:
   // their offsets are rb + (q ^ r)
   __device__ static __forceinline__ void group8(int line, int i0, int& rb, int& q) {
@@ -337,6 +343,10 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
         SL::group8(line, base, rb, qq);
 #pragma unroll
         for (int r = 0; r < ROUT; ++r) s[rb + (qq ^ r)] = c_norm(v[q][r]);
+      } else if constexpr (SL::half_shift(NS)) {
+        const int o0 = SL::off(line, base), p0 = o0 & (SL::E - 1), rb = o0 - p0;
+#pragma unroll
+        for (int r = 0; r < ROUT; ++r) s[rb + r * NS + (p0 ^ ((r & 1) ? SL::HALF_FLIP : 0))] = c_norm(v[q][r]);
       } else {
 #pragma unroll
         for (int r = 0; r < ROUT; ++r) s[SL::off(line, base + r * NS)] = c_norm(v[q][r]);
