@@ -776,14 +776,13 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK
     for (int i = 0; i < NB; ++i)
       if (w + i < np) col[pos[w + i]] = extra[i];
   }
+  // column-oriented (right-looking): x_i final, then every x_r below it updated at once
 #pragma unroll
-  for (int i = 1; i < NB; ++i) {
+  for (int i = 0; i < NB - 1; ++i) {
     if (i < w) {
-      C acc = x[i];
 #pragma unroll
-      for (int l = 0; l < NB; ++l)
-        if (l < i) acc = cfms(acc, Ld[i][l], x[l]);
-      x[i] = acc;
+      for (int r = i + 1; r < NB; ++r)
+        if (r < w) x[r] = cfms(x[r], Ld[r][i], x[i]);
     }
   }
 #pragma unroll
@@ -792,14 +791,26 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower(LevelK
 }
 
 // Columns c in [smax, ncols): F[j0:j1, c] = U_blk^{-1} F[j0:j1, c] (non-unit upper).
+// Column-oriented (right-looking) substitution: once x_i is final, every x_l above it takes
+// its update at once, so a thread's dependent chain is one product per row (the dot-product
+// form chains up to 31 products per row); the reciprocals of the diagonal are formed once
+// per CTA.
 template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK<C> L, int j0, int j1) {
   const int z = blockIdx.x;
   const int fmax = L.fmax, w = j1 - j0;
   C* A = L.F + (size_t)z * fmax * L.ncols;
   __shared__ C Ud[NB][NB + 1];
+  __shared__ C rdg[NB];
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     const int i = idx % w, l = idx / w;
     Ud[i][l] = A[(size_t)(j0 + l) * fmax + j0 + i];
+  }
+  __syncthreads();
+  if (threadIdx.x < w) {
+    C one;
+    one.x = 1;
+    one.y = 0;
+    rdg[threadIdx.x] = cdiv(one, Ud[threadIdx.x][threadIdx.x]);
   }
   __syncthreads();
   const int c = L.smax + blockIdx.y * blockDim.x + threadIdx.x;
@@ -812,11 +823,9 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_upper(LevelK
 #pragma unroll
   for (int i = NB - 1; i >= 0; --i) {
     if (i < w) {
-      C acc = x[i];
+      x[i] = cmul(x[i], rdg[i]);
 #pragma unroll
-      for (int l = 0; l < NB; ++l)
-        if (l > i && l < w) acc = cfms(acc, Ud[i][l], x[l]);
-      x[i] = cdiv(acc, Ud[i][i]);
+      for (int l = 0; l < i; ++l) x[l] = cfms(x[l], Ud[l][i], x[i]);
     }
   }
 #pragma unroll
@@ -1212,14 +1221,13 @@ template <typename C> __global__ void __launch_bounds__(128) k_trsm_lower_swp(Le
     for (int i = 0; i < NB; ++i)
       if (i < np) col[bpos[i]] = extra[i];
   }
+  // column-oriented (right-looking): x_i final, then every x_r below it updated at once
 #pragma unroll
-  for (int i = 1; i < NB; ++i) {
+  for (int i = 0; i < NB - 1; ++i) {
     if (i < w) {
-      C acc = x[i];
 #pragma unroll
-      for (int l = 0; l < NB; ++l)
-        if (l < i) acc = cfms(acc, Ld[i][l], x[l]);
-      x[i] = acc;
+      for (int r = i + 1; r < NB; ++r)
+        if (r < w) x[r] = cfms(x[r], Ld[r][i], x[i]);
     }
   }
 #pragma unroll
