@@ -353,8 +353,8 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
   std::vector<int> iters(nrhs, 0), cycles(nrhs, 0);
   std::vector<char> conv(nrhs, 0);
   for (int j = 0; j < nrhs; ++j) conv[j] = rn[j] <= tol * gn[j];
-  // r = g for the first cycle (u = 0)
-  LS_CUDA(cudaMemcpyAsync(r, g, tot * sizeof(double2), cudaMemcpyDeviceToDevice, c->st));
+  // the first cycle's residual is g itself (u = 0): it is read in place, r holds the later ones
+  const double2* r0 = g;
 
   std::vector<cd> H((size_t)nrhs * (R + 1) * R), sn((size_t)nrhs * R), s((size_t)nrhs * (R + 1));
   std::vector<double> cs((size_t)nrhs * R), sc(nrhs);
@@ -384,8 +384,8 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       s[(size_t)j * (R + 1)] = act[j] ? rn[j] : 0.0;
     }
     LS_CUDA(cudaMemcpyAsync(sd, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    if (mixed) ls::scale_f<double2>(r, (float2*)c->V[0], sd, N, nrhs, c->st);
-    else ls::scale(r, c->V[0], sd, N, nrhs, c->st);
+    if (mixed) ls::scale_f<double2>(r0, (float2*)c->V[0], sd, N, nrhs, c->st);
+    else ls::scale(r0, c->V[0], sd, N, nrhs, c->st);
     int k = 0;
     for (; k < R; ++k) {
       bool live = false;
@@ -541,6 +541,7 @@ void solve_impl(ls_ctx* c, int nrhs, const double2* g, double tol, double2* u, l
       rn[j] = std::sqrt(hh[j].x);
       conv[j] = rn[j] <= tol * gn[j];
     }
+    r0 = r;
   }
   bool all = true;
   for (int j = 0; j < nrhs; ++j) {
