@@ -867,14 +867,14 @@ template <typename C> __global__ void __launch_bounds__(256) k_ring_trsm(LevelK<
   C f[NB];
 #pragma unroll
   for (int c = 0; c < NB; ++c) f[c] = c < w ? row[(size_t)c * fmax] : czero<C>();
+  // column-oriented (right-looking): f_c final, then every f_c2 right of it updated at once
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < w) {
-      C acc = f[c];
+      f[c] = cmul(f[c], invd[c]);
 #pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < c) acc = cfms(acc, f[i], u[c][i]);
-      f[c] = cmul(acc, invd[c]);
+      for (int c2 = c + 1; c2 < NB; ++c2)
+        if (c2 < w) f[c2] = cfms(f[c2], f[c], u[c2][c]);
     }
   }
 #pragma unroll
