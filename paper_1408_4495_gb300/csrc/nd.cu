@@ -2482,46 +2482,45 @@ __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const flo
 }
 
 // ---- small sweep levels (the bottom of the tree: at most 32 product rows and SMALL_MAX_K
-// columns, FP32, 16 right-hand sides per item): one warp per (front, group), SMALL_FPC warps
-// per CTA, no block barrier.  Before the programmatic-dependent wait the warp stages its
-// item's indices and copies its factor tile (rows x K) into its shared-memory slice with
-// cp.async, overlapping the previous level's tail; after it, it gathers the vector operand
-// (K x 16 right-hand sides; index and data loads of four pieces in flight) and every lane
-// stores its finished sums: 16 right-hand sides of one row when WIDE (more than 16 rows),
-// else 8 (lanes 16-31 take the second half).  Forward: rows are the ring rows of Y, the
-// children's ring updates added at the store.
-constexpr int SMALL_FPC = 4;
-// bytes of one warp's shared-memory slice: factor tile (RP x K complex, RP = 16 or 32 rows),
-// vector operand (K x 16 complex), indices (3 K + 2 RP ints), rounded up to 16 bytes so that
-// every slice's float4 accesses stay aligned
-__host__ __device__ constexpr size_t small_slice_bytes(int K, int rp) {
-  return (((size_t)rp * K + (size_t)K * 16) * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
+// columns, FP32, 16 right-hand sides per item): one CTA per front, one warp per group of 16
+// right-hand sides (ng warps).  Before the programmatic-dependent wait the CTA stages the
+// front's indices and copies its factor tile (rows x K, shared by the groups) into shared
+// memory with cp.async, overlapping the previous level's tail; after it, every warp gathers
+// its group's vector operand (K x 16 right-hand sides; index and data loads of four pieces in
+// flight) and every lane stores its finished sums: 16 right-hand sides of one row when WIDE
+// (more than 16 rows), else 8 (lanes 16-31 take the second half).  Forward: rows are the ring
+// rows of Y, the children's ring updates added at the store.
+constexpr int SMALL_FPC = 4;  // warps per CTA at most (groups of 16 of SOLVE_CHUNK)
+// bytes of the CTA's shared memory: factor tile (RP x K complex, RP = 16 or 32 rows), indices
+// (3 K + 2 RP ints, padded to 16 bytes), then ng vector operands (K x 16 complex each)
+__host__ __device__ constexpr size_t small_head_bytes(int K, int rp) {
+  return ((size_t)rp * K * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
+}
+__host__ __device__ constexpr size_t small_smem_bytes(int K, int rp, int ng) {
+  return small_head_bytes(K, rp) + (size_t)ng * K * 16 * sizeof(float2);
 }
 template <int MODE, bool WIDE>
-__global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S, int nitems) {
+__global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RP = WIDE ? 32 : 16, NJ = WIDE ? 16 : 8;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int item = blockIdx.x * SMALL_FPC + wp;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, NT = blockDim.x;
+  const int z = blockIdx.x;
   const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
   const int K = MODE == 0 ? smax : bmax + smax;
   const int rows = MODE == 0 ? bmax : smax;
-  unsigned char* base = smem_raw + (size_t)wp * small_slice_bytes(K, RP);
-  float2* As = reinterpret_cast<float2*>(base);  // [K][RP]
-  float2* vs = As + (size_t)RP * K;              // [K][16]
-  int* ix = reinterpret_cast<int*>(vs + (size_t)K * 16);  // [3 K] item sources, [2 RP] row indices
-  const bool on = item < nitems;
-  const int z = on ? item / S.ng : 0, g = on ? item - z * S.ng : 0;
+  float2* As = reinterpret_cast<float2*>(smem_raw);  // [K][RP]
+  int* ix = reinterpret_cast<int*>(As + (size_t)RP * K);  // [3 K] item sources, [2 RP] row indices
+  float2* vs = reinterpret_cast<float2*>(smem_raw + small_head_bytes(K, RP)) + (size_t)g * K * 16;  // [K][16]
   // ---- prologue: static data only
-  if (on) {
+  {
     const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
                       (MODE == 0 ? smax : 0);
-    for (int e = lane; e < K * RP; e += 32) {
+    for (int e = threadIdx.x; e < K * RP; e += NT) {
       const int k = e / RP, r = e - k * RP;
       cp_async_elem<8>(As + e, r < rows ? A + (size_t)k * fmax + r : A, r < rows);
     }
     cp_async_commit();
-    for (int c = lane; c < K; c += 32) {
+    for (int c = threadIdx.x; c < K; c += NT) {
       if (MODE == 0) {
         ix[3 * c] = __ldg(S.own + (size_t)z * smax + c);
         ix[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
@@ -2530,7 +2529,7 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
         ix[3 * c] = c < bmax ? __ldg(S.ring + (size_t)z * bmax + c) : -1;
       }
     }
-    for (int r = lane; r < RP; r += 32) {
+    for (int r = threadIdx.x; r < RP; r += NT) {
       if (MODE == 0) {
         const bool rv = r < rows;
         ix[3 * K + 2 * r] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2) : -1;
@@ -2542,8 +2541,7 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
   }
   pdl_wait();
   pdl_trigger();
-  if (!on) return;
-  __syncwarp();
+  __syncthreads();  // indices
   const size_t wrow = (size_t)g * S.nf * fmax + (size_t)z * fmax;
   const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
   constexpr int GB = 4;
@@ -2578,7 +2576,7 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
     }
   }
   cp_async_wait<0>();
-  __syncwarp();
+  __syncthreads();  // the factor tile (every thread's copies) and this warp's operand
   const int row = WIDE ? lane : (lane & 15), j0 = WIDE ? 0 : (lane >> 4) * 8;
   if (row >= rows) return;
   float2 acc[NJ];
@@ -2646,11 +2644,10 @@ template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, 
   S.ng = ng;
   S.N = p->N;
   const int K = MODE == 0 ? D.smax : D.bmax + D.smax;
-  const int nitems = D.nf * ng;
   const int rows = MODE == 0 ? D.bmax : D.smax;
   const bool wide = rows > 16;
-  const size_t smem = (size_t)SMALL_FPC * small_slice_bytes(K, wide ? 32 : 16);
-  const size_t smem_max = (size_t)SMALL_FPC * small_slice_bytes(SMALL_MAX_K, 32);
+  const size_t smem = small_smem_bytes(K, wide ? 32 : 16, ng);
+  const size_t smem_max = small_smem_bytes(SMALL_MAX_K, 32, SMALL_FPC);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
     LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2659,13 +2656,12 @@ template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, 
                                  (int)smem_max));
     attr.store(true, std::memory_order_release);
   }
-  const dim3 grid((unsigned)((nitems + SMALL_FPC - 1) / SMALL_FPC)), block(32 * SMALL_FPC);
+  // one CTA per front, one warp per group
+  const dim3 grid((unsigned)D.nf), block(32 * ng);
   if (wide)
-    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st,
-              launch_pdl(k_sweep_small<MODE, true>, grid, block, smem, st, S, nitems));
+    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st, launch_pdl(k_sweep_small<MODE, true>, grid, block, smem, st, S));
   else
-    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st,
-              launch_pdl(k_sweep_small<MODE, false>, grid, block, smem, st, S, nitems));
+    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st, launch_pdl(k_sweep_small<MODE, false>, grid, block, smem, st, S));
 }
 
 // whether level l's sweep product of this mode runs on the tensor cores
