@@ -388,8 +388,8 @@ ls_status ls_profile_stop(char* report, int capacity);
  * (rows) given to the tensor cores, the largest front factored Gauss-Jordan style in one CTA,
  * how many CTAs per SM the split of a solve sweep level aims at, and the smallest FP32
  * forward and backward solve levels (rows of their products, at least 32) run on the tensor
- * cores, and the largest bottom solve level (columns of its product, up to 64; rows up to
- * 32) run one warp per front.  A coordinate search
+ * cores, and the largest bottom solve level (columns of its product, up to 256; rows up to
+ * 64) run one CTA per front.  A coordinate search
  * keeps each alternative that is more than 2 % faster (the fastest of 2 factorizations / 3
  * solves of nrhs right-hand sides, CUDA events).  The choice is applied to c, kept for every
  * later context of the same (dim, n, prec, kernel) in this process, and, when the
@@ -408,7 +408,7 @@ ls_status ls_profile_stop(char* report, int capacity);
  *   a factorization choice needs a new ls_factor to take effect).  LS_EINVAL when a value is
  *   out of range (two_level_min <= 0, tc_min_rows < 1, sweep_ctas outside 1..4,
  *   gj_max_own outside 1..32, tcs_min_rows or tcs_bwd_min_rows < 1, small_max_k outside
- *   0..64).
+ *   0..256).
  * --------------------------------------------------------------------------------------- */
 ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity);
 ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity);

@@ -1489,9 +1489,10 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
           try_solve(t);
         }
       }
-      // the bottom levels one warp per front up to 64 columns (the default), up to 32, or none
+      // the bottom levels one CTA per front up to 64 columns (the default), up to 32, 128 or
+      // 256, or none
       const int small_base = best.small_max_k;
-      for (int v : {0, 32, 64}) {
+      for (int v : {0, 32, 64, 128, 256}) {
         if (v == small_base) continue;
         ls::NdTune t = best;
         t.small_max_k = v;
@@ -1561,7 +1562,7 @@ ls_status ls_set_tune(ls_ctx* c, const char* json) {
     int_key("gj_max_own", 1, 32, &t.gj_max_own);
     int_key("tcs_min_rows", 1, 1 << 30, &t.tcs_min_rows);
     int_key("tcs_bwd_min_rows", 1, 1 << 30, &t.tcs_bwd_min_rows);
-    int_key("small_max_k", 0, 64, &t.small_max_k);
+    int_key("small_max_k", 0, 256, &t.small_max_k);
     factor_wait(c);
     ls::nd_set_tune(c->nd, t);
     ++c->gen;  // the captured graphs hold the old launch sequences

@@ -2481,62 +2481,66 @@ __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const flo
   }
 }
 
-// ---- small sweep levels (the bottom of the tree: at most 32 product rows and SMALL_MAX_K
+// ---- small sweep levels (the bottom of the tree: at most 64 product rows and SMALL_MAX_K
 // columns, FP32, 16 right-hand sides per item): one CTA per front, one warp per group of 16
 // right-hand sides (ng warps).  Before the programmatic-dependent wait the CTA stages the
-// front's indices and copies its factor tile (rows x K, shared by the groups) into shared
-// memory with cp.async, overlapping the previous level's tail; after it, every warp gathers
-// its group's vector operand (K x 16 right-hand sides; index and data loads of four pieces in
-// flight) and every lane stores its finished sums: 16 right-hand sides of one row when WIDE
-// (more than 16 rows), else 8 (lanes 16-31 take the second half).  Forward: rows are the ring
-// rows of Y, the children's ring updates added at the store.
-constexpr int SMALL_FPC = 4;  // warps per CTA at most (groups of 16 of SOLVE_CHUNK)
-// bytes of the CTA's shared memory: factor tile (RP x K complex, RP = 16 or 32 rows), indices
-// (3 K + 2 RP ints, padded to 16 bytes), then ng vector operands (K x 16 complex each)
+// front's indices and copies the first SMALL_KCH columns of its factor tile (shared by the
+// groups) into shared memory with cp.async, overlapping the previous level's tail; after it,
+// column chunk by chunk, every warp gathers its group's vector operand (16 right-hand sides
+// per column; index and data loads of four pieces in flight) and accumulates.  Lane l holds
+// row l (and l + 32 when RP = 64) for all 16 right-hand sides, or, when RP = 16, row l & 15
+// for 8 of them (lanes 16-31 the second half).  Forward: rows are the ring rows of Y, the
+// children's ring updates added at the store.
+constexpr int SMALL_FPC = 4;   // warps per CTA at most (groups of 16 of SOLVE_CHUNK)
+constexpr int SMALL_KCH = 64;  // columns of the factor tile and operand staged at once
+// bytes of the CTA's shared memory: factor chunk (RP x KCH complex, RP = 16, 32 or 64 rows),
+// indices (3 K + 2 RP ints, padded to 16 bytes), then ng operand chunks (KCH x 16 complex)
 __host__ __device__ constexpr size_t small_head_bytes(int K, int rp) {
-  return ((size_t)rp * K * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
+  return ((size_t)rp * SMALL_KCH * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
 }
 __host__ __device__ constexpr size_t small_smem_bytes(int K, int rp, int ng) {
-  return small_head_bytes(K, rp) + (size_t)ng * K * 16 * sizeof(float2);
+  return small_head_bytes(K, rp) + (size_t)ng * SMALL_KCH * 16 * sizeof(float2);
 }
-template <int MODE, bool WIDE>
+template <int MODE, int RP, bool MULTI>
 __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int RP = WIDE ? 32 : 16, NJ = WIDE ? 16 : 8;
+  constexpr int NJ = RP == 16 ? 8 : 16, NRB = RP == 64 ? 2 : 1;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, NT = blockDim.x;
   const int z = blockIdx.x;
   const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
   const int K = MODE == 0 ? smax : bmax + smax;
   const int rows = MODE == 0 ? bmax : smax;
-  float2* As = reinterpret_cast<float2*>(smem_raw);  // [K][RP]
-  int* ix = reinterpret_cast<int*>(As + (size_t)RP * K);  // [3 K] item sources, [2 RP] row indices
-  float2* vs = reinterpret_cast<float2*>(smem_raw + small_head_bytes(K, RP)) + (size_t)g * K * 16;  // [K][16]
-  // ---- prologue: static data only
-  {
-    const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
-                      (MODE == 0 ? smax : 0);
-    for (int e = threadIdx.x; e < K * RP; e += NT) {
+  float2* As = reinterpret_cast<float2*>(smem_raw);  // [KCH][RP]
+  int* ix = reinterpret_cast<int*>(As + (size_t)RP * SMALL_KCH);  // [3 K] item sources, [2 RP] rows
+  float2* vs = reinterpret_cast<float2*>(smem_raw + small_head_bytes(K, RP)) + (size_t)g * SMALL_KCH * 16;
+  const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
+                    (MODE == 0 ? smax : 0);
+  auto load_chunk = [&](int kc) {
+    const int kw = min(SMALL_KCH, K - kc);
+    for (int e = threadIdx.x; e < kw * RP; e += NT) {
       const int k = e / RP, r = e - k * RP;
-      cp_async_elem<8>(As + e, r < rows ? A + (size_t)k * fmax + r : A, r < rows);
+      cp_async_elem<8>(As + e, r < rows ? A + (size_t)(kc + k) * fmax + r : A, r < rows);
     }
     cp_async_commit();
-    for (int c = threadIdx.x; c < K; c += NT) {
-      if (MODE == 0) {
-        ix[3 * c] = __ldg(S.own + (size_t)z * smax + c);
-        ix[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
-        ix[3 * c + 2] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
-      } else {
-        ix[3 * c] = c < bmax ? __ldg(S.ring + (size_t)z * bmax + c) : -1;
-      }
+  };
+  // ---- prologue: static data only
+  load_chunk(0);
+  for (int c = threadIdx.x; c < K; c += NT) {
+    if (MODE == 0) {
+      ix[3 * c] = __ldg(S.own + (size_t)z * smax + c);
+      ix[3 * c + 1] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2);
+      ix[3 * c + 2] = __ldg(S.fsrc + ((size_t)z * fmax + c) * 2 + 1);
+    } else {
+      ix[3 * c] = c < bmax ? __ldg(S.ring + (size_t)z * bmax + c) : -1;
     }
-    for (int r = threadIdx.x; r < RP; r += NT) {
-      if (MODE == 0) {
-        const bool rv = r < rows;
-        ix[3 * K + 2 * r] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2) : -1;
-        ix[3 * K + 2 * r + 1] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2 + 1) : -1;
-      } else {
-        ix[3 * K + 2 * r] = r < rows ? __ldg(S.own + (size_t)z * smax + r) : -1;
-      }
+  }
+  for (int r = threadIdx.x; r < RP; r += NT) {
+    if (MODE == 0) {
+      const bool rv = r < rows;
+      ix[3 * K + 2 * r] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2) : -1;
+      ix[3 * K + 2 * r + 1] = rv ? __ldg(S.fsrc + ((size_t)z * fmax + smax + r) * 2 + 1) : -1;
+    } else {
+      ix[3 * K + 2 * r] = r < rows ? __ldg(S.own + (size_t)z * smax + r) : -1;
     }
   }
   pdl_wait();
@@ -2544,82 +2548,100 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
   __syncthreads();  // indices
   const size_t wrow = (size_t)g * S.nf * fmax + (size_t)z * fmax;
   const size_t cg = (size_t)g * S.nf_c * S.fmax_c;
-  constexpr int GB = 4;
-  for (int p0 = lane; p0 < K * 8; p0 += 32 * GB) {
-    float4 x[GB];
+  const int row0 = RP == 16 ? (lane & 15) : lane, j0 = RP == 16 ? (lane >> 4) * 8 : 0;
+  float2 acc[NRB][NJ];
 #pragma unroll
-    for (int u = 0; u < GB; ++u) {
-      const int p = p0 + 32 * u, c = p >> 3, v = p & 7;
-      x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p >= K * 8) continue;
-      if (MODE == 0) {
-        const int pt = ix[3 * c], s0 = ix[3 * c + 1], s1 = ix[3 * c + 2];
-        if (pt >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v));
-        if (s0 >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16) + v));
-        if (s1 >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16) + v));
-      } else if (c < bmax) {
-        const int pt = ix[3 * c];
-        if (pt >= 0) {
-          const float4 t = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v);
-          x[u] = make_float4(-t.x, -t.y, -t.z, -t.w);  // the H columns enter with a minus sign
+  for (int b = 0; b < NRB; ++b)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[b][j] = make_float2(0.f, 0.f);
+  constexpr int GB = 4;
+  // MULTI: more than one column chunk (K > SMALL_KCH); else the loop runs once
+  for (int kc = 0; kc < (MULTI ? K : 1); kc += SMALL_KCH) {
+    const int kw = MULTI ? min(SMALL_KCH, K - kc) : K;
+    if (MULTI && kc > 0) {
+      __syncthreads();  // every warp is done with the previous chunk
+      load_chunk(kc);
+    }
+    for (int p0 = lane; p0 < kw * 8; p0 += 32 * GB) {
+      float4 x[GB];
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int p = p0 + 32 * u, c = kc + (p >> 3), v = p & 7;
+        x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p >= kw * 8) continue;
+        if (MODE == 0) {
+          const int pt = ix[3 * c], s0 = ix[3 * c + 1], s1 = ix[3 * c + 2];
+          if (pt >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v));
+          if (s0 >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16) + v));
+          if (s1 >= 0) x[u] = padd(x[u], __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16) + v));
+        } else if (c < bmax) {
+          const int pt = ix[3 * c];
+          if (pt >= 0) {
+            const float4 t = __ldcg(reinterpret_cast<const float4*>(S.T + ((size_t)g * S.N + pt) * 16) + v);
+            x[u] = make_float4(-t.x, -t.y, -t.z, -t.w);  // the H columns enter with a minus sign
+          }
+        } else {
+          x[u] = __ldcg(reinterpret_cast<const float4*>(S.W + (wrow + c - bmax) * 16) + v);
         }
-      } else {
-        x[u] = __ldcg(reinterpret_cast<const float4*>(S.W + (wrow + c - bmax) * 16) + v);
+      }
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int p = p0 + 32 * u, c = kc + (p >> 3), v = p & 7;
+        if (p >= kw * 8) continue;
+        if (MODE == 0) reinterpret_cast<float4*>(S.W + (wrow + c) * 16)[v] = x[u];
+        reinterpret_cast<float4*>(vs)[p] = x[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < GB; ++u) {
-      const int p = p0 + 32 * u, c = p >> 3, v = p & 7;
-      if (p >= K * 8) continue;
-      if (MODE == 0) reinterpret_cast<float4*>(S.W + (wrow + c) * 16)[v] = x[u];
-      reinterpret_cast<float4*>(vs)[p] = x[u];
-    }
-  }
-  cp_async_wait<0>();
-  __syncthreads();  // the factor tile (every thread's copies) and this warp's operand
-  const int row = WIDE ? lane : (lane & 15), j0 = WIDE ? 0 : (lane >> 4) * 8;
-  if (row >= rows) return;
-  float2 acc[NJ];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) acc[j] = make_float2(0.f, 0.f);
+    cp_async_wait<0>();
+    __syncthreads();  // the factor chunk (every thread's copies) and this warp's operand
 #pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    const float2 a = As[k * RP + row];
-    const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16 + j0);
+    for (int k = 0; k < kw; ++k) {
+      const float4* vv = reinterpret_cast<const float4*>(vs + (size_t)k * 16 + j0);
 #pragma unroll
-    for (int j = 0; j < NJ / 2; ++j) {
-      const float4 b = vv[j];
-      acc[2 * j] = cfma(acc[2 * j], a, make_float2(b.x, b.y));
-      acc[2 * j + 1] = cfma(acc[2 * j + 1], a, make_float2(b.z, b.w));
+      for (int b = 0; b < NRB; ++b) {
+        const float2 a = As[k * RP + row0 + 32 * b];
+#pragma unroll
+        for (int j = 0; j < NJ / 2; ++j) {
+          const float4 v4 = vv[j];
+          acc[b][2 * j] = cfma(acc[b][2 * j], a, make_float2(v4.x, v4.y));
+          acc[b][2 * j + 1] = cfma(acc[b][2 * j + 1], a, make_float2(v4.z, v4.w));
+        }
+      }
     }
   }
-  float2* dst;
-  if (MODE == 0) {
-    const int s0 = ix[3 * K + 2 * row], s1 = ix[3 * K + 2 * row + 1];
 #pragma unroll
-    for (int j = 0; j < NJ; j += 2) {
-      float4 x = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
-      if (s0 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16 + j0 + j)));
-      if (s1 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16 + j0 + j)));
-      acc[j] = make_float2(x.x, x.y);
-      acc[j + 1] = make_float2(x.z, x.w);
+  for (int b = 0; b < NRB; ++b) {
+    const int row = row0 + 32 * b;
+    if (row >= rows) continue;
+    float2* dst;
+    if (MODE == 0) {
+      const int s0 = ix[3 * K + 2 * row], s1 = ix[3 * K + 2 * row + 1];
+#pragma unroll
+      for (int j = 0; j < NJ; j += 2) {
+        float4 x = make_float4(acc[b][j].x, acc[b][j].y, acc[b][j + 1].x, acc[b][j + 1].y);
+        if (s0 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s0) * 16 + j0 + j)));
+        if (s1 >= 0) x = padd(x, __ldcg(reinterpret_cast<const float4*>(S.Wc + (cg + s1) * 16 + j0 + j)));
+        acc[b][j] = make_float2(x.x, x.y);
+        acc[b][j + 1] = make_float2(x.z, x.w);
+      }
+      dst = S.W + (wrow + smax + row) * 16 + j0;
+    } else {
+      const int pt = ix[3 * K + 2 * row];
+      if (pt < 0) continue;
+      dst = S.T + ((size_t)g * S.N + pt) * 16 + j0;
     }
-    dst = S.W + (wrow + smax + row) * 16 + j0;
-  } else {
-    const int pt = ix[3 * K + 2 * row];
-    if (pt < 0) return;
-    dst = S.T + ((size_t)g * S.N + pt) * 16 + j0;
-  }
 #pragma unroll
-  for (int j = 0; j < NJ; j += 2)
-    reinterpret_cast<float4*>(dst)[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+    for (int j = 0; j < NJ; j += 2)
+      reinterpret_cast<float4*>(dst)[j / 2] =
+          make_float4(acc[b][j].x, acc[b][j].y, acc[b][j + 1].x, acc[b][j + 1].y);
+  }
 }
 
-constexpr int SMALL_MAX_K = 64;
+constexpr int SMALL_MAX_K = 256;
 static bool small_level(const NdPlan* p, int l, int mode) {
   const LevelDev& D = p->lev[l];
   const int rows = mode == 0 ? D.bmax : D.smax, K = mode == 0 ? D.smax : D.bmax + D.smax;
-  return rows > 0 && rows <= 32 && K > 0 && K <= std::min(SMALL_MAX_K, p->tune.small_max_k);
+  return rows > 0 && rows <= 64 && K > 0 && K <= std::min(SMALL_MAX_K, p->tune.small_max_k);
 }
 
 template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, int ng, cudaStream_t st) {
@@ -2645,23 +2667,28 @@ template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, 
   S.N = p->N;
   const int K = MODE == 0 ? D.smax : D.bmax + D.smax;
   const int rows = MODE == 0 ? D.bmax : D.smax;
-  const bool wide = rows > 16;
-  const size_t smem = small_smem_bytes(K, wide ? 32 : 16, ng);
-  const size_t smem_max = small_smem_bytes(SMALL_MAX_K, 32, SMALL_FPC);
+  const int rp = rows > 32 ? 64 : (rows > 16 ? 32 : 16);
+  const size_t smem = small_smem_bytes(K, rp, ng);
+  const size_t smem_max = small_smem_bytes(SMALL_MAX_K, 64, SMALL_FPC);
   static std::atomic<bool> attr{false};  // set once per process; repeats are harmless
   if (!attr.load(std::memory_order_acquire)) {
-    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_max));
-    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    LS_CUDA(cudaFuncSetAttribute(k_sweep_small<MODE, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     attr.store(true, std::memory_order_release);
   }
   // one CTA per front, one warp per group
   const dim3 grid((unsigned)D.nf), block(32 * ng);
-  if (wide)
-    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st, launch_pdl(k_sweep_small<MODE, true>, grid, block, smem, st, S));
-  else
-    LS_LAUNCH(MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64", st, launch_pdl(k_sweep_small<MODE, false>, grid, block, smem, st, S));
+  const char* cls = MODE == 0 ? "nd_fwd_c64" : "nd_bwd_c64";
+  const bool multi = K > SMALL_KCH;
+#define LS_SMALL(RP_, M_) LS_LAUNCH(cls, st, launch_pdl(k_sweep_small<MODE, RP_, M_>, grid, block, smem, st, S))
+  if (rp == 64) { if (multi) LS_SMALL(64, true); else LS_SMALL(64, false); }
+  else if (rp == 32) { if (multi) LS_SMALL(32, true); else LS_SMALL(32, false); }
+  else { if (multi) LS_SMALL(16, true); else LS_SMALL(16, false); }
+#undef LS_SMALL
 }
 
 // whether level l's sweep product of this mode runs on the tensor cores
