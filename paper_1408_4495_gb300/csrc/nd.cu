@@ -2493,13 +2493,15 @@ __global__ void __launch_bounds__(256) k_tcs_scatter(SweepK<float2> S, const flo
 // children's ring updates added at the store.
 constexpr int SMALL_FPC = 4;   // warps per CTA at most (groups of 16 of SOLVE_CHUNK)
 constexpr int SMALL_KCH = 64;  // columns of the factor tile and operand staged at once
-// bytes of the CTA's shared memory: factor chunk (RP x KCH complex, RP = 16, 32 or 64 rows),
-// indices (3 K + 2 RP ints, padded to 16 bytes), then ng operand chunks (KCH x 16 complex)
+// bytes of the CTA's shared memory: factor chunk (RP x KC complex, RP = 16, 32 or 64 rows,
+// KC = min(K, SMALL_KCH) columns), indices (3 K + 2 RP ints, padded to 16 bytes), then ng
+// operand chunks (KC x 16 complex)
+__host__ __device__ constexpr int small_kc(int K) { return K < SMALL_KCH ? K : SMALL_KCH; }
 __host__ __device__ constexpr size_t small_head_bytes(int K, int rp) {
-  return ((size_t)rp * SMALL_KCH * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
+  return ((size_t)rp * small_kc(K) * sizeof(float2) + ((size_t)3 * K + 2 * rp) * sizeof(int) + 15) / 16 * 16;
 }
 __host__ __device__ constexpr size_t small_smem_bytes(int K, int rp, int ng) {
-  return small_head_bytes(K, rp) + (size_t)ng * SMALL_KCH * 16 * sizeof(float2);
+  return small_head_bytes(K, rp) + (size_t)ng * small_kc(K) * 16 * sizeof(float2);
 }
 template <int MODE, int RP, bool MULTI>
 __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S) {
@@ -2510,9 +2512,10 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
   const int smax = S.smax, bmax = S.bmax, fmax = S.fmax;
   const int K = MODE == 0 ? smax : bmax + smax;
   const int rows = MODE == 0 ? bmax : smax;
-  float2* As = reinterpret_cast<float2*>(smem_raw);  // [KCH][RP]
-  int* ix = reinterpret_cast<int*>(As + (size_t)RP * SMALL_KCH);  // [3 K] item sources, [2 RP] rows
-  float2* vs = reinterpret_cast<float2*>(smem_raw + small_head_bytes(K, RP)) + (size_t)g * SMALL_KCH * 16;
+  const int kcap = small_kc(K);
+  float2* As = reinterpret_cast<float2*>(smem_raw);  // [kcap][RP]
+  int* ix = reinterpret_cast<int*>(As + (size_t)RP * kcap);  // [3 K] item sources, [2 RP] rows
+  float2* vs = reinterpret_cast<float2*>(smem_raw + small_head_bytes(K, RP)) + (size_t)g * kcap * 16;
   const float2* A = S.F + (size_t)z * fmax * S.ncols + (size_t)(MODE == 0 ? fmax : smax) * fmax +
                     (MODE == 0 ? smax : 0);
   auto load_chunk = [&](int kc) {
