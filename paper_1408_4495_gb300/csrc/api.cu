@@ -1489,8 +1489,8 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
           try_solve(t);
         }
       }
-      // the bottom levels one CTA per front up to 64 columns (the default), up to 32, 128 or
-      // 256, or none
+      // the bottom levels one CTA per front up to 256 columns (the default), up to 32, 64 or
+      // 128, or none
       const int small_base = best.small_max_k;
       for (int v : {0, 32, 64, 128, 256}) {
         if (v == small_base) continue;

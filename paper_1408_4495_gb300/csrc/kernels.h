@@ -161,7 +161,7 @@ struct NdTune {
   int tcs_min_rows = 64;         // FP32 forward-sweep levels whose products have at least this
                                  // many rows (and 16 inner columns) run on the tensor cores
   int tcs_bwd_min_rows = 64;     // the same for the backward sweep
-  int small_max_k = 64;          // FP32 sweep levels with at most 64 product rows and this many
+  int small_max_k = 256;         // FP32 sweep levels with at most 64 product rows and this many
                                  // columns (up to 256) run one CTA per front (0: none)
 };
 constexpr int SWEEP_CTAS_MAX = 4;  // the solve's partial-sum buffers are sized for this target

@@ -302,8 +302,8 @@ TCS_CASES = [(2, 128, 16.0, 40, 2e-5), (2, 256, 32.0, 16, 2e-3), (3, 32, 4.0, 24
 OFF = 1 << 30
 GENERIC = {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 0}
 SWEEP_VARIANTS = {"tensor_core": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 0},
-                  "one_warp": {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 64},
-                  "default": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 64}}
+                  "one_cta_per_front": {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 256},
+                  "default": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 256}}
 
 
 @pytest.mark.parametrize("variant", sorted(SWEEP_VARIANTS))
@@ -312,8 +312,8 @@ def test_sweep_level_kernels(LS, d, n, freq, nrhs, bound, variant):
     """The solve-level kernels other than the general k_sweep, when 16 right-hand sides share
     an item (more than 4 right-hand sides): FP32 levels whose products have at least 64 rows
     as one batched tcgen05 GEMM (3xTF32) between a gather of the vector operand and a scatter
-    of the result ("tensor_core"); the bottom levels (at most 32 rows, 64 columns) one warp
-    per front ("one_warp"); both ("default").  The comparison is the same application with
+    of the result ("tensor_core"); the levels of at most 64 rows and 256 columns one CTA per
+    front, in column chunks of 64 ("one_cta_per_front"); both ("default").  The comparison is the same application with
     every level on k_sweep: both meet the backward-error bound against the oracle's
     assembled M, the variant within 5x of k_sweep (3xTF32 products carry about 2^-22
     relative error against 2^-24 for FP32 FMAs; measured 1-3.6x), and with the tensor-core
