@@ -344,8 +344,25 @@ ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec p
  * class), in the arithmetic prec. */
 ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec);
 
-/* Sec. 2.2 eq. PC: out = M^{-1} [A;B] in, with the factors of ls_factor (their precision). */
+/* Sec. 2.2 eq. PC: out = M^{-1} [A;B] in, with the factors of ls_factor (their precision).
+ * With the FP32 factors and the refinement of ls_set_precond_refine on, in is rounded to
+ * FP32 first (as the solver's Arnoldi vectors are) and the result carries one refinement
+ * step. */
 ls_status ls_precond(ls_ctx* c, int nrhs, const double* in, double* out);
+
+/* One step of iterative refinement of the FP32 preconditioner (the paper solves eq. PC
+ * exactly; its FP32 factors leave a residual that grows with the separators' conditioning):
+ * z = M^{-1} r, then z += M^{-1} (r - M z) with r = [A;B] v, both solves with the FP32
+ * factors and the residual in FP32.  FGMRES allows the preconditioner to change between
+ * iterations.
+ *   mode  1: on for every application of the mixed path; 0: off; -1: automatic (the
+ *         default: the first application after each ls_factor estimates
+ *         E = |[A;B] v - M z| / |[A;B] v| for its first right-hand side and refinement is on
+ *         from then on while that factorization lasts when E > 0.02); -2: no change.
+ *   err   when not NULL receives E of the current factorization, -1 when none was taken.
+ * A forced mode (0 or 1) persists across factorizations.  No effect on the FP64 path or on
+ * general domains (their stencils are per point).  LS_EINVAL for a mode outside -2..1. */
+ls_status ls_set_precond_refine(ls_ctx* c, int mode, double* err);
 
 /* Sizes of the nested-dissection factorization (Sec. 3.2). */
 typedef struct {

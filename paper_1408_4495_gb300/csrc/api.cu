@@ -100,7 +100,8 @@ struct ls_ctx {
   // GMRES iterations: -1 = not yet known for this factorization (measured in its first
   // iteration), 0 = off, 1 = on
   int pre_refine = -1;
-  double pre_err = 0.0;  // |[A;B] v - M z| / |[A;B] v| of the first application after a factorization
+  int pre_refine_mode = -1;  // ls_set_precond_refine: -1 automatic, 0 off, 1 on
+  double pre_err = -1.0;     // |[A;B] v - M z| / |[A;B] v| of the first application after a factorization (-1: none)
   std::map<std::string, GraphEntry> graphs;
 };
 
@@ -882,7 +883,8 @@ ls_status ls_factor(ls_ctx* c) {
     });
     c->factored = true;
     c->factor_pending = true;
-    c->pre_refine = -1;
+    c->pre_refine = c->pre_refine_mode;
+    c->pre_err = -1.0;
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -1198,7 +1200,8 @@ ls_status ls_import_factors(ls_ctx* c, const void* in, size_t size) {
     ls::nd_copy_factors(c->nd, const_cast<unsigned char*>(static_cast<const unsigned char*>(in)) + sizeof h, false,
                         c->st);
     c->factored = true;
-    c->pre_refine = -1;
+    c->pre_refine = c->pre_refine_mode;
+    c->pre_err = -1.0;
     return LS_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -1333,7 +1336,14 @@ ls_status ls_precond(ls_ctx* c, int nrhs, const double* in, double* out) {
     copy_in(c, x, in, tot * sizeof(double2));
     if (c->prec == LS_PREC_MIXED) {
       float2* z32 = buf<float2>(c, "io_out32", tot);
-      precond_apply<float2>(c, nrhs, x, z32);
+      if (c->pre_refine == 1 && !c->general) {
+        // the refined application takes FP32 input, as in the solver
+        float2* x32 = buf<float2>(c, "io_in32", tot);
+        ls::cast<double2, float2>(x, x32, tot, c->st);
+        precond_apply<float2, float2>(c, nrhs, x32, z32);
+      } else {
+        precond_apply<float2>(c, nrhs, x, z32);
+      }
       ls::cast<float2, double2>(z32, y, tot, c->st);
     } else {
       precond_apply<double2>(c, nrhs, x, y);
@@ -1505,7 +1515,8 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
     ++c->gen;  // the captured graphs hold the old launch sequences
     c->factored = true;
     c->factor_pending = false;
-    c->pre_refine = -1;
+    c->pre_refine = c->pre_refine_mode;
+    c->pre_err = -1.0;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       tune_load_locked();
@@ -1540,6 +1551,23 @@ static bool json_number(const char* js, const char* key, double* v) {
   if (end == p + 1) return false;
   *v = x;
   return true;
+}
+
+ls_status ls_set_precond_refine(ls_ctx* c, int mode, double* err) {
+  try {
+    check_ctx(c);
+    if (mode < -2 || mode > 1) throw Error{ls::EINVAL_, "precond refine mode " + std::to_string(mode) + " outside -2..1"};
+    if (mode >= -1) {
+      c->pre_refine_mode = mode;
+      if (mode >= 0) c->pre_refine = mode;
+      else if (c->pre_err < 0) c->pre_refine = -1;  // estimated at the next solve
+      else c->pre_refine = c->pre_err > PRE_REFINE_ABOVE ? 1 : 0;
+    }
+    if (err) *err = c->pre_err;
+    return LS_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
 }
 
 ls_status ls_set_tune(ls_ctx* c, const char* json) {

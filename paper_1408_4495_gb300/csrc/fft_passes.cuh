@@ -281,6 +281,48 @@ template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR_hi_c
   }
 }
 
+// Global-memory ends of a column tile (the column pass's first pass reads its inputs
+// straight from global memory, the last pass stores to global memory): entry e of line l is
+// in[e * es_in + l] / out[e * es_out + l], lines l < nlines of the tile valid.
+template <typename C> struct ColIO {
+  const C* in;
+  C* out;
+  long es_in, es_out;
+  int n_in, n_out;  // entries read (the rest zero) / stored
+  int nlines;
+  bool vec_in, vec_out;  // the tile's lines of one entry as 16-byte vectors (all lines valid, aligned)
+  const C* sym;          // symbol quadrant, (n + 1)^d
+  long c0, inner;        // first line of the tile within the outer index, lines per outer index
+  int n1, d;
+};
+
+// Pass geometry: butterfly b = threadIdx.x + q NT of the CTA works on line b / BPL,
+// butterfly j = b mod BPL.  When NT divides BPL a thread holds every line of each of its
+// butterflies j (q = line * (BPL / NT) + jj).
+template <int L, int R, int NLINES, int NT> struct PassGeo {
+  static constexpr int BPL = L / R;
+  static constexpr int BF = NLINES * BPL;
+  static constexpr int PER = (BF + NT - 1) / NT;
+  static constexpr bool ALL_LINES = BPL % NT == 0;
+  static constexpr int M = ALL_LINES ? BPL / NT : 1;
+};
+
+// symbol value of entry e of the column tile's line (2D: the entry is the axis-0 frequency
+// and the line the axis-1 one; 3D: the line packs axes 1 and 2)
+template <typename C, int L> __device__ __forceinline__ C col_symbol(const ColIO<C>& io, int line, int e) {
+  const long cc = io.c0 + line;
+  const int q0 = e <= L - e ? e : L - e;
+  long si;
+  if (io.d == 2) {
+    const int k1 = (int)cc;
+    si = (long)q0 * io.n1 + (k1 <= L - k1 ? k1 : L - k1);
+  } else {
+    const int k1 = (int)(cc / L), k2 = (int)(cc - (long)k1 * L);
+    si = ((long)q0 * io.n1 + (k1 <= L - k1 ? k1 : L - k1)) * io.n1 + (k2 <= L - k2 ? k2 : L - k2);
+  }
+  return ldg_c(&io.sym[si]);
+}
+
 // One radix-R Stockham pass over NLINES lines of length L held in shared memory.
 // Pass input: sub-transforms of length NS; output: sub-transforms of length NS * R.
 // Butterfly j of a line reads entries j + r L/R, multiplies by w^{r k} with
@@ -288,44 +330,139 @@ template <int R, int SIGN, typename C> __device__ __forceinline__ void dftR_hi_c
 // PRUNE 1: the first pass of a zero-padded transform (entries L/2.. are zero: inputs
 // r >= R/2 are neither read nor used); PRUNE 2: the last pass of a cropped transform
 // (outputs L/2.. are not needed: r >= R/2 neither computed nor stored).
-template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT, int PRUNE = 0>
-__device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
+// EP (column tiles, io): 1 the first pass reads global memory instead of shared memory;
+// 3 the last pass stores to global memory instead of shared memory.
+template <typename C, int L, int R, int NS, int SIGN, int NLINES, int NT, int PRUNE = 0, int EP = 0>
+__device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw, const ColIO<C>* io = nullptr) {
   using SL = SLay<C, L, NLINES>;
-  constexpr int BPL = L / R;
-  constexpr int BF = NLINES * BPL;
-  constexpr int PER = (BF + NT - 1) / NT;
+  using G = PassGeo<L, R, NLINES, NT>;
+  constexpr int BPL = G::BPL, BF = G::BF, PER = G::PER;
   static_assert(PRUNE != 1 || (NS == 1 && R == 8), "padded first pass: radix 8");
   static_assert(PRUNE != 2 || (NS * R == L && R % 2 == 0), "cropped last pass: even radix");
+  static_assert(EP != 1 || NS == 1, "global input: first pass");
+  static_assert(EP == 0 || EP == 1 || EP == 3, "pass ends: shared memory, global input, global output");
+  static_assert(EP != 3 || NS * R == L, "global output: last pass");
   constexpr int RIN = PRUNE == 1 ? R / 2 : R, ROUT = PRUNE == 2 ? R / 2 : R;
+  constexpr int VW = (int)(NLINES * sizeof(C) / sizeof(float4));  // 16-byte vectors per entry
+  constexpr bool VEC = G::ALL_LINES && NLINES * sizeof(C) % sizeof(float4) == 0 && VW > 0;
   C v[PER][R];
+  if constexpr (EP == 1) {
+    // every load issued before the first butterfly
+    bool vec = false;
+    if constexpr (VEC) {
+      if (io->vec_in) {
+        vec = true;
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int b = threadIdx.x + q * NT;
-    if (BF % NT == 0 || b < BF) {
-      const int line = b / BPL, j = b - line * BPL;
-      if constexpr (SL::shift_free(BPL)) {
-        const int o = SL::off(line, j);
+        for (int jj = 0; jj < G::M; ++jj) {
+          const int j = threadIdx.x + jj * NT;
 #pragma unroll
-        for (int r = 0; r < RIN; ++r) v[q][r] = s[o + r * BPL];
-      } else {
+          for (int r = 0; r < RIN; ++r) {
+            const int e = j + r * BPL;
+            float4 w[VW];
+            const float4* src = reinterpret_cast<const float4*>(io->in + (long)e * io->es_in);
 #pragma unroll
-        for (int r = 0; r < RIN; ++r) v[q][r] = s[SL::off(line, j + r * BPL)];
-      }
-      if constexpr (NS > 1) {
-        const int k = j % NS;
+            for (int u = 0; u < VW; ++u) w[u] = e < io->n_in ? __ldg(src + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            C c[NLINES];
+            memcpy(c, w, sizeof(c));
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C w = ldg_c(&tw[r * k * (L / (NS * R))]);
-          if (SIGN > 0) w.y = -w.y;
-          v[q][r] = cmul(v[q][r], w);
+            for (int line = 0; line < NLINES; ++line) v[line * G::M + jj][r] = c[line];
+          }
         }
       }
+    }
+    if (!vec) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (BF % NT == 0 || b < BF) {
+          const int line = b / BPL, j = b - line * BPL;
+#pragma unroll
+          for (int r = 0; r < RIN; ++r) {
+            const int e = j + r * BPL;
+            v[q][r] = (line < io->nlines && e < io->n_in) ? ldg_c(io->in + (long)e * io->es_in + line) : czero<C>();
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
       if constexpr (PRUNE == 1) dft8v_lo<SIGN>(v[q]);
-      else if constexpr (PRUNE == 2) dftR_hi_cut<R, SIGN>(v[q]);
       else dftR<R, SIGN>(v[q]);
     }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int b = threadIdx.x + q * NT;
+      if (BF % NT == 0 || b < BF) {
+        const int line = b / BPL, j = b - line * BPL;
+        if constexpr (SL::shift_free(BPL)) {
+          const int o = SL::off(line, j);
+#pragma unroll
+          for (int r = 0; r < RIN; ++r) v[q][r] = s[o + r * BPL];
+        } else {
+#pragma unroll
+          for (int r = 0; r < RIN; ++r) v[q][r] = s[SL::off(line, j + r * BPL)];
+        }
+        if constexpr (NS > 1) {
+          const int k = j % NS;
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            C w = ldg_c(&tw[r * k * (L / (NS * R))]);
+            if (SIGN > 0) w.y = -w.y;
+            v[q][r] = cmul(v[q][r], w);
+          }
+        }
+        if constexpr (PRUNE == 1) dft8v_lo<SIGN>(v[q]);
+        else if constexpr (PRUNE == 2) dftR_hi_cut<R, SIGN>(v[q]);
+        else dftR<R, SIGN>(v[q]);
+      }
+    }
   }
-  __syncthreads();
+  if constexpr (EP == 3) {
+    // last pass: outputs j + r NS of each line straight to global memory
+    bool vec = false;
+    if constexpr (VEC) {
+      if (io->vec_out) {
+        vec = true;
+#pragma unroll
+        for (int jj = 0; jj < G::M; ++jj) {
+          const int j = threadIdx.x + jj * NT;
+#pragma unroll
+          for (int r = 0; r < ROUT; ++r) {
+            const int e = j + r * NS;
+            if (e < io->n_out) {
+              C c[NLINES];
+#pragma unroll
+              for (int line = 0; line < NLINES; ++line) c[line] = c_norm(v[line * G::M + jj][r]);
+              float4 w[VW];
+              memcpy(w, c, sizeof(c));
+              float4* dst = reinterpret_cast<float4*>(io->out + (long)e * io->es_out);
+#pragma unroll
+              for (int u = 0; u < VW; ++u) dst[u] = w[u];
+            }
+          }
+        }
+      }
+    }
+    if (!vec) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (BF % NT == 0 || b < BF) {
+          const int line = b / BPL, j = b - line * BPL;
+          if (line < io->nlines) {
+#pragma unroll
+            for (int r = 0; r < ROUT; ++r) {
+              const int e = j + r * NS;
+              if (e < io->n_out) io->out[(long)e * io->es_out + line] = c_norm(v[q][r]);
+            }
+          }
+        }
+      }
+    }
+    return;
+  }
+  if constexpr (EP != 1) __syncthreads();  // (a first pass from global memory read no shared memory)
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int b = threadIdx.x + q * NT;
@@ -356,19 +493,32 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw) {
   __syncthreads();
 }
 
+// radix of the pass that starts from sub-transforms of length NS, and of the last pass
+__host__ __device__ constexpr int pass_radix(int L, int NS) {
+  return (L / NS) % 8 == 0 ? 8 : ((L / NS) % 4 == 0 ? 4 : ((L / NS) % 2 == 0 ? 2 : 3));
+}
+__host__ __device__ constexpr int last_radix(int L) {
+  int NS = 1;
+  while (NS * pass_radix(L, NS) < L) NS *= pass_radix(L, NS);
+  return pass_radix(L, NS);
+}
+
 // Radices 8, then 4 or 2 for the rest of the power of two, then 3 for L = 3 * 2^k.
 // HIN: the upper half of every line is zero padding (the first pass reads the lower half);
 // HOUT: only the lower half of the result is needed (the last pass stores only it, when its
-// radix is even)
-template <typename C, int L, int NS, int SIGN, int NLINES, int NT, bool HIN = false, bool HOUT = false>
-__device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw) {
+// radix is even).  EPF / EPL: the first / last pass's global-memory end (fft_pass's EP).
+template <typename C, int L, int NS, int SIGN, int NLINES, int NT, bool HIN = false, bool HOUT = false, int EPF = 0,
+          int EPL = 0>
+__device__ __forceinline__ void fft_lines(C* s, const C* __restrict__ tw, const ColIO<C>* io = nullptr) {
   if constexpr (NS < L) {
-    constexpr int REM = L / NS;
-    constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
-    static_assert(REM % R == 0, "FFT length must be 2^k or 3 * 2^k");
+    constexpr int R = pass_radix(L, NS);
+    static_assert((L / NS) % R == 0, "FFT length must be 2^k or 3 * 2^k");
     constexpr int PRUNE = (HIN && NS == 1 && R == 8) ? 1 : ((HOUT && NS * R == L && R % 2 == 0) ? 2 : 0);
-    fft_pass<C, L, R, NS, SIGN, NLINES, NT, PRUNE>(s, tw);
-    fft_lines<C, L, NS * R, SIGN, NLINES, NT, false, HOUT>(s, tw);
+    constexpr bool first = NS == 1, last = NS * R == L;
+    static_assert(!(first && last && EPF != 0 && EPL != 0), "one pass cannot take both ends");
+    constexpr int EP = first && EPF != 0 ? EPF : (last ? EPL : 0);
+    fft_pass<C, L, R, NS, SIGN, NLINES, NT, PRUNE, EP>(s, tw, io);
+    fft_lines<C, L, NS * R, SIGN, NLINES, NT, false, HOUT, 0, EPL>(s, tw, io);
   }
 }
 
@@ -563,12 +713,34 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
   const long tiles = (a.inner + TC - 1) / TC;
   const long o = blockIdx.x / tiles;
   const long c0 = (blockIdx.x - o * tiles) * TC;
-  const C* in = reinterpret_cast<const C*>(a.in) + o * a.in_os + c0;
-  const int n_in = (PR && MODE != 1) ? L / 2 : a.n_in;
-  {
+  ColIO<C> io;
+  io.in = reinterpret_cast<const C*>(a.in) + o * a.in_os + c0;
+  io.out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
+  io.es_in = a.in_es;
+  io.es_out = a.out_es;
+  io.n_in = (PR && MODE != 1) ? L / 2 : a.n_in;
+  io.n_out = (PR && MODE != 0) ? L / 2 : a.n_out;
+  io.nlines = a.inner - c0 < TC ? (int)(a.inner - c0) : TC;
+  io.vec_in = io.nlines == TC && (reinterpret_cast<uintptr_t>(io.in) & 15) == 0 && (a.in_es * sizeof(C)) % 16 == 0;
+  io.vec_out = io.nlines == TC && (reinterpret_cast<uintptr_t>(io.out) & 15) == 0 && (a.out_es * sizeof(C)) % 16 == 0;
+  io.sym = reinterpret_cast<const C*>(a.sym);
+  io.c0 = c0;
+  io.inner = a.inner;
+  io.n1 = a.n + 1;
+  io.d = a.d;
+  // The first pass loads the tile straight from global memory and the last one stores it
+  // there when a thread's accesses stay coalesced: it holds every line of its butterflies
+  // (16-byte vectors across the lines), or one entry of all lines fits a 32-byte sector.
+  // Otherwise consecutive threads fill and drain consecutive lines through shared memory
+  // (tiles of many short lines).
+  constexpr bool SECTOR = TC * sizeof(C) <= 32;
+  constexpr int EPF = (PassGeo<L, 8, TC, NT>::ALL_LINES || SECTOR) ? 1 : 0;
+  constexpr int EPL = (PassGeo<L, last_radix(L), TC, NT>::ALL_LINES || SECTOR) ? 3 : 0;
+  static_assert(L % 8 == 0, "column passes: the first radix is 8");
+  if constexpr (EPF == 0) {
     // LB independent loads in flight per thread before the first shared-memory store
     constexpr int LB = 4;
-    const int tot = n_in * TC;
+    const int tot = io.n_in * TC;
     for (int base = threadIdx.x; base < tot; base += NT * LB) {
       C v[LB];
 #pragma unroll
@@ -577,7 +749,7 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
         v[u] = czero<C>();
         if (idx < tot) {
           const int e = idx / TC, c = idx - e * TC;
-          if (c0 + c < a.inner) v[u] = in[(long)e * a.in_es + c];
+          if (c < io.nlines) v[u] = io.in[(long)e * a.in_es + c];
         }
       }
 #pragma unroll
@@ -589,23 +761,21 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
         }
       }
     }
-  }
-  if (!(PR && MODE != 1) && n_in < L) {
-    const int padn = L - n_in;
-    for (int idx = threadIdx.x; idx < padn * TC; idx += NT) {
-      const int e = n_in + idx / TC, c = idx % TC;
-      s[SL::off(c, e)] = czero<C>();
+    if (!(PR && MODE != 1) && io.n_in < L) {
+      const int padn = L - io.n_in;
+      for (int idx = threadIdx.x; idx < padn * TC; idx += NT) {
+        const int e = io.n_in + idx / TC, c = idx % TC;
+        s[SL::off(c, e)] = czero<C>();
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if constexpr (MODE == 0) {
-    fft_lines<C, L, 1, -1, TC, NT, PR, false>(s, tw);
+    fft_lines<C, L, 1, -1, TC, NT, PR, false, EPF, EPL>(s, tw, &io);
   } else if constexpr (MODE == 1) {
-    fft_lines<C, L, 1, 1, TC, NT, false, PR>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT, false, PR, EPF, EPL>(s, tw, &io);
   } else {
-    fft_lines<C, L, 1, -1, TC, NT, PR, false>(s, tw);
-    const C* __restrict__ sym = reinterpret_cast<const C*>(a.sym);
-    const int n1 = a.n + 1;
+    fft_lines<C, L, 1, -1, TC, NT, PR, false, EPF, 0>(s, tw, &io);
     // symbol values of SB entries loaded together, then applied
     constexpr int SB = 8;
     for (int base = threadIdx.x; base < L * TC; base += NT * SB) {
@@ -614,39 +784,27 @@ __global__ void __launch_bounds__(ColShape<C, L>::NT, ColShape<C, L>::MINB) k_co
       for (int u = 0; u < SB; ++u) {
         const int idx = base + u * NT;
         const int e = idx / TC, c = idx - e * TC;
-        const long cc = c0 + c;
         sv[u] = czero<C>();
-        if (idx < L * TC && cc < a.inner) {
-          const int q0 = e <= L - e ? e : L - e;
-          long si;
-          if (a.d == 2) {
-            const int k1 = (int)cc;
-            si = (long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1);
-          } else {
-            const int k1 = (int)(cc / L), k2 = (int)(cc - (long)k1 * L);
-            si = ((long)q0 * n1 + (k1 <= L - k1 ? k1 : L - k1)) * n1 + (k2 <= L - k2 ? k2 : L - k2);
-          }
-          sv[u] = ldg_c(&sym[si]);
-        }
+        if (idx < L * TC && c < io.nlines) sv[u] = col_symbol<C, L>(io, c, e);
       }
 #pragma unroll
       for (int u = 0; u < SB; ++u) {
         const int idx = base + u * NT;
         const int e = idx / TC, c = idx - e * TC;
-        if (idx < L * TC && c0 + c < a.inner) {
+        if (idx < L * TC && c < io.nlines) {
           C& v = s[SL::off(c, e)];
           v = cmul(v, sv[u]);
         }
       }
     }
     __syncthreads();
-    fft_lines<C, L, 1, 1, TC, NT, false, PR>(s, tw);
+    fft_lines<C, L, 1, 1, TC, NT, false, PR, 0, EPL>(s, tw, &io);
   }
-  C* out = reinterpret_cast<C*>(a.out) + o * a.out_os + c0;
-  const int n_out = (PR && MODE != 0) ? L / 2 : a.n_out;
-  for (int idx = threadIdx.x; idx < n_out * TC; idx += NT) {
-    const int e = idx / TC, c = idx - e * TC;
-    if (c0 + c < a.inner) out[(long)e * a.out_es + c] = s[SL::off(c, e)];
+  if constexpr (EPL == 0) {
+    for (int idx = threadIdx.x; idx < io.n_out * TC; idx += NT) {
+      const int e = idx / TC, c = idx - e * TC;
+      if (c < io.nlines) io.out[(long)e * a.out_es + c] = s[SL::off(c, e)];
+    }
   }
 }
 

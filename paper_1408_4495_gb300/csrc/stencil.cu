@@ -5,6 +5,8 @@
 // stores of r are coalesced, and the 3^d neighbours of adjacent points are shared in L1.  The coefficient table (3^d classes x 3^d offsets)
 // is staged in shared memory.  General domains (Sec. 4) give every point its own stencil
 // (PT: row i of an N x 3^d table, read from global memory).
+#include <type_traits>
+
 #include "common.cuh"
 #include "ffloat.cuh"
 #include "kernels.h"
@@ -76,6 +78,105 @@ __global__ void __launch_bounds__(256) k_stencil(int n, int nrhs, const Cin* __r
   }
 }
 
+// 2D FP32 stencil r = [A; B] v (RESID false) and preconditioner residual r2 (RESID true,
+// k_pre_resid's sums) with a rolling window along axis 0: a thread takes one grid column c
+// of one right-hand side over a run of R rows and reads the entries c - 1, c, c + 1 of each
+// row once for the three output rows that use them (three loads per point and array
+// instead of nine).  The 9-point sums keep k_stencil's and k_pre_resid's order; entries
+// outside the grid read as zero.
+template <bool RESID>
+__device__ __forceinline__ void roll_row(const float2* __restrict__ vr, const float2* __restrict__ zr,
+                                         const float* __restrict__ w2m, int n, int a0, int c, float2* d, float2* e) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    d[t] = make_float2(0.f, 0.f);
+    e[t] = make_float2(0.f, 0.f);
+  }
+  if (a0 < 0 || a0 >= n) return;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int a2 = c + t - 1;
+    if (a2 < 0 || a2 >= n) continue;
+    const long j = (long)a0 * n + a2;
+    if constexpr (RESID) {
+      const float2 zv = __ldg(&zr[j]);
+      d[t] = csub(__ldg(&vr[j]), zv);
+      const float w = __ldg(&w2m[j]);
+      e[t] = make_float2(w * zv.x, w * zv.y);
+    } else {
+      d[t] = __ldg(&vr[j]);
+    }
+  }
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(256, 3) k_stencil2_roll(int n, int nrhs, int R, int nseg, const float2* __restrict__ v,
+                                                       const float2* __restrict__ z, float2* __restrict__ out,
+                                                       const float2* __restrict__ alpha,
+                                                       const double2* __restrict__ cint, const float* __restrict__ w2m) {
+  __shared__ float2 sa[81];
+  __shared__ float2 sc[9];
+  for (int i = threadIdx.x; i < 81; i += blockDim.x) sa[i] = alpha[i];
+  if constexpr (RESID) {
+    for (int i = threadIdx.x; i < 9; i += blockDim.x) sc[i] = make_float2((float)cint[i].x, (float)cint[i].y);
+  }
+  __syncthreads();
+  const long per = (long)nseg * n;  // threads per right-hand side
+  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= per * nrhs) return;
+  const long rhs = g / per;
+  const int rem = (int)(g - rhs * per), seg = rem / n, c = rem - seg * n;
+  const int r0 = seg * R, r1 = r0 + R < n ? r0 + R : n;
+  const int k2 = c == 0 ? 0 : (c == n - 1 ? 2 : 1);
+  const long N = (long)n * n;
+  const float2* vr = v + rhs * N;
+  const float2* zr = RESID ? z + rhs * N : nullptr;
+  float2* o = out + rhs * N;
+  float2 D[3][3], E[3][3];  // rows a0 - 1, a0, a0 + 1; columns c - 1, c, c + 1
+  roll_row<RESID>(vr, zr, w2m, n, r0 - 1, c, D[0], E[0]);
+  roll_row<RESID>(vr, zr, w2m, n, r0, c, D[1], E[1]);
+#pragma unroll 2
+  for (int a0 = r0; a0 < r1; ++a0) {
+    roll_row<RESID>(vr, zr, w2m, n, a0 + 1, c, D[2], E[2]);
+    const int k0 = a0 == 0 ? 0 : (a0 == n - 1 ? 2 : 1);
+    const float2* al = sa + (k0 * 3 + k2) * 9;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      acc = cfma(acc, al[t], D[t / 3][t % 3]);
+      if constexpr (RESID) acc = cfms(acc, sc[t], E[t / 3][t % 3]);
+    }
+    o[(long)a0 * n + c] = acc;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      D[0][t] = D[1][t];
+      D[1][t] = D[2][t];
+      E[0][t] = E[1][t];
+      E[1][t] = E[2][t];
+    }
+  }
+}
+
+// rows per thread of k_stencil2_roll: runs of up to 32 rows, shorter while the grid would
+// give fewer than about 2048 threads per SM
+static int roll_rows(int n, int nrhs) {
+  int R = 32;
+  while (R > 1 && (long)nrhs * n * ((n + R - 1) / R) < 152L * 2048) R /= 2;
+  return R;
+}
+
+static void launch_roll(bool resid, int n, int nrhs, const float2* v, const float2* z, float2* out, const float2* alpha,
+                        const double2* cint, const float* w2m, cudaStream_t st) {
+  const int R = roll_rows(n, nrhs), nseg = (n + R - 1) / R;
+  const long threads = (long)nrhs * nseg * n;
+  if (threads == 0) return;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  if (resid)
+    LS_LAUNCH("stencil_c64", st, k_stencil2_roll<true><<<blocks, 256, 0, st>>>(n, nrhs, R, nseg, v, z, out, alpha, cint, w2m));
+  else
+    LS_LAUNCH("stencil_c64", st, k_stencil2_roll<false><<<blocks, 256, 0, st>>>(n, nrhs, R, nseg, v, z, out, alpha, cint, w2m));
+}
+
 static unsigned stencil_blocks(int d, int n, int nrhs) {
   const long lines = (d == 2 ? (long)n : (long)n * n) * nrhs;
   const int lpb = n < 256 ? 256 / n : 1;
@@ -87,6 +188,12 @@ static unsigned stencil_blocks(int d, int n, int nrhs) {
 template <typename Cin, typename Cout>
 void stencil_apply(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, long rs_r, const void* alpha,
                    cudaStream_t st) {
+  if constexpr (std::is_same<Cin, float2>::value && std::is_same<Cout, float2>::value) {
+    if (d == 2 && rs_i == 1 && rs_r == (long)n * n) {
+      launch_roll(false, n, nrhs, v, nullptr, r, (const float2*)alpha, nullptr, nullptr, st);
+      return;
+    }
+  }
   const unsigned blocks = stencil_blocks(d, n, nrhs);
   if (blocks == 0) return;
   const char* cls = sizeof(Cout) == 8 ? "stencil_c64" : "stencil_c128";
@@ -170,6 +277,10 @@ __global__ void k_add_to(float2* __restrict__ z, const float2* __restrict__ dz, 
 
 void pre_resid(int d, int n, int nrhs, const float2* v, const float2* z, float2* r2, const float2* alpha32,
                const double2* cint64, const float* w2m32, cudaStream_t st) {
+  if (d == 2) {
+    launch_roll(true, n, nrhs, v, z, r2, alpha32, cint64, w2m32, st);
+    return;
+  }
   const unsigned blocks = stencil_blocks(d, n, nrhs);
   if (blocks == 0) return;
   if (d == 2)

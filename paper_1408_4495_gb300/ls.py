@@ -33,7 +33,7 @@ EXPORTS = ["ls_setup", "ls_setup_laplace", "ls_factor", "ls_rhs_plane_wave", "ls
            "ls_export_factors", "ls_import_factors",
            "ls_last_error", "ls_free",
            "ls_kernel_table", "ls_stencils", "ls_apply", "ls_stencil_apply", "ls_precond", "ls_get_nd_stats",
-           "ls_profile_start", "ls_profile_stop", "ls_autotune", "ls_tune_info", "ls_set_tune", "ls_apply_noalloc"]
+           "ls_profile_start", "ls_profile_stop", "ls_autotune", "ls_tune_info", "ls_set_tune", "ls_apply_noalloc", "ls_set_precond_refine"]
 
 
 class LsGrid(ctypes.Structure):
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ls_autotune.argtypes = [vp, ip, ctypes.c_char_p, ip]
     lib.ls_tune_info.argtypes = [vp, ctypes.c_char_p, ip]
     lib.ls_set_tune.argtypes = [vp, ctypes.c_char_p]
+    lib.ls_set_precond_refine.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.ls_profile_start.argtypes = [ctypes.c_char_p]
     lib.ls_profile_stop.argtypes = [ctypes.c_char_p, ip]
     for name in EXPORTS:
@@ -453,6 +454,14 @@ class Solver:
         """ls_set_tune: apply launch-shape choices (any keys of tune()) to this context."""
         import json
         self._check(self.lib.ls_set_tune(self.h, json.dumps(choices).encode()))
+
+    def precond_refine(self, mode: int = -2) -> float:
+        """ls_set_precond_refine: the FP32 preconditioner's refinement step (1 on, 0 off,
+        -1 automatic, -2 unchanged); returns the current factorization's estimate E (-1:
+        none yet)."""
+        err = ctypes.c_double(-1.0)
+        self._check(self.lib.ls_set_precond_refine(self.h, int(mode), ctypes.byref(err)))
+        return err.value
 
     def nd_stats(self) -> dict:
         s = LsNdStats()

@@ -109,6 +109,27 @@ def test_operator_apply_float_float(LS, d, n, freq):
     assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
 
 
+# FFT lengths 1024 and 2048 (the benchmark's): the column passes' tiles are read and written
+# as 16-byte vectors holding every line of an entry; the FP32 and float-float arithmetics
+# against the FP64 oracle, elementwise for the float-float one
+@pytest.mark.parametrize("n,freq", [(512, 64.0), (1024, 128.0)])
+@pytest.mark.parametrize("prec", ["mixed", "ff"])
+def test_operator_apply_long_lines(LS, n, freq, prec):
+    omega = 2 * np.pi * freq
+    m = medium(2, n)
+    nrhs = 2
+    x = rand_c((nrhs, n, n), 13)
+    kt = O.kernel_table(n, 2, omega)
+    ref = np.array([O.apply_operator(kt, omega, m, x[j]) for j in range(nrhs)])
+    with LS.Solver(m, omega, mixed=True) as s:
+        y = s.apply(x, prec=LS.LS_PREC_MIXED if prec == "mixed" else LS.LS_PREC_FF)
+    if prec == "mixed":
+        assert rel(y, ref) < 2e-5
+    else:
+        assert rel(y, ref) < 1e-11
+        assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("d,n,freq", CASES)
 @pytest.mark.parametrize("mixed", [False, True])
 def test_rhs_plane_wave(LS, d, n, freq, mixed):
@@ -167,6 +188,41 @@ def test_preconditioner(LS, d, n, freq, mixed):
         zj = z[j].reshape(-1)
         be = np.linalg.norm(M @ zj - S @ x[j].reshape(-1)) / (normM * np.linalg.norm(zj))
         assert be < bound, be
+
+
+# The FP32 preconditioner's refinement step (its residual kernel reads every row's three
+# neighbours once for three output rows): one step contracts the backward error of
+# M z = [A;B] x (to the FP32 level where the unrefined error is small) and lowers the forward
+# error; n = 128 with 3 right-hand sides (one row per thread) and n = 256 with 16 (runs of
+# two rows).
+@pytest.mark.parametrize("n,freq,nrhs", [(128, 16.0, 3), (256, 32.0, 16)])
+def test_preconditioner_refinement(LS, n, freq, nrhs):
+    omega = 2 * np.pi * freq
+    m = medium(2, n)
+    x = rand_c((nrhs, n, n), 14)
+    sten, cint = O.all_stencils(n, 2, omega, 2)
+    M, S = O.assemble(n, 2, omega, m, sten, cint)
+    P = O.Preconditioner(M, S, n, 2)
+    x32 = x.astype(np.complex64).astype(np.complex128)  # the refined path rounds its input
+    ref = np.array([P(x32[j].reshape(-1)).reshape(n, n) for j in range(nrhs)])
+    with LS.Solver(m, omega, mixed=True) as s:
+        s.factor()
+        assert s.precond_refine(0) == -1.0
+        z0 = s.precond(x32)
+        s.precond_refine(1)
+        z1 = s.precond(x32)
+        s.factor()  # a forced mode persists across factorizations
+        z2 = s.precond(x32)
+        with pytest.raises(LS.LsError):
+            s.precond_refine(2)
+    assert np.array_equal(z1, z2)
+    normM = abs(M).sum(axis=1).max()
+    for j in range(nrhs):
+        rhs = S @ x32[j].reshape(-1)
+        be0 = np.linalg.norm(M @ z0[j].reshape(-1) - rhs) / (normM * np.linalg.norm(z0[j]))
+        be1 = np.linalg.norm(M @ z1[j].reshape(-1) - rhs) / (normM * np.linalg.norm(z1[j]))
+        assert be1 < 0.2 * be0, (be0, be1)
+        assert rel(z1[j], ref[j]) < rel(z0[j], ref[j]), (rel(z0[j], ref[j]), rel(z1[j], ref[j]))
 
 
 def test_plain_fp64_solve_matches_oracle_iterates():
