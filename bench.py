@@ -292,7 +292,7 @@ def algorithmic_bytes(cls, w, nd, counts, steps, rhs=None):
                  read and written once (N c each), spread over the sweep's launches (one per level
                  on the CUDA cores, three -- gather, tensor-core product, scatter -- per level on
                  the tensor cores: the launches per sweep come from ``counts``, one application
-                 being the two nd_items launches around its sweeps; one per level without counts).
+                 being one nd_items_out launch after its sweeps; one per level without counts).
     ``rhs``: right-hand sides per launch (default: all of the workload's)."""
     n, N, R = w.n, w.n ** w.d, (w.nrhs if rhs is None else rhs)
     c = 8 if cls.endswith("_c64") else 16
@@ -332,10 +332,10 @@ def sweep_bytes(cls, w, nd, rhs=None):
 
 def sweep_launches(cls, nd, counts):
     """Launches per sweep: from the class counts when they include the applications' item
-    launches, else one per level."""
-    items = (counts or {}).get("nd_items" + cls[6:], 0)
-    if items and (counts or {}).get(cls, 0):
-        return counts[cls] / (items / 2)
+    output launches (one per application), else one per level."""
+    apps = (counts or {}).get("nd_items_out" + cls[6:], 0)
+    if apps and (counts or {}).get(cls, 0):
+        return counts[cls] / apps
     return nd["levels"]
 
 

@@ -273,6 +273,21 @@ void op_apply_ff(ls_ctx* c, int nrhs, const double2* u, double2* y, const double
 // z = M^{-1} [A;B] v for FP64 input v; z in the factor precision C
 // z = M^{-1} [A;B] v for v in FP64 or FP32 pairs; z in the factor precision C
 template <typename C, typename Cv = double2> void precond_apply(ls_ctx* c, int nrhs, const Cv* v, C* z) {
+  if constexpr (sizeof(C) == 8 && std::is_same<Cv, float2>::value) {
+    if (c->d == 2 && !c->general && c->pre_refine >= 0 && nrhs <= ls::nd_items_max()) {
+      // 2D FP32 after the estimate: the stencil sums go straight into the solve's items
+      const int rc = ls::nd_item_width(nrhs);
+      float2* T = static_cast<float2*>(ls::nd_items(c->nd));
+      ls::stencil_items_2d(c->n, nrhs, rc, v, nullptr, T, c->alpha32, nullptr, nullptr, c->st);
+      ls::nd_solve_items<C>(c->nd, nrhs, z, c->st, false);
+      if (c->pre_refine == 1) {
+        // z += M^{-1} ([A;B] v - M z)
+        ls::stencil_items_2d(c->n, nrhs, rc, v, z, T, c->alpha32, c->cint64, c->w2m32, c->st);
+        ls::nd_solve_items<C>(c->nd, nrhs, z, c->st, true);
+      }
+      return;
+    }
+  }
   C* r = buf<C>(c, sizeof(C) == 8 ? "pre_r32" : "pre_r64", (size_t)nrhs * c->N);
   if (c->general) {
     const void* apt = sizeof(C) == 8 ? (const void*)c->apt32 : (const void*)c->apt64;
@@ -285,12 +300,10 @@ template <typename C, typename Cv = double2> void precond_apply(ls_ctx* c, int n
   if constexpr (sizeof(C) == 8 && std::is_same<Cv, float2>::value) {
     if (c->pre_refine == 1 && !c->general) {
       // one step of iterative refinement of z = M^{-1} [A;B] v with the FP32 factors:
-      // z += M^{-1} ([A;B] v - M z)
+      // z += M^{-1} ([A;B] v - M z), the correction added by the solve's last launch
       C* r2 = buf<C>(c, "pre_r2", (size_t)nrhs * c->N);
-      C* z2 = buf<C>(c, "pre_z2", (size_t)nrhs * c->N);
       ls::pre_resid(c->d, c->n, nrhs, v, z, r2, c->alpha32, c->cint64, c->w2m32, c->st);
-      ls::nd_solve<C>(c->nd, nrhs, r2, z2, c->st);
-      ls::add_to(z, z2, (long)nrhs * c->N, c->st);
+      ls::nd_solve<C>(c->nd, nrhs, r2, z, c->st, true);
     }
   }
 }

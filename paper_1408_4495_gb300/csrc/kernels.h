@@ -116,8 +116,10 @@ void stencil_apply_pt(int d, int n, int nrhs, const Cin* v, Cout* r, long rs_i, 
 // r2 = [A;B] v - M z (FP32), the residual of a preconditioner application (class stencils)
 void pre_resid(int d, int n, int nrhs, const float2* v, const float2* z, float2* r2, const float2* alpha32,
                const double2* cint64, const float* w2m32, cudaStream_t st);
-// z += dz
-void add_to(float2* z, const float2* dz, long tot, cudaStream_t st);
+// 2D, FP32: [A;B] v (z == nullptr) or [A;B] v - M z written straight into the solve's item
+// layout T[group][N][rc] (right-hand sides past nrhs zero; rc = nd_item_width(nrhs))
+void stencil_items_2d(int n, int nrhs, int rc, const float2* v, const float2* z, float2* T, const float2* alpha32,
+                      const double2* cint64, const float* w2m32, cudaStream_t st);
 
 // ---------------------------------------------------------------- nested dissection (nd.cu)
 struct NdPlan;  // opaque: host symbolic + device index arrays
@@ -167,8 +169,16 @@ struct NdTune {
 constexpr int SWEEP_CTAS_MAX = 4;  // the solve's partial-sum buffers are sized for this target
 void nd_set_tune(NdPlan* p, const NdTune& t);
 NdTune nd_get_tune(const NdPlan* p);
-// x = M^{-1} r for nrhs vectors; r and x in layout [nrhs][N] (path precision)
-template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st);
+// x = M^{-1} r (accumulate: x += M^{-1} r) for nrhs vectors; r and x in layout [nrhs][N]
+// (path precision)
+template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st, bool accumulate = false);
+// The solve's item buffer T[group][N][RC] (grid points in grid order, RC right-hand sides
+// per group) for up to nd_items_max() right-hand sides: a producer that writes it directly
+// then runs nd_solve_items instead of nd_solve (x = M^{-1} r, or x += M^{-1} r).
+void* nd_items(NdPlan* p);
+int nd_item_width(int nrhs);
+int nd_items_max();
+template <typename C> void nd_solve_items(NdPlan* p, int nrhs, C* x, cudaStream_t st, bool accumulate);
 size_t nd_device_bytes(const NdPlan* p, int elem_bytes);
 // bytes of the factored fronts (the factorization's whole state), and their copy to / from a
 // host array of that size (synchronous on st)

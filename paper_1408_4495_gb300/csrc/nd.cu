@@ -2339,8 +2339,9 @@ template <typename C, int RC> __global__ void __launch_bounds__(256) k_items_in(
   }
 }
 
-// T[group][N][RC] -> x[rhs][N] for the nr right-hand sides
-template <typename C, int RC> __global__ void __launch_bounds__(256) k_items_out(const C* T, C* __restrict__ x, int nr, long N) {
+// T[group][N][RC] -> x[rhs][N] for the nr right-hand sides (ACC: x += T)
+template <typename C, int RC, bool ACC>
+__global__ void __launch_bounds__(256) k_items_out(const C* T, C* __restrict__ x, int nr, long N) {
   constexpr int TP = 512 / RC;
   __shared__ C s[RC][TP + 1];
   pdl_wait();
@@ -2357,7 +2358,10 @@ template <typename C, int RC> __global__ void __launch_bounds__(256) k_items_out
     const int j = e / TP, ii = e % TP;
     const long i = i0 + ii;
     const int rhs = g * RC + j;
-    if (i < N && rhs < nr) x[(size_t)rhs * N + i] = s[j][ii];
+    if (i < N && rhs < nr) {
+      if constexpr (ACC) x[(size_t)rhs * N + i] = cadd(x[(size_t)rhs * N + i], s[j][ii]);
+      else x[(size_t)rhs * N + i] = s[j][ii];
+    }
   }
 }
 
@@ -2760,15 +2764,16 @@ template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int 
 }
 
 template <typename C, int RC>
-static void solve_chunk(NdPlan* p, int nr, const C* r, C* x, cudaStream_t st) {
+static void solve_chunk(NdPlan* p, int nr, const C* r, C* x, cudaStream_t st, bool acc) {
   const int depth = (int)p->lev.size();
   const int ng = (nr + RC - 1) / RC;
   const bool f32 = sizeof(C) == 8;
   C* T = reinterpret_cast<C*>(p->T);
   constexpr int TP = 512 / RC;
   const dim3 tgrid((unsigned)((p->N + TP - 1) / TP), ng);
-  LS_LAUNCH(f32 ? "nd_items_c64" : "nd_items_c128", st,
-            launch_pdl(k_items_in<C, RC>, tgrid, dim3(256), 0, st, r, T, nr, p->N));
+  if (r != nullptr)  // (else the items are in T already)
+    LS_LAUNCH(f32 ? "nd_items_c64" : "nd_items_c128", st,
+              launch_pdl(k_items_in<C, RC>, tgrid, dim3(256), 0, st, r, T, nr, p->N));
   for (int l = depth - 1; l >= 0; --l) {
     prof_tag(l);
     launch_sweep<C, RC, 0>(p, l, T, ng, st);
@@ -2778,18 +2783,24 @@ static void solve_chunk(NdPlan* p, int nr, const C* r, C* x, cudaStream_t st) {
     launch_sweep<C, RC, 1>(p, l, T, ng, st);
   }
   prof_tag(-1);
-  LS_LAUNCH(f32 ? "nd_items_c64" : "nd_items_c128", st,
-            launch_pdl(k_items_out<C, RC>, tgrid, dim3(256), 0, st, (const C*)T, x, nr, p->N));
+  // (its own class: one launch per application, whether or not the items came from k_items_in)
+  if (acc)
+    LS_LAUNCH(f32 ? "nd_items_out_c64" : "nd_items_out_c128", st,
+              launch_pdl(k_items_out<C, RC, true>, tgrid, dim3(256), 0, st, (const C*)T, x, nr, p->N));
+  else
+    LS_LAUNCH(f32 ? "nd_items_out_c64" : "nd_items_out_c128", st,
+              launch_pdl(k_items_out<C, RC, false>, tgrid, dim3(256), 0, st, (const C*)T, x, nr, p->N));
 }
 
-template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st) {
+// x = M^{-1} r, or x += M^{-1} r (accumulate: the refinement step's correction)
+template <typename C> void nd_solve(NdPlan* p, int nrhs, const C* r, C* x, cudaStream_t st, bool accumulate) {
   if (!p->F || p->F_bytes != (int)sizeof(C)) LS_FAIL(ESTATE_, "preconditioner not factored in this precision");
   for (int c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
     const int nr = std::min(SOLVE_CHUNK, nrhs - c0);
     const C* rr = r + (size_t)c0 * p->N;
     C* xx = x + (size_t)c0 * p->N;
-    if (nr <= 4) solve_chunk<C, 4>(p, nr, rr, xx, st);
-    else solve_chunk<C, 16>(p, nr, rr, xx, st);
+    if (nd_item_width(nr) == 4) solve_chunk<C, 4>(p, nr, rr, xx, st, accumulate);
+    else solve_chunk<C, 16>(p, nr, rr, xx, st, accumulate);
   }
 }
 
@@ -2801,7 +2812,20 @@ template void nd_factor_launch<float2>(NdPlan*, const void*, const void*, const 
                                        const void*, const unsigned char*);
 template void nd_factor_launch<double2>(NdPlan*, const void*, const void*, const void*, cudaStream_t, cudaEvent_t,
                                         const void*, const unsigned char*);
-template void nd_solve<float2>(NdPlan*, int, const float2*, float2*, cudaStream_t);
-template void nd_solve<double2>(NdPlan*, int, const double2*, double2*, cudaStream_t);
+void* nd_items(NdPlan* p) { return p->T; }
+int nd_item_width(int nrhs) { return nrhs <= 4 ? 4 : 16; }
+int nd_items_max() { return SOLVE_CHUNK; }
+
+template <typename C> void nd_solve_items(NdPlan* p, int nrhs, C* x, cudaStream_t st, bool accumulate) {
+  if (!p->F || p->F_bytes != (int)sizeof(C)) LS_FAIL(ESTATE_, "preconditioner not factored in this precision");
+  if (nrhs < 1 || nrhs > SOLVE_CHUNK) LS_FAIL(EINVAL_, "nd_solve_items: %d right-hand sides (1..%d)", nrhs, SOLVE_CHUNK);
+  if (nd_item_width(nrhs) == 4) solve_chunk<C, 4>(p, nrhs, nullptr, x, st, accumulate);
+  else solve_chunk<C, 16>(p, nrhs, nullptr, x, st, accumulate);
+}
+
+template void nd_solve_items<float2>(NdPlan*, int, float2*, cudaStream_t, bool);
+template void nd_solve_items<double2>(NdPlan*, int, double2*, cudaStream_t, bool);
+template void nd_solve<float2>(NdPlan*, int, const float2*, float2*, cudaStream_t, bool);
+template void nd_solve<double2>(NdPlan*, int, const double2*, double2*, cudaStream_t, bool);
 
 }  // namespace ls

@@ -177,6 +177,99 @@ static void launch_roll(bool resid, int n, int nrhs, const float2* v, const floa
     LS_LAUNCH("stencil_c64", st, k_stencil2_roll<false><<<blocks, 256, 0, st>>>(n, nrhs, R, nseg, v, z, out, alpha, cint, w2m));
 }
 
+// The same sums written straight into the solve's item layout T[group][N][RC] (right-hand
+// side j of group g at T[(g N + i) RC + j], sides past nrhs zero), so that the solve needs no
+// transposition pass: a CTA takes CW = 256 / RC columns of the RC right-hand sides of one
+// group over a run of R rows (warps read whole 128-byte runs of a row of one right-hand
+// side), and each output row goes through a shared-memory tile (double-buffered: one
+// barrier per row) to contiguous CW x RC stores.
+template <bool RESID, int RC>
+__global__ void __launch_bounds__(256, 3) k_stencil2_items(int n, int nrhs, int R, int ctiles,
+                                                           const float2* __restrict__ v, const float2* __restrict__ z,
+                                                           float2* __restrict__ T, const float2* __restrict__ alpha,
+                                                           const double2* __restrict__ cint,
+                                                           const float* __restrict__ w2m) {
+  constexpr int CW = 256 / RC;
+  __shared__ float2 sa[81];
+  __shared__ float2 sc[9];
+  __shared__ float2 tile[2][CW * (RC + 1)];
+  for (int i = threadIdx.x; i < 81; i += blockDim.x) sa[i] = alpha[i];
+  if constexpr (RESID) {
+    for (int i = threadIdx.x; i < 9; i += blockDim.x) sc[i] = make_float2((float)cint[i].x, (float)cint[i].y);
+  }
+  __syncthreads();
+  const int ct = (int)(blockIdx.x % ctiles), seg = (int)(blockIdx.x / ctiles), g = (int)blockIdx.y;
+  const int j = threadIdx.x / CW, cl = threadIdx.x - j * CW;
+  const int c = ct * CW + cl, rhs = g * RC + j;
+  const bool act = c < n && rhs < nrhs;
+  const int r0 = seg * R, r1 = r0 + R < n ? r0 + R : n;
+  const int k2 = c == 0 ? 0 : (c == n - 1 ? 2 : 1);
+  const long N = (long)n * n;
+  const float2* vr = v + (long)(act ? rhs : 0) * N;
+  const float2* zr = RESID ? z + (long)(act ? rhs : 0) * N : nullptr;
+  // the writer's entry of the tile: column oc, right-hand side oj
+  const int oc = threadIdx.x / RC, oj = threadIdx.x - oc * RC;
+  float2* Tg = T + (size_t)g * N * RC;
+  float2 D[3][3], E[3][3];
+  for (int t = 0; t < 9; ++t) D[t / 3][t % 3] = E[t / 3][t % 3] = make_float2(0.f, 0.f);
+  if (act) {
+    roll_row<RESID>(vr, zr, w2m, n, r0 - 1, c, D[0], E[0]);
+    roll_row<RESID>(vr, zr, w2m, n, r0, c, D[1], E[1]);
+  }
+  for (int a0 = r0; a0 < r1; ++a0) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (act) {
+      roll_row<RESID>(vr, zr, w2m, n, a0 + 1, c, D[2], E[2]);
+      const int k0 = a0 == 0 ? 0 : (a0 == n - 1 ? 2 : 1);
+      const float2* al = sa + (k0 * 3 + k2) * 9;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        acc = cfma(acc, al[t], D[t / 3][t % 3]);
+        if constexpr (RESID) acc = cfms(acc, sc[t], E[t / 3][t % 3]);
+      }
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        D[0][t] = D[1][t];
+        D[1][t] = D[2][t];
+        E[0][t] = E[1][t];
+        E[1][t] = E[2][t];
+      }
+    }
+    float2* tb = tile[(a0 - r0) & 1];
+    tb[cl * (RC + 1) + j] = acc;
+    __syncthreads();
+    if (ct * CW + oc < n) Tg[((long)a0 * n + ct * CW + oc) * RC + oj] = tb[oc * (RC + 1) + oj];
+  }
+}
+
+static void launch_items(bool resid, int n, int nrhs, int rc, const float2* v, const float2* z, float2* T,
+                         const float2* alpha, const double2* cint, const float* w2m, cudaStream_t st) {
+  const int cw = 256 / rc, ctiles = (n + cw - 1) / cw, ng = (nrhs + rc - 1) / rc;
+  int R = 32;  // runs of up to 32 rows, shorter while the grid would give fewer than ~2048 threads per SM
+  while (R > 1 && (long)ng * ctiles * ((n + R - 1) / R) * 256 < 152L * 2048) R /= 2;
+  const long tiles = (long)ctiles * ((n + R - 1) / R);
+  if (tiles == 0 || ng == 0) return;
+  const dim3 grid((unsigned)tiles, (unsigned)ng);
+#define LS_ITEMS(RS, RCC)                                                                                   \
+  LS_LAUNCH("stencil_c64", st,                                                                            \
+            k_stencil2_items<RS, RCC><<<grid, 256, 0, st>>>(n, nrhs, R, ctiles, v, z, T, alpha, cint, w2m))
+  if (rc == 16) {
+    if (resid) LS_ITEMS(true, 16);
+    else LS_ITEMS(false, 16);
+  } else if (rc == 4) {
+    if (resid) LS_ITEMS(true, 4);
+    else LS_ITEMS(false, 4);
+  } else {
+    LS_FAIL(EINVAL_, "stencil items: group width %d (4 or 16)", rc);
+  }
+#undef LS_ITEMS
+}
+
+void stencil_items_2d(int n, int nrhs, int rc, const float2* v, const float2* z, float2* T, const float2* alpha32,
+                      const double2* cint64, const float* w2m32, cudaStream_t st) {
+  launch_items(z != nullptr, n, nrhs, rc, v, z, T, alpha32, cint64, w2m32, st);
+}
+
 static unsigned stencil_blocks(int d, int n, int nrhs) {
   const long lines = (d == 2 ? (long)n : (long)n * n) * nrhs;
   const int lpb = n < 256 ? 256 / n : 1;
@@ -270,11 +363,6 @@ __global__ void __launch_bounds__(256) k_pre_resid(int n, int nrhs, const float2
   }
 }
 
-__global__ void k_add_to(float2* __restrict__ z, const float2* __restrict__ dz, long tot) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
-    z[e] = cadd(z[e], dz[e]);
-}
-
 void pre_resid(int d, int n, int nrhs, const float2* v, const float2* z, float2* r2, const float2* alpha32,
                const double2* cint64, const float* w2m32, cudaStream_t st) {
   if (d == 2) {
@@ -283,18 +371,9 @@ void pre_resid(int d, int n, int nrhs, const float2* v, const float2* z, float2*
   }
   const unsigned blocks = stencil_blocks(d, n, nrhs);
   if (blocks == 0) return;
-  if (d == 2)
-    LS_LAUNCH("stencil_c64", st, k_pre_resid<2><<<blocks, 256, 0, st>>>(n, nrhs, v, z, r2, alpha32, cint64, w2m32));
-  else
-    LS_LAUNCH("stencil_c64", st, k_pre_resid<3><<<blocks, 256, 0, st>>>(n, nrhs, v, z, r2, alpha32, cint64, w2m32));
+  LS_LAUNCH("stencil_c64", st, k_pre_resid<3><<<blocks, 256, 0, st>>>(n, nrhs, v, z, r2, alpha32, cint64, w2m32));
 }
 
-void add_to(float2* z, const float2* dz, long tot, cudaStream_t st) {
-  long b = (tot + 255) / 256;
-  if (b > 152L * 32) b = 152L * 32;
-  if (b < 1) return;
-  LS_LAUNCH("kr_update_u", st, k_add_to<<<(unsigned)b, 256, 0, st>>>(z, dz, tot));
-}
 
 template void stencil_apply<float2, float2>(int, int, int, const float2*, float2*, long, long, const void*, cudaStream_t);
 template void stencil_apply<double2, float2>(int, int, int, const double2*, float2*, long, long, const void*, cudaStream_t);

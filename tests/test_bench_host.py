@@ -42,11 +42,13 @@ def test_3d_pass_bytes():
 def test_sweep_launches_follow_the_counts():
     """A sweep is one launch per level on the CUDA cores; a tensor-core level adds its gather
     and scatter: the launches per sweep come from the class counts over the applications
-    (two nd_items launches each), else one per level."""
+    (one nd_items_out launch each, whether the items came from a transposition launch or
+    from the fused stencil), else one per level."""
     nd = {"levels": 10, "fwd_factor_bytes": 1e6, "bwd_factor_bytes": 2e6}
     assert bench.sweep_launches("nd_fwd_c64", nd, None) == 10
-    assert bench.sweep_launches("nd_fwd_c64", nd, {"nd_fwd_c64": 42, "nd_items_c64": 6}) == 14
+    assert bench.sweep_launches("nd_fwd_c64", nd, {"nd_fwd_c64": 42, "nd_items_out_c64": 3}) == 14
+    assert bench.sweep_launches("nd_fwd_c64", nd, {"nd_fwd_c64": 42, "nd_items_c64": 1, "nd_items_out_c64": 3}) == 14
     w = bench.workload("2d_bumps_n256_omega2pi32_16rhs")
     N = w.n ** 2
     per = (1e6 + 16 * N * 8 * 2) / 14
-    assert bench.algorithmic_bytes("nd_fwd_c64", w, nd, {"nd_fwd_c64": 42, "nd_items_c64": 6}, 3) == per
+    assert bench.algorithmic_bytes("nd_fwd_c64", w, nd, {"nd_fwd_c64": 42, "nd_items_out_c64": 3}, 3) == per
