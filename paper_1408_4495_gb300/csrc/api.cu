@@ -760,19 +760,21 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     c->w2m32 = dalloc<float>(c->N);
     LS_CUDA(cudaMemcpyAsync(c->w2m64, w64.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, c->st));
     LS_CUDA(cudaMemcpyAsync(c->w2m32, w32.data(), c->N * sizeof(float), cudaMemcpyHostToDevice, c->st));
-    // twiddles exp(-2 pi i m / L)
+    // twiddles: exp(-2 pi i m / L) for the FP64 and float-float passes, the per-pass table of
+    // the FP32 passes (fft_plan.h)
     const int L = c->L;
-    std::vector<double2> t64(L);
-    std::vector<float2> t32(L);
+    std::vector<double2> t64(L), tp;
     for (int q = 0; q < L; ++q) {
       const double a = -2.0 * M_PI * (double)q / (double)L;
       t64[q] = make_double2(std::cos(a), std::sin(a));
-      t32[q] = make_float2((float)t64[q].x, (float)t64[q].y);
     }
+    ls::fft_twiddles(L, tp);
+    std::vector<float2> t32(tp.size());
+    for (size_t q = 0; q < tp.size(); ++q) t32[q] = make_float2((float)tp[q].x, (float)tp[q].y);
     c->tw64 = dalloc<double2>(L);
-    c->tw32 = dalloc<float2>(L);
+    c->tw32 = dalloc<float2>(t32.size());
     LS_CUDA(cudaMemcpyAsync(c->tw64, t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice, c->st));
-    LS_CUDA(cudaMemcpyAsync(c->tw32, t32.data(), L * sizeof(float2), cudaMemcpyHostToDevice, c->st));
+    LS_CUDA(cudaMemcpyAsync(c->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, c->st));
     // Nystrom table quadrant and symbol (Sec. 2.1)
     const long n1 = n + 1;
     const long nq = c->d == 2 ? n1 * n1 : n1 * n1 * n1;
@@ -811,14 +813,14 @@ static ls_status setup_common(const ls_grid* g, double omega, const double* m, b
     c->plan.sym32 = c->sym32;
     c->plan.sym64 = c->sym64;
     {
-      const size_t ntw = 2 * (size_t)L, nsy = 2 * (size_t)nq;
-      c->ffbuf = dalloc<float2>(ntw + nsy + (size_t)c->N);
-      ls::to_ff(reinterpret_cast<const double*>(c->tw64), c->ffbuf, (long)ntw, c->st);
-      ls::to_ff(reinterpret_cast<const double*>(c->sym64), c->ffbuf + ntw, (long)nsy, c->st);
-      ls::to_ff(c->w2m64, c->ffbuf + ntw + nsy, c->N, c->st);
+      const size_t ntwf = 2 * (size_t)L, nsy = 2 * (size_t)nq;  // FP64 components: one float pair each
+      c->ffbuf = dalloc<float2>(ntwf + nsy + (size_t)c->N);
+      ls::to_ff(reinterpret_cast<const double*>(c->tw64), c->ffbuf, (long)ntwf, c->st);
+      ls::to_ff(reinterpret_cast<const double*>(c->sym64), c->ffbuf + ntwf, (long)nsy, c->st);
+      ls::to_ff(c->w2m64, c->ffbuf + ntwf + nsy, c->N, c->st);
       c->plan.twff = c->ffbuf;
-      c->plan.symff = c->ffbuf + ntw;
-      c->plan.w2mff = c->ffbuf + ntw + nsy;
+      c->plan.symff = c->ffbuf + ntwf;
+      c->plan.w2mff = c->ffbuf + ntwf + nsy;
     }
     // stencils (Sec. 3.1), cached per (d, n, b, omega); omega = 0 is the Laplace kernel
     {
@@ -1125,12 +1127,10 @@ ls_status ls_set_medium(ls_ctx* c, const double* m) {
       c->general = false;
       ++c->gen;  // captured graphs hold the per-point tables
     }
-    const long n1 = c->n + 1;
-    const size_t nq = c->d == 2 ? (size_t)(n1 * n1) : (size_t)(n1 * n1 * n1);
-    const size_t ntw = 2 * (size_t)c->L, nsy = 2 * nq;
     LS_CUDA(cudaMemcpyAsync(c->w2m64, w64.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, c->st));
     LS_CUDA(cudaMemcpyAsync(c->w2m32, w32.data(), c->N * sizeof(float), cudaMemcpyHostToDevice, c->st));
-    ls::to_ff(c->w2m64, c->ffbuf + ntw + nsy, c->N, c->st);
+    // the float-float copy where the setup placed it (after the twiddles and the symbol)
+    ls::to_ff(c->w2m64, const_cast<float2*>(static_cast<const float2*>(c->plan.w2mff)), c->N, c->st);
     LS_CUDA(cudaStreamSynchronize(c->st));
     return LS_OK;
   } catch (const Error& e) {

@@ -23,6 +23,7 @@
 
 #include "common.cuh"
 #include "ffloat.cuh"
+#include "fft_plan.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -277,6 +278,22 @@ void point_source(int d, int n, int nrhs, const int* pts, const double2* q, cons
 
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st) {
   LS_LAUNCH("kernel_table", st, k_kernel_quadrant<<<1024, 256, 0, st>>>(ktq, d, n, omega, h));
+}
+
+void fft_twiddles(int L, std::vector<double2>& tw) {
+  tw.assign((size_t)tw_table_size(L), make_double2(0.0, 0.0));
+  for (int NS = 1; NS < L; NS *= pass_radix(L, NS)) {
+    const int R = pass_radix(L, NS);
+    if (NS == 1) continue;  // the first pass has no factors
+    double2* t = tw.data() + tw_pass_offset(L, NS);
+    for (int k = 0; k < NS; ++k)
+      for (int r = 0; r < R; ++r) {
+        // w^{r k}, w = exp(-2 pi i / (NS R)); the exponent reduced mod NS R
+        const long e = ((long)r * k) % ((long)NS * R);
+        const double a = -2.0 * M_PI * (double)e / (double)(NS * R);
+        t[(size_t)k * R + r] = make_double2(std::cos(a), std::sin(a));
+      }
+  }
 }
 
 void build_symbol(const ConvPlan& p, const double2* ktq, double2* sym64, float2* sym32, double2* work,

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "ffloat.cuh"
+#include "fft_plan.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -405,11 +406,38 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw, const C
         }
         if constexpr (NS > 1) {
           const int k = j % NS;
+          if constexpr (std::is_same<C, float2>::value) {
+            float2 w[R];
+            // FP32: the butterfly's factors w^{r k} are one contiguous run of the per-pass
+            // table (fft_plan.h), two per 16-byte load
+            const float2* twk = tw + tw_pass_offset(L, NS) + k * R;
+            if constexpr (R % 2 == 0) {
+              const float4* t4 = reinterpret_cast<const float4*>(twk);
 #pragma unroll
-          for (int r = 1; r < R; ++r) {
-            C w = ldg_c(&tw[r * k * (L / (NS * R))]);
-            if (SIGN > 0) w.y = -w.y;
-            v[q][r] = cmul(v[q][r], w);
+              for (int u = 0; u < R / 2; ++u) {
+                const float4 t = __ldg(t4 + u);
+                w[2 * u] = make_float2(t.x, t.y);
+                w[2 * u + 1] = make_float2(t.z, t.w);
+              }
+            } else {
+#pragma unroll
+              for (int r = 1; r < R; ++r) w[r] = __ldg(twk + r);
+            }
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+              if (SIGN > 0) w[r].y = -w[r].y;
+              v[q][r] = cmul(v[q][r], w[r]);
+            }
+          } else {
+            // FP64 and float-float (16-byte entries): the L-entry table exp(-2 pi i m / L),
+            // whose entries r k L / (NS R) of neighbouring butterflies are close together;
+            // each factor applied as it arrives (fewer live registers)
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+              C w = ldg_c(&tw[r * k * (L / (NS * R))]);
+              if (SIGN > 0) w.y = -w.y;
+              v[q][r] = cmul(v[q][r], w);
+            }
           }
         }
         if constexpr (PRUNE == 1) dft8v_lo<SIGN>(v[q]);
@@ -491,16 +519,6 @@ __device__ __forceinline__ void fft_pass(C* s, const C* __restrict__ tw, const C
     }
   }
   __syncthreads();
-}
-
-// radix of the pass that starts from sub-transforms of length NS, and of the last pass
-__host__ __device__ constexpr int pass_radix(int L, int NS) {
-  return (L / NS) % 8 == 0 ? 8 : ((L / NS) % 4 == 0 ? 4 : ((L / NS) % 2 == 0 ? 2 : 3));
-}
-__host__ __device__ constexpr int last_radix(int L) {
-  int NS = 1;
-  while (NS * pass_radix(L, NS) < L) NS *= pass_radix(L, NS);
-  return pass_radix(L, NS);
 }
 
 // Radices 8, then 4 or 2 for the rest of the power of two, then 3 for L = 3 * 2^k.

@@ -84,6 +84,9 @@ bool tc_enabled();
 // float-float copy of count FP64 reals (dst: 2 * count floats)
 void to_ff(const double* src, void* dst, long count, cudaStream_t st);
 size_t conv_scratch1_elems(int d, int n, int nrhs);
+// the FP32 passes' per-pass twiddle table for lines of length L (layout in fft_plan.h),
+// computed in FP64
+void fft_twiddles(int L, std::vector<double2>& tw);
 size_t conv_scratch2_elems(int d, int n, int nrhs);
 void build_kernel_table(int d, int n, double omega, double h, double2* ktq, cudaStream_t st);
 // Sec. 5: g_r = q_r K delta_{p_r} / h^d for nrhs point sources (pts: nrhs x d grid indices;
