@@ -406,7 +406,10 @@ ls_status ls_profile_stop(char* report, int capacity);
  * how many CTAs per SM the split of a solve sweep level aims at, and the smallest FP32
  * forward and backward solve levels (rows of their products, at least 32) run on the tensor
  * cores, and the largest bottom solve level (columns of its product, up to 256; rows up to
- * 64) run one CTA per front.  A coordinate search
+ * 64) run one CTA per front.  The last three default to -1, automatic per solve: tensor-core
+ * levels from 64 rows in 3D or with more than 16 right-hand sides, none for at most 16 in
+ * 2D; one-CTA-per-front levels up to 256 columns with more than 16 right-hand sides, up to
+ * 64 with at most 16.  A coordinate search
  * keeps each alternative that is more than 2 % faster (the fastest of 2 factorizations / 3
  * solves of nrhs right-hand sides, CUDA events).  The choice is applied to c, kept for every
  * later context of the same (dim, n, prec, kernel) in this process, and, when the
@@ -424,8 +427,8 @@ ls_status ls_profile_stop(char* report, int capacity);
  *   ls_factor uses the factorization choices, the next solve the solve choices (a change of
  *   a factorization choice needs a new ls_factor to take effect).  LS_EINVAL when a value is
  *   out of range (two_level_min <= 0, tc_min_rows < 1, sweep_ctas outside 1..4,
- *   gj_max_own outside 1..32, tcs_min_rows or tcs_bwd_min_rows < 1, small_max_k outside
- *   0..256).
+ *   gj_max_own outside 1..32, tcs_min_rows or tcs_bwd_min_rows neither -1 nor >= 1,
+ *   small_max_k outside -1..256).
  * --------------------------------------------------------------------------------------- */
 ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity);
 ls_status ls_tune_info(const ls_ctx* c, char* report, int capacity);

@@ -1501,21 +1501,21 @@ ls_status ls_autotune(ls_ctx* c, int nrhs, char* report, int capacity) {
       try_solve(t);
     }
     if (mixed) {
-      // forward and backward solve levels on the tensor cores from 64 rows (the default),
-      // from 32, 128 or 256, or none
+      // forward and backward solve levels on the tensor cores: automatic (the default), from
+      // 32, 64, 128 or 256 rows, or none
       for (int bwd = 0; bwd < 2; ++bwd) {
         const int base = bwd ? best.tcs_bwd_min_rows : best.tcs_min_rows;
-        for (int v : {32, 64, 128, 256, 1 << 30}) {
+        for (int v : {-1, 32, 64, 128, 256, 1 << 30}) {
           if (v == base) continue;
           ls::NdTune t = best;
           (bwd ? t.tcs_bwd_min_rows : t.tcs_min_rows) = v;
           try_solve(t);
         }
       }
-      // the bottom levels one CTA per front up to 256 columns (the default), up to 32, 64 or
-      // 128, or none
+      // the bottom levels one CTA per front: automatic (the default), up to 32, 64, 128 or
+      // 256 columns, or none
       const int small_base = best.small_max_k;
-      for (int v : {0, 32, 64, 128, 256}) {
+      for (int v : {-1, 0, 32, 64, 128, 256}) {
         if (v == small_base) continue;
         ls::NdTune t = best;
         t.small_max_k = v;
@@ -1601,9 +1601,11 @@ ls_status ls_set_tune(ls_ctx* c, const char* json) {
     int_key("tc_min_rows", 1, 1 << 30, &t.tc_min_rows);
     int_key("sweep_ctas", 1, ls::SWEEP_CTAS_MAX, &t.sweep_ctas);
     int_key("gj_max_own", 1, 32, &t.gj_max_own);
-    int_key("tcs_min_rows", 1, 1 << 30, &t.tcs_min_rows);
-    int_key("tcs_bwd_min_rows", 1, 1 << 30, &t.tcs_bwd_min_rows);
-    int_key("small_max_k", 0, 256, &t.small_max_k);
+    int_key("tcs_min_rows", -1, 1 << 30, &t.tcs_min_rows);
+    int_key("tcs_bwd_min_rows", -1, 1 << 30, &t.tcs_bwd_min_rows);
+    int_key("small_max_k", -1, 256, &t.small_max_k);
+    if (t.tcs_min_rows == 0 || t.tcs_bwd_min_rows == 0)
+      throw Error{ls::EINVAL_, "tcs_min_rows / tcs_bwd_min_rows: -1 (automatic) or >= 1"};
     factor_wait(c);
     ls::nd_set_tune(c->nd, t);
     ++c->gen;  // the captured graphs hold the old launch sequences

@@ -163,12 +163,20 @@ struct NdTune {
                                  // inner columns) run on the tensor cores
   int sweep_ctas = 2;            // CTAs per SM that the split of a sweep level's columns aims at
   int gj_max_own = 16;           // fronts with at most this many own rows: Gauss-Jordan in one CTA
-  int tcs_min_rows = 64;         // FP32 forward-sweep levels whose products have at least this
-                                 // many rows (and 16 inner columns) run on the tensor cores
-  int tcs_bwd_min_rows = 64;     // the same for the backward sweep
-  int small_max_k = 256;         // FP32 sweep levels with at most 64 product rows and this many
-                                 // columns (up to 256) run one CTA per front (0: none)
+  int tcs_min_rows = -1;         // FP32 forward-sweep levels whose products have at least this
+                                 // many rows (and 16 inner columns) run on the tensor cores;
+                                 // -1: automatic (nd_tcs_min_rows)
+  int tcs_bwd_min_rows = -1;     // the same for the backward sweep
+  int small_max_k = -1;          // FP32 sweep levels with at most 64 product rows and this many
+                                 // columns (up to 256) run one CTA per front (0: none; -1:
+                                 // automatic, nd_small_max_k)
 };
+// The automatic values, per solve (ng groups of 16 right-hand sides): tensor-core solve levels
+// from 64 rows in 3D or with at least two groups, none for one group in 2D (their 16-column
+// products lose to the CUDA-core sweep there); one-CTA-per-front levels up to 256 columns with
+// at least two groups, up to 64 with one.
+int nd_tcs_min_rows(int d, int ng, int tune_value);
+int nd_small_max_k(int ng, int tune_value);
 constexpr int SWEEP_CTAS_MAX = 4;  // the solve's partial-sum buffers are sized for this target
 void nd_set_tune(NdPlan* p, const NdTune& t);
 NdTune nd_get_tune(const NdPlan* p);

@@ -2645,10 +2645,17 @@ __global__ void __launch_bounds__(32 * SMALL_FPC) k_sweep_small(SweepK<float2> S
 }
 
 constexpr int SMALL_MAX_K = 256;
-static bool small_level(const NdPlan* p, int l, int mode) {
+// the automatic values of the solve-level choices (measured: 2D n = 256 with 16 right-hand
+// sides solves 1.9x faster with neither tensor-core levels nor one-CTA-per-front levels past
+// 64 columns than with the 64-right-hand-side choices; 3D n = 64 with 8 keeps its
+// tensor-core levels)
+int nd_tcs_min_rows(int d, int ng, int v) { return v >= 0 ? v : ((d == 3 || ng >= 2) ? 64 : (1 << 30)); }
+int nd_small_max_k(int ng, int v) { return v >= 0 ? v : (ng >= 2 ? SMALL_MAX_K : 64); }
+
+static bool small_level(const NdPlan* p, int l, int mode, int ng) {
   const LevelDev& D = p->lev[l];
   const int rows = mode == 0 ? D.bmax : D.smax, K = mode == 0 ? D.smax : D.bmax + D.smax;
-  return rows > 0 && rows <= 64 && K > 0 && K <= std::min(SMALL_MAX_K, p->tune.small_max_k);
+  return rows > 0 && rows <= 64 && K > 0 && K <= std::min(SMALL_MAX_K, nd_small_max_k(ng, p->tune.small_max_k));
 }
 
 template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, int ng, cudaStream_t st) {
@@ -2702,7 +2709,7 @@ template <int MODE> static void launch_sweep_small(NdPlan* p, int l, float2* T, 
 static bool tcs_level(const NdPlan* p, int l, int mode, int ng) {
   const LevelDev& D = p->lev[l];
   const int rows = tcs_rows(D, mode);
-  const int min_rows = mode == 0 ? p->tune.tcs_min_rows : p->tune.tcs_bwd_min_rows;
+  const int min_rows = nd_tcs_min_rows(p->d, ng, mode == 0 ? p->tune.tcs_min_rows : p->tune.tcs_bwd_min_rows);
   return p->use_tc && tc_enabled() && p->tcs_B && p->tcs_C && rows >= std::max(TCS_MIN_ROWS, min_rows) &&
          tcs_k(D, mode) >= TC_MIN_K && (size_t)D.nf * tcs_k(D, mode) * ng * 16 <= p->tcs_B_elems &&
          (size_t)D.nf * rows * ng * 16 * tcs_split(D, mode).nsplit <= p->tcs_C_elems;
@@ -2750,7 +2757,7 @@ template <typename C, int RC, int MODE> static void launch_sweep(NdPlan* p, int 
       launch_sweep_tc<MODE>(p, l, reinterpret_cast<float2*>(T), ng, st);
       return;
     }
-    if (small_level(p, l, MODE)) {
+    if (small_level(p, l, MODE, ng)) {
       launch_sweep_small<MODE>(p, l, reinterpret_cast<float2*>(T), ng, st);
       return;
     }

@@ -37,8 +37,8 @@ def test_autotune_applies_keeps_and_persists_its_choice(LS, tmp_path, monkeypatc
         assert s.tune() == choice
         assert len(rep["factor_ms"]) >= 4 and all(ms > 0 for _, ms in rep["factor_ms"])
         # sweep split: the base and 2 alternatives; forward and backward solve levels on the
-        # tensor cores: 4 more each; the one-CTA-per-front bottom levels: 4 more
-        assert len(rep["solve_ms"]) == 15 and all(ms > 0 for _, ms in rep["solve_ms"])
+        # tensor cores: 5 more each (the base is automatic); the one-CTA-per-front levels: 5 more
+        assert len(rep["solve_ms"]) == 18 and all(ms > 0 for _, ms in rep["solve_ms"])
         # left factored with the chosen shapes
         g = s.rhs_plane_wave(dirs)
         u, info = s.solve(g, tol=1e-6)
@@ -68,8 +68,12 @@ def test_set_tune_validates_and_applies(LS):
         assert {k: v for k, v in t.items() if k not in ("tcs_min_rows", "sweep_ctas")} == \
             {k: v for k, v in base.items() if k not in ("tcs_min_rows", "sweep_ctas")}
         for bad in ({"sweep_ctas": 5}, {"gj_max_own": 0}, {"two_level_min": -1}, {"tcs_min_rows": 1.5},
-                    {"small_max_k": 257}):
+                    {"small_max_k": 257}, {"small_max_k": -2}, {"tcs_bwd_min_rows": 0}):
             with pytest.raises(LS.LsError) as e:
                 s.set_tune(bad)
             assert e.value.status == LS.LS_EINVAL
         assert s.tune() == t
+        # -1: the automatic choice (the default)
+        assert base["tcs_min_rows"] == base["tcs_bwd_min_rows"] == base["small_max_k"] == -1
+        s.set_tune({"tcs_min_rows": -1})
+        assert s.tune()["tcs_min_rows"] == -1

@@ -359,7 +359,8 @@ OFF = 1 << 30
 GENERIC = {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 0}
 SWEEP_VARIANTS = {"tensor_core": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 0},
                   "one_cta_per_front": {"tcs_min_rows": OFF, "tcs_bwd_min_rows": OFF, "small_max_k": 256},
-                  "default": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 256}}
+                  "both": {"tcs_min_rows": 64, "tcs_bwd_min_rows": 64, "small_max_k": 256},
+                  "automatic": {"tcs_min_rows": -1, "tcs_bwd_min_rows": -1, "small_max_k": -1}}
 
 
 @pytest.mark.parametrize("variant", sorted(SWEEP_VARIANTS))
@@ -395,7 +396,7 @@ def test_sweep_level_kernels(LS, d, n, freq, nrhs, bound, variant):
                           / (normM * np.linalg.norm(z[key][j].reshape(-1))) for j in (0, nrhs - 1))
     print(f"d={d} n={n} {variant}: launches {launches}, backward errors {be}, relative difference "
           f"{rel(z['variant'], z['generic']):.3g}")
-    if SWEEP_VARIANTS[variant]["tcs_min_rows"] < OFF:
+    if 0 < SWEEP_VARIANTS[variant]["tcs_min_rows"] < OFF:
         assert launches["variant"] > launches["generic"]
     assert be["generic"] < bound and be["variant"] < bound
     assert be["variant"] < 5 * be["generic"] + 1e-8
