@@ -341,7 +341,8 @@ ls_status ls_stencils(ls_ctx* c, double* alpha_out, double* c_out);
 ls_status ls_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec);
 
 /* Sec. 2.2 eq. PC, right-hand factor: out = [A;B] in (the 3^d-point stencil of each point's
- * class), in the arithmetic prec. */
+ * class), in the arithmetic prec (LS_PREC_MIXED in 2D rounds in to FP32 first, as the solver's
+ * vectors are). */
 ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, ls_prec prec);
 
 /* Sec. 2.2 eq. PC: out = M^{-1} [A;B] in, with the factors of ls_factor (their precision).

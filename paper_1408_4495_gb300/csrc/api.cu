@@ -1321,8 +1321,16 @@ ls_status ls_stencil_apply(ls_ctx* c, int nrhs, const double* in, double* out, l
     copy_in(c, x, in, tot * sizeof(double2));
     if (prec == LS_PREC_MIXED) {
       float2* y32 = buf<float2>(c, "io_out32", tot);
-      if (c->general) ls::stencil_apply_pt<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->apt32, c->st);
-      else ls::stencil_apply<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->alpha32, c->st);
+      if (c->general) {
+        ls::stencil_apply_pt<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->apt32, c->st);
+      } else if (c->d == 2) {
+        // FP32 input, as in the solver (the 2D FP32 stencil kernel)
+        float2* x32 = buf<float2>(c, "io_in32", tot);
+        ls::cast<double2, float2>(x, x32, tot, c->st);
+        ls::stencil_apply<float2, float2>(c->d, c->n, nrhs, x32, y32, 1, c->N, c->alpha32, c->st);
+      } else {
+        ls::stencil_apply<double2, float2>(c->d, c->n, nrhs, x, y32, 1, c->N, c->alpha32, c->st);
+      }
       ls::cast<float2, double2>(y32, y, tot, c->st);
     } else {
       if (c->general) ls::stencil_apply_pt<double2, double2>(c->d, c->n, nrhs, x, y, 1, c->N, c->apt64, c->st);

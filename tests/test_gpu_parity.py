@@ -158,6 +158,25 @@ def test_stencil_apply(LS, d, n, freq, mixed):
     assert rel(r, ref) < (1e-6 if mixed else 1e-12)
 
 
+# The 2D FP32 stencil kernel (a thread walks one grid column down a run of rows): runs of one
+# row (n = 48, 3 right-hand sides), two (n = 256, 16) and four (n = 512, 8), against the
+# oracle's sparse [A;B] on the FP32-rounded input, elementwise
+@pytest.mark.parametrize("n,freq,nrhs", [(48, 5.0, 3), (256, 32.0, 16), (512, 64.0, 8)])
+def test_stencil_apply_fp32_rows(LS, n, freq, nrhs):
+    omega = 2 * np.pi * freq
+    m = medium(2, n)
+    x = rand_c((nrhs, n, n), 15).astype(np.complex64).astype(np.complex128)
+    sten, cint = O.all_stencils(n, 2, omega, 2)
+    _, S = O.assemble(n, 2, omega, m, sten, cint)
+    ref = np.array([(S @ x[j].reshape(-1)).reshape(n, n) for j in range(nrhs)])
+    with LS.Solver(m, omega, mixed=True) as s:
+        r = s.stencil_apply(x)
+    # FP32 sums of 9 products of FP32 coefficients: |error| <= ~1e-6 of the row's magnitude
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(r - ref)) < 2e-6 * scale
+    assert rel(r, ref) < 1e-6
+
+
 # n = 128 and 256 take the register-resident blocked factorization for their top fronts
 @pytest.mark.parametrize("d,n,freq", CASES + [(2, 128, 16.0), (2, 256, 32.0)])
 @pytest.mark.parametrize("mixed", [False, True])
