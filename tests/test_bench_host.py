@@ -52,3 +52,23 @@ def test_sweep_launches_follow_the_counts():
     N = w.n ** 2
     per = (1e6 + 16 * N * 8 * 2) / 14
     assert bench.algorithmic_bytes("nd_fwd_c64", w, nd, {"nd_fwd_c64": 42, "nd_items_out_c64": 3}, 3) == per
+
+
+def test_recorded_traffic_follows_the_sources(monkeypatch):
+    """The recorded ncu traffic of a sweep is used only while the sources it was captured with
+    are unchanged (sha1 of their regions), and is scaled to the live right-hand sides by the
+    byte model and spread over the sweep's launches."""
+    rec = dict(bench.TRAFFIC["nd_fwd_c64"])
+    rec["sha1"] = bench.source_sha1(rec["src"])
+    assert rec["sha1"] is not None
+    monkeypatch.setitem(bench.TRAFFIC, "nd_fwd_c64", rec)
+    assert bench.recorded_traffic("nd_fwd_c64") == rec["bytes_per_sweep"]
+    nd = {"levels": 17, "fwd_factor_bytes": 1e9, "bwd_factor_bytes": 1.2e9}
+    w = bench.workload("2d_noise_n1024_omega2pi128_64rhs")
+    counts = {"nd_fwd_c64": 41 * 9, "nd_items_out_c64": 9}
+    per = bench.recorded_traffic("nd_fwd_c64", w, nd, 32, counts)
+    scale = bench.sweep_bytes("nd_fwd_c64", w, nd, 32) / bench.sweep_bytes("nd_fwd_c64", w, nd, rec["rhs"])
+    assert np.isclose(per, rec["bytes_per_sweep"] * scale / 41)
+    stale = dict(rec, sha1="0" * 40)
+    monkeypatch.setitem(bench.TRAFFIC, "nd_fwd_c64", stale)
+    assert bench.recorded_traffic("nd_fwd_c64") is None
